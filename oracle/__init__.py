@@ -1,0 +1,238 @@
+"""ctypes view of the CPU oracle (liboracle.so).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py.  The product path never imports this package.
+Every function mirrors one in fro.h; the docstrings there cite the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+i8p = ctypes.POINTER(ctypes.c_int8)
+i32p = ctypes.POINTER(ctypes.c_int32)
+i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mb", ctypes.c_int32), ("mb_reps", ctypes.c_int32), ("adaptive", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class PairResult(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int64), ("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64),
+                ("wA_before", ctypes.c_int64), ("wB_before", ctypes.c_int64), ("wA_after", ctypes.c_int64),
+                ("wB_after", ctypes.c_int64), ("corridor_n", ctypes.c_int32), ("corridor_arcs", ctypes.c_int32),
+                ("accepted", ctypes.c_int32), ("iters", ctypes.c_int32), ("alpha_final", ctypes.c_double),
+                ("status", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("round", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.fro_validate.restype = ctypes.c_int32
+        L.fro_validate.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32]
+        for f in ("fro_total_weight", "fro_max_weight"):
+            getattr(L, f).restype = ctypes.c_int64
+            getattr(L, f).argtypes = [ctypes.c_int32, i32p]
+        L.fro_lmax.restype = ctypes.c_int64
+        L.fro_lmax.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double]
+        L.fro_budget_base.restype = ctypes.c_int64
+        L.fro_budget_base.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+        L.fro_pair_cut.restype = ctypes.c_int64
+        L.fro_pair_cut.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32]
+        L.fro_build.restype = ctypes.c_void_p
+        L.fro_build.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_int64]
+        L.fro_from_network.restype = ctypes.c_void_p
+        L.fro_from_network.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i8p, i32p, i32p, i8p, ctypes.c_int64,
+                                       ctypes.c_int64]
+        L.fro_free.argtypes = [ctypes.c_void_p]
+        L.fro_nc.restype = ctypes.c_int32
+        L.fro_nc.argtypes = [ctypes.c_void_p]
+        L.fro_m.restype = ctypes.c_int32
+        L.fro_m.argtypes = [ctypes.c_void_p]
+        L.fro_export.argtypes = [ctypes.c_void_p, i32p, i32p, i32p, i32p, i8p, i32p, i8p, i32p]
+        L.fro_maxflow.restype = ctypes.c_int64
+        L.fro_maxflow.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        L.fro_flow.argtypes = [ctypes.c_void_p, i64p, i64p]
+        L.fro_residual_sets.argtypes = [ctypes.c_void_p, i8p, i8p, i32p]
+        L.fro_sweep.restype = ctypes.c_int32
+        L.fro_sweep.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, i32p, i64p]
+        L.fro_cut.restype = ctypes.c_int64
+        L.fro_cut.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, i8p, i32p, i32p]
+        L.fro_refine_pair.restype = ctypes.c_int32
+        L.fro_refine_pair.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(Options), ctypes.POINTER(PairResult)]
+        L.fro_rounds.restype = ctypes.c_int32
+        L.fro_rounds.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
+                                 i32p, i32p]
+        L.fro_refine_batch.restype = ctypes.c_int32
+        L.fro_refine_batch.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
+                                       ctypes.POINTER(PairResult), i32p, i32p]
+        L.fro_splitmix64.restype = ctypes.c_uint64
+        L.fro_splitmix64.argtypes = [ctypes.c_uint64]
+        _LIB = L
+    return _LIB
+
+
+def _p(a, t=i32p):
+    return a.ctypes.data_as(t)
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def options(mb=0, mb_reps=1, adaptive=0, max_iters=1, alpha_max=1.0, seed=0):
+    return Options(mb, mb_reps, adaptive, max_iters, alpha_max, seed)
+
+
+def validate(w):
+    return lib().fro_validate(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]),
+                              _p(w["part"]), w["k"])
+
+
+def total_weight(vwgt):
+    return lib().fro_total_weight(len(vwgt), _p(_c32(vwgt)))
+
+
+def lmax(W, maxc, k, eps):
+    return lib().fro_lmax(W, maxc, k, eps)
+
+
+def budget_base(W, k, eps, alpha):
+    return lib().fro_budget_base(W, k, eps, alpha)
+
+
+def pair_cut(w, part, a, b):
+    return lib().fro_pair_cut(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(_c32(part)), a, b)
+
+
+def splitmix64(x):
+    return lib().fro_splitmix64(x & 0xFFFFFFFFFFFFFFFF)
+
+
+class Problem:
+    """One corridor flow problem (corridor, network, max flow, residual structure)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().fro_free(self.h)
+            self.h = None
+
+    @classmethod
+    def build(cls, w, a, b, Ubase, part=None):
+        part = _c32(w["part"] if part is None else part)
+        return cls(lib().fro_build(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]),
+                                   _p(part), a, b, Ubase))
+
+    @classmethod
+    def from_network(cls, off, head, cap, border, infcap, vw, side0, cA, cB):
+        off, head, cap, infcap, vw = map(_c32, (off, head, cap, infcap, vw))
+        border = np.ascontiguousarray(border, np.int8)
+        side0 = np.ascontiguousarray(side0, np.int8)
+        return cls(lib().fro_from_network(len(off) - 1, _p(off), _p(head), _p(cap), _p(border, i8p), _p(infcap),
+                                          _p(vw), _p(side0, i8p), cA, cB))
+
+    @property
+    def nc(self):
+        return lib().fro_nc(self.h)
+
+    @property
+    def m(self):
+        return lib().fro_m(self.h)
+
+    def export(self):
+        nc, m = self.nc, self.m
+        out = dict(gid=np.empty(nc, np.int32), off=np.empty(nc + 1, np.int32), head=np.empty(m, np.int32),
+                   cap=np.empty(m, np.int32), border=np.empty(nc, np.int8), infcap=np.empty(nc, np.int32),
+                   side0=np.empty(nc, np.int8), dist=np.empty(nc, np.int32))
+        lib().fro_export(self.h, _p(out["gid"]), _p(out["off"]), _p(out["head"]), _p(out["cap"]),
+                         _p(out["border"], i8p), _p(out["infcap"]), _p(out["side0"], i8p), _p(out["dist"]))
+        return out
+
+    def maxflow(self, method=0):
+        return lib().fro_maxflow(self.h, method)
+
+    def flow(self):
+        af = np.empty(self.m, np.int64)
+        sf = np.empty(self.nc, np.int64)
+        lib().fro_flow(self.h, _p(af, i64p), _p(sf, i64p))
+        return af, sf
+
+    def residual_sets(self):
+        nc = self.nc
+        in_s, to_t, comp = np.empty(nc, np.int8), np.empty(nc, np.int8), np.empty(nc, np.int32)
+        lib().fro_residual_sets(self.h, _p(in_s, i8p), _p(to_t, i8p), _p(comp))
+        return in_s.astype(bool), to_t.astype(bool), comp
+
+    def sweep(self, r=0, seed=0):
+        nc = self.nc
+        order = np.empty(nc + 1, np.int32)
+        d = np.empty(nc + 2, np.int64)
+        c = lib().fro_sweep(self.h, r, seed & 0xFFFFFFFFFFFFFFFF, _p(order), _p(d, i64p))
+        return order[:max(c, 0)], d[:max(c, 0) + 1]
+
+    def cut(self, mb=0, reps=1, seed=0):
+        side = np.empty(self.nc, np.int8)
+        bj, br = ctypes.c_int32(), ctypes.c_int32()
+        capv = lib().fro_cut(self.h, mb, reps, seed & 0xFFFFFFFFFFFFFFFF, _p(side, i8p), ctypes.byref(bj),
+                             ctypes.byref(br))
+        return capv, side, bj.value, br.value
+
+
+def refine_pair(w, a=0, b=1, part=None, eps=None, alpha=None, opts=None):
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    alpha = w["alpha"] if alpha is None else alpha
+    if opts is None:
+        opts = options(mb=w.get("mb", 0), adaptive=w.get("adaptive", 0), max_iters=w.get("max_iters", 1),
+                       alpha_max=w.get("alpha_max", alpha))
+    res = PairResult()
+    st = lib().fro_refine_pair(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
+                               w["k"], a, b, eps, alpha, ctypes.byref(opts), ctypes.byref(res))
+    return st, part, res
+
+
+def rounds(w, part=None):
+    part = _c32(w["part"] if part is None else part)
+    k = w["k"]
+    cap = k * (k - 1) // 2
+    pa, pb, pr = np.empty(cap, np.int32), np.empty(cap, np.int32), np.empty(cap, np.int32)
+    nr = ctypes.c_int32()
+    np_ = lib().fro_rounds(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(part), k, cap, _p(pa), _p(pb), _p(pr),
+                           ctypes.byref(nr))
+    return pa[:np_], pb[:np_], pr[:np_], nr.value
+
+
+def refine_batch(w, part=None, eps=None, alpha=None, opts=None):
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    alpha = w["alpha"] if alpha is None else alpha
+    if opts is None:
+        opts = options(mb=w.get("mb", 0), adaptive=w.get("adaptive", 0), max_iters=w.get("max_iters", 1),
+                       alpha_max=w.get("alpha_max", alpha))
+    k = w["k"]
+    cap = k * (k - 1) // 2
+    res = (PairResult * max(cap, 1))()
+    npairs, nrounds = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().fro_refine_batch(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
+                                k, eps, alpha, ctypes.byref(opts), cap, res, ctypes.byref(npairs),
+                                ctypes.byref(nrounds))
+    return st, part, [res[i].as_dict() for i in range(npairs.value)], nrounds.value

@@ -1,0 +1,26 @@
+"""Builds liboracle.so (plain C, -O2, no fast-math, no FMA contraction).
+
+Test infrastructure: the oracle is only loaded by the tests, the smoke check and
+the benchmark's CPU-baseline leg.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "liboracle.so")
+
+
+def build(force=False):
+    src = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "fro.h")]
+    if not force and os.path.exists(OUT) and all(os.path.getmtime(s) <= os.path.getmtime(OUT) for s in src):
+        return OUT
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-o", OUT, src[0], "-lm"]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle build failed:\n" + r.stdout)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force=True))

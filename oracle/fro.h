@@ -1,0 +1,144 @@
+/*
+ * fro.h -- CPU oracle for flow-based refinement of a block pair.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The product path
+ * (libflowref.so and its binding) never calls, links or reads anything here, and
+ * the two share no code: no headers, no helpers, no tables.
+ *
+ * Sources (Sanders & Schulz, "Engineering Multilevel Graph Partitioning
+ * Algorithms"):
+ *   Section 2.1   graph G = (V, E, c, omega), blocks, L_max, cut objective
+ *   Section 4.1   boundary, corridor by two bounded BFS, B-corridor network
+ *                 G' = G[B] + s + t with infinite s/t arcs, max flow, adaptive
+ *                 flow iterations (eps' = alpha * eps)
+ *   Section 4.1.1 Picard-Queyranne closed sets, smallest source set from
+ *                 Ford-Fulkerson labelling, SCC contraction of the residual
+ *                 graph, removal of S/T components, topological sweeps
+ *
+ * Readings where the paper is silent or ambiguous are fixed as follows and are
+ * shared with the CUDA path only as a written specification:
+ *   budget     U_side = max(0, floor((1 + alpha*eps) * W / k) - c(other block)),
+ *              evaluated as that double expression without FMA contraction;
+ *              L_max = floor((1 + eps) * W / k) + max_v c(v)
+ *   corridor   reached vertices ordered by (BFS distance, vertex id); the longest
+ *              prefix whose weight stays <= U is taken (no skipping)
+ *   border     w.r.t. G[A u B]: a corridor vertex with a neighbour in A u B
+ *              outside the corridor; A-side border <- s, B-side border -> t
+ *   infinity   INF_v = 1 + sum of omega over all edges at v
+ *   plain cut  the smallest source set (vertices reachable from s in the
+ *              residual graph of a maximum flow)
+ *   MB cut     sweeps r = 0..R-1 of Kahn's algorithm over the SCC DAG of the
+ *              vertices neither reachable from s nor reaching t; ready set is a
+ *              min-heap on key_0 = min vertex id, key_r = (splitmix64(seed ^ r ^
+ *              minid), minid); step j moves the first j components to the sink
+ *              side; the (j, r) minimising |c(A') - c(B')| wins, ties to smaller
+ *              j, then smaller r
+ *   accept     max(c(A'), c(B')) <= L_max and (cut decreases, or cut equal and
+ *              max(c(A'), c(B')) decreases)
+ *   adaptive   feasible & smaller: apply, alpha = min(2 alpha, alpha');
+ *              feasible & equal: apply if better balanced, stop;
+ *              infeasible: stop if alpha == 1 else alpha = max(alpha/2, 1)
+ *   batch      greedy edge colouring of the quotient graph in lexicographic
+ *              (a, b) order (smallest free colour); each colour is a round of
+ *              block-disjoint pairs; rounds in colour order, pairs of a round
+ *              see the partition as it stands at the start of the round
+ */
+#ifndef FRO_H
+#define FRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { FRO_OK = 0, FRO_ERR_INVALID_ARG = 1, FRO_ERR_TOO_LARGE = 5 };
+
+typedef struct fro_options {
+    int32_t mb;          /* 1: most balanced minimum cut, 0: smallest source set */
+    int32_t mb_reps;     /* R >= 1 sweeps */
+    int32_t adaptive;    /* adaptive flow iterations */
+    int32_t max_iters;   /* iteration cap of the adaptive loop (>= 1) */
+    double alpha_max;    /* alpha' */
+    uint64_t seed;       /* sweep keys for r >= 1 */
+} fro_options;
+
+typedef struct fro_pair_result {
+    int64_t flow, cut_before, cut_after, wA_before, wB_before, wA_after, wB_after;
+    int32_t corridor_n, corridor_arcs, accepted, iters;
+    double alpha_final;
+    int32_t status, a, b, round;
+} fro_pair_result;
+
+/* Input checks of Section 2.1 (omega > 0, c >= 0, symmetric simple CSR, 0 <= part < k). */
+int32_t fro_validate(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, const int32_t *part, int32_t k);
+
+/* W = c(V), max_v c(v), L_max and the per-call budget base floor((1+alpha*eps) W/k). */
+int64_t fro_total_weight(int32_t n, const int32_t *vwgt);
+int64_t fro_max_weight(int32_t n, const int32_t *vwgt);
+int64_t fro_lmax(int64_t W, int64_t maxc, int32_t k, double eps);
+int64_t fro_budget_base(int64_t W, int32_t k, double eps, double alpha);
+
+/* ---- one flow problem: corridor + network + max flow + cuts ------------- */
+typedef struct fro_problem fro_problem;
+
+/* Corridor of pair (a, b) under budget base Ubase (Section 4.1). */
+fro_problem *fro_build(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                       const int32_t *vwgt, const int32_t *part, int32_t a, int32_t b, int64_t Ubase);
+/* A problem given directly as a network in the export format (for pins on arbitrary networks). */
+fro_problem *fro_from_network(int32_t nc, const int32_t *off, const int32_t *head, const int32_t *cap,
+                              const int8_t *border, const int32_t *infcap, const int32_t *vw,
+                              const int8_t *side0, int64_t cA, int64_t cB);
+void fro_free(fro_problem *p);
+
+int32_t fro_nc(const fro_problem *p);   /* corridor vertices */
+int32_t fro_m(const fro_problem *p);    /* corridor arcs (both directions of each edge) */
+/* Export format: gid[nc] ascending; off[nc+1]; head/cap[m] (corridor arcs in CSR order);
+ * border[nc] 0 none, 1 s -> v, 2 v -> t; infcap[nc] INF_v of border vertices (0 otherwise);
+ * side0[nc] 0 = block a, 1 = block b; dist[nc] BFS distance inside its block. */
+void fro_export(const fro_problem *p, int32_t *gid, int32_t *off, int32_t *head, int32_t *cap,
+                int8_t *border, int32_t *infcap, int8_t *side0, int32_t *dist);
+
+/* Max flow: method 0 = Dinic, 1 = Edmonds-Karp scanning arcs in reverse order. */
+int64_t fro_maxflow(fro_problem *p, int32_t method);
+/* Flow on corridor arcs (m) and on the s/t arc of each corridor vertex (nc). */
+void fro_flow(const fro_problem *p, int64_t *arcflow, int64_t *stflow);
+/* Residual sets after the max flow: in_s (reachable from s), to_t (reaches t),
+ * comp (min gid of the vertex's residual SCC for vertices in neither, else -1). */
+void fro_residual_sets(fro_problem *p, int8_t *in_s, int8_t *to_t, int32_t *comp);
+/* Sweep r: writes component labels in sweep order and d[j] = c(A'_j) - c(B'_j) for
+ * j = 0..ncomp; returns ncomp. */
+int32_t fro_sweep(fro_problem *p, int32_t r, uint64_t seed, int32_t *order, int64_t *d);
+/* Output sides (0 = source/A, 1 = sink/B) of the plain or MB cut; returns the cut
+ * capacity in G' (must equal the flow). */
+int64_t fro_cut(fro_problem *p, int32_t mb, int32_t reps, uint64_t seed, int8_t *side, int32_t *best_j,
+                int32_t *best_r);
+
+/* ---- full method --------------------------------------------------------- */
+int32_t fro_refine_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, int32_t *part, int32_t k, int32_t a, int32_t b, double eps,
+                        double alpha, const fro_options *opt, fro_pair_result *res);
+
+/* Quotient graph rounds: pair list (a < b, lexicographic) with the colour of each pair. */
+int32_t fro_rounds(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *part, int32_t k,
+                   int32_t cap, int32_t *pair_a, int32_t *pair_b, int32_t *pair_round, int32_t *nrounds);
+
+/* One sweep over all rounds; per-pair results in round order, then (a, b) order. */
+int32_t fro_refine_batch(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                         const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                         const fro_options *opt, int32_t cap, fro_pair_result *res, int32_t *npairs,
+                         int32_t *nrounds);
+
+/* Pair cut omega(E_ab) of the current partition. */
+int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *part, int32_t a, int32_t b);
+
+/* splitmix64(x): first output of a splitmix64 generator seeded with x. */
+uint64_t fro_splitmix64(uint64_t x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

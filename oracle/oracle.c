@@ -1,0 +1,841 @@
+/*
+ * CPU oracle for flow-based refinement of a block pair -- TEST INFRASTRUCTURE.
+ *
+ * Plain, single-threaded, deliberately unoptimised C.  Each step follows the
+ * paper's description in the paper's order (Sanders & Schulz, Section 4.1 and
+ * 4.1.1); the readings of points the paper leaves open are listed in fro.h.
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg use it.
+ * It shares no code with the CUDA path.
+ */
+#include "fro.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define XALLOC(T, n) ((T *)calloc((size_t)((n) > 0 ? (n) : 1), sizeof(T)))
+
+uint64_t fro_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------ Section 2.1: the problem -- */
+
+int32_t fro_validate(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, const int32_t *part, int32_t k) {
+    if (n < 1 || k < 2 || !xadj || !adjncy || !adjwgt || !vwgt || !part) return FRO_ERR_INVALID_ARG;
+    if (xadj[0] != 0) return FRO_ERR_INVALID_ARG;
+    for (int32_t v = 0; v < n; ++v)
+        if (xadj[v + 1] < xadj[v]) return FRO_ERR_INVALID_ARG;
+    for (int32_t v = 0; v < n; ++v) {
+        if (vwgt[v] < 0) return FRO_ERR_INVALID_ARG;           /* c >= 0 */
+        if (part[v] < 0 || part[v] >= k) return FRO_ERR_INVALID_ARG;
+        int64_t wdeg = 0;
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            int32_t u = adjncy[j];
+            if (u < 0 || u >= n || u == v) return FRO_ERR_INVALID_ARG;
+            if (adjwgt[j] < 1) return FRO_ERR_INVALID_ARG;      /* omega > 0 */
+            wdeg += adjwgt[j];
+            /* simple graph: u appears once in v's row */
+            for (int32_t q = xadj[v]; q < j; ++q)
+                if (adjncy[q] == u) return FRO_ERR_INVALID_ARG;
+            /* undirected: v appears in u's row with the same weight */
+            int found = 0;
+            for (int32_t q = xadj[u]; q < xadj[u + 1]; ++q)
+                if (adjncy[q] == v) { found = adjwgt[q] == adjwgt[j] ? 1 : -1; break; }
+            if (found != 1) return FRO_ERR_INVALID_ARG;
+        }
+        if (wdeg >= (1LL << 30)) return FRO_ERR_TOO_LARGE;
+    }
+    return FRO_OK;
+}
+
+int64_t fro_total_weight(int32_t n, const int32_t *vwgt) {
+    int64_t w = 0;
+    for (int32_t v = 0; v < n; ++v) w += vwgt[v];
+    return w;
+}
+
+int64_t fro_max_weight(int32_t n, const int32_t *vwgt) {
+    int64_t w = 0;
+    for (int32_t v = 0; v < n; ++v) if (vwgt[v] > w) w = vwgt[v];
+    return w;
+}
+
+/* L_max = (1 + eps) c(V)/k + max_v c(v), integerised: block weights are integers. */
+int64_t fro_lmax(int64_t W, int64_t maxc, int32_t k, double eps) {
+    double t = 1.0 + eps;
+    t = t * (double)W;
+    t = t / (double)k;
+    return (int64_t)floor(t) + maxc;
+}
+
+/* Corridor budget base: (1 + eps') c(V)/k with eps' = alpha * eps. */
+int64_t fro_budget_base(int64_t W, int32_t k, double eps, double alpha) {
+    double ae = alpha * eps;
+    double t = 1.0 + ae;
+    t = t * (double)W;
+    t = t / (double)k;
+    return (int64_t)floor(t);
+}
+
+int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *part, int32_t a, int32_t b) {
+    int64_t cut = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        if (part[v] != a) continue;
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j)
+            if (part[adjncy[j]] == b) cut += adjwgt[j];
+    }
+    return cut;
+}
+
+/* --------------------------------------------------- the flow problem ----- */
+
+struct fro_problem {
+    /* corridor and its network in the export format */
+    int32_t nc, m;
+    int32_t *gid, *off, *head, *cap, *infcap, *dist;
+    int8_t *border, *side0;
+    int64_t *vw;
+    int64_t cA, cB;
+    /* explicit network on N = nc + 2 vertices: s = nc, t = nc + 1 */
+    int32_t N, M;
+    int32_t *noff, *nhead, *nrev;
+    int64_t *ncap, *nres;
+    int64_t flow;
+    int ok;
+    /* residual structure */
+    int8_t *in_s, *to_t;
+    int32_t *comp;   /* SCC label (min gid) of vertices in neither set, else -1 */
+    int sets_done;
+};
+
+void fro_free(fro_problem *p) {
+    if (!p) return;
+    free(p->gid); free(p->off); free(p->head); free(p->cap); free(p->infcap); free(p->dist);
+    free(p->border); free(p->side0); free(p->vw);
+    free(p->noff); free(p->nhead); free(p->nrev); free(p->ncap); free(p->nres);
+    free(p->in_s); free(p->to_t); free(p->comp);
+    free(p);
+}
+
+int32_t fro_nc(const fro_problem *p) { return p->nc; }
+int32_t fro_m(const fro_problem *p) { return p->m; }
+
+void fro_export(const fro_problem *p, int32_t *gid, int32_t *off, int32_t *head, int32_t *cap,
+                int8_t *border, int32_t *infcap, int8_t *side0, int32_t *dist) {
+    if (gid) memcpy(gid, p->gid, sizeof(int32_t) * (size_t)p->nc);
+    if (off) memcpy(off, p->off, sizeof(int32_t) * (size_t)(p->nc + 1));
+    if (head) memcpy(head, p->head, sizeof(int32_t) * (size_t)p->m);
+    if (cap) memcpy(cap, p->cap, sizeof(int32_t) * (size_t)p->m);
+    if (border) memcpy(border, p->border, (size_t)p->nc);
+    if (infcap) memcpy(infcap, p->infcap, sizeof(int32_t) * (size_t)p->nc);
+    if (side0) memcpy(side0, p->side0, (size_t)p->nc);
+    if (dist) memcpy(dist, p->dist, sizeof(int32_t) * (size_t)p->nc);
+}
+
+/* Explicit network: corridor arcs of vertex i in export order, then its s/t arc;
+ * s's arcs to s-border vertices and t's arcs to t-border vertices, ascending. */
+static int build_network(fro_problem *p) {
+    int32_t nc = p->nc, N = nc + 2, s = nc, t = nc + 1;
+    p->N = N;
+    p->noff = XALLOC(int32_t, N + 1);
+    int32_t *deg = XALLOC(int32_t, N);
+    for (int32_t i = 0; i < nc; ++i) {
+        deg[i] = p->off[i + 1] - p->off[i] + (p->border[i] ? 1 : 0);
+        if (p->border[i] == 1) deg[s]++;
+        if (p->border[i] == 2) deg[t]++;
+    }
+    for (int32_t v = 0; v < N; ++v) p->noff[v + 1] = p->noff[v] + deg[v];
+    int32_t M = p->noff[N];
+    p->M = M;
+    p->nhead = XALLOC(int32_t, M);
+    p->nrev = XALLOC(int32_t, M);
+    p->ncap = XALLOC(int64_t, M);
+    p->nres = XALLOC(int64_t, M);
+    int32_t *pos = XALLOC(int32_t, N);
+    for (int32_t v = 0; v < N; ++v) pos[v] = p->noff[v];
+    int32_t *stpos = XALLOC(int32_t, nc);   /* position of i's s/t arc */
+    for (int32_t i = 0; i < nc; ++i) {
+        for (int32_t j = p->off[i]; j < p->off[i + 1]; ++j) {
+            int32_t a = pos[i]++;
+            p->nhead[a] = p->head[j];
+            p->ncap[a] = p->cap[j];
+        }
+        if (p->border[i] == 1) {          /* reverse of s -> i, capacity 0 */
+            int32_t a = pos[i]++;
+            p->nhead[a] = s; p->ncap[a] = 0; stpos[i] = a;
+        } else if (p->border[i] == 2) {   /* i -> t, "infinite" capacity */
+            int32_t a = pos[i]++;
+            p->nhead[a] = t; p->ncap[a] = p->infcap[i]; stpos[i] = a;
+        }
+    }
+    for (int32_t i = 0; i < nc; ++i) {
+        if (p->border[i] == 1) {
+            int32_t a = pos[s]++;
+            p->nhead[a] = i; p->ncap[a] = p->infcap[i];
+            p->nrev[a] = stpos[i]; p->nrev[stpos[i]] = a;
+        } else if (p->border[i] == 2) {
+            int32_t a = pos[t]++;
+            p->nhead[a] = i; p->ncap[a] = 0;
+            p->nrev[a] = stpos[i]; p->nrev[stpos[i]] = a;
+        }
+    }
+    /* reverse of a corridor arc i -> h: the q-th arc h -> i, where q counts earlier i -> h arcs */
+    int ok = 1;
+    for (int32_t i = 0; i < nc && ok; ++i) {
+        int32_t base = p->noff[i];
+        int32_t ncorr = p->off[i + 1] - p->off[i];
+        for (int32_t x = 0; x < ncorr; ++x) {
+            int32_t h = p->nhead[base + x];
+            int32_t q = 0;
+            for (int32_t y = 0; y < x; ++y) if (p->nhead[base + y] == h) ++q;
+            int32_t found = -1;
+            int32_t hn = p->off[h + 1] - p->off[h];
+            for (int32_t y = 0; y < hn; ++y)
+                if (p->nhead[p->noff[h] + y] == i) { if (q == 0) { found = p->noff[h] + y; break; } --q; }
+            if (found < 0) { ok = 0; break; }
+            p->nrev[base + x] = found;
+        }
+    }
+    for (int32_t a = 0; a < M; ++a) p->nres[a] = p->ncap[a];
+    free(deg); free(pos); free(stpos);
+    return ok;
+}
+
+/* Corridor side (Section 4.1): BFS inside block X from the vertices of X with a
+ * neighbour in Y; reached vertices in (distance, id) order; longest prefix of
+ * weight <= U.  Writes dist (n-sized, -1 = not taken). */
+typedef struct { int32_t d, v; } dv_pair;
+
+static int cmp_dv(const void *pa, const void *pb) {
+    const dv_pair *a = (const dv_pair *)pa, *b = (const dv_pair *)pb;
+    if (a->d != b->d) return a->d < b->d ? -1 : 1;
+    return (a->v > b->v) - (a->v < b->v);
+}
+
+static void corridor_side(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                          const int32_t *part, int32_t X, int32_t Y, int64_t U, int32_t *taken_dist) {
+    int32_t *dist = XALLOC(int32_t, n);
+    int32_t *queue = XALLOC(int32_t, n);
+    int32_t qh = 0, qt = 0;
+    for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+    for (int32_t v = 0; v < n; ++v) {            /* boundary delta_X towards Y */
+        if (part[v] != X) continue;
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j)
+            if (part[adjncy[j]] == Y) { dist[v] = 0; queue[qt++] = v; break; }
+    }
+    while (qh < qt) {                             /* expand only inside block X */
+        int32_t v = queue[qh++];
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            int32_t u = adjncy[j];
+            if (part[u] == X && dist[u] < 0) { dist[u] = dist[v] + 1; queue[qt++] = u; }
+        }
+    }
+    dv_pair *order = XALLOC(dv_pair, qt);
+    for (int32_t i = 0; i < qt; ++i) { order[i].d = dist[queue[i]]; order[i].v = queue[i]; }
+    qsort(order, (size_t)qt, sizeof(dv_pair), cmp_dv);
+    int64_t run = 0;
+    for (int32_t i = 0; i < qt; ++i) {            /* stop at the first vertex that would exceed */
+        int32_t v = order[i].v;
+        if (run + vwgt[v] > U) break;
+        run += vwgt[v];
+        taken_dist[v] = order[i].d;
+    }
+    free(order); free(queue); free(dist);
+}
+
+fro_problem *fro_build(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                       const int32_t *vwgt, const int32_t *part, int32_t a, int32_t b, int64_t Ubase) {
+    fro_problem *p = XALLOC(fro_problem, 1);
+    int64_t cA = 0, cB = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        if (part[v] == a) cA += vwgt[v];
+        else if (part[v] == b) cB += vwgt[v];
+    }
+    p->cA = cA; p->cB = cB;
+    int64_t UA = Ubase - cB, UB = Ubase - cA;
+    if (UA < 0) UA = 0;
+    if (UB < 0) UB = 0;
+    int32_t *tdist = XALLOC(int32_t, n);
+    for (int32_t v = 0; v < n; ++v) tdist[v] = -1;
+    corridor_side(n, xadj, adjncy, vwgt, part, a, b, UA, tdist);
+    corridor_side(n, xadj, adjncy, vwgt, part, b, a, UB, tdist);
+    /* local ids in ascending global id */
+    int32_t *lid = XALLOC(int32_t, n);
+    int32_t nc = 0;
+    for (int32_t v = 0; v < n; ++v) lid[v] = tdist[v] >= 0 ? nc++ : -1;
+    p->nc = nc;
+    p->gid = XALLOC(int32_t, nc);
+    p->dist = XALLOC(int32_t, nc);
+    p->side0 = XALLOC(int8_t, nc);
+    p->border = XALLOC(int8_t, nc);
+    p->infcap = XALLOC(int32_t, nc);
+    p->vw = XALLOC(int64_t, nc);
+    p->off = XALLOC(int32_t, nc + 1);
+    for (int32_t v = 0; v < n; ++v)
+        if (lid[v] >= 0) {
+            int32_t i = lid[v];
+            p->gid[i] = v; p->dist[i] = tdist[v]; p->side0[i] = part[v] == b; p->vw[i] = vwgt[v];
+        }
+    /* G' = G[B] plus s, t (Section 4.1); border w.r.t. G[A u B] */
+    int32_t m = 0;
+    for (int32_t i = 0; i < nc; ++i) {
+        int32_t v = p->gid[i];
+        int64_t wdeg = 0;
+        int border = 0;
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            int32_t u = adjncy[j];
+            wdeg += adjwgt[j];
+            if (part[u] != a && part[u] != b) continue;
+            if (lid[u] >= 0) ++m; else border = 1;
+        }
+        p->off[i + 1] = m;
+        if (border) {
+            p->border[i] = p->side0[i] ? 2 : 1;
+            p->infcap[i] = (int32_t)(wdeg + 1);
+        }
+    }
+    p->m = m;
+    p->head = XALLOC(int32_t, m);
+    p->cap = XALLOC(int32_t, m);
+    int32_t e = 0;
+    for (int32_t i = 0; i < nc; ++i) {
+        int32_t v = p->gid[i];
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            int32_t u = adjncy[j];
+            if ((part[u] == a || part[u] == b) && lid[u] >= 0) { p->head[e] = lid[u]; p->cap[e] = adjwgt[j]; ++e; }
+        }
+    }
+    free(lid); free(tdist);
+    p->ok = build_network(p);
+    return p;
+}
+
+fro_problem *fro_from_network(int32_t nc, const int32_t *off, const int32_t *head, const int32_t *cap,
+                              const int8_t *border, const int32_t *infcap, const int32_t *vw,
+                              const int8_t *side0, int64_t cA, int64_t cB) {
+    fro_problem *p = XALLOC(fro_problem, 1);
+    p->nc = nc; p->m = off[nc]; p->cA = cA; p->cB = cB;
+    p->gid = XALLOC(int32_t, nc); p->dist = XALLOC(int32_t, nc);
+    p->off = XALLOC(int32_t, nc + 1); p->head = XALLOC(int32_t, p->m); p->cap = XALLOC(int32_t, p->m);
+    p->border = XALLOC(int8_t, nc); p->infcap = XALLOC(int32_t, nc); p->side0 = XALLOC(int8_t, nc);
+    p->vw = XALLOC(int64_t, nc);
+    for (int32_t i = 0; i < nc; ++i) {
+        p->gid[i] = i; p->border[i] = border[i]; p->infcap[i] = infcap[i];
+        p->side0[i] = side0[i]; p->vw[i] = vw[i];
+    }
+    memcpy(p->off, off, sizeof(int32_t) * (size_t)(nc + 1));
+    memcpy(p->head, head, sizeof(int32_t) * (size_t)p->m);
+    memcpy(p->cap, cap, sizeof(int32_t) * (size_t)p->m);
+    p->ok = build_network(p);
+    return p;
+}
+
+/* ------------------------------------------------------------ max flow ---- */
+
+/* Dinic: BFS level graph from s, then blocking flow by DFS with current-arc pointers. */
+static int64_t maxflow_dinic(fro_problem *p) {
+    int32_t N = p->N, s = p->nc, t = p->nc + 1;
+    int32_t *level = XALLOC(int32_t, N), *queue = XALLOC(int32_t, N), *it = XALLOC(int32_t, N);
+    int32_t *stack = XALLOC(int32_t, N + 1);   /* arcs of the current path */
+    int64_t flow = 0;
+    for (;;) {
+        for (int32_t v = 0; v < N; ++v) level[v] = -1;
+        int32_t qh = 0, qt = 0;
+        level[s] = 0; queue[qt++] = s;
+        while (qh < qt) {
+            int32_t v = queue[qh++];
+            for (int32_t a = p->noff[v]; a < p->noff[v + 1]; ++a) {
+                int32_t u = p->nhead[a];
+                if (p->nres[a] > 0 && level[u] < 0) { level[u] = level[v] + 1; queue[qt++] = u; }
+            }
+        }
+        if (level[t] < 0) break;
+        for (int32_t v = 0; v < N; ++v) it[v] = p->noff[v];
+        int32_t depth = 0, v = s;
+        for (;;) {
+            if (v == t) {
+                int64_t aug = INT64_MAX;
+                for (int32_t d = 0; d < depth; ++d) if (p->nres[stack[d]] < aug) aug = p->nres[stack[d]];
+                for (int32_t d = 0; d < depth; ++d) {
+                    p->nres[stack[d]] -= aug;
+                    p->nres[p->nrev[stack[d]]] += aug;
+                }
+                flow += aug;
+                depth = 0; v = s;
+                continue;
+            }
+            int advanced = 0;
+            for (; it[v] < p->noff[v + 1]; ++it[v]) {
+                int32_t a = it[v], u = p->nhead[a];
+                if (p->nres[a] > 0 && level[u] == level[v] + 1) {
+                    stack[depth++] = a; v = u; advanced = 1;
+                    break;
+                }
+            }
+            if (advanced) continue;
+            if (v == s) break;                      /* blocking flow complete */
+            level[v] = -1;                          /* dead end: retreat */
+            int32_t a = stack[--depth];
+            v = p->nhead[p->nrev[a]];
+            ++it[v];
+        }
+    }
+    free(level); free(queue); free(it); free(stack);
+    return flow;
+}
+
+/* Edmonds-Karp with arcs scanned last to first: a second, independent max flow. */
+static int64_t maxflow_ek_reverse(fro_problem *p) {
+    int32_t N = p->N, s = p->nc, t = p->nc + 1;
+    int32_t *parent = XALLOC(int32_t, N), *queue = XALLOC(int32_t, N);
+    int64_t flow = 0;
+    for (;;) {
+        for (int32_t v = 0; v < N; ++v) parent[v] = -2;
+        parent[s] = -1;
+        int32_t qh = 0, qt = 0;
+        queue[qt++] = s;
+        while (qh < qt && parent[t] == -2) {
+            int32_t v = queue[qh++];
+            for (int32_t a = p->noff[v + 1] - 1; a >= p->noff[v]; --a) {
+                int32_t u = p->nhead[a];
+                if (p->nres[a] > 0 && parent[u] == -2) { parent[u] = a; queue[qt++] = u; }
+            }
+        }
+        if (parent[t] == -2) break;
+        int64_t aug = INT64_MAX;
+        for (int32_t v = t; v != s; v = p->nhead[p->nrev[parent[v]]])
+            if (p->nres[parent[v]] < aug) aug = p->nres[parent[v]];
+        for (int32_t v = t; v != s; v = p->nhead[p->nrev[parent[v]]]) {
+            p->nres[parent[v]] -= aug;
+            p->nres[p->nrev[parent[v]]] += aug;
+        }
+        flow += aug;
+    }
+    free(parent); free(queue);
+    return flow;
+}
+
+int64_t fro_maxflow(fro_problem *p, int32_t method) {
+    if (!p->ok) return -1;
+    for (int32_t a = 0; a < p->M; ++a) p->nres[a] = p->ncap[a];
+    p->flow = method == 1 ? maxflow_ek_reverse(p) : maxflow_dinic(p);
+    p->sets_done = 0;
+    return p->flow;
+}
+
+void fro_flow(const fro_problem *p, int64_t *arcflow, int64_t *stflow) {
+    for (int32_t i = 0; i < p->nc; ++i) {
+        int32_t ncorr = p->off[i + 1] - p->off[i];
+        for (int32_t x = 0; x < ncorr; ++x) {
+            int32_t a = p->noff[i] + x;
+            if (arcflow) arcflow[p->off[i] + x] = p->ncap[a] - p->nres[a];
+        }
+        if (stflow) {
+            stflow[i] = 0;
+            if (p->border[i]) {
+                int32_t a = p->noff[i + 1] - 1;     /* i's s/t arc */
+                stflow[i] = p->border[i] == 1 ? p->nres[a] /* flow on s -> i */ : p->ncap[a] - p->nres[a];
+            }
+        }
+    }
+}
+
+/* ----------------------------------------- residual structure (4.1.1) ----- */
+
+/* Tarjan's SCC algorithm, iterative, on the residual graph (arcs with res > 0). */
+static void tarjan(const fro_problem *p, int32_t *scc) {
+    int32_t N = p->N;
+    int32_t *index = XALLOC(int32_t, N), *low = XALLOC(int32_t, N), *stk = XALLOC(int32_t, N);
+    int32_t *cs_v = XALLOC(int32_t, N), *cs_a = XALLOC(int32_t, N);
+    int8_t *on = XALLOC(int8_t, N);
+    for (int32_t v = 0; v < N; ++v) { index[v] = -1; scc[v] = -1; }
+    int32_t counter = 0, sp = 0, nscc = 0;
+    for (int32_t root = 0; root < N; ++root) {
+        if (index[root] >= 0) continue;
+        int32_t csp = 0;
+        cs_v[csp] = root; cs_a[csp] = p->noff[root]; ++csp;
+        index[root] = low[root] = counter++; stk[sp++] = root; on[root] = 1;
+        while (csp > 0) {
+            int32_t v = cs_v[csp - 1];
+            if (cs_a[csp - 1] < p->noff[v + 1]) {
+                int32_t a = cs_a[csp - 1]++;
+                if (p->nres[a] <= 0) continue;
+                int32_t u = p->nhead[a];
+                if (index[u] < 0) {
+                    index[u] = low[u] = counter++; stk[sp++] = u; on[u] = 1;
+                    cs_v[csp] = u; cs_a[csp] = p->noff[u]; ++csp;
+                } else if (on[u] && index[u] < low[v]) {
+                    low[v] = index[u];
+                }
+            } else {
+                if (low[v] == index[v]) {
+                    int32_t w;
+                    do { w = stk[--sp]; on[w] = 0; scc[w] = nscc; } while (w != v);
+                    ++nscc;
+                }
+                --csp;
+                if (csp > 0) {
+                    int32_t parent = cs_v[csp - 1];
+                    if (low[v] < low[parent]) low[parent] = low[v];
+                }
+            }
+        }
+    }
+    free(index); free(low); free(stk); free(cs_v); free(cs_a); free(on);
+}
+
+static void compute_sets(fro_problem *p) {
+    if (p->sets_done) return;
+    int32_t N = p->N, s = p->nc, t = p->nc + 1, nc = p->nc;
+    free(p->in_s); free(p->to_t); free(p->comp);
+    p->in_s = XALLOC(int8_t, N); p->to_t = XALLOC(int8_t, N); p->comp = XALLOC(int32_t, N);
+    int32_t *queue = XALLOC(int32_t, N);
+    /* vertices reachable from s (Ford-Fulkerson labelling) */
+    int32_t qh = 0, qt = 0;
+    p->in_s[s] = 1; queue[qt++] = s;
+    while (qh < qt) {
+        int32_t v = queue[qh++];
+        for (int32_t a = p->noff[v]; a < p->noff[v + 1]; ++a)
+            if (p->nres[a] > 0 && !p->in_s[p->nhead[a]]) { p->in_s[p->nhead[a]] = 1; queue[qt++] = p->nhead[a]; }
+    }
+    /* vertices that reach t: walk residual arcs backwards */
+    qh = qt = 0;
+    p->to_t[t] = 1; queue[qt++] = t;
+    while (qh < qt) {
+        int32_t v = queue[qh++];
+        for (int32_t a = p->noff[v]; a < p->noff[v + 1]; ++a) {
+            int32_t u = p->nhead[a];
+            if (p->nres[p->nrev[a]] > 0 && !p->to_t[u]) { p->to_t[u] = 1; queue[qt++] = u; }
+        }
+    }
+    /* SCCs of the residual graph, labelled by the minimum global id of their members */
+    int32_t *scc = XALLOC(int32_t, N);
+    tarjan(p, scc);
+    int32_t *minid = XALLOC(int32_t, N);
+    for (int32_t v = 0; v < N; ++v) minid[v] = INT32_MAX;
+    for (int32_t v = 0; v < nc; ++v) if (p->gid[v] < minid[scc[v]]) minid[scc[v]] = p->gid[v];
+    for (int32_t v = 0; v < N; ++v)
+        p->comp[v] = (v < nc && !p->in_s[v] && !p->to_t[v]) ? minid[scc[v]] : -1;
+    free(scc); free(minid); free(queue);
+    p->sets_done = 1;
+}
+
+void fro_residual_sets(fro_problem *p, int8_t *in_s, int8_t *to_t, int32_t *comp) {
+    compute_sets(p);
+    for (int32_t i = 0; i < p->nc; ++i) {
+        if (in_s) in_s[i] = p->in_s[i];
+        if (to_t) to_t[i] = p->to_t[i];
+        if (comp) comp[i] = p->comp[i];
+    }
+}
+
+/* ---------------------------------------------- topological sweeps ------- */
+
+typedef struct { uint64_t k1; int32_t minid; int32_t c; } heap_item;
+
+static int item_less(const heap_item *x, const heap_item *y) {
+    if (x->k1 != y->k1) return x->k1 < y->k1;
+    return x->minid < y->minid;
+}
+
+static void heap_push(heap_item *h, int32_t *hn, heap_item it) {
+    int32_t i = (*hn)++;
+    h[i] = it;
+    while (i > 0) {
+        int32_t par = (i - 1) / 2;
+        if (!item_less(&h[i], &h[par])) break;
+        heap_item tmp = h[i]; h[i] = h[par]; h[par] = tmp;
+        i = par;
+    }
+}
+
+static heap_item heap_pop(heap_item *h, int32_t *hn) {
+    heap_item top = h[0];
+    h[0] = h[--(*hn)];
+    int32_t i = 0;
+    for (;;) {
+        int32_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *hn && item_less(&h[l], &h[m])) m = l;
+        if (r < *hn && item_less(&h[r], &h[m])) m = r;
+        if (m == i) break;
+        heap_item tmp = h[i]; h[i] = h[m]; h[m] = tmp;
+        i = m;
+    }
+    return top;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Sweep r over the DAG of residual SCCs outside the S and T sets (Section 4.1.1):
+ * Kahn's algorithm in residual arc direction (a component is ready once all of its
+ * residual predecessors are on the sink side); ready components leave a min-heap
+ * by key.  order[j] = label of the j-th component moved to the sink side;
+ * d[j] = c(A'_j) - c(B'_j) after j moves.  Returns the number of components. */
+int32_t fro_sweep(fro_problem *p, int32_t r, uint64_t seed, int32_t *order, int64_t *d) {
+    compute_sets(p);
+    int32_t nc = p->nc;
+    int32_t *labels = XALLOC(int32_t, nc);
+    int32_t nl = 0;
+    for (int32_t i = 0; i < nc; ++i) if (p->comp[i] >= 0) labels[nl++] = p->comp[i];
+    qsort(labels, (size_t)nl, sizeof(int32_t), cmp_i32);
+    int32_t ncomp = 0;
+    for (int32_t i = 0; i < nl; ++i) if (i == 0 || labels[i] != labels[i - 1]) labels[ncomp++] = labels[i];
+    /* component index of each vertex via binary search over the sorted labels */
+    int32_t *cidx = XALLOC(int32_t, nc);
+    int64_t *cw = XALLOC(int64_t, ncomp);
+    for (int32_t i = 0; i < nc; ++i) {
+        cidx[i] = -1;
+        if (p->comp[i] < 0) continue;
+        int32_t lo = 0, hi = ncomp - 1;
+        while (lo < hi) { int32_t mid = (lo + hi) / 2; if (labels[mid] < p->comp[i]) lo = mid + 1; else hi = mid; }
+        cidx[i] = lo;
+        cw[lo] += p->vw[i];
+    }
+    /* DAG arcs between components (with multiplicity) */
+    int32_t *indeg = XALLOC(int32_t, ncomp), *outdeg = XALLOC(int32_t, ncomp + 1);
+    for (int32_t i = 0; i < nc; ++i) {
+        if (cidx[i] < 0) continue;
+        for (int32_t a = p->noff[i]; a < p->noff[i + 1]; ++a) {
+            int32_t u = p->nhead[a];
+            if (p->nres[a] <= 0 || u >= nc || cidx[u] < 0 || cidx[u] == cidx[i]) continue;
+            indeg[cidx[u]]++; outdeg[cidx[i] + 1]++;
+        }
+    }
+    for (int32_t c = 0; c < ncomp; ++c) outdeg[c + 1] += outdeg[c];
+    int32_t *outs = XALLOC(int32_t, outdeg[ncomp]);
+    int32_t *fill = XALLOC(int32_t, ncomp);
+    for (int32_t i = 0; i < nc; ++i) {
+        if (cidx[i] < 0) continue;
+        for (int32_t a = p->noff[i]; a < p->noff[i + 1]; ++a) {
+            int32_t u = p->nhead[a];
+            if (p->nres[a] <= 0 || u >= nc || cidx[u] < 0 || cidx[u] == cidx[i]) continue;
+            outs[outdeg[cidx[i]] + fill[cidx[i]]++] = cidx[u];
+        }
+    }
+    /* d_0: source side = everything that does not reach t */
+    int64_t cA0 = p->cA;
+    for (int32_t i = 0; i < nc; ++i) {
+        if (!p->side0[i] && p->to_t[i]) cA0 -= p->vw[i];
+        if (p->side0[i] && !p->to_t[i]) cA0 += p->vw[i];
+    }
+    int64_t total = p->cA + p->cB;
+    d[0] = cA0 - (total - cA0);
+    heap_item *heap = XALLOC(heap_item, ncomp);
+    int32_t hn = 0, done = 0;
+    for (int32_t c = 0; c < ncomp; ++c)
+        if (indeg[c] == 0) {
+            heap_item it = { r == 0 ? 0 : fro_splitmix64(seed ^ (uint64_t)r ^ (uint64_t)labels[c]), labels[c], c };
+            heap_push(heap, &hn, it);
+        }
+    while (hn > 0) {
+        heap_item top = heap_pop(heap, &hn);
+        order[done] = top.minid;
+        d[done + 1] = d[done] - 2 * cw[top.c];
+        ++done;
+        for (int32_t e = outdeg[top.c]; e < outdeg[top.c + 1]; ++e) {
+            int32_t c = outs[e];
+            if (--indeg[c] == 0) {
+                heap_item it = { r == 0 ? 0 : fro_splitmix64(seed ^ (uint64_t)r ^ (uint64_t)labels[c]), labels[c], c };
+                heap_push(heap, &hn, it);
+            }
+        }
+    }
+    free(labels); free(cidx); free(cw); free(indeg); free(outdeg); free(outs); free(fill); free(heap);
+    return done == ncomp ? ncomp : -1;
+}
+
+static int64_t abs64(int64_t x) { return x < 0 ? -x : x; }
+
+int64_t fro_cut(fro_problem *p, int32_t mb, int32_t reps, uint64_t seed, int8_t *side, int32_t *best_j,
+                int32_t *best_r) {
+    compute_sets(p);
+    int32_t nc = p->nc, N = p->N;
+    int8_t *src = XALLOC(int8_t, N);
+    for (int32_t v = 0; v < N; ++v) src[v] = p->in_s[v];     /* smallest source set */
+    int32_t bj = -1, br = -1;
+    if (mb) {
+        int32_t *order = XALLOC(int32_t, nc + 1), *best_order = XALLOC(int32_t, nc + 1);
+        int64_t *d = XALLOC(int64_t, nc + 2);
+        int64_t best = INT64_MAX;
+        int32_t ncomp = 0;
+        for (int32_t r = 0; r < (reps < 1 ? 1 : reps); ++r) {
+            ncomp = fro_sweep(p, r, seed, order, d);
+            if (ncomp < 0) break;
+            for (int32_t j = 0; j <= ncomp; ++j) {
+                int64_t ad = abs64(d[j]);
+                if (ad < best || (ad == best && j < bj)) {
+                    best = ad; bj = j; br = r;
+                    memcpy(best_order, order, sizeof(int32_t) * (size_t)ncomp);
+                }
+            }
+        }
+        if (ncomp >= 0) {
+            /* source side = complement of (T set u first bj components of sweep br) */
+            for (int32_t i = 0; i < nc; ++i) {
+                if (p->comp[i] < 0) continue;
+                int moved = 0;
+                for (int32_t j = 0; j < bj; ++j) if (best_order[j] == p->comp[i]) { moved = 1; break; }
+                src[i] = !moved;
+            }
+        }
+        free(order); free(best_order); free(d);
+    }
+    int64_t capv = 0;
+    for (int32_t v = 0; v < N; ++v) {
+        if (!src[v]) continue;
+        for (int32_t a = p->noff[v]; a < p->noff[v + 1]; ++a)
+            if (!src[p->nhead[a]]) capv += p->ncap[a];
+    }
+    if (side) for (int32_t i = 0; i < nc; ++i) side[i] = src[i] ? 0 : 1;
+    if (best_j) *best_j = bj;
+    if (best_r) *best_r = br;
+    free(src);
+    return capv;
+}
+
+/* ------------------------------------- refinement of one pair (4.1) ------ */
+
+static int32_t check_pair_args(int32_t k, int32_t a, int32_t b, double eps, double alpha, const fro_options *opt) {
+    if (k < 2 || a < 0 || b < 0 || a >= k || b >= k || a == b) return FRO_ERR_INVALID_ARG;
+    if (!(eps > 0.0) || !(alpha >= 1.0)) return FRO_ERR_INVALID_ARG;
+    if (opt && (opt->mb_reps < 0 || opt->max_iters < 0 || (opt->adaptive && !(opt->alpha_max >= 1.0))))
+        return FRO_ERR_INVALID_ARG;
+    return FRO_OK;
+}
+
+static int32_t refine_pair_core(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                                const int32_t *vwgt, int32_t *part, int32_t k, int32_t a, int32_t b, double eps,
+                                double alpha, const fro_options *opt, int64_t W, int64_t Lmax,
+                                fro_pair_result *res) {
+    int32_t mb = opt ? opt->mb : 0, reps = opt && opt->mb_reps > 0 ? opt->mb_reps : 1;
+    int32_t adaptive = opt ? opt->adaptive : 0;
+    int32_t max_iters = adaptive ? (opt && opt->max_iters > 0 ? opt->max_iters : 10) : 1;
+    double alpha_max = adaptive ? opt->alpha_max : alpha;
+    uint64_t seed = opt ? opt->seed : 0;
+    memset(res, 0, sizeof(*res));
+    res->a = a; res->b = b;
+    int64_t cut = fro_pair_cut(n, xadj, adjncy, adjwgt, part, a, b);
+    int64_t wA = 0, wB = 0;
+    for (int32_t v = 0; v < n; ++v) { if (part[v] == a) wA += vwgt[v]; else if (part[v] == b) wB += vwgt[v]; }
+    res->cut_before = cut; res->wA_before = wA; res->wB_before = wB;
+    int32_t *trial = XALLOC(int32_t, n);
+    double al = alpha;
+    int32_t iters = 0;
+    while (iters < max_iters) {
+        ++iters;
+        fro_problem *p = fro_build(n, xadj, adjncy, adjwgt, vwgt, part, a, b, fro_budget_base(W, k, eps, al));
+        int64_t F = fro_maxflow(p, 0);
+        int8_t *side = XALLOC(int8_t, p->nc);
+        fro_cut(p, mb, reps, seed, side, NULL, NULL);
+        memcpy(trial, part, sizeof(int32_t) * (size_t)n);
+        for (int32_t i = 0; i < p->nc; ++i) trial[p->gid[i]] = side[i] ? b : a;
+        res->flow = F; res->corridor_n = p->nc; res->corridor_arcs = p->m;
+        free(side);
+        fro_free(p);
+        int64_t ncut = fro_pair_cut(n, xadj, adjncy, adjwgt, trial, a, b);
+        int64_t nA = 0, nB = 0;
+        for (int32_t v = 0; v < n; ++v) { if (trial[v] == a) nA += vwgt[v]; else if (trial[v] == b) nB += vwgt[v]; }
+        int64_t nmax = nA > nB ? nA : nB, omax = wA > wB ? wA : wB;
+        int feasible = nmax <= Lmax;
+        if (feasible && ncut < cut) {
+            memcpy(part, trial, sizeof(int32_t) * (size_t)n);
+            cut = ncut; wA = nA; wB = nB; res->accepted = 1;
+            if (!adaptive) break;
+            al = 2.0 * al < alpha_max ? 2.0 * al : alpha_max;
+            continue;
+        }
+        if (feasible) {
+            if (ncut == cut && nmax < omax) {
+                memcpy(part, trial, sizeof(int32_t) * (size_t)n);
+                cut = ncut; wA = nA; wB = nB; res->accepted = 1;
+            }
+            break;
+        }
+        if (!adaptive || al == 1.0) break;
+        al = al / 2.0 > 1.0 ? al / 2.0 : 1.0;
+    }
+    res->iters = iters;
+    res->alpha_final = al;
+    res->cut_after = cut; res->wA_after = wA; res->wB_after = wB;
+    res->status = FRO_OK;
+    free(trial);
+    return FRO_OK;
+}
+
+int32_t fro_refine_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, int32_t *part, int32_t k, int32_t a, int32_t b, double eps,
+                        double alpha, const fro_options *opt, fro_pair_result *res) {
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK) st = check_pair_args(k, a, b, eps, alpha, opt);
+    if (st != FRO_OK) { if (res) { memset(res, 0, sizeof(*res)); res->status = st; } return st; }
+    int64_t W = fro_total_weight(n, vwgt);
+    int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
+    return refine_pair_core(n, xadj, adjncy, adjwgt, vwgt, part, k, a, b, eps, alpha, opt, W, Lmax, res);
+}
+
+/* --------------------------------------------- rounds of block pairs ------ */
+
+int32_t fro_rounds(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *part, int32_t k,
+                   int32_t cap, int32_t *pair_a, int32_t *pair_b, int32_t *pair_round, int32_t *nrounds) {
+    /* quotient graph: an edge wherever two blocks are adjacent */
+    int8_t *adj = XALLOC(int8_t, (int64_t)k * k);
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            int32_t x = part[v], y = part[adjncy[j]];
+            if (x != y) adj[(int64_t)x * k + y] = 1;
+        }
+    int32_t ncol = 2 * k;
+    int8_t *used = XALLOC(int8_t, (int64_t)k * ncol);
+    int32_t np = 0, nr = 0;
+    for (int32_t a = 0; a < k; ++a)
+        for (int32_t b = a + 1; b < k; ++b) {
+            if (!adj[(int64_t)a * k + b]) continue;
+            int32_t c = 0;
+            while (used[(int64_t)a * ncol + c] || used[(int64_t)b * ncol + c]) ++c;
+            used[(int64_t)a * ncol + c] = used[(int64_t)b * ncol + c] = 1;
+            if (np < cap) { pair_a[np] = a; pair_b[np] = b; pair_round[np] = c; }
+            ++np;
+            if (c + 1 > nr) nr = c + 1;
+        }
+    free(adj); free(used);
+    if (nrounds) *nrounds = nr;
+    return np;
+}
+
+int32_t fro_refine_batch(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                         const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                         const fro_options *opt, int32_t cap, fro_pair_result *res, int32_t *npairs,
+                         int32_t *nrounds) {
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0))) st = FRO_ERR_INVALID_ARG;
+    if (st != FRO_OK) return st;
+    int64_t W = fro_total_weight(n, vwgt);
+    int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
+    int32_t maxp = k * (k - 1) / 2;
+    int32_t *pa = XALLOC(int32_t, maxp), *pb = XALLOC(int32_t, maxp), *pr = XALLOC(int32_t, maxp);
+    int32_t nr = 0;
+    int32_t np = fro_rounds(n, xadj, adjncy, part, k, maxp, pa, pb, pr, &nr);
+    int32_t out = 0;
+    for (int32_t r = 0; r < nr; ++r)
+        for (int32_t i = 0; i < np; ++i) {
+            if (pr[i] != r) continue;
+            fro_pair_result tmp;
+            refine_pair_core(n, xadj, adjncy, adjwgt, vwgt, part, k, pa[i], pb[i], eps, alpha, opt, W, Lmax, &tmp);
+            tmp.round = r;
+            if (out < cap) res[out] = tmp;
+            ++out;
+        }
+    free(pa); free(pb); free(pr);
+    if (npairs) *npairs = np;
+    if (nrounds) *nrounds = nr;
+    return FRO_OK;
+}
