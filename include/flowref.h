@@ -1,0 +1,263 @@
+/*
+ * flowref.h -- C ABI of the GB300 flow-refinement library (libflowref.so).
+ *
+ * The library improves a k-way partition of an undirected graph by max-flow /
+ * min-cut computations on block pairs (Sanders & Schulz, "Engineering
+ * Multilevel Graph Partitioning Algorithms", Section 4.1 "Using Max-Flow
+ * Min-Cut Computations for Local Improvement" and Section 4.1.1 "Most Balanced
+ * Minimum Cuts").  All compute runs in hand-written CUDA kernels for sm_103a;
+ * there is no CPU fallback.  If the device or the kernels are unavailable the
+ * calls fail with FR_ERR_CUDA.
+ *
+ * Conventions shared by every entry point
+ *   - Graph (Section 2.1): G = (V, E, c, omega), CSR with n vertices and nnz =
+ *     2|E| directed entries.  omega(e) >= 1, c(v) >= 0, int32.  The CSR must be
+ *     symmetric (v in row u iff u in row v, equal weights), simple and without
+ *     self loops; the sum of omega around any vertex must stay below 2^30.
+ *   - part[v] in [0, k) is the block of v.  All graph arrays and part are
+ *     DEVICE pointers owned by the caller unless the name says _host.
+ *   - Blocks are balanced when c(V_i) <= L_max = floor((1 + eps) c(V) / k) +
+ *     max_v c(v) (Section 2.1, integer form).
+ *   - The corridor of pair (a, b) uses eps' = alpha * eps (Section 4.1): side a
+ *     may take weight U_a = max(0, floor((1 + alpha*eps) c(V) / k) - c(V_b)),
+ *     side b likewise.  The double expression is evaluated on the host without
+ *     fused multiply-adds.
+ *   - Calls are ordered on the context's stream and synchronise before
+ *     returning (results are in host structs on return).
+ *   - part is written only when a pair's new cut is accepted; on any error it is
+ *     left unchanged.  Errors are reported by status and fr_last_error().
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef FLOWREF_H
+#define FLOWREF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fr_status {
+    FR_OK = 0,
+    FR_ERR_INVALID_ARG = 1,  /* an argument violates the conventions above */
+    FR_ERR_CUDA = 2,         /* CUDA runtime error or no usable device */
+    FR_ERR_OOM = 3,          /* the context's arena cannot hold the workspace */
+    FR_ERR_ITER_LIMIT = 4,   /* a device loop hit its cap (pulses, levels, SCC rounds) */
+    FR_ERR_TOO_LARGE = 5,    /* nnz >= 2^31 or weighted degree >= 2^30 */
+    FR_ERR_ABORTED = 6,      /* device-side barrier wait timed out or abort flag set */
+    FR_ERR_INTERNAL = 7      /* a device-side consistency check failed (e.g. cut != flow) */
+} fr_status;
+
+typedef struct fr_ctx fr_ctx;
+typedef struct fr_corridor fr_corridor;
+
+/* CSR graph, DEVICE pointers, caller-owned.  vwgt = c, adjwgt = omega. */
+typedef struct fr_graph {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *xadj;    /* [n+1], xadj[0] = 0, non-decreasing, xadj[n] = nnz */
+    const int32_t *adjncy;  /* [nnz] neighbour ids */
+    const int32_t *adjwgt;  /* [nnz] omega >= 1 */
+    const int32_t *vwgt;    /* [n]   c >= 0 */
+} fr_graph;
+
+typedef struct fr_options {
+    int32_t mb;            /* 1: most balanced minimum cut (Section 4.1.1); 0: smallest source set */
+    int32_t mb_reps;       /* R >= 1 topological sweeps; sweep r >= 1 keys components by splitmix64(seed ^ r ^ minid) */
+    int32_t adaptive;      /* 1: adaptive flow iterations (Section 4.1); fr_refine_pair only */
+    int32_t max_iters;     /* iteration cap of the adaptive loop (default 10) */
+    double alpha_max;      /* alpha' >= 1, the upper bound of alpha */
+    uint64_t seed;         /* sweep keys for r >= 1 */
+    int64_t pulse_cap;     /* push-relabel pulse cap per flow (0: default 1<<20) */
+    int32_t checked;       /* 1: verify CSR symmetry and weights on the device first */
+    int32_t block_threads; /* launch shape; 0 = tuned default (see fr_autotune) */
+    int32_t grid_blocks;   /* CTAs of the persistent kernel; 0 = tuned default */
+    int32_t gr_interval;   /* pulses between global relabels; 0 = tuned default */
+    int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
+    int32_t pad0;
+} fr_options;
+
+/* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b). */
+typedef struct fr_pair_result {
+    int64_t flow;           /* value of the maximum s-t flow of the last iteration */
+    int64_t cut_before, cut_after;
+    int64_t wA_before, wB_before, wA_after, wB_after;
+    int32_t corridor_n;     /* corridor vertices of the last iteration */
+    int32_t corridor_arcs;  /* arcs between corridor vertices (both directions) */
+    int32_t accepted;       /* 1 if part was changed */
+    int32_t iters;          /* flow iterations run */
+    double alpha_final;     /* alpha after the adaptive loop */
+    int32_t status;         /* fr_status of this pair */
+    int32_t a, b, round;    /* the pair and its round (batch) */
+    int64_t pulses;         /* push-relabel pulses of the pair's last flow (step-wide) */
+    int64_t relabels;       /* global relabels (step-wide) */
+    int32_t bfs_levels;     /* corridor BFS levels (step-wide) */
+    int32_t scc_rounds;     /* SCC colouring rounds (step-wide) */
+    int32_t ncomp;          /* SCCs outside the S and T sets (MB only) */
+    int32_t pad0;
+} fr_pair_result;
+
+typedef struct fr_batch_result {
+    int32_t npairs;         /* quotient-graph edges = pairs refined */
+    int32_t nrounds;        /* matchings (launches of the persistent kernel) */
+    int32_t accepted;       /* pairs whose cut was applied */
+    int32_t status;
+    int64_t cut_before;     /* total cut sum_{i<j} omega(E_ij) before and after */
+    int64_t cut_after;
+    int64_t corridor_arcs;  /* sum of corridor arcs over all pairs */
+    int64_t device_ns;      /* device time of the rounds (CUDA events) */
+    int64_t flow_ns;        /* device time spent in the max-flow phase (in-kernel timers) */
+} fr_batch_result;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Fills the defaults: mb 0, mb_reps 1, adaptive 0, max_iters 10, alpha_max 1,
+ * seed 0, pulse_cap 1<<20, checked 0, launch shape 0 (tuned). */
+void fr_default_options(fr_options *opt);
+
+/* Creates a context on `device` using `stream` (a cudaStream_t; NULL = a new
+ * non-blocking stream owned by the context).  arena_bytes bounds the device
+ * workspace (0 = no bound); exceeding it returns FR_ERR_OOM. */
+fr_status fr_create(fr_ctx **ctx, int32_t device, size_t arena_bytes, void *stream);
+fr_status fr_destroy(fr_ctx *ctx);
+/* Message of the last failing call on this context (static storage in ctx). */
+const char *fr_last_error(const fr_ctx *ctx);
+const char *fr_status_string(fr_status st);
+/* Bytes of device workspace the context holds now. */
+size_t fr_workspace_bytes(const fr_ctx *ctx);
+
+/* ---- the three steps of Section 4.1 on one pair --------------------------- */
+
+/* Corridor of pair (a, b) (Section 4.1): two BFS inside blocks a and b from
+ * their boundary towards the other block, vertices taken in (distance, id)
+ * order while the side's weight stays <= U_side; then the network G' = G[B] +
+ * s + t, s -> border of side a, border of side b -> t with capacity INF_v = 1 +
+ * sum of omega at v, border taken with respect to G[V_a u V_b].
+ * The corridor lives in the context's workspace: building another corridor or
+ * calling another refinement on the same context invalidates the handle (later
+ * use returns FR_ERR_INVALID_ARG).  Free with fr_corridor_free. */
+fr_status fr_build_corridor(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, int32_t a,
+                            int32_t b, double eps, double alpha, fr_corridor **out);
+fr_status fr_corridor_info(const fr_corridor *c, int32_t *corridor_n, int32_t *corridor_arcs);
+/* Copies the network to HOST buffers in a canonical layout: gid[nc] ascending
+ * global ids (local id = position), off[nc+1]/head[m]/cap[m] arcs between corridor
+ * vertices in CSR order of the graph, border[nc] (0 none, 1 s->v, 2 v->t),
+ * infcap[nc] (INF_v for border vertices, else 0), side0[nc] (0 = block a),
+ * dist[nc] (BFS distance inside the vertex's block).  Any pointer may be NULL. */
+fr_status fr_corridor_export(fr_ctx *ctx, const fr_corridor *c, int32_t *gid, int32_t *off, int32_t *head,
+                             int32_t *cap, int8_t *border, int32_t *infcap, int8_t *side0, int32_t *dist);
+/* Maximum s-t flow of the corridor network (Section 4.1): push-relabel with
+ * global relabels, then excess returned to s so that the result is a flow,
+ * not a preflow.  *flow_out receives its value. */
+fr_status fr_maxflow(fr_ctx *ctx, fr_corridor *c, int64_t *flow_out);
+/* Flow on each corridor arc (net, antisymmetric; m entries) and on the s/t arc
+ * of each corridor vertex (nc entries), HOST buffers. */
+fr_status fr_corridor_flow(fr_ctx *ctx, const fr_corridor *c, int64_t *arcflow, int64_t *stflow);
+/* Minimum cut from the residual graph and its application to part.
+ * most_balanced = 0: the smallest source set (vertices reachable from s; the
+ * Ford-Fulkerson labelling cut).  most_balanced = 1: SCCs of the residual graph
+ * outside the sets reachable from s / reaching t, mb_reps deterministic
+ * topological sweeps, the cut with the smallest |c(A') - c(B')| (Section 4.1.1).
+ * Corridor vertices on the source side go to block a, the others to block b;
+ * the result is applied to part (DEVICE, in/out) only if it is accepted:
+ * max(c(A'), c(B')) <= L_max and (cut decreases, or cut equal and
+ * max(c(A'), c(B')) decreases).  res receives the outcome. */
+fr_status fr_extract_cut(fr_ctx *ctx, fr_corridor *c, int32_t most_balanced, int32_t mb_reps, uint64_t seed,
+                         int32_t *part, fr_pair_result *res);
+/* After fr_extract_cut: residual sets and output side per corridor vertex (HOST
+ * buffers): in_s reachable from s, to_t reaches t, comp = min global id of the
+ * vertex's residual SCC (vertices in neither set, else -1), side 0 = source. */
+fr_status fr_corridor_sets(fr_ctx *ctx, const fr_corridor *c, int8_t *in_s, int8_t *to_t, int32_t *comp,
+                           int8_t *side);
+fr_status fr_corridor_free(fr_ctx *ctx, fr_corridor *c);
+
+/* ---- whole refinements ------------------------------------------------------ */
+
+/* Corridor + max flow + cut + acceptance for pair (a, b) in one persistent launch
+ * per flow iteration.  With opt->adaptive the iterations follow Section 4.1:
+ * accepted smaller cut -> alpha = min(2 alpha, alpha') and repeat; feasible cut
+ * that is not smaller -> apply if better balanced and stop; infeasible -> stop at
+ * alpha = 1, else alpha = max(alpha / 2, 1) and repeat; at most max_iters. */
+fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, int32_t a, int32_t b,
+                         double eps, double alpha, const fr_options *opt, fr_pair_result *res);
+
+/* All block pairs that are adjacent in the quotient graph of part (Section 2.1),
+ * scheduled as rounds of block-disjoint pairs: greedy colouring of the quotient
+ * edges in lexicographic (a, b) order, smallest free colour.  Each round runs as
+ * one persistent launch over the union of its pairs' flow networks; the rounds are
+ * replayed from a captured CUDA graph.  One flow iteration per pair at the given
+ * alpha.  results (HOST, capacity cap) receives the pairs in round order, then
+ * (a, b) order.  Equivalent to fr_refine_pair over the pairs in that order. */
+fr_status fr_refine_batch(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
+                          const fr_options *opt, int32_t cap, fr_pair_result *results, fr_batch_result *summary);
+
+/* Same as fr_refine_batch for a graph and partition in HOST memory: uploads the
+ * arrays, refines, and copies part back (the end-to-end form; graph buffers are
+ * reused across calls of the same size). */
+fr_status fr_refine_batch_host(fr_ctx *ctx, int32_t n, int32_t nnz, const int32_t *xadj_host,
+                               const int32_t *adjncy_host, const int32_t *adjwgt_host, const int32_t *vwgt_host,
+                               int32_t *part_host, int32_t k, double eps, double alpha, const fr_options *opt,
+                               int32_t cap, fr_pair_result *results, fr_batch_result *summary);
+
+/* Rounds of the quotient graph of part (HOST outputs, capacity cap): pair_a <
+ * pair_b in lexicographic order and the round of each.  Returns counts. */
+fr_status fr_rounds(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, int32_t cap, int32_t *pair_a,
+                    int32_t *pair_b, int32_t *pair_round, int32_t *npairs, int32_t *nrounds);
+
+/* ---- launch-shape autotuner -------------------------------------------------- */
+
+/* Times fr_refine_batch on a copy of part for a set of launch shapes
+ * (block_threads, grid_blocks, gr_interval, inner_ops) and writes the fastest into
+ * *best.  Results are identical for every shape; only time differs.  The choice is
+ * also cached in the context and used when opt fields are 0. */
+fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, double eps, double alpha,
+                      const fr_options *opt, int32_t trials, fr_options *best, double *best_ms);
+
+/* ---- serving: continuous batching of refinement requests ------------------- */
+
+typedef struct fr_server fr_server;
+
+typedef struct fr_server_config {
+    int32_t device;
+    int32_t max_inflight;    /* requests resident on the device at once */
+    size_t arena_bytes;      /* device bytes for request workspaces (admission bound) */
+    fr_options opt;          /* options applied to every request */
+} fr_server_config;
+
+typedef struct fr_request {
+    int32_t graph_id;        /* from fr_server_add_graph */
+    int32_t k;
+    double eps, alpha;
+    const int32_t *part_host;/* initial partition, HOST, copied at submit */
+    uint64_t tag;            /* caller's id, returned with the result */
+} fr_request;
+
+typedef struct fr_response {
+    uint64_t tag;
+    int32_t status, npairs, nrounds, accepted;
+    int64_t cut_before, cut_after;
+    double latency_ms;       /* submit -> completion, host clock */
+    double queue_ms;         /* submit -> admission */
+} fr_response;
+
+fr_status fr_server_create(fr_server **srv, const fr_server_config *cfg);
+/* Copies a graph (HOST arrays) to the device once; requests refer to it by id. */
+fr_status fr_server_add_graph(fr_server *srv, int32_t n, int32_t nnz, const int32_t *xadj, const int32_t *adjncy,
+                              const int32_t *adjwgt, const int32_t *vwgt, int32_t *graph_id);
+/* Queues a request (non-blocking).  Requests are admitted when a slot and enough
+ * arena bytes are free; admitted requests advance one round per device step, so
+ * requests that arrive while others run join the next step. */
+fr_status fr_server_submit(fr_server *srv, const fr_request *req);
+/* Blocks until one result is available (timeout_ms < 0: wait forever) and copies
+ * the refined partition into part_out (HOST, may be NULL). */
+fr_status fr_server_next(fr_server *srv, fr_response *resp, int32_t *part_out, int32_t part_cap,
+                         int32_t timeout_ms);
+fr_status fr_server_stats(fr_server *srv, int64_t *steps, int64_t *admitted, int64_t *completed,
+                          int32_t *max_concurrent);
+fr_status fr_server_destroy(fr_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLOWREF_H */

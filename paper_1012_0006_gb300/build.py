@@ -27,6 +27,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 
 CUDA_SOURCES = [
     "api.cu",
+    "api_batch.cu",
     "round_kernel.cu",
     "prep_kernel.cu",
     "serve.cu",

@@ -1,0 +1,108 @@
+// Context and host-side helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "flowref.h"
+#include "fr_internal.cuh"
+#include "round_kernel.cuh"
+
+constexpr int kMaxK = 1024;                 // blocks per partition (quotient graph in device bitmaps)
+constexpr size_t kHostStage = 8u << 20;     // pinned staging for small host<->device copies
+
+struct GraphCacheEntry {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct fr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t arena_limit = 0;
+    char err[512] = {0};
+    int sms = 0, max_coop = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    char *h_stage = nullptr;
+    // launch shape (fr_autotune writes these)
+    int tune_tpb = 512, tune_grid = 0, tune_gr = 8, tune_inner = 4;
+    // graph-size workspace
+    void *base_mem = nullptr;
+    size_t base_bytes = 0;
+    int n_cap = 0, nnz_cap = 0, k_cap = 0, reps_cap = 0;
+    int *dist = nullptr, *lid = nullptr, *vq_v = nullptr, *vq_s = nullptr;
+    int *gid = nullptr, *sid = nullptr, *off = nullptr, *infc = nullptr, *fx = nullptr, *lab = nullptr;
+    int *rflag = nullptr, *color = nullptr, *scc = nullptr, *vc = nullptr, *fq0 = nullptr, *fq1 = nullptr;
+    int *spare = nullptr;
+    long long *ex = nullptr;
+    unsigned char *border = nullptr, *side_out = nullptr;
+    int *head = nullptr, *rev = nullptr, *res = nullptr, *cap = nullptr;
+    int *cta_cnt = nullptr;
+    long long *cw = nullptr;
+    int *cpair = nullptr, *cmin = nullptr, *cid = nullptr, *indeg = nullptr, *outoff = nullptr, *ocur = nullptr;
+    int *plist = nullptr, *sinkc = nullptr, *part_backup = nullptr, *outs = nullptr;
+    int *indeg_r = nullptr, *order = nullptr, *hcomp = nullptr;
+    unsigned long long *hkey = nullptr;
+    long long *blockw = nullptr;
+    unsigned int *qbits = nullptr, *used = nullptr;
+    int *sob_round = nullptr, *pair_a = nullptr, *pair_b = nullptr, *pair_round = nullptr, *round_off = nullptr;
+    fr::PrepOut *prep = nullptr;
+    int *sob1 = nullptr, *flags = nullptr;
+    // pair-count workspace
+    void *pair_mem = nullptr;
+    size_t pair_bytes = 0;
+    int pairs_cap = 0, rounds_cap = 0, reps_cap_pairs = 0;
+    fr::GraphDev *graphs = nullptr;
+    fr::PairDev *pairs = nullptr;
+    fr::SideDev *sides = nullptr;
+    fr::PairAcc *pacc = nullptr;
+    fr::Ctl *ctl = nullptr;
+    long long *hist = nullptr;
+    int *pcur = nullptr;
+    long long *sw_absd = nullptr;
+    int *sw_j = nullptr;
+    bool graph_valid = false;
+    // corridor handle state
+    unsigned long long gen = 0;
+    fr_corridor *live = nullptr;
+    bool dirty = false;
+    // device copies of host graphs (fr_refine_batch_host)
+    void *hg_mem = nullptr;
+    size_t hg_bytes = 0;
+    int *hg_xadj = nullptr, *hg_adjncy = nullptr, *hg_adjwgt = nullptr, *hg_vwgt = nullptr, *hg_part = nullptr;
+    // captured CUDA graphs of batch sweeps
+    std::vector<GraphCacheEntry> gcache;
+    bool use_graphs = true;
+    long long last_launches = 0;   // kernels launched by the last call
+};
+
+struct fr_corridor {
+    fr_ctx *ctx;
+    unsigned long long gen;
+    int nc, m, k, a, b, stage;
+    int32_t *part;
+    fr_graph g;
+    long long Ubase, Lmax;
+};
+
+void ctx_error(fr_ctx *ctx, const char *fmt, ...);
+fr_status cuda_fail(fr_ctx *ctx, cudaError_t e, const char *what);
+long long host_budget_base(long long W, int k, double eps, double alpha);
+long long host_lmax(long long W, long long maxc, int k, double eps);
+fr_status status_from_ctl(fr_ctx *ctx, const fr::Ctl &c, const char *where);
+fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps);
+fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps);
+fr::Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt);
+int choose_tpb(fr_ctx *ctx, const fr_options *opt);
+int choose_grid(fr_ctx *ctx, const fr_options *opt, int tpb, int nsides, long long est_vertices);
+fr_status check_graph(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k);
+fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *opt);
+fr_status run_prep(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, bool quotient, bool checked,
+                   fr::PrepOut *host_out);
+fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, int32_t a, int32_t b,
+                       long long Ubase, long long Lmax, int mb);
+fr_status reset_idle(fr_ctx *ctx);
+void release_corridor(fr_ctx *ctx);
+void destroy_graph_cache(fr_ctx *ctx);

@@ -1,0 +1,1415 @@
+// Kernels of one refinement step: the boundary scan and the persistent step
+// kernel (Sanders & Schulz, Section 4.1 and 4.1.1).
+//
+// A step refines a set of block-disjoint pairs (one pair, or one round of a
+// matching of the quotient graph).  All pairs' corridors form one union network;
+// every phase runs grid-wide over that union, so uneven corridors share the GPU
+// instead of each pair waiting for its own launch.
+//
+//   scan_kernel      full CSR pass: boundary delta_a / delta_b of every pair
+//                    (BFS level 0) and the pair cut omega(E_ab); HBM bound
+//   step_kernel      cooperative persistent kernel, grid barriers between phases
+//     PH_BFS         level-synchronous BFS per side, overflow level picked by a
+//                    weighted radix select on vertex ids ((distance, id) order)
+//     PH_LID         local ids in (graph, id) order: scan over the vertex range
+//     PH_BUILD       corridor CSR with reverse arcs, INF_v border arcs
+//     PH_FLOW        push-relabel (lock-free pulses, global relabel by reverse BFS
+//                    from t), then excess returned to s: a maximum flow
+//     PH_CUT         reachability from s / to t; MB: SCC colouring, DAG, sweeps
+//     PH_EVAL        new weights, cut change, cut == flow check, acceptance
+//     PH_COMMIT      apply accepted pairs to part, release dist / lid
+#include <climits>
+
+#include "fr_internal.cuh"
+#include "round_kernel.cuh"
+
+namespace fr {
+
+#define FULL 0xffffffffu
+
+// ====================================================================== scan ==
+
+template <int TPB, bool VEC>
+__global__ void __launch_bounds__(TPB) scan_kernel(Work w, int g) {
+    extern __shared__ long long s_cut[];   // [npairs]
+    __shared__ int s_seed[TPB];
+    if (w.prev_err && __ldcg(w.prev_err)) {   // an earlier round failed: propagate, do nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) { w.ctl->error = E_ABORT; w.ctl->error_where = 999; }
+        return;
+    }
+    const GraphDev G = w.graphs[g];
+    for (int i = threadIdx.x; i < w.npairs; i += TPB) s_cut[i] = 0;
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < w.nsides; s += TPB) {
+            const PairDev P = w.pairs[s >> 1];
+            if (P.g == g) w.sides[s].cw = G.blockw[(s & 1) ? P.b : P.a];
+        }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wslot = threadIdx.x & ~31;
+    const long long nw = (long long)gridDim.x * (TPB / 32);
+    const long long gw = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
+    const int n = G.n, nnz = G.nnz;
+    const int *__restrict__ xadj = G.xadj;
+    const int *__restrict__ adjncy = G.adjncy;
+    const int *__restrict__ part = G.part;
+    const int e_end = __ldg(xadj + n);
+    for (long long base = gw * 32; base < n; base += nw * 32) {
+        const int v = (int)(base + lane);
+        const bool valid = v < n;
+        const int blk = valid ? __ldg(part + v) : -1;
+        const int sd = valid ? __ldg(G.sob + blk) : -1;
+        if (__ballot_sync(FULL, sd >= 0) == 0) continue;
+        int pb = -2;
+        if (sd >= 0) {
+            const PairDev P = w.pairs[sd >> 1];
+            pb = (sd & 1) ? P.a : P.b;
+        }
+        const int rs = valid ? __ldg(xadj + v) : e_end;
+        const int re = valid ? __ldg(xadj + v + 1) : e_end;
+        s_seed[threadIdx.x] = 0;
+        __syncwarp();
+        const int e0 = __shfl_sync(FULL, rs, 0);
+        const int e1 = __shfl_sync(FULL, re, 31);
+        for (int ea = VEC ? (e0 & ~3) : e0; ea < e1; ea += VEC ? 128 : 32) {
+            int u4[4] = {0, 0, 0, 0};
+            int q;
+            if (VEC) {
+                q = ea + 4 * lane;
+                if (q + 3 < nnz) {
+                    const int4 x = __ldg(reinterpret_cast<const int4 *>(adjncy + q));
+                    u4[0] = x.x; u4[1] = x.y; u4[2] = x.z; u4[3] = x.w;
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) u4[t] = (q + t < nnz) ? __ldg(adjncy + q + t) : 0;
+                }
+            } else {
+                q = ea + lane;
+                u4[0] = q < e1 ? __ldg(adjncy + q) : 0;
+            }
+#pragma unroll
+            for (int t = 0; t < (VEC ? 4 : 1); ++t) {
+                const int e = q + t;
+                const bool act = e >= e0 && e < e1;
+                int src = 0;   // source row: the last lane whose row starts at or before e
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int rc = __shfl_sync(FULL, rs, src + step);
+                    if (rc <= e) src += step;
+                }
+                const int sd_s = __shfl_sync(FULL, sd, src);
+                const int pb_s = __shfl_sync(FULL, pb, src);
+                const int blk_s = __shfl_sync(FULL, blk, src);
+                if (act && sd_s >= 0) {
+                    const int pu = __ldg(part + u4[t]);
+                    if (pu == pb_s) {
+                        s_seed[wslot + src] = 1;
+                        if (blk_s < pb_s)
+                            atomicAdd((unsigned long long *)&s_cut[sd_s >> 1],
+                                      (unsigned long long)__ldg(G.adjwgt + e));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        const bool seed = sd >= 0 && s_seed[threadIdx.x] != 0;
+        if (seed) G.dist[v] = 0;
+        const int pos = warp_agg_inc(&w.ctl->qcnt[0], seed);
+        if (seed) {
+            if (pos < w.vq_cap) {
+                w.vq_v[pos] = v;
+                w.vq_s[pos] = sd;
+            } else {
+                fail(w.ctl, E_INTERNAL, 1);
+            }
+        }
+        warp_agg_add(seed ? &w.sides[sd].lw[0] : nullptr, seed ? (long long)__ldg(G.vwgt + v) : 0, seed);
+        warp_agg_inc(seed ? &w.sides[sd].lc[0] : nullptr, seed);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < w.npairs; i += TPB)
+        if (s_cut[i]) atomicAddLL(&w.pacc[i].oldcut, s_cut[i]);
+}
+
+// ============================================================ step helpers ==
+
+struct Grid {
+    long long tid, size, warp, nwarps;
+    __device__ Grid(int tpb) {
+        tid = (long long)blockIdx.x * tpb + threadIdx.x;
+        size = (long long)gridDim.x * tpb;
+        warp = tid >> 5;
+        nwarps = size >> 5;
+    }
+};
+
+// Warp-cooperative walk over the arcs of many rows: each warp takes 32 rows,
+// flattens their arc ranges and visits 32 arcs per iteration with all lanes
+// converged, so appends can be aggregated with one atomic per warp.
+template <class RowF, class ArcF>
+__device__ __forceinline__ void warp_rows(long long begin, long long end, const Grid &G, RowF row, ArcF arc) {
+    const int lane = threadIdx.x & 31;
+    for (long long b = begin + G.warp * 32; b < end; b += G.nwarps * 32) {
+        const long long idx = b + lane;
+        int rs = 0, deg = 0, ctx = 0;
+        if (idx < end) row(idx, rs, deg, ctx);
+        int incl = deg;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - deg;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(FULL, incl, src + step - 1) <= t) src += step;
+            const int rs_s = __shfl_sync(FULL, rs, src);
+            const int ex_s = __shfl_sync(FULL, excl, src);
+            const int ctx_s = __shfl_sync(FULL, ctx, src);
+            const bool valid = t < total;
+            arc(valid, rs_s + (t - ex_s), ctx_s);
+        }
+    }
+}
+
+// Append a lane's element to a queue with one atomic per warp.  Returns the slot or -1.
+__device__ __forceinline__ int warp_append(int *counter, bool want) {
+    const unsigned int m = __ballot_sync(FULL, want);
+    if (m == 0) return -1;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(FULL, base, __ffs(m) - 1);
+    return want ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+__device__ __forceinline__ void timer_mark(const Work &w, unsigned long long &t0, int idx) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t1 = globaltimer();
+        w.ctl->timers[idx] += (long long)(t1 - t0);
+        t0 = t1;
+    }
+}
+
+// Ranks of elements in index order over [0, N): val(x) >= 0 is the element's
+// count; emit(x, offset) is called for every x (offset = exclusive prefix).
+// Chunked per CTA: count pass, barrier, prefix of CTA totals, write pass.
+template <int TPB, class ValF, class EmitF>
+__device__ bool grid_scan(const Work &w, long long N, ValF val, EmitF emit, long long *total_out) {
+    const long long per = ((N + gridDim.x - 1) / gridDim.x + TPB - 1) / TPB * TPB;
+    const long long c0 = per * blockIdx.x, c1 = min(N, c0 + per);
+    long long mine = 0;
+    for (long long x = c0 + threadIdx.x; x < c1; x += TPB) mine += val(x);
+    long long tot = block_sum_ll<TPB>(mine);
+    if (threadIdx.x == 0) w.cta_cnt[blockIdx.x] = (int)tot;
+    if (!grid_sync(w.ctl)) return false;
+    long long before = 0, all = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += TPB) {
+        const long long c = __ldcg(&w.cta_cnt[b]);
+        all += c;
+        if (b < (int)blockIdx.x) before += c;
+    }
+    __shared__ long long s_before, s_all;
+    long long bsum = block_sum_ll<TPB>(before);
+    long long asum = block_sum_ll<TPB>(all);
+    if (threadIdx.x == 0) { s_before = bsum; s_all = asum; }
+    __syncthreads();
+    long long run = s_before;
+    for (long long x0 = c0; x0 < c1; x0 += TPB) {
+        const long long x = x0 + threadIdx.x;
+        const int v = x < c1 ? val(x) : 0;
+        int tile_total;
+        const int excl = block_exclusive_scan<TPB>(v, &tile_total);
+        if (x < c1) emit(x, run + excl);
+        run += tile_total;
+    }
+    if (total_out) *total_out = s_all;
+    return true;
+}
+
+// ============================================================== step kernel ==
+
+template <int TPB>
+struct StepKernel {
+    const Work &w;
+    const Grid G;
+    int fl, pl, cl;   // running indices of the triple-buffered counters (identical in every CTA)
+    long long vtotal; // BFS entries in the visit list
+    int *s_state, *s_lstar, *s_T;
+    long long *s_wcum, *s_rem, *s_lw;
+    int *s_lc;
+
+    __device__ StepKernel(const Work &w_, int *smem) : w(w_), G(TPB) {
+        const int ns = w.nsides;
+        fl = w.ctl->fl;
+        pl = w.ctl->pl;
+        cl = w.ctl->cl;
+        vtotal = w.ctl->vq_total;
+        s_wcum = reinterpret_cast<long long *>(smem);
+        s_rem = s_wcum + ns;
+        s_lw = s_rem + ns;
+        s_state = reinterpret_cast<int *>(s_lw + ns);
+        s_lstar = s_state + ns;
+        s_T = s_lstar + ns;
+        s_lc = s_T + ns;
+    }
+
+    // U_side = max(0, Ubase - c(other block))
+    __device__ long long budget(int s) const {
+        const long long U = w.pairs[s >> 1].Ubase - __ldcg(&w.sides[s ^ 1].cw);
+        return U < 0 ? 0 : U;
+    }
+
+    __device__ void save_indices() const {
+        if (G.tid == 0) {
+            w.ctl->fl = fl;
+            w.ctl->pl = pl;
+            w.ctl->cl = cl;
+        }
+    }
+
+    // ---------------------------------------------------------------- BFS --
+    __device__ bool bfs() {
+        Ctl *ctl = w.ctl;
+        const int ns = w.nsides;
+        unsigned long long t0 = globaltimer();
+        for (int s = threadIdx.x; s < ns; s += TPB) {
+            s_state[s] = SS_EXPAND;
+            s_lstar[s] = INT_MAX;
+            s_wcum[s] = 0;
+            s_rem[s] = 0;
+            s_T[s] = INT_MAX;
+        }
+        __syncthreads();
+        int level = 0;
+        long long base = 0, arcs = 0;
+        for (;;) {
+            const int cnt = __ldcg(&ctl->qcnt[level % 3]);
+            bool any = false;
+            for (int s = threadIdx.x; s < ns; s += TPB) {
+                SideDev *S = &w.sides[s];
+                if (s_state[s] == SS_EXPAND) {
+                    const long long U = budget(s);
+                    const long long W = __ldcg(&S->lw[level % 3]);
+                    const int c = __ldcg(&S->lc[level % 3]);
+                    if (c == 0) {
+                        s_state[s] = SS_DONE;                 // BFS exhausted its block
+                    } else if (s_wcum[s] + W <= U) {
+                        s_wcum[s] += W;                       // whole level fits
+                        any = true;
+                    } else {
+                        s_state[s] = SS_SELECT;               // overflow level: take an id prefix
+                        s_lstar[s] = level;
+                        s_rem[s] = U - s_wcum[s];
+                    }
+                    if (blockIdx.x == 0) S->U = U;
+                }
+                if (blockIdx.x == 0) {
+                    S->lw[(level + 2) % 3] = 0;
+                    S->lc[(level + 2) % 3] = 0;
+                }
+                s_lw[s] = 0;
+                s_lc[s] = 0;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qcnt[(level + 2) % 3] = 0;
+            any = __syncthreads_or(any);
+            if (!any) {
+                vtotal = base + cnt;
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    ctl->vq_total = (int)vtotal;
+                    ctl->levels = level + 1;
+                }
+                break;
+            }
+            const long long next_base = base + cnt;
+            int *qc = &ctl->qcnt[(level + 1) % 3];
+            const int nlev = level + 1;
+            warp_rows(
+                base, base + cnt, G,
+                [&](long long e, int &rs, int &deg, int &ctx) {
+                    const int v = w.vq_v[e], s = w.vq_s[e];
+                    if (s_state[s] != SS_EXPAND) return;
+                    const GraphDev &Gr = w.graphs[w.pairs[s >> 1].g];
+                    rs = __ldg(Gr.xadj + v);
+                    deg = __ldg(Gr.xadj + v + 1) - rs;
+                    ctx = s;
+                },
+                [&](bool valid, int e, int s) {
+                    bool got = false;
+                    int u = 0;
+                    if (valid) {
+                        const PairDev P = w.pairs[s >> 1];
+                        const GraphDev &Gr = w.graphs[P.g];
+                        const int blk = (s & 1) ? P.b : P.a;
+                        u = __ldg(Gr.adjncy + e);
+                        if (Gr.part[u] == blk && __ldcg(Gr.dist + u) == -1)
+                            got = atomicCAS(Gr.dist + u, -1, nlev) == -1;
+                        ++arcs;
+                    }
+                    const int slot = warp_append(qc, got);
+                    if (got) {
+                        const long long idx = next_base + slot;
+                        if (idx < w.vq_cap) {
+                            w.vq_v[idx] = u;
+                            w.vq_s[idx] = s;
+                        } else {
+                            fail(w.ctl, E_INTERNAL, 10);
+                        }
+                        const GraphDev &Gr = w.graphs[w.pairs[s >> 1].g];
+                        atomicAdd((unsigned long long *)&s_lw[s], (unsigned long long)__ldg(Gr.vwgt + u));
+                        atomicAdd(&s_lc[s], 1);
+                    }
+                });
+            __syncthreads();
+            for (int s = threadIdx.x; s < ns; s += TPB) {
+                if (s_lw[s]) atomicAddLL(&w.sides[s].lw[nlev % 3], s_lw[s]);
+                if (s_lc[s]) atomicAdd(&w.sides[s].lc[nlev % 3], s_lc[s]);
+            }
+            base = next_base;
+            if (!grid_sync(ctl)) return false;
+            level = nlev;
+            if (level > w.total_n + 1) {
+                fail(ctl, E_ITER, 11);
+                return false;
+            }
+        }
+        if (arcs) atomicAdd((unsigned long long *)&ctl->arcs_scanned, (unsigned long long)arcs);
+        timer_mark(w, t0, T_BFS);
+        return select(t0);
+    }
+
+    // Weighted radix select per SELECT side: the overflow vertex v* is the first
+    // vertex of level lstar, in id order, at which the running weight exceeds rem;
+    // vertices of that level with id < v* are taken.
+    __device__ bool select(unsigned long long &t0) {
+        Ctl *ctl = w.ctl;
+        const int ns = w.nsides;
+        bool anysel = false;
+        for (int s = threadIdx.x; s < ns; s += TPB) anysel |= s_state[s] == SS_SELECT;
+        anysel = __syncthreads_or(anysel);
+        const long long total = vtotal;
+        if (anysel) {
+            for (int s = threadIdx.x; s < ns; s += TPB) s_T[s] = 0;   // prefix being built
+            __syncthreads();
+            // histograms are triple buffered: pass p fills buffer p % 3 (cleared by the
+            // host or during pass p - 2) and clears buffer (p + 1) % 3, last read in pass p - 2
+            const long long hsz = (long long)ns * kHistBins;
+            for (int pass = 0; pass < 4; ++pass) {
+                const int shift = 24 - 8 * pass;
+                long long *hist = w.hist + (pass % 3) * hsz;
+                if (pass >= 1) {
+                    long long *nxt = w.hist + ((pass + 1) % 3) * hsz;
+                    for (long long i = G.tid; i < hsz; i += G.size) nxt[i] = 0;
+                }
+                for (long long e = G.tid; e < total; e += G.size) {
+                    const int v = w.vq_v[e], s = w.vq_s[e];
+                    if (s_state[s] != SS_SELECT) continue;
+                    const GraphDev &Gr = w.graphs[w.pairs[s >> 1].g];
+                    if (__ldcg(Gr.dist + v) != s_lstar[s]) continue;
+                    if (pass > 0 && ((unsigned)v >> (shift + 8)) != ((unsigned)s_T[s] >> (shift + 8))) continue;
+                    const int digit = ((unsigned)v >> shift) & 255;
+                    atomicAdd((unsigned long long *)&hist[(long long)s * kHistBins + digit],
+                              (unsigned long long)__ldg(Gr.vwgt + v));
+                }
+                if (!grid_sync(ctl)) return false;
+                // every CTA picks the same bucket for every side
+                for (int s = threadIdx.x; s < ns; s += TPB) {
+                    if (s_state[s] != SS_SELECT) continue;
+                    long long acc = 0;
+                    int b = 0;
+                    for (; b < kHistBins; ++b) {
+                        const long long h = __ldcg(&hist[(long long)s * kHistBins + b]);
+                        if (acc + h > s_rem[s]) break;
+                        acc += h;
+                    }
+                    if (b == kHistBins) {   // cannot happen: the level's weight exceeds rem
+                        fail(ctl, E_INTERNAL, 20);
+                        b = kHistBins - 1;
+                    }
+                    s_rem[s] -= acc;
+                    s_T[s] |= b << shift;
+                }
+                __syncthreads();
+            }
+        }
+        if (blockIdx.x == 0) {
+            for (int s = threadIdx.x; s < ns; s += TPB) {
+                SideDev *S = &w.sides[s];
+                S->state = s_state[s];
+                S->lstar = s_lstar[s];
+                S->T = s_state[s] == SS_SELECT ? s_T[s] : INT_MAX;
+                S->wcum = s_wcum[s];
+                S->rem = s_rem[s];
+            }
+        }
+        for (int s = threadIdx.x; s < ns; s += TPB)
+            if (s_state[s] != SS_SELECT) s_T[s] = INT_MAX;
+        __syncthreads();
+        timer_mark(w, t0, T_SELECT);
+        return true;
+    }
+
+    __device__ bool in_corridor(const GraphDev &Gr, int v) const {
+        const int d = __ldcg(Gr.dist + v);
+        if (d < 0) return false;
+        const int s = __ldg(Gr.sob + Gr.part[v]);
+        if (s < 0) return false;
+        const int ls = s_lstar[s];
+        return d < ls || (d == ls && v < s_T[s]);
+    }
+
+    __device__ int graph_of(long long x) const {
+        int g = 0;
+        while (g + 1 < w.ngraphs && w.graphs[g + 1].base <= x) ++g;
+        return g;
+    }
+
+    // -------------------------------------------------------------- local ids --
+    __device__ bool lids() {
+        unsigned long long t0 = globaltimer();
+        long long nu = 0;
+        bool ok = grid_scan<TPB>(
+            w, w.total_n,
+            [&](long long x) -> int {
+                const int g = graph_of(x);
+                const GraphDev &Gr = w.graphs[g];
+                return in_corridor(Gr, (int)(x - Gr.base)) ? 1 : 0;
+            },
+            [&](long long x, long long off) {
+                const int g = graph_of(x);
+                const GraphDev &Gr = w.graphs[g];
+                const int v = (int)(x - Gr.base);
+                if (in_corridor(Gr, v)) {
+                    if (off < w.nu_cap) {
+                        Gr.lid[v] = (int)off;
+                        w.gid[off] = v;
+                        w.sid[off] = __ldg(Gr.sob + Gr.part[v]);
+                    } else {
+                        fail(w.ctl, E_INTERNAL, 30);
+                    }
+                }
+            },
+            &nu);
+        if (!ok) return false;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            w.ctl->nu = (int)nu;
+            w.ctl->hmax = (int)nu + 2;
+        }
+        if (!grid_sync(w.ctl)) return false;
+        timer_mark(w, t0, T_LID);
+        return true;
+    }
+
+    // ---------------------------------------------------------- network build --
+    __device__ bool build() {
+        unsigned long long t0 = globaltimer();
+        Ctl *ctl = w.ctl;
+        const int nu = __ldcg(&ctl->nu);
+        // degree, border, INF_v
+        for (long long b0 = G.warp * 32; b0 < nu; b0 += G.nwarps * 32) {
+            const long long i = b0 + (threadIdx.x & 31);
+            const bool valid = i < nu;
+            int cnt = 0, p = 0;
+            if (valid) {
+                const int v = w.gid[i], s = w.sid[i];
+                p = s >> 1;
+                const PairDev P = w.pairs[p];
+                const GraphDev &Gr = w.graphs[P.g];
+                int bor = 0;
+                long long wdeg = 0;
+                const int j1 = __ldg(Gr.xadj + v + 1);
+                for (int j = __ldg(Gr.xadj + v); j < j1; ++j) {
+                    const int u = __ldg(Gr.adjncy + j);
+                    wdeg += __ldg(Gr.adjwgt + j);
+                    const int pu = Gr.part[u];
+                    if (pu != P.a && pu != P.b) continue;
+                    if (__ldcg(Gr.lid + u) >= 0) ++cnt; else bor = 1;
+                }
+                w.off[i] = cnt;   // degree for now
+                w.border[i] = bor ? ((s & 1) ? 2 : 1) : 0;
+                w.infc[i] = (int)(wdeg + 1);
+            }
+            warp_agg_add_i(valid ? &w.pacc[p].nc : nullptr, 1, valid);
+            warp_agg_add_i(valid ? &w.pacc[p].m : nullptr, cnt, valid);
+        }
+        if (!grid_sync(ctl)) return false;
+        // offsets: exclusive scan of the degrees (in place via the deg copy in rev)
+        for (long long i = G.tid; i < nu; i += G.size) w.rev[i] = w.off[i];
+        if (!grid_sync(ctl)) return false;
+        long long mu = 0;
+        bool ok = grid_scan<TPB>(
+            w, nu, [&](long long i) -> int { return __ldcg(&w.rev[i]); },
+            [&](long long i, long long off) { w.off[i] = (int)off; }, &mu);
+        if (!ok) return false;
+        if (mu > w.mu_cap) {
+            if (G.tid == 0) fail(ctl, E_INTERNAL, 40);
+        }
+        if (G.tid == 0) {
+            w.off[nu] = (int)mu;
+            ctl->mu = (int)mu;
+        }
+        if (!grid_sync(ctl)) return false;
+        // arcs, reverse arcs, residual = capacity, preflow initialisation
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int v = w.gid[i], s = w.sid[i];
+            const PairDev P = w.pairs[s >> 1];
+            const GraphDev &Gr = w.graphs[P.g];
+            int j = __ldcg(&w.off[i]);
+            const int j1 = __ldg(Gr.xadj + v + 1);
+            for (int e = __ldg(Gr.xadj + v); e < j1; ++e) {
+                const int u = __ldg(Gr.adjncy + e);
+                const int pu = Gr.part[u];
+                if (pu != P.a && pu != P.b) continue;
+                const int h = __ldcg(Gr.lid + u);
+                if (h < 0) continue;
+                const int c = __ldg(Gr.adjwgt + e);
+                w.head[j] = h;
+                w.cap[j] = c;
+                w.res[j] = c;
+                // position of v among u's corridor arcs
+                int q = 0;
+                const int k1 = __ldg(Gr.xadj + u + 1);
+                for (int f = __ldg(Gr.xadj + u); f < k1; ++f) {
+                    const int x = __ldg(Gr.adjncy + f);
+                    if (x == v) break;
+                    const int px = Gr.part[x];
+                    if ((px == P.a || px == P.b) && __ldcg(Gr.lid + x) >= 0) ++q;
+                }
+                w.rev[j] = __ldcg(&w.off[h]) + q;
+                ++j;
+            }
+            const unsigned char bd = w.border[i];
+            const int fx0 = bd == 1 ? w.infc[i] : 0;   // saturate s -> v
+            w.fx[i] = fx0;
+            w.ex[i] = fx0;
+            w.lab[i] = 0;
+        }
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_BUILD);
+        return true;
+    }
+
+    // ------------------------------------------------------------- max flow --
+
+    // Exact distance labels by reverse BFS over residual arcs, from t (phase 1)
+    // or from s (phase 2).  Vertices that cannot reach the target get hmax.
+    __device__ bool global_relabel(int phase2, int hmax, int nu) {
+        Ctl *ctl = w.ctl;
+        {
+            int *cnt = &ctl->fcnt[(fl + 1) % 3];
+            int *q = ((fl + 1) & 1) ? w.fq1 : w.fq0;
+            for (long long b = G.warp * 32; b < nu; b += G.nwarps * 32) {
+                const long long i = b + (threadIdx.x & 31);
+                bool src = false;
+                if (i < nu) {
+                    const unsigned char bd = w.border[i];
+                    src = phase2 ? (bd == 1 && __ldcg(&w.fx[i]) > 0) : (bd == 2);
+                    w.lab[i] = src ? 1 : hmax;
+                }
+                const int slot = warp_append(cnt, src);
+                if (src) q[slot] = (int)i;
+            }
+            if (G.tid == 0) ctl->fcnt[(fl + 2) % 3] = 0;
+            if (!grid_sync(ctl)) return false;
+            ++fl;
+        }
+        long long arcs = 0;
+        for (int d = 1;; ++d) {
+            const int cur = __ldcg(&ctl->fcnt[fl % 3]);
+            if (cur == 0) break;
+            const int *q = (fl & 1) ? w.fq1 : w.fq0;
+            int *nq = ((fl + 1) & 1) ? w.fq1 : w.fq0;
+            int *ncnt = &ctl->fcnt[(fl + 1) % 3];
+            warp_rows(
+                0, cur, G,
+                [&](long long e, int &rs, int &deg, int &ctx) {
+                    const int x = q[e];
+                    rs = w.off[x];
+                    deg = w.off[x + 1] - rs;
+                    ctx = x;
+                },
+                [&](bool valid, int j, int x) {
+                    bool got = false;
+                    int y = 0;
+                    if (valid) {
+                        ++arcs;
+                        y = w.head[j];
+                        if (__ldcg(&w.res[w.rev[j]]) > 0 && __ldcg(&w.lab[y]) == hmax)
+                            got = atomicCAS(&w.lab[y], hmax, d + 1) == hmax;
+                    }
+                    const int slot = warp_append(ncnt, got);
+                    if (got) nq[slot] = y;
+                    (void)x;
+                });
+            if (G.tid == 0) ctl->fcnt[(fl + 2) % 3] = 0;
+            if (!grid_sync(ctl)) return false;
+            ++fl;
+            if (d > nu + 2) {
+                fail(ctl, E_ITER, 50);
+                return false;
+            }
+        }
+        if (G.tid == 0) ctl->relabels += 1;
+        if (arcs) atomicAdd((unsigned long long *)&ctl->gr_arcs, (unsigned long long)arcs);
+        return true;
+    }
+
+    // One pulse of lock-free push-relabel (every active vertex pushes to its
+    // lowest residual neighbour or relabels, a few times).  Counts vertices that
+    // may be active afterwards.
+    __device__ void pulse(int phase2, int hmax, int nu, int *act) {
+        int local = 0;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            long long e = __ldcg(&w.ex[i]);
+            if (e <= 0) continue;
+            int h = __ldcg(&w.lab[i]);
+            if (h >= hmax) continue;
+            const int j0 = w.off[i], j1 = w.off[i + 1];
+            const unsigned char bd = w.border[i];
+            for (int it = 0; it < w.inner; ++it) {
+                int hmin = INT_MAX, best = -1;
+                for (int j = j0; j < j1; ++j) {
+                    if (__ldcg(&w.res[j]) > 0) {
+                        const int hh = __ldcg(&w.lab[w.head[j]]);
+                        if (hh < hmin) { hmin = hh; best = j; }
+                    }
+                }
+                if (phase2 ? (bd == 1 && w.fx[i] > 0) : (bd == 2)) { hmin = 0; best = -2; }
+                if (best == -1) { h = hmax; w.lab[i] = h; break; }
+                if (h > hmin) {
+                    long long d;
+                    if (best == -2) {
+                        if (!phase2) {
+                            d = e;                       // v -> t is never saturated
+                            w.fx[i] += (int)d;
+                        } else {
+                            const int f = w.fx[i];
+                            d = e < f ? e : f;
+                            w.fx[i] = f - (int)d;
+                        }
+                    } else {
+                        const int r = __ldcg(&w.res[best]);
+                        d = e < r ? e : r;
+                        atomicSub(&w.res[best], (int)d);
+                        atomicAdd(&w.res[w.rev[best]], (int)d);
+                        atomicAddLL(&w.ex[w.head[best]], d);
+                        ++local;
+                    }
+                    atomicAddLL(&w.ex[i], -d);
+                    e -= d;
+                    if (e == 0) break;
+                } else {
+                    h = hmin + 1;
+                    if (h >= hmax) h = hmax;
+                    w.lab[i] = h;
+                    if (h >= hmax) break;
+                }
+            }
+            if (e > 0 && h < hmax) ++local;
+        }
+        __syncthreads();
+        const long long tot = block_sum_ll<TPB>(local);
+        if (threadIdx.x == 0 && tot) atomicAdd(act, (int)tot);
+    }
+
+    __device__ bool count_active(int hmax, int nu, bool any_excess, int *out) {
+        // counts vertices with excess (any_excess) or active vertices into *out
+        int local = 0;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const long long e = __ldcg(&w.ex[i]);
+            if (e > 0 && (any_excess || __ldcg(&w.lab[i]) < hmax)) ++local;
+            if (e < 0) fail(w.ctl, E_INTERNAL, 60);
+        }
+        __syncthreads();
+        const long long tot = block_sum_ll<TPB>(local);
+        if (threadIdx.x == 0 && tot) atomicAdd(out, (int)tot);
+        return grid_sync(w.ctl);
+    }
+
+    __device__ bool flow_phase(int phase2, int hmax, int nu) {
+        Ctl *ctl = w.ctl;
+        unsigned long long t0 = globaltimer();
+        if (!global_relabel(phase2, hmax, nu)) return false;
+        timer_mark(w, t0, T_GR);
+        long long pulses = 0;
+        int since_gr = 0;
+        for (;;) {
+            int *act = &ctl->act[pl % 3];
+            if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
+            pulse(phase2, hmax, nu, act);
+            if (!grid_sync(ctl)) return false;
+            const int a = __ldcg(act);
+            ++pl;
+            ++pulses;
+            ++since_gr;
+            if (pulses > w.pulse_cap) {
+                fail(ctl, E_ITER, 70);
+                return false;
+            }
+            timer_mark(w, t0, phase2 ? T_FLOW2 : T_FLOW1);
+            if (a == 0 || since_gr >= w.gr_interval) {
+                if (!global_relabel(phase2, hmax, nu)) return false;
+                since_gr = 0;
+                timer_mark(w, t0, T_GR);
+                if (a == 0) {
+                    // exact labels: done when no vertex with excess can reach the target
+                    int *cnt = &ctl->act[pl % 3];
+                    if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
+                    if (!count_active(hmax, nu, false, cnt)) return false;
+                    const int left = __ldcg(cnt);
+                    ++pl;
+                    if (left == 0) break;
+                }
+            }
+        }
+        if (G.tid == 0) ctl->pulses += pulses;
+        return true;
+    }
+
+    __device__ bool maxflow() {
+        Ctl *ctl = w.ctl;
+        const int nu = __ldcg(&ctl->nu), hmax = __ldcg(&ctl->hmax);
+        if (!flow_phase(0, hmax, nu)) return false;
+        if (!flow_phase(1, hmax, nu)) return false;
+        // every excess must have returned to s: the result is a flow
+        unsigned long long t0 = globaltimer();
+        int *cnt = &ctl->act[pl % 3];
+        if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
+        if (!count_active(hmax, nu, true, cnt)) return false;
+        if (__ldcg(cnt) != 0 && G.tid == 0) fail(ctl, E_INTERNAL, 80);
+        // flow value per pair: flow into t
+        for (long long i = G.tid; i < nu; i += G.size)
+            if (w.border[i] == 2) atomicAddLL(&w.pacc[w.sid[i] >> 1].flow, (long long)w.fx[i]);
+        ++pl;
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_FLOW2);
+        return true;
+    }
+
+    // ---------------------------------------------------------- residual sets --
+    __device__ bool reach() {
+        Ctl *ctl = w.ctl;
+        unsigned long long t0 = globaltimer();
+        const int nu = __ldcg(&ctl->nu);
+        {
+            int *cnt = &ctl->fcnt[(fl + 1) % 3];
+            int *q = ((fl + 1) & 1) ? w.fq1 : w.fq0;
+            for (long long b = G.warp * 32; b < nu; b += G.nwarps * 32) {
+                const long long i = b + (threadIdx.x & 31);
+                bool sb = false, tb = false;
+                if (i < nu) {
+                    const unsigned char bd = w.border[i];
+                    sb = bd == 1;
+                    tb = bd == 2;
+                    w.rflag[i] = (sb ? 1 : 0) | (tb ? 2 : 0);
+                }
+                const int slot = warp_append(cnt, sb || tb);
+                if (sb || tb) q[slot] = (int)i | (tb ? (int)0x80000000 : 0);
+            }
+            if (G.tid == 0) ctl->fcnt[(fl + 2) % 3] = 0;
+            if (!grid_sync(ctl)) return false;
+            ++fl;
+        }
+        for (int d = 1;; ++d) {
+            const int cur = __ldcg(&ctl->fcnt[fl % 3]);
+            if (cur == 0) break;
+            const int *q = (fl & 1) ? w.fq1 : w.fq0;
+            int *nq = ((fl + 1) & 1) ? w.fq1 : w.fq0;
+            int *ncnt = &ctl->fcnt[(fl + 1) % 3];
+            warp_rows(
+                0, cur, G,
+                [&](long long e, int &rs, int &deg, int &ctx) {
+                    const int ent = q[e];
+                    const int x = ent & 0x7fffffff;
+                    rs = w.off[x];
+                    deg = w.off[x + 1] - rs;
+                    ctx = ent;
+                },
+                [&](bool valid, int j, int ent) {
+                    bool got = false;
+                    int y = 0;
+                    const bool tside = ent < 0;
+                    if (valid) {
+                        y = w.head[j];
+                        if (!tside) {
+                            if (__ldcg(&w.res[j]) > 0 && !(__ldcg(&w.rflag[y]) & 1))
+                                got = !(atomicOr(&w.rflag[y], 1) & 1);
+                        } else {
+                            if (__ldcg(&w.res[w.rev[j]]) > 0 && !(__ldcg(&w.rflag[y]) & 2))
+                                got = !(atomicOr(&w.rflag[y], 2) & 2);
+                        }
+                    }
+                    const int slot = warp_append(ncnt, got);
+                    if (got) nq[slot] = y | (tside ? (int)0x80000000 : 0);
+                });
+            if (G.tid == 0) ctl->fcnt[(fl + 2) % 3] = 0;
+            if (!grid_sync(ctl)) return false;
+            ++fl;
+            if (d > nu + 2) {
+                fail(ctl, E_ITER, 90);
+                return false;
+            }
+        }
+        // s must not reach t (maximality); plain pairs take the smallest source set
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int f = __ldcg(&w.rflag[i]);
+            if (f == 3) fail(ctl, E_INTERNAL, 91);
+            w.side_out[i] = (f & 1) ? 0 : 1;
+        }
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_REACH);
+        return true;
+    }
+
+    // ------------------------------------------------------- SCC colouring --
+    // SCCs of the residual graph on X = vertices of MB pairs reached from
+    // neither s nor t.  Forward min-label propagation gives every vertex the
+    // smallest local id that reaches it; a root (label == own id) collects by
+    // backward BFS the vertices of its colour that reach it: its SCC.  The label
+    // of an SCC is therefore its smallest local id, i.e. its smallest global id.
+    __device__ bool scc() {
+        Ctl *ctl = w.ctl;
+        unsigned long long t0 = globaltimer();
+        const int nu = __ldcg(&ctl->nu);
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const bool mbp = w.pairs[w.sid[i] >> 1].mb != 0;
+            w.scc[i] = (mbp && __ldcg(&w.rflag[i]) == 0) ? -1 : -2;
+        }
+        if (!grid_sync(ctl)) return false;
+        int rounds = 0;
+        for (;;) {
+            // remaining unassigned?
+            int *rem = &ctl->chg[cl % 3];
+            if (G.tid == 0) ctl->chg[(cl + 1) % 3] = 0;
+            int local = 0;
+            for (long long i = G.tid; i < nu; i += G.size)
+                if (__ldcg(&w.scc[i]) == -1) { w.color[i] = (int)i; ++local; }
+            if (local) atomicAdd(rem, local);
+            if (!grid_sync(ctl)) return false;
+            ++cl;
+            if (__ldcg(rem) == 0) break;
+            ++rounds;
+            if (rounds > nu + 1) { fail(ctl, E_ITER, 100); return false; }
+            // forward propagation of the minimum label
+            for (int it = 0;; ++it) {
+                int *chg = &ctl->chg[cl % 3];
+                if (G.tid == 0) ctl->chg[(cl + 1) % 3] = 0;
+                int changed = 0;
+                for (long long i = G.tid; i < nu; i += G.size) {
+                    if (__ldcg(&w.scc[i]) != -1) continue;
+                    const int c = __ldcg(&w.color[i]);
+                    const int j1 = w.off[i + 1];
+                    for (int j = w.off[i]; j < j1; ++j) {
+                        if (__ldcg(&w.res[j]) <= 0) continue;
+                        const int y = w.head[j];
+                        if (__ldcg(&w.scc[y]) != -1) continue;
+                        if (__ldcg(&w.color[y]) > c && atomicMin(&w.color[y], c) > c) changed = 1;
+                    }
+                }
+                if (changed) atomicAdd(chg, 1);
+                if (!grid_sync(ctl)) return false;
+                ++cl;
+                if (__ldcg(chg) == 0) break;
+                if (it > nu + 1) { fail(ctl, E_ITER, 101); return false; }
+            }
+            // roots and backward BFS inside each colour class
+            {
+                int *cnt = &ctl->fcnt[(fl + 1) % 3];
+                int *q = ((fl + 1) & 1) ? w.fq1 : w.fq0;
+                for (long long b = G.warp * 32; b < nu; b += G.nwarps * 32) {
+                    const long long i = b + (threadIdx.x & 31);
+                    bool root = false;
+                    if (i < nu) root = __ldcg(&w.scc[i]) == -1 && __ldcg(&w.color[i]) == (int)i;
+                    const int slot = warp_append(cnt, root);
+                    if (root) { q[slot] = (int)i; w.scc[i] = (int)i; }
+                }
+                if (G.tid == 0) ctl->fcnt[(fl + 2) % 3] = 0;
+                if (!grid_sync(ctl)) return false;
+                ++fl;
+            }
+            for (int d = 1;; ++d) {
+                const int cur = __ldcg(&ctl->fcnt[fl % 3]);
+                if (cur == 0) break;
+                const int *q = (fl & 1) ? w.fq1 : w.fq0;
+                int *nq = ((fl + 1) & 1) ? w.fq1 : w.fq0;
+                int *ncnt = &ctl->fcnt[(fl + 1) % 3];
+                warp_rows(
+                    0, cur, G,
+                    [&](long long e, int &rs, int &deg, int &ctx) {
+                        const int x = q[e];
+                        rs = w.off[x];
+                        deg = w.off[x + 1] - rs;
+                        ctx = x;
+                    },
+                    [&](bool valid, int j, int x) {
+                        bool got = false;
+                        int y = 0;
+                        if (valid) {
+                            y = w.head[j];
+                            const int cx = __ldcg(&w.color[x]);
+                            if (__ldcg(&w.res[w.rev[j]]) > 0 && __ldcg(&w.scc[y]) == -1 &&
+                                __ldcg(&w.color[y]) == cx)
+                                got = atomicCAS(&w.scc[y], -1, cx) == -1;
+                        }
+                        const int slot = warp_append(ncnt, got);
+                        if (got) nq[slot] = y;
+                    });
+                if (G.tid == 0) ctl->fcnt[(fl + 2) % 3] = 0;
+                if (!grid_sync(ctl)) return false;
+                ++fl;
+                if (d > nu + 2) { fail(ctl, E_ITER, 102); return false; }
+            }
+        }
+        if (G.tid == 0) ctl->scc_rounds += rounds;
+        timer_mark(w, t0, T_SCC);
+        return true;
+    }
+
+    // --------------------------------------------------- DAG and sweeps (MB) --
+    __device__ bool sweeps() {
+        Ctl *ctl = w.ctl;
+        unsigned long long t0 = globaltimer();
+        const int nu = __ldcg(&ctl->nu);
+        const int P = w.npairs, R = w.reps;
+        // component ids for roots, in local-id order
+        long long ncomp = 0;
+        bool ok = grid_scan<TPB>(
+            w, nu, [&](long long i) -> int { return __ldcg(&w.scc[i]) == (int)i ? 1 : 0; },
+            [&](long long i, long long off) {
+                if (__ldcg(&w.scc[i]) == (int)i) {
+                    w.cid[i] = (int)off;
+                    w.cpair[off] = w.sid[i] >> 1;
+                    w.cmin[off] = w.gid[i];
+                    w.cw[off] = 0;
+                    w.indeg[off] = 0;
+                    w.ocur[off] = 0;
+                    w.outoff[off] = 0;
+                    w.sinkc[off] = 0;
+                }
+            },
+            &ncomp);
+        if (!ok) return false;
+        if (G.tid == 0) ctl->ncomp = (int)ncomp;
+        for (int p = G.tid; p < P; p += G.size) w.pcur[p] = 0;
+        if (!grid_sync(ctl)) return false;
+        // vertex -> component, component weights, d_0 terms
+        for (long long b0 = G.warp * 32; b0 < nu; b0 += G.nwarps * 32) {
+            const long long i = b0 + (threadIdx.x & 31);
+            bool valid = i < nu;
+            long long dd = 0;
+            int p = 0;
+            if (valid) {
+                const int sc = __ldcg(&w.scc[i]);
+                const int s = w.sid[i];
+                p = s >> 1;
+                const PairDev Pd = w.pairs[p];
+                valid = Pd.mb != 0;
+                if (valid) {
+                    const GraphDev &Gr = w.graphs[Pd.g];
+                    const long long c = __ldg(Gr.vwgt + w.gid[i]);
+                    const int f = __ldcg(&w.rflag[i]);
+                    // d_0: the source side is every corridor vertex that does not reach t
+                    if (!(s & 1) && (f & 2)) dd = -c;
+                    if ((s & 1) && !(f & 2)) dd = c;
+                    if (sc >= 0) {
+                        const int cc = __ldcg(&w.cid[sc]);
+                        w.vc[i] = cc;
+                        atomicAddLL(&w.cw[cc], c);
+                    }
+                }
+            }
+            warp_agg_add(valid ? &w.pacc[p].d0 : nullptr, dd, valid);
+        }
+        if (!grid_sync(ctl)) return false;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int sc = __ldcg(&w.scc[i]);
+            if (sc < 0) continue;
+            const int cc = __ldcg(&w.vc[i]);
+            if (sc == (int)i) atomicAdd(&w.pacc[w.sid[i] >> 1].ncomp, 1);
+            const int j1 = w.off[i + 1];
+            for (int j = w.off[i]; j < j1; ++j) {
+                if (__ldcg(&w.res[j]) <= 0) continue;
+                const int y = w.head[j];
+                if (__ldcg(&w.scc[y]) < 0) continue;
+                const int cy = __ldcg(&w.vc[y]);
+                if (cy == cc) continue;
+                atomicAdd(&w.outoff[cc], 1);
+                atomicAdd(&w.indeg[cy], 1);
+            }
+        }
+        if (!grid_sync(ctl)) return false;
+        // pair offsets of the component lists (few pairs: one thread)
+        if (G.tid == 0) {
+            int acc = 0;
+            for (int p = 0; p < P; ++p) {
+                w.pacc[p].cbase = acc;
+                acc += __ldcg(&w.pacc[p].ncomp);
+            }
+        }
+        // out-arc offsets
+        for (long long c = G.tid; c < ncomp; c += G.size) w.indeg_r[c] = __ldcg(&w.outoff[c]);
+        if (!grid_sync(ctl)) return false;
+        long long narcs = 0;
+        ok = grid_scan<TPB>(
+            w, ncomp, [&](long long c) -> int { return __ldcg(&w.indeg_r[c]); },
+            [&](long long c, long long off) { w.outoff[c] = (int)off; }, &narcs);
+        if (!ok) return false;
+        if (G.tid == 0) w.outoff[ncomp] = (int)narcs;
+        // per-pair lists of components
+        for (long long c = G.tid; c < ncomp; c += G.size) {
+            const int p = w.cpair[c];
+            const int slot = atomicAdd(&w.pcur[p], 1);
+            w.plist[__ldcg(&w.pacc[p].cbase) + slot] = (int)c;
+        }
+        if (!grid_sync(ctl)) return false;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int sc = __ldcg(&w.scc[i]);
+            if (sc < 0) continue;
+            const int cc = __ldcg(&w.vc[i]);
+            const int j1 = w.off[i + 1];
+            for (int j = w.off[i]; j < j1; ++j) {
+                if (__ldcg(&w.res[j]) <= 0) continue;
+                const int y = w.head[j];
+                if (__ldcg(&w.scc[y]) < 0) continue;
+                const int cy = __ldcg(&w.vc[y]);
+                if (cy == cc) continue;
+                w.outs[__ldcg(&w.outoff[cc]) + atomicAdd(&w.ocur[cc], 1)] = cy;
+            }
+        }
+        for (long long x = G.tid; x < (long long)R * ncomp; x += G.size)
+            w.indeg_r[x] = __ldcg(&w.indeg[x % ncomp]);
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_SCC);
+
+        // Kahn sweeps: one warp per (pair, r); ready components leave a binary
+        // heap keyed (key_r, minid); sweep position j moves the j-th component to
+        // the sink side and changes c(A') - c(B') by -2 c(component).
+        const int lane = threadIdx.x & 31;
+        for (long long task = G.warp; task < (long long)P * R; task += G.nwarps) {
+            const int p = (int)(task / R), r = (int)(task % R);
+            const PairDev Pd = w.pairs[p];
+            const int nc = __ldcg(&w.pacc[p].ncomp);
+            if (!Pd.mb) continue;
+            const int cb = __ldcg(&w.pacc[p].cbase);
+            const long long cA = __ldcg(&w.sides[2 * p].cw), cB = __ldcg(&w.sides[2 * p + 1].cw);
+            long long d = 2 * (cA + __ldcg(&w.pacc[p].d0)) - (cA + cB);
+            long long best = d < 0 ? -d : d;
+            int bestj = 0;
+            unsigned long long *hk = w.hkey + (long long)r * nu + cb;
+            int *hc = w.hcomp + (long long)r * nu + cb;
+            int *ord = w.order + (long long)r * nu + cb;
+            int *ind = w.indeg_r + (long long)r * ncomp;
+            int hn = 0;
+            auto key_of = [&](int c) -> unsigned long long {
+                return r == 0 ? 0ull : splitmix64(w.seed ^ (unsigned long long)r ^ (unsigned long long)w.cmin[c]);
+            };
+            auto less = [&](int i1, int i2) -> bool {
+                if (hk[i1] != hk[i2]) return hk[i1] < hk[i2];
+                return w.cmin[hc[i1]] < w.cmin[hc[i2]];
+            };
+            auto push = [&](int c) {
+                int i = hn++;
+                hk[i] = key_of(c);
+                hc[i] = c;
+                while (i > 0) {
+                    const int par = (i - 1) >> 1;
+                    if (!less(i, par)) break;
+                    const unsigned long long tk = hk[i]; hk[i] = hk[par]; hk[par] = tk;
+                    const int tc = hc[i]; hc[i] = hc[par]; hc[par] = tc;
+                    i = par;
+                }
+            };
+            auto pop = [&]() -> int {
+                const int top = hc[0];
+                --hn;
+                hk[0] = hk[hn];
+                hc[0] = hc[hn];
+                int i = 0;
+                for (;;) {
+                    const int l = 2 * i + 1, rr = l + 1;
+                    int m = i;
+                    if (l < hn && less(l, m)) m = l;
+                    if (rr < hn && less(rr, m)) m = rr;
+                    if (m == i) break;
+                    const unsigned long long tk = hk[i]; hk[i] = hk[m]; hk[m] = tk;
+                    const int tc = hc[i]; hc[i] = hc[m]; hc[m] = tc;
+                    i = m;
+                }
+                return top;
+            };
+            // initial ready set
+            for (int x0 = 0; x0 < nc; x0 += 32) {
+                const int x = x0 + lane;
+                int c = -1;
+                bool ready = false;
+                if (x < nc) {
+                    c = w.plist[cb + x];
+                    ready = __ldcg(&ind[c]) == 0;
+                }
+                unsigned int m = __ballot_sync(FULL, ready);
+                while (m) {
+                    const int l = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int cc = __shfl_sync(FULL, c, l);
+                    if (lane == 0) push(cc);
+                }
+            }
+            int done = 0;
+            for (;;) {
+                int c = -1;
+                if (lane == 0 && hn > 0) c = pop();
+                c = __shfl_sync(FULL, c, 0);
+                if (c < 0) break;
+                if (lane == 0) ord[done] = c;
+                ++done;
+                d -= 2 * __ldcg(&w.cw[c]);
+                const long long ad = d < 0 ? -d : d;
+                if (ad < best) { best = ad; bestj = done; }
+                const int o0 = __ldcg(&w.outoff[c]), o1 = __ldcg(&w.outoff[c + 1]);
+                for (int x0 = o0; x0 < o1; x0 += 32) {
+                    const int x = x0 + lane;
+                    int cy = -1;
+                    bool ready = false;
+                    if (x < o1) {
+                        cy = __ldcg(&w.outs[x]);
+                        ready = atomicSub(&ind[cy], 1) == 1;
+                    }
+                    unsigned int m = __ballot_sync(FULL, ready);
+                    while (m) {
+                        const int l = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int cc = __shfl_sync(FULL, cy, l);
+                        if (lane == 0) push(cc);
+                    }
+                }
+                hn = __shfl_sync(FULL, hn, 0);
+            }
+            if (lane == 0) {
+                if (done != nc) fail(ctl, E_INTERNAL, 110);
+                w.sw_absd[task] = best;
+                w.sw_j[task] = bestj;
+            }
+        }
+        if (!grid_sync(ctl)) return false;
+        // best (|d|, j, r) per pair, then mark the moved components
+        for (int p = G.tid; p < P; p += G.size) {
+            long long best = LLONG_MAX;
+            int bj = 0, br = 0;
+            if (w.pairs[p].mb) {
+                for (int r = 0; r < R; ++r) {
+                    const long long ad = __ldcg(&w.sw_absd[(long long)p * R + r]);
+                    const int j = __ldcg(&w.sw_j[(long long)p * R + r]);
+                    if (ad < best || (ad == best && j < bj)) { best = ad; bj = j; br = r; }
+                }
+            }
+            w.pacc[p].best_j = bj;
+            w.pacc[p].best_r = br;
+        }
+        if (!grid_sync(ctl)) return false;
+        for (int p = 0; p < P; ++p) {
+            if (!w.pairs[p].mb) continue;
+            const int bj = __ldcg(&w.pacc[p].best_j), br = __ldcg(&w.pacc[p].best_r);
+            const int cb = __ldcg(&w.pacc[p].cbase);
+            const int *ord = w.order + (long long)br * nu + cb;
+            for (long long x = G.tid; x < bj; x += G.size) w.sinkc[ord[x]] = 1;
+        }
+        if (!grid_sync(ctl)) return false;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int sc = __ldcg(&w.scc[i]);
+            if (sc >= 0) w.side_out[i] = __ldcg(&w.sinkc[__ldcg(&w.vc[i])]) ? 1 : 0;
+        }
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_SWEEP);
+        return true;
+    }
+
+    // ------------------------------------------------------------ evaluation --
+    __device__ bool eval() {
+        Ctl *ctl = w.ctl;
+        unsigned long long t0 = globaltimer();
+        const int nu = __ldcg(&ctl->nu);
+        for (long long b0 = G.warp * 32; b0 < nu; b0 += G.nwarps * 32) {
+            const long long i = b0 + (threadIdx.x & 31);
+            const bool valid = i < nu;
+            long long dwa = 0, dc = 0, cin = 0;
+            int p = 0;
+            if (valid) {
+                const int s = w.sid[i];
+                p = s >> 1;
+                const int s0 = s & 1, so = w.side_out[i];
+                if (so != s0) {
+                    const GraphDev &Gr = w.graphs[w.pairs[p].g];
+                    const long long c = __ldg(Gr.vwgt + w.gid[i]);
+                    dwa = so == 0 ? c : -c;
+                }
+                const int j1 = w.off[i + 1];
+                for (int j = w.off[i]; j < j1; ++j) {
+                    const int y = w.head[j];
+                    if (y <= i) continue;   // each corridor edge once
+                    const int oldc = s0 != (w.sid[y] & 1);
+                    const int newc = so != w.side_out[y];
+                    dc += (long long)w.cap[j] * (newc - oldc);
+                    cin += (long long)w.cap[j] * newc;
+                }
+            }
+            warp_agg_add(valid ? &w.pacc[p].dwA : nullptr, dwa, valid);
+            warp_agg_add(valid ? &w.pacc[p].dcut : nullptr, dc, valid);
+            warp_agg_add(valid ? &w.pacc[p].cutin : nullptr, cin, valid);
+        }
+        if (!grid_sync(ctl)) return false;
+        for (int p = G.tid; p < w.npairs; p += G.size) {
+            PairAcc *A = &w.pacc[p];
+            const PairDev Pd = w.pairs[p];
+            const long long cA = __ldcg(&w.sides[2 * p].cw), cB = __ldcg(&w.sides[2 * p + 1].cw);
+            const long long dwA = __ldcg(&A->dwA), dcut = __ldcg(&A->dcut);
+            const long long nA = cA + dwA, nB = cB - dwA;
+            const long long nmax = nA > nB ? nA : nB, omax = cA > cB ? cA : cB;
+            const int feasible = nmax <= w.graphs[Pd.g].Lmax;
+            if (__ldcg(&A->cutin) != __ldcg(&A->flow)) fail(ctl, E_INTERNAL, 120 + (p & 7));
+            A->feasible = feasible;
+            A->accept = feasible && (dcut < 0 || (dcut == 0 && nmax < omax));
+        }
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_EVAL);
+        return true;
+    }
+
+    // ---------------------------------------------------------------- commit --
+    __device__ bool commit() {
+        Ctl *ctl = w.ctl;
+        unsigned long long t0 = globaltimer();
+        const int nu = __ldcg(&ctl->nu);
+        const bool ok = __ldcg(&ctl->error) == 0;
+        if (ok) {
+            for (int p = G.tid; p < w.npairs; p += G.size) {
+                if (!__ldcg(&w.pacc[p].accept)) continue;
+                const PairDev Pd = w.pairs[p];
+                const long long dwA = __ldcg(&w.pacc[p].dwA);
+                w.graphs[Pd.g].blockw[Pd.a] += dwA;
+                w.graphs[Pd.g].blockw[Pd.b] -= dwA;
+            }
+            for (long long i = G.tid; i < nu; i += G.size) {
+                const int s = w.sid[i], p = s >> 1;
+                if (!__ldcg(&w.pacc[p].accept)) continue;
+                const PairDev Pd = w.pairs[p];
+                const int nb = w.side_out[i] ? Pd.b : Pd.a;
+                w.graphs[Pd.g].part[w.gid[i]] = nb;
+            }
+        }
+        for (long long e = G.tid; e < vtotal; e += G.size) {
+            const int v = w.vq_v[e], s = w.vq_s[e];
+            const GraphDev &Gr = w.graphs[w.pairs[s >> 1].g];
+            Gr.dist[v] = -1;
+            Gr.lid[v] = -1;
+        }
+        if (!grid_sync(ctl)) return false;
+        timer_mark(w, t0, T_COMMIT);
+        return true;
+    }
+};
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) step_kernel(Work w, uint32_t phases) {
+    extern __shared__ __align__(16) int smem[];
+    if (w.prev_err && __ldcg(w.prev_err)) return;
+    if (__ldcg(&w.ctl->error)) return;   // the scan of this round failed
+    StepKernel<TPB> K(w, smem);
+    if (phases & PH_BFS) {
+        if (!K.bfs()) return;
+    } else {
+        // later phases need the side decisions in shared memory
+        for (int s = threadIdx.x; s < w.nsides; s += TPB) {
+            K.s_state[s] = w.sides[s].state;
+            K.s_lstar[s] = w.sides[s].lstar;
+            K.s_T[s] = w.sides[s].T;
+        }
+        __syncthreads();
+    }
+    if (phases & PH_LID) {
+        if (!K.lids()) return;
+    }
+    if (phases & PH_BUILD) {
+        if (!K.build()) return;
+    }
+    if (phases & PH_FLOW) {
+        if (!K.maxflow()) return;
+    }
+    if (phases & PH_CUT) {
+        if (!K.reach()) return;
+        if (w.any_mb) {
+            if (!K.scc()) return;
+            if (!K.sweeps()) return;
+        }
+    }
+    if (phases & PH_EVAL) {
+        if (!K.eval()) return;
+    }
+    if (phases & PH_COMMIT) {
+        if (!K.commit()) return;
+    }
+    K.save_indices();
+}
+
+size_t step_smem_bytes(int nsides) {
+    return (size_t)nsides * (3 * sizeof(long long) + 4 * sizeof(int)) + 16;
+}
+
+template <int TPB>
+static cudaError_t launch_step_t(const Work &w, uint32_t phases, int grid, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TPB);
+    cfg.dynamicSmemBytes = step_smem_bytes(w.nsides);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = grid > 1 ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_kernel<TPB>, w, phases);
+}
+
+cudaError_t launch_step(const Work &w, uint32_t phases, int grid, int tpb, cudaStream_t st) {
+    switch (tpb) {
+        case 256: return launch_step_t<256>(w, phases, grid, st);
+        case 512: return launch_step_t<512>(w, phases, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t step_max_grid(int tpb, int nsides, int *max_blocks, int *sms) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t sm = step_smem_bytes(nsides);
+    if (tpb == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<256>, 256, sm);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<512>, 512, sm);
+    if (e != cudaSuccess) return e;
+    *max_blocks = per * nsm;
+    *sms = nsm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_scan(const Work &w, int g, int n, bool vec, cudaStream_t st) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int tpb = 256;
+    long long warps = ((long long)n + 31) / 32;
+    long long blocks = (warps + tpb / 32 - 1) / (tpb / 32);
+    long long cap = (long long)nsm * 8;
+    int grid = (int)(blocks < cap ? blocks : cap);
+    if (grid < 1) grid = 1;
+    const size_t sm = (size_t)w.npairs * sizeof(long long);
+    if (vec) scan_kernel<256, true><<<grid, tpb, sm, st>>>(w, g);
+    else scan_kernel<256, false><<<grid, tpb, sm, st>>>(w, g);
+    return cudaGetLastError();
+}
+
+}  // namespace fr

@@ -1,0 +1,352 @@
+"""Python binding of libflowref (include/flowref.h).
+
+Argument marshalling only: every step of the refinement runs in the CUDA kernels
+of lib/libflowref.so.  PyTorch provides device memory and streams.  There is no
+fallback: if the library or a CUDA device is missing, loading fails loudly.
+
+The C entry points are exposed under their own names (fr_create,
+fr_refine_pair, ...) on the loaded library `lib()`; `Context` wraps them for
+torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libflowref.so")
+
+FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_OOM = 0, 1, 2, 3
+FR_ERR_ITER_LIMIT, FR_ERR_TOO_LARGE, FR_ERR_ABORTED, FR_ERR_INTERNAL = 4, 5, 6, 7
+
+i8p = ctypes.POINTER(ctypes.c_int8)
+i32p = ctypes.POINTER(ctypes.c_int32)
+i64p = ctypes.POINTER(ctypes.c_int64)
+vp = ctypes.c_void_p
+
+
+class Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("xadj", vp), ("adjncy", vp), ("adjwgt", vp),
+                ("vwgt", vp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mb", ctypes.c_int32), ("mb_reps", ctypes.c_int32), ("adaptive", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
+                ("pad0", ctypes.c_int32)]
+
+
+class PairResult(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int64), ("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64),
+                ("wA_before", ctypes.c_int64), ("wB_before", ctypes.c_int64), ("wA_after", ctypes.c_int64),
+                ("wB_after", ctypes.c_int64), ("corridor_n", ctypes.c_int32), ("corridor_arcs", ctypes.c_int32),
+                ("accepted", ctypes.c_int32), ("iters", ctypes.c_int32), ("alpha_final", ctypes.c_double),
+                ("status", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("round", ctypes.c_int32),
+                ("pulses", ctypes.c_int64), ("relabels", ctypes.c_int64), ("bfs_levels", ctypes.c_int32),
+                ("scc_rounds", ctypes.c_int32), ("ncomp", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.c_int32), ("nrounds", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64),
+                ("corridor_arcs", ctypes.c_int64), ("device_ns", ctypes.c_int64), ("flow_ns", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
+                ("opt", Options)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("graph_id", ctypes.c_int32), ("k", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("part_host", i32p), ("tag", ctypes.c_uint64)]
+
+
+class Response(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("npairs", ctypes.c_int32),
+                ("nrounds", ctypes.c_int32), ("accepted", ctypes.c_int32), ("cut_before", ctypes.c_int64),
+                ("cut_after", ctypes.c_int64), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Every symbol declared in include/flowref.h (checked by the CPU test suite).
+SYMBOLS = {
+    "fr_default_options": (None, [ctypes.POINTER(Options)]),
+    "fr_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_size_t, vp]),
+    "fr_destroy": (ctypes.c_int, [vp]),
+    "fr_last_error": (ctypes.c_char_p, [vp]),
+    "fr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fr_workspace_bytes": (ctypes.c_size_t, [vp]),
+    "fr_build_corridor": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(vp)]),
+    "fr_corridor_info": (ctypes.c_int, [vp, i32p, i32p]),
+    "fr_corridor_export": (ctypes.c_int, [vp, vp, i32p, i32p, i32p, i32p, i8p, i32p, i8p, i32p]),
+    "fr_maxflow": (ctypes.c_int, [vp, vp, i64p]),
+    "fr_corridor_flow": (ctypes.c_int, [vp, vp, i64p, i64p]),
+    "fr_extract_cut": (ctypes.c_int, [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, vp,
+                                      ctypes.POINTER(PairResult)]),
+    "fr_corridor_sets": (ctypes.c_int, [vp, vp, i8p, i8p, i32p, i8p]),
+    "fr_corridor_free": (ctypes.c_int, [vp, vp]),
+    "fr_refine_pair": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
+                                      ctypes.POINTER(PairResult)]),
+    "fr_refine_batch": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
+                                       ctypes.POINTER(PairResult), ctypes.POINTER(BatchResult)]),
+    "fr_refine_batch_host": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
+                                            ctypes.c_int32, ctypes.POINTER(PairResult),
+                                            ctypes.POINTER(BatchResult)]),
+    "fr_rounds": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p,
+                                 i32p, i32p]),
+    "fr_autotune": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(Options), ctypes.c_int32, ctypes.POINTER(Options),
+                                   ctypes.POINTER(ctypes.c_double)]),
+    "fr_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]),
+    "fr_server_add_graph": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, i32p]),
+    "fr_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request)]),
+    "fr_server_next": (ctypes.c_int, [vp, ctypes.POINTER(Response), i32p, ctypes.c_int32, ctypes.c_int32]),
+    "fr_server_stats": (ctypes.c_int, [vp, i64p, i64p, i64p, i32p]),
+    "fr_server_destroy": (ctypes.c_int, [vp]),
+}
+
+_LIB = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA path has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SYMBOLS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        L.fr_last_launch_count.restype = ctypes.c_int64
+        L.fr_last_launch_count.argtypes = [vp]
+        _LIB = L
+    return _LIB
+
+
+class FlowRefError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status}: {msg}")
+        self.status = status
+
+
+def default_options(**kw):
+    o = Options()
+    lib().fr_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class DeviceGraph:
+    """CSR graph held in torch int32 CUDA tensors (the caller-owned device arrays of fr_graph)."""
+
+    def __init__(self, xadj, adjncy, adjwgt, vwgt, device="cuda"):
+        import torch
+        self.xadj = torch.as_tensor(_np32(xadj)).to(device)
+        self.adjncy = torch.as_tensor(_np32(adjncy)).to(device)
+        self.adjwgt = torch.as_tensor(_np32(adjwgt)).to(device)
+        self.vwgt = torch.as_tensor(_np32(vwgt)).to(device)
+        self.n = int(self.vwgt.numel())
+        self.nnz = int(self.adjncy.numel())
+
+    @classmethod
+    def from_workload(cls, w, device="cuda"):
+        return cls(w["xadj"], w["adjncy"], w["adjwgt"], w["vwgt"], device)
+
+    def c(self):
+        return Graph(self.n, self.nnz, self.xadj.data_ptr(), self.adjncy.data_ptr(), self.adjwgt.data_ptr(),
+                     self.vwgt.data_ptr())
+
+
+class Corridor:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    @property
+    def info(self):
+        nc, m = ctypes.c_int32(), ctypes.c_int32()
+        lib().fr_corridor_info(self.h, ctypes.byref(nc), ctypes.byref(m))
+        return nc.value, m.value
+
+    def export(self, with_dist=True):
+        nc, m = self.info
+        out = dict(gid=np.empty(nc, np.int32), off=np.empty(nc + 1, np.int32), head=np.empty(m, np.int32),
+                   cap=np.empty(m, np.int32), border=np.empty(nc, np.int8), infcap=np.empty(nc, np.int32),
+                   side0=np.empty(nc, np.int8), dist=np.empty(nc, np.int32))
+        P = lambda a, t=i32p: a.ctypes.data_as(t)
+        st = lib().fr_corridor_export(self.ctx.h, self.h, P(out["gid"]), P(out["off"]), P(out["head"]),
+                                      P(out["cap"]), P(out["border"], i8p), P(out["infcap"]), P(out["side0"], i8p),
+                                      P(out["dist"]) if with_dist else None)
+        self.ctx._check(st)
+        if not with_dist:
+            out.pop("dist")
+        return out
+
+    def maxflow(self):
+        f = ctypes.c_int64()
+        self.ctx._check(lib().fr_maxflow(self.ctx.h, self.h, ctypes.byref(f)))
+        return f.value
+
+    def flow(self):
+        nc, m = self.info
+        af, sf = np.empty(m, np.int64), np.empty(nc, np.int64)
+        self.ctx._check(lib().fr_corridor_flow(self.ctx.h, self.h, af.ctypes.data_as(i64p),
+                                               sf.ctypes.data_as(i64p)))
+        return af, sf
+
+    def extract_cut(self, part, mb=0, reps=1, seed=0):
+        res = PairResult()
+        st = lib().fr_extract_cut(self.ctx.h, self.h, mb, reps, seed & 0xFFFFFFFFFFFFFFFF, _ptr(part),
+                                  ctypes.byref(res))
+        self.ctx._check(st)
+        return res
+
+    def sets(self):
+        nc, _ = self.info
+        ins, tot, comp, side = (np.empty(nc, np.int8), np.empty(nc, np.int8), np.empty(nc, np.int32),
+                                np.empty(nc, np.int8))
+        self.ctx._check(lib().fr_corridor_sets(self.ctx.h, self.h, ins.ctypes.data_as(i8p), tot.ctypes.data_as(i8p),
+                                               comp.ctypes.data_as(i32p), side.ctypes.data_as(i8p)))
+        return ins.astype(bool), tot.astype(bool), comp, side
+
+    def free(self):
+        if self.h:
+            lib().fr_corridor_free(self.ctx.h, self.h)
+            self.h = None
+
+
+class Context:
+    """One fr_ctx on a CUDA device (and a stream)."""
+
+    def __init__(self, device=0, arena_bytes=0, stream=None):
+        h = ctypes.c_void_p()
+        st = lib().fr_create(ctypes.byref(h), device, arena_bytes, stream)
+        if st != FR_OK:
+            raise FlowRefError(st, "fr_create failed (no CUDA device?)")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().fr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self):
+        m = lib().fr_last_error(self.h)
+        return m.decode() if m else ""
+
+    def _check(self, st):
+        if st != FR_OK:
+            raise FlowRefError(st, self.last_error())
+
+    @property
+    def workspace_bytes(self):
+        return lib().fr_workspace_bytes(self.h)
+
+    @property
+    def last_launches(self):
+        return lib().fr_last_launch_count(self.h)
+
+    def build_corridor(self, g: DeviceGraph, part, k, a, b, eps, alpha):
+        h = ctypes.c_void_p()
+        gc = g.c()
+        st = lib().fr_build_corridor(self.h, ctypes.byref(gc), _ptr(part), k, a, b, eps, alpha, ctypes.byref(h))
+        self._check(st)
+        return Corridor(self, h)
+
+    def refine_pair(self, g: DeviceGraph, part, k, a, b, eps, alpha, opts=None, check=True):
+        res = PairResult()
+        gc = g.c()
+        o = opts if opts is not None else default_options()
+        st = lib().fr_refine_pair(self.h, ctypes.byref(gc), _ptr(part), k, a, b, eps, alpha, ctypes.byref(o),
+                                  ctypes.byref(res))
+        if check:
+            self._check(st)
+        return st, res
+
+    def refine_batch(self, g: DeviceGraph, part, k, eps, alpha, opts=None, check=True):
+        cap = k * (k - 1) // 2
+        res = (PairResult * max(cap, 1))()
+        summ = BatchResult()
+        gc = g.c()
+        o = opts if opts is not None else default_options()
+        st = lib().fr_refine_batch(self.h, ctypes.byref(gc), _ptr(part), k, eps, alpha, ctypes.byref(o), cap, res,
+                                   ctypes.byref(summ))
+        if check:
+            self._check(st)
+        return st, [res[i].as_dict() for i in range(summ.npairs)], summ.as_dict()
+
+    def refine_batch_host(self, xadj, adjncy, adjwgt, vwgt, part, k, eps, alpha, opts=None, cap=0):
+        """Host-buffer form: arrays are numpy or (pinned) CPU tensors; part is updated in place."""
+        def p(a):
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        res = (PairResult * max(cap, 1))()
+        summ = BatchResult()
+        o = opts if opts is not None else default_options()
+        n = len(vwgt)
+        nnz = len(adjncy)
+        st = lib().fr_refine_batch_host(self.h, n, nnz, p(xadj), p(adjncy), p(adjwgt), p(vwgt), p(part), k, eps,
+                                        alpha, ctypes.byref(o), cap, res, ctypes.byref(summ))
+        self._check(st)
+        return summ.as_dict()
+
+    def rounds(self, g: DeviceGraph, part, k):
+        cap = k * (k - 1) // 2
+        pa, pb, pr = np.empty(cap, np.int32), np.empty(cap, np.int32), np.empty(cap, np.int32)
+        npairs, nrounds = ctypes.c_int32(), ctypes.c_int32()
+        gc = g.c()
+        st = lib().fr_rounds(self.h, ctypes.byref(gc), _ptr(part), k, cap, pa.ctypes.data_as(i32p),
+                             pb.ctypes.data_as(i32p), pr.ctypes.data_as(i32p),
+                             ctypes.byref(npairs), ctypes.byref(nrounds))
+        self._check(st)
+        return pa[:npairs.value], pb[:npairs.value], pr[:npairs.value], nrounds.value
+
+    def autotune(self, g: DeviceGraph, part, k, eps, alpha, opts=None, trials=2):
+        best = Options()
+        ms = ctypes.c_double()
+        gc = g.c()
+        o = opts if opts is not None else default_options()
+        st = lib().fr_autotune(self.h, ctypes.byref(gc), _ptr(part), k, eps, alpha, ctypes.byref(o), trials,
+                               ctypes.byref(best), ctypes.byref(ms))
+        self._check(st)
+        return best, ms.value
