@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of batched flow refinement (Sanders & Schulz, Section 4.1 / 4.1.1) on GB300.
+
+One step = one sweep of fr_refine_batch over the 3D random geometric graph
+(n = 4,194,304, mean degree ~12, omega in [1,10], c in [1,4], k = 64, eps = 0.01,
+alpha = 4, most balanced cuts): boundary scan, quotient-graph rounds, and per
+round one persistent launch doing corridor BFS, network build, max flow,
+residual SCCs / sweeps and the commit.  The partition is restored before every
+step, so each step refines the same input.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the method has no
+cross-GPU exchange in this build); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "block-pair refinements/sec"
+UNIT = "pairs/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- workloads --
+
+def make_workload(name):
+    from paper_1012_0006_gb300 import inputs as I
+    if name == "rgg3d":
+        w = I.config(4)
+        desc = "rgg3d n=4194304 deg~12 omega[1,10] c[1,4] k=64 eps=0.01 alpha=4 MB R=1"
+    elif name == "grid3d":
+        w = I.config(3)
+        desc = "grid3d 128^3 k=16 eps=0.03 alpha=2 MB R=1"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w, desc
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed ----
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def reduce_max(pg, x, device=None):
+    """Max over ranks of a float (gloo or nccl)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ CPU baseline ----
+
+def oracle_sample(w, budget_s=12.0):
+    """The oracle as it stands, on the first pairs of one sweep in round order (bounded sample)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    st, _, done = O.refine_batch_sample(w, 4)
+    t_small = time.perf_counter() - t0
+    assert st == 0
+    per = max(t_small / max(done, 1), 1e-4)
+    pa, pb, pr, nr = O.rounds(w)
+    P = int(min(len(pa), max(4, budget_s / per)))
+    t0 = time.perf_counter()
+    st, _, done = O.refine_batch_sample(w, P)
+    el = time.perf_counter() - t0
+    return dict(value=done / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"first {done} of {len(pa)} pairs of one sweep in round order, one validation pass "
+                       f"and rounds included, single thread, {el:.1f} s"), done, el
+
+
+# ---------------------------------------------------------------- roofline ----
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("round_kernel.cu", "fr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1012_0006_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        e = rec.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e.get("dram_bytes_per_launch_full"), e
+    except Exception:
+        pass
+    return None, None
+
+
+def bytes_model(P):
+    """Algorithmic bytes per kernel type for one sweep (element bytes the method must touch)."""
+    n, nnz = P["n"], P["nnz"]
+    scan = (8 * n + 8 * nnz + 4) * P["nrounds"]            # xadj, part[v], adjncy, part[u]
+    vis, arcs = P["bfs_visited"], P["bfs_arcs"]
+    nc, m = P["corridor_n"], P["corridor_arcs"]
+    bfs = 16 * vis + 12 * arcs
+    select = 4 * 8 * vis
+    lid = (2 * 4 * n) * P["nrounds"] + 12 * nc
+    build = 12 * nc + 28 * m
+    flow = 12 * P["pr_arcs"] + 24 * P["pushes"] + 12 * P["gr_arcs"]
+    cut = 2 * (12 * m + 8 * nc)
+    step = bfs + select + lid + build + flow + cut
+    return dict(scan=scan, step=step, bfs=bfs, relabel=12 * P["gr_arcs"], flow=flow, build=build)
+
+
+# ------------------------------------------------------------------ ours ----
+
+def run_ours(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+    from paper_1012_0006_gb300 import flowref as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    w, desc = make_workload(args.workload)
+    log(f"[rank {rank}] workload {w['name']} generated in {time.time() - t0:.1f}s")
+    g = F.DeviceGraph.from_workload(w, device=dev)
+    part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
+    part = part0.clone()
+    ctx = F.Context(local)
+    opts = F.default_options(mb=int(w["mb"]))
+    k, eps, alpha = w["k"], w["eps"], w["alpha"]
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.time()
+        best, ms = ctx.autotune(g, part0, k, eps, alpha, opts, trials=1)
+        tuned = dict(block_threads=best.block_threads, grid_blocks=best.grid_blocks, gr_interval=best.gr_interval,
+                     inner_ops=best.inner_ops, ms=round(ms, 3))
+        log(f"[rank {rank}] autotune {tuned} in {time.time() - t0:.1f}s")
+
+    def step():
+        part.copy_(part0)
+        st, _, summ = ctx.refine_batch(g, part, k, eps, alpha, opts, results=False)
+        return summ
+
+    for _ in range(args.warmup):
+        summ = step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    pairs = arcs = flow_ns = 0
+    launches = 0
+    for _ in range(args.steps):
+        summ = step()
+        pairs += summ["npairs"]
+        arcs += summ["corridor_arcs"]
+        flow_ns += summ["flow_ns"]
+        launches += ctx.last_launches
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = reduce_max(pg, t_ms, dev)
+    pairs_all = reduce_sum(pg, pairs, dev)
+    value = pairs_all / (t_max / 1e3)
+    arcs_rate = reduce_sum(pg, arcs / max(flow_ns * 1e-9, 1e-12), dev)
+
+    # per-kernel timing with CUDA events around each launch (same workload, after the timed region)
+    ctx.set_profiling(True)
+    profs = []
+    for _ in range(3):
+        step()
+        profs.append(ctx.profile())
+    ctx.set_profiling(False)
+    P = profs[-1]
+    nr = P["nrounds"]
+    scan_ms = statistics.median(p["scan_ms"] for p in profs)
+    step_ms = statistics.median(p["step_ms"] for p in profs)
+    bm = bytes_model(P)
+    peak, peak_kind = measured_peak_gbs()
+    dominant = "step_kernel" if step_ms >= scan_ms else "scan_kernel"
+    if dominant == "step_kernel":
+        per_launch_bytes, per_launch_ms = bm["step"] / nr, step_ms / nr
+    else:
+        per_launch_bytes, per_launch_ms = bm["scan"] / nr, scan_ms / nr
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic, _ = recorded_traffic(dominant)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dominant,
+                "peak_kind": peak_kind, "bytes_per_launch": int(per_launch_bytes),
+                "launch_ms": round(per_launch_ms, 4)}
+    ph = P["phase_ms"]
+    kernels = {
+        "scan_kernel": {"ms_per_launch": round(scan_ms / nr, 4), "bytes_per_launch": int(bm["scan"] / nr),
+                        "gbs": round(bm["scan"] / nr / (scan_ms / nr * 1e-3) / 1e9, 1),
+                        "frac": round(bm["scan"] / nr / (scan_ms / nr * 1e-3) / 1e9 / peak, 4)},
+        "step_kernel": {"ms_per_launch": round(step_ms / nr, 4), "bytes_per_launch": int(bm["step"] / nr),
+                        "gbs": round(bm["step"] / nr / (step_ms / nr * 1e-3) / 1e9, 1),
+                        "frac": round(bm["step"] / nr / (step_ms / nr * 1e-3) / 1e9 / peak, 4)},
+        "phases_ms": {kk: round(v, 3) for kk, v in ph.items()},
+        "bfs_gbs": round(bm["bfs"] / max(ph["bfs"] * 1e-3, 1e-12) / 1e9, 1),
+        "relabel_gbs": round(bm["relabel"] / max(ph["relabel"] * 1e-3, 1e-12) / 1e9, 1),
+        "counters": {kk: P[kk] for kk in ("bfs_visited", "bfs_arcs", "corridor_n", "corridor_arcs", "pulses",
+                                           "relabels", "gr_arcs", "pr_arcs", "pushes", "scc_rounds")},
+    }
+
+    # end to end through the host-buffer entry point: H2D of graph and part, D2H of part
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.int32)).pin_memory()
+        hx, ha, hw, hv = pin(w["xadj"]), pin(w["adjncy"]), pin(w["adjwgt"]), pin(w["vwgt"])
+        hp0 = np.array(w["part"], np.int32)
+        hp = pin(hp0)
+        ctx.refine_batch_host(hx, ha, hw, hv, hp, k, eps, alpha, opts)   # warm (allocations)
+        n, nnz = w["n"], w["nnz"]
+        tot = 0.0
+        ke = max(3, args.steps // 2)
+        for _ in range(ke):
+            hp.numpy()[:] = hp0
+            t0 = time.perf_counter()
+            ctx.refine_batch_host(hx, ha, hw, hv, hp, k, eps, alpha, opts)
+            tot += time.perf_counter() - t0
+        tot = reduce_max(pg, tot, dev)
+        e2e = {"value": round(pairs_all / args.steps * ke / tot, 2), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * ((n + 1) + 2 * nnz + 2 * n), "d2h_bytes_per_step": 4 * n,
+               "ms_per_step": round(tot / ke * 1e3, 3)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, _, _ = oracle_sample(w, budget_s=args.cpu_budget)
+        cpu["value"] = round(cpu["value"], 3)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "n": w["n"], "nnz": w["nnz"], "k": k,
+                       "pairs_per_step": int(pairs / args.steps), "rounds_per_step": nr,
+                       "l2": "inputs larger than L2 (graph + part ~0.45 GB per replica)",
+                       "parallelism": "replicas" if world > 1 else "single", "launch_shape": tuned},
+            "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
+            "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+# --------------------------------------------------------- reference arm ----
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    import oracle as O
+    w, desc = make_workload(args.workload)
+    per_step = []
+    P = args.ref_pairs
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        st, _, done = O.refine_batch_sample(w, P)
+        el = time.perf_counter() - t0
+        assert st == 0
+        if i >= args.warmup:
+            per_step.append((done, el))
+    pairs = sum(d for d, _ in per_step)
+    tot = sum(e for _, e in per_step)
+    value = pairs / tot
+    sample = (f"first {P} pairs of one sweep in round order per step (validation and rounds included), "
+              f"single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": desc, "n": w["n"], "nnz": w["nnz"], "k": w["k"]},
+           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rgg3d", choices=["rgg3d", "grid3d"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-pairs", type=int, default=6)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("warm-up raised to 3 (timing rule)")
+        args.warmup = 3
+    world, rank, local, pg = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,34 @@ fr_status fr_refine_batch_host(fr_ctx *ctx, int32_t n, int32_t nnz, const int32_
 fr_status fr_rounds(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, int32_t cap, int32_t *pair_a,
                     int32_t *pair_b, int32_t *pair_round, int32_t *npairs, int32_t *nrounds);
 
+/* ---- measurement --------------------------------------------------------------- */
+
+/* Per-kernel timing and the work counters behind the bytes model of a sweep. */
+typedef struct fr_profile_info {
+    int32_t nrounds;          /* rounds of the last fr_refine_batch */
+    int32_t launches;         /* kernels launched by it */
+    double scan_ms;           /* boundary-scan kernels, CUDA events around each launch (profiling on) */
+    double step_ms;           /* persistent step kernels, CUDA events around each launch (profiling on) */
+    double phase_ms[12];      /* in-kernel timers: bfs, select, lid, build, flow, relabel, return,
+                                 reach, scc, sweep, eval, commit (summed over rounds) */
+    int64_t n, nnz;           /* graph scanned by each boundary-scan launch */
+    int64_t bfs_visited;      /* BFS entries */
+    int64_t bfs_arcs;         /* arcs scanned by the corridor BFS */
+    int64_t corridor_n;       /* corridor vertices, all pairs */
+    int64_t corridor_arcs;    /* corridor arcs, all pairs */
+    int64_t pulses;           /* push-relabel pulses, summed over rounds */
+    int64_t relabels;         /* global relabels */
+    int64_t gr_arcs;          /* arcs scanned by global relabels */
+    int64_t pr_arcs;          /* arcs scanned by push-relabel pulses */
+    int64_t pushes;           /* pushes */
+    int64_t scc_rounds;       /* SCC colouring rounds */
+} fr_profile_info;
+
+/* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with
+ * CUDA events around each one, for fr_profile_last; on = 0: graph replay. */
+fr_status fr_set_profiling(fr_ctx *ctx, int32_t on);
+fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info);
+
 /* ---- launch-shape autotuner -------------------------------------------------- */
 
 /* Times fr_refine_batch on a copy of part for a set of launch shapes

@@ -82,6 +82,10 @@ def lib():
         L.fro_refine_batch.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
                                        ctypes.POINTER(PairResult), i32p, i32p]
+        L.fro_refine_batch_sample.restype = ctypes.c_int32
+        L.fro_refine_batch_sample.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
+                                              ctypes.c_int32, i32p]
         L.fro_splitmix64.restype = ctypes.c_uint64
         L.fro_splitmix64.argtypes = [ctypes.c_uint64]
         _LIB = L
@@ -236,3 +240,15 @@ def refine_batch(w, part=None, eps=None, alpha=None, opts=None):
                                 k, eps, alpha, ctypes.byref(opts), cap, res, ctypes.byref(npairs),
                                 ctypes.byref(nrounds))
     return st, part, [res[i].as_dict() for i in range(npairs.value)], nrounds.value
+
+
+def refine_batch_sample(w, max_pairs, part=None, opts=None):
+    """The oracle's sweep stopped after max_pairs pairs; returns (status, part, pairs done)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    if opts is None:
+        opts = options(mb=w.get("mb", 0))
+    done = ctypes.c_int32()
+    st = lib().fro_refine_batch_sample(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]),
+                                       _p(part), w["k"], w["eps"], w["alpha"], ctypes.byref(opts), max_pairs,
+                                       ctypes.byref(done))
+    return st, part, done.value

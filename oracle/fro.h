@@ -131,6 +131,11 @@ int32_t fro_refine_batch(int32_t n, const int32_t *xadj, const int32_t *adjncy, 
                          const fro_options *opt, int32_t cap, fro_pair_result *res, int32_t *npairs,
                          int32_t *nrounds);
 
+/* The same sweep stopped after max_pairs pairs (a bounded sample for timing; all if < 0). */
+int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                                const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                                const fro_options *opt, int32_t max_pairs, int32_t *done);
+
 /* Pair cut omega(E_ab) of the current partition. */
 int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                      const int32_t *part, int32_t a, int32_t b);

@@ -839,3 +839,28 @@ int32_t fro_refine_batch(int32_t n, const int32_t *xadj, const int32_t *adjncy, 
     if (nrounds) *nrounds = nr;
     return FRO_OK;
 }
+
+int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                                const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                                const fro_options *opt, int32_t max_pairs, int32_t *done) {
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0))) st = FRO_ERR_INVALID_ARG;
+    if (st != FRO_OK) return st;
+    int64_t W = fro_total_weight(n, vwgt);
+    int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
+    int32_t maxp = k * (k - 1) / 2;
+    int32_t *pa = XALLOC(int32_t, maxp), *pb = XALLOC(int32_t, maxp), *pr = XALLOC(int32_t, maxp);
+    int32_t nr = 0;
+    int32_t np = fro_rounds(n, xadj, adjncy, part, k, maxp, pa, pb, pr, &nr);
+    int32_t cnt = 0;
+    for (int32_t r = 0; r < nr; ++r)
+        for (int32_t i = 0; i < np; ++i) {
+            if (pr[i] != r || (max_pairs >= 0 && cnt >= max_pairs)) continue;
+            fro_pair_result tmp;
+            refine_pair_core(n, xadj, adjncy, adjwgt, vwgt, part, k, pa[i], pb[i], eps, alpha, opt, W, Lmax, &tmp);
+            ++cnt;
+        }
+    free(pa); free(pb); free(pr);
+    if (done) *done = cnt;
+    return FRO_OK;
+}

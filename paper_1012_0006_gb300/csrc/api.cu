@@ -354,6 +354,7 @@ extern "C" fr_status fr_destroy(fr_ctx *ctx) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     cudaEventDestroy(ctx->ev0);
     cudaEventDestroy(ctx->ev1);
+    for (auto e : ctx->pev) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return FR_OK;

@@ -342,6 +342,33 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
     return FR_OK;
 }
 
+// Same launches as enqueue_sweep, each bracketed by CUDA events (profiling mode).
+static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const BatchPlan &pl, const fr_options *opt) {
+    const int np = pl.np, nr = pl.nr;
+    while ((int)ctx->pev.size() < 4 * nr) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->pev.push_back(e);
+    }
+    CK(launch_fill_pairs(ctx->pairs, ctx->pair_a, ctx->pair_b, np, 0, opt->mb ? 1 : 0, pl.Ubase, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl) * nr, ctx->stream));
+    CK(cudaMemsetAsync(ctx->sides, 0, sizeof(SideDev) * 2 * np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc) * np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * (size_t)np * kHistBins, ctx->stream));
+    const bool vec = (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0;
+    for (int r = 0; r < nr; ++r) {
+        const int P = pl.off[r + 1] - pl.off[r];
+        Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
+        CK(cudaEventRecord(ctx->pev[4 * r], ctx->stream));
+        CK(launch_scan(w, 0, g->n, vec, ctx->stream));
+        CK(cudaEventRecord(ctx->pev[4 * r + 1], ctx->stream));
+        CK(cudaEventRecord(ctx->pev[4 * r + 2], ctx->stream));
+        CK(launch_step(w, PH_ALL, pl.grid[r], pl.tpb, ctx->stream));
+        CK(cudaEventRecord(ctx->pev[4 * r + 3], ctx->stream));
+    }
+    return FR_OK;
+}
+
 static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const BatchPlan &pl,
                            const fr_options *opt, float *ms) {
     // per-round graph descriptors (sob of round r) go up before the launches
@@ -367,6 +394,27 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
+    if (ctx->profiling) {
+        CK(cudaEventRecord(ctx->ev0, ctx->stream));
+        fr_status st = enqueue_sweep_profiled(ctx, g, pl, opt);
+        if (st != FR_OK) return st;
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
+        double sc = 0, stp = 0;
+        for (int r = 0; r < pl.nr; ++r) {
+            float a = 0, b = 0;
+            CK(cudaEventElapsedTime(&a, ctx->pev[4 * r], ctx->pev[4 * r + 1]));
+            CK(cudaEventElapsedTime(&b, ctx->pev[4 * r + 2], ctx->pev[4 * r + 3]));
+            sc += a;
+            stp += b;
+        }
+        ctx->prof.scan_ms = sc;
+        ctx->prof.step_ms = stp;
+        ctx->last_launches = 3 + 2LL * pl.nr;
+        return FR_OK;
+    }
+    ctx->prof.scan_ms = ctx->prof.step_ms = 0;
     if (ctx->use_graphs) {
         for (auto &e : ctx->gcache)
             if (e.key == key) { exec = e.exec; break; }
@@ -408,7 +456,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
-    ctx->last_launches = 1 + 2LL * pl.nr;
+    ctx->last_launches = 3 + 2LL * pl.nr;   // prep + colour + fill + (scan + step) per round
     return FR_OK;
 }
 
@@ -488,6 +536,30 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
     }
     long long flow_ns = 0;
     for (int r = 0; r < pl.nr; ++r) flow_ns += C[r].timers[T_FLOW1] + C[r].timers[T_GR] + C[r].timers[T_FLOW2];
+    {
+        fr_profile_info &P = ctx->prof;
+        const double sc = P.scan_ms, stp = P.step_ms;
+        memset(&P, 0, sizeof(P));
+        P.scan_ms = sc;
+        P.step_ms = stp;
+        P.nrounds = pl.nr;
+        P.launches = (int32_t)ctx->last_launches;
+        P.n = g->n;
+        P.nnz = g->nnz;
+        for (int r = 0; r < pl.nr; ++r) {
+            for (int t = 0; t < T_COUNT && t < 12; ++t) P.phase_ms[t] += C[r].timers[t] * 1e-6;
+            P.bfs_visited += C[r].vq_total;
+            P.bfs_arcs += C[r].arcs_scanned;
+            P.corridor_n += C[r].nu;
+            P.corridor_arcs += C[r].mu;
+            P.pulses += C[r].pulses;
+            P.relabels += C[r].relabels;
+            P.gr_arcs += C[r].gr_arcs;
+            P.pr_arcs += C[r].pr_arcs;
+            P.pushes += C[r].pushes;
+            P.scc_rounds += C[r].scc_rounds;
+        }
+    }
     for (int r = 0; r < pl.nr; ++r)
         for (int i = pl.off[r]; i < pl.off[r + 1]; ++i) {
             const PairAcc &a = A[i];
@@ -667,3 +739,15 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
 }
 
 extern "C" int64_t fr_last_launch_count(const fr_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+extern "C" fr_status fr_set_profiling(fr_ctx *ctx, int32_t on) {
+    if (!ctx) return FR_ERR_INVALID_ARG;
+    ctx->profiling = on != 0;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info) {
+    if (!ctx || !info) return FR_ERR_INVALID_ARG;
+    *info = ctx->prof;
+    return FR_OK;
+}

@@ -76,6 +76,10 @@ struct fr_ctx {
     std::vector<GraphCacheEntry> gcache;
     bool use_graphs = true;
     long long last_launches = 0;   // kernels launched by the last call
+    // profiling: direct launches with an event pair around each kernel
+    bool profiling = false;
+    std::vector<cudaEvent_t> pev;
+    fr_profile_info prof = {};
 };
 
 struct fr_corridor {

@@ -23,6 +23,10 @@ constexpr int kMaxSides = 2048;        // pairs per step <= 1024
 constexpr int kHistBins = 256;
 constexpr int kMaxGraphs = 64;         // graphs per step (serving)
 constexpr unsigned int kSpinLimit = 1u << 22;   // barrier spins (~1 s with backoff)
+constexpr unsigned int kBarrierCap = 1u << 21;  // grid barriers per launch before E_ITER (a few seconds)
+
+// Grid barriers passed by this CTA in the current launch (reset by the kernel prologue).
+__shared__ unsigned int g_nsync;
 
 enum PhaseBits : uint32_t {
     PH_BFS = 1u << 0,
@@ -101,6 +105,8 @@ struct Ctl {
     long long timers[T_COUNT];
     long long arcs_scanned;   // BFS arcs scanned (for the bytes model)
     long long gr_arcs;        // arcs scanned by global relabels
+    long long pr_arcs;        // arcs scanned by push-relabel pulses
+    long long pushes;         // pushes
 };
 
 // Everything a kernel needs, passed by value.
@@ -188,6 +194,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        if (++g_nsync > kBarrierCap) fail(ctl, E_ITER, 901);
         if (gridDim.x > 1) {
             unsigned int gen = ld_acquire(&ctl->bar_gen);
             __threadfence();

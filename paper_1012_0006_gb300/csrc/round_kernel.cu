@@ -663,6 +663,7 @@ struct StepKernel {
     // may be active afterwards.
     __device__ void pulse(int phase2, int hmax, int nu, int *act) {
         int local = 0;
+        long long scanned = 0, pushes = 0;
         for (long long i = G.tid; i < nu; i += G.size) {
             long long e = __ldcg(&w.ex[i]);
             if (e <= 0) continue;
@@ -672,6 +673,7 @@ struct StepKernel {
             const unsigned char bd = w.border[i];
             for (int it = 0; it < w.inner; ++it) {
                 int hmin = INT_MAX, best = -1;
+                scanned += j1 - j0;
                 for (int j = j0; j < j1; ++j) {
                     if (__ldcg(&w.res[j]) > 0) {
                         const int hh = __ldcg(&w.lab[w.head[j]]);
@@ -682,6 +684,7 @@ struct StepKernel {
                 if (best == -1) { h = hmax; w.lab[i] = h; break; }
                 if (h > hmin) {
                     long long d;
+                    ++pushes;
                     if (best == -2) {
                         if (!phase2) {
                             d = e;                       // v -> t is never saturated
@@ -713,7 +716,13 @@ struct StepKernel {
         }
         __syncthreads();
         const long long tot = block_sum_ll<TPB>(local);
-        if (threadIdx.x == 0 && tot) atomicAdd(act, (int)tot);
+        const long long tsc = block_sum_ll<TPB>(scanned);
+        const long long tpu = block_sum_ll<TPB>(pushes);
+        if (threadIdx.x == 0) {
+            if (tot) atomicAdd(act, (int)tot);
+            if (tsc) atomicAddLL(&w.ctl->pr_arcs, tsc);
+            if (tpu) atomicAddLL(&w.ctl->pushes, tpu);
+        }
     }
 
     __device__ bool count_active(int hmax, int nu, bool any_excess, int *out) {
@@ -1315,6 +1324,8 @@ struct StepKernel {
 template <int TPB>
 __global__ void __launch_bounds__(TPB) step_kernel(Work w, uint32_t phases) {
     extern __shared__ __align__(16) int smem[];
+    if (threadIdx.x == 0) g_nsync = 0;
+    __syncthreads();
     if (w.prev_err && __ldcg(w.prev_err)) return;
     if (__ldcg(&w.ctl->error)) return;   // the scan of this round failed
     StepKernel<TPB> K(w, smem);

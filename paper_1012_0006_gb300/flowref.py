@@ -62,6 +62,23 @@ class BatchResult(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ProfileInfo(ctypes.Structure):
+    _fields_ = [("nrounds", ctypes.c_int32), ("launches", ctypes.c_int32), ("scan_ms", ctypes.c_double),
+                ("step_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 12), ("n", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("bfs_visited", ctypes.c_int64), ("bfs_arcs", ctypes.c_int64),
+                ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
+                ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
+                ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64)]
+
+    PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
+              "commit")
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
+        return d
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
                 ("opt", Options)]
@@ -114,6 +131,8 @@ SYMBOLS = {
     "fr_autotune": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(Options), ctypes.c_int32, ctypes.POINTER(Options),
                                    ctypes.POINTER(ctypes.c_double)]),
+    "fr_set_profiling": (ctypes.c_int, [vp, ctypes.c_int32]),
+    "fr_profile_last": (ctypes.c_int, [vp, ctypes.POINTER(ProfileInfo)]),
     "fr_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]),
     "fr_server_add_graph": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, i32p]),
     "fr_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request)]),
@@ -304,8 +323,8 @@ class Context:
             self._check(st)
         return st, res
 
-    def refine_batch(self, g: DeviceGraph, part, k, eps, alpha, opts=None, check=True):
-        cap = k * (k - 1) // 2
+    def refine_batch(self, g: DeviceGraph, part, k, eps, alpha, opts=None, check=True, results=True):
+        cap = k * (k - 1) // 2 if results else 0
         res = (PairResult * max(cap, 1))()
         summ = BatchResult()
         gc = g.c()
@@ -340,6 +359,14 @@ class Context:
                              ctypes.byref(npairs), ctypes.byref(nrounds))
         self._check(st)
         return pa[:npairs.value], pb[:npairs.value], pr[:npairs.value], nrounds.value
+
+    def set_profiling(self, on=True):
+        self._check(lib().fr_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        info = ProfileInfo()
+        self._check(lib().fr_profile_last(self.h, ctypes.byref(info)))
+        return info.as_dict()
 
     def autotune(self, g: DeviceGraph, part, k, eps, alpha, opts=None, trials=2):
         best = Options()
