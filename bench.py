@@ -234,7 +234,7 @@ def run_ours(args, world, rank, local, pg):
         t0 = time.time()
         best, ms = ctx.autotune(g, part0, k, eps, alpha, opts, trials=1)
         tuned = dict(block_threads=best.block_threads, grid_blocks=best.grid_blocks, gr_interval=best.gr_interval,
-                     inner_ops=best.inner_ops, ms=round(ms, 3))
+                     inner_ops=best.inner_ops, pulse_passes=best.pulse_passes, ms=round(ms, 3))
         log(f"[rank {rank}] autotune {tuned} in {time.time() - t0:.1f}s")
 
     def step():
@@ -307,7 +307,8 @@ def run_ours(args, world, rank, local, pg):
         "bfs_gbs": round(bm["bfs"] / max(ph["bfs"] * 1e-3, 1e-12) / 1e9, 1),
         "relabel_gbs": round(bm["relabel"] / max(ph["relabel"] * 1e-3, 1e-12) / 1e9, 1),
         "counters": {kk: P[kk] for kk in ("bfs_visited", "bfs_arcs", "corridor_n", "corridor_arcs", "pulses",
-                                           "relabels", "gr_arcs", "pr_arcs", "pushes", "scc_rounds")},
+                                           "relabels", "gr_arcs", "pr_arcs", "pushes", "scc_rounds",
+                                           "barriers")},
     }
 
     # end to end through the host-buffer entry point: H2D of graph and part, D2H of part

@@ -75,7 +75,7 @@ typedef struct fr_options {
     int32_t grid_blocks;   /* CTAs of the persistent kernel; 0 = tuned default */
     int32_t gr_interval;   /* pulses between global relabels; 0 = tuned default */
     int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
-    int32_t pad0;
+    int32_t pulse_passes;  /* lock-free pulse passes between grid barriers; 0 = default */
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b). */
@@ -226,6 +226,7 @@ typedef struct fr_profile_info {
     int64_t pr_arcs;          /* arcs scanned by push-relabel pulses */
     int64_t pushes;           /* pushes */
     int64_t scc_rounds;       /* SCC colouring rounds */
+    int64_t barriers;         /* grid barriers passed by the persistent kernels */
 } fr_profile_info;
 
 /* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with

@@ -97,8 +97,6 @@ static size_t base_bytes(long long n, long long nnz, int k, int reps, int grid) 
     add(8, nu);                                             // cw
     for (int i = 0; i < 9; ++i) add(4, nu + 1);             // cpair cmin cid indeg outoff ocur plist sinkc part_backup(n)
     add(4, mu);                                             // outs
-    add(4, (long long)reps * nu); add(4, (long long)reps * nu); add(4, (long long)reps * nu);  // indeg_r order hcomp
-    add(8, (long long)reps * nu);                           // hkey
     add(8, k);                                              // blockw
     add(4, ((long long)k * k + 31) / 32);                   // qbits
     add(4, (long long)k * ((2 * k + 31) / 32));             // used
@@ -122,9 +120,53 @@ static size_t pair_bytes(long long P, int R, int reps) {
     add(sizeof(Ctl), R);
     add(8, 3LL * 2 * P * kHistBins);
     add(4, P);
-    add(8, P * reps);
-    add(4, P * reps);
+    (void)reps;
     return b;
+}
+
+// Arrays whose size grows with the number of sweeps R (they hold no state between
+// steps, so they can be reallocated without touching a live corridor).
+static size_t reps_bytes(long long nu, long long P, int reps) {
+    size_t b = 0;
+    auto add = [&](size_t elem, long long cnt) { b += ((elem * (size_t)cnt + 255) / 256) * 256; };
+    add(4, (long long)reps * nu); add(4, (long long)reps * nu); add(4, (long long)reps * nu);  // indeg_r order hcomp
+    add(8, (long long)reps * nu);                           // hkey
+    add(8, P * reps);                                       // sw_absd
+    add(4, P * reps);                                       // sw_j
+    return b;
+}
+
+fr_status ensure_reps(fr_ctx *ctx, int reps) {
+    if (reps < 1) reps = 1;
+    const long long nu = ctx->n_cap;
+    const long long P = std::max(ctx->pairs_cap, 1);
+    if (ctx->reps_mem && reps <= ctx->reps_cap && nu <= ctx->reps_nu && P <= ctx->reps_P) return FR_OK;
+    const int rr = std::max(reps, ctx->reps_cap);
+    const size_t bytes = reps_bytes(nu, P, rr);
+    if (ctx->arena_limit && bytes + ctx->base_bytes + ctx->pair_bytes > ctx->arena_limit) {
+        ctx_error(ctx, "sweep workspace exceeds the arena bound");
+        return FR_ERR_OOM;
+    }
+    if (ctx->reps_mem) cudaFree(ctx->reps_mem);
+    ctx->reps_mem = nullptr;
+    ctx->reps_bytes = 0;
+    if (cudaMalloc(&ctx->reps_mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ctx_error(ctx, "cudaMalloc(%zu) for sweep state failed", bytes);
+        return FR_ERR_OOM;
+    }
+    ctx->reps_bytes = bytes;
+    ctx->reps_cap = rr;
+    ctx->reps_nu = nu;
+    ctx->reps_P = P;
+    char *p = reinterpret_cast<char *>(ctx->reps_mem);
+    ctx->indeg_r = carve<int>(p, (long long)rr * nu);
+    ctx->order = carve<int>(p, (long long)rr * nu);
+    ctx->hcomp = carve<int>(p, (long long)rr * nu);
+    ctx->hkey = carve<unsigned long long>(p, (long long)rr * nu);
+    ctx->sw_absd = carve<long long>(p, P * rr);
+    ctx->sw_j = carve<int>(p, P * rr);
+    return FR_OK;
 }
 
 static void free_base(fr_ctx *ctx) {
@@ -143,10 +185,10 @@ static void free_pairs(fr_ctx *ctx) {
 
 fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     if (reps < 1) reps = 1;
-    if (ctx->base_mem && n <= ctx->n_cap && nnz <= ctx->nnz_cap && k <= ctx->k_cap && reps <= ctx->reps_cap)
-        return FR_OK;
+    if (ctx->base_mem && n <= ctx->n_cap && nnz <= ctx->nnz_cap && k <= ctx->k_cap)
+        return ensure_reps(ctx, reps);
     const int nn = std::max(n, ctx->n_cap), mm = std::max(nnz, ctx->nnz_cap);
-    const int kk = std::max(k, ctx->k_cap), rr = std::max(reps, ctx->reps_cap);
+    const int kk = std::max(k, ctx->k_cap), rr = reps;
     const int grid = ctx->max_coop + 1;
     const size_t bytes = base_bytes(nn, mm, kk, rr, grid);
     if (ctx->arena_limit && bytes + ctx->pair_bytes > ctx->arena_limit) {
@@ -162,7 +204,7 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
         return FR_ERR_OOM;
     }
     ctx->base_bytes = bytes;
-    ctx->n_cap = nn; ctx->nnz_cap = mm; ctx->k_cap = kk; ctx->reps_cap = rr;
+    ctx->n_cap = nn; ctx->nnz_cap = mm; ctx->k_cap = kk;
     char *p = reinterpret_cast<char *>(ctx->base_mem);
     const long long nu = nn, mu = mm;
     ctx->dist = carve<int>(p, nn); ctx->lid = carve<int>(p, nn);
@@ -182,9 +224,6 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     ctx->indeg = carve<int>(p, nu + 1); ctx->outoff = carve<int>(p, nu + 1); ctx->ocur = carve<int>(p, nu + 1);
     ctx->plist = carve<int>(p, nu + 1); ctx->sinkc = carve<int>(p, nu + 1); ctx->part_backup = carve<int>(p, nu + 1);
     ctx->outs = carve<int>(p, mu);
-    ctx->indeg_r = carve<int>(p, (long long)rr * nu); ctx->order = carve<int>(p, (long long)rr * nu);
-    ctx->hcomp = carve<int>(p, (long long)rr * nu);
-    ctx->hkey = carve<unsigned long long>(p, (long long)rr * nu);
     ctx->blockw = carve<long long>(p, kk);
     ctx->qbits = carve<unsigned int>(p, ((long long)kk * kk + 31) / 32);
     ctx->used = carve<unsigned int>(p, (long long)kk * ((2 * kk + 31) / 32));
@@ -200,14 +239,14 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     CK(cudaMemsetAsync(ctx->dist, 0xFF, sizeof(int) * (size_t)nn, ctx->stream));
     CK(cudaMemsetAsync(ctx->lid, 0xFF, sizeof(int) * (size_t)nn, ctx->stream));
     ctx->graph_valid = false;
-    return FR_OK;
+    return ensure_reps(ctx, rr);
 }
 
 fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps) {
     if (reps < 1) reps = 1;
-    if (ctx->pair_mem && P <= ctx->pairs_cap && R <= ctx->rounds_cap && reps <= ctx->reps_cap_pairs) return FR_OK;
+    if (ctx->pair_mem && P <= ctx->pairs_cap && R <= ctx->rounds_cap) return ensure_reps(ctx, reps);
     const int pp = std::max(P, ctx->pairs_cap), rr = std::max(R, ctx->rounds_cap);
-    const int rp = std::max(reps, ctx->reps_cap_pairs);
+    const int rp = reps;
     const size_t bytes = pair_bytes(pp, rr, rp);
     if (ctx->arena_limit && bytes + ctx->base_bytes > ctx->arena_limit) {
         ctx_error(ctx, "pair workspace of %zu bytes exceeds the arena bound", bytes);
@@ -222,7 +261,7 @@ fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps) {
         return FR_ERR_OOM;
     }
     ctx->pair_bytes = bytes;
-    ctx->pairs_cap = pp; ctx->rounds_cap = rr; ctx->reps_cap_pairs = rp;
+    ctx->pairs_cap = pp; ctx->rounds_cap = rr;
     char *p = reinterpret_cast<char *>(ctx->pair_mem);
     ctx->graphs = carve<GraphDev>(p, rr);
     ctx->pairs = carve<PairDev>(p, pp);
@@ -231,10 +270,8 @@ fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps) {
     ctx->ctl = carve<Ctl>(p, rr);
     ctx->hist = carve<long long>(p, 3LL * 2 * pp * kHistBins);
     ctx->pcur = carve<int>(p, pp);
-    ctx->sw_absd = carve<long long>(p, (long long)pp * rp);
-    ctx->sw_j = carve<int>(p, (long long)pp * rp);
     ctx->graph_valid = false;
-    return FR_OK;
+    return ensure_reps(ctx, rp);
 }
 
 // Work descriptor of round r (pairs [p0, p0 + P) of the pair arrays).
@@ -268,6 +305,7 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.reps = reps;
     w.gr_interval = opt && opt->gr_interval > 0 ? opt->gr_interval : ctx->tune_gr;
     w.inner = opt && opt->inner_ops > 0 ? opt->inner_ops : ctx->tune_inner;
+    w.passes = opt && opt->pulse_passes > 0 ? opt->pulse_passes : ctx->tune_passes;
     w.any_mb = opt && opt->mb ? 1 : 0;
     w.seed = opt ? opt->seed : 0;
     w.pulse_cap = opt && opt->pulse_cap > 0 ? opt->pulse_cap : (1LL << 20);
@@ -350,6 +388,7 @@ extern "C" fr_status fr_destroy(fr_ctx *ctx) {
     destroy_graph_cache(ctx);
     free_base(ctx);
     free_pairs(ctx);
+    if (ctx->reps_mem) cudaFree(ctx->reps_mem);
     if (ctx->hg_mem) cudaFree(ctx->hg_mem);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     cudaEventDestroy(ctx->ev0);
@@ -376,7 +415,9 @@ extern "C" const char *fr_status_string(fr_status st) {
     return "unknown status";
 }
 
-extern "C" size_t fr_workspace_bytes(const fr_ctx *ctx) { return ctx ? ctx->base_bytes + ctx->pair_bytes : 0; }
+extern "C" size_t fr_workspace_bytes(const fr_ctx *ctx) {
+    return ctx ? ctx->base_bytes + ctx->pair_bytes + ctx->reps_bytes : 0;
+}
 
 // ---------------------------------------------------------- argument checks --
 

@@ -215,12 +215,7 @@ extern "C" fr_status fr_extract_cut(fr_ctx *ctx, fr_corridor *c, int32_t most_ba
     opt.mb = most_balanced ? 1 : 0;
     opt.mb_reps = mb_reps > 0 ? mb_reps : 1;
     opt.seed = seed;
-    if (opt.mb_reps > ctx->reps_cap || opt.mb_reps > ctx->reps_cap_pairs) {
-        ctx_error(ctx, "mb_reps larger than the workspace built for this corridor (build with the same context first)");
-        // grow would invalidate the corridor state held in the workspace
-        if (opt.mb_reps > ctx->reps_cap) return FR_ERR_INVALID_ARG;
-        if ((st = ensure_pairs(ctx, ctx->pairs_cap, ctx->rounds_cap, opt.mb_reps)) != FR_OK) return st;
-    }
+    if ((st = ensure_reps(ctx, opt.mb_reps)) != FR_OK) return st;   // sweep arrays hold no corridor state
     int mbv = opt.mb;
     int *h = reinterpret_cast<int *>(ctx->h_stage + 8192);
     h[0] = mbv;
@@ -390,7 +385,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
     std::vector<long long> key = {(long long)(uintptr_t)g->xadj, (long long)(uintptr_t)part, g->n, g->nnz,
                                   pl.np, pl.nr, pl.tpb, pl.Ubase, opt->mb, opt->mb_reps, (long long)opt->seed,
                                   opt->gr_interval, opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,
-                                  (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner};
+                                  (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
+                                  opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
@@ -558,6 +554,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.pr_arcs += C[r].pr_arcs;
             P.pushes += C[r].pushes;
             P.scc_rounds += C[r].scc_rounds;
+            P.barriers += C[r].barriers;
         }
     }
     for (int r = 0; r < pl.nr; ++r)
@@ -699,8 +696,9 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     };
     fr_options cand = base;
     cand.block_threads = base.block_threads ? base.block_threads : 512;
-    cand.gr_interval = base.gr_interval ? base.gr_interval : 8;
-    cand.inner_ops = base.inner_ops ? base.inner_ops : 4;
+    cand.gr_interval = base.gr_interval ? base.gr_interval : ctx->tune_gr;
+    cand.inner_ops = base.inner_ops ? base.inner_ops : ctx->tune_inner;
+    cand.pulse_passes = base.pulse_passes ? base.pulse_passes : ctx->tune_passes;
     cand.grid_blocks = base.grid_blocks;
     double bms = 0;
     st = time_shape(cand, &bms);
@@ -710,15 +708,17 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     const std::vector<int> tpbs = {256, 512};
     const std::vector<int> grs = {2, 4, 8, 16, 32};
     const std::vector<int> inners = {1, 2, 4, 8};
+    const std::vector<int> passes = {1, 2, 4, 8};
     for (int sweep = 0; sweep < 2 && st == FR_OK; ++sweep) {
-        for (int dim = 0; dim < 4 && st == FR_OK; ++dim) {
-            const std::vector<int> &vals = dim == 0 ? tpbs : dim == 1 ? grids : dim == 2 ? grs : inners;
+        for (int dim = 0; dim < 5 && st == FR_OK; ++dim) {
+            const std::vector<int> &vals = dim == 0 ? tpbs : dim == 1 ? grids : dim == 2 ? grs : dim == 3 ? inners : passes;
             for (int v : vals) {
                 fr_options o = cand;
                 if (dim == 0) o.block_threads = v;
                 if (dim == 1) { if (v < 0) continue; o.grid_blocks = v; }
                 if (dim == 2) o.gr_interval = v;
                 if (dim == 3) o.inner_ops = v;
+                if (dim == 4) o.pulse_passes = v;
                 if (memcmp(&o, &cand, sizeof(o)) == 0) continue;
                 double ms = 0;
                 st = time_shape(o, &ms);
@@ -733,6 +733,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     ctx->tune_grid = cand.grid_blocks;
     ctx->tune_gr = cand.gr_interval;
     ctx->tune_inner = cand.inner_ops;
+    ctx->tune_passes = cand.pulse_passes;
     if (best) *best = cand;
     if (best_ms) *best_ms = bms;
     return FR_OK;

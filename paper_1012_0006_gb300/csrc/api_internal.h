@@ -27,7 +27,7 @@ struct fr_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     char *h_stage = nullptr;
     // launch shape (fr_autotune writes these)
-    int tune_tpb = 512, tune_grid = 0, tune_gr = 8, tune_inner = 4;
+    int tune_tpb = 512, tune_grid = 0, tune_gr = 16, tune_inner = 2, tune_passes = 2;
     // graph-size workspace
     void *base_mem = nullptr;
     size_t base_bytes = 0;
@@ -53,7 +53,11 @@ struct fr_ctx {
     // pair-count workspace
     void *pair_mem = nullptr;
     size_t pair_bytes = 0;
-    int pairs_cap = 0, rounds_cap = 0, reps_cap_pairs = 0;
+    int pairs_cap = 0, rounds_cap = 0;
+    // sweep-count workspace
+    void *reps_mem = nullptr;
+    size_t reps_bytes = 0;
+    long long reps_nu = 0, reps_P = 0;
     fr::GraphDev *graphs = nullptr;
     fr::PairDev *pairs = nullptr;
     fr::SideDev *sides = nullptr;
@@ -98,6 +102,7 @@ long long host_lmax(long long W, long long maxc, int k, double eps);
 fr_status status_from_ctl(fr_ctx *ctx, const fr::Ctl &c, const char *where);
 fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps);
 fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps);
+fr_status ensure_reps(fr_ctx *ctx, int reps);
 fr::Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt);
 int choose_tpb(fr_ctx *ctx, const fr_options *opt);
 int choose_grid(fr_ctx *ctx, const fr_options *opt, int tpb, int nsides, long long est_vertices);

@@ -107,6 +107,7 @@ struct Ctl {
     long long gr_arcs;        // arcs scanned by global relabels
     long long pr_arcs;        // arcs scanned by push-relabel pulses
     long long pushes;         // pushes
+    long long barriers;       // grid barriers passed (CTA 0)
 };
 
 // Everything a kernel needs, passed by value.
@@ -141,6 +142,7 @@ struct Work {
     int *sw_j;                   // [npairs*reps]
     // options
     int reps, gr_interval, inner, any_mb;
+    int passes, pad_p;           // lock-free pulse passes per grid barrier
     unsigned long long seed;
     long long pulse_cap;
 };

@@ -143,16 +143,19 @@ struct Grid {
     }
 };
 
-// Warp-cooperative walk over the arcs of many rows: each warp takes 32 rows,
-// flattens their arc ranges and visits 32 arcs per iteration with all lanes
-// converged, so appends can be aggregated with one atomic per warp.
+// Warp-cooperative walk over the arcs of many rows: each warp takes R consecutive
+// rows, R = ceil(rows / warps) clamped to [1, 32], so that small frontiers still
+// spread over every warp; the warp flattens its rows' arc ranges and visits 32
+// arcs per iteration with all lanes converged (appends aggregate per warp).
 template <class RowF, class ArcF>
 __device__ __forceinline__ void warp_rows(long long begin, long long end, const Grid &G, RowF row, ArcF arc) {
     const int lane = threadIdx.x & 31;
-    for (long long b = begin + G.warp * 32; b < end; b += G.nwarps * 32) {
+    long long R = (end - begin + G.nwarps - 1) / G.nwarps;
+    R = R < 1 ? 1 : (R > 32 ? 32 : R);
+    for (long long b = begin + G.warp * R; b < end; b += G.nwarps * R) {
         const long long idx = b + lane;
         int rs = 0, deg = 0, ctx = 0;
-        if (idx < end) row(idx, rs, deg, ctx);
+        if (lane < R && idx < end) row(idx, rs, deg, ctx);
         int incl = deg;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -269,6 +272,7 @@ struct StepKernel {
             w.ctl->fl = fl;
             w.ctl->pl = pl;
             w.ctl->cl = cl;
+            w.ctl->barriers += g_nsync;
         }
     }
 
@@ -416,22 +420,39 @@ struct StepKernel {
                               (unsigned long long)__ldg(Gr.vwgt + v));
                 }
                 if (!grid_sync(ctl)) return false;
-                // every CTA picks the same bucket for every side
-                for (int s = threadIdx.x; s < ns; s += TPB) {
-                    if (s_state[s] != SS_SELECT) continue;
-                    long long acc = 0;
-                    int b = 0;
-                    for (; b < kHistBins; ++b) {
-                        const long long h = __ldcg(&hist[(long long)s * kHistBins + b]);
-                        if (acc + h > s_rem[s]) break;
-                        acc += h;
+                // every CTA picks the same bucket for every side (one warp per side)
+                {
+                    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                    for (int s = wid; s < ns; s += TPB / 32) {
+                        if (s_state[s] != SS_SELECT) continue;
+                        const long long *hs = hist + (long long)s * kHistBins + lane * 8;
+                        long long hv[8], lsum = 0;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) { hv[u] = __ldcg(hs + u); lsum += hv[u]; }
+                        long long incl = lsum;
+#pragma unroll
+                        for (int dd = 1; dd < 32; dd <<= 1) {
+                            const long long y = __shfl_up_sync(FULL, incl, dd);
+                            if (lane >= dd) incl += y;
+                        }
+                        const long long rem = s_rem[s];
+                        const unsigned int over = __ballot_sync(FULL, incl > rem);
+                        if (over == 0) {   // cannot happen: the level's weight exceeds rem
+                            if (lane == 0) fail(ctl, E_INTERNAL, 20);
+                            continue;
+                        }
+                        const int L = __ffs(over) - 1;
+                        if (lane == L) {
+                            long long acc = incl - lsum;
+                            int b = 0;
+                            for (; b < 8; ++b) {
+                                if (acc + hv[b] > rem) break;
+                                acc += hv[b];
+                            }
+                            s_rem[s] = rem - acc;
+                            s_T[s] |= (L * 8 + b) << shift;
+                        }
                     }
-                    if (b == kHistBins) {   // cannot happen: the level's weight exceeds rem
-                        fail(ctl, E_INTERNAL, 20);
-                        b = kHistBins - 1;
-                    }
-                    s_rem[s] -= acc;
-                    s_T[s] |= b << shift;
                 }
                 __syncthreads();
             }
@@ -559,6 +580,7 @@ struct StepKernel {
             const PairDev P = w.pairs[s >> 1];
             const GraphDev &Gr = w.graphs[P.g];
             int j = __ldcg(&w.off[i]);
+            long long cout = 0;
             const int j1 = __ldg(Gr.xadj + v + 1);
             for (int e = __ldg(Gr.xadj + v); e < j1; ++e) {
                 const int u = __ldg(Gr.adjncy + e);
@@ -567,6 +589,7 @@ struct StepKernel {
                 const int h = __ldcg(Gr.lid + u);
                 if (h < 0) continue;
                 const int c = __ldg(Gr.adjwgt + e);
+                cout += c;
                 w.head[j] = h;
                 w.cap[j] = c;
                 w.res[j] = c;
@@ -582,8 +605,11 @@ struct StepKernel {
                 w.rev[j] = __ldcg(&w.off[h]) + q;
                 ++j;
             }
+            // Preflow: s -> v carries what v can pass on, c_out(v) < INF_v.  Flow
+            // through s -> v never exceeds c_out(v), so the max flow is unchanged and
+            // only the excess that is pushed in and then stranded has to return.
             const unsigned char bd = w.border[i];
-            const int fx0 = bd == 1 ? w.infc[i] : 0;   // saturate s -> v
+            const int fx0 = bd == 1 ? (int)(cout < w.infc[i] ? cout : w.infc[i]) : 0;
             w.fx[i] = fx0;
             w.ex[i] = fx0;
             w.lab[i] = 0;
@@ -595,8 +621,10 @@ struct StepKernel {
 
     // ------------------------------------------------------------- max flow --
 
-    // Exact distance labels by reverse BFS over residual arcs, from t (phase 1)
-    // or from s (phase 2).  Vertices that cannot reach the target get hmax.
+    // Exact distance labels, to t (phase 1) or to s (phase 2): reverse BFS over
+    // residual arcs, level by level from the target's border.  Each frontier row is
+    // expanded once; warp_rows spreads a level over all warps.  Vertices that cannot
+    // reach the target keep hmax (the gap heuristic comes with it).
     __device__ bool global_relabel(int phase2, int hmax, int nu) {
         Ctl *ctl = w.ctl;
         {
@@ -638,8 +666,9 @@ struct StepKernel {
                     if (valid) {
                         ++arcs;
                         y = w.head[j];
-                        if (__ldcg(&w.res[w.rev[j]]) > 0 && __ldcg(&w.lab[y]) == hmax)
-                            got = atomicCAS(&w.lab[y], hmax, d + 1) == hmax;
+                        const int rv = w.rev[j];
+                        const int ly = __ldcg(&w.lab[y]);
+                        if (ly == hmax && __ldcg(&w.res[rv]) > 0) got = atomicCAS(&w.lab[y], hmax, d + 1) == hmax;
                     }
                     const int slot = warp_append(ncnt, got);
                     if (got) nq[slot] = y;
@@ -654,7 +683,7 @@ struct StepKernel {
             }
         }
         if (G.tid == 0) ctl->relabels += 1;
-        if (arcs) atomicAdd((unsigned long long *)&ctl->gr_arcs, (unsigned long long)arcs);
+        if (arcs) atomicAddLL(&ctl->gr_arcs, arcs);
         return true;
     }
 
@@ -664,6 +693,8 @@ struct StepKernel {
     __device__ void pulse(int phase2, int hmax, int nu, int *act) {
         int local = 0;
         long long scanned = 0, pushes = 0;
+        for (int pass = 0; pass < w.passes; ++pass) {
+        const bool last = pass + 1 == w.passes;
         for (long long i = G.tid; i < nu; i += G.size) {
             long long e = __ldcg(&w.ex[i]);
             if (e <= 0) continue;
@@ -674,11 +705,18 @@ struct StepKernel {
             for (int it = 0; it < w.inner; ++it) {
                 int hmin = INT_MAX, best = -1;
                 scanned += j1 - j0;
-                for (int j = j0; j < j1; ++j) {
-                    if (__ldcg(&w.res[j]) > 0) {
-                        const int hh = __ldcg(&w.lab[w.head[j]]);
-                        if (hh < hmin) { hmin = hh; best = j; }
+                for (int j = j0; j < j1; j += 4) {
+                    int r[4], hd[4], hh[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        r[u] = j + u < j1 ? __ldcg(&w.res[j + u]) : 0;
+                        hd[u] = j + u < j1 ? w.head[j + u] : 0;
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) hh[u] = r[u] > 0 ? __ldcg(&w.lab[hd[u]]) : INT_MAX;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (hh[u] < hmin) { hmin = hh[u]; best = j + u; }
                 }
                 if (phase2 ? (bd == 1 && w.fx[i] > 0) : (bd == 2)) { hmin = 0; best = -2; }
                 if (best == -1) { h = hmax; w.lab[i] = h; break; }
@@ -700,7 +738,7 @@ struct StepKernel {
                         atomicSub(&w.res[best], (int)d);
                         atomicAdd(&w.res[w.rev[best]], (int)d);
                         atomicAddLL(&w.ex[w.head[best]], d);
-                        ++local;
+                        if (last) ++local;
                     }
                     atomicAddLL(&w.ex[i], -d);
                     e -= d;
@@ -712,7 +750,8 @@ struct StepKernel {
                     if (h >= hmax) break;
                 }
             }
-            if (e > 0 && h < hmax) ++local;
+            if (last && e > 0 && h < hmax) ++local;
+        }
         }
         __syncthreads();
         const long long tot = block_sum_ll<TPB>(local);
@@ -760,19 +799,22 @@ struct StepKernel {
                 return false;
             }
             timer_mark(w, t0, phase2 ? T_FLOW2 : T_FLOW1);
-            if (a == 0 || since_gr >= w.gr_interval) {
+            // Nothing moved in the last pass.  Pushes of earlier lock-free passes may
+            // have landed after their target was scanned, so count once more behind
+            // the barrier: no vertex with excess below hmax (labels are valid lower
+            // bounds on the residual distance) means no excess can reach the target.
+            if (a == 0) {
+                int *cnt = &ctl->act[pl % 3];
+                if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
+                if (!count_active(hmax, nu, false, cnt)) return false;
+                const int left = __ldcg(cnt);
+                ++pl;
+                if (left == 0) break;
+            }
+            if (since_gr >= w.gr_interval) {
                 if (!global_relabel(phase2, hmax, nu)) return false;
                 since_gr = 0;
                 timer_mark(w, t0, T_GR);
-                if (a == 0) {
-                    // exact labels: done when no vertex with excess can reach the target
-                    int *cnt = &ctl->act[pl % 3];
-                    if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
-                    if (!count_active(hmax, nu, false, cnt)) return false;
-                    const int left = __ldcg(cnt);
-                    ++pl;
-                    if (left == 0) break;
-                }
             }
         }
         if (G.tid == 0) ctl->pulses += pulses;
@@ -800,6 +842,9 @@ struct StepKernel {
     }
 
     // ---------------------------------------------------------- residual sets --
+    // Bit 1: reachable from s (the smallest source set, Ford-Fulkerson labelling);
+    // bit 2: reaches t.  Both searches share one frontier queue, entries tagged by
+    // the top bit.
     __device__ bool reach() {
         Ctl *ctl = w.ctl;
         unsigned long long t0 = globaltimer();
@@ -844,13 +889,9 @@ struct StepKernel {
                     const bool tside = ent < 0;
                     if (valid) {
                         y = w.head[j];
-                        if (!tside) {
-                            if (__ldcg(&w.res[j]) > 0 && !(__ldcg(&w.rflag[y]) & 1))
-                                got = !(atomicOr(&w.rflag[y], 1) & 1);
-                        } else {
-                            if (__ldcg(&w.res[w.rev[j]]) > 0 && !(__ldcg(&w.rflag[y]) & 2))
-                                got = !(atomicOr(&w.rflag[y], 2) & 2);
-                        }
+                        const int bit = tside ? 2 : 1;
+                        if (!(__ldcg(&w.rflag[y]) & bit) && __ldcg(&w.res[tside ? w.rev[j] : j]) > 0)
+                            got = !(atomicOr(&w.rflag[y], bit) & bit);
                     }
                     const int slot = warp_append(ncnt, got);
                     if (got) nq[slot] = y | (tside ? (int)0x80000000 : 0);
@@ -1322,7 +1363,7 @@ struct StepKernel {
 };
 
 template <int TPB>
-__global__ void __launch_bounds__(TPB) step_kernel(Work w, uint32_t phases) {
+__global__ void __launch_bounds__(TPB, 1) step_kernel(Work w, uint32_t phases) {
     extern __shared__ __align__(16) int smem[];
     if (threadIdx.x == 0) g_nsync = 0;
     __syncthreads();

@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
-                ("pad0", ctypes.c_int32)]
+                ("pulse_passes", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -68,7 +68,7 @@ class ProfileInfo(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("bfs_visited", ctypes.c_int64), ("bfs_arcs", ctypes.c_int64),
                 ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
                 ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
-                ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64)]
+                ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64), ("barriers", ctypes.c_int64)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")
@@ -333,7 +333,8 @@ class Context:
                                    ctypes.byref(summ))
         if check:
             self._check(st)
-        return st, [res[i].as_dict() for i in range(summ.npairs)], summ.as_dict()
+        pairs = [res[i].as_dict() for i in range(min(summ.npairs, cap))]
+        return st, pairs, summ.as_dict()
 
     def refine_batch_host(self, xadj, adjncy, adjwgt, vwgt, part, k, eps, alpha, opts=None, cap=0):
         """Host-buffer form: arrays are numpy or (pinned) CPU tensors; part is updated in place."""

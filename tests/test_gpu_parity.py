@@ -253,7 +253,8 @@ def test_launch_shapes_give_identical_partitions(F, ctx):
     w = I.config(4, scale=1 / 128)
     ref = None
     for shape in [dict(), dict(grid_blocks=1), dict(grid_blocks=3, block_threads=256), dict(gr_interval=1),
-                  dict(gr_interval=32, inner_ops=1), dict(inner_ops=16, block_threads=256)]:
+                  dict(gr_interval=32, inner_ops=1), dict(inner_ops=16, block_threads=256), dict(pulse_passes=8),
+                  dict(pulse_passes=1, grid_blocks=300)]:
         g, part = _dev(F, w)
         ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], F.default_options(mb=1, **shape))
         got = part.cpu().numpy()
