@@ -243,6 +243,39 @@ fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info);
 fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, double eps, double alpha,
                       const fr_options *opt, int32_t trials, fr_options *best, double *best_ms);
 
+/* ---- refinement without device allocation ------------------------------------ */
+
+/* Size limits of fr_refine_pair_noalloc (its scratch is fixed at build time). */
+#define FR_NOALLOC_MAX_N 65536       /* vertices */
+#define FR_NOALLOC_MAX_NNZ 524288    /* directed CSR entries (2|E|) */
+#define FR_NOALLOC_MAX_K 256         /* blocks */
+#define FR_NOALLOC_MAX_REPS 4        /* most-balanced sweeps */
+
+/* Same refinement as fr_refine_pair (same arguments and results), for callers
+ * that cannot allocate device memory: a process whose device memory belongs to
+ * another allocator (a framework's caching allocator or a quota-managed
+ * service), or a latency-critical loop that must not stall on cudaMalloc /
+ * cudaFree or risk an allocation failure halfway through.  No paper
+ * counterpart: this is a deployment variant, not part of the method.
+ *
+ * It needs no fr_ctx and never calls cudaMalloc, cudaFree or any other
+ * allocating routine.  Its workspace is one static device array of about 23 MB
+ * that every GPU which loads libflowref.so holds until the process exits.  The
+ * first call on a device looks up that array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.
+ * Work is queued on `stream` (a cudaStream_t, NULL = the legacy default stream)
+ * and the call returns when it is done.
+ *
+ * Limits: n <= FR_NOALLOC_MAX_N, nnz <= FR_NOALLOC_MAX_NNZ, k <=
+ * FR_NOALLOC_MAX_K, mb_reps <= FR_NOALLOC_MAX_REPS; larger problems return
+ * FR_ERR_TOO_LARGE without touching part (use fr_refine_pair for them).
+ * Every call uses the same array, which keeps the previous call's contents;
+ * each call clears what it needs before use.  Two calls whose work overlaps on
+ * the GPU (concurrent streams or host threads, on the same device) race on the
+ * array and corrupt each other: serialise them. */
+fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, int32_t k, int32_t a, int32_t b, double eps,
+                                 double alpha, const fr_options *opt, fr_pair_result *res, void *stream);
+
 /* ---- serving: continuous batching of refinement requests ------------------- */
 
 typedef struct fr_server fr_server;

@@ -31,6 +31,7 @@ CUDA_SOURCES = [
     "round_kernel.cu",
     "prep_kernel.cu",
     "serve.cu",
+    "noalloc.cu",
 ]
 
 

@@ -131,6 +131,9 @@ SYMBOLS = {
     "fr_autotune": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(Options), ctypes.c_int32, ctypes.POINTER(Options),
                                    ctypes.POINTER(ctypes.c_double)]),
+    "fr_refine_pair_noalloc": (ctypes.c_int, [ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                              ctypes.POINTER(Options), ctypes.POINTER(PairResult), vp]),
     "fr_set_profiling": (ctypes.c_int, [vp, ctypes.c_int32]),
     "fr_profile_last": (ctypes.c_int, [vp, ctypes.POINTER(ProfileInfo)]),
     "fr_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]),
