@@ -332,6 +332,11 @@ def run_ours(args, world, rank, local, pg):
                "h2d_bytes_per_step": 4 * ((n + 1) + 2 * nnz + 2 * n), "d2h_bytes_per_step": 4 * n,
                "ms_per_step": round(tot / ke * 1e3, 3)}
 
+    serving = None
+    if args.serve or args.serve_full:
+        serving = run_serving(F, local, full=args.serve_full, requests=args.serve_requests,
+                              log_prefix=f"[rank {rank}] ")
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu, _, _ = oracle_sample(w, budget_s=args.cpu_budget)
@@ -348,10 +353,86 @@ def run_ours(args, world, rank, local, pg):
                        "parallelism": "replicas" if world > 1 else "single", "launch_shape": tuned},
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
-            "cpu_baseline": cpu, "clocks": clk,
+            "cpu_baseline": cpu, "clocks": clk, "serving": serving,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+# ------------------------------------------------------------------ serving ----
+
+def run_serving(F, device, full=False, requests=None, log_prefix=""):
+    """Continuous-batching serving of seeded refinement requests (Poisson arrivals).
+
+    Pool: 2D grids and 2D/3D rggs (mean degree 8-12, unit or [1,10] weights), k in {2,4,8},
+    eps in {0.01,0.03,0.05}, alpha 2, most balanced cuts, one sweep of rounds per request.
+    First the closed-loop saturated rate is measured (max_inflight requests always queued),
+    then requests arrive as a Poisson process at 0.7 x that rate; latency is submit ->
+    completion on the host clock."""
+    import threading
+    import numpy as np
+    from paper_1012_0006_gb300 import inputs as I
+    t0 = time.time()
+    if full:
+        pool = I.serving_pool(count=48, max_n=1 << 21)
+        nreq = requests or 10000
+    else:
+        pool = I.serving_pool(count=24, max_n=1 << 18)
+        nreq = requests or 1500
+    rs = np.random.Generator(np.random.Philox(I.SEED_BASE + 5))
+    parts = {}
+    reqs = []
+    for t in range(nreq):
+        gi = int(rs.integers(0, len(pool)))
+        k = int(rs.choice([2, 4, 8]))
+        if (gi, k) not in parts:
+            parts[(gi, k)] = I.serving_partition(pool[gi], k)
+        reqs.append((gi, k, float(rs.choice([0.01, 0.03, 0.05]))))
+    log(f"{log_prefix}serving pool {len(pool)} graphs, {len(parts)} partitions, {nreq} requests "
+        f"prepared in {time.time() - t0:.1f}s")
+    nmax = max(g["n"] for g in pool)
+    opts = F.default_options(mb=1)
+    srv = F.Server(device, max_inflight=32, opts=opts)
+    ids = [srv.add_graph(g["xadj"], g["adjncy"], g["adjwgt"], g["vwgt"]) for g in pool]
+
+    def drain(count, lat, stat):
+        for _ in range(count):
+            resp, _ = srv.next(nmax, timeout_ms=600000)
+            lat.append(resp["latency_ms"])
+            stat.append(resp["status"])
+
+    # closed loop: everything queued at once (saturated)
+    nsat = min(len(reqs), 400)
+    lat, stat = [], []
+    t1 = time.perf_counter()
+    for t, (gi, k, eps) in enumerate(reqs[:nsat]):
+        srv.submit(ids[gi], parts[(gi, k)], k, eps, 2.0, t)
+    drain(nsat, lat, stat)
+    sat = nsat / (time.perf_counter() - t1)
+    # open loop: Poisson arrivals at 0.7 x saturated
+    lam = 0.7 * sat
+    gaps = rs.exponential(1.0 / lam, len(reqs))
+    lat, stat = [], []
+    th = threading.Thread(target=drain, args=(len(reqs), lat, stat))
+    th.start()
+    t1 = time.perf_counter()
+    nxt = t1
+    for t, (gi, k, eps) in enumerate(reqs):
+        nxt += gaps[t]
+        d = nxt - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        srv.submit(ids[gi], parts[(gi, k)], k, eps, 2.0, 10_000_000 + t)
+    th.join()
+    el = time.perf_counter() - t1
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(reqs), "failed": int(sum(1 for x in stat if x != 0)),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "requests_per_s": round(len(reqs) / el, 2), "saturated_requests_per_s": round(sat, 2),
+            "arrival_rate": round(lam, 2), "steps": st["steps"], "max_concurrent": st["max_concurrent"],
+            "pool": f"{len(pool)} graphs up to {nmax} vertices" + ("" if full else " (bounded sample of the mix)")}
 
 
 # --------------------------------------------------------- reference arm ----
@@ -396,6 +477,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-pairs", type=int, default=6)
+    ap.add_argument("--serve", action=argparse.BooleanOptionalAction, default=True,
+                    help="bounded serving measurement (p50/p99) in the JSON line")
+    ap.add_argument("--serve-full", action="store_true", help="the full serving mix: 48 graphs, 10,000 requests")
+    ap.add_argument("--serve-requests", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 (timing rule)")

@@ -55,7 +55,14 @@ struct GraphDev {
     long long *blockw;   // [k] c(V_i), maintained by the commit phase
     int n, nnz, k, base; // base: offset of this graph in the concatenated vertex range
     long long Lmax;
+    int sbase, pad;      // sob values are relative to this graph's first side in the step
 };
+
+// Side of block `blk` of graph Gr in this step, or -1.
+__device__ __forceinline__ int side_of(const GraphDev &Gr, int blk) {
+    const int s = __ldg(Gr.sob + blk);
+    return s < 0 ? -1 : s + Gr.sbase;
+}
 
 struct PairDev {
     int g, a, b, mb;

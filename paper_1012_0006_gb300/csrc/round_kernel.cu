@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(TPB) scan_kernel(Work w, int g) {
         const int v = (int)(base + lane);
         const bool valid = v < n;
         const int blk = valid ? __ldg(part + v) : -1;
-        const int sd = valid ? __ldg(G.sob + blk) : -1;
+        const int sd = valid ? side_of(G, blk) : -1;
         if (__ballot_sync(FULL, sd >= 0) == 0) continue;
         int pb = -2;
         if (sd >= 0) {
@@ -477,16 +477,19 @@ struct StepKernel {
     __device__ bool in_corridor(const GraphDev &Gr, int v) const {
         const int d = __ldcg(Gr.dist + v);
         if (d < 0) return false;
-        const int s = __ldg(Gr.sob + Gr.part[v]);
+        const int s = side_of(Gr, Gr.part[v]);
         if (s < 0) return false;
         const int ls = s_lstar[s];
         return d < ls || (d == ls && v < s_T[s]);
     }
 
-    __device__ int graph_of(long long x) const {
-        int g = 0;
-        while (g + 1 < w.ngraphs && w.graphs[g + 1].base <= x) ++g;
-        return g;
+    __device__ int graph_of(long long x) const {   // last graph whose base <= x
+        int lo = 0, hi = w.ngraphs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (w.graphs[mid].base <= x) lo = mid; else hi = mid - 1;
+        }
+        return lo;
     }
 
     // -------------------------------------------------------------- local ids --
@@ -508,7 +511,7 @@ struct StepKernel {
                     if (off < w.nu_cap) {
                         Gr.lid[v] = (int)off;
                         w.gid[off] = v;
-                        w.sid[off] = __ldg(Gr.sob + Gr.part[v]);
+                        w.sid[off] = side_of(Gr, Gr.part[v]);
                     } else {
                         fail(w.ctl, E_INTERNAL, 30);
                     }

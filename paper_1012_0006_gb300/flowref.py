@@ -381,3 +381,64 @@ class Context:
                                ctypes.byref(best), ctypes.byref(ms))
         self._check(st)
         return best, ms.value
+
+
+class Server:
+    """Continuous-batching refinement server (fr_server_*): graphs stay on the device,
+    requests are admitted by free slots and arena bytes, each device step advances
+    every in-flight request by one round."""
+
+    def __init__(self, device=0, max_inflight=16, arena_bytes=0, opts=None):
+        cfg = ServerConfig()
+        cfg.device = device
+        cfg.max_inflight = max_inflight
+        cfg.arena_bytes = arena_bytes
+        cfg.opt = opts if opts is not None else default_options()
+        h = ctypes.c_void_p()
+        st = lib().fr_server_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != FR_OK:
+            raise FlowRefError(st, "fr_server_create failed")
+        self.h = h
+        self.sizes = []
+
+    def add_graph(self, xadj, adjncy, adjwgt, vwgt):
+        xadj, adjncy, adjwgt, vwgt = (_np32(a) for a in (xadj, adjncy, adjwgt, vwgt))
+        gid = ctypes.c_int32()
+        st = lib().fr_server_add_graph(self.h, len(vwgt), len(adjncy), xadj.ctypes.data, adjncy.ctypes.data,
+                                       adjwgt.ctypes.data, vwgt.ctypes.data, ctypes.byref(gid))
+        if st != FR_OK:
+            raise FlowRefError(st, "fr_server_add_graph failed")
+        self.sizes.append(len(vwgt))
+        return gid.value
+
+    def submit(self, graph_id, part, k, eps, alpha, tag):
+        part = _np32(part)
+        req = Request(graph_id, k, eps, alpha, part.ctypes.data_as(i32p), tag)
+        st = lib().fr_server_submit(self.h, ctypes.byref(req))
+        if st != FR_OK:
+            raise FlowRefError(st, "fr_server_submit failed")
+
+    def next(self, n_max, timeout_ms=-1):
+        resp = Response()
+        out = np.empty(n_max, np.int32)
+        st = lib().fr_server_next(self.h, ctypes.byref(resp), out.ctypes.data_as(i32p), n_max, timeout_ms)
+        if st != FR_OK:
+            raise FlowRefError(st, "fr_server_next: nothing completed in time")
+        return resp.as_dict(), out
+
+    def stats(self):
+        s, a, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        m = ctypes.c_int32()
+        lib().fr_server_stats(self.h, ctypes.byref(s), ctypes.byref(a), ctypes.byref(c), ctypes.byref(m))
+        return dict(steps=s.value, admitted=a.value, completed=c.value, max_concurrent=m.value)
+
+    def close(self):
+        if self.h:
+            lib().fr_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
