@@ -332,6 +332,8 @@ def run_ours(args, world, rank, local, pg):
                "h2d_bytes_per_step": 4 * ((n + 1) + 2 * nnz + 2 * n), "d2h_bytes_per_step": 4 * n,
                "ms_per_step": round(tot / ke * 1e3, 3)}
 
+    compare = batched_vs_per_pair(F, ctx, dev) if args.compare else None
+
     serving = None
     if args.serve or args.serve_full:
         serving = run_serving(F, local, full=args.serve_full, requests=args.serve_requests,
@@ -353,10 +355,47 @@ def run_ours(args, world, rank, local, pg):
                        "parallelism": "replicas" if world > 1 else "single", "launch_shape": tuned},
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
-            "cpu_baseline": cpu, "clocks": clk, "serving": serving,
+            "cpu_baseline": cpu, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+# ------------------------------------------------- batched vs one pair per launch ----
+
+def batched_vs_per_pair(F, ctx, dev, reps=3):
+    """128^3 grid, k = 16: one fr_refine_batch sweep against the same pairs refined by
+    fr_refine_pair one launch at a time, in round order (same results, checked)."""
+    import numpy as np
+    import torch
+    from paper_1012_0006_gb300 import inputs as I
+    w = I.config(3)
+    g = F.DeviceGraph.from_workload(w, device=dev)
+    part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
+    opts = F.default_options(mb=1)
+    k, eps, alpha = w["k"], w["eps"], w["alpha"]
+    part = part0.clone()
+    st, res, summ = ctx.refine_batch(g, part, k, eps, alpha, opts)
+    ref = part.clone()
+    pairs = [(r["a"], r["b"]) for r in res]
+    tb, tp = [], []
+    for _ in range(reps):
+        part.copy_(part0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.refine_batch(g, part, k, eps, alpha, opts, results=False)
+        tb.append(time.perf_counter() - t0)
+        part.copy_(part0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in pairs:
+            ctx.refine_pair(g, part, k, a, b, eps, alpha, opts)
+        tp.append(time.perf_counter() - t0)
+        assert torch.equal(part, ref), "one-pair-per-launch result differs from the batch"
+    b, p = min(tb), min(tp)
+    return {"workload": "grid3d 128^3 k=16 eps=0.03 alpha=2 MB", "pairs": len(pairs),
+            "rounds": summ["nrounds"], "batched_ms": round(b * 1e3, 3), "per_pair_ms": round(p * 1e3, 3),
+            "speedup": round(p / b, 2)}
 
 
 # ------------------------------------------------------------------ serving ----
@@ -480,6 +519,8 @@ def main():
     ap.add_argument("--serve", action=argparse.BooleanOptionalAction, default=True,
                     help="bounded serving measurement (p50/p99) in the JSON line")
     ap.add_argument("--serve-full", action="store_true", help="the full serving mix: 48 graphs, 10,000 requests")
+    ap.add_argument("--compare", action=argparse.BooleanOptionalAction, default=True,
+                    help="128^3 grid: batched sweep vs one pair per launch")
     ap.add_argument("--serve-requests", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

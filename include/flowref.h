@@ -213,6 +213,7 @@ typedef struct fr_profile_info {
     int32_t launches;         /* kernels launched by it */
     double scan_ms;           /* boundary-scan kernels, CUDA events around each launch (profiling on) */
     double step_ms;           /* persistent step kernels, CUDA events around each launch (profiling on) */
+    double cluster_ms;        /* per-pair cluster max-flow kernels, CUDA events (profiling on) */
     double phase_ms[12];      /* in-kernel timers: bfs, select, lid, build, flow, relabel, return,
                                  reach, scc, sweep, eval, commit (summed over rounds) */
     int64_t n, nnz;           /* graph scanned by each boundary-scan launch */

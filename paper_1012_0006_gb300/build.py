@@ -32,6 +32,7 @@ CUDA_SOURCES = [
     "prep_kernel.cu",
     "serve.cu",
     "noalloc.cu",
+    "cluster_flow.cu",
 ]
 
 

@@ -371,6 +371,14 @@ extern "C" fr_status fr_create(fr_ctx **out, int32_t device, size_t arena_bytes,
     if (step_max_grid(512, 64, &maxb, &sms) != cudaSuccess) { delete ctx; return FR_ERR_CUDA; }
     ctx->sms = sms;
     ctx->max_coop = std::max(maxb, 1) * 4;
+    {
+        int mc = 0;
+        if (cluster_flow_capacity(ctx->cluster_size, &mc) != cudaSuccess) {
+            cudaGetLastError();
+            mc = 0;
+        }
+        ctx->max_clusters = mc;
+    }
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
     if (cudaHostAlloc(&ctx->h_stage, kHostStage, cudaHostAllocDefault) != cudaSuccess) {
@@ -512,6 +520,33 @@ fr_status reset_idle(fr_ctx *ctx) {
     return FR_OK;
 }
 
+cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev) {
+    // ev (optional): 6 events bracketing step 1, the cluster kernel and step 2
+    if (ctx->max_clusters <= 0) {
+        w.cluster_mode = 0;
+        if (ev) cudaEventRecord(ev[0], st);
+        cudaError_t e = launch_step(w, PH_ALL, grid, tpb, st);
+        if (ev) {
+            cudaEventRecord(ev[1], st);
+            for (int i = 2; i < 6; ++i) cudaEventRecord(ev[i], st);
+        }
+        return e;
+    }
+    w.cluster_mode = 1;
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaError_t e = launch_step(w, PH_BFS | PH_LID | PH_BUILD, grid, tpb, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
+    e = launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, st);
+    if (ev) cudaEventRecord(ev[3], st);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[4], st);
+    e = launch_step(w, PH_FLOW | PH_CUT | PH_EVAL | PH_COMMIT, grid, tpb, st);
+    if (ev) cudaEventRecord(ev[5], st);
+    return e;
+}
+
 // ------------------------------------------------------------ one pair ------
 
 struct IterOut {
@@ -531,7 +566,7 @@ static fr_status run_pair_iteration(fr_ctx *ctx, const fr_graph *g, int32_t *par
     const int grid = choose_grid(ctx, opt, tpb, 2, est);
     const bool vec = ((reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0);
     CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-    CK(launch_step(w, PH_ALL, grid, tpb, ctx->stream));
+    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr));
     char *h = ctx->h_stage + 2048;
     CK(cudaMemcpyAsync(h, ctx->pacc, sizeof(PairAcc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(h + 512, ctx->sides, 2 * sizeof(SideDev), cudaMemcpyDeviceToHost, ctx->stream));

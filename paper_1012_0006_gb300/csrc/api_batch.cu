@@ -174,6 +174,10 @@ extern "C" fr_status fr_maxflow(fr_ctx *ctx, fr_corridor *c, int64_t *flow_out) 
     Work w = make_work(ctx, 0, 0, 1, c->g.n, &opt);
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
+    if (ctx->max_clusters > 0) {
+        w.cluster_mode = 1;
+        CK(launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, ctx->stream));
+    }
     CK(launch_step(w, PH_FLOW, grid, tpb, ctx->stream));
     PairAcc A;
     Ctl C;
@@ -221,6 +225,7 @@ extern "C" fr_status fr_extract_cut(fr_ctx *ctx, fr_corridor *c, int32_t most_ba
     h[0] = mbv;
     CK(cudaMemcpyAsync(&ctx->pairs[0].mb, h, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     Work w = make_work(ctx, 0, 0, 1, c->g.n, &opt);
+    w.cluster_mode = ctx->max_clusters > 0 ? 1 : 0;
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
     CK(launch_step(w, PH_CUT | PH_EVAL | PH_COMMIT, grid, tpb, ctx->stream));
@@ -332,7 +337,7 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-        CK(launch_step(w, PH_ALL, pl.grid[r], pl.tpb, ctx->stream));
+        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr));
     }
     return FR_OK;
 }
@@ -340,7 +345,7 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
 // Same launches as enqueue_sweep, each bracketed by CUDA events (profiling mode).
 static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const BatchPlan &pl, const fr_options *opt) {
     const int np = pl.np, nr = pl.nr;
-    while ((int)ctx->pev.size() < 4 * nr) {
+    while ((int)ctx->pev.size() < 8 * nr) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         ctx->pev.push_back(e);
@@ -354,12 +359,10 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
-        CK(cudaEventRecord(ctx->pev[4 * r], ctx->stream));
+        CK(cudaEventRecord(ctx->pev[8 * r], ctx->stream));
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-        CK(cudaEventRecord(ctx->pev[4 * r + 1], ctx->stream));
-        CK(cudaEventRecord(ctx->pev[4 * r + 2], ctx->stream));
-        CK(launch_step(w, PH_ALL, pl.grid[r], pl.tpb, ctx->stream));
-        CK(cudaEventRecord(ctx->pev[4 * r + 3], ctx->stream));
+        CK(cudaEventRecord(ctx->pev[8 * r + 1], ctx->stream));
+        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, &ctx->pev[8 * r + 2]));
     }
     return FR_OK;
 }
@@ -397,20 +400,24 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
-        double sc = 0, stp = 0;
+        double sc = 0, stp = 0, clu = 0;
         for (int r = 0; r < pl.nr; ++r) {
-            float a = 0, b = 0;
-            CK(cudaEventElapsedTime(&a, ctx->pev[4 * r], ctx->pev[4 * r + 1]));
-            CK(cudaEventElapsedTime(&b, ctx->pev[4 * r + 2], ctx->pev[4 * r + 3]));
+            float a = 0, b1 = 0, c = 0, b2 = 0;
+            CK(cudaEventElapsedTime(&a, ctx->pev[8 * r], ctx->pev[8 * r + 1]));
+            CK(cudaEventElapsedTime(&b1, ctx->pev[8 * r + 2], ctx->pev[8 * r + 3]));
+            CK(cudaEventElapsedTime(&c, ctx->pev[8 * r + 4], ctx->pev[8 * r + 5]));
+            CK(cudaEventElapsedTime(&b2, ctx->pev[8 * r + 6], ctx->pev[8 * r + 7]));
             sc += a;
-            stp += b;
+            stp += b1 + b2;
+            clu += c;
         }
         ctx->prof.scan_ms = sc;
         ctx->prof.step_ms = stp;
-        ctx->last_launches = 3 + 2LL * pl.nr;
+        ctx->prof.cluster_ms = clu;
+        ctx->last_launches = 3 + (ctx->max_clusters > 0 ? 4LL : 2LL) * pl.nr;
         return FR_OK;
     }
-    ctx->prof.scan_ms = ctx->prof.step_ms = 0;
+    ctx->prof.scan_ms = ctx->prof.step_ms = ctx->prof.cluster_ms = 0;
     if (ctx->use_graphs) {
         for (auto &e : ctx->gcache)
             if (e.key == key) { exec = e.exec; break; }
@@ -452,7 +459,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
-    ctx->last_launches = 3 + 2LL * pl.nr;   // prep + colour + fill + (scan + step) per round
+    // prep + colour + fill + per round scan and step (two steps and the cluster kernel in cluster mode)
+    ctx->last_launches = 3 + (ctx->max_clusters > 0 ? 4LL : 2LL) * pl.nr;
     return FR_OK;
 }
 
@@ -534,10 +542,11 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
     for (int r = 0; r < pl.nr; ++r) flow_ns += C[r].timers[T_FLOW1] + C[r].timers[T_GR] + C[r].timers[T_FLOW2];
     {
         fr_profile_info &P = ctx->prof;
-        const double sc = P.scan_ms, stp = P.step_ms;
+        const double sc = P.scan_ms, stp = P.step_ms, clu = P.cluster_ms;
         memset(&P, 0, sizeof(P));
         P.scan_ms = sc;
         P.step_ms = stp;
+        P.cluster_ms = clu;
         P.nrounds = pl.nr;
         P.launches = (int32_t)ctx->last_launches;
         P.n = g->n;

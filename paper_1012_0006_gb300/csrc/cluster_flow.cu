@@ -1,0 +1,488 @@
+// Max flow of each pair inside one thread-block cluster, on distributed shared
+// memory (Sanders & Schulz, Section 4.1: the max-flow problem of the B-corridor
+// network; Section 4.1.1: residual reachability).
+//
+// The round's persistent kernel builds every pair's corridor network in HBM.
+// This kernel then gives each pair one cluster of C CTAs: the pair's vertices are
+// split into C contiguous ranges with about equal arc counts, and every CTA loads
+// its range -- labels, excess, s/t-arc flow, CSR offsets, packed head and reverse
+// arc references, residual capacities -- into its shared memory.  Push-relabel
+// (lock-free pulses), global relabels (pull passes over residual arcs), the return
+// of excess to s and the reachability sets then run on SMEM, with the cluster's
+// hardware barrier (~0.3 us) instead of a grid barrier (~3 us) and with DSMEM
+// latency instead of L2 latency.  Results go back to HBM for the cut phases.  A
+// pair whose network does not fit is left to the grid-wide path (ctl->fallback).
+#include <cooperative_groups.h>
+
+#include <climits>
+
+#include "fr_internal.cuh"
+#include "round_kernel.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fr {
+
+#define FULL 0xffffffffu
+
+constexpr int kClusterMax = 16;
+constexpr int kHdrBytes = 1024;
+
+struct ClusterHdr {
+    int klo[kClusterMax + 1];   // member ranges of the CTAs (identical in every CTA)
+    int cnt[3];                 // rotating counters (CTA 0's copy is the cluster's)
+    int err;                    // cluster error (CTA 0's copy)
+    int nvcap, nacap;           // common capacities (identical in every CTA)
+    int nv, na;                 // this CTA's vertices and arcs
+    int counts[kClusterMax];    // scratch for the member scan (CTA 0's copy)
+    long long flow;
+};
+
+__device__ __forceinline__ int cpack(int r, int i) { return (r << 24) | i; }
+__device__ __forceinline__ int crank(int p) { return (int)((unsigned)p >> 24); }
+__device__ __forceinline__ int cidx(int p) { return p & 0xFFFFFF; }
+
+template <int TPB>
+struct ClusterFlow {
+    const Work &w;
+    cg::cluster_group cl;
+    const int rank, C;
+    ClusterHdr *hdr;
+    ClusterHdr *hdr0;          // CTA 0's header
+    // local arrays
+    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *href, *rref, *res;
+    unsigned char *bord;
+    int rot;                   // rotating counter index (identical in every CTA)
+
+    // element i of this CTA's array `a`, in the shared memory of CTA r (DSMEM)
+    __device__ __forceinline__ int *at(int *a, int packed) const {
+        return cl.map_shared_rank(a + cidx(packed), crank(packed));
+    }
+
+    __device__ ClusterFlow(const Work &w_, char *smem)
+        : w(w_), cl(cg::this_cluster()), rank((int)cg::this_cluster().block_rank()),
+          C((int)cg::this_cluster().num_blocks()) {
+        hdr = reinterpret_cast<ClusterHdr *>(smem);
+        hdr0 = cl.map_shared_rank(hdr, 0);
+        rot = 0;
+    }
+
+    __device__ void sync() { cl.sync(); }
+
+    // cluster-wide sum of x (one value per thread); every thread gets the total
+    __device__ int cluster_sum(int x) {
+        __shared__ int s_part;
+        __syncthreads();
+        if (threadIdx.x == 0) s_part = 0;
+        __syncthreads();
+        if (x) atomicAdd(&s_part, x);
+        __syncthreads();
+        int *c = &hdr0->cnt[rot];
+        if (threadIdx.x == 0 && s_part) atomicAdd(c, s_part);
+        if (rank == 0 && threadIdx.x == 0) hdr->cnt[(rot + 1) % 3] = 0;
+        sync();
+        const int tot = *(volatile int *)c;
+        rot = (rot + 1) % 3;
+        return tot;
+    }
+
+    __device__ void carve(char *smem, int nvcap, int nacap) {
+        char *p = smem + kHdrBytes;
+        auto take = [&](size_t bytes) {
+            char *r = p;
+            p += (bytes + 15) / 16 * 16;
+            return r;
+        };
+        lab = reinterpret_cast<int *>(take(4ull * nvcap));
+        ex = reinterpret_cast<int *>(take(4ull * nvcap));
+        fx = reinterpret_cast<int *>(take(4ull * nvcap));
+        cofs = reinterpret_cast<int *>(take(4ull * (nvcap + 1)));
+        gidx = reinterpret_cast<int *>(take(4ull * nvcap));
+        rfl = reinterpret_cast<int *>(take(4ull * nvcap));
+        bord = reinterpret_cast<unsigned char *>(take(nvcap));
+        href = reinterpret_cast<int *>(take(4ull * nacap));
+        rref = reinterpret_cast<int *>(take(4ull * nacap));
+        res = reinterpret_cast<int *>(take(4ull * nacap));
+    }
+
+    static __host__ __device__ size_t bytes_for(int nvcap, int nacap) {
+        auto a = [](size_t b) { return (b + 15) / 16 * 16; };
+        return kHdrBytes + 6 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + 3 * a(4ull * nacap);
+    }
+
+    __device__ int owner(int k) const {   // CTA whose range holds member k
+        int r = 0;
+        while (r + 1 < C && hdr->klo[r + 1] <= k) ++r;
+        return r;
+    }
+
+    // ------------------------------------------------------------ one pair --
+    // Returns false when the pair does not fit (left to the grid-wide path).
+    __device__ bool solve(int p, char *smem, size_t smem_bytes) {
+        const int nu = __ldcg(&w.ctl->nu);
+        const int V = __ldcg(&w.pacc[p].nc), A = __ldcg(&w.pacc[p].m);
+        if (V == 0) return true;
+        // members of pair p in local-id order: pmem = cid, their arc prefix = outoff, plocal = color
+        int pbase = 0;
+        for (int q = 0; q < p; ++q) pbase += __ldcg(&w.pacc[q].nc);
+        int *pmem = w.cid + pbase, *pacs = w.outoff + pbase, *plocal = w.color;
+        {
+            const long long per = (nu + C - 1) / C;
+            const long long c0 = per * rank, c1 = min((long long)nu, c0 + per);
+            int mine = 0;
+            for (long long i = c0 + threadIdx.x; i < c1; i += TPB) mine += (w.sid[i] >> 1) == p;
+            __shared__ int s_tot;
+            if (threadIdx.x == 0) s_tot = 0;
+            __syncthreads();
+            if (mine) atomicAdd(&s_tot, mine);
+            __syncthreads();
+            if (threadIdx.x == 0) hdr0->counts[rank] = s_tot;
+            sync();
+            int before = 0;
+            for (int r = 0; r < rank; ++r) before += *(volatile int *)&hdr0->counts[r];
+            sync();   // counts read before they are reused
+            int run = before;
+            for (long long x0 = c0; x0 < c1; x0 += TPB) {
+                const long long i = x0 + threadIdx.x;
+                const int f = i < c1 && (w.sid[i] >> 1) == p;
+                int tile;
+                const int ex0 = block_exclusive_scan<TPB>(f, &tile);
+                if (f) {
+                    pmem[run + ex0] = (int)i;
+                    plocal[i] = run + ex0;
+                }
+                run += tile;
+            }
+        }
+        __threadfence();
+        sync();
+        // arc prefix over members (each CTA a slice of the member list)
+        {
+            const int per = (V + C - 1) / C;
+            const int k0 = per * rank, k1 = min(V, k0 + per);
+            int mine = 0;
+            for (int k = k0 + threadIdx.x; k < k1; k += TPB) {
+                const int i = __ldcg(&pmem[k]);
+                mine += w.off[i + 1] - w.off[i];
+            }
+            __shared__ int s_tot2;
+            if (threadIdx.x == 0) s_tot2 = 0;
+            __syncthreads();
+            if (mine) atomicAdd(&s_tot2, mine);
+            __syncthreads();
+            if (threadIdx.x == 0) hdr0->counts[rank] = s_tot2;
+            sync();
+            int before = 0;
+            for (int r = 0; r < rank; ++r) before += *(volatile int *)&hdr0->counts[r];
+            sync();
+            int run = before;
+            for (int x0 = k0; x0 < k1; x0 += TPB) {
+                const int k = x0 + threadIdx.x;
+                int d = 0;
+                if (k < k1) {
+                    const int i = __ldcg(&pmem[k]);
+                    d = w.off[i + 1] - w.off[i];
+                }
+                int tile;
+                const int e0 = block_exclusive_scan<TPB>(d, &tile);
+                if (k < k1) pacs[k] = run + e0;
+                run += tile;
+            }
+        }
+        __threadfence();
+        sync();
+        // split members into C ranges of about A / C arcs each (same in every CTA)
+        if (threadIdx.x == 0) {
+            hdr->klo[0] = 0;
+            for (int r = 1; r < C; ++r) {
+                const long long target = (long long)A * r / C;
+                int lo = hdr->klo[r - 1], hi = V;   // first k with pacs[k] >= target
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldcg(&pacs[mid]) < target) lo = mid + 1; else hi = mid;
+                }
+                hdr->klo[r] = lo;
+            }
+            hdr->klo[C] = V;
+            int nvcap = 0, nacap = 0;
+            for (int r = 0; r < C; ++r) {
+                const int kv = hdr->klo[r + 1] - hdr->klo[r];
+                const int a0 = hdr->klo[r] < V ? __ldcg(&pacs[hdr->klo[r]]) : A;
+                const int a1 = hdr->klo[r + 1] < V ? __ldcg(&pacs[hdr->klo[r + 1]]) : A;
+                nvcap = max(nvcap, kv);
+                nacap = max(nacap, a1 - a0);
+            }
+            hdr->nvcap = nvcap;
+            hdr->nacap = nacap;
+        }
+        __syncthreads();
+        const int nvcap = hdr->nvcap, nacap = hdr->nacap;
+        if (bytes_for(nvcap, nacap) > smem_bytes) return false;   // same decision in every CTA
+        carve(smem, nvcap, nacap);
+        const int klo = hdr->klo[rank], khi = hdr->klo[rank + 1];
+        const int nv = khi - klo;
+        const int abase = klo < V ? __ldcg(&pacs[klo]) : A;
+        // load this CTA's vertices and arcs
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+            const int i = __ldcg(&pmem[klo + lv]);
+            gidx[lv] = i;
+            ex[lv] = (int)__ldcg(&w.ex[i]);
+            fx[lv] = __ldcg(&w.fx[i]);
+            bord[lv] = w.border[i];
+            const int a0 = __ldcg(&pacs[klo + lv]) - abase;
+            cofs[lv] = a0;
+            const int j0 = w.off[i], j1 = w.off[i + 1];
+            for (int j = j0; j < j1; ++j) {
+                const int la = a0 + (j - j0);
+                const int h = w.head[j];
+                const int kh = __ldcg(&plocal[h]);
+                const int rh = owner(kh);
+                href[la] = cpack(rh, kh - hdr->klo[rh]);
+                const int rv = w.rev[j];
+                const int ar = __ldcg(&pacs[kh]) - (hdr->klo[rh] < V ? __ldcg(&pacs[hdr->klo[rh]]) : A) + (rv - w.off[h]);
+                rref[la] = cpack(rh, ar);
+                res[la] = __ldcg(&w.res[j]);
+            }
+        }
+        if (threadIdx.x == 0) {
+            hdr->nv = nv;
+            const int a1 = khi < V ? __ldcg(&pacs[khi]) : A;
+            cofs[nv] = a1 - abase;
+            if (rank == 0) { hdr->cnt[0] = hdr->cnt[1] = hdr->cnt[2] = 0; hdr->err = 0; }
+        }
+        rot = 0;
+        sync();
+        const int hmax = V + 2;
+        if (!phase(0, nv, hmax) || !phase(1, nv, hmax)) {
+            // cap reached: report, leave the pair's arrays as they were
+            if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_ITER, 300);
+            sync();
+            return true;
+        }
+        reach(nv);
+        // write back: residuals, s/t flows, zero excess, reachability and plain sides
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+            const int i = gidx[lv];
+            const int j0 = w.off[i];
+            const int a0 = cofs[lv], a1 = cofs[lv + 1];
+            for (int a = a0; a < a1; ++a) w.res[j0 + (a - a0)] = res[a];
+            w.fx[i] = fx[lv];
+            w.ex[i] = ex[lv];
+            w.rflag[i] = rfl[lv];
+            w.side_out[i] = (rfl[lv] & 1) ? 0 : 1;
+            if (ex[lv] != 0) fail(w.ctl, E_INTERNAL, 301);
+            if (rfl[lv] == 3) fail(w.ctl, E_INTERNAL, 302);
+        }
+        sync();
+        return true;
+    }
+
+    // Exact labels by pull passes: an unlabelled vertex with a residual arc into
+    // level d gets d + 1.  phase 0: distance to t; phase 1: distance to s.
+    __device__ void relabel(int ph, int nv, int hmax) {
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+            const bool src = ph ? (bord[lv] == 1 && fx[lv] > 0) : (bord[lv] == 2);
+            lab[lv] = src ? 1 : hmax;
+        }
+        sync();
+        for (int d = 1; d < hmax; ++d) {
+            int changed = 0;
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                if (lab[lv] != hmax) continue;
+                const int a1 = cofs[lv + 1];
+                for (int a = cofs[lv]; a < a1; ++a) {
+                    if (res[a] <= 0) continue;
+                    const int h = href[a];
+                    if (*(volatile int *)at(lab, h) == d) {
+                        lab[lv] = d + 1;
+                        changed = 1;
+                        break;
+                    }
+                }
+            }
+            if (cluster_sum(changed) == 0) break;
+        }
+    }
+
+    // Lock-free pulses (push to the lowest residual neighbour or relabel) until no
+    // vertex with excess has a label below hmax; phase 1 returns excess to s.
+    __device__ bool phase(int ph, int nv, int hmax) {
+        relabel(ph, nv, hmax);
+        long long pulses = 0;
+        int since = 0;
+        for (;;) {
+            int act = 0;
+            for (int pass = 0; pass < w.passes; ++pass) {
+                const bool last = pass + 1 == w.passes;
+                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                    int e = *(volatile int *)&ex[lv];
+                    if (e <= 0) continue;
+                    int h = lab[lv];
+                    if (h >= hmax) continue;
+                    const int a0 = cofs[lv], a1 = cofs[lv + 1];
+                    const unsigned char bd = bord[lv];
+                    for (int it = 0; it < w.inner; ++it) {
+                        int hmin = INT_MAX, best = -1;
+                        for (int a = a0; a < a1; ++a) {
+                            if (*(volatile int *)&res[a] <= 0) continue;
+                            const int hh = href[a];
+                            const int l = *(volatile int *)at(lab, hh);
+                            if (l < hmin) { hmin = l; best = a; }
+                        }
+                        if (ph ? (bd == 1 && fx[lv] > 0) : (bd == 2)) { hmin = 0; best = -2; }
+                        if (best == -1) { h = hmax; lab[lv] = h; break; }
+                        if (h > hmin) {
+                            int d;
+                            if (best == -2) {
+                                if (!ph) { d = e; fx[lv] += d; }
+                                else { d = e < fx[lv] ? e : fx[lv]; fx[lv] -= d; }
+                            } else {
+                                const int r = *(volatile int *)&res[best];
+                                d = e < r ? e : r;
+                                const int hh = href[best], rv = rref[best];
+                                atomicSub(&res[best], d);
+                                atomicAdd(at(res, rv), d);
+                                atomicAdd(at(ex, hh), d);
+                                if (last) ++act;
+                            }
+                            atomicSub(&ex[lv], d);
+                            e -= d;
+                            if (e == 0) break;
+                        } else {
+                            h = hmin + 1;
+                            if (h >= hmax) h = hmax;
+                            lab[lv] = h;
+                            if (h >= hmax) break;
+                        }
+                    }
+                    if (last && e > 0 && h < hmax) ++act;
+                }
+            }
+            ++pulses;
+            ++since;
+            const int a = cluster_sum(act);
+            if (pulses > w.pulse_cap) return false;
+            if (a == 0) {
+                // pushes of earlier passes may land after their target was scanned
+                int left = 0;
+                for (int lv = threadIdx.x; lv < nv; lv += TPB)
+                    left += ex[lv] > 0 && lab[lv] < hmax;
+                if (cluster_sum(left) == 0) break;
+            }
+            if (since >= w.gr_interval) {
+                relabel(ph, nv, hmax);
+                since = 0;
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->pulses, pulses);
+        return true;
+    }
+
+    // bit 1: reachable from s; bit 2: reaches t (monotone pull passes)
+    __device__ void reach(int nv) {
+        for (int lv = threadIdx.x; lv < nv; lv += TPB)
+            rfl[lv] = (bord[lv] == 1 ? 1 : 0) | (bord[lv] == 2 ? 2 : 0);
+        sync();
+        for (int it = 0; it < 1 << 30; ++it) {
+            int changed = 0;
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                const int f = rfl[lv];
+                if (f == 3) continue;
+                int add = 0;
+                const int a1 = cofs[lv + 1];
+                for (int a = cofs[lv]; a < a1 && (f | add) != 3; ++a) {
+                    const int hh = href[a], rv = rref[a];
+                    const int fh = *(volatile int *)at(rfl, hh);
+                    if (!((f | add) & 1) && (fh & 1) && *(volatile int *)at(res, rv) > 0) add |= 1;
+                    if (!((f | add) & 2) && (fh & 2) && res[a] > 0) add |= 2;
+                }
+                if (add) {
+                    rfl[lv] = f | add;
+                    changed = 1;
+                }
+            }
+            if (cluster_sum(changed) == 0) break;
+        }
+    }
+};
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB, 1) cluster_flow_kernel(Work w, int nclusters, size_t smem_bytes) {
+    extern __shared__ __align__(16) char csmem[];
+    if (w.prev_err && __ldcg(w.prev_err)) return;
+    if (__ldcg(&w.ctl->error)) return;
+    ClusterFlow<TPB> K(w, csmem);
+    const int cid = blockIdx.x / K.C;
+    for (int p = cid; p < w.npairs; p += nclusters) {
+        const bool done = K.solve(p, csmem, smem_bytes);
+        if (!done && K.rank == 0 && threadIdx.x == 0) {
+            atomicAdd(&w.ctl->fallback, 1);
+            w.pacc[p].status = 1;   // solved by the grid-wide path
+        }
+        K.sync();
+    }
+}
+
+// Dynamic shared memory of the cluster kernel: the opt-in maximum per block minus
+// its static shared memory (set once per process).
+static int g_cluster_dyn_smem = -1;
+
+static cudaError_t cluster_setup() {
+    if (g_cluster_dyn_smem >= 0) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, cluster_flow_kernel<512>);
+    if (e != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes - 64;
+    e = cudaFuncSetAttribute(cluster_flow_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(cluster_flow_kernel<512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    g_cluster_dyn_smem = dyn;
+    return cudaSuccess;
+}
+
+cudaError_t launch_cluster_flow(const Work &w, int cluster, int max_clusters, cudaStream_t st) {
+    const int tpb = 512;
+    cudaError_t e0 = cluster_setup();
+    if (e0 != cudaSuccess) return e0;
+    const size_t smem = (size_t)g_cluster_dyn_smem;
+    int nclusters = w.npairs < max_clusters ? w.npairs : max_clusters;
+    if (nclusters < 1) nclusters = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nclusters * cluster);
+    cfg.blockDim = dim3(tpb);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cluster_flow_kernel<512>, w, nclusters, smem);
+}
+
+cudaError_t cluster_flow_capacity(int cluster, int *max_clusters) {
+    cudaError_t e = cluster_setup();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * 64);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = (size_t)g_cluster_dyn_smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_clusters, cluster_flow_kernel<512>, &cfg);
+}
+
+}  // namespace fr

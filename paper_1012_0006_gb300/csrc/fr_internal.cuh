@@ -115,6 +115,7 @@ struct Ctl {
     long long pr_arcs;        // arcs scanned by push-relabel pulses
     long long pushes;         // pushes
     long long barriers;       // grid barriers passed (CTA 0)
+    int fallback, pad3;       // pairs the cluster kernel left to the grid-wide flow
 };
 
 // Everything a kernel needs, passed by value.
@@ -149,7 +150,7 @@ struct Work {
     int *sw_j;                   // [npairs*reps]
     // options
     int reps, gr_interval, inner, any_mb;
-    int passes, pad_p;           // lock-free pulse passes per grid barrier
+    int passes, cluster_mode;    // lock-free pulse passes per barrier; 1: the cluster kernel ran the flow
     unsigned long long seed;
     long long pulse_cap;
 };

@@ -827,8 +827,12 @@ struct StepKernel {
     __device__ bool maxflow() {
         Ctl *ctl = w.ctl;
         const int nu = __ldcg(&ctl->nu), hmax = __ldcg(&ctl->hmax);
-        if (!flow_phase(0, hmax, nu)) return false;
-        if (!flow_phase(1, hmax, nu)) return false;
+        // pairs already solved in their clusters have no excess left, so the grid-wide
+        // phases only move the excess of the pairs that did not fit a cluster
+        if (!w.cluster_mode || __ldcg(&ctl->fallback) > 0) {
+            if (!flow_phase(0, hmax, nu)) return false;
+            if (!flow_phase(1, hmax, nu)) return false;
+        }
         // every excess must have returned to s: the result is a flow
         unsigned long long t0 = globaltimer();
         int *cnt = &ctl->act[pl % 3];
@@ -852,6 +856,7 @@ struct StepKernel {
         Ctl *ctl = w.ctl;
         unsigned long long t0 = globaltimer();
         const int nu = __ldcg(&ctl->nu);
+        if (w.cluster_mode && __ldcg(&ctl->fallback) == 0) return true;   // the clusters wrote the sets
         {
             int *cnt = &ctl->fcnt[(fl + 1) % 3];
             int *q = ((fl + 1) & 1) ? w.fq1 : w.fq0;

@@ -11,6 +11,9 @@ cudaError_t launch_scan(const Work &w, int g, int n, bool vec, cudaStream_t st);
 cudaError_t launch_step(const Work &w, uint32_t phases, int grid, int tpb, cudaStream_t st);
 cudaError_t step_max_grid(int tpb, int nsides, int *max_blocks, int *sms);
 size_t step_smem_bytes(int nsides);
+// cluster_flow.cu: per-pair max flow and reachability on distributed shared memory
+cudaError_t launch_cluster_flow(const Work &w, int cluster, int max_clusters, cudaStream_t st);
+cudaError_t cluster_flow_capacity(int cluster, int *max_clusters);
 
 // prep_kernel.cu
 struct PrepOut {

@@ -263,7 +263,7 @@ static fr_status run_step(fr_server *S, std::vector<Req *> &act) {
                std::max<long long>(1, act[i]->Ubase / std::max(1, act[i]->k));
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2 * P, std::max<long long>(1, est));
-    if (launch_step(w, PH_ALL, grid, tpb, st) != cudaSuccess) return FR_ERR_CUDA;
+    if (launch_round(ctx, w, grid, tpb, st, nullptr) != cudaSuccess) return FR_ERR_CUDA;
     std::vector<PairAcc> A(P);
     Ctl C;
     if (cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * P, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -64,7 +64,7 @@ class BatchResult(ctypes.Structure):
 
 class ProfileInfo(ctypes.Structure):
     _fields_ = [("nrounds", ctypes.c_int32), ("launches", ctypes.c_int32), ("scan_ms", ctypes.c_double),
-                ("step_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 12), ("n", ctypes.c_int64),
+                ("step_ms", ctypes.c_double), ("cluster_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 12), ("n", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("bfs_visited", ctypes.c_int64), ("bfs_arcs", ctypes.c_int64),
                 ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
                 ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
