@@ -76,6 +76,8 @@ typedef struct fr_options {
     int32_t gr_interval;   /* pulses between global relabels; 0 = tuned default */
     int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
     int32_t pulse_passes;  /* lock-free pulse passes between grid barriers; 0 = default */
+    int32_t flow_sched;    /* per-pair cluster max flow: 0 lock-free pulses, 1 level-ordered waves */
+    int32_t pad0;
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b). */

@@ -306,6 +306,7 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.gr_interval = opt && opt->gr_interval > 0 ? opt->gr_interval : ctx->tune_gr;
     w.inner = opt && opt->inner_ops > 0 ? opt->inner_ops : ctx->tune_inner;
     w.passes = opt && opt->pulse_passes > 0 ? opt->pulse_passes : ctx->tune_passes;
+    w.flow_sched = opt ? opt->flow_sched : 0;
     w.any_mb = opt && opt->mb ? 1 : 0;
     w.seed = opt ? opt->seed : 0;
     w.pulse_cap = opt && opt->pulse_cap > 0 ? opt->pulse_cap : (1LL << 20);
@@ -372,12 +373,17 @@ extern "C" fr_status fr_create(fr_ctx **out, int32_t device, size_t arena_bytes,
     ctx->sms = sms;
     ctx->max_coop = std::max(maxb, 1) * 4;
     {
-        int mc = 0;
+        int mc = 0, mc16 = 0;
         if (cluster_flow_capacity(ctx->cluster_size, &mc) != cudaSuccess) {
             cudaGetLastError();
             mc = 0;
         }
+        if (cluster_flow_capacity(16, &mc16) != cudaSuccess) {
+            cudaGetLastError();
+            mc16 = 0;
+        }
         ctx->max_clusters = mc;
+        ctx->max_clusters16 = mc16;
     }
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
@@ -520,7 +526,8 @@ fr_status reset_idle(fr_ctx *ctx) {
     return FR_OK;
 }
 
-cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev) {
+cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev,
+                         long long est_pair_vertices, double avg_degree) {
     // ev (optional): 6 events bracketing step 1, the cluster kernel and step 2
     if (ctx->max_clusters <= 0) {
         w.cluster_mode = 0;
@@ -538,7 +545,11 @@ cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t s
     if (ev) cudaEventRecord(ev[1], st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
-    e = launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, st);
+    // shared memory a pair needs (~25 B per vertex, 12 B per arc), with room for an uneven split
+    const double need = 1.4 * (double)est_pair_vertices * (25.0 + 12.0 * avg_degree);
+    const bool big = ctx->max_clusters16 > 0 && need > 8.0 * 200e3;
+    e = big ? launch_cluster_flow(w, 16, ctx->max_clusters16, st)
+            : launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, st);
     if (ev) cudaEventRecord(ev[3], st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
@@ -556,17 +567,20 @@ struct IterOut {
 };
 
 static fr_status run_pair_iteration(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, int32_t a, int32_t b,
-                                    long long Ubase, long long Lmax, const fr_options *opt, IterOut *o) {
+                                    long long Ubase, long long Lmax, long long W, const fr_options *opt,
+                                    IterOut *o) {
     const int mb = opt && opt->mb ? 1 : 0;
     fr_status st = setup_single(ctx, g, part, k, a, b, Ubase, Lmax, mb);
     if (st != FR_OK) return st;
     Work w = make_work(ctx, 0, 0, 1, g->n, opt);
     const int tpb = choose_tpb(ctx, opt);
-    const long long est = std::max<long long>(1, 2 * Ubase);
+    // corridor estimate: two sides of about (Ubase - W/k) weight each
+    const double avgc = std::max(1.0, (double)W / g->n);
+    const long long est = std::max<long long>(1, (long long)(2.0 * std::max(0LL, Ubase - W / k) / avgc));
     const int grid = choose_grid(ctx, opt, tpb, 2, est);
     const bool vec = ((reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0);
     CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr));
+    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, est, (double)g->nnz / g->n));
     char *h = ctx->h_stage + 2048;
     CK(cudaMemcpyAsync(h, ctx->pacc, sizeof(PairAcc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(h + 512, ctx->sides, 2 * sizeof(SideDev), cudaMemcpyDeviceToHost, ctx->stream));
@@ -629,7 +643,7 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
     int levels = 0, sccr = 0;
     while (iters < max_iters) {
         ++iters;
-        st = run_pair_iteration(ctx, g, part, k, a, b, host_budget_base(W, k, eps, al), Lmax, &opt, &o);
+        st = run_pair_iteration(ctx, g, part, k, a, b, host_budget_base(W, k, eps, al), Lmax, W, &opt, &o);
         if (st != FR_OK) break;
         if (cut_before < 0) { cut_before = o.oldcut; wA0 = o.cA; wB0 = o.cB; }
         cur_cut = o.oldcut; cur_A = o.cA; cur_B = o.cB;

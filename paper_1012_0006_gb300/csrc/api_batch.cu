@@ -176,7 +176,11 @@ extern "C" fr_status fr_maxflow(fr_ctx *ctx, fr_corridor *c, int64_t *flow_out) 
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
     if (ctx->max_clusters > 0) {
         w.cluster_mode = 1;
-        CK(launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, ctx->stream));
+        const double need = 1.4 * (double)c->nc * (25.0 + 12.0 * (double)c->m / std::max(1, c->nc));
+        if (ctx->max_clusters16 > 0 && need > 8.0 * 200e3)
+            CK(launch_cluster_flow(w, 16, ctx->max_clusters16, ctx->stream));
+        else
+            CK(launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, ctx->stream));
     }
     CK(launch_step(w, PH_FLOW, grid, tpb, ctx->stream));
     PairAcc A;
@@ -321,6 +325,8 @@ struct BatchPlan {
     std::vector<int> grid;     // persistent-kernel CTAs per round
     int tpb, k;
     long long Ubase, Lmax, totcut;
+    std::vector<long long> est_max;   // estimated corridor vertices of each round's largest pair
+    double avg_degree = 12.0;
 };
 
 // Enqueues a whole sweep: pair descriptors, cleared per-round state, then per
@@ -337,7 +343,7 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr));
+        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr, pl.est_max[r], pl.avg_degree));
     }
     return FR_OK;
 }
@@ -362,7 +368,8 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
         CK(cudaEventRecord(ctx->pev[8 * r], ctx->stream));
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
         CK(cudaEventRecord(ctx->pev[8 * r + 1], ctx->stream));
-        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, &ctx->pev[8 * r + 2]));
+        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, &ctx->pev[8 * r + 2], pl.est_max[r],
+                        pl.avg_degree));
     }
     return FR_OK;
 }
@@ -389,7 +396,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   pl.np, pl.nr, pl.tpb, pl.Ubase, opt->mb, opt->mb_reps, (long long)opt->seed,
                                   opt->gr_interval, opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
-                                  opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem};
+                                  opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
+                                  opt->flow_sched};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
@@ -491,10 +499,14 @@ static fr_status plan_sweep(fr_ctx *ctx, const fr_graph *g, const int32_t *part,
     CK(cudaStreamSynchronize(ctx->stream));
     const double avgc = std::max(1.0, (double)po.W / (double)g->n);
     pl->grid.assign(pl->nr, 1);
+    pl->est_max.assign(pl->nr, 0);
+    pl->avg_degree = (double)g->nnz / g->n;
     for (int r = 0; r < pl->nr; ++r) {
         long long est = 0;
         for (int i = pl->off[r]; i < pl->off[r + 1]; ++i) {
-            est += std::max(0LL, pl->Ubase - bw[pb[i]]) + std::max(0LL, pl->Ubase - bw[pa[i]]);
+            const long long e1 = std::max(0LL, pl->Ubase - bw[pb[i]]) + std::max(0LL, pl->Ubase - bw[pa[i]]);
+            est += e1;
+            pl->est_max[r] = std::max(pl->est_max[r], (long long)(e1 / avgc));
         }
         pl->grid[r] = choose_grid(ctx, opt, pl->tpb, 2 * (pl->off[r + 1] - pl->off[r]),
                                   std::max<long long>(1, (long long)(est / avgc)));

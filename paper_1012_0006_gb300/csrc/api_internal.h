@@ -29,7 +29,7 @@ struct fr_ctx {
     // launch shape (fr_autotune writes these)
     int tune_tpb = 512, tune_grid = 0, tune_gr = 16, tune_inner = 2, tune_passes = 2;
     // per-pair max flow in thread-block clusters (0 clusters: grid-wide path only)
-    int cluster_size = 8, max_clusters = 0;
+    int cluster_size = 8, max_clusters = 0, max_clusters16 = 0;
     // graph-size workspace
     void *base_mem = nullptr;
     size_t base_bytes = 0;
@@ -117,6 +117,8 @@ fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k,
 fr_status reset_idle(fr_ctx *ctx);
 // Launches of one flow iteration over the pairs of w after the boundary scan:
 // step (BFS, ids, build) -> cluster max flow -> step (rest), or one step kernel.
-cudaError_t launch_round(fr_ctx *ctx, fr::Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev);
+// est_pair_vertices: estimated corridor size of the largest pair (chooses 8- or 16-CTA clusters).
+cudaError_t launch_round(fr_ctx *ctx, fr::Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev,
+                         long long est_pair_vertices = 0, double avg_degree = 12.0);
 void release_corridor(fr_ctx *ctx);
 void destroy_graph_cache(fr_ctx *ctx);

@@ -7,8 +7,8 @@
 // split into C contiguous ranges with about equal arc counts, and every CTA loads
 // its range -- labels, excess, s/t-arc flow, CSR offsets, packed head and reverse
 // arc references, residual capacities -- into its shared memory.  Push-relabel
-// (lock-free pulses), global relabels (pull passes over residual arcs), the return
-// of excess to s and the reachability sets then run on SMEM, with the cluster's
+// in waves (exact labels by pull passes over residual arcs, then the levels top
+// down), the return of excess to s and the reachability sets then run on SMEM, with the cluster's
 // hardware barrier (~0.3 us) instead of a grid barrier (~3 us) and with DSMEM
 // latency instead of L2 latency.  Results go back to HBM for the cut phases.  A
 // pair whose network does not fit is left to the grid-wide path (ctl->fallback).
@@ -54,10 +54,34 @@ struct ClusterFlow {
     unsigned char *bord;
     int rot;                   // rotating counter index (identical in every CTA)
 
-    // element i of this CTA's array `a`, in the shared memory of CTA r (DSMEM)
+    // element i of this CTA's array `a`, in the shared memory of CTA r: a plain
+    // shared-memory address when r is this CTA, a DSMEM address otherwise
     __device__ __forceinline__ int *at(int *a, int packed) const {
-        return cl.map_shared_rank(a + cidx(packed), crank(packed));
+        const int r = crank(packed);
+        return r == rank ? a + cidx(packed) : cl.map_shared_rank(a + cidx(packed), r);
     }
+
+    static constexpr int U = 8;   // arcs whose loads are issued together
+
+    // Lowest label over the residual arcs [a0, a1) (res > 0), and the arc holding it.
+    __device__ __forceinline__ void lowest(int a0, int a1, int &hmin, int &best) const {
+        hmin = INT_MAX;
+        best = -1;
+        for (int a = a0; a < a1; a += U) {
+            int r[U], hr[U], l[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                r[u] = a + u < a1 ? *(volatile int *)&res[a + u] : 0;
+                hr[u] = a + u < a1 ? href[a + u] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? *(volatile int *)at(lab, hr[u]) : INT_MAX;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (l[u] < hmin) { hmin = l[u]; best = a + u; }
+        }
+    }
+
 
     __device__ ClusterFlow(const Work &w_, char *smem)
         : w(w_), cl(cg::this_cluster()), rank((int)cg::this_cluster().block_rank()),
@@ -118,7 +142,16 @@ struct ClusterFlow {
 
     // ------------------------------------------------------------ one pair --
     // Returns false when the pair does not fit (left to the grid-wide path).
+    // adds the time since t to timer slot idx (one thread per cluster; sums over clusters)
+    __device__ bool mark(unsigned long long &t, int idx) {
+        const unsigned long long now = globaltimer();
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->timers[idx], (long long)(now - t));
+        t = now;
+        return true;
+    }
+
     __device__ bool solve(int p, char *smem, size_t smem_bytes) {
+        unsigned long long t_in = globaltimer();
         const int nu = __ldcg(&w.ctl->nu);
         const int V = __ldcg(&w.pacc[p].nc), A = __ldcg(&w.pacc[p].m);
         if (V == 0) return true;
@@ -253,13 +286,19 @@ struct ClusterFlow {
         rot = 0;
         sync();
         const int hmax = V + 2;
-        if (!phase(0, nv, hmax) || !phase(1, nv, hmax)) {
+        unsigned long long t1 = globaltimer();
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->timers[T_BUILD], (long long)(t1 - t_in));
+        const bool ok = w.flow_sched == 1 ? (phase_wave(0, nv, hmax) && (mark(t1, T_FLOW1), phase_wave(1, nv, hmax)))
+                                          : (phase_pulse(0, nv, hmax) && (mark(t1, T_FLOW1), phase_pulse(1, nv, hmax)));
+        mark(t1, T_FLOW2);
+        if (!ok) {
             // cap reached: report, leave the pair's arrays as they were
             if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_ITER, 300);
             sync();
             return true;
         }
         reach(nv);
+        mark(t1, T_REACH);
         // write back: residuals, s/t flows, zero excess, reachability and plain sides
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const int i = gidx[lv];
@@ -279,21 +318,30 @@ struct ClusterFlow {
 
     // Exact labels by pull passes: an unlabelled vertex with a residual arc into
     // level d gets d + 1.  phase 0: distance to t; phase 1: distance to s.
-    __device__ void relabel(int ph, int nv, int hmax) {
+    // Returns the highest label below hmax.
+    __device__ int relabel(int ph, int nv, int hmax) {
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const bool src = ph ? (bord[lv] == 1 && fx[lv] > 0) : (bord[lv] == 2);
             lab[lv] = src ? 1 : hmax;
         }
         sync();
+        int top = 1;
         for (int d = 1; d < hmax; ++d) {
             int changed = 0;
             for (int lv = threadIdx.x; lv < nv; lv += TPB) {
                 if (lab[lv] != hmax) continue;
                 const int a1 = cofs[lv + 1];
-                for (int a = cofs[lv]; a < a1; ++a) {
-                    if (res[a] <= 0) continue;
-                    const int h = href[a];
-                    if (*(volatile int *)at(lab, h) == d) {
+                for (int a = cofs[lv]; a < a1; a += U) {
+                    int r[U], hr[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        r[u] = a + u < a1 ? res[a + u] : 0;
+                        hr[u] = a + u < a1 ? href[a + u] : 0;
+                    }
+                    bool hit = false;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) hit |= r[u] > 0 && *(volatile int *)at(lab, hr[u]) == d;
+                    if (hit) {
                         lab[lv] = d + 1;
                         changed = 1;
                         break;
@@ -301,14 +349,75 @@ struct ClusterFlow {
                 }
             }
             if (cluster_sum(changed) == 0) break;
+            top = d + 1;
         }
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->gr_arcs, top);   // levels, summed
+        return top;
+    }
+
+    // Push-relabel in waves: exact labels, then the levels from the top down, each
+    // level pushing only along admissible arcs into the level below (level 1 into
+    // the sink), one cluster barrier per level; repeat until no vertex with excess
+    // can reach the sink.  Within a level step a vertex is the only writer of its
+    // own excess and of the residuals of its arcs and their reverses, so only the
+    // excess of the receiving vertex needs an atomic.  Phase 0 sends excess to t,
+    // phase 1 returns what is left to s.
+    __device__ bool phase_wave(int ph, int nv, int hmax) {
+        long long waves = 0;
+        for (;;) {
+            const int top = relabel(ph, nv, hmax);
+            int act = 0;
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) act += ex[lv] > 0 && lab[lv] < hmax;
+            if (cluster_sum(act) == 0) break;
+            if (++waves > w.pulse_cap) return false;
+            for (int L = top; L >= 1; --L) {
+                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                    if (lab[lv] != L) continue;
+                    int e = ex[lv];
+                    if (e <= 0) continue;
+                    if (L == 1) {
+                        if (!ph) { fx[lv] += e; e = 0; }
+                        else if (bord[lv] == 1) { const int d = e < fx[lv] ? e : fx[lv]; fx[lv] -= d; e -= d; }
+                    } else {
+                        const int a1 = cofs[lv + 1];
+                        for (int a = cofs[lv]; a < a1 && e > 0; a += U) {
+                            int r[U], hr[U], l[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                r[u] = a + u < a1 ? res[a + u] : 0;
+                                hr[u] = a + u < a1 ? href[a + u] : 0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? *(volatile int *)at(lab, hr[u]) : -1;
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (e > 0 && l[u] == L - 1) {
+                                    const int d = e < r[u] ? e : r[u];
+                                    res[a + u] = r[u] - d;
+                                    atomicAdd(at(res, rref[a + u]), d);
+                                    atomicAdd(at(ex, hr[u]), d);
+                                    e -= d;
+                                }
+                            }
+                        }
+                    }
+                    ex[lv] = e;
+                }
+                sync();
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            atomicAddLL(&w.ctl->pulses, waves);
+            atomicAddLL(&w.ctl->relabels, waves + 1);
+        }
+        return true;
     }
 
     // Lock-free pulses (push to the lowest residual neighbour or relabel) until no
     // vertex with excess has a label below hmax; phase 1 returns excess to s.
-    __device__ bool phase(int ph, int nv, int hmax) {
+    __device__ bool phase_pulse(int ph, int nv, int hmax) {
         relabel(ph, nv, hmax);
-        long long pulses = 0;
+        long long pulses = 0, relabels = 1;
         int since = 0;
         for (;;) {
             int act = 0;
@@ -322,13 +431,8 @@ struct ClusterFlow {
                     const int a0 = cofs[lv], a1 = cofs[lv + 1];
                     const unsigned char bd = bord[lv];
                     for (int it = 0; it < w.inner; ++it) {
-                        int hmin = INT_MAX, best = -1;
-                        for (int a = a0; a < a1; ++a) {
-                            if (*(volatile int *)&res[a] <= 0) continue;
-                            const int hh = href[a];
-                            const int l = *(volatile int *)at(lab, hh);
-                            if (l < hmin) { hmin = l; best = a; }
-                        }
+                        int hmin, best;
+                        lowest(a0, a1, hmin, best);
                         if (ph ? (bd == 1 && fx[lv] > 0) : (bd == 2)) { hmin = 0; best = -2; }
                         if (best == -1) { h = hmax; lab[lv] = h; break; }
                         if (h > hmin) {
@@ -372,9 +476,13 @@ struct ClusterFlow {
             if (since >= w.gr_interval) {
                 relabel(ph, nv, hmax);
                 since = 0;
+                ++relabels;
             }
         }
-        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->pulses, pulses);
+        if (rank == 0 && threadIdx.x == 0) {
+            atomicAddLL(&w.ctl->pulses, pulses);
+            atomicAddLL(&w.ctl->relabels, relabels);
+        }
         return true;
     }
 
@@ -390,12 +498,22 @@ struct ClusterFlow {
                 if (f == 3) continue;
                 int add = 0;
                 const int a1 = cofs[lv + 1];
-                for (int a = cofs[lv]; a < a1 && (f | add) != 3; ++a) {
-                    const int hh = href[a], rv = rref[a];
-                    const int fh = *(volatile int *)at(rfl, hh);
-                    if (!((f | add) & 1) && (fh & 1) && *(volatile int *)at(res, rv) > 0) add |= 1;
-                    if (!((f | add) & 2) && (fh & 2) && res[a] > 0) add |= 2;
+                for (int a = cofs[lv]; a < a1 && (f | add) != 3; a += U) {
+                    int fh[U], rr[U], ro[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const bool v = a + u < a1;
+                        fh[u] = v ? *(volatile int *)at(rfl, href[a + u]) : 0;
+                        ro[u] = v ? res[a + u] : 0;
+                        rr[u] = v && (fh[u] & 1) ? *(volatile int *)at(res, rref[a + u]) : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if ((fh[u] & 1) && rr[u] > 0) add |= 1;   // s ~> head -> this vertex
+                        if ((fh[u] & 2) && ro[u] > 0) add |= 2;   // this vertex -> head ~> t
+                    }
                 }
+                add &= ~f;
                 if (add) {
                     rfl[lv] = f | add;
                     changed = 1;

@@ -55,7 +55,8 @@ struct GraphDev {
     long long *blockw;   // [k] c(V_i), maintained by the commit phase
     int n, nnz, k, base; // base: offset of this graph in the concatenated vertex range
     long long Lmax;
-    int sbase, pad;      // sob values are relative to this graph's first side in the step
+    int sbase;           // sob values are relative to this graph's first side in the step
+    int ebase;           // offset of this graph's CSR entries in the concatenated arc range
 };
 
 // Side of block `blk` of graph Gr in this step, or -1.
@@ -151,6 +152,7 @@ struct Work {
     // options
     int reps, gr_interval, inner, any_mb;
     int passes, cluster_mode;    // lock-free pulse passes per barrier; 1: the cluster kernel ran the flow
+    int flow_sched, pad_f;       // cluster max flow: 0 lock-free pulses, 1 level-ordered waves
     unsigned long long seed;
     long long pulse_cap;
 };

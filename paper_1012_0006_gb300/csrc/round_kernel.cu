@@ -533,7 +533,9 @@ struct StepKernel {
         unsigned long long t0 = globaltimer();
         Ctl *ctl = w.ctl;
         const int nu = __ldcg(&ctl->nu);
-        // degree, border, INF_v
+        // degree, border, INF_v; crank[e] = rank of arc e among its row's corridor
+        // arcs (-1 for other arcs), so that reverse arcs need no re-filtering later
+        int *crank = w.outs;
         for (long long b0 = G.warp * 32; b0 < nu; b0 += G.nwarps * 32) {
             const long long i = b0 + (threadIdx.x & 31);
             const bool valid = i < nu;
@@ -550,8 +552,11 @@ struct StepKernel {
                     const int u = __ldg(Gr.adjncy + j);
                     wdeg += __ldg(Gr.adjwgt + j);
                     const int pu = Gr.part[u];
-                    if (pu != P.a && pu != P.b) continue;
-                    if (__ldcg(Gr.lid + u) >= 0) ++cnt; else bor = 1;
+                    int rk = -1;
+                    if (pu == P.a || pu == P.b) {
+                        if (__ldcg(Gr.lid + u) >= 0) rk = cnt++; else bor = 1;
+                    }
+                    crank[Gr.ebase + j] = rk;
                 }
                 w.off[i] = cnt;   // degree for now
                 w.border[i] = bor ? ((s & 1) ? 2 : 1) : 0;
@@ -586,25 +591,27 @@ struct StepKernel {
             long long cout = 0;
             const int j1 = __ldg(Gr.xadj + v + 1);
             for (int e = __ldg(Gr.xadj + v); e < j1; ++e) {
+                if (__ldcg(&crank[Gr.ebase + e]) < 0) continue;
                 const int u = __ldg(Gr.adjncy + e);
-                const int pu = Gr.part[u];
-                if (pu != P.a && pu != P.b) continue;
                 const int h = __ldcg(Gr.lid + u);
-                if (h < 0) continue;
                 const int c = __ldg(Gr.adjwgt + e);
                 cout += c;
                 w.head[j] = h;
                 w.cap[j] = c;
                 w.res[j] = c;
-                // position of v among u's corridor arcs
-                int q = 0;
-                const int k1 = __ldg(Gr.xadj + u + 1);
-                for (int f = __ldg(Gr.xadj + u); f < k1; ++f) {
-                    const int x = __ldg(Gr.adjncy + f);
-                    if (x == v) break;
-                    const int px = Gr.part[x];
-                    if ((px == P.a || px == P.b) && __ldcg(Gr.lid + x) >= 0) ++q;
+                // the reverse arc: v's position in u's row, then its rank among u's corridor arcs
+                const int k0 = __ldg(Gr.xadj + u), k1 = __ldg(Gr.xadj + u + 1);
+                int t = -1;
+                for (int f = k0; f < k1 && t < 0; f += 8) {
+                    int x[8];
+#pragma unroll
+                    for (int z = 0; z < 8; ++z) x[z] = f + z < k1 ? __ldg(Gr.adjncy + f + z) : -1;
+#pragma unroll
+                    for (int z = 7; z >= 0; --z)
+                        if (x[z] == v) t = f + z;
                 }
+                const int q = t >= 0 ? __ldcg(&crank[Gr.ebase + t]) : 0;
+                if (t < 0) fail(w.ctl, E_INVALID, 41);   // no reverse arc: the CSR is not symmetric
                 w.rev[j] = __ldcg(&w.off[h]) + q;
                 ++j;
             }

@@ -47,7 +47,7 @@ struct Req {
     int n = 0, nnz = 0, k = 0;
     int npairs = 0, nrounds = 0, round = 0;
     std::vector<int> off;
-    long long Ubase = 0, Lmax = 0, totcut = 0, dcut = 0;
+    long long Ubase = 0, Lmax = 0, totcut = 0, dcut = 0, W = 0;
     int accepted = 0;
     fr_status status = FR_OK;
 };
@@ -145,6 +145,7 @@ static fr_status admit(fr_server *S, Req *q) {
     q->npairs = po.npairs;
     q->nrounds = po.nrounds;
     q->totcut = po.totcut;
+    q->W = po.W;
     q->Ubase = host_budget_base(po.W, k, q->r.eps, q->r.alpha);
     q->Lmax = host_lmax(po.W, po.maxc, k, q->r.eps);
     q->off.assign(q->nrounds + 1, 0);
@@ -216,7 +217,7 @@ static fr_status run_step(fr_server *S, std::vector<Req *> &act) {
         if (cudaMallocAsync(&S->d_graphs, sizeof(GraphDev) * S->graphs_cap, st) != cudaSuccess) return FR_ERR_OOM;
     }
     std::vector<GraphDev> gds(act.size());
-    long long base = 0;
+    long long base = 0, ebase = 0;
     for (size_t i = 0; i < act.size(); ++i) {
         Req *q = act[i];
         const SGraph &G = S->graphs[q->r.graph_id];
@@ -230,7 +231,9 @@ static fr_status run_step(fr_server *S, std::vector<Req *> &act) {
         gd.blockw = q->blockw;
         gd.n = q->n; gd.nnz = q->nnz; gd.k = q->k; gd.base = (int)base; gd.Lmax = q->Lmax;
         gd.sbase = 2 * pbase[i];
+        gd.ebase = (int)ebase;
         base += q->n;
+        ebase += q->nnz;
     }
     memcpy(ctx->h_stage + 65536, gds.data(), sizeof(GraphDev) * gds.size());
     if (cudaMemcpyAsync(S->d_graphs, ctx->h_stage + 65536, sizeof(GraphDev) * gds.size(), cudaMemcpyHostToDevice,
@@ -263,7 +266,15 @@ static fr_status run_step(fr_server *S, std::vector<Req *> &act) {
                std::max<long long>(1, act[i]->Ubase / std::max(1, act[i]->k));
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2 * P, std::max<long long>(1, est));
-    if (launch_round(ctx, w, grid, tpb, st, nullptr) != cudaSuccess) return FR_ERR_CUDA;
+    long long emax = 0;   // corridor vertices of the largest pair: two sides of (Ubase - W/k) weight
+    for (size_t i = 0; i < act.size(); ++i) {
+        const Req *q = act[i];
+        const double avgc = std::max(1.0, (double)q->W / q->n);
+        const long long side = std::max(0LL, q->Ubase - q->W / q->k);
+        emax = std::max(emax, (long long)(2.0 * side / avgc));
+    }
+    if (launch_round(ctx, w, grid, tpb, st, nullptr, emax, (double)totm / std::max(1LL, totn)) != cudaSuccess)
+        return FR_ERR_CUDA;
     std::vector<PairAcc> A(P);
     Ctl C;
     if (cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * P, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
