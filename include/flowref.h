@@ -77,7 +77,9 @@ typedef struct fr_options {
     int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
     int32_t pulse_passes;  /* lock-free pulse passes between grid barriers; 0 = default */
     int32_t flow_sched;    /* per-pair cluster max flow: 0 lock-free pulses, 1 level-ordered waves */
-    int32_t pad0;
+    int32_t cluster_ctas;  /* CTAs of the first per-pair cluster launch (4, 8 or 16); 0 = by the
+                              estimated corridor size.  Pairs that do not fit go to 16-CTA
+                              clusters, then to the grid-wide flow; results do not depend on it */
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b). */
@@ -230,6 +232,11 @@ typedef struct fr_profile_info {
     int64_t pushes;           /* pushes */
     int64_t scc_rounds;       /* SCC colouring rounds */
     int64_t barriers;         /* grid barriers passed by the persistent kernels */
+    double cluster_phase_ms[4]; /* cluster kernel timers summed over pairs: member scan and load,
+                                   flow to t, return of excess to s, residual reachability */
+    int64_t cluster_syncs;    /* cluster barriers, summed over pairs */
+    int64_t cluster_remote_arcs; /* arcs held in a cluster whose head another CTA holds (DSMEM) */
+    int64_t fallback_pairs;   /* pairs left to the grid-wide flow */
 } fr_profile_info;
 
 /* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with

@@ -372,18 +372,14 @@ extern "C" fr_status fr_create(fr_ctx **out, int32_t device, size_t arena_bytes,
     if (step_max_grid(512, 64, &maxb, &sms) != cudaSuccess) { delete ctx; return FR_ERR_CUDA; }
     ctx->sms = sms;
     ctx->max_coop = std::max(maxb, 1) * 4;
-    {
-        int mc = 0, mc16 = 0;
-        if (cluster_flow_capacity(ctx->cluster_size, &mc) != cudaSuccess) {
+    for (int t = 0; t < 3; ++t) {
+        int mc = 0;
+        if (cluster_flow_capacity(4 << t, &mc) != cudaSuccess) {
             cudaGetLastError();
             mc = 0;
         }
-        if (cluster_flow_capacity(16, &mc16) != cudaSuccess) {
-            cudaGetLastError();
-            mc16 = 0;
-        }
-        ctx->max_clusters = mc;
-        ctx->max_clusters16 = mc16;
+        ctx->cl_cap[t] = mc;
+        ctx->max_clusters = std::max(ctx->max_clusters, mc);
     }
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
@@ -459,6 +455,10 @@ fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *
             return FR_ERR_INVALID_ARG;
         }
         if (opt->mb_reps > 64) { ctx_error(ctx, "mb_reps > 64"); return FR_ERR_INVALID_ARG; }
+        if (opt->cluster_ctas != 0 && opt->cluster_ctas != 4 && opt->cluster_ctas != 8 && opt->cluster_ctas != 16) {
+            ctx_error(ctx, "cluster_ctas must be 0, 4, 8 or 16");
+            return FR_ERR_INVALID_ARG;
+        }
     }
     return FR_OK;
 }
@@ -526,9 +526,45 @@ fr_status reset_idle(fr_ctx *ctx) {
     return FR_OK;
 }
 
+// Cluster launches of one round's max flows: tier 0 with the smallest cluster that
+// holds the estimated largest network (or opt->cluster_ctas), then, if tier 0 was
+// smaller than 16 CTAs, tier 1 with 16-CTA clusters for the pairs that did not fit
+// (it returns at once when there are none).  Returns the launches enqueued in *nl.
+cudaError_t launch_clusters(fr_ctx *ctx, Work &w, long long est_pair_vertices, double avg_degree, int force,
+                            cudaStream_t st, int *nl) {
+    *nl = 0;
+    // shared memory a pair needs: ~29 B per vertex and 20 B per arc, plus slack for
+    // an uneven split; a CTA has cluster_flow_smem() bytes
+    const double need = 1.15 * (double)est_pair_vertices * (29.0 + 20.0 * avg_degree);
+    const double per_cta = 0.9 * (double)cluster_flow_smem();
+    int t0 = -1;
+    for (int t = 0; t < 3; ++t) {
+        if (ctx->cl_cap[t] <= 0) continue;
+        if (force == (4 << t)) { t0 = t; break; }
+        if (force == 0 && t0 < 0 && need <= per_cta * (4 << t)) t0 = t;
+    }
+    if (t0 < 0) {   // nothing fits the estimate (or the forced size is unavailable): the largest
+        for (int t = 2; t >= 0 && t0 < 0; --t)
+            if (ctx->cl_cap[t] > 0) t0 = t;
+    }
+    if (t0 < 0) return cudaErrorInvalidValue;
+    w.cl_tier = 0;
+    cudaError_t e = launch_cluster_flow(w, 4 << t0, ctx->cl_cap[t0], st);
+    if (e != cudaSuccess) return e;
+    ++*nl;
+    if (t0 < 2 && ctx->cl_cap[2] > 0) {
+        w.cl_tier = 1;
+        e = launch_cluster_flow(w, 16, ctx->cl_cap[2], st);
+        w.cl_tier = 0;
+        if (e != cudaSuccess) return e;
+        ++*nl;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev,
-                         long long est_pair_vertices, double avg_degree) {
-    // ev (optional): 6 events bracketing step 1, the cluster kernel and step 2
+                         long long est_pair_vertices, double avg_degree, int cluster_ctas) {
+    // ev (optional): 6 events bracketing step 1, the cluster kernels and step 2
     if (ctx->max_clusters <= 0) {
         w.cluster_mode = 0;
         if (ev) cudaEventRecord(ev[0], st);
@@ -537,6 +573,7 @@ cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t s
             cudaEventRecord(ev[1], st);
             for (int i = 2; i < 6; ++i) cudaEventRecord(ev[i], st);
         }
+        ctx->round_launches = 1;
         return e;
     }
     w.cluster_mode = 1;
@@ -545,16 +582,14 @@ cudaError_t launch_round(fr_ctx *ctx, Work &w, int grid, int tpb, cudaStream_t s
     if (ev) cudaEventRecord(ev[1], st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
-    // shared memory a pair needs (~25 B per vertex, 12 B per arc), with room for an uneven split
-    const double need = 1.4 * (double)est_pair_vertices * (25.0 + 12.0 * avg_degree);
-    const bool big = ctx->max_clusters16 > 0 && need > 8.0 * 200e3;
-    e = big ? launch_cluster_flow(w, 16, ctx->max_clusters16, st)
-            : launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, st);
+    int nl = 0;
+    e = launch_clusters(ctx, w, est_pair_vertices, avg_degree, cluster_ctas, st, &nl);
     if (ev) cudaEventRecord(ev[3], st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
     e = launch_step(w, PH_FLOW | PH_CUT | PH_EVAL | PH_COMMIT, grid, tpb, st);
     if (ev) cudaEventRecord(ev[5], st);
+    ctx->round_launches = 2 + nl;
     return e;
 }
 
@@ -580,7 +615,7 @@ static fr_status run_pair_iteration(fr_ctx *ctx, const fr_graph *g, int32_t *par
     const int grid = choose_grid(ctx, opt, tpb, 2, est);
     const bool vec = ((reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0);
     CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, est, (double)g->nnz / g->n));
+    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, est, (double)g->nnz / g->n, opt ? opt->cluster_ctas : 0));
     char *h = ctx->h_stage + 2048;
     CK(cudaMemcpyAsync(h, ctx->pacc, sizeof(PairAcc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(h + 512, ctx->sides, 2 * sizeof(SideDev), cudaMemcpyDeviceToHost, ctx->stream));

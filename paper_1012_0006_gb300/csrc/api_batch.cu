@@ -176,11 +176,8 @@ extern "C" fr_status fr_maxflow(fr_ctx *ctx, fr_corridor *c, int64_t *flow_out) 
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
     if (ctx->max_clusters > 0) {
         w.cluster_mode = 1;
-        const double need = 1.4 * (double)c->nc * (25.0 + 12.0 * (double)c->m / std::max(1, c->nc));
-        if (ctx->max_clusters16 > 0 && need > 8.0 * 200e3)
-            CK(launch_cluster_flow(w, 16, ctx->max_clusters16, ctx->stream));
-        else
-            CK(launch_cluster_flow(w, ctx->cluster_size, ctx->max_clusters, ctx->stream));
+        int nl = 0;
+        CK(launch_clusters(ctx, w, c->nc, (double)c->m / std::max(1, c->nc), 0, ctx->stream, &nl));
     }
     CK(launch_step(w, PH_FLOW, grid, tpb, ctx->stream));
     PairAcc A;
@@ -339,12 +336,16 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
     CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc) * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * (size_t)np * kHistBins, ctx->stream));
     const bool vec = (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0;
+    long long nl = 3;   // prep, colouring, pair fill
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr, pl.est_max[r], pl.avg_degree));
+        CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr, pl.est_max[r], pl.avg_degree,
+                        opt->cluster_ctas));
+        nl += 1 + ctx->round_launches;
     }
+    ctx->sweep_launches = nl;
     return FR_OK;
 }
 
@@ -362,6 +363,7 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
     CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc) * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * (size_t)np * kHistBins, ctx->stream));
     const bool vec = (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0;
+    long long nl = 3;
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
@@ -369,8 +371,10 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
         CK(cudaEventRecord(ctx->pev[8 * r + 1], ctx->stream));
         CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, &ctx->pev[8 * r + 2], pl.est_max[r],
-                        pl.avg_degree));
+                        pl.avg_degree, opt->cluster_ctas));
+        nl += 1 + ctx->round_launches;
     }
+    ctx->sweep_launches = nl;
     return FR_OK;
 }
 
@@ -397,10 +401,11 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   opt->gr_interval, opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
-                                  opt->flow_sched};
+                                  opt->flow_sched, opt->cluster_ctas};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
+    long long exec_launches = 0;
     if (ctx->profiling) {
         CK(cudaEventRecord(ctx->ev0, ctx->stream));
         fr_status st = enqueue_sweep_profiled(ctx, g, pl, opt);
@@ -422,13 +427,13 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
         ctx->prof.scan_ms = sc;
         ctx->prof.step_ms = stp;
         ctx->prof.cluster_ms = clu;
-        ctx->last_launches = 3 + (ctx->max_clusters > 0 ? 4LL : 2LL) * pl.nr;
+        ctx->last_launches = ctx->sweep_launches;
         return FR_OK;
     }
     ctx->prof.scan_ms = ctx->prof.step_ms = ctx->prof.cluster_ms = 0;
     if (ctx->use_graphs) {
         for (auto &e : ctx->gcache)
-            if (e.key == key) { exec = e.exec; break; }
+            if (e.key == key) { exec = e.exec; exec_launches = e.launches; break; }
         if (!exec) {
             cudaGraph_t graph = nullptr;
             CK(cudaStreamSynchronize(ctx->stream));
@@ -451,7 +456,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                     cudaGraphExecDestroy(ctx->gcache.front().exec);
                     ctx->gcache.erase(ctx->gcache.begin());
                 }
-                ctx->gcache.push_back({key, exec});
+                exec_launches = ctx->sweep_launches;
+                ctx->gcache.push_back({key, exec, exec_launches});
             } else {
                 ctx->use_graphs = false;   // capture unsupported here: launch directly from now on
             }
@@ -467,8 +473,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
-    // prep + colour + fill + per round scan and step (two steps and the cluster kernel in cluster mode)
-    ctx->last_launches = 3 + (ctx->max_clusters > 0 ? 4LL : 2LL) * pl.nr;
+    // prep + colour + fill + per round the scan, the steps and the cluster launches
+    ctx->last_launches = exec ? exec_launches : ctx->sweep_launches;
     return FR_OK;
 }
 
@@ -551,7 +557,9 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
         return bad;
     }
     long long flow_ns = 0;
-    for (int r = 0; r < pl.nr; ++r) flow_ns += C[r].timers[T_FLOW1] + C[r].timers[T_GR] + C[r].timers[T_FLOW2];
+    for (int r = 0; r < pl.nr; ++r)
+        flow_ns += C[r].timers[T_FLOW1] + C[r].timers[T_GR] + C[r].timers[T_FLOW2] + C[r].timers[T_CL_FLOW] +
+                   C[r].timers[T_CL_RETURN];
     {
         fr_profile_info &P = ctx->prof;
         const double sc = P.scan_ms, stp = P.step_ms, clu = P.cluster_ms;
@@ -576,6 +584,10 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.pushes += C[r].pushes;
             P.scc_rounds += C[r].scc_rounds;
             P.barriers += C[r].barriers;
+            for (int t = 0; t < 4; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
+            P.cluster_syncs += C[r].cl_syncs;
+            P.cluster_remote_arcs += C[r].cl_remote;
+            P.fallback_pairs += C[r].fallback;
         }
     }
     for (int r = 0; r < pl.nr; ++r)

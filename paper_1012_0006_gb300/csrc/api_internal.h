@@ -15,6 +15,7 @@ constexpr size_t kHostStage = 8u << 20;     // pinned staging for small host<->d
 struct GraphCacheEntry {
     std::vector<long long> key;
     cudaGraphExec_t exec = nullptr;
+    long long launches = 0;   // kernels in the captured sweep
 };
 
 struct fr_ctx {
@@ -28,8 +29,11 @@ struct fr_ctx {
     char *h_stage = nullptr;
     // launch shape (fr_autotune writes these)
     int tune_tpb = 512, tune_grid = 0, tune_gr = 16, tune_inner = 2, tune_passes = 2;
-    // per-pair max flow in thread-block clusters (0 clusters: grid-wide path only)
-    int cluster_size = 8, max_clusters = 0, max_clusters16 = 0;
+    // per-pair max flow in thread-block clusters of 4, 8 or 16 CTAs: how many of each
+    // can be resident (all 0: grid-wide path only); max_clusters = the largest
+    int cl_cap[3] = {0, 0, 0};
+    int max_clusters = 0;
+    int round_launches = 0;   // kernels the last launch_round enqueued
     // graph-size workspace
     void *base_mem = nullptr;
     size_t base_bytes = 0;
@@ -82,6 +86,7 @@ struct fr_ctx {
     std::vector<GraphCacheEntry> gcache;
     bool use_graphs = true;
     long long last_launches = 0;   // kernels launched by the last call
+    long long sweep_launches = 0;  // kernels the last enqueued sweep holds
     // profiling: direct launches with an event pair around each kernel
     bool profiling = false;
     std::vector<cudaEvent_t> pev;
@@ -117,8 +122,11 @@ fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k,
 fr_status reset_idle(fr_ctx *ctx);
 // Launches of one flow iteration over the pairs of w after the boundary scan:
 // step (BFS, ids, build) -> cluster max flow -> step (rest), or one step kernel.
-// est_pair_vertices: estimated corridor size of the largest pair (chooses 8- or 16-CTA clusters).
+// est_pair_vertices: estimated corridor size of the largest pair (chooses the cluster size);
+// cluster_ctas: 4, 8 or 16 forces the first cluster size, 0 chooses it.
 cudaError_t launch_round(fr_ctx *ctx, fr::Work &w, int grid, int tpb, cudaStream_t st, cudaEvent_t *ev,
-                         long long est_pair_vertices = 0, double avg_degree = 12.0);
+                         long long est_pair_vertices = 0, double avg_degree = 12.0, int cluster_ctas = 0);
+cudaError_t launch_clusters(fr_ctx *ctx, fr::Work &w, long long est_pair_vertices, double avg_degree, int force,
+                            cudaStream_t st, int *nl);
 void release_corridor(fr_ctx *ctx);
 void destroy_graph_cache(fr_ctx *ctx);

@@ -35,6 +35,7 @@ struct ClusterHdr {
     int nvcap, nacap;           // common capacities (identical in every CTA)
     int nv, na;                 // this CTA's vertices and arcs
     int counts[kClusterMax];    // scratch for the member scan (CTA 0's copy)
+    int grab[2];                // slot of the size order taken (CTA 0's copy, by parity)
     long long flow;
 };
 
@@ -50,7 +51,8 @@ struct ClusterFlow {
     ClusterHdr *hdr;
     ClusterHdr *hdr0;          // CTA 0's header
     // local arrays
-    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *href, *rref, *res;
+    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *href, *rref, *res, *csum;
+    int *hlab;                 // per arc: the label of its head as last published by the head
     unsigned char *bord;
     int rot;                   // rotating counter index (identical in every CTA)
 
@@ -63,25 +65,36 @@ struct ClusterFlow {
 
     static constexpr int U = 8;   // arcs whose loads are issued together
 
-    // Lowest label over the residual arcs [a0, a1) (res > 0), and the arc holding it.
+    // Lowest head label over the residual arcs [a0, a1) (res > 0), and the arc holding
+    // it.  Reads only this CTA's memory: the arcs' copies of their head labels.
     __device__ __forceinline__ void lowest(int a0, int a1, int &hmin, int &best) const {
         hmin = INT_MAX;
         best = -1;
         for (int a = a0; a < a1; a += U) {
-            int r[U], hr[U], l[U];
+            int r[U], l[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 r[u] = a + u < a1 ? *(volatile int *)&res[a + u] : 0;
-                hr[u] = a + u < a1 ? href[a + u] : 0;
+                l[u] = a + u < a1 ? *(volatile int *)&hlab[a + u] : INT_MAX;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? *(volatile int *)at(lab, hr[u]) : INT_MAX;
-#pragma unroll
             for (int u = 0; u < U; ++u)
-                if (l[u] < hmin) { hmin = l[u]; best = a + u; }
+                if (r[u] > 0 && l[u] < hmin) { hmin = l[u]; best = a + u; }
         }
     }
 
+
+    // New label h of local vertex lv: its own word and the copies on the reverse
+    // arcs of its arcs (the arcs of which lv is the head), local or in other CTAs.
+    // The copies may lag; they never run ahead of the label, and labels only rise
+    // between exact relabels, so a lagging copy only makes a push look admissible
+    // that is not -- capacities and excesses stay exact, and the phases end only
+    // after an exact relabel has confirmed that no excess can move.
+    __device__ __forceinline__ void set_label(int lv, int h) {
+        lab[lv] = h;
+        const int a1 = cofs[lv + 1];
+        for (int a = cofs[lv]; a < a1; ++a) *(volatile int *)at(hlab, rref[a]) = h;
+    }
 
     __device__ ClusterFlow(const Work &w_, char *smem)
         : w(w_), cl(cg::this_cluster()), rank((int)cg::this_cluster().block_rank()),
@@ -91,18 +104,21 @@ struct ClusterFlow {
         rot = 0;
     }
 
-    __device__ void sync() { cl.sync(); }
+    long long nsync = 0;       // cluster barriers of the current pair (CTA 0, thread 0)
 
-    // cluster-wide sum of x (one value per thread); every thread gets the total
+    __device__ void sync() {
+        ++nsync;
+        cl.sync();
+    }
+
+    // Cluster-wide sum of x (one value per thread); every thread gets the total.
+    // Each warp adds its sum straight into CTA 0's counter, so one cluster barrier
+    // is the only synchronisation.  The counters rotate over three slots: slot
+    // rot + 1 was last read before the previous barrier, so CTA 0 may clear it now.
     __device__ int cluster_sum(int x) {
-        __shared__ int s_part;
-        __syncthreads();
-        if (threadIdx.x == 0) s_part = 0;
-        __syncthreads();
-        if (x) atomicAdd(&s_part, x);
-        __syncthreads();
+        x = (int)__reduce_add_sync(FULL, (unsigned)x);
         int *c = &hdr0->cnt[rot];
-        if (threadIdx.x == 0 && s_part) atomicAdd(c, s_part);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(c, x);
         if (rank == 0 && threadIdx.x == 0) hdr->cnt[(rot + 1) % 3] = 0;
         sync();
         const int tot = *(volatile int *)c;
@@ -127,11 +143,13 @@ struct ClusterFlow {
         href = reinterpret_cast<int *>(take(4ull * nacap));
         rref = reinterpret_cast<int *>(take(4ull * nacap));
         res = reinterpret_cast<int *>(take(4ull * nacap));
+        csum = reinterpret_cast<int *>(take(4ull * nacap));
+        hlab = reinterpret_cast<int *>(take(4ull * nacap));
     }
 
     static __host__ __device__ size_t bytes_for(int nvcap, int nacap) {
         auto a = [](size_t b) { return (b + 15) / 16 * 16; };
-        return kHdrBytes + 6 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + 3 * a(4ull * nacap);
+        return kHdrBytes + 6 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + 5 * a(4ull * nacap);
     }
 
     __device__ int owner(int k) const {   // CTA whose range holds member k
@@ -152,6 +170,7 @@ struct ClusterFlow {
 
     __device__ bool solve(int p, char *smem, size_t smem_bytes) {
         unsigned long long t_in = globaltimer();
+        nsync = 0;
         const int nu = __ldcg(&w.ctl->nu);
         const int V = __ldcg(&w.pacc[p].nc), A = __ldcg(&w.pacc[p].m);
         if (V == 0) return true;
@@ -256,6 +275,7 @@ struct ClusterFlow {
         const int nv = khi - klo;
         const int abase = klo < V ? __ldcg(&pacs[klo]) : A;
         // load this CTA's vertices and arcs
+        int nremote = 0;   // arcs whose head another CTA holds
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const int i = __ldcg(&pmem[klo + lv]);
             gidx[lv] = i;
@@ -270,27 +290,32 @@ struct ClusterFlow {
                 const int h = w.head[j];
                 const int kh = __ldcg(&plocal[h]);
                 const int rh = owner(kh);
+                nremote += rh != rank;
                 href[la] = cpack(rh, kh - hdr->klo[rh]);
                 const int rv = w.rev[j];
                 const int ar = __ldcg(&pacs[kh]) - (hdr->klo[rh] < V ? __ldcg(&pacs[hdr->klo[rh]]) : A) + (rv - w.off[h]);
                 rref[la] = cpack(rh, ar);
                 res[la] = __ldcg(&w.res[j]);
+                csum[la] = w.cap[j] + w.cap[rv];   // res(a) + res(reverse of a), fixed
             }
         }
+        nremote = (int)__reduce_add_sync(FULL, (unsigned)nremote);
+        if ((threadIdx.x & 31) == 0 && nremote) atomicAddLL(&w.ctl->cl_remote, (long long)nremote);
         if (threadIdx.x == 0) {
             hdr->nv = nv;
             const int a1 = khi < V ? __ldcg(&pacs[khi]) : A;
             cofs[nv] = a1 - abase;
+            hdr->na = a1 - abase;
             if (rank == 0) { hdr->cnt[0] = hdr->cnt[1] = hdr->cnt[2] = 0; hdr->err = 0; }
         }
         rot = 0;
         sync();
         const int hmax = V + 2;
-        unsigned long long t1 = globaltimer();
-        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->timers[T_BUILD], (long long)(t1 - t_in));
-        const bool ok = w.flow_sched == 1 ? (phase_wave(0, nv, hmax) && (mark(t1, T_FLOW1), phase_wave(1, nv, hmax)))
-                                          : (phase_pulse(0, nv, hmax) && (mark(t1, T_FLOW1), phase_pulse(1, nv, hmax)));
-        mark(t1, T_FLOW2);
+        unsigned long long t1 = t_in;
+        mark(t1, T_CL_LOAD);
+        const bool ok = w.flow_sched == 1 ? (phase_wave(0, nv, hmax) && (mark(t1, T_CL_FLOW), phase_wave(1, nv, hmax)))
+                                          : (phase_pulse(0, nv, hmax) && (mark(t1, T_CL_FLOW), phase_pulse(1, nv, hmax)));
+        mark(t1, T_CL_RETURN);
         if (!ok) {
             // cap reached: report, leave the pair's arrays as they were
             if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_ITER, 300);
@@ -298,7 +323,7 @@ struct ClusterFlow {
             return true;
         }
         reach(nv);
-        mark(t1, T_REACH);
+        mark(t1, T_CL_REACH);
         // write back: residuals, s/t flows, zero excess, reachability and plain sides
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const int i = gidx[lv];
@@ -313,44 +338,46 @@ struct ClusterFlow {
             if (rfl[lv] == 3) fail(w.ctl, E_INTERNAL, 302);
         }
         sync();
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->cl_syncs, nsync);
         return true;
     }
 
-    // Exact labels by pull passes: an unlabelled vertex with a residual arc into
-    // level d gets d + 1.  phase 0: distance to t; phase 1: distance to s.
-    // Returns the highest label below hmax.
+    // Exact labels by a breadth-first search over residual arcs, pushed outward
+    // from the level-1 vertices: a vertex u of level d lowers the label of each v
+    // with a residual arc v -> u to d + 1 (an atomic min into v's CTA, so no CTA
+    // reads another's labels).  The residual of v -> u is csum - res of u -> v.
+    // phase 0: distance to t; phase 1: distance to s.  One cluster barrier per
+    // level; returns the highest label below hmax.
     __device__ int relabel(int ph, int nv, int hmax) {
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const bool src = ph ? (bord[lv] == 1 && fx[lv] > 0) : (bord[lv] == 2);
             lab[lv] = src ? 1 : hmax;
         }
+        const int na = hdr->na;
+        for (int a = threadIdx.x; a < na; a += TPB) hlab[a] = hmax;
         sync();
-        int top = 1;
-        for (int d = 1; d < hmax; ++d) {
-            int changed = 0;
-            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                if (lab[lv] != hmax) continue;
-                const int a1 = cofs[lv + 1];
-                for (int a = cofs[lv]; a < a1; a += U) {
-                    int r[U], hr[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        r[u] = a + u < a1 ? res[a + u] : 0;
-                        hr[u] = a + u < a1 ? href[a + u] : 0;
-                    }
-                    bool hit = false;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) hit |= r[u] > 0 && *(volatile int *)at(lab, hr[u]) == d;
-                    if (hit) {
-                        lab[lv] = d + 1;
-                        changed = 1;
-                        break;
+        const int lane = threadIdx.x & 31;
+        int d = 1;
+        for (; d < hmax; ++d) {
+            int nf = 0;
+            // each warp finds the level-d vertices among its 32, then runs over the
+            // arcs of each of them with all lanes
+            for (int base = threadIdx.x - lane; base < nv; base += TPB) {
+                const int lv = base + lane;
+                const bool fr = lv < nv && *(volatile int *)&lab[lv] == d;
+                nf += fr;
+                for (unsigned m = __ballot_sync(FULL, fr); m; m &= m - 1) {
+                    const int u = base + __ffs(m) - 1;
+                    const int a1 = cofs[u + 1];
+                    for (int a = cofs[u] + lane; a < a1; a += 32) {
+                        *(volatile int *)at(hlab, rref[a]) = d;   // publish: the labelled vertex is final
+                        if (csum[a] > res[a]) atomicMin(at(lab, href[a]), d + 1);
                     }
                 }
             }
-            if (cluster_sum(changed) == 0) break;
-            top = d + 1;
+            if (cluster_sum(nf) == 0) break;
         }
+        const int top = d > 1 ? d - 1 : 1;
         if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->gr_arcs, top);   // levels, summed
         return top;
     }
@@ -386,9 +413,10 @@ struct ClusterFlow {
                             for (int u = 0; u < U; ++u) {
                                 r[u] = a + u < a1 ? res[a + u] : 0;
                                 hr[u] = a + u < a1 ? href[a + u] : 0;
+                                l[u] = a + u < a1 ? hlab[a + u] : -1;
                             }
 #pragma unroll
-                            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? *(volatile int *)at(lab, hr[u]) : -1;
+                            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? l[u] : -1;
 #pragma unroll
                             for (int u = 0; u < U; ++u) {
                                 if (e > 0 && l[u] == L - 1) {
@@ -434,7 +462,7 @@ struct ClusterFlow {
                         int hmin, best;
                         lowest(a0, a1, hmin, best);
                         if (ph ? (bd == 1 && fx[lv] > 0) : (bd == 2)) { hmin = 0; best = -2; }
-                        if (best == -1) { h = hmax; lab[lv] = h; break; }
+                        if (best == -1) { h = hmax; set_label(lv, h); break; }
                         if (h > hmin) {
                             int d;
                             if (best == -2) {
@@ -455,7 +483,7 @@ struct ClusterFlow {
                         } else {
                             h = hmin + 1;
                             if (h >= hmax) h = hmax;
-                            lab[lv] = h;
+                            set_label(lv, h);
                             if (h >= hmax) break;
                         }
                     }
@@ -471,7 +499,20 @@ struct ClusterFlow {
                 int left = 0;
                 for (int lv = threadIdx.x; lv < nv; lv += TPB)
                     left += ex[lv] > 0 && lab[lv] < hmax;
-                if (cluster_sum(left) == 0) break;
+                if (cluster_sum(left) == 0) {
+                    // Nothing can move by the current labels.  Exact labels decide:
+                    // the phase ends only if no vertex with excess can reach its
+                    // target (the preflow of phase 0 is then maximum; phase 1 has
+                    // returned every excess); otherwise they start the next pulse.
+                    relabel(ph, nv, hmax);
+                    since = 0;
+                    ++relabels;
+                    left = 0;
+                    for (int lv = threadIdx.x; lv < nv; lv += TPB)
+                        left += ex[lv] > 0 && lab[lv] < hmax;
+                    if (cluster_sum(left) == 0) break;
+                    continue;
+                }
             }
             if (since >= w.gr_interval) {
                 relabel(ph, nv, hmax);
@@ -486,59 +527,76 @@ struct ClusterFlow {
         return true;
     }
 
-    // bit 1: reachable from s; bit 2: reaches t (monotone pull passes)
+    // bit 1: reachable from s; bit 2: reaches t.  Frontier pushes: a vertex with
+    // a bit not yet passed on sets bit 1 at the heads of its residual arcs and
+    // bit 2 at the tails of residual arcs into it (atomic or into the owner's CTA).
+    // lab, free after the flow, holds the bits already passed on.
     __device__ void reach(int nv) {
-        for (int lv = threadIdx.x; lv < nv; lv += TPB)
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             rfl[lv] = (bord[lv] == 1 ? 1 : 0) | (bord[lv] == 2 ? 2 : 0);
+            lab[lv] = 0;
+        }
         sync();
-        for (int it = 0; it < 1 << 30; ++it) {
-            int changed = 0;
-            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                const int f = rfl[lv];
-                if (f == 3) continue;
-                int add = 0;
-                const int a1 = cofs[lv + 1];
-                for (int a = cofs[lv]; a < a1 && (f | add) != 3; a += U) {
-                    int fh[U], rr[U], ro[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const bool v = a + u < a1;
-                        fh[u] = v ? *(volatile int *)at(rfl, href[a + u]) : 0;
-                        ro[u] = v ? res[a + u] : 0;
-                        rr[u] = v && (fh[u] & 1) ? *(volatile int *)at(res, rref[a + u]) : 0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if ((fh[u] & 1) && rr[u] > 0) add |= 1;   // s ~> head -> this vertex
-                        if ((fh[u] & 2) && ro[u] > 0) add |= 2;   // this vertex -> head ~> t
-                    }
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            int nproc = 0;
+            for (int base = threadIdx.x - lane; base < nv; base += TPB) {
+                const int lv = base + lane;
+                int nw = 0;
+                if (lv < nv) {
+                    const int f = *(volatile int *)&rfl[lv], dn = lab[lv];
+                    nw = f & ~dn;
+                    if (nw) lab[lv] = dn | nw;
                 }
-                add &= ~f;
-                if (add) {
-                    rfl[lv] = f | add;
-                    changed = 1;
+                nproc += nw != 0;
+                for (unsigned m = __ballot_sync(FULL, nw != 0); m; m &= m - 1) {
+                    const int src = __ffs(m) - 1;
+                    const int u = base + src;
+                    const int nwu = __shfl_sync(FULL, nw, src);
+                    const int a1 = cofs[u + 1];
+                    for (int a = cofs[u] + lane; a < a1; a += 32) {
+                        const int r = res[a];
+                        const int bits = ((nwu & 1) && r > 0 ? 1 : 0) | ((nwu & 2) && csum[a] > r ? 2 : 0);
+                        if (bits) atomicOr(at(rfl, href[a]), bits);
+                    }
                 }
             }
-            if (cluster_sum(changed) == 0) break;
+            if (cluster_sum(nproc) == 0) break;
         }
     }
 };
 
 template <int TPB>
-__global__ void __launch_bounds__(TPB, 1) cluster_flow_kernel(Work w, int nclusters, size_t smem_bytes) {
+__global__ void __launch_bounds__(TPB, 1) cluster_flow_kernel(Work w, size_t smem_bytes) {
     extern __shared__ __align__(16) char csmem[];
     if (w.prev_err && __ldcg(w.prev_err)) return;
-    if (__ldcg(&w.ctl->error)) return;
+    if (w.cl_tier == 1 && __ldcg(&w.ctl->cl_left) == 0) return;
     ClusterFlow<TPB> K(w, csmem);
-    const int cid = blockIdx.x / K.C;
-    for (int p = cid; p < w.npairs; p += nclusters) {
-        const bool done = K.solve(p, csmem, smem_bytes);
-        if (!done && K.rank == 0 && threadIdx.x == 0) {
-            atomicAdd(&w.ctl->fallback, 1);
-            w.pacc[p].status = 1;   // solved by the grid-wide path
-        }
+    for (int it = 0;; ++it) {
+        // slot grab: CTA 0 takes it, every CTA reads it after the barrier; the two
+        // parities keep a slot readable until every CTA has passed the next barrier
+        if (K.rank == 0 && threadIdx.x == 0)
+            K.hdr->grab[it & 1] = __ldcg(&w.ctl->error) ? INT_MAX : atomicAdd(&w.ctl->cl_next[w.cl_tier], 1);
         K.sync();
+        const int j = *(volatile int *)&K.hdr0->grab[it & 1];
+        if (j >= w.npairs) break;
+        const int p = __ldcg(&w.pacc[j].ord);
+        if (w.cl_tier == 1 && __ldcg(&w.pacc[p].status) != 1) continue;
+        const bool done = K.solve(p, csmem, smem_bytes);
+        if (K.rank == 0 && threadIdx.x == 0) {
+            if (w.cl_tier == 0) {
+                if (!done) {
+                    atomicAdd(&w.ctl->fallback, 1);
+                    atomicAdd(&w.ctl->cl_left, 1);
+                    w.pacc[p].status = 1;
+                }
+            } else {
+                w.pacc[p].status = done ? 2 : 3;
+                if (done) atomicAdd(&w.ctl->fallback, -1);
+            }
+        }
     }
+    K.sync();   // no CTA exits while another may still read its shared memory (the last slot)
 }
 
 // Dynamic shared memory of the cluster kernel: the opt-in maximum per block minus
@@ -571,6 +629,7 @@ cudaError_t launch_cluster_flow(const Work &w, int cluster, int max_clusters, cu
     const size_t smem = (size_t)g_cluster_dyn_smem;
     int nclusters = w.npairs < max_clusters ? w.npairs : max_clusters;
     if (nclusters < 1) nclusters = 1;
+    if (cluster < 1 || cluster > kClusterMax) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nclusters * cluster);
     cfg.blockDim = dim3(tpb);
@@ -583,8 +642,10 @@ cudaError_t launch_cluster_flow(const Work &w, int cluster, int max_clusters, cu
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_flow_kernel<512>, w, nclusters, smem);
+    return cudaLaunchKernelEx(&cfg, cluster_flow_kernel<512>, w, smem);
 }
+
+size_t cluster_flow_smem() { return g_cluster_dyn_smem > 0 ? (size_t)g_cluster_dyn_smem : 0; }
 
 cudaError_t cluster_flow_capacity(int cluster, int *max_clusters) {
     cudaError_t e = cluster_setup();

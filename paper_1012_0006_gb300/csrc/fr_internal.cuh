@@ -40,7 +40,9 @@ enum PhaseBits : uint32_t {
 };
 
 enum TimerIdx { T_BFS = 0, T_SELECT, T_LID, T_BUILD, T_FLOW1, T_GR, T_FLOW2, T_REACH, T_SCC, T_SWEEP, T_EVAL,
-                T_COMMIT, T_COUNT };
+                T_COMMIT,
+                // cluster kernel, summed over pairs: member scan and load, flow to t, return to s, reach
+                T_CL_LOAD, T_CL_FLOW, T_CL_RETURN, T_CL_REACH, T_COUNT };
 
 enum SideCode { SS_EXPAND = 1, SS_SELECT = 2, SS_DONE = 3 };
 
@@ -93,7 +95,9 @@ struct PairAcc {
     int ncomp, cbase;    // MB components and their offset in the pair-ordered list
     int best_j, best_r;
     int accept, feasible;
-    int status, pad;
+    int status;          // cluster max flow: 0 solved or pending, 1 left by the first cluster
+                         // launch, 2 solved by the second, 3 left to the grid-wide flow
+    int ord;             // the pair whose network is the ord-th largest of the round (slot ord)
 };
 
 struct Ctl {
@@ -116,7 +120,11 @@ struct Ctl {
     long long pr_arcs;        // arcs scanned by push-relabel pulses
     long long pushes;         // pushes
     long long barriers;       // grid barriers passed (CTA 0)
-    int fallback, pad3;       // pairs the cluster kernel left to the grid-wide flow
+    long long cl_syncs;       // cluster barriers, summed over pairs
+    long long cl_remote;      // cluster-held arcs whose head is in another CTA's shared memory
+    int fallback;             // pairs the cluster kernels left to the grid-wide flow
+    int cl_next[2];           // next slot of the size order each cluster launch takes
+    int cl_left;              // pairs the first cluster launch left (written by it only)
 };
 
 // Everything a kernel needs, passed by value.
@@ -152,7 +160,8 @@ struct Work {
     // options
     int reps, gr_interval, inner, any_mb;
     int passes, cluster_mode;    // lock-free pulse passes per barrier; 1: the cluster kernel ran the flow
-    int flow_sched, pad_f;       // cluster max flow: 0 lock-free pulses, 1 level-ordered waves
+    int flow_sched;              // cluster max flow: 0 lock-free pulses, 1 level-ordered waves
+    int cl_tier;                 // cluster launch: 0 every pair, 1 the pairs the first left
     unsigned long long seed;
     long long pulse_cap;
 };

@@ -595,7 +595,7 @@ struct StepKernel {
                 const int u = __ldg(Gr.adjncy + e);
                 const int h = __ldcg(Gr.lid + u);
                 const int c = __ldg(Gr.adjwgt + e);
-                cout += c;
+                if (__ldcg(&w.border[h]) != 1) cout += c;   // arcs into other s-border vertices carry nothing s could not send directly
                 w.head[j] = h;
                 w.cap[j] = c;
                 w.res[j] = c;
@@ -615,14 +615,27 @@ struct StepKernel {
                 w.rev[j] = __ldcg(&w.off[h]) + q;
                 ++j;
             }
-            // Preflow: s -> v carries what v can pass on, c_out(v) < INF_v.  Flow
-            // through s -> v never exceeds c_out(v), so the max flow is unchanged and
-            // only the excess that is pushed in and then stranded has to return.
+            // Preflow: s -> v carries what v can pass on to vertices outside the
+            // s-border, c_out(v) < INF_v.  Some maximum flow sends no more through
+            // s -> v (flow s -> v -> u with u on the s-border can go s -> u directly),
+            // so the max flow is unchanged and only the excess that is pushed in and
+            // then stranded has to return.
             const unsigned char bd = w.border[i];
             const int fx0 = bd == 1 ? (int)(cout < w.infc[i] ? cout : w.infc[i]) : 0;
             w.fx[i] = fx0;
             w.ex[i] = fx0;
             w.lab[i] = 0;
+        }
+        // pairs by network size, largest first (ties by index): the order in which
+        // the clusters take them
+        for (long long i = G.tid; i < w.npairs; i += G.size) {
+            const int mi = __ldcg(&w.pacc[i].m);
+            int rk = 0;
+            for (int q = 0; q < w.npairs; ++q) {
+                const int mq = __ldcg(&w.pacc[q].m);
+                rk += mq > mi || (mq == mi && q < i);
+            }
+            w.pacc[rk].ord = (int)i;
         }
         if (!grid_sync(ctl)) return false;
         timer_mark(w, t0, T_BUILD);

@@ -14,6 +14,7 @@ size_t step_smem_bytes(int nsides);
 // cluster_flow.cu: per-pair max flow and reachability on distributed shared memory
 cudaError_t launch_cluster_flow(const Work &w, int cluster, int max_clusters, cudaStream_t st);
 cudaError_t cluster_flow_capacity(int cluster, int *max_clusters);
+size_t cluster_flow_smem();   // dynamic shared memory of one CTA of the cluster kernel
 
 // prep_kernel.cu
 struct PrepOut {

@@ -273,7 +273,8 @@ static fr_status run_step(fr_server *S, std::vector<Req *> &act) {
         const long long side = std::max(0LL, q->Ubase - q->W / q->k);
         emax = std::max(emax, (long long)(2.0 * side / avgc));
     }
-    if (launch_round(ctx, w, grid, tpb, st, nullptr, emax, (double)totm / std::max(1LL, totn)) != cudaSuccess)
+    if (launch_round(ctx, w, grid, tpb, st, nullptr, emax, (double)totm / std::max(1LL, totn), opt.cluster_ctas) !=
+        cudaSuccess)
         return FR_ERR_CUDA;
     std::vector<PairAcc> A(P);
     Ctl C;

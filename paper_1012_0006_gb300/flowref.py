@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
-                ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -68,14 +68,18 @@ class ProfileInfo(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("bfs_visited", ctypes.c_int64), ("bfs_arcs", ctypes.c_int64),
                 ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
                 ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
-                ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64), ("barriers", ctypes.c_int64)]
+                ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64), ("barriers", ctypes.c_int64),
+                ("cluster_phase_ms", ctypes.c_double * 4), ("cluster_syncs", ctypes.c_int64),
+                ("cluster_remote_arcs", ctypes.c_int64),
+                ("fallback_pairs", ctypes.c_int64)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("phase_ms", "cluster_phase_ms")}
         d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
+        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach"), list(self.cluster_phase_ms)))
         return d
 
 

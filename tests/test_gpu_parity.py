@@ -263,6 +263,30 @@ def test_launch_shapes_give_identical_partitions(F, ctx):
         assert np.array_equal(got, ref), shape
 
 
+@pytest.mark.parametrize("ctas,sched", [(4, 0), (8, 0), (16, 0), (4, 1)])
+def test_cluster_sizes_parity(F, ctx, ctas, sched):
+    """Each first-tier cluster size (and the wave schedule) against the oracle."""
+    _check_batch(F, ctx, I.config(4, scale=1 / 16), dict(cluster_ctas=ctas, flow_sched=sched))
+
+
+@pytest.mark.parametrize("k,alpha,grid_pairs", [(6, 4.0, False), (4, 16.0, True)])
+def test_cluster_tiers_and_grid_fallback(F, ctx, k, alpha, grid_pairs):
+    """64^3 grid.  k = 6, alpha = 4: networks of 0.4-1 MB, so with 4-CTA clusters
+    first some pairs fit and the rest go to 16-CTA clusters.  k = 4, alpha = 16:
+    ~6 MB networks fit no cluster and go to the grid-wide flow.  The partition is
+    the oracle's either way."""
+    w = I.grid3d_rcb(64, 64, 64, k=k, alpha=alpha)
+    ctx.set_profiling(True)
+    try:
+        _, summ = _check_batch(F, ctx, w, dict(cluster_ctas=4))
+        prof = ctx.profile()
+    finally:
+        ctx.set_profiling(False)
+    assert (prof["fallback_pairs"] > 0) == grid_pairs
+    if not grid_pairs:
+        assert prof["cluster_syncs"] > 0
+
+
 def test_repeated_runs_are_identical(F, ctx):
     w = I.config(3, scale=1 / 64)
     outs = []
