@@ -172,6 +172,7 @@ extern "C" fr_status fr_maxflow(fr_ctx *ctx, fr_corridor *c, int64_t *flow_out) 
     fr_options opt;
     fr_default_options(&opt);
     Work w = make_work(ctx, 0, 0, 1, c->g.n, &opt);
+    w.full_flow = 1;   // fr_corridor_flow hands out the arc flows
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
     if (ctx->max_clusters > 0) {
@@ -227,6 +228,7 @@ extern "C" fr_status fr_extract_cut(fr_ctx *ctx, fr_corridor *c, int32_t most_ba
     CK(cudaMemcpyAsync(&ctx->pairs[0].mb, h, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     Work w = make_work(ctx, 0, 0, 1, c->g.n, &opt);
     w.cluster_mode = ctx->max_clusters > 0 ? 1 : 0;
+    w.full_flow = 1;
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
     CK(launch_step(w, PH_CUT | PH_EVAL | PH_COMMIT, grid, tpb, ctx->stream));

@@ -115,10 +115,16 @@ struct ClusterFlow {
     // Each warp adds its sum straight into CTA 0's counter, so one cluster barrier
     // is the only synchronisation.  The counters rotate over three slots: slot
     // rot + 1 was last read before the previous barrier, so CTA 0 may clear it now.
-    __device__ int cluster_sum(int x) {
-        x = (int)__reduce_add_sync(FULL, (unsigned)x);
+    __device__ int cluster_sum(int x) { return cluster_reduce(x, false); }
+    // cluster-wide maximum of non-negative x
+    __device__ int cluster_max(int x) { return cluster_reduce(x, true); }
+
+    __device__ int cluster_reduce(int x, bool is_max) {
+        x = is_max ? (int)__reduce_max_sync(FULL, (unsigned)x) : (int)__reduce_add_sync(FULL, (unsigned)x);
         int *c = &hdr0->cnt[rot];
-        if ((threadIdx.x & 31) == 0 && x) atomicAdd(c, x);
+        if ((threadIdx.x & 31) == 0 && x) {
+            if (is_max) atomicMax(c, x); else atomicAdd(c, x);
+        }
         if (rank == 0 && threadIdx.x == 0) hdr->cnt[(rot + 1) % 3] = 0;
         sync();
         const int tot = *(volatile int *)c;
@@ -313,8 +319,11 @@ struct ClusterFlow {
         const int hmax = V + 2;
         unsigned long long t1 = t_in;
         mark(t1, T_CL_LOAD);
-        const bool ok = w.flow_sched == 1 ? (phase_wave(0, nv, hmax) && (mark(t1, T_CL_FLOW), phase_wave(1, nv, hmax)))
-                                          : (phase_pulse(0, nv, hmax) && (mark(t1, T_CL_FLOW), phase_pulse(1, nv, hmax)));
+        // a maximum preflow is enough for the cut (see the grid-wide maxflow); the
+        // excess goes back to s only when the flow itself is handed out
+        bool ok = w.flow_sched == 1 ? phase_wave(0, nv, hmax) : phase_pulse(0, nv, hmax);
+        mark(t1, T_CL_FLOW);
+        if (ok && w.full_flow) ok = w.flow_sched == 1 ? phase_wave(1, nv, hmax) : phase_pulse(1, nv, hmax);
         mark(t1, T_CL_RETURN);
         if (!ok) {
             // cap reached: report, leave the pair's arrays as they were
@@ -334,7 +343,7 @@ struct ClusterFlow {
             w.ex[i] = ex[lv];
             w.rflag[i] = rfl[lv];
             w.side_out[i] = (rfl[lv] & 1) ? 0 : 1;
-            if (ex[lv] != 0) fail(w.ctl, E_INTERNAL, 301);
+            if (w.full_flow && ex[lv] != 0) fail(w.ctl, E_INTERNAL, 301);
             if (rfl[lv] == 3) fail(w.ctl, E_INTERNAL, 302);
         }
         sync();
@@ -342,44 +351,53 @@ struct ClusterFlow {
         return true;
     }
 
-    // Exact labels by a breadth-first search over residual arcs, pushed outward
-    // from the level-1 vertices: a vertex u of level d lowers the label of each v
-    // with a residual arc v -> u to d + 1 (an atomic min into v's CTA, so no CTA
-    // reads another's labels).  The residual of v -> u is csum - res of u -> v.
-    // phase 0: distance to t; phase 1: distance to s.  One cluster barrier per
-    // level; returns the highest label below hmax.
-    __device__ int relabel(int ph, int nv, int hmax) {
+    static constexpr int kScans = 4;   // local scans between cluster barriers (relabel, reach)
+
+    // Exact labels: distances over residual arcs to the level-1 vertices, found by
+    // label correction pushed outward.  A vertex whose label dropped since it last
+    // passed it on lowers the label of each v with a residual arc v -> u to its own
+    // + 1 (an atomic min into v's CTA; the residual of v -> u is csum - res of
+    // u -> v) and publishes it to the arcs' copies.  Every CTA rescans its own
+    // vertices kScans times between cluster barriers, without waiting for the
+    // others; a barrier window in which no CTA had a vertex to pass on ends it
+    // (every update sent before the window's barrier was seen in it), and the
+    // fixed point is the breadth-first distance.  rfl, free during the flow, holds
+    // the label each vertex last passed on.  phase 0: distance to t; phase 1:
+    // distance to s.  Returns the highest label below hmax if want_top.
+    __device__ int relabel(int ph, int nv, int hmax, bool want_top = false) {
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const bool src = ph ? (bord[lv] == 1 && fx[lv] > 0) : (bord[lv] == 2);
             lab[lv] = src ? 1 : hmax;
+            rfl[lv] = hmax;
         }
         const int na = hdr->na;
         for (int a = threadIdx.x; a < na; a += TPB) hlab[a] = hmax;
         sync();
-        const int lane = threadIdx.x & 31;
-        int d = 1;
-        for (; d < hmax; ++d) {
-            int nf = 0;
-            // each warp finds the level-d vertices among its 32, then runs over the
-            // arcs of each of them with all lanes
-            for (int base = threadIdx.x - lane; base < nv; base += TPB) {
-                const int lv = base + lane;
-                const bool fr = lv < nv && *(volatile int *)&lab[lv] == d;
-                nf += fr;
-                for (unsigned m = __ballot_sync(FULL, fr); m; m &= m - 1) {
-                    const int u = base + __ffs(m) - 1;
-                    const int a1 = cofs[u + 1];
-                    for (int a = cofs[u] + lane; a < a1; a += 32) {
-                        *(volatile int *)at(hlab, rref[a]) = d;   // publish: the labelled vertex is final
-                        if (csum[a] > res[a]) atomicMin(at(lab, href[a]), d + 1);
+        long long rounds = 0;
+        for (;;) {
+            int nproc = 0;
+            for (int k = 0; k < kScans; ++k) {
+                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                    const int L = *(volatile int *)&lab[lv];
+                    if (L >= rfl[lv]) continue;
+                    rfl[lv] = L;
+                    ++nproc;
+                    const int a1 = cofs[lv + 1];
+                    for (int a = cofs[lv]; a < a1; ++a) {
+                        *(volatile int *)at(hlab, rref[a]) = L;
+                        if (csum[a] > res[a]) atomicMin(at(lab, href[a]), L + 1);
                     }
                 }
             }
-            if (cluster_sum(nf) == 0) break;
+            ++rounds;
+            if (cluster_sum(nproc) == 0) break;
         }
-        const int top = d > 1 ? d - 1 : 1;
-        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->gr_arcs, top);   // levels, summed
-        return top;
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->gr_arcs, rounds);   // barrier windows, summed
+        if (!want_top) return 0;
+        int top = 1;
+        for (int lv = threadIdx.x; lv < nv; lv += TPB)
+            if (lab[lv] < hmax && lab[lv] > top) top = lab[lv];
+        return cluster_max(top);
     }
 
     // Push-relabel in waves: exact labels, then the levels from the top down, each
@@ -392,7 +410,7 @@ struct ClusterFlow {
     __device__ bool phase_wave(int ph, int nv, int hmax) {
         long long waves = 0;
         for (;;) {
-            const int top = relabel(ph, nv, hmax);
+            const int top = relabel(ph, nv, hmax, true);
             int act = 0;
             for (int lv = threadIdx.x; lv < nv; lv += TPB) act += ex[lv] > 0 && lab[lv] < hmax;
             if (cluster_sum(act) == 0) break;
@@ -527,36 +545,32 @@ struct ClusterFlow {
         return true;
     }
 
-    // bit 1: reachable from s; bit 2: reaches t.  Frontier pushes: a vertex with
-    // a bit not yet passed on sets bit 1 at the heads of its residual arcs and
-    // bit 2 at the tails of residual arcs into it (atomic or into the owner's CTA).
-    // lab, free after the flow, holds the bits already passed on.
+    // bit 1: reachable from s, seeded with the s-border and with every vertex
+    // holding excess (the flow that carries each excess back over a new arc v -> s
+    // leaves the residual arc s -> v); bit 2: reaches t.  Frontier pushes: a vertex
+    // with a bit not yet passed on sets bit 1 at the heads of its residual arcs and
+    // bit 2 at the tails of residual arcs into it (atomic or into the owner's CTA),
+    // kScans local scans per cluster barrier as in relabel.  lab, free after the
+    // flow, holds the bits already passed on.
     __device__ void reach(int nv) {
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-            rfl[lv] = (bord[lv] == 1 ? 1 : 0) | (bord[lv] == 2 ? 2 : 0);
+            rfl[lv] = (bord[lv] == 1 || ex[lv] > 0 ? 1 : 0) | (bord[lv] == 2 ? 2 : 0);
             lab[lv] = 0;
         }
         sync();
-        const int lane = threadIdx.x & 31;
         for (;;) {
             int nproc = 0;
-            for (int base = threadIdx.x - lane; base < nv; base += TPB) {
-                const int lv = base + lane;
-                int nw = 0;
-                if (lv < nv) {
+            for (int k = 0; k < kScans; ++k) {
+                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
                     const int f = *(volatile int *)&rfl[lv], dn = lab[lv];
-                    nw = f & ~dn;
-                    if (nw) lab[lv] = dn | nw;
-                }
-                nproc += nw != 0;
-                for (unsigned m = __ballot_sync(FULL, nw != 0); m; m &= m - 1) {
-                    const int src = __ffs(m) - 1;
-                    const int u = base + src;
-                    const int nwu = __shfl_sync(FULL, nw, src);
-                    const int a1 = cofs[u + 1];
-                    for (int a = cofs[u] + lane; a < a1; a += 32) {
+                    const int nw = f & ~dn;
+                    if (!nw) continue;
+                    lab[lv] = dn | nw;
+                    ++nproc;
+                    const int a1 = cofs[lv + 1];
+                    for (int a = cofs[lv]; a < a1; ++a) {
                         const int r = res[a];
-                        const int bits = ((nwu & 1) && r > 0 ? 1 : 0) | ((nwu & 2) && csum[a] > r ? 2 : 0);
+                        const int bits = ((nw & 1) && r > 0 ? 1 : 0) | ((nw & 2) && csum[a] > r ? 2 : 0);
                         if (bits) atomicOr(at(rfl, href[a]), bits);
                     }
                 }

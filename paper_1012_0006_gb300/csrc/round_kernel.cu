@@ -824,15 +824,28 @@ struct StepKernel {
             timer_mark(w, t0, phase2 ? T_FLOW2 : T_FLOW1);
             // Nothing moved in the last pass.  Pushes of earlier lock-free passes may
             // have landed after their target was scanned, so count once more behind
-            // the barrier: no vertex with excess below hmax (labels are valid lower
-            // bounds on the residual distance) means no excess can reach the target.
+            // the barrier; if no vertex with excess is below hmax, an exact global
+            // relabel confirms that no excess can reach the target.
             if (a == 0) {
                 int *cnt = &ctl->act[pl % 3];
                 if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
                 if (!count_active(hmax, nu, false, cnt)) return false;
-                const int left = __ldcg(cnt);
+                int left = __ldcg(cnt);
                 ++pl;
-                if (left == 0) break;
+                if (left == 0) {
+                    // exact labels decide: the phase ends only if no vertex with
+                    // excess can reach the target
+                    if (!global_relabel(phase2, hmax, nu)) return false;
+                    since_gr = 0;
+                    timer_mark(w, t0, T_GR);
+                    cnt = &ctl->act[pl % 3];
+                    if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
+                    if (!count_active(hmax, nu, false, cnt)) return false;
+                    left = __ldcg(cnt);
+                    ++pl;
+                    if (left == 0) break;
+                    continue;
+                }
             }
             if (since_gr >= w.gr_interval) {
                 if (!global_relabel(phase2, hmax, nu)) return false;
@@ -844,32 +857,43 @@ struct StepKernel {
         return true;
     }
 
+    // Maximum preflow (phase 0).  The cut needs no more: with an arc v -> s of
+    // capacity e(v) for every vertex v left with excess e(v), the preflow is a flow
+    // of the same value, the new arcs enter s and change no cut capacity, so the
+    // network has the same minimum cuts and this flow is maximum; its residual
+    // graph is the preflow's plus s -> v for each such v.  The residual sets
+    // therefore take vertices with excess as reached from s (reach), and phase 1,
+    // which returns the excess to s, runs only where a flow is handed out
+    // (full_flow).
     __device__ bool maxflow() {
         Ctl *ctl = w.ctl;
         const int nu = __ldcg(&ctl->nu), hmax = __ldcg(&ctl->hmax);
-        // pairs already solved in their clusters have no excess left, so the grid-wide
-        // phases only move the excess of the pairs that did not fit a cluster
+        // pairs already solved in their clusters have no excess that can move, so the
+        // grid-wide phases only move the excess of the pairs that did not fit a cluster
         if (!w.cluster_mode || __ldcg(&ctl->fallback) > 0) {
             if (!flow_phase(0, hmax, nu)) return false;
-            if (!flow_phase(1, hmax, nu)) return false;
+            if (w.full_flow && !flow_phase(1, hmax, nu)) return false;
         }
-        // every excess must have returned to s: the result is a flow
         unsigned long long t0 = globaltimer();
-        int *cnt = &ctl->act[pl % 3];
-        if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
-        if (!count_active(hmax, nu, true, cnt)) return false;
-        if (__ldcg(cnt) != 0 && G.tid == 0) fail(ctl, E_INTERNAL, 80);
+        if (w.full_flow) {
+            // every excess must have returned to s: the result is a flow
+            int *cnt = &ctl->act[pl % 3];
+            if (G.tid == 0) ctl->act[(pl + 1) % 3] = 0;
+            if (!count_active(hmax, nu, true, cnt)) return false;
+            if (__ldcg(cnt) != 0 && G.tid == 0) fail(ctl, E_INTERNAL, 80);
+            ++pl;
+        }
         // flow value per pair: flow into t
         for (long long i = G.tid; i < nu; i += G.size)
             if (w.border[i] == 2) atomicAddLL(&w.pacc[w.sid[i] >> 1].flow, (long long)w.fx[i]);
-        ++pl;
         if (!grid_sync(ctl)) return false;
         timer_mark(w, t0, T_FLOW2);
         return true;
     }
 
     // ---------------------------------------------------------- residual sets --
-    // Bit 1: reachable from s (the smallest source set, Ford-Fulkerson labelling);
+    // Bit 1: reachable from s (the smallest source set, Ford-Fulkerson labelling),
+    // seeded with the s-border and every vertex holding excess (see maxflow);
     // bit 2: reaches t.  Both searches share one frontier queue, entries tagged by
     // the top bit.
     __device__ bool reach() {
@@ -885,7 +909,7 @@ struct StepKernel {
                 bool sb = false, tb = false;
                 if (i < nu) {
                     const unsigned char bd = w.border[i];
-                    sb = bd == 1;
+                    sb = bd == 1 || __ldcg(&w.ex[i]) > 0;
                     tb = bd == 2;
                     w.rflag[i] = (sb ? 1 : 0) | (tb ? 2 : 0);
                 }
