@@ -77,7 +77,7 @@ typedef struct fr_options {
     int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
     int32_t pulse_passes;  /* lock-free pulse passes between grid barriers; 0 = default */
     int32_t flow_sched;    /* per-pair cluster max flow: 0 lock-free pulses, 1 level-ordered waves */
-    int32_t cluster_ctas;  /* CTAs of the first per-pair cluster launch (4, 8 or 16); 0 = by the
+    int32_t cluster_ctas;  /* CTAs of the first per-pair cluster launch (4, 6, 8, 12 or 16); 0 = by the
                               estimated corridor size.  Pairs that do not fit go to 16-CTA
                               clusters, then to the grid-wide flow; results do not depend on it */
 } fr_options;

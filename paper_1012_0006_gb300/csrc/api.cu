@@ -90,6 +90,7 @@ static size_t base_bytes(long long n, long long nnz, int k, int reps, int grid) 
     auto add = [&](size_t elem, long long cnt) { b += ((elem * (size_t)cnt + 255) / 256) * 256; };
     add(4, n); add(4, n);                                   // dist, lid
     add(4, n); add(4, n);                                   // vq_v, vq_s
+    add(4, n / 32 + 2);                                     // cbits
     for (int i = 0; i < 13; ++i) add(4, nu + 1);            // gid sid off infc fx lab rflag color scc vc fq0 fq1 ...
     add(8, nu); add(1, nu); add(1, nu);                     // ex border side_out
     for (int i = 0; i < 4; ++i) add(4, mu);                 // head rev res cap
@@ -209,6 +210,7 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     const long long nu = nn, mu = mm;
     ctx->dist = carve<int>(p, nn); ctx->lid = carve<int>(p, nn);
     ctx->vq_v = carve<int>(p, nn); ctx->vq_s = carve<int>(p, nn);
+    ctx->cbits = carve<unsigned int>(p, nn / 32 + 2);
     ctx->gid = carve<int>(p, nu + 1); ctx->sid = carve<int>(p, nu + 1); ctx->off = carve<int>(p, nu + 1);
     ctx->infc = carve<int>(p, nu + 1); ctx->fx = carve<int>(p, nu + 1); ctx->lab = carve<int>(p, nu + 1);
     ctx->rflag = carve<int>(p, nu + 1); ctx->color = carve<int>(p, nu + 1); ctx->scc = carve<int>(p, nu + 1);
@@ -238,6 +240,7 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     // idle state: dist = lid = -1
     CK(cudaMemsetAsync(ctx->dist, 0xFF, sizeof(int) * (size_t)nn, ctx->stream));
     CK(cudaMemsetAsync(ctx->lid, 0xFF, sizeof(int) * (size_t)nn, ctx->stream));
+    CK(cudaMemsetAsync(ctx->cbits, 0, sizeof(unsigned int) * (size_t)(nn / 32 + 2), ctx->stream));
     ctx->graph_valid = false;
     return ensure_reps(ctx, rr);
 }
@@ -288,7 +291,7 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.npairs = P;
     w.nsides = 2 * P;
     w.total_n = n;
-    w.vq_v = ctx->vq_v; w.vq_s = ctx->vq_s; w.vq_cap = ctx->n_cap;
+    w.vq_v = ctx->vq_v; w.vq_s = ctx->vq_s; w.vq_cap = ctx->n_cap; w.cbits = ctx->cbits;
     w.gid = ctx->gid; w.sid = ctx->sid; w.off = ctx->off; w.head = ctx->head; w.rev = ctx->rev; w.res = ctx->res;
     w.cap = ctx->cap; w.infc = ctx->infc; w.fx = ctx->fx; w.lab = ctx->lab; w.rflag = ctx->rflag;
     w.color = ctx->color; w.scc = ctx->scc; w.vc = ctx->vc; w.ex = ctx->ex; w.border = ctx->border;
@@ -372,9 +375,9 @@ extern "C" fr_status fr_create(fr_ctx **out, int32_t device, size_t arena_bytes,
     if (step_max_grid(512, 64, &maxb, &sms) != cudaSuccess) { delete ctx; return FR_ERR_CUDA; }
     ctx->sms = sms;
     ctx->max_coop = std::max(maxb, 1) * 4;
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) {
         int mc = 0;
-        if (cluster_flow_capacity(4 << t, &mc) != cudaSuccess) {
+        if (cluster_flow_capacity(fr_ctx::kClusterSizes[t], &mc) != cudaSuccess) {
             cudaGetLastError();
             mc = 0;
         }
@@ -455,9 +458,13 @@ fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *
             return FR_ERR_INVALID_ARG;
         }
         if (opt->mb_reps > 64) { ctx_error(ctx, "mb_reps > 64"); return FR_ERR_INVALID_ARG; }
-        if (opt->cluster_ctas != 0 && opt->cluster_ctas != 4 && opt->cluster_ctas != 8 && opt->cluster_ctas != 16) {
-            ctx_error(ctx, "cluster_ctas must be 0, 4, 8 or 16");
-            return FR_ERR_INVALID_ARG;
+        if (opt->cluster_ctas != 0) {
+            bool known = false;
+            for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) known |= opt->cluster_ctas == fr_ctx::kClusterSizes[t];
+            if (!known) {
+                ctx_error(ctx, "cluster_ctas must be 0, 4, 6, 8, 12 or 16");
+                return FR_ERR_INVALID_ARG;
+            }
         }
     }
     return FR_OK;
@@ -522,39 +529,41 @@ fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k,
 fr_status reset_idle(fr_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->dist, 0xFF, sizeof(int) * (size_t)ctx->n_cap, ctx->stream));
     CK(cudaMemsetAsync(ctx->lid, 0xFF, sizeof(int) * (size_t)ctx->n_cap, ctx->stream));
+    CK(cudaMemsetAsync(ctx->cbits, 0, sizeof(unsigned int) * (size_t)(ctx->n_cap / 32 + 2), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return FR_OK;
 }
 
 // Cluster launches of one round's max flows: tier 0 with the smallest cluster that
 // holds the estimated largest network (or opt->cluster_ctas), then, if tier 0 was
-// smaller than 16 CTAs, tier 1 with 16-CTA clusters for the pairs that did not fit
-// (it returns at once when there are none).  Returns the launches enqueued in *nl.
+// smaller than the largest size, tier 1 with the largest clusters for the pairs that
+// did not fit (it returns at once when there are none).  Smaller clusters let more
+// pairs of a round run at once.  Returns the launches enqueued in *nl.
 cudaError_t launch_clusters(fr_ctx *ctx, Work &w, long long est_pair_vertices, double avg_degree, int force,
                             cudaStream_t st, int *nl) {
     *nl = 0;
-    // shared memory a pair needs: ~29 B per vertex and 20 B per arc, plus slack for
-    // an uneven split; a CTA has cluster_flow_smem() bytes
-    const double need = 1.15 * (double)est_pair_vertices * (29.0 + 20.0 * avg_degree);
-    const double per_cta = 0.9 * (double)cluster_flow_smem();
-    int t0 = -1;
-    for (int t = 0; t < 3; ++t) {
+    const int T = fr_ctx::kNumClusterSizes;
+    // shared memory a pair needs: ~29 B per vertex and 20 B per arc, plus a little
+    // for an uneven split; a CTA has cluster_flow_smem() bytes
+    const double need = 1.05 * (double)est_pair_vertices * (29.0 + 20.0 * avg_degree);
+    const double per_cta = 0.95 * (double)cluster_flow_smem();
+    int t0 = -1, tmax = -1;
+    for (int t = 0; t < T; ++t) {
         if (ctx->cl_cap[t] <= 0) continue;
-        if (force == (4 << t)) { t0 = t; break; }
-        if (force == 0 && t0 < 0 && need <= per_cta * (4 << t)) t0 = t;
+        tmax = t;
+        const int c = fr_ctx::kClusterSizes[t];
+        if (force == c && t0 < 0) t0 = t;
+        if (force == 0 && t0 < 0 && need <= per_cta * c) t0 = t;
     }
-    if (t0 < 0) {   // nothing fits the estimate (or the forced size is unavailable): the largest
-        for (int t = 2; t >= 0 && t0 < 0; --t)
-            if (ctx->cl_cap[t] > 0) t0 = t;
-    }
+    if (t0 < 0) t0 = tmax;   // nothing fits the estimate (or the forced size is unavailable)
     if (t0 < 0) return cudaErrorInvalidValue;
     w.cl_tier = 0;
-    cudaError_t e = launch_cluster_flow(w, 4 << t0, ctx->cl_cap[t0], st);
+    cudaError_t e = launch_cluster_flow(w, fr_ctx::kClusterSizes[t0], ctx->cl_cap[t0], st);
     if (e != cudaSuccess) return e;
     ++*nl;
-    if (t0 < 2 && ctx->cl_cap[2] > 0) {
+    if (t0 < tmax) {
         w.cl_tier = 1;
-        e = launch_cluster_flow(w, 16, ctx->cl_cap[2], st);
+        e = launch_cluster_flow(w, fr_ctx::kClusterSizes[tmax], ctx->cl_cap[tmax], st);
         w.cl_tier = 0;
         if (e != cudaSuccess) return e;
         ++*nl;

@@ -29,9 +29,11 @@ struct fr_ctx {
     char *h_stage = nullptr;
     // launch shape (fr_autotune writes these)
     int tune_tpb = 512, tune_grid = 0, tune_gr = 16, tune_inner = 2, tune_passes = 2;
-    // per-pair max flow in thread-block clusters of 4, 8 or 16 CTAs: how many of each
-    // can be resident (all 0: grid-wide path only); max_clusters = the largest
-    int cl_cap[3] = {0, 0, 0};
+    // per-pair max flow in thread-block clusters of kClusterSizes[t] CTAs: how many of
+    // each can be resident (all 0: grid-wide path only); max_clusters = the largest
+    static constexpr int kNumClusterSizes = 5;
+    static constexpr int kClusterSizes[kNumClusterSizes] = {4, 6, 8, 12, 16};
+    int cl_cap[kNumClusterSizes] = {0, 0, 0, 0, 0};
     int max_clusters = 0;
     int round_launches = 0;   // kernels the last launch_round enqueued
     // graph-size workspace
@@ -39,6 +41,7 @@ struct fr_ctx {
     size_t base_bytes = 0;
     int n_cap = 0, nnz_cap = 0, k_cap = 0, reps_cap = 0;
     int *dist = nullptr, *lid = nullptr, *vq_v = nullptr, *vq_s = nullptr;
+    unsigned int *cbits = nullptr;
     int *gid = nullptr, *sid = nullptr, *off = nullptr, *infc = nullptr, *fx = nullptr, *lab = nullptr;
     int *rflag = nullptr, *color = nullptr, *scc = nullptr, *vc = nullptr, *fq0 = nullptr, *fq1 = nullptr;
     int *spare = nullptr;

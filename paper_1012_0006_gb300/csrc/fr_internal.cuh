@@ -139,6 +139,7 @@ struct Work {
     // visit list
     int *vq_v, *vq_s;
     int vq_cap;
+    unsigned int *cbits;         // one bit per vertex of the graphs (base + v): corridor marks, zero between phases
     // union network
     int *gid, *sid, *off, *head, *rev, *res, *cap, *infc, *fx, *lab, *rflag, *color, *scc, *vc;
     long long *ex;

@@ -26,6 +26,7 @@ constexpr size_t al(size_t b) { return (b + 255) / 256 * 256; }
 // Bytes of every carved array, in carving order (must match carve_all below).
 constexpr size_t kNaBytes =
     4 * al(4ull * kNaMaxN) +                                  // dist lid vq_v vq_s
+    al(4ull * (kNaMaxN / 32 + 2)) +                           // cbits
     21 * al(4ull * (kNaMaxN + 1)) +                           // union vertex arrays
     2 * al(8ull * kNaMaxN) + 2 * al(1ull * kNaMaxN) +         // ex cw / border side_out
     5 * al(4ull * kNaMaxNNZ) +                                // head rev res cap outs
@@ -41,6 +42,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 struct Scratch {
     int *dist, *lid, *vq_v, *vq_s;
+    unsigned int *cbits;
     int *gid, *sid, *off, *infc, *fx, *lab, *rflag, *color, *scc, *vc, *fq0, *fq1, *spare;
     int *cpair, *cmin, *cid, *indeg, *outoff, *ocur, *plist, *sinkc;
     long long *ex, *cw;
@@ -73,6 +75,7 @@ T *take(char *&p, size_t count) {
 void carve_all(char *p, Scratch &s) {
     const size_t N = kNaMaxN, N1 = kNaMaxN + 1, M = kNaMaxNNZ, R = kNaMaxReps;
     s.dist = take<int>(p, N); s.lid = take<int>(p, N); s.vq_v = take<int>(p, N); s.vq_s = take<int>(p, N);
+    s.cbits = take<unsigned int>(p, N / 32 + 2);
     int **v21[21] = {&s.gid, &s.sid, &s.off, &s.infc, &s.fx, &s.lab, &s.rflag, &s.color, &s.scc, &s.vc, &s.fq0,
                      &s.fq1, &s.spare, &s.cpair, &s.cmin, &s.cid, &s.indeg, &s.outoff, &s.ocur, &s.plist, &s.sinkc};
     for (auto a : v21) *a = take<int>(p, N1);
@@ -153,7 +156,7 @@ static fr_status na_iteration(const Scratch &S, const fr_graph *g, int32_t *part
     w.graphs = S.graph; w.pairs = S.pair; w.sides = S.sides; w.pacc = S.pacc; w.ctl = S.ctl;
     w.prev_err = nullptr;
     w.ngraphs = 1; w.npairs = 1; w.nsides = 2; w.total_n = g->n;
-    w.vq_v = S.vq_v; w.vq_s = S.vq_s; w.vq_cap = kNaMaxN;
+    w.vq_v = S.vq_v; w.vq_s = S.vq_s; w.vq_cap = kNaMaxN; w.cbits = S.cbits;
     w.gid = S.gid; w.sid = S.sid; w.off = S.off; w.head = S.head; w.rev = S.rev; w.res = S.res; w.cap = S.cap;
     w.infc = S.infc; w.fx = S.fx; w.lab = S.lab; w.rflag = S.rflag; w.color = S.color; w.scc = S.scc;
     w.vc = S.vc; w.ex = S.ex; w.border = S.border; w.side_out = S.side_out;
@@ -235,6 +238,7 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
     memset(&po, 0, sizeof(po));
     if (cudaMemsetAsync(S.dist, 0xFF, sizeof(int) * g->n, s) != cudaSuccess ||
         cudaMemsetAsync(S.lid, 0xFF, sizeof(int) * g->n, s) != cudaSuccess ||
+        cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (g->n / 32 + 2), s) != cudaSuccess ||
         cudaMemsetAsync(S.prep, 0, sizeof(PrepOut), s) != cudaSuccess ||
         cudaMemsetAsync(S.blockw, 0, sizeof(long long) * k, s) != cudaSuccess ||
         launch_prep(g->xadj, g->adjncy, g->adjwgt, g->vwgt, part, g->n, g->nnz, k, S.blockw, nullptr, S.prep, s) !=

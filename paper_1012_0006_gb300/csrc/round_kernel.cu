@@ -493,21 +493,33 @@ struct StepKernel {
     }
 
     // -------------------------------------------------------------- local ids --
+    // Union ids in increasing (base + v) order: the corridor vertices, found on the
+    // visit list, set their bit in cbits; a scan over the words (popcounts, then
+    // the set bits of each word in order) numbers them and clears the words again.
+    // The SCC labels rely on this order (smallest local id = smallest global id).
     __device__ bool lids() {
         unsigned long long t0 = globaltimer();
+        for (long long e = G.tid; e < vtotal; e += G.size) {
+            const int v = w.vq_v[e], s = w.vq_s[e];
+            const GraphDev &Gr = w.graphs[w.pairs[s >> 1].g];
+            if (in_corridor(Gr, v)) {
+                const long long x = Gr.base + v;
+                atomicOr(&w.cbits[x >> 5], 1u << (x & 31));
+            }
+        }
+        if (!grid_sync(w.ctl)) return false;
         long long nu = 0;
+        const long long nwords = (w.total_n + 31) >> 5;
         bool ok = grid_scan<TPB>(
-            w, w.total_n,
-            [&](long long x) -> int {
-                const int g = graph_of(x);
-                const GraphDev &Gr = w.graphs[g];
-                return in_corridor(Gr, (int)(x - Gr.base)) ? 1 : 0;
-            },
+            w, nwords, [&](long long x) -> int { return __popc(__ldcg(&w.cbits[x])); },
             [&](long long x, long long off) {
-                const int g = graph_of(x);
-                const GraphDev &Gr = w.graphs[g];
-                const int v = (int)(x - Gr.base);
-                if (in_corridor(Gr, v)) {
+                unsigned m = __ldcg(&w.cbits[x]);
+                if (!m) return;
+                w.cbits[x] = 0;
+                for (; m; m &= m - 1) {
+                    const long long y = (x << 5) + (__ffs(m) - 1);
+                    const GraphDev &Gr = w.graphs[graph_of(y)];
+                    const int v = (int)(y - Gr.base);
                     if (off < w.nu_cap) {
                         Gr.lid[v] = (int)off;
                         w.gid[off] = v;
@@ -515,6 +527,7 @@ struct StepKernel {
                     } else {
                         fail(w.ctl, E_INTERNAL, 30);
                     }
+                    ++off;
                 }
             },
             &nu);

@@ -263,7 +263,7 @@ def test_launch_shapes_give_identical_partitions(F, ctx):
         assert np.array_equal(got, ref), shape
 
 
-@pytest.mark.parametrize("ctas,sched", [(4, 0), (8, 0), (16, 0), (4, 1)])
+@pytest.mark.parametrize("ctas,sched", [(4, 0), (6, 0), (8, 0), (12, 0), (16, 0), (4, 1)])
 def test_cluster_sizes_parity(F, ctx, ctas, sched):
     """Each first-tier cluster size (and the wave schedule) against the oracle."""
     _check_batch(F, ctx, I.config(4, scale=1 / 16), dict(cluster_ctas=ctas, flow_sched=sched))
