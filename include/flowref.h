@@ -232,8 +232,9 @@ typedef struct fr_profile_info {
     int64_t pushes;           /* pushes */
     int64_t scc_rounds;       /* SCC colouring rounds */
     int64_t barriers;         /* grid barriers passed by the persistent kernels */
-    double cluster_phase_ms[4]; /* cluster kernel timers summed over pairs: member scan and load,
-                                   flow to t, return of excess to s, residual reachability */
+    double cluster_phase_ms[5]; /* cluster kernel timers summed over pairs: member scan and load,
+                                   flow to t, return of excess to s, residual reachability,
+                                   residual SCCs (most balanced cuts) */
     int64_t cluster_syncs;    /* cluster barriers, summed over pairs */
     int64_t cluster_remote_arcs; /* arcs held in a cluster whose head another CTA holds (DSMEM) */
     int64_t fallback_pairs;   /* pairs left to the grid-wide flow */

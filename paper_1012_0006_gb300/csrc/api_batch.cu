@@ -227,7 +227,9 @@ extern "C" fr_status fr_extract_cut(fr_ctx *ctx, fr_corridor *c, int32_t most_ba
     h[0] = mbv;
     CK(cudaMemcpyAsync(&ctx->pairs[0].mb, h, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     Work w = make_work(ctx, 0, 0, 1, c->g.n, &opt);
-    w.cluster_mode = ctx->max_clusters > 0 ? 1 : 0;
+    // the cut kind is chosen only now: the residual sets and SCCs are computed here,
+    // grid-wide, from the flow fr_maxflow left
+    w.cluster_mode = 0;
     w.full_flow = 1;
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max(1, c->nc));
@@ -586,7 +588,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.pushes += C[r].pushes;
             P.scc_rounds += C[r].scc_rounds;
             P.barriers += C[r].barriers;
-            for (int t = 0; t < 4; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
+            for (int t = 0; t < 5; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
             P.cluster_syncs += C[r].cl_syncs;
             P.cluster_remote_arcs += C[r].cl_remote;
             P.fallback_pairs += C[r].fallback;

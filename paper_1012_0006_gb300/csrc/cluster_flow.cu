@@ -51,7 +51,7 @@ struct ClusterFlow {
     ClusterHdr *hdr;
     ClusterHdr *hdr0;          // CTA 0's header
     // local arrays
-    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *href, *rref, *res, *csum;
+    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *cla, *href, *rref, *res, *csum;
     int *hlab;                 // per arc: the label of its head as last published by the head
     unsigned char *bord;
     int rot;                   // rotating counter index (identical in every CTA)
@@ -145,6 +145,7 @@ struct ClusterFlow {
         cofs = reinterpret_cast<int *>(take(4ull * (nvcap + 1)));
         gidx = reinterpret_cast<int *>(take(4ull * nvcap));
         rfl = reinterpret_cast<int *>(take(4ull * nvcap));
+        cla = reinterpret_cast<int *>(take(4ull * nvcap));
         bord = reinterpret_cast<unsigned char *>(take(nvcap));
         href = reinterpret_cast<int *>(take(4ull * nacap));
         rref = reinterpret_cast<int *>(take(4ull * nacap));
@@ -155,7 +156,7 @@ struct ClusterFlow {
 
     static __host__ __device__ size_t bytes_for(int nvcap, int nacap) {
         auto a = [](size_t b) { return (b + 15) / 16 * 16; };
-        return kHdrBytes + 6 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + 5 * a(4ull * nacap);
+        return kHdrBytes + 7 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + 5 * a(4ull * nacap);
     }
 
     __device__ int owner(int k) const {   // CTA whose range holds member k
@@ -347,8 +348,95 @@ struct ClusterFlow {
             if (rfl[lv] == 3) fail(w.ctl, E_INTERNAL, 302);
         }
         sync();
+        // most balanced cut: SCCs of the residual graph on the vertices reached from
+        // neither s nor t (lab, ex, fx are free now)
+        int *sc = fx;
+        if (w.pairs[p].mb) {
+            scc_local(nv, sc);
+        } else {
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) sc[lv] = -2;
+        }
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) w.scc[gidx[lv]] = sc[lv];
+        mark(t1, T_CL_SCC);
+        sync();
         if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->cl_syncs, nsync);
         return true;
+    }
+
+    // SCCs of the residual graph on X = the vertices with rfl == 0, labelled by
+    // their smallest union id (the same labels as the grid-wide colouring): in
+    // rounds, every unassigned vertex takes the smallest union id that reaches it
+    // over unassigned vertices (colour; label correction pushed along residual arcs
+    // with an atomic min), a vertex whose colour is its own id is a root, and the
+    // vertices of its colour that reach it join it: members claim the tails of
+    // their residual in-arcs with an atomic max of their colour, and a vertex
+    // joins when the largest claim it received is its own colour (claims from
+    // other classes are smaller: whatever reaches a vertex reaches its
+    // successors).  sc: -2 outside X, else the root's union id.
+    __device__ void scc_local(int nv, int *sc) {
+        int *col = lab, *done = ex;
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) sc[lv] = rfl[lv] == 0 ? -1 : -2;
+        sync();
+        long long rounds = 0;
+        for (;;) {
+            int rem = 0;
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                const bool un = sc[lv] == -1;
+                col[lv] = un ? gidx[lv] : INT_MAX;
+                done[lv] = un ? INT_MAX : 0;   // colour last passed on
+                cla[lv] = -1;
+                rem += un;
+            }
+            if (cluster_sum(rem) == 0) break;
+            if (++rounds > (long long)nv + 1) {
+                if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_ITER, 303);
+                break;
+            }
+            // colours
+            for (;;) {
+                int nproc = 0;
+                for (int k = 0; k < kScans; ++k) {
+                    for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                        if (sc[lv] != -1) continue;
+                        const int c = *(volatile int *)&col[lv];
+                        if (c >= done[lv]) continue;
+                        done[lv] = c;
+                        ++nproc;
+                        const int a1 = cofs[lv + 1];
+                        for (int a = cofs[lv]; a < a1; ++a)
+                            if (res[a] > 0) atomicMin(at(col, href[a]), c);
+                    }
+                }
+                if (cluster_sum(nproc) == 0) break;
+            }
+            // roots, then members claim the vertices of their colour that reach them
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                done[lv] = sc[lv] == -1 ? 0 : 1;   // 1: nothing to pass on
+                if (sc[lv] == -1 && col[lv] == gidx[lv]) sc[lv] = gidx[lv];
+            }
+            sync();
+            for (;;) {
+                int nproc = 0;
+                for (int k = 0; k < kScans; ++k) {
+                    for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                        if (done[lv]) continue;
+                        int s = sc[lv];
+                        if (s == -1) {
+                            if (*(volatile int *)&cla[lv] != col[lv]) continue;
+                            s = col[lv];
+                            sc[lv] = s;
+                        }
+                        done[lv] = 1;
+                        ++nproc;
+                        const int a1 = cofs[lv + 1];
+                        for (int a = cofs[lv]; a < a1; ++a)
+                            if (csum[a] > res[a]) atomicMax(at(cla, href[a]), s);
+                    }
+                }
+                if (cluster_sum(nproc) == 0) break;
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) atomicAdd(&w.ctl->scc_rounds, (int)rounds);
     }
 
     static constexpr int kScans = 4;   // local scans between cluster barriers (relabel, reach)

@@ -990,6 +990,7 @@ struct StepKernel {
         Ctl *ctl = w.ctl;
         unsigned long long t0 = globaltimer();
         const int nu = __ldcg(&ctl->nu);
+        if (w.cluster_mode && __ldcg(&ctl->fallback) == 0) return true;   // the clusters wrote scc
         for (long long i = G.tid; i < nu; i += G.size) {
             const bool mbp = w.pairs[w.sid[i] >> 1].mb != 0;
             w.scc[i] = (mbp && __ldcg(&w.rflag[i]) == 0) ? -1 : -2;

@@ -69,7 +69,7 @@ class ProfileInfo(ctypes.Structure):
                 ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
                 ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64), ("barriers", ctypes.c_int64),
-                ("cluster_phase_ms", ctypes.c_double * 4), ("cluster_syncs", ctypes.c_int64),
+                ("cluster_phase_ms", ctypes.c_double * 5), ("cluster_syncs", ctypes.c_int64),
                 ("cluster_remote_arcs", ctypes.c_int64),
                 ("fallback_pairs", ctypes.c_int64)]
 
@@ -79,7 +79,7 @@ class ProfileInfo(ctypes.Structure):
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("phase_ms", "cluster_phase_ms")}
         d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
-        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach"), list(self.cluster_phase_ms)))
+        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach", "scc"), list(self.cluster_phase_ms)))
         return d
 
 
