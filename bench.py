@@ -196,21 +196,22 @@ def recorded_traffic(kernel):
 
 
 def bytes_model(P):
-    """Algorithmic bytes per kernel type for one sweep (element bytes the method must touch)."""
+    """Algorithmic HBM bytes per kernel type for one sweep (element bytes the method must touch)."""
     n, nnz = P["n"], P["nnz"]
     scan = (8 * n + 8 * nnz + 4) * P["nrounds"]            # xadj, part[v], adjncy, part[u]
     vis, arcs = P["bfs_visited"], P["bfs_arcs"]
     nc, m = P["corridor_n"], P["corridor_arcs"]
-    bfs = 16 * vis + 12 * arcs
-    select = 4 * 8 * vis
-    lid = (2 * 4 * n) * P["nrounds"] + 12 * nc
-    build = 12 * nc + 28 * m
-    flow = 12 * P["pr_arcs"] + 24 * P["pushes"] + 12 * P["gr_arcs"]
-    cut = 2 * (12 * m + 8 * nc)
-    step = bfs + select + lid + build + flow + cut
-    # cluster kernel: member scan of the union per pair, load of the network, write-back
-    cluster = 32 * nc + 28 * m + 8 * m + 16 * nc
-    return dict(scan=scan, step=step, bfs=bfs, relabel=12 * P["gr_arcs"], flow=flow, build=build, cluster=cluster)
+    bfs = 16 * vis + 12 * arcs                              # queue entries, dist, adjncy + part + dist per arc
+    select = 4 * 8 * vis                                    # four radix passes over the overflow levels
+    lid = 12 * vis + (n // 8) * P["nrounds"] + 12 * nc      # marks, bitmap words, gid/sid/lid
+    build = 12 * nc + 28 * m                                # rows, head, rev, res, cap, ranks
+    cut = 24 * nc                                           # DAG of components, sweeps, eval, commit
+    step = bfs + select + lid + build + cut
+    # cluster kernel: network in (vertex 32 B: ids, offsets, excess, flow, border;
+    # arc 24 B: head, reverse, residual, both capacities), results out (vertex 20 B,
+    # arc residual 4 B)
+    cluster = 52 * nc + 28 * m
+    return dict(scan=scan, step=step, bfs=bfs, build=build, cluster=cluster)
 
 
 # ------------------------------------------------------------------ ours ----
@@ -236,7 +237,8 @@ def run_ours(args, world, rank, local, pg):
         t0 = time.time()
         best, ms = ctx.autotune(g, part0, k, eps, alpha, opts, trials=1)
         tuned = dict(block_threads=best.block_threads, grid_blocks=best.grid_blocks, gr_interval=best.gr_interval,
-                     inner_ops=best.inner_ops, pulse_passes=best.pulse_passes, ms=round(ms, 3))
+                     inner_ops=best.inner_ops, pulse_passes=best.pulse_passes, cluster_ctas=best.cluster_ctas,
+                     ms=round(ms, 3))
         log(f"[rank {rank}] autotune {tuned} in {time.time() - t0:.1f}s")
 
     def step():
@@ -304,14 +306,18 @@ def run_ours(args, world, rank, local, pg):
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dominant,
                 "peak_kind": peak_kind, "bytes_per_launch": int(byts / nl), "launch_ms": round(ms / nl, 4)}
     ph = P["phase_ms"]
+    # wall time of the max flows: the cluster kernels (flow, reach and SCCs of every
+    # pair) plus the grid-wide flow phases of pairs left to them
     flow_ms = clu_ms + ph["flow"] + ph["relabel"] + ph["return"]
     arcs_rate = reduce_sum(pg, P["corridor_arcs"] / max(flow_ms * 1e-3, 1e-12), dev)
     kernels.update({
         "phases_ms": {kk: round(v, 3) for kk, v in ph.items()},
         "bfs_gbs": round(bm["bfs"] / max(ph["bfs"] * 1e-3, 1e-12) / 1e9, 1),
+        "cluster_phases_ms_summed_over_pairs": {kk: round(v, 3) for kk, v in P["cluster_phase_ms"].items()},
         "counters": {kk: P[kk] for kk in ("bfs_visited", "bfs_arcs", "corridor_n", "corridor_arcs", "pulses",
                                            "relabels", "gr_arcs", "pr_arcs", "pushes", "scc_rounds",
-                                           "barriers")},
+                                           "barriers", "cluster_syncs", "cluster_remote_arcs",
+                                           "fallback_pairs")},
     })
 
     # end to end through the host-buffer entry point: H2D of graph and part, D2H of part

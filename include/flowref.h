@@ -248,9 +248,10 @@ fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info);
 /* ---- launch-shape autotuner -------------------------------------------------- */
 
 /* Times fr_refine_batch on a copy of part for a set of launch shapes
- * (block_threads, grid_blocks, gr_interval, inner_ops) and writes the fastest into
- * *best.  Results are identical for every shape; only time differs.  The choice is
- * also cached in the context and used when opt fields are 0. */
+ * (block_threads, grid_blocks, gr_interval, inner_ops, pulse_passes, cluster_ctas;
+ * coordinate descent, two sweeps) and writes the fastest into *best.  Results are
+ * identical for every shape; only time differs.  The choice is also cached in the
+ * context and used when opt fields are 0. */
 fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, double eps, double alpha,
                       const fr_options *opt, int32_t trials, fr_options *best, double *best_ms);
 

@@ -624,7 +624,8 @@ static fr_status run_pair_iteration(fr_ctx *ctx, const fr_graph *g, int32_t *par
     const int grid = choose_grid(ctx, opt, tpb, 2, est);
     const bool vec = ((reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0);
     CK(launch_scan(w, 0, g->n, vec, ctx->stream));
-    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, est, (double)g->nnz / g->n, opt ? opt->cluster_ctas : 0));
+    CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, est, (double)g->nnz / g->n,
+                    opt && opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
     char *h = ctx->h_stage + 2048;
     CK(cudaMemcpyAsync(h, ctx->pacc, sizeof(PairAcc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(h + 512, ctx->sides, 2 * sizeof(SideDev), cudaMemcpyDeviceToHost, ctx->stream));

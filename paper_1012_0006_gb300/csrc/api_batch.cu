@@ -346,7 +346,7 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
         CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr, pl.est_max[r], pl.avg_degree,
-                        opt->cluster_ctas));
+                        opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
         nl += 1 + ctx->round_launches;
     }
     ctx->sweep_launches = nl;
@@ -375,7 +375,7 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
         CK(launch_scan(w, 0, g->n, vec, ctx->stream));
         CK(cudaEventRecord(ctx->pev[8 * r + 1], ctx->stream));
         CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, &ctx->pev[8 * r + 2], pl.est_max[r],
-                        pl.avg_degree, opt->cluster_ctas));
+                        pl.avg_degree, opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
         nl += 1 + ctx->round_launches;
     }
     ctx->sweep_launches = nl;
@@ -405,7 +405,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   opt->gr_interval, opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
-                                  opt->flow_sched, opt->cluster_ctas};
+                                  opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
@@ -746,9 +746,18 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     const std::vector<int> grs = {2, 4, 8, 16, 32};
     const std::vector<int> inners = {1, 2, 4, 8};
     const std::vector<int> passes = {1, 2, 4, 8};
+    std::vector<int> ctas = {0};
+    for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t)
+        if (ctx->cl_cap[t] > 0) ctas.push_back(fr_ctx::kClusterSizes[t]);
+    cand.cluster_ctas = base.cluster_ctas ? base.cluster_ctas : ctx->tune_ctas;
     for (int sweep = 0; sweep < 2 && st == FR_OK; ++sweep) {
-        for (int dim = 0; dim < 5 && st == FR_OK; ++dim) {
-            const std::vector<int> &vals = dim == 0 ? tpbs : dim == 1 ? grids : dim == 2 ? grs : dim == 3 ? inners : passes;
+        for (int dim = 0; dim < 6 && st == FR_OK; ++dim) {
+            const std::vector<int> &vals = dim == 0   ? tpbs
+                                           : dim == 1 ? grids
+                                           : dim == 2 ? grs
+                                           : dim == 3 ? inners
+                                           : dim == 4 ? passes
+                                                      : ctas;
             for (int v : vals) {
                 fr_options o = cand;
                 if (dim == 0) o.block_threads = v;
@@ -756,6 +765,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
                 if (dim == 2) o.gr_interval = v;
                 if (dim == 3) o.inner_ops = v;
                 if (dim == 4) o.pulse_passes = v;
+                if (dim == 5) o.cluster_ctas = v;
                 if (memcmp(&o, &cand, sizeof(o)) == 0) continue;
                 double ms = 0;
                 st = time_shape(o, &ms);
@@ -771,6 +781,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     ctx->tune_gr = cand.gr_interval;
     ctx->tune_inner = cand.inner_ops;
     ctx->tune_passes = cand.pulse_passes;
+    ctx->tune_ctas = cand.cluster_ctas;
     if (best) *best = cand;
     if (best_ms) *best_ms = bms;
     return FR_OK;

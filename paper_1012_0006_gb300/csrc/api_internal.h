@@ -29,6 +29,7 @@ struct fr_ctx {
     char *h_stage = nullptr;
     // launch shape (fr_autotune writes these)
     int tune_tpb = 512, tune_grid = 0, tune_gr = 16, tune_inner = 2, tune_passes = 2;
+    int tune_ctas = 0;   // first cluster size (0: by the estimated corridor size)
     // per-pair max flow in thread-block clusters of kClusterSizes[t] CTAs: how many of
     // each can be resident (all 0: grid-wide path only); max_clusters = the largest
     static constexpr int kNumClusterSizes = 5;

@@ -352,7 +352,7 @@ struct ClusterFlow {
         // neither s nor t (lab, ex, fx are free now)
         int *sc = fx;
         if (w.pairs[p].mb) {
-            scc_local(nv, sc);
+            scc_local(nv, V, sc);
         } else {
             for (int lv = threadIdx.x; lv < nv; lv += TPB) sc[lv] = -2;
         }
@@ -373,7 +373,9 @@ struct ClusterFlow {
     // joins when the largest claim it received is its own colour (claims from
     // other classes are smaller: whatever reaches a vertex reaches its
     // successors).  sc: -2 outside X, else the root's union id.
-    __device__ void scc_local(int nv, int *sc) {
+    // V, the pair's vertex count, bounds the rounds: the same bound in every CTA, so
+    // that every CTA leaves the loop after the same barrier.
+    __device__ void scc_local(int nv, int V, int *sc) {
         int *col = lab, *done = ex;
         for (int lv = threadIdx.x; lv < nv; lv += TPB) sc[lv] = rfl[lv] == 0 ? -1 : -2;
         sync();
@@ -388,7 +390,7 @@ struct ClusterFlow {
                 rem += un;
             }
             if (cluster_sum(rem) == 0) break;
-            if (++rounds > (long long)nv + 1) {
+            if (++rounds > (long long)V + 1) {
                 if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_ITER, 303);
                 break;
             }

@@ -263,6 +263,16 @@ def test_launch_shapes_give_identical_partitions(F, ctx):
         assert np.array_equal(got, ref), shape
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_tiny_networks_in_large_clusters(F, ctx, seed):
+    """Small corridors in 16-CTA clusters: most CTAs hold no vertex, and most
+    balanced cuts take several colouring rounds; every CTA must leave each loop
+    after the same barrier."""
+    w = I.random_small(5000 + seed, n_max=300, k_max=6)
+    w["mb"] = 1
+    _check_batch(F, ctx, w, dict(mb_reps=2, seed=seed, cluster_ctas=16))
+
+
 @pytest.mark.parametrize("ctas,sched", [(4, 0), (6, 0), (8, 0), (12, 0), (16, 0), (4, 1)])
 def test_cluster_sizes_parity(F, ctx, ctas, sched):
     """Each first-tier cluster size (and the wave schedule) against the oracle."""
