@@ -76,7 +76,8 @@ typedef struct fr_options {
     int32_t gr_interval;   /* pulses between global relabels; 0 = tuned default */
     int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
     int32_t pulse_passes;  /* lock-free pulse passes between grid barriers; 0 = default */
-    int32_t flow_sched;    /* per-pair cluster max flow: 0 lock-free pulses, 1 level-ordered waves */
+    int32_t flow_sched;    /* per-pair cluster max flow: 1 level-ordered waves, 2 lock-free pulses;
+                              0 = tuned default (pulses unless fr_autotune chose waves) */
     int32_t cluster_ctas;  /* CTAs of the first per-pair cluster launch (4, 6, 8, 12 or 16); 0 = by the
                               estimated corridor size.  Pairs that do not fit go to 16-CTA
                               clusters, then to the grid-wide flow; results do not depend on it */
@@ -248,7 +249,7 @@ fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info);
 /* ---- launch-shape autotuner -------------------------------------------------- */
 
 /* Times fr_refine_batch on a copy of part for a set of launch shapes
- * (block_threads, grid_blocks, gr_interval, inner_ops, pulse_passes, cluster_ctas;
+ * (block_threads, grid_blocks, gr_interval, inner_ops, pulse_passes, cluster_ctas, flow_sched;
  * coordinate descent, two sweeps) and writes the fastest into *best.  Results are
  * identical for every shape; only time differs.  The choice is also cached in the
  * context and used when opt fields are 0. */

@@ -309,7 +309,7 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.gr_interval = opt && opt->gr_interval > 0 ? opt->gr_interval : ctx->tune_gr;
     w.inner = opt && opt->inner_ops > 0 ? opt->inner_ops : ctx->tune_inner;
     w.passes = opt && opt->pulse_passes > 0 ? opt->pulse_passes : ctx->tune_passes;
-    w.flow_sched = opt ? opt->flow_sched : 0;
+    w.flow_sched = opt && opt->flow_sched ? opt->flow_sched : ctx->tune_sched;
     w.any_mb = opt && opt->mb ? 1 : 0;
     w.seed = opt ? opt->seed : 0;
     w.pulse_cap = opt && opt->pulse_cap > 0 ? opt->pulse_cap : (1LL << 20);

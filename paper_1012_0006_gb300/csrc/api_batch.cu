@@ -405,7 +405,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   opt->gr_interval, opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
-                                  opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas};
+                                  opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas, ctx->tune_sched};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
@@ -750,14 +750,17 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t)
         if (ctx->cl_cap[t] > 0) ctas.push_back(fr_ctx::kClusterSizes[t]);
     cand.cluster_ctas = base.cluster_ctas ? base.cluster_ctas : ctx->tune_ctas;
+    cand.flow_sched = base.flow_sched ? base.flow_sched : (ctx->tune_sched ? ctx->tune_sched : 2);
+    const std::vector<int> scheds = {2, 1};
     for (int sweep = 0; sweep < 2 && st == FR_OK; ++sweep) {
-        for (int dim = 0; dim < 6 && st == FR_OK; ++dim) {
+        for (int dim = 0; dim < 7 && st == FR_OK; ++dim) {
             const std::vector<int> &vals = dim == 0   ? tpbs
                                            : dim == 1 ? grids
                                            : dim == 2 ? grs
                                            : dim == 3 ? inners
                                            : dim == 4 ? passes
-                                                      : ctas;
+                                           : dim == 5 ? ctas
+                                                      : scheds;
             for (int v : vals) {
                 fr_options o = cand;
                 if (dim == 0) o.block_threads = v;
@@ -766,6 +769,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
                 if (dim == 3) o.inner_ops = v;
                 if (dim == 4) o.pulse_passes = v;
                 if (dim == 5) o.cluster_ctas = v;
+                if (dim == 6) o.flow_sched = v;
                 if (memcmp(&o, &cand, sizeof(o)) == 0) continue;
                 double ms = 0;
                 st = time_shape(o, &ms);
@@ -782,6 +786,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     ctx->tune_inner = cand.inner_ops;
     ctx->tune_passes = cand.pulse_passes;
     ctx->tune_ctas = cand.cluster_ctas;
+    ctx->tune_sched = cand.flow_sched;
     if (best) *best = cand;
     if (best_ms) *best_ms = bms;
     return FR_OK;

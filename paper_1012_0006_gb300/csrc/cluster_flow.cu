@@ -84,6 +84,27 @@ struct ClusterFlow {
     }
 
 
+    // Runs f(src, gl, G) once on every lane for the flagged vertices among this
+    // warp's 32 (flag is the lane's own vertex, base + lane).  Up to eight flagged:
+    // group g = lane / 4 takes the g-th of them, src = its lane (-1: none for this
+    // group), gl = lane % 4 the lane's place in the group, G = 4, so a vertex's arcs
+    // are walked four at a time.  More than eight: each lane takes its own vertex
+    // (src = lane or -1, gl = 0, G = 1).  f gets per-vertex values from lane src with
+    // __shfl_sync on all lanes before it tests src.
+    template <class Fn>
+    __device__ __forceinline__ void for_flagged(bool flag, Fn f) const {
+        const int lane = threadIdx.x & 31;
+        const unsigned m = __ballot_sync(FULL, flag);
+        if (!m) return;
+        if (__popc(m) > 8) {
+            f(flag ? lane : -1, 0, 1);
+            return;
+        }
+        unsigned mm = m;
+        for (int i = 0; i < (lane >> 2); ++i) mm &= mm - 1;
+        f(mm ? __ffs(mm) - 1 : -1, lane & 3, 4);
+    }
+
     // New label h of local vertex lv: its own word and the copies on the reverse
     // arcs of its arcs (the arcs of which lv is the head), local or in other CTAs.
     // The copies may lag; they never run ahead of the label, and labels only rise
@@ -395,18 +416,27 @@ struct ClusterFlow {
                 break;
             }
             // colours
+            const int lane = threadIdx.x & 31;
             for (;;) {
                 int nproc = 0;
                 for (int k = 0; k < kScans; ++k) {
-                    for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                        if (sc[lv] != -1) continue;
-                        const int c = *(volatile int *)&col[lv];
-                        if (c >= done[lv]) continue;
-                        done[lv] = c;
-                        ++nproc;
-                        const int a1 = cofs[lv + 1];
-                        for (int a = cofs[lv]; a < a1; ++a)
-                            if (res[a] > 0) atomicMin(at(col, href[a]), c);
+                    for (int base = threadIdx.x - lane; base < nv; base += TPB) {
+                        const int lv = base + lane;
+                        int c = 0;
+                        bool fl = false;
+                        if (lv < nv && sc[lv] == -1) {
+                            c = *(volatile int *)&col[lv];
+                            fl = c < done[lv];
+                            if (fl) done[lv] = c;
+                        }
+                        nproc += fl;
+                        for_flagged(fl, [&](int src, int gl, int G) {
+                            const int cu = __shfl_sync(FULL, c, src < 0 ? 0 : src);
+                            if (src < 0) return;
+                            const int u = base + src, a1 = cofs[u + 1];
+                            for (int a = cofs[u] + gl; a < a1; a += G)
+                                if (res[a] > 0) atomicMin(at(col, href[a]), cu);
+                        });
                     }
                 }
                 if (cluster_sum(nproc) == 0) break;
@@ -420,19 +450,27 @@ struct ClusterFlow {
             for (;;) {
                 int nproc = 0;
                 for (int k = 0; k < kScans; ++k) {
-                    for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                        if (done[lv]) continue;
-                        int s = sc[lv];
-                        if (s == -1) {
-                            if (*(volatile int *)&cla[lv] != col[lv]) continue;
-                            s = col[lv];
-                            sc[lv] = s;
+                    for (int base = threadIdx.x - lane; base < nv; base += TPB) {
+                        const int lv = base + lane;
+                        int s = -1;
+                        bool fl = false;
+                        if (lv < nv && !done[lv]) {
+                            s = sc[lv];
+                            if (s == -1 && *(volatile int *)&cla[lv] == col[lv]) {
+                                s = col[lv];
+                                sc[lv] = s;
+                            }
+                            fl = s >= 0;
+                            if (fl) done[lv] = 1;
                         }
-                        done[lv] = 1;
-                        ++nproc;
-                        const int a1 = cofs[lv + 1];
-                        for (int a = cofs[lv]; a < a1; ++a)
-                            if (csum[a] > res[a]) atomicMax(at(cla, href[a]), s);
+                        nproc += fl;
+                        for_flagged(fl, [&](int src, int gl, int G) {
+                            const int su = __shfl_sync(FULL, s, src < 0 ? 0 : src);
+                            if (src < 0) return;
+                            const int u = base + src, a1 = cofs[u + 1];
+                            for (int a = cofs[u] + gl; a < a1; a += G)
+                                if (csum[a] > res[a]) atomicMax(at(cla, href[a]), su);
+                        });
                     }
                 }
                 if (cluster_sum(nproc) == 0) break;
@@ -464,19 +502,29 @@ struct ClusterFlow {
         for (int a = threadIdx.x; a < na; a += TPB) hlab[a] = hmax;
         sync();
         long long rounds = 0;
+        const int lane = threadIdx.x & 31;
         for (;;) {
             int nproc = 0;
             for (int k = 0; k < kScans; ++k) {
-                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                    const int L = *(volatile int *)&lab[lv];
-                    if (L >= rfl[lv]) continue;
-                    rfl[lv] = L;
-                    ++nproc;
-                    const int a1 = cofs[lv + 1];
-                    for (int a = cofs[lv]; a < a1; ++a) {
-                        *(volatile int *)at(hlab, rref[a]) = L;
-                        if (csum[a] > res[a]) atomicMin(at(lab, href[a]), L + 1);
+                for (int base = threadIdx.x - lane; base < nv; base += TPB) {
+                    const int lv = base + lane;
+                    int L = 0;
+                    bool fr = false;
+                    if (lv < nv) {
+                        L = *(volatile int *)&lab[lv];
+                        fr = L < rfl[lv];
+                        if (fr) rfl[lv] = L;
                     }
+                    nproc += fr;
+                    for_flagged(fr, [&](int src, int gl, int G) {
+                        const int Lu = __shfl_sync(FULL, L, src < 0 ? 0 : src);
+                        if (src < 0) return;
+                        const int u = base + src, a1 = cofs[u + 1];
+                        for (int a = cofs[u] + gl; a < a1; a += G) {
+                            *(volatile int *)at(hlab, rref[a]) = Lu;
+                            if (csum[a] > res[a]) atomicMin(at(lab, href[a]), Lu + 1);
+                        }
+                    });
                 }
             }
             ++rounds;
@@ -648,21 +696,29 @@ struct ClusterFlow {
             lab[lv] = 0;
         }
         sync();
+        const int lane = threadIdx.x & 31;
         for (;;) {
             int nproc = 0;
             for (int k = 0; k < kScans; ++k) {
-                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                    const int f = *(volatile int *)&rfl[lv], dn = lab[lv];
-                    const int nw = f & ~dn;
-                    if (!nw) continue;
-                    lab[lv] = dn | nw;
-                    ++nproc;
-                    const int a1 = cofs[lv + 1];
-                    for (int a = cofs[lv]; a < a1; ++a) {
-                        const int r = res[a];
-                        const int bits = ((nw & 1) && r > 0 ? 1 : 0) | ((nw & 2) && csum[a] > r ? 2 : 0);
-                        if (bits) atomicOr(at(rfl, href[a]), bits);
+                for (int base = threadIdx.x - lane; base < nv; base += TPB) {
+                    const int lv = base + lane;
+                    int nw = 0;
+                    if (lv < nv) {
+                        const int f = *(volatile int *)&rfl[lv], dn = lab[lv];
+                        nw = f & ~dn;
+                        if (nw) lab[lv] = dn | nw;
                     }
+                    nproc += nw != 0;
+                    for_flagged(nw != 0, [&](int src, int gl, int G) {
+                        const int nwu = __shfl_sync(FULL, nw, src < 0 ? 0 : src);
+                        if (src < 0) return;
+                        const int u = base + src, a1 = cofs[u + 1];
+                        for (int a = cofs[u] + gl; a < a1; a += G) {
+                            const int r = res[a];
+                            const int bits = ((nwu & 1) && r > 0 ? 1 : 0) | ((nwu & 2) && csum[a] > r ? 2 : 0);
+                            if (bits) atomicOr(at(rfl, href[a]), bits);
+                        }
+                    });
                 }
             }
             if (cluster_sum(nproc) == 0) break;

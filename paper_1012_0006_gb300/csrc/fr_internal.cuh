@@ -161,7 +161,7 @@ struct Work {
     // options
     int reps, gr_interval, inner, any_mb;
     int passes, cluster_mode;    // lock-free pulse passes per barrier; 1: the cluster kernel ran the flow
-    int flow_sched;              // cluster max flow: 0 lock-free pulses, 1 level-ordered waves
+    int flow_sched;              // cluster max flow: 1 level-ordered waves, otherwise lock-free pulses
     int cl_tier;                 // cluster launch: 0 every pair, 1 the pairs the first left
     int full_flow;               // 1: return every excess to s (a flow); 0: a maximum preflow
     int pad_w;
