@@ -373,9 +373,10 @@ def run_ours(args, world, rank, local, pg):
 
 # ------------------------------------------------- batched vs one pair per launch ----
 
-def batched_vs_per_pair(F, ctx, dev, reps=3):
+def batched_vs_per_pair(F, ctx0, dev, reps=3):
     """128^3 grid, k = 16: one fr_refine_batch sweep against the same pairs refined by
-    fr_refine_pair one launch at a time, in round order (same results, checked)."""
+    fr_refine_pair one launch at a time, in round order (same results, checked).  Both
+    arms run on one context whose launch shape fr_autotune chose for this workload."""
     import numpy as np
     import torch
     from paper_1012_0006_gb300 import inputs as I
@@ -384,6 +385,8 @@ def batched_vs_per_pair(F, ctx, dev, reps=3):
     part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
     opts = F.default_options(mb=1)
     k, eps, alpha = w["k"], w["eps"], w["alpha"]
+    ctx = F.Context(dev.index if dev.index is not None else 0)
+    best, _ = ctx.autotune(g, part0, k, eps, alpha, opts, trials=1)
     part = part0.clone()
     st, res, summ = ctx.refine_batch(g, part, k, eps, alpha, opts)
     ref = part.clone()
@@ -403,9 +406,13 @@ def batched_vs_per_pair(F, ctx, dev, reps=3):
         tp.append(time.perf_counter() - t0)
         assert torch.equal(part, ref), "one-pair-per-launch result differs from the batch"
     b, p = min(tb), min(tp)
+    ctx.close()
     return {"workload": "grid3d 128^3 k=16 eps=0.03 alpha=2 MB", "pairs": len(pairs),
             "rounds": summ["nrounds"], "batched_ms": round(b * 1e3, 3), "per_pair_ms": round(p * 1e3, 3),
-            "speedup": round(p / b, 2)}
+            "speedup": round(p / b, 2),
+            "launch_shape": dict(flow_sched=best.flow_sched, cluster_ctas=best.cluster_ctas,
+                                 inner_ops=best.inner_ops, gr_interval=best.gr_interval,
+                                 pulse_passes=best.pulse_passes)}
 
 
 # ------------------------------------------------------------------ serving ----

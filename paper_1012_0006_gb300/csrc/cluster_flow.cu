@@ -1,17 +1,21 @@
-// Max flow of each pair inside one thread-block cluster, on distributed shared
-// memory (Sanders & Schulz, Section 4.1: the max-flow problem of the B-corridor
-// network; Section 4.1.1: residual reachability).
+// Max flow, residual sets and SCCs of each pair inside one thread-block cluster, on
+// distributed shared memory (Sanders & Schulz, Section 4.1: the max-flow problem of
+// the B-corridor network; Section 4.1.1: residual reachability and the strongly
+// connected components that represent all minimum cuts).
 //
-// The round's persistent kernel builds every pair's corridor network in HBM.
-// This kernel then gives each pair one cluster of C CTAs: the pair's vertices are
-// split into C contiguous ranges with about equal arc counts, and every CTA loads
-// its range -- labels, excess, s/t-arc flow, CSR offsets, packed head and reverse
-// arc references, residual capacities -- into its shared memory.  Push-relabel
-// in waves (exact labels by pull passes over residual arcs, then the levels top
-// down), the return of excess to s and the reachability sets then run on SMEM, with the cluster's
-// hardware barrier (~0.3 us) instead of a grid barrier (~3 us) and with DSMEM
-// latency instead of L2 latency.  Results go back to HBM for the cut phases.  A
-// pair whose network does not fit is left to the grid-wide path (ctl->fallback).
+// The round's persistent kernel builds every pair's corridor network in HBM.  This
+// kernel then gives each pair one cluster of C CTAs: the pair's vertices are split
+// into C contiguous ranges with about equal arc counts, and every CTA loads its
+// range -- labels, excess, s/t-arc flow, CSR offsets, the shared::cluster addresses
+// of each arc's head label and reverse residual, residual capacities -- into its
+// shared memory.  Push-relabel (lock-free pulses, or waves by levels), the exact
+// relabels, the reachability sets and the SCCs then run on shared memory with the
+// cluster's hardware barrier (~0.3 us) instead of a grid barrier (~3 us).  No CTA
+// reads another's vertex state in these loops: updates travel as remote stores and
+// relaxed reductions into the owner's memory, and each arc keeps a copy of its head's
+// label that the head publishes.  Results go back to HBM for the DAG and sweep
+// phases.  A pair whose network does not fit is left to a second launch with larger
+// clusters, then to the grid-wide path (ctl->fallback).
 #include <cooperative_groups.h>
 
 #include <climits>
@@ -39,9 +43,31 @@ struct ClusterHdr {
     long long flow;
 };
 
-__device__ __forceinline__ int cpack(int r, int i) { return (r << 24) | i; }
-__device__ __forceinline__ int crank(int p) { return (int)((unsigned)p >> 24); }
-__device__ __forceinline__ int cidx(int p) { return p & 0xFFFFFF; }
+// Distributed shared memory by explicit address: a shared::cluster address (32 bits) of an
+// element of some CTA's shared memory, and plain stores / relaxed reductions to it.  Every
+// CTA carves its arrays at the same offsets, so the address of array X at the same index
+// is the address of array Y plus a fixed byte offset.
+__device__ __forceinline__ unsigned cta_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned map_rank(unsigned a, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void dsm_st(unsigned a, int v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_add(unsigned a, int v) {
+    asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_min(unsigned a, int v) {
+    asm volatile("red.shared::cluster.min.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_max(unsigned a, int v) {
+    asm volatile("red.shared::cluster.max.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_or(unsigned a, int v) {
+    asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
 
 template <int TPB>
 struct ClusterFlow {
@@ -51,17 +77,14 @@ struct ClusterFlow {
     ClusterHdr *hdr;
     ClusterHdr *hdr0;          // CTA 0's header
     // local arrays
-    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *cla, *href, *rref, *res, *csum;
+    int *lab, *ex, *fx, *cofs, *gidx, *rfl, *cla, *res, *csum;
+    // per arc: shared::cluster addresses of the head's label (hadr) and of the reverse
+    // arc's residual (radr); other arrays of the same element are a fixed offset away
+    unsigned *hadr, *radr;
+    unsigned o_ex, o_rfl, o_cla, o_hlab;   // byte offsets: ex/rfl/cla from lab, hlab from res
     int *hlab;                 // per arc: the label of its head as last published by the head
     unsigned char *bord;
     int rot;                   // rotating counter index (identical in every CTA)
-
-    // element i of this CTA's array `a`, in the shared memory of CTA r: a plain
-    // shared-memory address when r is this CTA, a DSMEM address otherwise
-    __device__ __forceinline__ int *at(int *a, int packed) const {
-        const int r = crank(packed);
-        return r == rank ? a + cidx(packed) : cl.map_shared_rank(a + cidx(packed), r);
-    }
 
     static constexpr int U = 8;   // arcs whose loads are issued together
 
@@ -114,7 +137,7 @@ struct ClusterFlow {
     __device__ __forceinline__ void set_label(int lv, int h) {
         lab[lv] = h;
         const int a1 = cofs[lv + 1];
-        for (int a = cofs[lv]; a < a1; ++a) *(volatile int *)at(hlab, rref[a]) = h;
+        for (int a = cofs[lv]; a < a1; ++a) dsm_st(radr[a] + o_hlab, h);
     }
 
     __device__ ClusterFlow(const Work &w_, char *smem)
@@ -168,11 +191,15 @@ struct ClusterFlow {
         rfl = reinterpret_cast<int *>(take(4ull * nvcap));
         cla = reinterpret_cast<int *>(take(4ull * nvcap));
         bord = reinterpret_cast<unsigned char *>(take(nvcap));
-        href = reinterpret_cast<int *>(take(4ull * nacap));
-        rref = reinterpret_cast<int *>(take(4ull * nacap));
+        hadr = reinterpret_cast<unsigned *>(take(4ull * nacap));
+        radr = reinterpret_cast<unsigned *>(take(4ull * nacap));
         res = reinterpret_cast<int *>(take(4ull * nacap));
         csum = reinterpret_cast<int *>(take(4ull * nacap));
         hlab = reinterpret_cast<int *>(take(4ull * nacap));
+        o_ex = cta_addr(ex) - cta_addr(lab);
+        o_rfl = cta_addr(rfl) - cta_addr(lab);
+        o_cla = cta_addr(cla) - cta_addr(lab);
+        o_hlab = cta_addr(hlab) - cta_addr(res);
     }
 
     static __host__ __device__ size_t bytes_for(int nvcap, int nacap) {
@@ -319,10 +346,10 @@ struct ClusterFlow {
                 const int kh = __ldcg(&plocal[h]);
                 const int rh = owner(kh);
                 nremote += rh != rank;
-                href[la] = cpack(rh, kh - hdr->klo[rh]);
+                hadr[la] = map_rank(cta_addr(lab + (kh - hdr->klo[rh])), rh);
                 const int rv = w.rev[j];
                 const int ar = __ldcg(&pacs[kh]) - (hdr->klo[rh] < V ? __ldcg(&pacs[hdr->klo[rh]]) : A) + (rv - w.off[h]);
-                rref[la] = cpack(rh, ar);
+                radr[la] = map_rank(cta_addr(res + ar), rh);
                 res[la] = __ldcg(&w.res[j]);
                 csum[la] = w.cap[j] + w.cap[rv];   // res(a) + res(reverse of a), fixed
             }
@@ -435,7 +462,7 @@ struct ClusterFlow {
                             if (src < 0) return;
                             const int u = base + src, a1 = cofs[u + 1];
                             for (int a = cofs[u] + gl; a < a1; a += G)
-                                if (res[a] > 0) atomicMin(at(col, href[a]), cu);
+                                if (res[a] > 0) dsm_min(hadr[a], cu);   // col is lab
                         });
                     }
                 }
@@ -469,7 +496,7 @@ struct ClusterFlow {
                             if (src < 0) return;
                             const int u = base + src, a1 = cofs[u + 1];
                             for (int a = cofs[u] + gl; a < a1; a += G)
-                                if (csum[a] > res[a]) atomicMax(at(cla, href[a]), su);
+                                if (csum[a] > res[a]) dsm_max(hadr[a] + o_cla, su);
                         });
                     }
                 }
@@ -521,8 +548,8 @@ struct ClusterFlow {
                         if (src < 0) return;
                         const int u = base + src, a1 = cofs[u + 1];
                         for (int a = cofs[u] + gl; a < a1; a += G) {
-                            *(volatile int *)at(hlab, rref[a]) = Lu;
-                            if (csum[a] > res[a]) atomicMin(at(lab, href[a]), Lu + 1);
+                            dsm_st(radr[a] + o_hlab, Lu);
+                            if (csum[a] > res[a]) dsm_min(hadr[a], Lu + 1);
                         }
                     });
                 }
@@ -568,7 +595,7 @@ struct ClusterFlow {
 #pragma unroll
                             for (int u = 0; u < U; ++u) {
                                 r[u] = a + u < a1 ? res[a + u] : 0;
-                                hr[u] = a + u < a1 ? href[a + u] : 0;
+                                hr[u] = a + u < a1 ? (int)hadr[a + u] : 0;
                                 l[u] = a + u < a1 ? hlab[a + u] : -1;
                             }
 #pragma unroll
@@ -578,8 +605,8 @@ struct ClusterFlow {
                                 if (e > 0 && l[u] == L - 1) {
                                     const int d = e < r[u] ? e : r[u];
                                     res[a + u] = r[u] - d;
-                                    atomicAdd(at(res, rref[a + u]), d);
-                                    atomicAdd(at(ex, hr[u]), d);
+                                    dsm_add(radr[a + u], d);
+                                    dsm_add((unsigned)hr[u] + o_ex, d);
                                     e -= d;
                                 }
                             }
@@ -627,10 +654,10 @@ struct ClusterFlow {
                             } else {
                                 const int r = *(volatile int *)&res[best];
                                 d = e < r ? e : r;
-                                const int hh = href[best], rv = rref[best];
+                                const unsigned hh = hadr[best], rv = radr[best];
                                 atomicSub(&res[best], d);
-                                atomicAdd(at(res, rv), d);
-                                atomicAdd(at(ex, hh), d);
+                                dsm_add(rv, d);
+                                dsm_add(hh + o_ex, d);
                                 if (last) ++act;
                             }
                             atomicSub(&ex[lv], d);
@@ -716,7 +743,7 @@ struct ClusterFlow {
                         for (int a = cofs[u] + gl; a < a1; a += G) {
                             const int r = res[a];
                             const int bits = ((nwu & 1) && r > 0 ? 1 : 0) | ((nwu & 2) && csum[a] > r ? 2 : 0);
-                            if (bits) atomicOr(at(rfl, href[a]), bits);
+                            if (bits) dsm_or(hadr[a] + o_rfl, bits);
                         }
                     });
                 }
