@@ -46,6 +46,9 @@ def make_workload(name):
     elif name == "grid3d":
         w = I.config(3)
         desc = "grid3d 128^3 k=16 eps=0.03 alpha=2 MB R=1"
+    elif name == "grid2d":
+        w = I.config(1)
+        desc = "grid2d 64x64 k=2 eps=0.03 alpha=1 (quick checks)"
     else:
         raise SystemExit(f"unknown workload {name}")
     return w, desc
@@ -527,7 +530,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rgg3d", choices=["rgg3d", "grid3d"])
+    ap.add_argument("--workload", default="rgg3d", choices=["rgg3d", "grid3d", "grid2d"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
