@@ -86,6 +86,10 @@ def lib():
         L.fro_refine_batch_sample.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
                                               ctypes.c_int32, i32p]
+        L.fro_refine_active.restype = ctypes.c_int32
+        L.fro_refine_active.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.POINTER(PairResult), i32p, i32p]
         L.fro_splitmix64.restype = ctypes.c_uint64
         L.fro_splitmix64.argtypes = [ctypes.c_uint64]
         _LIB = L
@@ -240,6 +244,24 @@ def refine_batch(w, part=None, eps=None, alpha=None, opts=None):
                                 k, eps, alpha, ctypes.byref(opts), cap, res, ctypes.byref(npairs),
                                 ctypes.byref(nrounds))
     return st, part, [res[i].as_dict() for i in range(npairs.value)], nrounds.value
+
+
+def refine_active(w, part=None, eps=None, alpha=None, opts=None, max_outer=16, cap=None):
+    """Active block scheduling with flow refinement (fro_refine_active); returns
+    (status, part, per-refinement results in processing order, outer rounds run)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    alpha = w["alpha"] if alpha is None else alpha
+    if opts is None:
+        opts = options(mb=w.get("mb", 0))
+    k = w["k"]
+    cap = cap if cap is not None else max(1, max_outer * k * (k - 1) // 2)
+    res = (PairResult * cap)()
+    npairs, nouter = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().fro_refine_active(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
+                                 k, eps, alpha, ctypes.byref(opts), max_outer, cap, res,
+                                 ctypes.byref(npairs), ctypes.byref(nouter))
+    return st, part, [res[i].as_dict() for i in range(min(npairs.value, cap))], nouter.value
 
 
 def refine_batch_sample(w, max_pairs, part=None, opts=None):

@@ -136,6 +136,15 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
                                 const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                                 const fro_options *opt, int32_t max_pairs, int32_t *done);
 
+/* Active block scheduling with flow refinement of each scheduled pair (adaptive
+ * flow iterations if opt->adaptive): outer rounds over the quotient edges with an
+ * active end until no block is active or max_outer rounds ran.  Per-pair results in
+ * processing order (round = matching index counted over all outer rounds). */
+int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                          const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                          const fro_options *opt, int32_t max_outer, int32_t cap, fro_pair_result *res,
+                          int32_t *npairs, int32_t *nouter);
+
 /* Pair cut omega(E_ab) of the current partition. */
 int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                      const int32_t *part, int32_t a, int32_t b);

@@ -864,3 +864,76 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
     if (done) *done = cnt;
     return FRO_OK;
 }
+
+/* --------------------------------------- active block scheduling --------- */
+
+/* Section 4.3 (scheduling quotient graph refinement) and the appendix pseudocode
+ * of active block scheduling, with the pairwise improvement restricted to the flow
+ * refinement of Section 4.1 (the paper's pairwise step also runs FM searches,
+ * which are not part of this build).  Every block starts active.  An outer round
+ * takes the quotient edges (a, b) of the current partition with a or b active,
+ * marks every block inactive, and refines those pairs; a pair whose refinement
+ * changed the partition marks a and b active again.  The outer rounds end when no
+ * block is active, or after max_outer of them.  Inside an outer round the pairs
+ * are coloured into matchings exactly as in fro_rounds (lexicographic order,
+ * smallest colour free at both ends) and refined matching by matching. */
+int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                          const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                          const fro_options *opt, int32_t max_outer, int32_t cap, fro_pair_result *res,
+                          int32_t *npairs, int32_t *nouter) {
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || max_outer < 1)) st = FRO_ERR_INVALID_ARG;
+    if (st != FRO_OK) return st;
+    int64_t W = fro_total_weight(n, vwgt);
+    int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
+    int8_t *active = XALLOC(int8_t, k);
+    int8_t *adj = XALLOC(int8_t, (int64_t)k * k);
+    int32_t ncol = 2 * k;
+    int8_t *used = XALLOC(int8_t, (int64_t)k * ncol);
+    int32_t maxp = k * (k - 1) / 2;
+    int32_t *pa = XALLOC(int32_t, maxp), *pb = XALLOC(int32_t, maxp), *pr = XALLOC(int32_t, maxp);
+    for (int32_t x = 0; x < k; ++x) active[x] = 1;
+    int32_t out = 0, outer = 0, round_base = 0;
+    for (; outer < max_outer; ++outer) {
+        int32_t any = 0;
+        for (int32_t x = 0; x < k; ++x) any |= active[x];
+        if (!any) break;
+        /* quotient graph of the current partition */
+        memset(adj, 0, (size_t)k * k);
+        for (int32_t v = 0; v < n; ++v)
+            for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+                int32_t x = part[v], y = part[adjncy[j]];
+                if (x != y) adj[(int64_t)x * k + y] = 1;
+            }
+        /* the edges with an active end, coloured into matchings */
+        memset(used, 0, (size_t)k * ncol);
+        int32_t np = 0, nr = 0;
+        for (int32_t a = 0; a < k; ++a)
+            for (int32_t b = a + 1; b < k; ++b) {
+                if (!adj[(int64_t)a * k + b] || !(active[a] || active[b])) continue;
+                int32_t c = 0;
+                while (used[(int64_t)a * ncol + c] || used[(int64_t)b * ncol + c]) ++c;
+                used[(int64_t)a * ncol + c] = used[(int64_t)b * ncol + c] = 1;
+                pa[np] = a; pb[np] = b; pr[np] = c;
+                ++np;
+                if (c + 1 > nr) nr = c + 1;
+            }
+        for (int32_t x = 0; x < k; ++x) active[x] = 0;
+        for (int32_t r = 0; r < nr; ++r)
+            for (int32_t i = 0; i < np; ++i) {
+                if (pr[i] != r) continue;
+                fro_pair_result tmp;
+                refine_pair_core(n, xadj, adjncy, adjwgt, vwgt, part, k, pa[i], pb[i], eps, alpha, opt, W, Lmax,
+                                 &tmp);
+                tmp.round = round_base + r;
+                if (tmp.accepted) active[pa[i]] = active[pb[i]] = 1;
+                if (out < cap) res[out] = tmp;
+                ++out;
+            }
+        round_base += nr;
+    }
+    free(active); free(adj); free(used); free(pa); free(pb); free(pr);
+    if (npairs) *npairs = out;
+    if (nouter) *nouter = outer;
+    return FRO_OK;
+}

@@ -1,0 +1,96 @@
+"""Pins of the oracle's active block scheduling (Section 4.3 and the appendix
+pseudocode, pairwise step = flow refinement of Section 4.1).
+
+The schedule is checked against what the pseudocode fixes, recomputed here from
+the partitions the run passes through: every outer round refines exactly the
+quotient edges of the partition at its start that have an active end, in the
+matching order of the rounds; a block is active in the next outer round iff a
+refinement of one of its pairs changed the partition; the run ends when no block
+is active.  The refinements themselves are pinned by replaying them one by one
+with fro_refine_pair (pinned elsewhere), and the first outer round with every
+block active is the already pinned one-sweep batch."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_0006_gb300 import inputs as I
+
+
+def _quotient_edges(w, part):
+    k = w["k"]
+    xadj, adj = np.asarray(w["xadj"]), np.asarray(w["adjncy"])
+    src = np.repeat(np.arange(w["n"]), np.diff(xadj))
+    pa, pb = part[src], part[adj]
+    m = pa < pb
+    return sorted(set(zip(pa[m].tolist(), pb[m].tolist())))
+
+
+def _matching_order(edges):
+    """Greedy colouring in lexicographic order (the rounds' rule), then edges by colour."""
+    used, col = {}, {}
+    for a, b in edges:
+        c = 0
+        while c in used.get(a, ()) or c in used.get(b, ()):
+            c += 1
+        used.setdefault(a, set()).add(c)
+        used.setdefault(b, set()).add(c)
+        col[(a, b)] = c
+    return sorted(edges, key=lambda e: (col[e], e))
+
+
+CASES = [
+    ("grid2d-64", lambda: I.config(1), dict(mb=0)),
+    ("rgg2d-4096", lambda: I.config(2, scale=1 / 16), dict(mb=1)),
+    ("grid3d-32", lambda: I.config(3, scale=1 / 64), dict(mb=1, mb_reps=2, seed=5)),
+    ("small-adaptive-a", lambda: I.random_small(4100, n_max=3000, k_max=8),
+     dict(mb=1, adaptive=1, max_iters=6, alpha_max=8.0)),
+    ("small-adaptive-b", lambda: I.random_small(4101, n_max=3000, k_max=8),
+     dict(mb=0, adaptive=1, max_iters=4, alpha_max=4.0)),
+    ("small-c", lambda: I.random_small(4102, n_max=3000, k_max=8), dict(mb=1)),
+]
+
+
+@pytest.mark.parametrize("name,make,okw", CASES, ids=[c[0] for c in CASES])
+def test_schedule_replay_and_termination(name, make, okw):
+    w = make()
+    max_outer = 12
+    st, final, res, nouter = O.refine_active(w, opts=O.options(**okw), max_outer=max_outer)
+    assert st == 0
+    part = np.array(w["part"], np.int32)
+    active = set(range(w["k"]))
+    i = 0
+    for outer in range(nouter):
+        assert active, "an outer round ran with no active block"
+        expect = _matching_order([(a, b) for a, b in _quotient_edges(w, part) if a in active or b in active])
+        nxt = set()
+        for a, b in expect:
+            r = res[i]
+            assert (r["a"], r["b"]) == (a, b), (outer, i)
+            cut0 = sum(O.pair_cut(w, part, x, y) for x, y in _quotient_edges(w, part))
+            st2, part2, rr = O.refine_pair(w, a, b, part=part, opts=O.options(**okw))
+            assert st2 == 0
+            assert rr.accepted == r["accepted"] and rr.cut_after == r["cut_after"] and rr.iters == r["iters"]
+            assert bool(r["accepted"]) == (not np.array_equal(part, part2))
+            cut1 = sum(O.pair_cut(w, part2, x, y) for x, y in _quotient_edges(w, part2))
+            assert cut1 <= cut0                       # the total cut never grows
+            if r["accepted"]:
+                nxt |= {a, b}
+            part = part2
+            i += 1
+        active = nxt
+    assert i == len(res)
+    assert np.array_equal(part, final)
+    # ended because no block is active, or at the cap
+    assert not active or nouter == max_outer
+
+
+def test_first_outer_round_is_the_batch():
+    for seed in range(5):
+        w = I.random_small(4200 + seed, n_max=2500, k_max=8)
+        opts = O.options(mb=seed % 2, mb_reps=1 + seed % 2, seed=seed)
+        st, p1, r1, nouter = O.refine_active(w, opts=opts, max_outer=1)
+        st2, p2, r2, _ = O.refine_batch(w, opts=opts)
+        assert st == st2 == 0 and nouter == 1
+        assert np.array_equal(p1, p2)
+        assert [(r["a"], r["b"], r["round"], r["accepted"], r["cut_after"]) for r in r1] == \
+               [(r["a"], r["b"], r["round"], r["accepted"], r["cut_after"]) for r in r2]
