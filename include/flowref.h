@@ -197,6 +197,24 @@ fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t 
 fr_status fr_refine_batch(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
                           const fr_options *opt, int32_t cap, fr_pair_result *results, fr_batch_result *summary);
 
+/* Active block scheduling (Section 4.3 and the appendix pseudocode of active block
+ * scheduling) with the flow refinement of Section 4.1 as the pairwise step (the
+ * paper's pairwise step also runs FM searches, which this library does not have).
+ * Every block starts active; an outer round takes the quotient edges (a, b) of the
+ * current partition with a or b active, marks every block inactive, colours the
+ * edges into matchings (lexicographic order, smallest colour free at both ends) and
+ * refines the pairs matching by matching, each with adaptive flow iterations
+ * (Section 4.1) when opt->adaptive; a pair whose refinement changed part marks a and
+ * b active.  Stops when no block is active or after max_outer (>= 1) outer rounds.
+ * part: DEVICE, updated in place, unchanged on error.  results (HOST, cap entries,
+ * may be NULL if cap = 0): one entry per pair refinement in processing order, round =
+ * the matching's index counted over all outer rounds.  summary (HOST, optional):
+ * npairs = refinements, nrounds = matchings, accepted, total cut before/after.
+ * *nouter (HOST, optional): outer rounds run. */
+fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
+                           const fr_options *opt, int32_t max_outer, int32_t cap, fr_pair_result *results,
+                           fr_batch_result *summary, int32_t *nouter);
+
 /* Same as fr_refine_batch for a graph and partition in HOST memory: uploads the
  * arrays, refines, and copies part back (the end-to-end form; graph buffers are
  * reused across calls of the same size). */

@@ -28,6 +28,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 CUDA_SOURCES = [
     "api.cu",
     "api_batch.cu",
+    "api_active.cu",
     "round_kernel.cu",
     "prep_kernel.cu",
     "serve.cu",

@@ -126,6 +126,10 @@ SYMBOLS = {
     "fr_refine_batch": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
                                        ctypes.POINTER(PairResult), ctypes.POINTER(BatchResult)]),
+    "fr_refine_active": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(PairResult), ctypes.POINTER(BatchResult),
+                                        ctypes.POINTER(ctypes.c_int32)]),
     "fr_refine_batch_host": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_int32,
                                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
                                             ctypes.c_int32, ctypes.POINTER(PairResult),
@@ -342,6 +346,22 @@ class Context:
             self._check(st)
         pairs = [res[i].as_dict() for i in range(min(summ.npairs, cap))]
         return st, pairs, summ.as_dict()
+
+    def refine_active(self, g: DeviceGraph, part, k, eps, alpha, opts=None, max_outer=16, cap=None, check=True):
+        """Active block scheduling (fr_refine_active); returns (status, per-refinement
+        results in processing order, summary, outer rounds run)."""
+        cap = cap if cap is not None else max(1, max_outer * k * (k - 1) // 2)
+        res = (PairResult * max(cap, 1))()
+        summ = BatchResult()
+        nouter = ctypes.c_int32()
+        gc = g.c()
+        o = opts if opts is not None else default_options()
+        st = lib().fr_refine_active(self.h, ctypes.byref(gc), _ptr(part), k, eps, alpha, ctypes.byref(o), max_outer,
+                                    cap, res, ctypes.byref(summ), ctypes.byref(nouter))
+        if check:
+            self._check(st)
+        pairs = [res[i].as_dict() for i in range(min(summ.npairs, cap))]
+        return st, pairs, summ.as_dict(), nouter.value
 
     def refine_batch_host(self, xadj, adjncy, adjwgt, vwgt, part, k, eps, alpha, opts=None, cap=0):
         """Host-buffer form: arrays are numpy or (pinned) CPU tensors; part is updated in place."""
