@@ -346,6 +346,7 @@ def run_ours(args, world, rank, local, pg):
                "ms_per_step": round(tot / ke * 1e3, 3)}
 
     compare = batched_vs_per_pair(F, ctx, dev) if args.compare else None
+    active = active_blocks(F, ctx, g, part0, w) if args.active else None
 
     serving = None
     if args.serve or args.serve_full:
@@ -369,9 +370,30 @@ def run_ours(args, world, rank, local, pg):
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare,
+            "active_blocks": active,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+# ------------------------------------------------------- active block scheduling ----
+
+def active_blocks(F, ctx, g, part0, w, max_outer=16):
+    """The bench workload under active block scheduling (fr_refine_active): outer
+    rounds until no block is active, every pair with adaptive flow iterations from
+    alpha = 1 up to alpha' = 16 (Section 4.1).  One run, after the timed region."""
+    import torch
+    opts = F.default_options(mb=int(w["mb"]), adaptive=1, max_iters=10, alpha_max=16.0)
+    part = part0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, res, summ, nouter = ctx.refine_active(g, part, w["k"], w["eps"], 1.0, opts, max_outer=max_outer, cap=0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"workload": "bench workload, alpha 1 -> 16 adaptive, until no block is active",
+            "outer_rounds": nouter, "refinements": summ["npairs"], "matchings": summ["nrounds"],
+            "accepted": summ["accepted"], "cut_before": summ["cut_before"], "cut_after": summ["cut_after"],
+            "ms": round(el * 1e3, 2), "refinements_per_s": round(summ["npairs"] / el, 2)}
 
 
 # ------------------------------------------------- batched vs one pair per launch ----
@@ -542,6 +564,8 @@ def main():
     ap.add_argument("--compare", action=argparse.BooleanOptionalAction, default=True,
                     help="128^3 grid: batched sweep vs one pair per launch")
     ap.add_argument("--serve-requests", type=int, default=None)
+    ap.add_argument("--active", action=argparse.BooleanOptionalAction, default=True,
+                    help="active block scheduling with adaptive flow iterations on the bench workload")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 (timing rule)")

@@ -370,18 +370,33 @@ struct ClusterFlow {
         mark(t1, T_CL_LOAD);
         // a maximum preflow is enough for the cut (see the grid-wide maxflow); the
         // excess goes back to s only when the flow itself is handed out
-        bool ok = w.flow_sched == 1 ? phase_wave(0, nv, hmax) : phase_pulse(0, nv, hmax);
-        mark(t1, T_CL_FLOW);
-        if (ok && w.full_flow) ok = w.flow_sched == 1 ? phase_wave(1, nv, hmax) : phase_pulse(1, nv, hmax);
-        mark(t1, T_CL_RETURN);
+        // The pulse phase stops when no excess can move by its labels; whether the
+        // preflow is maximum is then read off the residual sets: no vertex reached
+        // from s -- the s-border or one holding excess -- may reach t.  If one does
+        // (lagging label copies), the phase resumes from exact labels.
+        bool ok = true;
+        for (int attempt = 0;; ++attempt) {
+            ok = w.flow_sched == 1 ? phase_wave(0, nv, hmax) : phase_pulse(0, nv, hmax, false);
+            mark(t1, T_CL_FLOW);
+            if (ok && w.full_flow) ok = w.flow_sched == 1 ? phase_wave(1, nv, hmax) : phase_pulse(1, nv, hmax, true);
+            mark(t1, T_CL_RETURN);
+            if (!ok) break;
+            reach(nv);
+            mark(t1, T_CL_REACH);
+            int open = 0;
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) open += rfl[lv] == 3;
+            if (cluster_sum(open) == 0) break;
+            if (attempt >= 16) {   // the same count in every CTA
+                if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_INTERNAL, 304);
+                break;
+            }
+        }
         if (!ok) {
             // cap reached: report, leave the pair's arrays as they were
             if (rank == 0 && threadIdx.x == 0) fail(w.ctl, E_ITER, 300);
             sync();
             return true;
         }
-        reach(nv);
-        mark(t1, T_CL_REACH);
         // write back: residuals, s/t flows, zero excess, reachability and plain sides
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const int i = gidx[lv];
@@ -626,7 +641,9 @@ struct ClusterFlow {
 
     // Lock-free pulses (push to the lowest residual neighbour or relabel) until no
     // vertex with excess has a label below hmax; phase 1 returns excess to s.
-    __device__ bool phase_pulse(int ph, int nv, int hmax) {
+    // certify: end only after an exact relabel confirms that no excess can move
+    // (phase 1; phase 0 is checked by the residual sets instead).
+    __device__ bool phase_pulse(int ph, int nv, int hmax, bool certify) {
         relabel(ph, nv, hmax);
         long long pulses = 0, relabels = 1;
         int since = 0;
@@ -683,6 +700,7 @@ struct ClusterFlow {
                 for (int lv = threadIdx.x; lv < nv; lv += TPB)
                     left += ex[lv] > 0 && lab[lv] < hmax;
                 if (cluster_sum(left) == 0) {
+                    if (!certify) break;
                     // Nothing can move by the current labels.  Exact labels decide:
                     // the phase ends only if no vertex with excess can reach its
                     // target (the preflow of phase 0 is then maximum; phase 1 has
