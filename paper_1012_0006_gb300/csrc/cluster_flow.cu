@@ -132,8 +132,9 @@ struct ClusterFlow {
     // arcs of its arcs (the arcs of which lv is the head), local or in other CTAs.
     // The copies may lag; they never run ahead of the label, and labels only rise
     // between exact relabels, so a lagging copy only makes a push look admissible
-    // that is not -- capacities and excesses stay exact, and the phases end only
-    // after an exact relabel has confirmed that no excess can move.
+    // that is not -- capacities and excesses stay exact, and a phase ends only once
+    // exact labels (phase 1) or the residual sets (phase 0) show that no excess can
+    // still reach its target.
     __device__ __forceinline__ void set_label(int lv, int h) {
         lab[lv] = h;
         const int a1 = cofs[lv + 1];
