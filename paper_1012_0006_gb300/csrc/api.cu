@@ -313,6 +313,7 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.any_mb = opt && opt->mb ? 1 : 0;
     w.seed = opt ? opt->seed : 0;
     w.pulse_cap = opt && opt->pulse_cap > 0 ? opt->pulse_cap : (1LL << 20);
+    w.narrow = ctx->narrow_ok;
     return w;
 }
 
@@ -486,6 +487,7 @@ fr_status run_prep(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t 
     CK(cudaMemcpyAsync(h, ctx->prep, sizeof(PrepOut), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     *host_out = *h;
+    ctx->narrow_ok = h->maxw < (1 << 15) ? 1 : 0;
     if (h->err) {
         ctx_error(ctx, h->err == E_TOO_LARGE ? "weighted degree >= 2^30" :
                        "graph or partition violates the input conventions (ids, weights, part range, symmetry)");
@@ -543,9 +545,10 @@ cudaError_t launch_clusters(fr_ctx *ctx, Work &w, long long est_pair_vertices, d
                             cudaStream_t st, int *nl) {
     *nl = 0;
     const int T = fr_ctx::kNumClusterSizes;
-    // shared memory a pair needs: ~29 B per vertex and 20 B per arc, plus a little
-    // for an uneven split; a CTA has cluster_flow_smem() bytes
-    const double need = 1.05 * (double)est_pair_vertices * (29.0 + 20.0 * avg_degree);
+    // shared memory a pair needs: ~29 B per vertex and 16 B per arc (20 B when
+    // capacities do not pack into 16 bits), plus a little for an uneven split; a CTA
+    // has cluster_flow_smem() bytes
+    const double need = 1.05 * (double)est_pair_vertices * (29.0 + (w.narrow ? 16.0 : 20.0) * avg_degree);
     const double per_cta = 0.95 * (double)cluster_flow_smem();
     int t0 = -1, tmax = -1;
     for (int t = 0; t < T; ++t) {

@@ -405,7 +405,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   opt->gr_interval, opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
-                                  opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas, ctx->tune_sched};
+                                  opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas, ctx->tune_sched,
+                                  ctx->narrow_ok};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;

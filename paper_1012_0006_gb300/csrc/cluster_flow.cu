@@ -78,6 +78,16 @@ struct ClusterFlow {
     ClusterHdr *hdr0;          // CTA 0's header
     // local arrays
     int *lab, *ex, *fx, *cofs, *gidx, *rfl, *cla, *res, *csum;
+    // narrow: every capacity sum csum(a) = c(a) + c(reverse a) is below 2^16, and
+    // res[a] holds res(a) | csum(a) << 16 (csum unused); additions to the residual
+    // never carry into the upper half because res(a) <= csum(a)
+    bool narrow;
+    __device__ __forceinline__ int rs(int a) const {
+        const int x = *(volatile int *)&res[a];
+        return narrow ? (x & 0xFFFF) : x;
+    }
+    __device__ __forceinline__ int cs(int a) const { return narrow ? (int)((unsigned)res[a] >> 16) : csum[a]; }
+    __device__ __forceinline__ void set_rs(int a, int v) { res[a] = narrow ? ((res[a] & ~0xFFFF) | v) : v; }
     // per arc: shared::cluster addresses of the head's label (hadr) and of the reverse
     // arc's residual (radr); other arrays of the same element are a fixed offset away
     unsigned *hadr, *radr;
@@ -97,7 +107,7 @@ struct ClusterFlow {
             int r[U], l[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                r[u] = a + u < a1 ? *(volatile int *)&res[a + u] : 0;
+                r[u] = a + u < a1 ? rs(a + u) : 0;
                 l[u] = a + u < a1 ? *(volatile int *)&hlab[a + u] : INT_MAX;
             }
 #pragma unroll
@@ -177,7 +187,8 @@ struct ClusterFlow {
         return tot;
     }
 
-    __device__ void carve(char *smem, int nvcap, int nacap) {
+    __device__ void carve(char *smem, int nvcap, int nacap, bool narrow_) {
+        narrow = narrow_;
         char *p = smem + kHdrBytes;
         auto take = [&](size_t bytes) {
             char *r = p;
@@ -195,7 +206,7 @@ struct ClusterFlow {
         hadr = reinterpret_cast<unsigned *>(take(4ull * nacap));
         radr = reinterpret_cast<unsigned *>(take(4ull * nacap));
         res = reinterpret_cast<int *>(take(4ull * nacap));
-        csum = reinterpret_cast<int *>(take(4ull * nacap));
+        csum = narrow ? nullptr : reinterpret_cast<int *>(take(4ull * nacap));
         hlab = reinterpret_cast<int *>(take(4ull * nacap));
         o_ex = cta_addr(ex) - cta_addr(lab);
         o_rfl = cta_addr(rfl) - cta_addr(lab);
@@ -203,9 +214,9 @@ struct ClusterFlow {
         o_hlab = cta_addr(hlab) - cta_addr(res);
     }
 
-    static __host__ __device__ size_t bytes_for(int nvcap, int nacap) {
+    static __host__ __device__ size_t bytes_for(int nvcap, int nacap, bool narrow) {
         auto a = [](size_t b) { return (b + 15) / 16 * 16; };
-        return kHdrBytes + 7 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + 5 * a(4ull * nacap);
+        return kHdrBytes + 7 * a(4ull * nvcap) + a(4ull * (nvcap + 1)) + a(nvcap) + (narrow ? 4 : 5) * a(4ull * nacap);
     }
 
     __device__ int owner(int k) const {   // CTA whose range holds member k
@@ -325,8 +336,9 @@ struct ClusterFlow {
         }
         __syncthreads();
         const int nvcap = hdr->nvcap, nacap = hdr->nacap;
-        if (bytes_for(nvcap, nacap) > smem_bytes) return false;   // same decision in every CTA
-        carve(smem, nvcap, nacap);
+        const bool nar = w.narrow != 0;
+        if (bytes_for(nvcap, nacap, nar) > smem_bytes) return false;   // same decision in every CTA
+        carve(smem, nvcap, nacap, nar);
         const int klo = hdr->klo[rank], khi = hdr->klo[rank + 1];
         const int nv = khi - klo;
         const int abase = klo < V ? __ldcg(&pacs[klo]) : A;
@@ -351,8 +363,14 @@ struct ClusterFlow {
                 const int rv = w.rev[j];
                 const int ar = __ldcg(&pacs[kh]) - (hdr->klo[rh] < V ? __ldcg(&pacs[hdr->klo[rh]]) : A) + (rv - w.off[h]);
                 radr[la] = map_rank(cta_addr(res + ar), rh);
-                res[la] = __ldcg(&w.res[j]);
-                csum[la] = w.cap[j] + w.cap[rv];   // res(a) + res(reverse of a), fixed
+                const int r0 = __ldcg(&w.res[j]);
+                const int c0 = w.cap[j] + w.cap[rv];   // res(a) + res(reverse of a), fixed
+                if (nar) {
+                    res[la] = r0 | (c0 << 16);
+                } else {
+                    res[la] = r0;
+                    csum[la] = c0;
+                }
             }
         }
         nremote = (int)__reduce_add_sync(FULL, (unsigned)nremote);
@@ -403,7 +421,7 @@ struct ClusterFlow {
             const int i = gidx[lv];
             const int j0 = w.off[i];
             const int a0 = cofs[lv], a1 = cofs[lv + 1];
-            for (int a = a0; a < a1; ++a) w.res[j0 + (a - a0)] = res[a];
+            for (int a = a0; a < a1; ++a) w.res[j0 + (a - a0)] = rs(a);
             w.fx[i] = fx[lv];
             w.ex[i] = ex[lv];
             w.rflag[i] = rfl[lv];
@@ -478,7 +496,7 @@ struct ClusterFlow {
                             if (src < 0) return;
                             const int u = base + src, a1 = cofs[u + 1];
                             for (int a = cofs[u] + gl; a < a1; a += G)
-                                if (res[a] > 0) dsm_min(hadr[a], cu);   // col is lab
+                                if (rs(a) > 0) dsm_min(hadr[a], cu);   // col is lab
                         });
                     }
                 }
@@ -512,7 +530,7 @@ struct ClusterFlow {
                             if (src < 0) return;
                             const int u = base + src, a1 = cofs[u + 1];
                             for (int a = cofs[u] + gl; a < a1; a += G)
-                                if (csum[a] > res[a]) dsm_max(hadr[a] + o_cla, su);
+                                if (cs(a) > rs(a)) dsm_max(hadr[a] + o_cla, su);
                         });
                     }
                 }
@@ -565,7 +583,7 @@ struct ClusterFlow {
                         const int u = base + src, a1 = cofs[u + 1];
                         for (int a = cofs[u] + gl; a < a1; a += G) {
                             dsm_st(radr[a] + o_hlab, Lu);
-                            if (csum[a] > res[a]) dsm_min(hadr[a], Lu + 1);
+                            if (cs(a) > rs(a)) dsm_min(hadr[a], Lu + 1);
                         }
                     });
                 }
@@ -610,7 +628,7 @@ struct ClusterFlow {
                             int r[U], hr[U], l[U];
 #pragma unroll
                             for (int u = 0; u < U; ++u) {
-                                r[u] = a + u < a1 ? res[a + u] : 0;
+                                r[u] = a + u < a1 ? rs(a + u) : 0;
                                 hr[u] = a + u < a1 ? (int)hadr[a + u] : 0;
                                 l[u] = a + u < a1 ? hlab[a + u] : -1;
                             }
@@ -620,7 +638,7 @@ struct ClusterFlow {
                             for (int u = 0; u < U; ++u) {
                                 if (e > 0 && l[u] == L - 1) {
                                     const int d = e < r[u] ? e : r[u];
-                                    res[a + u] = r[u] - d;
+                                    set_rs(a + u, r[u] - d);
                                     dsm_add(radr[a + u], d);
                                     dsm_add((unsigned)hr[u] + o_ex, d);
                                     e -= d;
@@ -670,7 +688,7 @@ struct ClusterFlow {
                                 if (!ph) { d = e; fx[lv] += d; }
                                 else { d = e < fx[lv] ? e : fx[lv]; fx[lv] -= d; }
                             } else {
-                                const int r = *(volatile int *)&res[best];
+                                const int r = rs(best);
                                 d = e < r ? e : r;
                                 const unsigned hh = hadr[best], rv = radr[best];
                                 atomicSub(&res[best], d);
@@ -760,8 +778,8 @@ struct ClusterFlow {
                         if (src < 0) return;
                         const int u = base + src, a1 = cofs[u + 1];
                         for (int a = cofs[u] + gl; a < a1; a += G) {
-                            const int r = res[a];
-                            const int bits = ((nwu & 1) && r > 0 ? 1 : 0) | ((nwu & 2) && csum[a] > r ? 2 : 0);
+                            const int r = rs(a);
+                            const int bits = ((nwu & 1) && r > 0 ? 1 : 0) | ((nwu & 2) && cs(a) > r ? 2 : 0);
                             if (bits) dsm_or(hadr[a] + o_rfl, bits);
                         }
                     });

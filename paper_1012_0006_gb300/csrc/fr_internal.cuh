@@ -164,7 +164,7 @@ struct Work {
     int flow_sched;              // cluster max flow: 1 level-ordered waves, otherwise lock-free pulses
     int cl_tier;                 // cluster launch: 0 every pair, 1 the pairs the first left
     int full_flow;               // 1: return every excess to s (a flow); 0: a maximum preflow
-    int pad_w;
+    int narrow;                  // 1: every arc capacity < 2^15 (cluster kernel packs residual and capacity sum)
     unsigned long long seed;
     long long pulse_cap;
 };

@@ -38,6 +38,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
     __syncthreads();
     int err = 0;
     long long W = 0, maxc = 0, cut = 0;
+    int maxw = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (xadj[0] != 0 || xadj[n] != nnz)) err = E_INVALID;
     for (long long v = (long long)blockIdx.x * kPrepTPB + threadIdx.x; v < n; v += (long long)gridDim.x * kPrepTPB) {
         const int pv = part[v];
@@ -64,6 +65,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
                 break;
             }
             wdeg += om;
+            if (om > maxw) maxw = om;
             const int pu = part[u];
             if (pu > pv && pu < k) {
                 cut += om;
@@ -84,16 +86,18 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
     const long long bW = block_sum_ll<kPrepTPB>(W);
     const long long bC = block_sum_ll<kPrepTPB>(cut);
     __shared__ long long s_max;
-    __shared__ int s_err;
-    if (threadIdx.x == 0) { s_max = 0; s_err = 0; }
+    __shared__ int s_err, s_maxw;
+    if (threadIdx.x == 0) { s_max = 0; s_err = 0; s_maxw = 0; }
     __syncthreads();
     if (maxc) atomicMax((unsigned long long *)&s_max, (unsigned long long)maxc);
+    if (maxw) atomicMax(&s_maxw, maxw);
     if (err) atomicMax(&s_err, err);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (bW) atomicAdd((unsigned long long *)&out->W, (unsigned long long)bW);
         if (bC) atomicAdd((unsigned long long *)&out->totcut, (unsigned long long)bC);
         if (s_max) atomicMax((unsigned long long *)&out->maxc, (unsigned long long)s_max);
+        if (s_maxw) atomicMax(&out->maxw, s_maxw);
         if (s_err) atomicMax(&out->err, s_err);
     }
 }

@@ -21,6 +21,7 @@ struct PrepOut {
     long long W, maxc, totcut;
     int err, err_where;
     int npairs, nrounds;
+    int maxw, pad;       // max edge weight
 };
 cudaError_t launch_prep(const int *xadj, const int *adjncy, const int *adjwgt, const int *vwgt, const int *part,
                         int n, int nnz, int k, long long *blockw, unsigned int *qbits, PrepOut *out,

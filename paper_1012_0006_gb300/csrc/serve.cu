@@ -48,7 +48,7 @@ struct Req {
     int npairs = 0, nrounds = 0, round = 0;
     std::vector<int> off;
     long long Ubase = 0, Lmax = 0, totcut = 0, dcut = 0, W = 0;
-    int accepted = 0;
+    int accepted = 0, maxw = 0;
     fr_status status = FR_OK;
 };
 
@@ -146,6 +146,7 @@ static fr_status admit(fr_server *S, Req *q) {
     q->nrounds = po.nrounds;
     q->totcut = po.totcut;
     q->W = po.W;
+    q->maxw = po.maxw;
     q->Ubase = host_budget_base(po.W, k, q->r.eps, q->r.alpha);
     q->Lmax = host_lmax(po.W, po.maxc, k, q->r.eps);
     q->off.assign(q->nrounds + 1, 0);
@@ -253,6 +254,8 @@ static fr_status run_step(fr_server *S, std::vector<Req *> &act) {
         cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * (size_t)P * kHistBins, st) != cudaSuccess)
         return FR_ERR_CUDA;
     Work w = make_work(ctx, 0, 0, P, (int)totn, &opt);
+    w.narrow = 1;
+    for (const Req *q : act) w.narrow &= q->maxw < (1 << 15) ? 1 : 0;
     w.graphs = S->d_graphs;
     w.ngraphs = (int)act.size();
     w.prev_err = nullptr;

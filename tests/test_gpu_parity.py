@@ -263,6 +263,19 @@ def test_launch_shapes_give_identical_partitions(F, ctx):
         assert np.array_equal(got, ref), shape
 
 
+@pytest.mark.parametrize("scale", [32767, 40000])
+def test_edge_weights_at_and_above_the_packed_range(F, ctx, scale):
+    """Edge weights up to 32767 keep residual and capacity sum in one 32-bit word in
+    the cluster kernel; larger ones use separate words.  Both layouts against the
+    oracle (weights rescaled so that the largest is `scale`)."""
+    for seed in range(4):
+        w = I.random_small(6100 + seed, n_max=3000, k_max=6)
+        adjw = np.asarray(w["adjwgt"], np.int64)
+        w["adjwgt"] = np.ascontiguousarray(np.maximum(1, adjw * scale // adjw.max()), np.int32)
+        w["mb"] = seed % 2
+        _check_batch(F, ctx, w, dict(mb_reps=1 + seed % 2, seed=seed))
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_tiny_networks_in_large_clusters(F, ctx, seed):
     """Small corridors in 16-CTA clusters: most CTAs hold no vertex, and most
