@@ -251,12 +251,15 @@ typedef struct fr_profile_info {
     int64_t pushes;           /* pushes */
     int64_t scc_rounds;       /* SCC colouring rounds */
     int64_t barriers;         /* grid barriers passed by the persistent kernels */
-    double cluster_phase_ms[5]; /* cluster kernel timers summed over pairs: member scan and load,
-                                   flow to t, return of excess to s, residual reachability,
-                                   residual SCCs (most balanced cuts) */
+    double cluster_phase_ms[6]; /* cluster kernel timers summed over pairs: network load into
+                                   shared memory, flow to t, return of excess to s, residual
+                                   reachability, residual SCCs (most balanced cuts), member scan
+                                   and split (before the load) */
     int64_t cluster_syncs;    /* cluster barriers, summed over pairs */
     int64_t cluster_remote_arcs; /* arcs held in a cluster whose head another CTA holds (DSMEM) */
     int64_t fallback_pairs;   /* pairs left to the grid-wide flow */
+    int32_t cluster_sizes[5]; /* CTAs per cluster the library can launch (4, 6, 8, 12, 16) */
+    int32_t cluster_max_active[5]; /* clusters of each size resident at once on this GPU */
 } fr_profile_info;
 
 /* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with

@@ -550,13 +550,26 @@ cudaError_t launch_clusters(fr_ctx *ctx, Work &w, long long est_pair_vertices, d
     // has cluster_flow_smem() bytes
     const double need = 1.05 * (double)est_pair_vertices * (29.0 + (w.narrow ? 16.0 : 20.0) * avg_degree);
     const double per_cta = 0.95 * (double)cluster_flow_smem();
+    // Among the sizes that hold the estimate, the one with the least expected time:
+    // waves of resident clusters times the relative time of one pair, measured on
+    // 3D rgg / grid pairs (a pair's time falls slowly with more CTAs: its steps are
+    // bound by barriers and latency).  Many pairs favour small clusters, few pairs
+    // large ones.
+    static const double kRelTime[fr_ctx::kNumClusterSizes] = {1.25, 1.05, 1.0, 0.85, 0.74};
     int t0 = -1, tmax = -1;
+    double best = 0;
+    const int P = std::max(1, w.npairs);
     for (int t = 0; t < T; ++t) {
         if (ctx->cl_cap[t] <= 0) continue;
         tmax = t;
         const int c = fr_ctx::kClusterSizes[t];
-        if (force == c && t0 < 0) t0 = t;
-        if (force == 0 && t0 < 0 && need <= per_cta * c) t0 = t;
+        if (force) {
+            if (force == c && t0 < 0) t0 = t;
+            continue;
+        }
+        if (need > per_cta * c) continue;
+        const double cost = (double)((P + ctx->cl_cap[t] - 1) / ctx->cl_cap[t]) * kRelTime[t];
+        if (t0 < 0 || cost < best) { t0 = t; best = cost; }
     }
     if (t0 < 0) t0 = tmax;   // nothing fits the estimate (or the forced size is unavailable)
     if (t0 < 0) return cudaErrorInvalidValue;

@@ -574,6 +574,10 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
         P.cluster_ms = clu;
         P.nrounds = pl.nr;
         P.launches = (int32_t)ctx->last_launches;
+        for (int t = 0; t < fr_ctx::kNumClusterSizes && t < 5; ++t) {
+            P.cluster_sizes[t] = fr_ctx::kClusterSizes[t];
+            P.cluster_max_active[t] = ctx->cl_cap[t];
+        }
         P.n = g->n;
         P.nnz = g->nnz;
         for (int r = 0; r < pl.nr; ++r) {
@@ -589,7 +593,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.pushes += C[r].pushes;
             P.scc_rounds += C[r].scc_rounds;
             P.barriers += C[r].barriers;
-            for (int t = 0; t < 5; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
+            for (int t = 0; t < 6; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
             P.cluster_syncs += C[r].cl_syncs;
             P.cluster_remote_arcs += C[r].cl_remote;
             P.fallback_pairs += C[r].fallback;

@@ -34,6 +34,7 @@ constexpr int kHdrBytes = 1024;
 
 struct ClusterHdr {
     int klo[kClusterMax + 1];   // member ranges of the CTAs (identical in every CTA)
+    int cab[kClusterMax + 1];   // first arc (pair-local prefix) of each CTA's range
     int cnt[3];                 // rotating counters (CTA 0's copy is the cluster's)
     int err;                    // cluster error (CTA 0's copy)
     int nvcap, nacap;           // common capacities (identical in every CTA)
@@ -246,90 +247,87 @@ struct ClusterFlow {
         for (int q = 0; q < p; ++q) pbase += __ldcg(&w.pacc[q].nc);
         int *pmem = w.cid + pbase, *pacs = w.outoff + pbase, *plocal = w.color;
         {
+            // one pass: every thread counts a contiguous slice of the CTA's share of
+            // the union, one block scan and one cluster prefix place its members
             const long long per = (nu + C - 1) / C;
             const long long c0 = per * rank, c1 = min((long long)nu, c0 + per);
+            const long long tper = (max(0LL, c1 - c0) + TPB - 1) / TPB;
+            const long long t0 = c0 + tper * threadIdx.x, t1 = min(c1, t0 + tper);
             int mine = 0;
-            for (long long i = c0 + threadIdx.x; i < c1; i += TPB) mine += (w.sid[i] >> 1) == p;
-            __shared__ int s_tot;
-            if (threadIdx.x == 0) s_tot = 0;
-            __syncthreads();
-            if (mine) atomicAdd(&s_tot, mine);
-            __syncthreads();
-            if (threadIdx.x == 0) hdr0->counts[rank] = s_tot;
+            for (long long i = t0; i < t1; ++i) mine += (__ldcg(&w.sid[i]) >> 1) == p;
+            int tot;
+            const int ex0 = block_exclusive_scan<TPB>(mine, &tot);
+            if (threadIdx.x == 0) hdr0->counts[rank] = tot;
             sync();
-            int before = 0;
-            for (int r = 0; r < rank; ++r) before += *(volatile int *)&hdr0->counts[r];
+            int pos = ex0;
+            for (int r = 0; r < rank; ++r) pos += *(volatile int *)&hdr0->counts[r];
             sync();   // counts read before they are reused
-            int run = before;
-            for (long long x0 = c0; x0 < c1; x0 += TPB) {
-                const long long i = x0 + threadIdx.x;
-                const int f = i < c1 && (w.sid[i] >> 1) == p;
-                int tile;
-                const int ex0 = block_exclusive_scan<TPB>(f, &tile);
-                if (f) {
-                    pmem[run + ex0] = (int)i;
-                    plocal[i] = run + ex0;
+            for (long long i = t0; i < t1; ++i)
+                if ((__ldcg(&w.sid[i]) >> 1) == p) {
+                    pmem[pos] = (int)i;
+                    plocal[i] = pos;
+                    ++pos;
                 }
-                run += tile;
-            }
         }
         __threadfence();
         sync();
-        // arc prefix over members (each CTA a slice of the member list)
+        // arc prefix over members (each CTA a slice of the member list, each thread a
+        // contiguous part of it)
         {
             const int per = (V + C - 1) / C;
-            const int k0 = per * rank, k1 = min(V, k0 + per);
+            const int k0 = min(V, per * rank), k1 = min(V, k0 + per);
+            const int tper = (k1 - k0 + TPB - 1) / TPB;
+            const int s0 = min(k1, k0 + tper * (int)threadIdx.x), s1 = min(k1, s0 + tper);
             int mine = 0;
-            for (int k = k0 + threadIdx.x; k < k1; k += TPB) {
+            for (int k = s0; k < s1; ++k) {
                 const int i = __ldcg(&pmem[k]);
                 mine += w.off[i + 1] - w.off[i];
             }
-            __shared__ int s_tot2;
-            if (threadIdx.x == 0) s_tot2 = 0;
-            __syncthreads();
-            if (mine) atomicAdd(&s_tot2, mine);
-            __syncthreads();
-            if (threadIdx.x == 0) hdr0->counts[rank] = s_tot2;
+            int tot;
+            const int e0 = block_exclusive_scan<TPB>(mine, &tot);
+            if (threadIdx.x == 0) hdr0->counts[rank] = tot;
             sync();
-            int before = 0;
-            for (int r = 0; r < rank; ++r) before += *(volatile int *)&hdr0->counts[r];
+            int run = e0;
+            for (int r = 0; r < rank; ++r) run += *(volatile int *)&hdr0->counts[r];
             sync();
-            int run = before;
-            for (int x0 = k0; x0 < k1; x0 += TPB) {
-                const int k = x0 + threadIdx.x;
-                int d = 0;
-                if (k < k1) {
-                    const int i = __ldcg(&pmem[k]);
-                    d = w.off[i + 1] - w.off[i];
+            // split points: klo[r] = the first member whose prefix reaches A * r / C, so
+            // the member whose arcs (prefix, prefix + degree] hold that target is the one
+            // before it; its thread writes klo and the range's first arc into CTA 0
+            if (rank == 0 && threadIdx.x == 0) {
+                hdr->klo[0] = 0;
+                hdr->cab[0] = 0;
+                hdr->klo[C] = V;
+                hdr->cab[C] = A;
+                for (int r = 1; r < C; ++r)
+                    if ((long long)A * r / C <= 0) { hdr->klo[r] = 0; hdr->cab[r] = 0; }
+            }
+            for (int k = s0; k < s1; ++k) {
+                const int i = __ldcg(&pmem[k]);
+                const int d = w.off[i + 1] - w.off[i];
+                pacs[k] = run;
+                for (int r = 1; r < C; ++r) {
+                    const long long target = (long long)A * r / C;
+                    if (target > run && target <= run + d) {
+                        hdr0->klo[r] = k + 1;
+                        hdr0->cab[r] = run + d;
+                    }
                 }
-                int tile;
-                const int e0 = block_exclusive_scan<TPB>(d, &tile);
-                if (k < k1) pacs[k] = run + e0;
-                run += tile;
+                run += d;
             }
         }
         __threadfence();
         sync();
-        // split members into C ranges of about A / C arcs each (same in every CTA)
+        // the C ranges of about A / C arcs each, copied from CTA 0 (same in every CTA)
+        if (threadIdx.x <= C && rank != 0) {
+            hdr->klo[threadIdx.x] = *(volatile int *)&hdr0->klo[threadIdx.x];
+            hdr->cab[threadIdx.x] = *(volatile int *)&hdr0->cab[threadIdx.x];
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            hdr->klo[0] = 0;
-            for (int r = 1; r < C; ++r) {
-                const long long target = (long long)A * r / C;
-                int lo = hdr->klo[r - 1], hi = V;   // first k with pacs[k] >= target
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__ldcg(&pacs[mid]) < target) lo = mid + 1; else hi = mid;
-                }
-                hdr->klo[r] = lo;
-            }
-            hdr->klo[C] = V;
             int nvcap = 0, nacap = 0;
             for (int r = 0; r < C; ++r) {
-                const int kv = hdr->klo[r + 1] - hdr->klo[r];
-                const int a0 = hdr->klo[r] < V ? __ldcg(&pacs[hdr->klo[r]]) : A;
-                const int a1 = hdr->klo[r + 1] < V ? __ldcg(&pacs[hdr->klo[r + 1]]) : A;
-                nvcap = max(nvcap, kv);
-                nacap = max(nacap, a1 - a0);
+                nvcap = max(nvcap, hdr->klo[r + 1] - hdr->klo[r]);
+                nacap = max(nacap, hdr->cab[r + 1] - hdr->cab[r]);
             }
             hdr->nvcap = nvcap;
             hdr->nacap = nacap;
@@ -337,11 +335,13 @@ struct ClusterFlow {
         __syncthreads();
         const int nvcap = hdr->nvcap, nacap = hdr->nacap;
         const bool nar = w.narrow != 0;
+        unsigned long long t1 = t_in;
+        mark(t1, T_CL_MEMBERS);
         if (bytes_for(nvcap, nacap, nar) > smem_bytes) return false;   // same decision in every CTA
         carve(smem, nvcap, nacap, nar);
         const int klo = hdr->klo[rank], khi = hdr->klo[rank + 1];
         const int nv = khi - klo;
-        const int abase = klo < V ? __ldcg(&pacs[klo]) : A;
+        const int abase = hdr->cab[rank];
         // load this CTA's vertices and arcs
         int nremote = 0;   // arcs whose head another CTA holds
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
@@ -353,23 +353,42 @@ struct ClusterFlow {
             const int a0 = __ldcg(&pacs[klo + lv]) - abase;
             cofs[lv] = a0;
             const int j0 = w.off[i], j1 = w.off[i + 1];
-            for (int j = j0; j < j1; ++j) {
-                const int la = a0 + (j - j0);
-                const int h = w.head[j];
-                const int kh = __ldcg(&plocal[h]);
-                const int rh = owner(kh);
-                nremote += rh != rank;
-                hadr[la] = map_rank(cta_addr(lab + (kh - hdr->klo[rh])), rh);
-                const int rv = w.rev[j];
-                const int ar = __ldcg(&pacs[kh]) - (hdr->klo[rh] < V ? __ldcg(&pacs[hdr->klo[rh]]) : A) + (rv - w.off[h]);
-                radr[la] = map_rank(cta_addr(res + ar), rh);
-                const int r0 = __ldcg(&w.res[j]);
-                const int c0 = w.cap[j] + w.cap[rv];   // res(a) + res(reverse of a), fixed
-                if (nar) {
-                    res[la] = r0 | (c0 << 16);
-                } else {
-                    res[la] = r0;
-                    csum[la] = c0;
+            // four arcs at a time, their loads issued together (each arc is a chain
+            // head -> head's member index -> its arc prefix)
+            for (int jb = j0; jb < j1; jb += 4) {
+                int h[4], rv[4], r0[4], cj[4], kh[4], oh[4], cr[4], ph[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = min(jb + u, j1 - 1);
+                    h[u] = w.head[j];
+                    rv[u] = w.rev[j];
+                    r0[u] = __ldcg(&w.res[j]);
+                    cj[u] = w.cap[j];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    kh[u] = __ldcg(&plocal[h[u]]);
+                    oh[u] = w.off[h[u]];
+                    cr[u] = w.cap[rv[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ph[u] = __ldcg(&pacs[kh[u]]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (jb + u >= j1) break;
+                    const int la = a0 + (jb + u - j0);
+                    const int rh = owner(kh[u]);
+                    nremote += rh != rank;
+                    hadr[la] = map_rank(cta_addr(lab + (kh[u] - hdr->klo[rh])), rh);
+                    const int ar = ph[u] - hdr->cab[rh] + (rv[u] - oh[u]);
+                    radr[la] = map_rank(cta_addr(res + ar), rh);
+                    const int c0 = cj[u] + cr[u];   // res(a) + res(reverse of a), fixed
+                    if (nar) {
+                        res[la] = r0[u] | (c0 << 16);
+                    } else {
+                        res[la] = r0[u];
+                        csum[la] = c0;
+                    }
                 }
             }
         }
@@ -385,7 +404,6 @@ struct ClusterFlow {
         rot = 0;
         sync();
         const int hmax = V + 2;
-        unsigned long long t1 = t_in;
         mark(t1, T_CL_LOAD);
         // a maximum preflow is enough for the cut (see the grid-wide maxflow); the
         // excess goes back to s only when the flow itself is handed out

@@ -69,17 +69,22 @@ class ProfileInfo(ctypes.Structure):
                 ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
                 ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64), ("barriers", ctypes.c_int64),
-                ("cluster_phase_ms", ctypes.c_double * 5), ("cluster_syncs", ctypes.c_int64),
+                ("cluster_phase_ms", ctypes.c_double * 6), ("cluster_syncs", ctypes.c_int64),
                 ("cluster_remote_arcs", ctypes.c_int64),
-                ("fallback_pairs", ctypes.c_int64)]
+                ("fallback_pairs", ctypes.c_int64),
+                ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("phase_ms", "cluster_phase_ms")}
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("phase_ms", "cluster_phase_ms", "cluster_sizes", "cluster_max_active")}
         d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
-        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach", "scc"), list(self.cluster_phase_ms)))
+        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach", "scc", "members"),
+                                         list(self.cluster_phase_ms)))
+        d["cluster_sizes"] = list(self.cluster_sizes)
+        d["cluster_max_active"] = list(self.cluster_max_active)
         return d
 
 
