@@ -595,23 +595,36 @@ struct StepKernel {
             ctl->mu = (int)mu;
         }
         if (!grid_sync(ctl)) return false;
-        // arcs, reverse arcs, residual = capacity, preflow initialisation
-        for (long long i = G.tid; i < nu; i += G.size) {
-            const int v = w.gid[i], s = w.sid[i];
-            const PairDev P = w.pairs[s >> 1];
-            const GraphDev &Gr = w.graphs[P.g];
-            int j = __ldcg(&w.off[i]);
-            long long cout = 0;
-            const int j1 = __ldg(Gr.xadj + v + 1);
-            for (int e = __ldg(Gr.xadj + v); e < j1; ++e) {
-                if (__ldcg(&crank[Gr.ebase + e]) < 0) continue;
+        // arcs, reverse arcs, residual = capacity: the corridor arcs of every row,
+        // flattened over the lanes of a warp (warp_rows) so that long rows do not hold
+        // up one thread; arc e of row i goes to off[i] + crank[e].  ex[i] collects, for
+        // s-border rows, the capacity toward vertices off the s-border.
+        for (long long i = G.tid; i < nu; i += G.size) w.ex[i] = 0;
+        if (!grid_sync(ctl)) return false;
+        warp_rows(
+            0, nu, G,
+            [&](long long i, int &rs, int &deg, int &ctx) {
+                const int v = w.gid[i];
+                const GraphDev &Gr = w.graphs[w.pairs[w.sid[i] >> 1].g];
+                rs = __ldg(Gr.xadj + v);
+                deg = __ldg(Gr.xadj + v + 1) - rs;
+                ctx = (int)i;
+            },
+            [&](bool valid, int e, int i) {
+                if (!valid) return;
+                const GraphDev &Gr = w.graphs[w.pairs[w.sid[i] >> 1].g];
+                const int rk = __ldcg(&crank[Gr.ebase + e]);
+                if (rk < 0) return;
+                const int v = w.gid[i];
                 const int u = __ldg(Gr.adjncy + e);
                 const int h = __ldcg(Gr.lid + u);
                 const int c = __ldg(Gr.adjwgt + e);
-                if (__ldcg(&w.border[h]) != 1) cout += c;   // arcs into other s-border vertices carry nothing s could not send directly
+                const int j = __ldcg(&w.off[i]) + rk;
                 w.head[j] = h;
                 w.cap[j] = c;
                 w.res[j] = c;
+                if (w.border[i] == 1 && __ldcg(&w.border[h]) != 1)   // arcs into other s-border vertices carry
+                    atomicAddLL(&w.ex[i], (long long)c);             // nothing s could not send directly
                 // the reverse arc: v's position in u's row, then its rank among u's corridor arcs
                 const int k0 = __ldg(Gr.xadj + u), k1 = __ldg(Gr.xadj + u + 1);
                 int t = -1;
@@ -626,14 +639,16 @@ struct StepKernel {
                 const int q = t >= 0 ? __ldcg(&crank[Gr.ebase + t]) : 0;
                 if (t < 0) fail(w.ctl, E_INVALID, 41);   // no reverse arc: the CSR is not symmetric
                 w.rev[j] = __ldcg(&w.off[h]) + q;
-                ++j;
-            }
-            // Preflow: s -> v carries what v can pass on to vertices outside the
-            // s-border, c_out(v) < INF_v.  Some maximum flow sends no more through
-            // s -> v (flow s -> v -> u with u on the s-border can go s -> u directly),
-            // so the max flow is unchanged and only the excess that is pushed in and
-            // then stranded has to return.
+            });
+        if (!grid_sync(ctl)) return false;
+        // Preflow: s -> v carries what v can pass on to vertices outside the s-border,
+        // c_out(v) < INF_v.  Some maximum flow sends no more through s -> v (flow
+        // s -> v -> u with u on the s-border can go s -> u directly), so the max flow
+        // is unchanged and only the excess that is pushed in and then stranded has to
+        // move again.
+        for (long long i = G.tid; i < nu; i += G.size) {
             const unsigned char bd = w.border[i];
+            const long long cout = __ldcg(&w.ex[i]);
             const int fx0 = bd == 1 ? (int)(cout < w.infc[i] ? cout : w.infc[i]) : 0;
             w.fx[i] = fx0;
             w.ex[i] = fx0;
