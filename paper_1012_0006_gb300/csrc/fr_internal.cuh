@@ -22,7 +22,7 @@ namespace fr {
 constexpr int kMaxSides = 2048;        // pairs per step <= 1024
 constexpr int kHistBins = 256;
 constexpr int kMaxGraphs = 64;         // graphs per step (serving)
-constexpr unsigned int kSpinLimit = 1u << 22;   // barrier spins (~1 s with backoff)
+constexpr unsigned int kSpinLimit = 1u << 22;   // barrier polls (a few seconds with backoff)
 constexpr unsigned int kBarrierCap = 1u << 21;  // grid barriers per launch before E_ITER (a few seconds)
 
 // Grid barriers passed by this CTA in the current launch (reset by the kernel prologue).
@@ -213,6 +213,12 @@ __device__ __forceinline__ void fail(Ctl *ctl, int code, int where) {
 // false; every CTA that sees the flag returns false too, so the kernel ends in
 // bounded time and the host reports FR_ERR_ABORTED.  A single CTA synchronises
 // with __syncthreads only.
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool grid_sync(Ctl *ctl) {
     __shared__ int s_ok;
     __syncthreads();
@@ -220,25 +226,26 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl) {
         int ok = 1;
         if (++g_nsync > kBarrierCap) fail(ctl, E_ITER, 901);
         if (gridDim.x > 1) {
-            unsigned int gen = ld_acquire(&ctl->bar_gen);
-            __threadfence();
-            unsigned int prev = atomicAdd(&ctl->bar_count, 1u);
+            // The arrival is a release (it covers the block's writes ordered before it
+            // by the block barrier), the wait an acquire; the last arrival resets the
+            // count before it releases the next generation.
+            const unsigned int gen = ld_acquire(&ctl->bar_gen);
+            const unsigned int prev = atom_add_acq_rel(&ctl->bar_count, 1u);
             if (prev == gridDim.x - 1) {
-                atomicExch(&ctl->bar_count, 0u);
-                __threadfence();
+                *(volatile unsigned int *)&ctl->bar_count = 0u;
                 st_release(&ctl->bar_gen, gen + 1);
             } else {
                 unsigned int spins = 0;
                 while (ld_acquire(&ctl->bar_gen) == gen) {
-                    if (*(volatile int *)&ctl->abort) break;
-                    if (++spins > kSpinLimit) {
+                    ++spins;
+                    if ((spins & 255) == 0 && *(volatile int *)&ctl->abort) break;
+                    if (spins > kSpinLimit) {
                         fail(ctl, E_ABORT, 900);
                         break;
                     }
-                    if (spins > 32) __nanosleep(spins > 4096 ? 256 : 32);
+                    if (spins > 2048) __nanosleep(256);
                 }
             }
-            __threadfence();
         } else {
             __threadfence_block();
         }
