@@ -91,6 +91,7 @@ static size_t base_bytes(long long n, long long nnz, int k, int reps, int grid) 
     add(4, n); add(4, n);                                   // dist, lid
     add(4, n); add(4, n);                                   // vq_v, vq_s
     add(4, n / 32 + 2);                                     // cbits
+    add(4, n); add(4, n); add(4, 1);                        // bl, inb, blc
     for (int i = 0; i < 13; ++i) add(4, nu + 1);            // gid sid off infc fx lab rflag color scc vc fq0 fq1 ...
     add(8, nu); add(1, nu); add(1, nu);                     // ex border side_out
     for (int i = 0; i < 4; ++i) add(4, mu);                 // head rev res cap
@@ -211,6 +212,7 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     ctx->dist = carve<int>(p, nn); ctx->lid = carve<int>(p, nn);
     ctx->vq_v = carve<int>(p, nn); ctx->vq_s = carve<int>(p, nn);
     ctx->cbits = carve<unsigned int>(p, nn / 32 + 2);
+    ctx->bl = carve<int>(p, nn); ctx->inb = carve<int>(p, nn); ctx->blc = carve<int>(p, 1);
     ctx->gid = carve<int>(p, nu + 1); ctx->sid = carve<int>(p, nu + 1); ctx->off = carve<int>(p, nu + 1);
     ctx->infc = carve<int>(p, nu + 1); ctx->fx = carve<int>(p, nu + 1); ctx->lab = carve<int>(p, nu + 1);
     ctx->rflag = carve<int>(p, nu + 1); ctx->color = carve<int>(p, nu + 1); ctx->scc = carve<int>(p, nu + 1);
@@ -478,7 +480,7 @@ fr_status run_prep(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t 
     CK(cudaMemsetAsync(ctx->blockw, 0, sizeof(long long) * k, ctx->stream));
     if (quotient) CK(cudaMemsetAsync(ctx->qbits, 0, sizeof(unsigned int) * (((size_t)k * k + 31) / 32), ctx->stream));
     CK(launch_prep(g->xadj, g->adjncy, g->adjwgt, g->vwgt, part, g->n, g->nnz, k, ctx->blockw,
-                   quotient ? ctx->qbits : nullptr, ctx->prep, ctx->stream));
+                   quotient ? ctx->qbits : nullptr, ctx->prep, ctx->stream, ctx->bl, ctx->blc, ctx->inb));
     if (checked) CK(launch_check_symmetric(g->xadj, g->adjncy, g->adjwgt, g->n, ctx->prep, ctx->stream));
     if (quotient)
         CK(launch_color(ctx->qbits, k, ctx->pair_a, ctx->pair_b, ctx->pair_round, ctx->round_off, ctx->sob_round,
@@ -504,6 +506,7 @@ fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k,
     gd.xadj = g->xadj; gd.adjncy = g->adjncy; gd.adjwgt = g->adjwgt; gd.vwgt = g->vwgt;
     gd.part = part; gd.dist = ctx->dist; gd.lid = ctx->lid; gd.sob = ctx->sob1; gd.blockw = ctx->blockw;
     gd.n = g->n; gd.nnz = g->nnz; gd.k = k; gd.base = 0; gd.Lmax = Lmax;
+    gd.bl = ctx->bl; gd.blc = ctx->blc; gd.inb = ctx->inb;
     PairDev pd;
     pd.g = 0; pd.a = a; pd.b = b; pd.mb = mb; pd.Ubase = Ubase;
     char *h = ctx->h_stage + 1024;   // staging after the PrepOut slot
@@ -638,8 +641,7 @@ static fr_status run_pair_iteration(fr_ctx *ctx, const fr_graph *g, int32_t *par
     const double avgc = std::max(1.0, (double)W / g->n);
     const long long est = std::max<long long>(1, (long long)(2.0 * std::max(0LL, Ubase - W / k) / avgc));
     const int grid = choose_grid(ctx, opt, tpb, 2, est);
-    const bool vec = ((reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0);
-    CK(launch_scan(w, 0, g->n, vec, ctx->stream));
+    CK(launch_scan_list(w, 0, ctx->stream));
     CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, est, (double)g->nnz / g->n,
                     opt && opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
     char *h = ctx->h_stage + 2048;

@@ -56,6 +56,7 @@ fr_status run_pairs_step(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t 
     gd.xadj = g->xadj; gd.adjncy = g->adjncy; gd.adjwgt = g->adjwgt; gd.vwgt = g->vwgt;
     gd.part = part; gd.dist = ctx->dist; gd.lid = ctx->lid; gd.sob = ctx->sob1; gd.blockw = ctx->blockw;
     gd.n = g->n; gd.nnz = g->nnz; gd.k = k; gd.base = 0; gd.Lmax = Lmax;
+    gd.bl = ctx->bl; gd.blc = ctx->blc; gd.inb = ctx->inb;
     memcpy(h, &gd, sizeof(gd));
     PairDev *hp = reinterpret_cast<PairDev *>(h + 1024);
     int *hs = reinterpret_cast<int *>(hp + P);
@@ -86,8 +87,7 @@ fr_status run_pairs_step(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t 
         emax = std::max(emax, e1);
     }
     const int grid = choose_grid(ctx, opt, tpb, 2 * P, std::max(1LL, est));
-    const bool vec = (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0;
-    CK(launch_scan(w, 0, g->n, vec, ctx->stream));
+    CK(launch_scan_list(w, 0, ctx->stream));
     CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, emax, (double)g->nnz / g->n,
                     opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
     PairAcc *ha = reinterpret_cast<PairAcc *>(ctx->h_stage + (kHostStage / 2));

@@ -96,7 +96,7 @@ extern "C" fr_status fr_build_corridor(fr_ctx *ctx, const fr_graph *g, const int
     Work w = make_work(ctx, 0, 0, 1, g->n, &opt);
     const int tpb = choose_tpb(ctx, &opt);
     const int grid = choose_grid(ctx, &opt, tpb, 2, std::max<long long>(1, 2 * Ubase));
-    CK(launch_scan(w, 0, g->n, (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0, ctx->stream));
+    CK(launch_scan_list(w, 0, ctx->stream));
     CK(launch_step(w, PH_BFS | PH_LID | PH_BUILD, grid, tpb, ctx->stream));
     PairAcc A;
     Ctl C;
@@ -339,12 +339,11 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
     CK(cudaMemsetAsync(ctx->sides, 0, sizeof(SideDev) * 2 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc) * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * (size_t)np * kHistBins, ctx->stream));
-    const bool vec = (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0;
     long long nl = 3;   // prep, colouring, pair fill
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
-        CK(launch_scan(w, 0, g->n, vec, ctx->stream));
+        CK(launch_scan_list(w, 0, ctx->stream));
         CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr, pl.est_max[r], pl.avg_degree,
                         opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
         nl += 1 + ctx->round_launches;
@@ -366,13 +365,12 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
     CK(cudaMemsetAsync(ctx->sides, 0, sizeof(SideDev) * 2 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc) * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * (size_t)np * kHistBins, ctx->stream));
-    const bool vec = (reinterpret_cast<uintptr_t>(g->adjncy) & 15) == 0;
     long long nl = 3;
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
         CK(cudaEventRecord(ctx->pev[8 * r], ctx->stream));
-        CK(launch_scan(w, 0, g->n, vec, ctx->stream));
+        CK(launch_scan_list(w, 0, ctx->stream));
         CK(cudaEventRecord(ctx->pev[8 * r + 1], ctx->stream));
         CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, &ctx->pev[8 * r + 2], pl.est_max[r],
                         pl.avg_degree, opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
@@ -394,6 +392,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
         gd.sob = ctx->sob_round + (long long)r * pl.k;
         gd.blockw = ctx->blockw;
         gd.n = g->n; gd.nnz = g->nnz; gd.k = pl.k; gd.base = 0; gd.Lmax = pl.Lmax;
+        gd.bl = ctx->bl; gd.blc = ctx->blc; gd.inb = ctx->inb;
     }
     memcpy(ctx->h_stage + 16384, gds.data(), sizeof(GraphDev) * pl.nr);
     CK(cudaMemcpyAsync(ctx->graphs, ctx->h_stage + 16384, sizeof(GraphDev) * pl.nr, cudaMemcpyHostToDevice,

@@ -45,6 +45,7 @@ struct fr_ctx {
     int n_cap = 0, nnz_cap = 0, k_cap = 0, reps_cap = 0;
     int *dist = nullptr, *lid = nullptr, *vq_v = nullptr, *vq_s = nullptr;
     unsigned int *cbits = nullptr;
+    int *bl = nullptr, *blc = nullptr, *inb = nullptr;   // boundary candidates of the current sweep
     int *gid = nullptr, *sid = nullptr, *off = nullptr, *infc = nullptr, *fx = nullptr, *lab = nullptr;
     int *rflag = nullptr, *color = nullptr, *scc = nullptr, *vc = nullptr, *fq0 = nullptr, *fq1 = nullptr;
     int *spare = nullptr;

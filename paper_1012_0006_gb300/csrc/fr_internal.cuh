@@ -59,6 +59,12 @@ struct GraphDev {
     long long Lmax;
     int sbase;           // sob values are relative to this graph's first side in the step
     int ebase;           // offset of this graph's CSR entries in the concatenated arc range
+    // boundary candidates (optional; NULL: the boundary scan reads every vertex): every
+    // vertex with a neighbour in another block is on the list bl[0, *blc), inb[v] = 1
+    // marks the listed ones; the commit phase appends moved vertices and their
+    // neighbours, so the list stays a superset of the boundary during a sweep
+    int *bl, *blc;
+    int *inb;
 };
 
 // Side of block `blk` of graph Gr in this step, or -1.

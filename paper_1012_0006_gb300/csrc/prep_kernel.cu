@@ -23,7 +23,7 @@ constexpr int kSmemQuotientK = 256;   // k up to this keeps the quotient bits in
 __global__ void __launch_bounds__(kPrepTPB)
 prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const int *__restrict__ adjwgt,
             const int *__restrict__ vwgt, const int *__restrict__ part, int n, int nnz, int k, long long *blockw,
-            unsigned int *qbits, PrepOut *out) {
+            unsigned int *qbits, PrepOut *out, int *inb) {
     extern __shared__ unsigned int s_dyn[];
     // shared: block weights [k] (long long) when k <= 4096, quotient bits when k <= 256
     const bool smem_w = k <= 4096;
@@ -57,6 +57,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
             continue;
         }
         long long wdeg = 0;
+        bool bnd = false;
         for (int j = r0; j < r1; ++j) {
             const int u = adjncy[j];
             const int om = adjwgt[j];
@@ -67,6 +68,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
             wdeg += om;
             if (om > maxw) maxw = om;
             const int pu = part[u];
+            bnd |= pu != pv;
             if (pu > pv && pu < k) {
                 cut += om;
                 const int bit = pv * k + pu;
@@ -75,6 +77,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
             }
         }
         if (wdeg >= (1LL << 30) && err == 0) err = E_TOO_LARGE;
+        if (inb) inb[v] = bnd ? 1 : 0;
     }
     __syncthreads();
     if (smem_w)
@@ -206,14 +209,35 @@ static int grid_for(long long n, int tpb) {
     return (int)b;
 }
 
+// The marked vertices in increasing order per warp of 32 (one atomic per warp).
+__global__ void __launch_bounds__(kPrepTPB) compact_kernel(const int *inb, int n, int *bl, int *blc) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (kPrepTPB / 32);
+    for (long long b = ((long long)blockIdx.x * (kPrepTPB / 32) + (threadIdx.x >> 5)) * 32; b < n; b += nw * 32) {
+        const long long v = b + lane;
+        const bool f = v < n && inb[v];
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(blc, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (f) bl[base + __popc(m & ((1u << lane) - 1u))] = (int)v;
+    }
+}
+
 cudaError_t launch_prep(const int *xadj, const int *adjncy, const int *adjwgt, const int *vwgt, const int *part,
                         int n, int nnz, int k, long long *blockw, unsigned int *qbits, PrepOut *out,
-                        cudaStream_t st) {
+                        cudaStream_t st, int *bl, int *blc, int *inb) {
     size_t sm = 0;
     if (k <= 4096) sm += sizeof(long long) * k;
     if (qbits && k <= kSmemQuotientK) sm += sizeof(unsigned int) * ((k * k + 31) / 32);
     prep_kernel<<<grid_for(n, kPrepTPB), kPrepTPB, sm, st>>>(xadj, adjncy, adjwgt, vwgt, part, n, nnz, k, blockw,
-                                                            qbits, out);
+                                                            qbits, out, bl ? inb : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !bl) return e;
+    e = cudaMemsetAsync(blc, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    compact_kernel<<<grid_for(n, kPrepTPB), kPrepTPB, 0, st>>>(inb, n, bl, blc);
     return cudaGetLastError();
 }
 

@@ -131,6 +131,99 @@ __global__ void __launch_bounds__(TPB) scan_kernel(Work w, int g) {
         if (s_cut[i]) atomicAddLL(&w.pacc[i].oldcut, s_cut[i]);
 }
 
+// S1 over the boundary candidates (GraphDev.bl): each warp takes 32 listed
+// vertices, spreads the adjacency rows of those in the round's blocks over its
+// lanes, and a vertex is a seed when it has a neighbour in its pair's other block;
+// omega(E_ab) sums the arcs seen from the lower-numbered block.  The list holds
+// every vertex with a neighbour in another block, so the seeds and the cut are
+// those of the full scan.
+template <int TPB>
+__global__ void __launch_bounds__(TPB) scan_list_kernel(Work w, int g) {
+    extern __shared__ long long s_cut[];   // [npairs]
+    __shared__ int s_seed[TPB];
+    if (w.prev_err && __ldcg(w.prev_err)) {   // an earlier round failed: propagate, do nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) { w.ctl->error = E_ABORT; w.ctl->error_where = 999; }
+        return;
+    }
+    const GraphDev G = w.graphs[g];
+    for (int i = threadIdx.x; i < w.npairs; i += TPB) s_cut[i] = 0;
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < w.nsides; s += TPB) {
+            const PairDev P = w.pairs[s >> 1];
+            if (P.g == g) w.sides[s].cw = G.blockw[(s & 1) ? P.b : P.a];
+        }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wslot = threadIdx.x & ~31;
+    const long long nw = (long long)gridDim.x * (TPB / 32);
+    const long long gw = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
+    const int cnt = __ldcg(G.blc);
+    for (long long base = gw * 32; base < cnt; base += nw * 32) {
+        const long long li = base + lane;
+        int v = 0, blk = -1, sd = -1, pb = -2, rs = 0, deg = 0;
+        if (li < cnt) {
+            v = __ldcg(G.bl + li);
+            blk = __ldg(G.part + v);
+            sd = side_of(G, blk);
+        }
+        if (__ballot_sync(FULL, sd >= 0) == 0) continue;
+        if (sd >= 0) {
+            const PairDev P = w.pairs[sd >> 1];
+            pb = (sd & 1) ? P.a : P.b;
+            rs = __ldg(G.xadj + v);
+            deg = __ldg(G.xadj + v + 1) - rs;
+        }
+        int incl = deg;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - deg;
+        s_seed[threadIdx.x] = 0;
+        __syncwarp();
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(FULL, incl, src + step - 1) <= t) src += step;
+            const int rs_s = __shfl_sync(FULL, rs, src);
+            const int ex_s = __shfl_sync(FULL, excl, src);
+            const int pb_s = __shfl_sync(FULL, pb, src);
+            const int blk_s = __shfl_sync(FULL, blk, src);
+            const int sd_s = __shfl_sync(FULL, sd, src);
+            if (t < total) {
+                const int e = rs_s + (t - ex_s);
+                const int u = __ldg(G.adjncy + e);
+                if (__ldg(G.part + u) == pb_s) {
+                    s_seed[wslot + src] = 1;
+                    if (blk_s < pb_s)
+                        atomicAdd((unsigned long long *)&s_cut[sd_s >> 1], (unsigned long long)__ldg(G.adjwgt + e));
+                }
+            }
+        }
+        __syncwarp();
+        const bool seed = sd >= 0 && s_seed[threadIdx.x] != 0;
+        if (seed) G.dist[v] = 0;
+        const int pos = warp_agg_inc(&w.ctl->qcnt[0], seed);
+        if (seed) {
+            if (pos < w.vq_cap) {
+                w.vq_v[pos] = v;
+                w.vq_s[pos] = sd;
+            } else {
+                fail(w.ctl, E_INTERNAL, 1);
+            }
+        }
+        warp_agg_add(seed ? &w.sides[sd].lw[0] : nullptr, seed ? (long long)__ldg(G.vwgt + v) : 0, seed);
+        warp_agg_inc(seed ? &w.sides[sd].lc[0] : nullptr, seed);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < w.npairs; i += TPB)
+        if (s_cut[i]) atomicAddLL(&w.pacc[i].oldcut, s_cut[i]);
+}
+
 // ============================================================ step helpers ==
 
 struct Grid {
@@ -1428,7 +1521,21 @@ struct StepKernel {
                 if (!__ldcg(&w.pacc[p].accept)) continue;
                 const PairDev Pd = w.pairs[p];
                 const int nb = w.side_out[i] ? Pd.b : Pd.a;
-                w.graphs[Pd.g].part[w.gid[i]] = nb;
+                const GraphDev &Gr = w.graphs[Pd.g];
+                const int v = w.gid[i];
+                Gr.part[v] = nb;
+                const int ob = (s & 1) ? Pd.b : Pd.a;
+                if (Gr.bl && nb != ob) {
+                    // A moved vertex may now be on a boundary, and so may its neighbours
+                    // in its old block (the others had it as a foreign neighbour already).
+                    if (!__ldcg(Gr.inb + v) && atomicExch(Gr.inb + v, 1) == 0) Gr.bl[atomicAdd(Gr.blc, 1)] = v;
+                    const int j1 = __ldg(Gr.xadj + v + 1);
+                    for (int j = __ldg(Gr.xadj + v); j < j1; ++j) {
+                        const int x = __ldg(Gr.adjncy + j);
+                        if (__ldcg(Gr.inb + x)) continue;
+                        if (Gr.part[x] == ob && atomicExch(Gr.inb + x, 1) == 0) Gr.bl[atomicAdd(Gr.blc, 1)] = x;
+                    }
+                }
             }
         }
         for (long long e = G.tid; e < vtotal; e += G.size) {
@@ -1527,6 +1634,15 @@ cudaError_t step_max_grid(int tpb, int nsides, int *max_blocks, int *sms) {
     *max_blocks = per * nsm;
     *sms = nsm;
     return cudaSuccess;
+}
+
+cudaError_t launch_scan_list(const Work &w, int g, cudaStream_t st) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t sm = (size_t)w.npairs * sizeof(long long);
+    scan_list_kernel<256><<<nsm * 8, 256, sm, st>>>(w, g);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const Work &w, int g, int n, bool vec, cudaStream_t st) {

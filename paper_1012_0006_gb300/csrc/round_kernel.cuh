@@ -23,9 +23,13 @@ struct PrepOut {
     int npairs, nrounds;
     int maxw, pad;       // max edge weight
 };
+// bl, blc, inb (optional, all or none): the boundary candidate list of the sweep
+// (GraphDev.bl); inb needs no clearing, prep writes every entry.
 cudaError_t launch_prep(const int *xadj, const int *adjncy, const int *adjwgt, const int *vwgt, const int *part,
                         int n, int nnz, int k, long long *blockw, unsigned int *qbits, PrepOut *out,
-                        cudaStream_t st);
+                        cudaStream_t st, int *bl = nullptr, int *blc = nullptr, int *inb = nullptr);
+// The boundary scan over the candidate list of graph g (GraphDev.bl must be set).
+cudaError_t launch_scan_list(const Work &w, int g, cudaStream_t st);
 cudaError_t launch_check_symmetric(const int *xadj, const int *adjncy, const int *adjwgt, int n, PrepOut *out,
                                    cudaStream_t st);
 cudaError_t launch_color(const unsigned int *qbits, int k, int *pair_a, int *pair_b, int *pair_round,
