@@ -241,7 +241,7 @@ def run_ours(args, world, rank, local, pg):
         best, ms = ctx.autotune(g, part0, k, eps, alpha, opts, trials=1)
         tuned = dict(block_threads=best.block_threads, grid_blocks=best.grid_blocks, gr_interval=best.gr_interval,
                      inner_ops=best.inner_ops, pulse_passes=best.pulse_passes, cluster_ctas=best.cluster_ctas,
-                     flow_sched=best.flow_sched,
+                     flow_sched=best.flow_sched, pre_waves=best.pre_waves,
                      ms=round(ms, 3))
         log(f"[rank {rank}] autotune {tuned} in {time.time() - t0:.1f}s")
 

@@ -81,6 +81,9 @@ typedef struct fr_options {
     int32_t cluster_ctas;  /* CTAs of the first per-pair cluster launch (4, 6, 8, 12 or 16); 0 = by the
                               estimated corridor size.  Pairs that do not fit go to 16-CTA
                               clusters, then to the grid-wide flow; results do not depend on it */
+    int32_t pre_waves;     /* cluster pulses: level-ordered waves before the first pulse (0-2);
+                              -1 = none, 0 = tuned default */
+    int32_t pad0;
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b). */
@@ -270,8 +273,9 @@ fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info);
 /* ---- launch-shape autotuner -------------------------------------------------- */
 
 /* Times fr_refine_batch on a copy of part for a set of launch shapes
- * (block_threads, grid_blocks, gr_interval, inner_ops, pulse_passes, cluster_ctas, flow_sched;
- * coordinate descent, two sweeps) and writes the fastest into *best.  Results are
+ * (block_threads, grid_blocks, gr_interval, inner_ops, pulse_passes, cluster_ctas,
+ * flow_sched, pre_waves; coordinate descent, two sweeps) and writes the fastest into
+ * *best.  Results are
  * identical for every shape; only time differs.  The choice is also cached in the
  * context and used when opt fields are 0. */
 fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, double eps, double alpha,

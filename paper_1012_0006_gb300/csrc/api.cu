@@ -316,6 +316,7 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.seed = opt ? opt->seed : 0;
     w.pulse_cap = opt && opt->pulse_cap > 0 ? opt->pulse_cap : (1LL << 20);
     w.narrow = ctx->narrow_ok;
+    w.pre_waves = opt && opt->pre_waves ? (opt->pre_waves < 0 ? 0 : opt->pre_waves) : ctx->tune_prewaves;
     return w;
 }
 
@@ -461,6 +462,10 @@ fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *
             return FR_ERR_INVALID_ARG;
         }
         if (opt->mb_reps > 64) { ctx_error(ctx, "mb_reps > 64"); return FR_ERR_INVALID_ARG; }
+        if (opt->pre_waves < -1 || opt->pre_waves > 4) {
+            ctx_error(ctx, "pre_waves must be in [-1, 4]");
+            return FR_ERR_INVALID_ARG;
+        }
         if (opt->cluster_ctas != 0) {
             bool known = false;
             for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) known |= opt->cluster_ctas == fr_ctx::kClusterSizes[t];

@@ -405,7 +405,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
                                   opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas, ctx->tune_sched,
-                                  ctx->narrow_ok};
+                                  ctx->narrow_ok, opt->pre_waves, ctx->tune_prewaves};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
@@ -756,15 +756,18 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     cand.cluster_ctas = base.cluster_ctas ? base.cluster_ctas : ctx->tune_ctas;
     cand.flow_sched = base.flow_sched ? base.flow_sched : (ctx->tune_sched ? ctx->tune_sched : 2);
     const std::vector<int> scheds = {2, 1};
+    const std::vector<int> prewaves = {-1, 1, 2};
+    cand.pre_waves = base.pre_waves ? base.pre_waves : (ctx->tune_prewaves ? ctx->tune_prewaves : -1);
     for (int sweep = 0; sweep < 2 && st == FR_OK; ++sweep) {
-        for (int dim = 0; dim < 7 && st == FR_OK; ++dim) {
+        for (int dim = 0; dim < 8 && st == FR_OK; ++dim) {
             const std::vector<int> &vals = dim == 0   ? tpbs
                                            : dim == 1 ? grids
                                            : dim == 2 ? grs
                                            : dim == 3 ? inners
                                            : dim == 4 ? passes
                                            : dim == 5 ? ctas
-                                                      : scheds;
+                                           : dim == 6 ? scheds
+                                                      : prewaves;
             for (int v : vals) {
                 fr_options o = cand;
                 if (dim == 0) o.block_threads = v;
@@ -774,6 +777,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
                 if (dim == 4) o.pulse_passes = v;
                 if (dim == 5) o.cluster_ctas = v;
                 if (dim == 6) o.flow_sched = v;
+                if (dim == 7) o.pre_waves = v;
                 if (memcmp(&o, &cand, sizeof(o)) == 0) continue;
                 double ms = 0;
                 st = time_shape(o, &ms);
@@ -791,6 +795,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     ctx->tune_passes = cand.pulse_passes;
     ctx->tune_ctas = cand.cluster_ctas;
     ctx->tune_sched = cand.flow_sched;
+    ctx->tune_prewaves = cand.pre_waves > 0 ? cand.pre_waves : 0;
     if (best) *best = cand;
     if (best_ms) *best_ms = bms;
     return FR_OK;

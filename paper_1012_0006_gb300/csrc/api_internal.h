@@ -31,6 +31,7 @@ struct fr_ctx {
     int tune_tpb = 512, tune_grid = 0, tune_gr = 16, tune_inner = 2, tune_passes = 2;
     int tune_ctas = 0;   // first cluster size (0: by the estimated corridor size)
     int tune_sched = 0;  // cluster max-flow schedule (fr_options.flow_sched)
+    int tune_prewaves = 0;   // waves before the first pulse (fr_options.pre_waves)
     int narrow_ok = 0;   // the last prep found every edge weight < 2^15 (packed residuals in clusters)
     // per-pair max flow in thread-block clusters of kClusterSizes[t] CTAs: how many of
     // each can be resident (all 0: grid-wide path only); max_clusters = the largest

@@ -624,6 +624,53 @@ struct ClusterFlow {
     // own excess and of the residuals of its arcs and their reverses, so only the
     // excess of the receiving vertex needs an atomic.  Phase 0 sends excess to t,
     // phase 1 returns what is left to s.
+    // One wave: the levels from the top down, each level pushing only along
+    // admissible arcs into the level below (level 1 into the target), one cluster
+    // barrier per level.  Within a level step a vertex is the only writer of its own
+    // excess and of the residuals of its arcs and their reverses, so only the excess
+    // of the receiving vertex needs an atomic.
+    __device__ void wave_levels(int ph, int nv, int top) {
+        for (int L = top; L >= 1; --L) {
+            for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                if (lab[lv] != L) continue;
+                int e = ex[lv];
+                if (e <= 0) continue;
+                if (L == 1) {
+                    if (!ph) { fx[lv] += e; e = 0; }
+                    else if (bord[lv] == 1) { const int d = e < fx[lv] ? e : fx[lv]; fx[lv] -= d; e -= d; }
+                } else {
+                    const int a1 = cofs[lv + 1];
+                    for (int a = cofs[lv]; a < a1 && e > 0; a += U) {
+                        int r[U], hr[U], l[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            r[u] = a + u < a1 ? rs(a + u) : 0;
+                            hr[u] = a + u < a1 ? (int)hadr[a + u] : 0;
+                            l[u] = a + u < a1 ? hlab[a + u] : -1;
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? l[u] : -1;
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (e > 0 && l[u] == L - 1) {
+                                const int d = e < r[u] ? e : r[u];
+                                set_rs(a + u, r[u] - d);
+                                dsm_add(radr[a + u], d);
+                                dsm_add((unsigned)hr[u] + o_ex, d);
+                                e -= d;
+                            }
+                        }
+                    }
+                }
+                ex[lv] = e;
+            }
+            sync();
+        }
+    }
+
+    // Push-relabel in waves: exact labels, then one wave; repeat until no vertex
+    // with excess can reach the target.  Phase 0 sends excess to t, phase 1 returns
+    // what is left to s.
     __device__ bool phase_wave(int ph, int nv, int hmax) {
         long long waves = 0;
         for (;;) {
@@ -632,42 +679,7 @@ struct ClusterFlow {
             for (int lv = threadIdx.x; lv < nv; lv += TPB) act += ex[lv] > 0 && lab[lv] < hmax;
             if (cluster_sum(act) == 0) break;
             if (++waves > w.pulse_cap) return false;
-            for (int L = top; L >= 1; --L) {
-                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
-                    if (lab[lv] != L) continue;
-                    int e = ex[lv];
-                    if (e <= 0) continue;
-                    if (L == 1) {
-                        if (!ph) { fx[lv] += e; e = 0; }
-                        else if (bord[lv] == 1) { const int d = e < fx[lv] ? e : fx[lv]; fx[lv] -= d; e -= d; }
-                    } else {
-                        const int a1 = cofs[lv + 1];
-                        for (int a = cofs[lv]; a < a1 && e > 0; a += U) {
-                            int r[U], hr[U], l[U];
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                r[u] = a + u < a1 ? rs(a + u) : 0;
-                                hr[u] = a + u < a1 ? (int)hadr[a + u] : 0;
-                                l[u] = a + u < a1 ? hlab[a + u] : -1;
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? l[u] : -1;
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                if (e > 0 && l[u] == L - 1) {
-                                    const int d = e < r[u] ? e : r[u];
-                                    set_rs(a + u, r[u] - d);
-                                    dsm_add(radr[a + u], d);
-                                    dsm_add((unsigned)hr[u] + o_ex, d);
-                                    e -= d;
-                                }
-                            }
-                        }
-                    }
-                    ex[lv] = e;
-                }
-                sync();
-            }
+            wave_levels(ph, nv, top);
         }
         if (rank == 0 && threadIdx.x == 0) {
             atomicAddLL(&w.ctl->pulses, waves);
@@ -681,7 +693,15 @@ struct ClusterFlow {
     // certify: end only after an exact relabel confirms that no excess can move
     // (phase 1; phase 0 is checked by the residual sets instead).
     __device__ bool phase_pulse(int ph, int nv, int hmax, bool certify) {
-        relabel(ph, nv, hmax);
+        {
+            // w.pre_waves waves first move the bulk of the excess along shortest paths
+            // (labels stay valid: pushes go one level down); the pulses finish
+            const int top = relabel(ph, nv, hmax, w.pre_waves > 0);
+            for (int k = 0; k < w.pre_waves; ++k) {
+                wave_levels(ph, nv, top);
+                if (k + 1 < w.pre_waves) relabel(ph, nv, hmax);
+            }
+        }
         long long pulses = 0, relabels = 1;
         int since = 0;
         for (;;) {

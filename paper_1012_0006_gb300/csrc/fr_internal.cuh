@@ -171,6 +171,8 @@ struct Work {
     int cl_tier;                 // cluster launch: 0 every pair, 1 the pairs the first left
     int full_flow;               // 1: return every excess to s (a flow); 0: a maximum preflow
     int narrow;                  // 1: every arc capacity < 2^15 (cluster kernel packs residual and capacity sum)
+    int pre_waves;               // cluster pulses: waves by levels before the first pulse
+    int pad_w2;
     unsigned long long seed;
     long long pulse_cap;
 };

@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
-                ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32)]
+                ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
+                ("pre_waves", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
