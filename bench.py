@@ -201,7 +201,9 @@ def recorded_traffic(kernel):
 def bytes_model(P):
     """Algorithmic HBM bytes per kernel type for one sweep (element bytes the method must touch)."""
     n, nnz = P["n"], P["nnz"]
-    scan = (8 * n + 8 * nnz + 4) * P["nrounds"]            # xadj, part[v], adjncy, part[u]
+    # boundary scan over the candidate list: entry and part[v] per listed vertex,
+    # xadj per row of the round's blocks, adjncy and part[u] per arc of those rows
+    scan = 8 * P["scan_listed"] + 8 * P["scan_rows"] + 8 * P["scan_arcs"]
     vis, arcs = P["bfs_visited"], P["bfs_arcs"]
     nc, m = P["corridor_n"], P["corridor_arcs"]
     bfs = 16 * vis + 12 * arcs                              # queue entries, dist, adjncy + part + dist per arc
@@ -321,7 +323,7 @@ def run_ours(args, world, rank, local, pg):
         "counters": {kk: P[kk] for kk in ("bfs_visited", "bfs_arcs", "corridor_n", "corridor_arcs", "pulses",
                                            "relabels", "gr_arcs", "pr_arcs", "pushes", "scc_rounds",
                                            "barriers", "cluster_syncs", "cluster_remote_arcs",
-                                           "fallback_pairs")},
+                                           "fallback_pairs", "scan_listed", "scan_rows", "scan_arcs")},
     })
 
     # end to end through the host-buffer entry point: H2D of graph and part, D2H of part

@@ -261,6 +261,9 @@ typedef struct fr_profile_info {
     int64_t cluster_syncs;    /* cluster barriers, summed over pairs */
     int64_t cluster_remote_arcs; /* arcs held in a cluster whose head another CTA holds (DSMEM) */
     int64_t fallback_pairs;   /* pairs left to the grid-wide flow */
+    int64_t scan_listed;      /* boundary-scan list entries read, summed over rounds */
+    int64_t scan_rows;        /* of them, vertices of the rounds' blocks (rows scanned) */
+    int64_t scan_arcs;        /* arcs of those rows */
     int32_t cluster_sizes[5]; /* CTAs per cluster the library can launch (4, 6, 8, 12, 16) */
     int32_t cluster_max_active[5]; /* clusters of each size resident at once on this GPU */
 } fr_profile_info;

@@ -595,6 +595,9 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             for (int t = 0; t < 6; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
             P.cluster_syncs += C[r].cl_syncs;
             P.cluster_remote_arcs += C[r].cl_remote;
+            P.scan_listed += C[r].scan_listed;
+            P.scan_rows += C[r].scan_rows;
+            P.scan_arcs += C[r].scan_arcs;
             P.fallback_pairs += C[r].fallback;
         }
     }

@@ -128,6 +128,7 @@ struct Ctl {
     long long barriers;       // grid barriers passed (CTA 0)
     long long cl_syncs;       // cluster barriers, summed over pairs
     long long cl_remote;      // cluster-held arcs whose head is in another CTA's shared memory
+    long long scan_listed, scan_rows, scan_arcs;   // boundary-list scan: entries, rows in the round, arcs
     int fallback;             // pairs the cluster kernels left to the grid-wide flow
     int cl_next[2];           // next slot of the size order each cluster launch takes
     int cl_left;              // pairs the first cluster launch left (written by it only)

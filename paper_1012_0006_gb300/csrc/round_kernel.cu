@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(TPB) scan_list_kernel(Work w, int g) {
     const long long nw = (long long)gridDim.x * (TPB / 32);
     const long long gw = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
     const int cnt = __ldcg(G.blc);
+    long long n_rows = 0, n_arcs = 0;
     for (long long base = gw * 32; base < cnt; base += nw * 32) {
         const long long li = base + lane;
         int v = 0, blk = -1, sd = -1, pb = -2, rs = 0, deg = 0;
@@ -181,6 +182,8 @@ __global__ void __launch_bounds__(TPB) scan_list_kernel(Work w, int g) {
         }
         const int total = __shfl_sync(FULL, incl, 31);
         const int excl = incl - deg;
+        n_rows += sd >= 0;
+        n_arcs += deg;
         s_seed[threadIdx.x] = 0;
         __syncwarp();
         for (int t0 = 0; t0 < total; t0 += 32) {
@@ -218,6 +221,13 @@ __global__ void __launch_bounds__(TPB) scan_list_kernel(Work w, int g) {
         }
         warp_agg_add(seed ? &w.sides[sd].lw[0] : nullptr, seed ? (long long)__ldg(G.vwgt + v) : 0, seed);
         warp_agg_inc(seed ? &w.sides[sd].lc[0] : nullptr, seed);
+    }
+    n_rows = block_sum_ll<TPB>(n_rows);
+    n_arcs = block_sum_ll<TPB>(n_arcs);
+    if (threadIdx.x == 0) {
+        if (n_rows) atomicAddLL(&w.ctl->scan_rows, n_rows);
+        if (n_arcs) atomicAddLL(&w.ctl->scan_arcs, n_arcs);
+        if (blockIdx.x == 0) atomicAddLL(&w.ctl->scan_listed, (long long)cnt);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < w.npairs; i += TPB)

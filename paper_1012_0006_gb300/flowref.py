@@ -73,6 +73,7 @@ class ProfileInfo(ctypes.Structure):
                 ("cluster_phase_ms", ctypes.c_double * 6), ("cluster_syncs", ctypes.c_int64),
                 ("cluster_remote_arcs", ctypes.c_int64),
                 ("fallback_pairs", ctypes.c_int64),
+                ("scan_listed", ctypes.c_int64), ("scan_rows", ctypes.c_int64), ("scan_arcs", ctypes.c_int64),
                 ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
