@@ -177,10 +177,15 @@ def measured_peak_gbs():
 
 
 def kernel_source_hash():
+    """Hash of the CUDA sources and headers (a recorded DRAM traffic is used only while
+    they are unchanged)."""
     h = hashlib.sha256()
-    for f in ("round_kernel.cu", "fr_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1012_0006_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_1012_0006_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
