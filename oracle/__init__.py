@@ -86,6 +86,11 @@ def lib():
         L.fro_refine_batch_sample.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
                                               ctypes.c_int32, i32p]
+        L.fro_refine_batch_mt.restype = ctypes.c_int32
+        L.fro_refine_batch_mt.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(PairResult), i32p, i32p,
+                                          i32p]
         L.fro_refine_active.restype = ctypes.c_int32
         L.fro_refine_active.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
                                         ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
@@ -274,3 +279,22 @@ def refine_batch_sample(w, max_pairs, part=None, opts=None):
                                        _p(part), w["k"], w["eps"], w["alpha"], ctypes.byref(opts), max_pairs,
                                        ctypes.byref(done))
     return st, part, done.value
+
+
+def refine_batch_mt(w, nthreads, max_rounds=-1, part=None, eps=None, alpha=None, opts=None):
+    """The sweep with the pairs of each round on up to nthreads threads
+    (fro_refine_batch_mt); returns (status, part, results, rounds, pairs done)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    alpha = w["alpha"] if alpha is None else alpha
+    if opts is None:
+        opts = options(mb=w.get("mb", 0), adaptive=w.get("adaptive", 0), max_iters=w.get("max_iters", 1),
+                       alpha_max=w.get("alpha_max", alpha))
+    k = w["k"]
+    cap = max(1, k * (k - 1) // 2)
+    res = (PairResult * cap)()
+    npairs, nrounds, done = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    st = lib().fro_refine_batch_mt(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]),
+                                   _p(part), k, eps, alpha, ctypes.byref(opts), nthreads, max_rounds, cap, res,
+                                   ctypes.byref(npairs), ctypes.byref(nrounds), ctypes.byref(done))
+    return st, part, [res[i].as_dict() for i in range(min(done.value, cap))], nrounds.value, done.value

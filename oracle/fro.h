@@ -136,6 +136,14 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
                                 const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                                 const fro_options *opt, int32_t max_pairs, int32_t *done);
 
+/* The sweep of fro_refine_batch with the pairs of each round refined on up to
+ * nthreads threads (pair-parallel CPU baseline; identical results, same order),
+ * stopped after max_rounds rounds (all if < 0).  done = pairs refined. */
+int32_t fro_refine_batch_mt(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                            const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
+                            const fro_options *opt, int32_t nthreads, int32_t max_rounds, int32_t cap,
+                            fro_pair_result *res, int32_t *npairs, int32_t *nrounds, int32_t *done);
+
 /* Active block scheduling with flow refinement of each scheduled pair (adaptive
  * flow iterations if opt->adaptive): outer rounds over the quotient edges with an
  * active end until no block is active or max_outer rounds ran.  Per-pair results in

@@ -94,3 +94,31 @@ def test_first_outer_round_is_the_batch():
         assert np.array_equal(p1, p2)
         assert [(r["a"], r["b"], r["round"], r["accepted"], r["cut_after"]) for r in r1] == \
                [(r["a"], r["b"], r["round"], r["accepted"], r["cut_after"]) for r in r2]
+
+
+@pytest.mark.parametrize("nthreads", [1, 3, 8])
+def test_pair_parallel_sweep_is_the_sequential_sweep(nthreads):
+    """The pairs of a round are a matching (disjoint blocks), so refining them side
+    by side on copies of the round's starting partition must give the sequential
+    sweep exactly: same partition, same per-pair results in the same order."""
+    cases = [I.random_small(4300 + s, n_max=2500, k_max=8) for s in range(4)] + [I.config(3, scale=1 / 64)]
+    for i, w in enumerate(cases):
+        opts = O.options(mb=i % 2, mb_reps=1 + i % 2, seed=i, adaptive=i % 3 == 2, max_iters=4,
+                         alpha_max=8.0)
+        st, p1, r1, nr1 = O.refine_batch(w, opts=opts)
+        st2, p2, r2, nr2, done = O.refine_batch_mt(w, nthreads, opts=opts)
+        assert st == st2 == 0 and nr1 == nr2 and done == len(r1)
+        assert np.array_equal(p1, p2)
+        assert r1 == r2
+
+
+def test_pair_parallel_sweep_stops_after_max_rounds():
+    w = I.config(3, scale=1 / 64)
+    opts = O.options(mb=1)
+    pa, pb, pr, nr = O.rounds(w)
+    assert nr >= 2
+    st, part, res, nr2, done = O.refine_batch_mt(w, 4, max_rounds=1, opts=opts)
+    assert st == 0 and nr2 == nr and done == int((pr == 0).sum())
+    assert all(r["round"] == 0 for r in res)
+    _, pseq, rseq, _ = O.refine_batch(w, opts=opts)
+    assert res == rseq[:done]
