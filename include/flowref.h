@@ -124,6 +124,12 @@ typedef struct fr_batch_result {
  * seed 0, pulse_cap 1<<20, checked 0, launch shape 0 (tuned). */
 void fr_default_options(fr_options *opt);
 
+/* sizeof of the structs of this header, for bindings to check their layouts:
+ * which = 0 fr_graph, 1 fr_options, 2 fr_pair_result, 3 fr_batch_result,
+ * 4 fr_profile_info, 5 fr_server_config, 6 fr_request, 7 fr_response; -1 for
+ * any other value.  Needs no device. */
+int32_t fr_struct_size(int32_t which);
+
 /* Creates a context on `device` using `stream` (a cudaStream_t; NULL = a new
  * non-blocking stream owned by the context).  arena_bytes bounds the device
  * workspace (0 = no bound); exceeding it returns FR_ERR_OOM. */
@@ -254,10 +260,11 @@ typedef struct fr_profile_info {
     int64_t pushes;           /* pushes */
     int64_t scc_rounds;       /* SCC colouring rounds */
     int64_t barriers;         /* grid barriers passed by the persistent kernels */
-    double cluster_phase_ms[6]; /* cluster kernel timers summed over pairs: network load into
+    double cluster_phase_ms[7]; /* cluster kernel timers summed over pairs: network load into
                                    shared memory, flow to t, return of excess to s, residual
                                    reachability, residual SCCs (most balanced cuts), member scan
-                                   and split (before the load) */
+                                   and split (before the load), and the exact relabels (part
+                                   of the flow and return times) */
     int64_t cluster_syncs;    /* cluster barriers, summed over pairs */
     int64_t cluster_remote_arcs; /* arcs held in a cluster whose head another CTA holds (DSMEM) */
     int64_t fallback_pairs;   /* pairs left to the grid-wide flow */
@@ -272,6 +279,23 @@ typedef struct fr_profile_info {
  * CUDA events around each one, for fr_profile_last; on = 0: graph replay. */
 fr_status fr_set_profiling(fr_ctx *ctx, int32_t on);
 fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info);
+/* Per-round times of the last profiled fr_refine_batch (CUDA events around each
+ * launch): ms[4r .. 4r+3] = boundary scan, step 1 (BFS, ids, build), cluster
+ * max-flow kernels, step 2 (flow accounting, cut, evaluation, commit) of round r,
+ * in milliseconds, for the first min(rounds, cap) rounds.  ms: host array of
+ * 4 * cap floats, owned by the caller.  Returns the number of rounds profiled
+ * (0 if the last call ran without profiling), -1 for a null ctx (or null ms with
+ * cap > 0). */
+int32_t fr_profile_rounds(const fr_ctx *ctx, float *ms, int32_t cap);
+/* Per pair of the last profiled fr_refine_batch, in the order of its results:
+ * ms[3i] = round, ms[3i+1], ms[3i+2] = when a thread-block cluster took pair i and
+ * when it finished it (max flow, residual sets and SCCs), in milliseconds after the
+ * first pair of the same round was taken (device global timer); -1 for a pair no
+ * cluster solved (empty network, or left to the grid-wide flow).  ms: host array
+ * of 3 * cap floats, owned by the caller.  Returns the number of pairs profiled
+ * (0 if the last call ran without profiling), -1 for a null ctx (or null ms with
+ * cap > 0). */
+int32_t fr_profile_pairs(const fr_ctx *ctx, float *ms, int32_t cap);
 
 /* ---- launch-shape autotuner -------------------------------------------------- */
 

@@ -344,6 +344,20 @@ int choose_grid(fr_ctx *ctx, const fr_options *opt, int tpb, int nsides, long lo
 
 // ---------------------------------------------------------------- context --
 
+extern "C" int32_t fr_struct_size(int32_t which) {
+    switch (which) {
+    case 0: return (int32_t)sizeof(fr_graph);
+    case 1: return (int32_t)sizeof(fr_options);
+    case 2: return (int32_t)sizeof(fr_pair_result);
+    case 3: return (int32_t)sizeof(fr_batch_result);
+    case 4: return (int32_t)sizeof(fr_profile_info);
+    case 5: return (int32_t)sizeof(fr_server_config);
+    case 6: return (int32_t)sizeof(fr_request);
+    case 7: return (int32_t)sizeof(fr_response);
+    default: return -1;
+    }
+}
+
 extern "C" void fr_default_options(fr_options *opt) {
     if (!opt) return;
     memset(opt, 0, sizeof(*opt));

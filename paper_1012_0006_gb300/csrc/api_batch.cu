@@ -418,6 +418,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
         CK(cudaStreamSynchronize(ctx->stream));
         CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
         double sc = 0, stp = 0, clu = 0;
+        ctx->round_ms.assign(4 * (size_t)pl.nr, 0.f);
         for (int r = 0; r < pl.nr; ++r) {
             float a = 0, b1 = 0, c = 0, b2 = 0;
             CK(cudaEventElapsedTime(&a, ctx->pev[8 * r], ctx->pev[8 * r + 1]));
@@ -427,14 +428,33 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
             sc += a;
             stp += b1 + b2;
             clu += c;
+            float *rm = &ctx->round_ms[4 * (size_t)r];
+            rm[0] = a; rm[1] = b1; rm[2] = c; rm[3] = b2;
         }
         ctx->prof.scan_ms = sc;
         ctx->prof.step_ms = stp;
         ctx->prof.cluster_ms = clu;
         ctx->last_launches = ctx->sweep_launches;
+        std::vector<PairAcc> A(pl.np);
+        CK(cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->pair_ms.assign(3 * (size_t)pl.np, 0.f);
+        for (int r = 0; r < pl.nr; ++r) {
+            unsigned long long first = ~0ull;
+            for (int i = pl.off[r]; i < pl.off[r + 1]; ++i)
+                if (A[i].t1 && A[i].t0 < first) first = A[i].t0;
+            for (int i = pl.off[r]; i < pl.off[r + 1]; ++i) {
+                float *pm = &ctx->pair_ms[3 * (size_t)i];
+                pm[0] = (float)r;
+                pm[1] = A[i].t1 ? (float)((A[i].t0 - first) * 1e-6) : -1.f;
+                pm[2] = A[i].t1 ? (float)((A[i].t1 - first) * 1e-6) : -1.f;
+            }
+        }
         return FR_OK;
     }
     ctx->prof.scan_ms = ctx->prof.step_ms = ctx->prof.cluster_ms = 0;
+    ctx->round_ms.clear();
+    ctx->pair_ms.clear();
     if (ctx->use_graphs) {
         for (auto &e : ctx->gcache)
             if (e.key == key) { exec = e.exec; exec_launches = e.launches; break; }
@@ -592,7 +612,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.pushes += C[r].pushes;
             P.scc_rounds += C[r].scc_rounds;
             P.barriers += C[r].barriers;
-            for (int t = 0; t < 6; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
+            for (int t = 0; t < 7; ++t) P.cluster_phase_ms[t] += C[r].timers[T_CL_LOAD + t] * 1e-6;
             P.cluster_syncs += C[r].cl_syncs;
             P.cluster_remote_arcs += C[r].cl_remote;
             P.scan_listed += C[r].scan_listed;
@@ -816,4 +836,18 @@ extern "C" fr_status fr_profile_last(const fr_ctx *ctx, fr_profile_info *info) {
     if (!ctx || !info) return FR_ERR_INVALID_ARG;
     *info = ctx->prof;
     return FR_OK;
+}
+
+extern "C" int32_t fr_profile_pairs(const fr_ctx *ctx, float *ms, int32_t cap) {
+    if (!ctx || (cap > 0 && !ms)) return -1;
+    const int np = (int)(ctx->pair_ms.size() / 3);
+    for (int i = 0; i < 3 * std::min(np, (int)std::max(cap, 0)); ++i) ms[i] = ctx->pair_ms[i];
+    return np;
+}
+
+extern "C" int32_t fr_profile_rounds(const fr_ctx *ctx, float *ms, int32_t cap) {
+    if (!ctx || (cap > 0 && !ms)) return -1;
+    const int nr = (int)(ctx->round_ms.size() / 4);
+    for (int i = 0; i < 4 * std::min(nr, (int)std::max(cap, 0)); ++i) ms[i] = ctx->round_ms[i];
+    return nr;
 }

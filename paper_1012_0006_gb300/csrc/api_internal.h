@@ -99,6 +99,8 @@ struct fr_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> pev;
     fr_profile_info prof = {};
+    std::vector<float> round_ms;   // per round: scan, step 1, cluster kernels, step 2 (profiling)
+    std::vector<float> pair_ms;    // per pair: round, cluster start and end after the round's first start
 };
 
 struct fr_corridor {

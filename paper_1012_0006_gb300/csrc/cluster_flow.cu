@@ -559,6 +559,8 @@ struct ClusterFlow {
     }
 
     static constexpr int kScans = 4;   // local scans between cluster barriers (relabel, reach)
+    static constexpr int kMaxSweeps = 1024;   // sweeps of one wave (a bound; a wave ends when one moves nothing)
+    static constexpr int kMaxLocalRounds = 4096;   // local rounds of one sweep (a bound)
 
     // Exact labels: distances over residual arcs to the level-1 vertices, found by
     // label correction pushed outward.  A vertex whose label dropped since it last
@@ -572,6 +574,7 @@ struct ClusterFlow {
     // the label each vertex last passed on.  phase 0: distance to t; phase 1:
     // distance to s.  Returns the highest label below hmax if want_top.
     __device__ int relabel(int ph, int nv, int hmax, bool want_top = false) {
+        const unsigned long long t_rel = globaltimer();
         for (int lv = threadIdx.x; lv < nv; lv += TPB) {
             const bool src = ph ? (bord[lv] == 1 && fx[lv] > 0) : (bord[lv] == 2);
             lab[lv] = src ? 1 : hmax;
@@ -610,26 +613,23 @@ struct ClusterFlow {
             if (cluster_sum(nproc) == 0) break;
         }
         if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->gr_arcs, rounds);   // barrier windows, summed
-        if (!want_top) return 0;
-        int top = 1;
-        for (int lv = threadIdx.x; lv < nv; lv += TPB)
-            if (lab[lv] < hmax && lab[lv] > top) top = lab[lv];
-        return cluster_max(top);
+        int top = 0;
+        if (want_top) {
+            top = 1;
+            for (int lv = threadIdx.x; lv < nv; lv += TPB)
+                if (lab[lv] < hmax && lab[lv] > top) top = lab[lv];
+            top = cluster_max(top);
+        }
+        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->timers[T_CL_RELABEL], (long long)(globaltimer() - t_rel));
+        return top;
     }
 
-    // Push-relabel in waves: exact labels, then the levels from the top down, each
-    // level pushing only along admissible arcs into the level below (level 1 into
-    // the sink), one cluster barrier per level; repeat until no vertex with excess
-    // can reach the sink.  Within a level step a vertex is the only writer of its
-    // own excess and of the residuals of its arcs and their reverses, so only the
-    // excess of the receiving vertex needs an atomic.  Phase 0 sends excess to t,
-    // phase 1 returns what is left to s.
-    // One wave: the levels from the top down, each level pushing only along
-    // admissible arcs into the level below (level 1 into the target), one cluster
-    // barrier per level.  Within a level step a vertex is the only writer of its own
-    // excess and of the residuals of its arcs and their reverses, so only the excess
-    // of the receiving vertex needs an atomic.
-    __device__ void wave_levels(int ph, int nv, int top) {
+    // One level-synchronous wave (the waves before the pulses): the levels from the
+    // top down, each level pushing only along admissible arcs into the level below
+    // (level 1 into the target), one cluster barrier per level.  Within a level step
+    // a vertex is the only writer of its own excess and of the residuals of its arcs
+    // and their reverses, so only the excess of the receiving vertex needs an atomic.
+    __device__ void wave_levels_sync(int ph, int nv, int top) {
         for (int L = top; L >= 1; --L) {
             for (int lv = threadIdx.x; lv < nv; lv += TPB) {
                 if (lab[lv] != L) continue;
@@ -668,6 +668,72 @@ struct ClusterFlow {
         }
     }
 
+    // One wave with fixed labels (the waves schedule).  Every vertex holding excess
+    // at a level L in [1, top] pushes along its admissible arcs into level L - 1
+    // (level 1 into the target).  Each CTA repeats local rounds -- one pass over its vertices, then a
+    // CTA barrier -- while a push lands on one of its own vertices; excess sent to
+    // another CTA lands there as an atomic addition whenever it lands.  One cluster
+    // barrier then ends a sweep, and sweeps repeat until one moves nothing: no
+    // excess has an admissible arc with residual capacity any more, and only new
+    // labels can move it.  With labels fixed, no two vertices push along an arc and
+    // its reverse at once (one of the two pushes would go uphill), so the owner of
+    // an arc is the only writer of its residual besides the atomic additions of
+    // pushes along the reverse, and every change of an excess is atomic (a vertex
+    // pushes at most what it read; others only add).  Every push lowers the sum of
+    // excess times label, so the rounds and the sweeps end.
+    __device__ void wave_levels(int ph, int nv, int top) {
+        const unsigned own_lo = map_rank(cta_addr(lab), rank), own_hi = own_lo + 4u * (unsigned)nv;
+        for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+            int moved = 0;
+            for (int round = 0; round < kMaxLocalRounds; ++round) {
+                int local = 0;
+                for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+                    const int L = lab[lv];
+                    if (L < 1 || L > top) continue;
+                    int e = *(volatile int *)&ex[lv];
+                    if (e <= 0) continue;
+                    int sent = 0;
+                    if (L == 1) {
+                        if (!ph) { sent = e; fx[lv] += e; }
+                        else if (bord[lv] == 1) { sent = e < fx[lv] ? e : fx[lv]; fx[lv] -= sent; }
+                    } else {
+                        const int a1 = cofs[lv + 1];
+                        for (int a = cofs[lv]; a < a1 && e > 0; a += U) {
+                            int r[U], l[U];
+                            unsigned hr[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                r[u] = a + u < a1 ? rs(a + u) : 0;
+                                hr[u] = a + u < a1 ? hadr[a + u] : 0u;
+                                l[u] = a + u < a1 ? hlab[a + u] : -1;
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) l[u] = r[u] > 0 ? l[u] : -1;
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (e > 0 && l[u] == L - 1) {
+                                    const int d = e < r[u] ? e : r[u];
+                                    set_rs(a + u, r[u] - d);
+                                    dsm_add(radr[a + u], d);
+                                    dsm_add(hr[u] + o_ex, d);
+                                    e -= d;
+                                    sent += d;
+                                    local |= hr[u] >= own_lo && hr[u] < own_hi;
+                                }
+                            }
+                        }
+                    }
+                    if (sent) {
+                        atomicSub(&ex[lv], sent);
+                        ++moved;
+                    }
+                }
+                if (!__syncthreads_or(local)) break;
+            }
+            if (cluster_sum(moved) == 0) break;
+        }
+    }
+
     // Push-relabel in waves: exact labels, then one wave; repeat until no vertex
     // with excess can reach the target.  Phase 0 sends excess to t, phase 1 returns
     // what is left to s.
@@ -698,7 +764,7 @@ struct ClusterFlow {
             // (labels stay valid: pushes go one level down); the pulses finish
             const int top = relabel(ph, nv, hmax, w.pre_waves > 0);
             for (int k = 0; k < w.pre_waves; ++k) {
-                wave_levels(ph, nv, top);
+                wave_levels_sync(ph, nv, top);
                 if (k + 1 < w.pre_waves) relabel(ph, nv, hmax);
             }
         }
@@ -844,8 +910,10 @@ __global__ void __launch_bounds__(TPB, 1) cluster_flow_kernel(Work w, size_t sme
         if (j >= w.npairs) break;
         const int p = __ldcg(&w.pacc[j].ord);
         if (w.cl_tier == 1 && __ldcg(&w.pacc[p].status) != 1) continue;
+        if (K.rank == 0 && threadIdx.x == 0) w.pacc[p].t0 = globaltimer();
         const bool done = K.solve(p, csmem, smem_bytes);
         if (K.rank == 0 && threadIdx.x == 0) {
+            w.pacc[p].t1 = globaltimer();
             if (w.cl_tier == 0) {
                 if (!done) {
                     atomicAdd(&w.ctl->fallback, 1);

@@ -42,7 +42,7 @@ enum PhaseBits : uint32_t {
 enum TimerIdx { T_BFS = 0, T_SELECT, T_LID, T_BUILD, T_FLOW1, T_GR, T_FLOW2, T_REACH, T_SCC, T_SWEEP, T_EVAL,
                 T_COMMIT,
                 // cluster kernel, summed over pairs: member scan and load, flow to t, return to s, reach
-                T_CL_LOAD, T_CL_FLOW, T_CL_RETURN, T_CL_REACH, T_CL_SCC, T_CL_MEMBERS, T_COUNT };
+                T_CL_LOAD, T_CL_FLOW, T_CL_RETURN, T_CL_REACH, T_CL_SCC, T_CL_MEMBERS, T_CL_RELABEL, T_COUNT };
 
 enum SideCode { SS_EXPAND = 1, SS_SELECT = 2, SS_DONE = 3 };
 
@@ -104,6 +104,7 @@ struct PairAcc {
     int status;          // cluster max flow: 0 solved or pending, 1 left by the first cluster
                          // launch, 2 solved by the second, 3 left to the grid-wide flow
     int ord;             // the pair whose network is the ord-th largest of the round (slot ord)
+    unsigned long long t0, t1;   // global timer when a cluster took the pair and finished it
 };
 
 struct Ctl {

@@ -70,7 +70,7 @@ class ProfileInfo(ctypes.Structure):
                 ("corridor_n", ctypes.c_int64), ("corridor_arcs", ctypes.c_int64), ("pulses", ctypes.c_int64),
                 ("relabels", ctypes.c_int64), ("gr_arcs", ctypes.c_int64), ("pr_arcs", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("scc_rounds", ctypes.c_int64), ("barriers", ctypes.c_int64),
-                ("cluster_phase_ms", ctypes.c_double * 6), ("cluster_syncs", ctypes.c_int64),
+                ("cluster_phase_ms", ctypes.c_double * 7), ("cluster_syncs", ctypes.c_int64),
                 ("cluster_remote_arcs", ctypes.c_int64),
                 ("fallback_pairs", ctypes.c_int64),
                 ("scan_listed", ctypes.c_int64), ("scan_rows", ctypes.c_int64), ("scan_arcs", ctypes.c_int64),
@@ -83,7 +83,7 @@ class ProfileInfo(ctypes.Structure):
         d = {f: getattr(self, f) for f, _ in self._fields_
              if f not in ("phase_ms", "cluster_phase_ms", "cluster_sizes", "cluster_max_active")}
         d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
-        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach", "scc", "members"),
+        d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach", "scc", "members", "relabel"),
                                          list(self.cluster_phase_ms)))
         d["cluster_sizes"] = list(self.cluster_sizes)
         d["cluster_max_active"] = list(self.cluster_max_active)
@@ -150,7 +150,10 @@ SYMBOLS = {
                                               ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                               ctypes.POINTER(Options), ctypes.POINTER(PairResult), vp]),
     "fr_set_profiling": (ctypes.c_int, [vp, ctypes.c_int32]),
+    "fr_struct_size": (ctypes.c_int32, [ctypes.c_int32]),
     "fr_profile_last": (ctypes.c_int, [vp, ctypes.POINTER(ProfileInfo)]),
+    "fr_profile_rounds": (ctypes.c_int32, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    "fr_profile_pairs": (ctypes.c_int32, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "fr_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]),
     "fr_server_add_graph": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, i32p]),
     "fr_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request)]),
@@ -402,6 +405,21 @@ class Context:
         info = ProfileInfo()
         self._check(lib().fr_profile_last(self.h, ctypes.byref(info)))
         return info.as_dict()
+
+    def profile_rounds(self):
+        """Per round of the last profiled batch: [scan, step 1, cluster, step 2] in ms."""
+        nr = lib().fr_profile_rounds(self.h, None, 0)
+        buf = (ctypes.c_float * max(4 * nr, 1))()
+        lib().fr_profile_rounds(self.h, buf, nr)
+        return [[round(buf[4 * r + i], 4) for i in range(4)] for r in range(nr)]
+
+    def profile_pairs(self):
+        """Per pair of the last profiled batch: (round, cluster start ms, end ms) after
+        the round's first start; -1 where no cluster solved the pair."""
+        np_ = lib().fr_profile_pairs(self.h, None, 0)
+        buf = (ctypes.c_float * max(3 * np_, 1))()
+        lib().fr_profile_pairs(self.h, buf, np_)
+        return [(int(buf[3 * i]), round(buf[3 * i + 1], 4), round(buf[3 * i + 2], 4)) for i in range(np_)]
 
     def autotune(self, g: DeviceGraph, part, k, eps, alpha, opts=None, trials=2):
         best = Options()

@@ -308,6 +308,18 @@ def test_cluster_tiers_and_grid_fallback(F, ctx, k, alpha, grid_pairs):
     assert (prof["fallback_pairs"] > 0) == grid_pairs
     if not grid_pairs:
         assert prof["cluster_syncs"] > 0
+    rounds = ctx.profile_rounds()
+    assert len(rounds) == prof["nrounds"] and all(min(r) >= 0 for r in rounds)
+    assert abs(sum(r[0] for r in rounds) - prof["scan_ms"]) < 1e-3 * max(1.0, prof["scan_ms"])
+    assert abs(sum(r[2] for r in rounds) - prof["cluster_ms"]) < 1e-3 * max(1.0, prof["cluster_ms"])
+    pairs = ctx.profile_pairs()
+    assert len(pairs) > 0 and [r for r, _, _ in pairs] == sorted(r for r, _, _ in pairs)
+    assert all(e >= s >= 0 for _, s, e in pairs if e >= 0)
+    solved = [(r, s, e) for r, s, e in pairs if e >= 0]
+    if not grid_pairs:
+        assert solved and all(e <= rounds[r][2] + 1e-3 for r, _, e in solved)
+    _check_batch(F, ctx, w, dict(cluster_ctas=4))   # unprofiled: no per-round or per-pair times
+    assert ctx.profile_rounds() == [] and ctx.profile_pairs() == []
 
 
 def test_repeated_runs_are_identical(F, ctx):
