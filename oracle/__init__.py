@@ -21,7 +21,8 @@ i64p = ctypes.POINTER(ctypes.c_int64)
 
 class Options(ctypes.Structure):
     _fields_ = [("mb", ctypes.c_int32), ("mb_reps", ctypes.c_int32), ("adaptive", ctypes.c_int32),
-                ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("fm_permille", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -29,7 +30,16 @@ class PairResult(ctypes.Structure):
                 ("wA_before", ctypes.c_int64), ("wB_before", ctypes.c_int64), ("wA_after", ctypes.c_int64),
                 ("wB_after", ctypes.c_int64), ("corridor_n", ctypes.c_int32), ("corridor_arcs", ctypes.c_int32),
                 ("accepted", ctypes.c_int32), ("iters", ctypes.c_int32), ("alpha_final", ctypes.c_double),
-                ("status", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("round", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("round", ctypes.c_int32),
+                ("cut_fm", ctypes.c_int64), ("fm_moves", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+
+
+class FMResult(ctypes.Structure):
+    _fields_ = [("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64), ("wA_after", ctypes.c_int64),
+                ("wB_after", ctypes.c_int64), ("tried", ctypes.c_int32), ("kept", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -95,6 +105,12 @@ def lib():
         L.fro_refine_active.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
                                         ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
                                         ctypes.c_int32, ctypes.POINTER(PairResult), i32p, i32p]
+        L.fro_fm_pair.restype = ctypes.c_int32
+        L.fro_fm_pair.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(FMResult), i32p,
+                                  ctypes.c_int32]
+        L.fro_fm_seed.restype = ctypes.c_uint64
+        L.fro_fm_seed.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32]
         L.fro_splitmix64.restype = ctypes.c_uint64
         L.fro_splitmix64.argtypes = [ctypes.c_uint64]
         _LIB = L
@@ -109,8 +125,8 @@ def _c32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
 
 
-def options(mb=0, mb_reps=1, adaptive=0, max_iters=1, alpha_max=1.0, seed=0):
-    return Options(mb, mb_reps, adaptive, max_iters, alpha_max, seed)
+def options(mb=0, mb_reps=1, adaptive=0, max_iters=1, alpha_max=1.0, seed=0, fm_permille=0):
+    return Options(mb, mb_reps, adaptive, max_iters, alpha_max, seed, fm_permille, 0)
 
 
 def validate(w):
@@ -298,3 +314,22 @@ def refine_batch_mt(w, nthreads, max_rounds=-1, part=None, eps=None, alpha=None,
                                    _p(part), k, eps, alpha, ctypes.byref(opts), nthreads, max_rounds, cap, res,
                                    ctypes.byref(npairs), ctypes.byref(nrounds), ctypes.byref(done))
     return st, part, [res[i].as_dict() for i in range(min(done.value, cap))], nrounds.value, done.value
+
+
+def fm_seed(seed, a, b):
+    return lib().fro_fm_seed(seed & 0xFFFFFFFFFFFFFFFF, a, b)
+
+
+def fm_pair(w, a, b, permille, seed=0, part=None, Lmax=None):
+    """Two-way FM with TopGain on pair (a, b) (fro_fm_pair); returns (status, part,
+    result dict, vertices moved in order before the rollback)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    if Lmax is None:
+        W = int(np.asarray(w["vwgt"], np.int64).sum())
+        Lmax = lmax(W, int(np.asarray(w["vwgt"]).max()), w["k"], w["eps"])
+    res = FMResult()
+    moves = np.zeros(w["n"], np.int32)
+    st = lib().fro_fm_pair(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
+                           a, b, Lmax, permille, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(res), _p(moves), w["n"])
+    d = res.as_dict()
+    return st, part, d, moves[:d["tried"]]

@@ -39,6 +39,17 @@
  *   adaptive   feasible & smaller: apply, alpha = min(2 alpha, alpha');
  *              feasible & equal: apply if better balanced, stop;
  *              infeasible: stop if alpha == 1 else alpha = max(alpha/2, 1)
+ *   FM         gains and boundary within G[A u B]; a block's queue holds its
+ *              unmoved vertices with an edge to the other block, keyed by (gain,
+ *              stamp), larger first: initial stamps are random 63-bit values in
+ *              the role of the random initial order, each later insertion or
+ *              gain change takes a larger stamp (one per adjacency position of the
+ *              moved vertex, in CSR order); TopGain: larger top gain, a seeded
+ *              random bit on equal top gains, the heavier block while either
+ *              block exceeds L_max; best state = smallest (overload, cut, max
+ *              block weight); stop after more than permille/1000 of the pair's
+ *              vertices moved since the last best, or when both queues are empty
+ *   pairwise   with FM on: FM first, then the flow iterations on its result
  *   batch      greedy edge colouring of the quotient graph in lexicographic
  *              (a, b) order (smallest free colour); each colour is a round of
  *              block-disjoint pairs; rounds in colour order, pairs of a round
@@ -61,7 +72,11 @@ typedef struct fro_options {
     int32_t adaptive;    /* adaptive flow iterations */
     int32_t max_iters;   /* iteration cap of the adaptive loop (>= 1) */
     double alpha_max;    /* alpha' */
-    uint64_t seed;       /* sweep keys for r >= 1 */
+    uint64_t seed;       /* sweep keys for r >= 1, FM keys */
+    int32_t fm_permille; /* > 0: two-way FM before the flows, stopped after more than
+                            fm_permille / 1000 of the pair's vertices moved without an
+                            improvement; 0: no FM */
+    int32_t pad0;
 } fro_options;
 
 typedef struct fro_pair_result {
@@ -69,7 +84,17 @@ typedef struct fro_pair_result {
     int32_t corridor_n, corridor_arcs, accepted, iters;
     double alpha_final;
     int32_t status, a, b, round;
+    int64_t cut_fm;      /* pair cut after the FM step (= cut_before without FM) */
+    int32_t fm_moves;    /* FM moves kept */
+    int32_t pad0;
 } fro_pair_result;
+
+/* Result of one two-way FM search. */
+typedef struct fro_fm_result {
+    int64_t cut_before, cut_after, wA_after, wB_after;
+    int32_t tried;       /* moves made before the stopping rule */
+    int32_t kept;        /* moves kept after the rollback (a prefix) */
+} fro_fm_result;
 
 /* Input checks of Section 2.1 (omega > 0, c >= 0, symmetric simple CSR, 0 <= part < k). */
 int32_t fro_validate(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
@@ -120,6 +145,17 @@ int64_t fro_cut(fro_problem *p, int32_t mb, int32_t reps, uint64_t seed, int8_t 
 int32_t fro_refine_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                         const int32_t *vwgt, int32_t *part, int32_t k, int32_t a, int32_t b, double eps,
                         double alpha, const fro_options *opt, fro_pair_result *res);
+
+/* Two-way FM with TopGain on pair (a, b) (Section 2.2; stopping rule of Section 5):
+ * moves vertices of a and b between the two blocks of part, then rolls back to the
+ * best prefix.  moves (optional, moves_cap entries) receives every vertex moved, in
+ * order, before the rollback.  FM keys: seed' = splitmix64(seed ^ a << 32 ^ b);
+ * initial stamp of v = splitmix64(seed' ^ v) >> 1; the block tie at move i takes
+ * b iff splitmix64(~seed' ^ i) is odd. */
+int32_t fro_fm_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                    const int32_t *vwgt, int32_t *part, int32_t a, int32_t b, int64_t Lmax, int32_t permille,
+                    uint64_t seed, fro_fm_result *out, int32_t *moves, int32_t moves_cap);
+uint64_t fro_fm_seed(uint64_t seed, int32_t a, int32_t b);
 
 /* Quotient graph rounds: pair list (a < b, lexicographic) with the colour of each pair. */
 int32_t fro_rounds(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *part, int32_t k,

@@ -705,12 +705,182 @@ int64_t fro_cut(fro_problem *p, int32_t mb, int32_t reps, uint64_t seed, int8_t 
     return capv;
 }
 
+/* ------------------------------------------ two-way FM, TopGain (2.2) ---- */
+
+/* Section 2.2 (two-way local search as in KaPPa): one priority queue of movable
+ * vertices per block, keyed by the gain (the decrease of the pair cut when the
+ * vertex moves to the other block); each vertex moves at most once; the queues
+ * start with the boundary vertices in random order; TopGain takes the block whose
+ * best vertex has the larger gain (random tie), but the heavier block while a block
+ * is overloaded; after the stopping rule the moves are rolled back to the best cut
+ * found within the balance constraint.  Section 5 (setup) gives the stopping rule:
+ * stop once more than a fraction of the pair's vertices moved without an
+ * improvement.  Readings (also in the header): gains and the boundary are taken
+ * within G[A u B]; a queue holds the unmoved vertices of its block with an edge to
+ * the other block; keys order by gain, then by stamp (larger first: the initial
+ * stamps are random 63-bit values, every later insertion or gain change takes a
+ * larger stamp than any before, one per adjacency position of the moved vertex);
+ * "best" is the smallest (overload, cut, max block weight). */
+
+typedef struct { int64_t gain; uint64_t stamp; int32_t v; } fm_key;
+
+static int fm_better(const fm_key *x, const fm_key *y) {
+    if (x->gain != y->gain) return x->gain > y->gain;
+    if (x->stamp != y->stamp) return x->stamp > y->stamp;
+    return x->v < y->v;
+}
+
+typedef struct { fm_key *h; int32_t n; int32_t *pos; } fm_heap;   /* max-heap, pos[v] = index or -1 */
+
+static void fm_swap(fm_heap *q, int32_t i, int32_t j) {
+    fm_key t = q->h[i]; q->h[i] = q->h[j]; q->h[j] = t;
+    q->pos[q->h[i].v] = i; q->pos[q->h[j].v] = j;
+}
+static void fm_up(fm_heap *q, int32_t i) {
+    while (i > 0 && fm_better(&q->h[i], &q->h[(i - 1) / 2])) { fm_swap(q, i, (i - 1) / 2); i = (i - 1) / 2; }
+}
+static void fm_down(fm_heap *q, int32_t i) {
+    for (;;) {
+        int32_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < q->n && fm_better(&q->h[l], &q->h[m])) m = l;
+        if (r < q->n && fm_better(&q->h[r], &q->h[m])) m = r;
+        if (m == i) return;
+        fm_swap(q, i, m);
+        i = m;
+    }
+}
+static void fm_set(fm_heap *q, fm_key k) {   /* insert, or replace the key of k.v */
+    int32_t i = q->pos[k.v];
+    if (i < 0) { i = q->n++; q->h[i] = k; q->pos[k.v] = i; }
+    else q->h[i] = k;
+    fm_up(q, i);
+    fm_down(q, q->pos[k.v]);
+}
+static void fm_remove(fm_heap *q, int32_t v) {
+    int32_t i = q->pos[v];
+    if (i < 0) return;
+    int32_t last = --q->n;
+    if (i != last) {
+        fm_swap(q, i, last);
+        q->pos[v] = -1;
+        fm_up(q, i);
+        fm_down(q, i);
+    } else {
+        q->pos[v] = -1;
+    }
+}
+
+uint64_t fro_fm_seed(uint64_t seed, int32_t a, int32_t b) {
+    return fro_splitmix64(seed ^ ((uint64_t)(uint32_t)a << 32) ^ (uint64_t)(uint32_t)b);
+}
+
+int32_t fro_fm_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                    const int32_t *vwgt, int32_t *part, int32_t a, int32_t b, int64_t Lmax, int32_t permille,
+                    uint64_t seed, fro_fm_result *out, int32_t *moves, int32_t moves_cap) {
+    memset(out, 0, sizeof(*out));
+    if (permille <= 0) return FRO_OK;
+    const uint64_t fs = fro_fm_seed(seed, a, b);
+    int64_t *in = XALLOC(int64_t, n), *ext = XALLOC(int64_t, n);
+    int8_t *moved = XALLOC(int8_t, n);
+    int32_t *log = XALLOC(int32_t, n);
+    fm_heap q[2];
+    for (int s = 0; s < 2; ++s) {
+        q[s].h = XALLOC(fm_key, n);
+        q[s].n = 0;
+        q[s].pos = XALLOC(int32_t, n);
+        for (int32_t v = 0; v < n; ++v) q[s].pos[v] = -1;
+    }
+    int64_t N = 0, wA = 0, wB = 0, cut = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        if (part[v] != a && part[v] != b) continue;
+        ++N;
+        if (part[v] == a) wA += vwgt[v]; else wB += vwgt[v];
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            const int32_t u = adjncy[j];
+            if (part[u] == part[v]) in[v] += adjwgt[j];
+            else if (part[u] == a || part[u] == b) { ext[v] += adjwgt[j]; if (v < u) cut += adjwgt[j]; }
+        }
+    }
+    /* initial queues: the boundary vertices, stamps random (63 bits) */
+    for (int32_t v = 0; v < n; ++v) {
+        if ((part[v] != a && part[v] != b) || ext[v] == 0) continue;
+        fm_key k = { ext[v] - in[v], fro_splitmix64(fs ^ (uint64_t)(uint32_t)v) >> 1, v };
+        fm_set(&q[part[v] == a ? 0 : 1], k);
+    }
+    const int64_t limit = (int64_t)permille * N / 1000;
+    uint64_t t = 0;   /* stamps handed out after the start: (1 << 63) + t */
+    int64_t best_cut = cut, best_wA = wA, best_wB = wB;
+    int32_t nm = 0, best_len = 0;
+    int64_t idle = 0;
+    out->cut_before = cut;
+    for (;;) {
+        if (q[0].n == 0 && q[1].n == 0) break;
+        int s;
+        if (wA > Lmax || wB > Lmax) {
+            s = wA >= wB ? 0 : 1;                     /* the heavier block while one is overloaded */
+            if (q[s].n == 0) s = 1 - s;
+        } else if (q[0].n == 0) {
+            s = 1;
+        } else if (q[1].n == 0) {
+            s = 0;
+        } else if (q[0].h[0].gain != q[1].h[0].gain) {
+            s = q[0].h[0].gain > q[1].h[0].gain ? 0 : 1;
+        } else {
+            s = (int)(fro_splitmix64(~fs ^ (uint64_t)nm) & 1);   /* random tie of the top gains */
+        }
+        const int32_t v = q[s].h[0].v;
+        const int64_t g = q[s].h[0].gain;
+        fm_remove(&q[s], v);
+        const int32_t from = s ? b : a, to = s ? a : b;
+        part[v] = to;
+        moved[v] = 1;
+        log[nm++] = v;
+        cut -= g;
+        if (s == 0) { wA -= vwgt[v]; wB += vwgt[v]; } else { wB -= vwgt[v]; wA += vwgt[v]; }
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            const int32_t u = adjncy[j];
+            if (moved[u] || (part[u] != a && part[u] != b)) continue;
+            if (part[u] == from) { in[u] -= adjwgt[j]; ext[u] += adjwgt[j]; }
+            else { in[u] += adjwgt[j]; ext[u] -= adjwgt[j]; }
+            fm_heap *qu = &q[part[u] == a ? 0 : 1];
+            if (ext[u] > 0) {
+                fm_key k = { ext[u] - in[u], (1ULL << 63) + t + (uint64_t)(j - xadj[v]), u };
+                fm_set(qu, k);
+            } else {
+                fm_remove(qu, u);
+            }
+        }
+        t += (uint64_t)(xadj[v + 1] - xadj[v]);
+        /* best: smallest (overload, cut, max block weight) */
+        const int64_t mx = wA > wB ? wA : wB, bmx = best_wA > best_wB ? best_wA : best_wB;
+        const int64_t ov = mx > Lmax ? mx - Lmax : 0, bov = bmx > Lmax ? bmx - Lmax : 0;
+        if (ov < bov || (ov == bov && (cut < best_cut || (cut == best_cut && mx < bmx)))) {
+            best_cut = cut; best_wA = wA; best_wB = wB; best_len = nm; idle = 0;
+        } else if (++idle > limit) {
+            break;
+        }
+    }
+    for (int32_t i = 0; i < nm && i < moves_cap; ++i) moves[i] = log[i];
+    for (int32_t i = nm - 1; i >= best_len; --i) part[log[i]] = part[log[i]] == a ? b : a;   /* roll back */
+    out->tried = nm;
+    out->kept = best_len;
+    out->cut_after = best_cut;
+    out->wA_after = best_wA;
+    out->wB_after = best_wB;
+    for (int s = 0; s < 2; ++s) { free(q[s].h); free(q[s].pos); }
+    free(in); free(ext); free(moved); free(log);
+    return FRO_OK;
+}
+
 /* ------------------------------------- refinement of one pair (4.1) ------ */
+
+static int bad_fm(const fro_options *opt) { return opt && (opt->fm_permille < 0 || opt->fm_permille > 1000); }
 
 static int32_t check_pair_args(int32_t k, int32_t a, int32_t b, double eps, double alpha, const fro_options *opt) {
     if (k < 2 || a < 0 || b < 0 || a >= k || b >= k || a == b) return FRO_ERR_INVALID_ARG;
     if (!(eps > 0.0) || !(alpha >= 1.0)) return FRO_ERR_INVALID_ARG;
-    if (opt && (opt->mb_reps < 0 || opt->max_iters < 0 || (opt->adaptive && !(opt->alpha_max >= 1.0))))
+    if (opt && (opt->mb_reps < 0 || opt->max_iters < 0 || (opt->adaptive && !(opt->alpha_max >= 1.0)) ||
+                opt->fm_permille < 0 || opt->fm_permille > 1000))
         return FRO_ERR_INVALID_ARG;
     return FRO_OK;
 }
@@ -730,6 +900,14 @@ static int32_t refine_pair_core(int32_t n, const int32_t *xadj, const int32_t *a
     int64_t wA = 0, wB = 0;
     for (int32_t v = 0; v < n; ++v) { if (part[v] == a) wA += vwgt[v]; else if (part[v] == b) wB += vwgt[v]; }
     res->cut_before = cut; res->wA_before = wA; res->wB_before = wB;
+    if (opt && opt->fm_permille > 0) {
+        /* pairwise improvement: FM first, then the flows on its result (Section 5 setup) */
+        fro_fm_result fr;
+        fro_fm_pair(n, xadj, adjncy, adjwgt, vwgt, part, a, b, Lmax, opt->fm_permille, seed, &fr, NULL, 0);
+        cut = fr.cut_after; wA = fr.wA_after; wB = fr.wB_after;
+        res->fm_moves = fr.kept;
+    }
+    res->cut_fm = cut;
     int32_t *trial = XALLOC(int32_t, n);
     double al = alpha;
     int32_t iters = 0;
@@ -819,7 +997,7 @@ int32_t fro_refine_batch(int32_t n, const int32_t *xadj, const int32_t *adjncy, 
                          const fro_options *opt, int32_t cap, fro_pair_result *res, int32_t *npairs,
                          int32_t *nrounds) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0))) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
@@ -847,7 +1025,7 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
                                 const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                                 const fro_options *opt, int32_t max_pairs, int32_t *done) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0))) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
@@ -885,7 +1063,7 @@ int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy,
                           const fro_options *opt, int32_t max_outer, int32_t cap, fro_pair_result *res,
                           int32_t *npairs, int32_t *nouter) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || max_outer < 1)) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || max_outer < 1 || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
@@ -993,7 +1171,7 @@ int32_t fro_refine_batch_mt(int32_t n, const int32_t *xadj, const int32_t *adjnc
                             const fro_options *opt, int32_t nthreads, int32_t max_rounds, int32_t cap,
                             fro_pair_result *res, int32_t *npairs, int32_t *nrounds, int32_t *done) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || nthreads < 1)) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || nthreads < 1 || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
