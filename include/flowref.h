@@ -83,17 +83,23 @@ typedef struct fr_options {
                               clusters, then to the grid-wide flow; results do not depend on it */
     int32_t pre_waves;     /* cluster pulses: level-ordered waves before the first pulse (0-2);
                               -1 = none, 0 = tuned default */
-    int32_t pad0;
+    int32_t fm_permille;   /* > 0: two-way FM with TopGain (Section 2.2) on each pair before its
+                              flow, stopped once more than fm_permille / 1000 of the pair's
+                              vertices moved without an improvement (50 = the 5 % of the
+                              paper's setup); 0 = no FM.  fr_refine_pair, fr_refine_batch and
+                              fr_refine_active; needs a simple graph and every gain within
+                              +-2047 (max edge weight x max degree), else FR_ERR_TOO_LARGE */
 } fr_options;
 
-/* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b). */
+/* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b);
+ * *_before is the state before the pair's FM step (if any) and flow, *_after the final one. */
 typedef struct fr_pair_result {
     int64_t flow;           /* value of the maximum s-t flow of the last iteration */
     int64_t cut_before, cut_after;
     int64_t wA_before, wB_before, wA_after, wB_after;
     int32_t corridor_n;     /* corridor vertices of the last iteration */
     int32_t corridor_arcs;  /* arcs between corridor vertices (both directions) */
-    int32_t accepted;       /* 1 if part was changed */
+    int32_t accepted;       /* 1 if a flow's cut was applied */
     int32_t iters;          /* flow iterations run */
     double alpha_final;     /* alpha after the adaptive loop */
     int32_t status;         /* fr_status of this pair */
@@ -103,7 +109,8 @@ typedef struct fr_pair_result {
     int32_t bfs_levels;     /* corridor BFS levels (step-wide) */
     int32_t scc_rounds;     /* SCC colouring rounds (step-wide) */
     int32_t ncomp;          /* SCCs outside the S and T sets (MB only) */
-    int32_t pad0;
+    int32_t fm_moves;       /* moves the FM step kept (fm_permille > 0) */
+    int64_t cut_fm;         /* omega(E_ab) after the FM step (= cut_before without FM) */
 } fr_pair_result;
 
 typedef struct fr_batch_result {
@@ -334,6 +341,7 @@ fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32
  * Limits: n <= FR_NOALLOC_MAX_N, nnz <= FR_NOALLOC_MAX_NNZ, k <=
  * FR_NOALLOC_MAX_K, mb_reps <= FR_NOALLOC_MAX_REPS; larger problems return
  * FR_ERR_TOO_LARGE without touching part (use fr_refine_pair for them).
+ * opt->fm_permille must be 0 (FR_ERR_INVALID_ARG otherwise).
  * Every call uses the same array, which keeps the previous call's contents;
  * each call clears what it needs before use.  Two calls whose work overlaps on
  * the GPU (concurrent streams or host threads, on the same device) race on the
@@ -349,7 +357,7 @@ typedef struct fr_server_config {
     int32_t device;
     int32_t max_inflight;    /* requests resident on the device at once */
     size_t arena_bytes;      /* device bytes for request workspaces (admission bound) */
-    fr_options opt;          /* options applied to every request */
+    fr_options opt;          /* options applied to every request (fm_permille must be 0) */
 } fr_server_config;
 
 typedef struct fr_request {

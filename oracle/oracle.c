@@ -1107,7 +1107,7 @@ int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy,
                 refine_pair_core(n, xadj, adjncy, adjwgt, vwgt, part, k, pa[i], pb[i], eps, alpha, opt, W, Lmax,
                                  &tmp);
                 tmp.round = round_base + r;
-                if (tmp.accepted) active[pa[i]] = active[pb[i]] = 1;
+                if (tmp.accepted || tmp.fm_moves > 0) active[pa[i]] = active[pb[i]] = 1;   /* partition changed */
                 if (out < cap) res[out] = tmp;
                 ++out;
             }

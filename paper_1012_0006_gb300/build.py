@@ -29,6 +29,7 @@ CUDA_SOURCES = [
     "api.cu",
     "api_batch.cu",
     "api_active.cu",
+    "fm_kernel.cu",
     "round_kernel.cu",
     "prep_kernel.cu",
     "serve.cu",

@@ -247,6 +247,70 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     return ensure_reps(ctx, rr);
 }
 
+fr_status ensure_fm(fr_ctx *ctx, int n, int nnz, int k, int P) {
+    if (ctx->fm_mem && n <= ctx->fm_n && nnz <= ctx->fm_nnz && k <= ctx->fm_k && P <= ctx->fm_p) return FR_OK;
+    const long long nn = std::max(n, ctx->fm_n), mm = std::max(nnz, ctx->fm_nnz);
+    const int kk = std::max(k, ctx->fm_k), pp = std::max(P, ctx->fm_p);
+    const long long ecap = nn + mm, scap = 2 * nn;
+    size_t b = 0;
+    auto add = [&](size_t elem, long long cnt) { b += ((elem * (size_t)cnt + 255) / 256) * 256; };
+    add(4, nn); add(4, nn); add(4, nn); add(1, nn);         // in ext ver flags
+    add(4, nn); add(4, nn);                                 // vlist mlog
+    add(4, kk); add(4, kk);                                 // blockn blockarcs
+    add(8, pp); add(8, pp + 1); add(4, pp); add(4, pp);     // voff eoff np bcnt
+    add(4, ecap); add(4, ecap); add(4, ecap);               // ent_v ent_ver ent_below
+    add(8, scap); add(4, scap); add(4, scap);               // skey sbkt sv
+    add(sizeof(FmRes), pp);                                 // res
+    if (ctx->arena_limit && b + ctx->base_bytes + ctx->pair_bytes > ctx->arena_limit) {
+        ctx_error(ctx, "FM workspace of %zu bytes exceeds the arena bound", b);
+        return FR_ERR_OOM;
+    }
+    free_fm(ctx);
+    if (cudaMalloc(&ctx->fm_mem, b) != cudaSuccess) {
+        ctx->fm_mem = nullptr;
+        cudaGetLastError();
+        ctx_error(ctx, "cudaMalloc(%zu) for the FM workspace failed", b);
+        return FR_ERR_OOM;
+    }
+    ctx->fm_bytes = b;
+    ctx->fm_n = (int)nn; ctx->fm_nnz = (int)mm; ctx->fm_k = kk; ctx->fm_p = pp;
+    char *p = reinterpret_cast<char *>(ctx->fm_mem);
+    FmDev &f = ctx->fm;
+    f.in = carve<int>(p, nn); f.ext = carve<int>(p, nn); f.ver = carve<int>(p, nn);
+    f.flags = carve<unsigned char>(p, nn);
+    f.vlist = carve<int>(p, nn); f.mlog = carve<int>(p, nn);
+    f.blockn = carve<int>(p, kk); f.blockarcs = carve<int>(p, kk);
+    f.voff = carve<long long>(p, pp); f.eoff = carve<long long>(p, pp + 1);
+    f.np = carve<int>(p, pp); f.bcnt = carve<int>(p, pp);
+    f.ent_v = carve<int>(p, ecap); f.ent_ver = carve<int>(p, ecap); f.ent_below = carve<int>(p, ecap);
+    f.skey = carve<unsigned long long>(p, scap); f.sbkt = carve<int>(p, scap); f.sv = carve<int>(p, scap);
+    f.res = carve<FmRes>(p, pp);
+    f.ecap = ecap; f.scap = scap;
+    // per-vertex state is zero between searches; block counts start at zero
+    CK(cudaMemsetAsync(f.ver, 0, sizeof(int) * (size_t)nn, ctx->stream));
+    CK(cudaMemsetAsync(f.flags, 0, (size_t)nn, ctx->stream));
+    CK(cudaMemsetAsync(f.blockn, 0, sizeof(int) * (size_t)kk, ctx->stream));
+    CK(cudaMemsetAsync(f.blockarcs, 0, sizeof(int) * (size_t)kk, ctx->stream));
+    ctx->graph_valid = false;
+    return FR_OK;
+}
+
+void free_fm(fr_ctx *ctx) {
+    if (ctx->fm_mem) cudaFree(ctx->fm_mem);
+    ctx->fm_mem = nullptr;
+    ctx->fm_bytes = 0;
+    ctx->fm_n = ctx->fm_nnz = ctx->fm_k = ctx->fm_p = 0;
+    ctx->fm = FmDev{};
+}
+
+FmDev fm_view(fr_ctx *ctx, int p0, const fr_options *opt) {
+    FmDev f = ctx->fm;
+    f.res = ctx->fm.res + p0;
+    f.maxwdeg = &ctx->prep->maxwdeg;
+    f.permille = opt ? opt->fm_permille : 0;
+    return f;
+}
+
 fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps) {
     if (reps < 1) reps = 1;
     if (ctx->pair_mem && P <= ctx->pairs_cap && R <= ctx->rounds_cap) return ensure_reps(ctx, reps);
@@ -419,6 +483,7 @@ extern "C" fr_status fr_destroy(fr_ctx *ctx) {
     destroy_graph_cache(ctx);
     free_base(ctx);
     free_pairs(ctx);
+    free_fm(ctx);
     if (ctx->reps_mem) cudaFree(ctx->reps_mem);
     if (ctx->hg_mem) cudaFree(ctx->hg_mem);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -478,6 +543,10 @@ fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *
         if (opt->mb_reps > 64) { ctx_error(ctx, "mb_reps > 64"); return FR_ERR_INVALID_ARG; }
         if (opt->pre_waves < -1 || opt->pre_waves > 4) {
             ctx_error(ctx, "pre_waves must be in [-1, 4]");
+            return FR_ERR_INVALID_ARG;
+        }
+        if (opt->fm_permille < 0 || opt->fm_permille > 1000) {
+            ctx_error(ctx, "fm_permille must be in [0, 1000]");
             return FR_ERR_INVALID_ARG;
         }
         if (opt->cluster_ctas != 0) {
@@ -723,6 +792,27 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
     long long cut_before = -1, wA0 = 0, wB0 = 0, cur_cut = 0, cur_A = 0, cur_B = 0;
     long long pulses = 0, relabels = 0;
     int levels = 0, sccr = 0;
+    // pairwise improvement: the FM step first (once), then the flow iterations on its result
+    FmRes fres;
+    memset(&fres, 0, sizeof(fres));
+    const bool fm_on = opt.fm_permille > 0;
+    if (fm_on) {
+        st = ensure_fm(ctx, g->n, g->nnz, k, 1);
+        if (st == FR_OK) st = setup_single(ctx, g, part, k, a, b, host_budget_base(W, k, eps, al), Lmax, opt.mb ? 1 : 0);
+        if (st == FR_OK) {
+            Work w = make_work(ctx, 0, 0, 1, g->n, &opt);
+            int nf = 0;
+            CK(launch_fm(w, fm_view(ctx, 0, &opt), k, ctx->sms, ctx->stream, &nf));
+            Ctl c;
+            CK(cudaMemcpyAsync(ctx->h_stage + 2048, ctx->fm.res, sizeof(FmRes), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->h_stage + 4096, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            memcpy(&fres, ctx->h_stage + 2048, sizeof(FmRes));
+            memcpy(&c, ctx->h_stage + 4096, sizeof(Ctl));
+            st = status_from_ctl(ctx, c, "fr_refine_pair (FM)");
+        }
+        if (st != FR_OK) { if (res) res->status = st; return st; }
+    }
     while (iters < max_iters) {
         ++iters;
         st = run_pair_iteration(ctx, g, part, k, a, b, host_budget_base(W, k, eps, al), Lmax, W, &opt, &o);
@@ -748,6 +838,13 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
         res->flow = o.flow;
         res->cut_before = cut_before < 0 ? 0 : cut_before;
         res->wA_before = wA0; res->wB_before = wB0;
+        res->cut_fm = res->cut_before;
+        if (fm_on) {
+            res->cut_before = fres.cut0;
+            res->wA_before = fres.wA0; res->wB_before = fres.wB0;
+            res->cut_fm = fres.cut1;
+            res->fm_moves = fres.kept;
+        }
         res->cut_after = cur_cut; res->wA_after = cur_A; res->wB_after = cur_B;
         res->corridor_n = o.nc; res->corridor_arcs = o.m;
         res->accepted = accepted;

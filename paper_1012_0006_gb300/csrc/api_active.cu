@@ -38,13 +38,16 @@ struct StepOut {
     long long flow, oldcut, newcut, cA, cB, nA, nB;
     int nc, m, accept, feasible;
     long long pulses, relabels;
+    FmRes fm;   // the FM step before this iteration (fm_first)
 };
 
 // One flow iteration of block-disjoint pairs, each with its budget base: scan, step,
 // cluster and step kernels over their union network.  Accepted pairs are applied
-// to part (and the device block weights) by the commit phase.
+// to part (and the device block weights) by the commit phase.  fm_first: the FM step
+// of every pair runs first (the pairwise improvement is FM, then the flows).
 fr_status run_pairs_step(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, const std::vector<StepPair> &ps,
-                         long long Lmax, long long W, const fr_options *opt, std::vector<StepOut> &out) {
+                         long long Lmax, long long W, const fr_options *opt, bool fm_first,
+                         std::vector<StepOut> &out) {
     const int P = (int)ps.size();
     const int reps = opt->mb_reps > 0 ? opt->mb_reps : 1;
     fr_status st = ensure_pairs(ctx, P, 1, reps);
@@ -87,12 +90,22 @@ fr_status run_pairs_step(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t 
         emax = std::max(emax, e1);
     }
     const int grid = choose_grid(ctx, opt, tpb, 2 * P, std::max(1LL, est));
+    if (fm_first) {
+        int nf = 0;
+        CK(launch_fm(w, fm_view(ctx, 0, opt), k, ctx->sms, ctx->stream, &nf));
+    }
     CK(launch_scan_list(w, 0, ctx->stream));
     CK(launch_round(ctx, w, grid, tpb, ctx->stream, nullptr, emax, (double)g->nnz / g->n,
                     opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
     PairAcc *ha = reinterpret_cast<PairAcc *>(ctx->h_stage + (kHostStage / 2));
     SideDev *hsd = reinterpret_cast<SideDev *>(ha + P);
     Ctl *hc = reinterpret_cast<Ctl *>(hsd + 2 * P);
+    FmRes *hf = reinterpret_cast<FmRes *>(hc + 1);
+    if ((size_t)((char *)(hf + P) - ctx->h_stage) > kHostStage) {
+        ctx_error(ctx, "active scheduling: %d pairs exceed the staging buffer", P);
+        return FR_ERR_TOO_LARGE;
+    }
+    if (fm_first) CK(cudaMemcpyAsync(hf, ctx->fm.res, sizeof(FmRes) * P, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ha, ctx->pacc, sizeof(PairAcc) * P, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hsd, ctx->sides, sizeof(SideDev) * 2 * P, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hc, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
@@ -118,6 +131,8 @@ fr_status run_pairs_step(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t 
         o.feasible = ha[i].feasible;
         o.pulses = hc->pulses;
         o.relabels = hc->relabels;
+        if (fm_first) o.fm = hf[i];
+        else memset(&o.fm, 0, sizeof(o.fm));
     }
     return FR_OK;
 }
@@ -125,8 +140,8 @@ fr_status run_pairs_step(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t 
 struct PairRun {
     int a, b;
     double al;
-    int iters, accepted, running;
-    long long cut_before, wA0, wB0, cur_cut, cur_A, cur_B, flow;
+    int iters, accepted, running, fm_moves;
+    long long cut_before, wA0, wB0, cut_fm, cur_cut, cur_A, cur_B, flow;
     int nc, m;
     long long pulses, relabels;
 };
@@ -151,6 +166,7 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
     CK(cudaSetDevice(ctx->device));
     release_corridor(ctx);
     st = ensure_base(ctx, g->n, g->nnz, k, opt.mb_reps);
+    if (st == FR_OK && opt.fm_permille > 0) st = ensure_fm(ctx, g->n, g->nnz, k, k / 2 + 1);
     if (st != FR_OK) { if (summary) summary->status = st; return st; }
     CK(cudaMemcpyAsync(ctx->part_backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
     const int adaptive = opt.adaptive ? 1 : 0;
@@ -200,8 +216,9 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
                 q.a = pa[i]; q.b = pb[i]; q.al = alpha; q.running = 1; q.cut_before = -1;
                 run.push_back(q);
             }
-            // adaptive flow iterations (Section 4.1), every pair on its own alpha
-            for (;;) {
+            // FM first (once), then adaptive flow iterations (Section 4.1), every pair on
+            // its own alpha
+            for (bool first = true;; first = false) {
                 std::vector<StepPair> ps;
                 std::vector<int> idx;
                 for (size_t i = 0; i < run.size(); ++i)
@@ -211,13 +228,20 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
                     }
                 if (ps.empty()) break;
                 std::vector<StepOut> outs;
-                st = run_pairs_step(ctx, g, part, k, ps, Lmax, W, &opt, outs);
+                const bool fm_first = first && opt.fm_permille > 0;
+                st = run_pairs_step(ctx, g, part, k, ps, Lmax, W, &opt, fm_first, outs);
                 if (st != FR_OK) break;
                 for (size_t j = 0; j < ps.size(); ++j) {
                     PairRun &q = run[idx[j]];
                     const StepOut &o = outs[j];
                     ++q.iters;
-                    if (q.cut_before < 0) { q.cut_before = o.oldcut; q.wA0 = o.cA; q.wB0 = o.cB; }
+                    if (q.cut_before < 0) {
+                        q.cut_before = o.oldcut; q.wA0 = o.cA; q.wB0 = o.cB; q.cut_fm = o.oldcut;
+                        if (fm_first) {
+                            q.cut_before = o.fm.cut0; q.wA0 = o.fm.wA0; q.wB0 = o.fm.wB0;
+                            q.fm_moves = o.fm.kept;
+                        }
+                    }
                     q.cur_cut = o.oldcut; q.cur_A = o.cA; q.cur_B = o.cB;
                     q.flow = o.flow; q.nc = o.nc; q.m = o.m; q.pulses = o.pulses; q.relabels = o.relabels;
                     corridor_arcs += o.m;
@@ -237,10 +261,8 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
             }
             if (st != FR_OK) break;
             for (const PairRun &q : run) {
-                if (q.accepted) {
-                    active[q.a] = active[q.b] = 1;
-                    ++accepted_total;
-                }
+                if (q.accepted || q.fm_moves > 0) active[q.a] = active[q.b] = 1;   // partition changed
+                accepted_total += q.accepted;
                 dcut_total += q.cur_cut - q.cut_before;
                 if (out_n < cap) {
                     fr_pair_result &res = results[out_n];
@@ -256,6 +278,7 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
                     res.corridor_n = q.nc; res.corridor_arcs = q.m;
                     res.accepted = q.accepted;
                     res.pulses = q.pulses; res.relabels = q.relabels;
+                    res.cut_fm = q.cut_fm; res.fm_moves = q.fm_moves;
                 }
                 ++out_n;
             }

@@ -343,6 +343,11 @@ static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
+        if (opt->fm_permille > 0) {   // pairwise improvement: FM first, then the flow
+            int nf = 0;
+            CK(launch_fm(w, fm_view(ctx, pl.off[r], opt), pl.k, ctx->sms, ctx->stream, &nf));
+            nl += nf;
+        }
         CK(launch_scan_list(w, 0, ctx->stream));
         CK(launch_round(ctx, w, pl.grid[r], pl.tpb, ctx->stream, nullptr, pl.est_max[r], pl.avg_degree,
                         opt->cluster_ctas ? opt->cluster_ctas : ctx->tune_ctas));
@@ -369,6 +374,11 @@ static fr_status enqueue_sweep_profiled(fr_ctx *ctx, const fr_graph *g, const Ba
     for (int r = 0; r < nr; ++r) {
         const int P = pl.off[r + 1] - pl.off[r];
         Work w = make_work(ctx, r, pl.off[r], P, g->n, opt);
+        if (opt->fm_permille > 0) {   // (not bracketed: the profile's phases are the flow path's)
+            int nf = 0;
+            CK(launch_fm(w, fm_view(ctx, pl.off[r], opt), pl.k, ctx->sms, ctx->stream, &nf));
+            nl += nf;
+        }
         CK(cudaEventRecord(ctx->pev[8 * r], ctx->stream));
         CK(launch_scan_list(w, 0, ctx->stream));
         CK(cudaEventRecord(ctx->pev[8 * r + 1], ctx->stream));
@@ -405,7 +415,8 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   (long long)(uintptr_t)ctx->pair_mem, ctx->tune_gr, ctx->tune_inner,
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
                                   opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas, ctx->tune_sched,
-                                  ctx->narrow_ok, opt->pre_waves, ctx->tune_prewaves};
+                                  ctx->narrow_ok, opt->pre_waves, ctx->tune_prewaves, opt->fm_permille,
+                                  (long long)(uintptr_t)ctx->fm_mem};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
     cudaGraphExec_t exec = nullptr;
@@ -558,12 +569,16 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
         if (summary) *summary = sum;
         return FR_OK;
     }
+    if (opt->fm_permille > 0 && (st = ensure_fm(ctx, g->n, g->nnz, k, pl.np)) != FR_OK) return st;
     float ms = 0.f;
     if ((st = run_sweep(ctx, g, part, pl, opt, &ms)) != FR_OK) return st;
     std::vector<PairAcc> A(pl.np);
     std::vector<SideDev> S(2 * pl.np);
     std::vector<Ctl> C(pl.nr);
     std::vector<int> pa(pl.np), pb(pl.np);
+    std::vector<FmRes> FR(opt->fm_permille > 0 ? pl.np : 0);
+    if (!FR.empty())
+        CK(cudaMemcpyAsync(FR.data(), ctx->fm.res, sizeof(FmRes) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(S.data(), ctx->sides, sizeof(SideDev) * 2 * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(C.data(), ctx->ctl, sizeof(Ctl) * pl.nr, cudaMemcpyDeviceToHost, ctx->stream));
@@ -627,6 +642,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             const int acc = a.accept;
             sum.accepted += acc;
             sum.cut_after += acc ? a.dcut : 0;
+            if (!FR.empty()) sum.cut_after += FR[i].cut1 - FR[i].cut0;
             sum.corridor_arcs += a.m;
             if (results && i < cap) {
                 fr_pair_result &R = results[i];
@@ -645,6 +661,13 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
                 R.status = FR_OK;
                 R.pulses = C[r].pulses; R.relabels = C[r].relabels;
                 R.bfs_levels = C[r].levels; R.scc_rounds = C[r].scc_rounds; R.ncomp = a.ncomp;
+                R.cut_fm = a.oldcut;
+                if (!FR.empty()) {   // before = before the FM step
+                    R.cut_before = FR[i].cut0;
+                    R.wA_before = FR[i].wA0;
+                    R.wB_before = FR[i].wB0;
+                    R.fm_moves = FR[i].kept;
+                }
             }
         }
     sum.device_ns = (long long)(ms * 1e6);

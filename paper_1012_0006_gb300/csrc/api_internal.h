@@ -8,6 +8,7 @@
 #include "flowref.h"
 #include "fr_internal.cuh"
 #include "round_kernel.cuh"
+#include "fm_kernel.cuh"
 
 constexpr int kMaxK = 1024;                 // blocks per partition (quotient graph in device bitmaps)
 constexpr size_t kHostStage = 8u << 20;     // pinned staging for small host<->device copies
@@ -90,6 +91,11 @@ struct fr_ctx {
     void *hg_mem = nullptr;
     size_t hg_bytes = 0;
     int *hg_xadj = nullptr, *hg_adjncy = nullptr, *hg_adjwgt = nullptr, *hg_vwgt = nullptr, *hg_part = nullptr;
+    // two-way FM state (allocated on the first call with fm_permille > 0)
+    void *fm_mem = nullptr;
+    size_t fm_bytes = 0;
+    int fm_n = 0, fm_nnz = 0, fm_k = 0, fm_p = 0;
+    fr::FmDev fm = {};
     // captured CUDA graphs of batch sweeps
     std::vector<GraphCacheEntry> gcache;
     bool use_graphs = true;
@@ -130,6 +136,11 @@ fr_status run_prep(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t 
 fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, int32_t a, int32_t b,
                        long long Ubase, long long Lmax, int mb);
 fr_status reset_idle(fr_ctx *ctx);
+// FM workspace for graphs up to n vertices / nnz arcs, k blocks and P pairs per call.
+fr_status ensure_fm(fr_ctx *ctx, int n, int nnz, int k, int P);
+void free_fm(fr_ctx *ctx);
+// The FM state of the pairs [p0, ...) of a call (results at res + p0).
+fr::FmDev fm_view(fr_ctx *ctx, int p0, const fr_options *opt);
 // Launches of one flow iteration over the pairs of w after the boundary scan:
 // step (BFS, ids, build) -> cluster max flow -> step (rest), or one step kernel.
 // est_pair_vertices: estimated corridor size of the largest pair (chooses the cluster size);

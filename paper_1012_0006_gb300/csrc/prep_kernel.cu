@@ -38,7 +38,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
     __syncthreads();
     int err = 0;
     long long W = 0, maxc = 0, cut = 0;
-    int maxw = 0;
+    int maxw = 0, maxwd = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (xadj[0] != 0 || xadj[n] != nnz)) err = E_INVALID;
     for (long long v = (long long)blockIdx.x * kPrepTPB + threadIdx.x; v < n; v += (long long)gridDim.x * kPrepTPB) {
         const int pv = part[v];
@@ -77,6 +77,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
             }
         }
         if (wdeg >= (1LL << 30) && err == 0) err = E_TOO_LARGE;
+        else if (wdeg > maxwd) maxwd = (int)wdeg;
         if (inb) inb[v] = bnd ? 1 : 0;
     }
     __syncthreads();
@@ -89,11 +90,12 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
     const long long bW = block_sum_ll<kPrepTPB>(W);
     const long long bC = block_sum_ll<kPrepTPB>(cut);
     __shared__ long long s_max;
-    __shared__ int s_err, s_maxw;
-    if (threadIdx.x == 0) { s_max = 0; s_err = 0; s_maxw = 0; }
+    __shared__ int s_err, s_maxw, s_maxwd;
+    if (threadIdx.x == 0) { s_max = 0; s_err = 0; s_maxw = 0; s_maxwd = 0; }
     __syncthreads();
     if (maxc) atomicMax((unsigned long long *)&s_max, (unsigned long long)maxc);
     if (maxw) atomicMax(&s_maxw, maxw);
+    if (maxwd) atomicMax(&s_maxwd, maxwd);
     if (err) atomicMax(&s_err, err);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -101,6 +103,7 @@ prep_kernel(const int *__restrict__ xadj, const int *__restrict__ adjncy, const 
         if (bC) atomicAdd((unsigned long long *)&out->totcut, (unsigned long long)bC);
         if (s_max) atomicMax((unsigned long long *)&out->maxc, (unsigned long long)s_max);
         if (s_maxw) atomicMax(&out->maxw, s_maxw);
+        if (s_maxwd) atomicMax(&out->maxwdeg, s_maxwd);
         if (s_err) atomicMax(&out->err, s_err);
     }
 }

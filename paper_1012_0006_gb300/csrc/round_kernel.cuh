@@ -21,7 +21,8 @@ struct PrepOut {
     long long W, maxc, totcut;
     int err, err_where;
     int npairs, nrounds;
-    int maxw, pad;       // max edge weight
+    int maxw;            // max edge weight
+    int maxwdeg;         // max weighted degree
 };
 // bl, blc, inb (optional, all or none): the boundary candidate list of the sweep
 // (GraphDev.bl); inb needs no clearing, prep writes every entry.

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
                 ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
-                ("pre_waves", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("pre_waves", ctypes.c_int32), ("fm_permille", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -48,7 +48,8 @@ class PairResult(ctypes.Structure):
                 ("accepted", ctypes.c_int32), ("iters", ctypes.c_int32), ("alpha_final", ctypes.c_double),
                 ("status", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("round", ctypes.c_int32),
                 ("pulses", ctypes.c_int64), ("relabels", ctypes.c_int64), ("bfs_levels", ctypes.c_int32),
-                ("scc_rounds", ctypes.c_int32), ("ncomp", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("scc_rounds", ctypes.c_int32), ("ncomp", ctypes.c_int32), ("fm_moves", ctypes.c_int32),
+                ("cut_fm", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
