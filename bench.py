@@ -380,6 +380,7 @@ def run_ours(args, world, rank, local, pg):
 
     compare = batched_vs_per_pair(F, ctx, dev) if args.compare else None
     active = active_blocks(F, ctx, g, part0, w) if args.active else None
+    fm = fm_sweeps(F, ctx, g, part0, w) if args.fm else None
 
     serving = None
     if args.serve or args.serve_full:
@@ -407,7 +408,7 @@ def run_ours(args, world, rank, local, pg):
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare,
-            "active_blocks": active,
+            "active_blocks": active, "fm": fm,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -431,6 +432,47 @@ def active_blocks(F, ctx, g, part0, w, max_outer=16):
             "outer_rounds": nouter, "refinements": summ["npairs"], "matchings": summ["nrounds"],
             "accepted": summ["accepted"], "cut_before": summ["cut_before"], "cut_after": summ["cut_after"],
             "ms": round(el * 1e3, 2), "refinements_per_s": round(summ["npairs"] / el, 2)}
+
+
+def fm_sweeps(F, ctx, g, part0, w, reps=3):
+    """The bench workload's sweep with the two-way FM step (TopGain, Section 2.2) before
+    every pair's flow, stopped after 1 % and 5 % of the pair's vertices moved without an
+    improvement, against the flow-only sweep: device time per sweep (CUDA events around
+    the call, min of reps after one warm run) and what each step gained on the cut."""
+    import torch
+    out = {"workload": "bench workload, FM then flow per pair"}
+    base = None
+    for pm in (0, 10, 50):
+        opts = F.default_options(mb=int(w["mb"]), fm_permille=pm)
+        part = part0.clone()
+        st, res, summ = ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], opts)
+        best = None
+        for _ in range(reps):
+            part.copy_(part0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], opts, results=False)
+            e1.record()
+            torch.cuda.synchronize()
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+        ctx.set_profiling(True)
+        part.copy_(part0)
+        ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], opts, results=False)
+        fm_ms = ctx.profile()["fm_ms"]
+        ctx.set_profiling(False)
+        d = {"ms_per_sweep": round(best, 3), "pairs_per_s": round(summ["npairs"] / (best / 1e3), 1),
+             "cut_before": summ["cut_before"], "cut_after": summ["cut_after"],
+             "fm_gain": int(sum(r["cut_before"] - r["cut_fm"] for r in res)),
+             "flow_gain": int(sum(r["cut_fm"] - r["cut_after"] for r in res)),
+             "fm_moves_kept": int(sum(r["fm_moves"] for r in res))}
+        if pm == 0:
+            base = best
+            out["flow_only"] = d
+        else:
+            d["fm_ms_per_sweep"] = round(best - base, 3)
+            d["fm_phases_ms_summed_over_pairs"] = {kk: round(v, 3) for kk, v in fm_ms.items()}
+            out[f"fm_permille_{pm}"] = d
+    return out
 
 
 # ------------------------------------------------- batched vs one pair per launch ----
@@ -603,6 +645,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=None)
     ap.add_argument("--active", action=argparse.BooleanOptionalAction, default=True,
                     help="active block scheduling with adaptive flow iterations on the bench workload")
+    ap.add_argument("--fm", action=argparse.BooleanOptionalAction, default=True,
+                    help="sweeps with the two-way FM step before each flow (1 %% and 5 %% stopping rules)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 (timing rule)")

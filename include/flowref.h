@@ -88,7 +88,7 @@ typedef struct fr_options {
                               vertices moved without an improvement (50 = the 5 % of the
                               paper's setup); 0 = no FM.  fr_refine_pair, fr_refine_batch and
                               fr_refine_active; needs a simple graph and every gain within
-                              +-2047 (max edge weight x max degree), else FR_ERR_TOO_LARGE */
+                              +-1023 (max weighted degree of the graph), else FR_ERR_TOO_LARGE */
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b);
@@ -278,6 +278,8 @@ typedef struct fr_profile_info {
     int64_t scan_listed;      /* boundary-scan list entries read, summed over rounds */
     int64_t scan_rows;        /* of them, vertices of the rounds' blocks (rows scanned) */
     int64_t scan_arcs;        /* arcs of those rows */
+    double fm_ms[3];          /* FM step (fm_permille > 0), summed over pairs: boundary sort and
+                                 initial stacks, the moves, rollback and bookkeeping */
     int32_t cluster_sizes[5]; /* CTAs per cluster the library can launch (4, 6, 8, 12, 16) */
     int32_t cluster_max_active[5]; /* clusters of each size resident at once on this GPU */
 } fr_profile_info;

@@ -80,16 +80,13 @@ __global__ void __launch_bounds__(1024) fm_offsets_kernel(Work w, FmDev f) {
     for (int i = threadIdx.x; i < G.k; i += blockDim.x) f.blockn[i] = f.blockarcs[i] = 0;
 }
 
-// Boundary of every pair: weights to the own block and to the partner block within
-// G[A u B]; vertices with an edge to the partner enter their pair's list.  Reads the
-// boundary candidate list when there is one (a superset of the k-way boundary).
+// Weights of every paired vertex to its own block and to the partner block within
+// G[A u B] (so that the moves never scan an adjacency for them); vertices with an edge
+// to the partner are the boundary and enter their pair's list.
 __global__ void __launch_bounds__(kFmTPB) fm_gather_kernel(Work w, FmDev f) {
     if ((w.prev_err && __ldcg(w.prev_err)) || __ldcg(&w.ctl->error)) return;
     const GraphDev G = w.graphs[0];
-    const long long cnt = G.bl ? (long long)__ldcg(G.blc) : (long long)G.n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int v = G.bl ? __ldcg(G.bl + i) : (int)i;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
         const int b = G.part[v];
         const int s = side_of(G, b);
         if (s < 0) continue;
@@ -103,9 +100,9 @@ __global__ void __launch_bounds__(kFmTPB) fm_gather_kernel(Work w, FmDev f) {
             if (pu == b) in += wt;
             else if (pu == partner) ex += wt;
         }
-        if (ex == 0) continue;
         f.in[v] = in;
         f.ext[v] = ex;
+        if (ex == 0) continue;
         f.flags[v] = kFmTouched | kFmInQ;
         const int pos = atomicAdd(f.bcnt + (s >> 1), 1);
         f.vlist[f.voff[s >> 1] + pos] = v;
@@ -149,15 +146,22 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+constexpr int kFmWords = kFmMaxBuckets / 32;   // bitmap words per block
+
 struct FmShared {
     int top[2 * kFmMaxBuckets];          // top entry of each (block, bucket) stack, -1 empty
-    unsigned bits[2 * kFmMaxBuckets / 32];   // non-empty (or holding stale entries) stacks
+    // where vbits says the top entry is current: its vertex, the entry below it and the
+    // vertex's adjacency range (so a move reads no entry and no offsets from memory)
+    int topv[2 * kFmMaxBuckets], topb[2 * kFmMaxBuckets];
+    int topj0[2 * kFmMaxBuckets], topj1[2 * kFmMaxBuckets];
+    unsigned bits[2 * kFmWords];         // non-empty stacks (possibly holding only stale entries)
+    unsigned vbits[2 * kFmWords];        // the top entry is known to be current
     long long red[kFmTPB / 32];
     int best_len, tried;
     long long best_cut, best_wA, best_wB;
 };
 
-__global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
+__global__ void __launch_bounds__(kFmTPB, 1) fm_pair_kernel(Work w, FmDev f) {
     extern __shared__ __align__(16) char fm_smem[];
     FmShared &S = *reinterpret_cast<FmShared *>(fm_smem);
     const GraphDev G = w.graphs[0];
@@ -194,6 +198,12 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
     const long long E = f.eoff[p];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+    unsigned long long t_mark = globaltimer();
+    auto mark = [&](int idx) {
+        const unsigned long long now = globaltimer();
+        if (threadIdx.x == 0) atomicAddLL(&w.ctl->timers[idx], (long long)(now - t_mark));
+        t_mark = now;
+    };
     // 1. sort the boundary by (block, bucket, stamp)
     int m = 1;
     while (m < B) m <<= 1;
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
         }
     }
     for (int i = threadIdx.x; i < 2 * kFmMaxBuckets; i += blockDim.x) S.top[i] = -1;
-    for (int i = threadIdx.x; i < 2 * kFmMaxBuckets / 32; i += blockDim.x) S.bits[i] = 0;
+    for (int i = threadIdx.x; i < 2 * kFmWords; i += blockDim.x) S.bits[i] = S.vbits[i] = 0;
     for (int o = 16; o > 0; o >>= 1) c0 += __shfl_down_sync(0xffffffffu, c0, o);
     if (lane == 0) S.red[warp] = c0;
     __syncthreads();
@@ -252,12 +262,22 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
         f.ent_below[E + i] = (i > 0 && sr.bk[i - 1] == bk) ? (int)(E + i - 1) : -1;
         if (i + 1 == B || sr.bk[i + 1] != bk) {
             S.top[bk] = (int)(E + i);
+            S.topv[bk] = sr.v[i];
+            S.topb[bk] = (i > 0 && sr.bk[i - 1] == bk) ? (int)(E + i - 1) : -1;
+            S.topj0[bk] = __ldg(G.xadj + sr.v[i]);
+            S.topj1[bk] = __ldg(G.xadj + sr.v[i] + 1);
             atomicOr(&S.bits[bk >> 5], 1u << (bk & 31));
+            atomicOr(&S.vbits[bk >> 5], 1u << (bk & 31));
         }
     }
     __syncthreads();
 
-    // 3. the moves (warp 0)
+    mark(T_FM_SORT);
+    // 3. the moves (warp 0).  vbits: the top entry of a stack is known to be current
+    // (set by a push or a check, cleared by a pop or when the top's vertex may have
+    // changed), with its vertex, the entry below and the adjacency range cached.  While
+    // a move updates its neighbours, lane 0 checks the entry below the popped one, so
+    // that the next pop from the same stack usually needs no memory round trip.
     if (warp == 0) {
         const long long Lmax = G.Lmax;
         const long long limit = (long long)f.permille * n_p / 1000;
@@ -269,32 +289,36 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
         const long long eend = f.eoff[p + 1];   // entries of this pair: [E, eend)
         bool bad = false;
         for (;;) {
-            // top entry of each block: highest bucket whose top is current
+            // top of each block: highest bucket whose top entry is current
             int tb[2];
             for (int s = 0; s < 2; ++s) {
                 tb[s] = -1;
                 for (;;) {
-                    // highest set bit among the block's bucket words (kFmMaxBuckets / 32 = 128
-                    // words: four per lane)
-                    // lane L looks at words 4L..4L+3, from the top
-                    int best = -1;
-                    for (int k4 = 3; k4 >= 0; --k4) {
-                        const unsigned word = S.bits[s * (kFmMaxBuckets / 32) + lane * 4 + k4];
-                        if (best < 0 && word) best = (lane * 4 + k4) * 32 + 31 - __clz(word);
+                    int best = -1;   // lane L looks at the words 2L, 2L + 1, from the top
+                    for (int k2 = 1; k2 >= 0; --k2) {
+                        const unsigned word = S.bits[s * kFmWords + lane * 2 + k2];
+                        if (best < 0 && word) best = (lane * 2 + k2) * 32 + 31 - __clz(word);
                     }
                     const unsigned has = __ballot_sync(0xffffffffu, best >= 0);
                     if (!has) break;
-                    const int src = 31 - __clz(has);
-                    const int hb = __shfl_sync(0xffffffffu, best, src);
+                    const int hb = __shfl_sync(0xffffffffu, best, 31 - __clz(has));
                     const int key = s * kFmMaxBuckets + hb;
-                    const int e = S.top[key];
+                    if ((S.vbits[key >> 5] >> (key & 31)) & 1u) { tb[s] = hb; break; }
                     int ok = 0;
                     if (lane == 0) {
+                        const int e = S.top[key];
                         const int v = f.ent_v[e];
+                        const int ev = f.ent_ver[e], below = f.ent_below[e];
                         const unsigned char fl = f.flags[v];
-                        ok = (fl & kFmInQ) && !(fl & kFmMoved) && f.ver[v] == f.ent_ver[e];
-                        if (!ok) {
-                            const int below = f.ent_below[e];
+                        const int vv = f.ver[v], x0 = __ldg(G.xadj + v), x1 = __ldg(G.xadj + v + 1);
+                        ok = (fl & kFmInQ) && !(fl & kFmMoved) && vv == ev;
+                        if (ok) {
+                            S.topv[key] = v;
+                            S.topb[key] = below;
+                            S.topj0[key] = x0;
+                            S.topj1[key] = x1;
+                            S.vbits[key >> 5] |= 1u << (key & 31);
+                        } else {
                             S.top[key] = below;
                             if (below < 0) S.bits[key >> 5] &= ~(1u << (key & 31));
                         }
@@ -319,63 +343,67 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
                 s = (int)(splitmix64(~fs ^ (unsigned long long)nm) & 1);
             }
             const int key = s * kFmMaxBuckets + tb[s];
-            const int e = S.top[key];
-            const int v = f.ent_v[e];
+            const int v = S.topv[key], below = S.topb[key];
+            const int j0 = S.topj0[key], j1 = S.topj1[key];
             const int g = tb[s] - gmax;
             const int from = s ? b : a, to = s ? a : b;
+            const long long cv = __ldg(G.vwgt + v);
             __syncwarp();
+            // pop; the check of the entry below starts now (lane 0)
+            int v2 = -1, ev2 = 0, b2 = -1;
             if (lane == 0) {
-                const int below = f.ent_below[e];
                 S.top[key] = below;
+                S.vbits[key >> 5] &= ~(1u << (key & 31));
                 if (below < 0) S.bits[key >> 5] &= ~(1u << (key & 31));
                 f.flags[v] = kFmTouched | kFmMoved;
                 G.part[v] = to;
                 ml[nm] = v;
+                if (below >= 0) { v2 = f.ent_v[below]; ev2 = f.ent_ver[below]; b2 = f.ent_below[below]; }
             }
             ++nm;
             cut -= g;
-            const long long cv = __ldg(G.vwgt + v);
-            if (s == 0) { wA -= cv; wB += cv; } else { wB -= cv; wA += cv; }
             __syncwarp();
+            unsigned char fl2 = 0;
+            int ver2 = -1, x20 = 0, x21 = 0;
+            bool hit2 = false;   // the entry below belongs to a neighbour updated by this move
             // the moved vertex's arcs, 32 at a time in adjacency order
-            const int j0 = __ldg(G.xadj + v), j1 = __ldg(G.xadj + v + 1);
             for (int jb = j0; jb < j1; jb += 32) {
                 const int j = jb + lane;
+                int u = -1, wt = 0;
+                if (j < j1) { u = __ldg(G.adjncy + j); wt = __ldg(G.adjwgt + j); }
+                if (jb == j0 && lane == 0 && below >= 0) {   // second half of the check
+                    fl2 = f.flags[v2]; ver2 = f.ver[v2];
+                    x20 = __ldg(G.xadj + v2); x21 = __ldg(G.xadj + v2 + 1);
+                }
                 bool act = false;
-                int u = -1, nin = 0, nex = 0, ukey = -1;
-                if (j < j1) {
-                    u = __ldg(G.adjncy + j);
+                int nin = 0, nex = 0, ukey = -1, okey = -1, nver = 0, ux0 = 0, ux1 = 0;
+                unsigned char fl = 0;
+                if (u >= 0) {
+                    // independent loads, issued together
                     const int pu = G.part[u];
-                    if (pu == a || pu == b) {
-                        const unsigned char fl = f.flags[u];
-                        if (!(fl & kFmMoved)) {
-                            act = true;
-                            if (fl & kFmTouched) {
-                                const int wt = __ldg(G.adjwgt + j);
-                                nin = f.in[u];
-                                nex = f.ext[u];
-                                if (pu == from) { nin -= wt; nex += wt; }
-                                else { nin += wt; nex -= wt; }
-                            } else {
-                                // first touch: weights from the current blocks (v already moved)
-                                const int partner = pu == a ? b : a;
-                                const int k1 = __ldg(G.xadj + u + 1);
-                                for (int k = __ldg(G.xadj + u); k < k1; ++k) {
-                                    const int px = G.part[__ldg(G.adjncy + k)];
-                                    const int wt = __ldg(G.adjwgt + k);
-                                    if (px == pu) nin += wt;
-                                    else if (px == partner) nex += wt;
-                                }
-                            }
-                            ukey = (pu == a ? 0 : kFmMaxBuckets) + (nex - nin) + gmax;
-                        }
+                    fl = f.flags[u];
+                    const int in0 = f.in[u], ex0 = f.ext[u], ver0 = f.ver[u];
+                    ux0 = __ldg(G.xadj + u); ux1 = __ldg(G.xadj + u + 1);
+                    if ((pu == a || pu == b) && !(fl & kFmMoved)) {
+                        act = true;
+                        nin = in0; nex = ex0;
+                        if (pu == from) { nin -= wt; nex += wt; }
+                        else { nin += wt; nex -= wt; }
+                        const int sb = pu == a ? 0 : kFmMaxBuckets;
+                        ukey = sb + (nex - nin) + gmax;
+                        if (fl & kFmInQ) okey = sb + (ex0 - in0) + gmax;
+                        nver = ver0 + 1;
                     }
                 }
-                // first touches join the touched list (for the cleanup)
-                const bool fresh = act && !(f.flags[u] & kFmTouched);
+                const int v2b = __shfl_sync(0xffffffffu, v2, 0);
+                hit2 |= __ballot_sync(0xffffffffu, act && u == v2b) != 0;
+                // first changes join the touched list (for the cleanup)
+                const bool fresh = act && !(fl & kFmTouched);
                 const unsigned fm_ = __ballot_sync(0xffffffffu, fresh);
                 if (fresh) vl[tl + __popc(fm_ & lanemask_lt())] = u;
                 tl += __popc(fm_);
+                // the stack holding u's old entry may have it on top: its top is unknown now
+                if (okey >= 0) atomicAnd(&S.vbits[okey >> 5], ~(1u << (okey & 31)));
                 const bool push = act && nex > 0;
                 const unsigned pm = __ballot_sync(0xffffffffu, push);
                 if (nxt + __popc(pm) > eend) {   // cannot happen: pushes <= boundary + arcs
@@ -388,22 +416,26 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
                 const unsigned grp = __match_any_sync(0xffffffffu, push ? ukey : -1 - lane);
                 const unsigned lower = grp & lanemask_lt();
                 const long long pos_lower = __shfl_sync(0xffffffffu, pos, lower ? 31 - __clz(lower) : lane);
-                int below = -1;
-                if (push) below = lower ? (int)pos_lower : S.top[ukey];
+                int ubelow = -1;
+                if (push) ubelow = lower ? (int)pos_lower : S.top[ukey];
                 __syncwarp();
                 if (act) {
                     f.in[u] = nin;
                     f.ext[u] = nex;
-                    const int nv = f.ver[u] + 1;
-                    f.ver[u] = nv;
+                    f.ver[u] = nver;
                     f.flags[u] = (unsigned char)(kFmTouched | (push ? kFmInQ : 0));
                     if (push) {
                         f.ent_v[pos] = u;
-                        f.ent_ver[pos] = nv;
-                        f.ent_below[pos] = below;
+                        f.ent_ver[pos] = nver;
+                        f.ent_below[pos] = ubelow;
                         if ((grp & ~lower & ~(1u << lane)) == 0) {   // highest lane of the group
                             S.top[ukey] = (int)pos;
+                            S.topv[ukey] = u;
+                            S.topb[ukey] = ubelow;
+                            S.topj0[ukey] = ux0;
+                            S.topj1[ukey] = ux1;
                             atomicOr(&S.bits[ukey >> 5], 1u << (ukey & 31));
+                            atomicOr(&S.vbits[ukey >> 5], 1u << (ukey & 31));
                         }
                     }
                 }
@@ -411,6 +443,22 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
                 __syncwarp();
             }
             if (bad) break;
+            if (s == 0) { wA -= cv; wB += cv; } else { wB -= cv; wA += cv; }   // (its load overlapped the arcs)
+            // the entry below the popped one: current, and still the top of its stack?
+            if (lane == 0 && below >= 0) {
+                if (j0 >= j1) {   // no arcs: the second half of the check did not run
+                    fl2 = f.flags[v2]; ver2 = f.ver[v2];
+                    x20 = __ldg(G.xadj + v2); x21 = __ldg(G.xadj + v2 + 1);
+                }
+                if (!hit2 && S.top[key] == below && (fl2 & kFmInQ) && !(fl2 & kFmMoved) && ver2 == ev2) {
+                    S.topv[key] = v2;
+                    S.topb[key] = b2;
+                    S.topj0[key] = x20;
+                    S.topj1[key] = x21;
+                    S.vbits[key >> 5] |= 1u << (key & 31);
+                }
+            }
+            __syncwarp();
             // best state: smallest (overload, cut, max block weight)
             const long long mx = wA > wB ? wA : wB, bmx = bwA > bwB ? bwA : bwB;
             const long long ov = mx > Lmax ? mx - Lmax : 0, bov = bmx > Lmax ? bmx - Lmax : 0;
@@ -430,6 +478,7 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
         }
     }
     __syncthreads();
+    mark(T_FM_MOVES);
     const int best_len = S.best_len, nm = S.tried, tl = (int)S.red[0];
     // 4. roll back the moves after the best prefix; clear what the search touched
     for (int i = best_len + threadIdx.x; i < nm; i += blockDim.x) {
@@ -462,6 +511,8 @@ __global__ void __launch_bounds__(kFmTPB) fm_pair_kernel(Work w, FmDev f) {
             }
         }
     }
+    __syncthreads();
+    mark(T_FM_FINISH);
 }
 
 size_t fm_pair_smem() {

@@ -7,8 +7,8 @@
 
 namespace fr {
 
-constexpr int kFmMaxBuckets = 4096;   // gain buckets per block: gains in [-2047, 2047]
-constexpr int kFmSortSmem = 8192;     // boundary entries a pair sorts in shared memory
+constexpr int kFmMaxBuckets = 2048;   // gain buckets per block: gains in [-1023, 1023]
+constexpr int kFmSortSmem = 4096;     // boundary entries a pair sorts in shared memory
 
 // Result of one pair's FM search (what fr_pair_result reports).
 struct FmRes {

@@ -42,7 +42,9 @@ enum PhaseBits : uint32_t {
 enum TimerIdx { T_BFS = 0, T_SELECT, T_LID, T_BUILD, T_FLOW1, T_GR, T_FLOW2, T_REACH, T_SCC, T_SWEEP, T_EVAL,
                 T_COMMIT,
                 // cluster kernel, summed over pairs: member scan and load, flow to t, return to s, reach
-                T_CL_LOAD, T_CL_FLOW, T_CL_RETURN, T_CL_REACH, T_CL_SCC, T_CL_MEMBERS, T_CL_RELABEL, T_COUNT };
+                T_CL_LOAD, T_CL_FLOW, T_CL_RETURN, T_CL_REACH, T_CL_SCC, T_CL_MEMBERS, T_CL_RELABEL,
+                // FM step, summed over pairs: boundary sort and initial stacks, moves, rollback
+                T_FM_SORT, T_FM_MOVES, T_FM_FINISH, T_COUNT };
 
 enum SideCode { SS_EXPAND = 1, SS_SELECT = 2, SS_DONE = 3 };
 

@@ -75,14 +75,15 @@ class ProfileInfo(ctypes.Structure):
                 ("cluster_remote_arcs", ctypes.c_int64),
                 ("fallback_pairs", ctypes.c_int64),
                 ("scan_listed", ctypes.c_int64), ("scan_rows", ctypes.c_int64), ("scan_arcs", ctypes.c_int64),
-                ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5)]
+                ("fm_ms", ctypes.c_double * 3), ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
-             if f not in ("phase_ms", "cluster_phase_ms", "cluster_sizes", "cluster_max_active")}
+             if f not in ("phase_ms", "cluster_phase_ms", "cluster_sizes", "cluster_max_active", "fm_ms")}
+        d["fm_ms"] = dict(zip(("sort", "moves", "finish"), list(self.fm_ms)))
         d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
         d["cluster_phase_ms"] = dict(zip(("load", "flow", "return", "reach", "scc", "members", "relabel"),
                                          list(self.cluster_phase_ms)))

@@ -62,7 +62,7 @@ def test_batch_fm_workloads(F, ctx, cfg, scale, pm):
 
 
 def test_batch_fm_boundary_sorted_in_global_memory(F, ctx):
-    """A pair whose boundary exceeds what one CTA sorts in shared memory (8192
+    """A pair whose boundary exceeds what one CTA sorts in shared memory (4096
     entries): 32 x 160 x 160 grid split in two across a 32 x 160 face per side."""
     w = I.grid3d_rcb(32, 160, 160, k=2, alpha=1.0)
     rref = _batch(F, ctx, w, dict(mb=1, fm_permille=10))
@@ -106,7 +106,7 @@ def test_active_fm(F, ctx, okw):
 
 
 def test_fm_gain_range_is_checked(F, ctx):
-    """Weighted degrees above 2047 do not fit the gain buckets: FR_ERR_TOO_LARGE, part untouched."""
+    """Weighted degrees above 1023 do not fit the gain buckets: FR_ERR_TOO_LARGE, part untouched."""
     w = I.random_small(6300, n_max=400, k_max=3)
     w = dict(w, adjwgt=np.full(len(w["adjncy"]), 2000, np.int32))
     g, part = _dev(F, w)
