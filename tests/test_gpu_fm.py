@@ -130,3 +130,21 @@ def test_fm_option_rejected_where_unsupported(F, ctx):
     cfg.opt.fm_permille = 50
     srv = ctypes.c_void_p()
     assert F.lib().fr_server_create(ctypes.byref(srv), ctypes.byref(cfg)) == F.FR_ERR_INVALID_ARG
+
+
+def test_batch_fm_full_rgg3d_bench_configuration(F, ctx):
+    """The full 4,194,304-vertex 3D rgg (k = 64, the bench workload) with the FM step at
+    the 1 % stopping rule, against the oracle's sweep run pair-parallel on the host cores
+    (identical to the sequential sweep, pinned on CPU)."""
+    import os
+    w = I.config(4)
+    okw = dict(mb=1, fm_permille=10)
+    st, pref, rref, nr, done = O.refine_batch_mt(w, len(os.sched_getaffinity(0)), opts=O.options(**okw))
+    assert st == 0 and done == len(rref)
+    g, part = _dev(F, w)
+    st, res, summ = ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], F.default_options(**okw))
+    assert summ["npairs"] == len(rref) and summ["nrounds"] == nr
+    for rg, rc in zip(res, rref):
+        for f in FIELDS:
+            assert rg[f] == rc[f], (f, rg["a"], rg["b"], rg["round"])
+    assert np.array_equal(part.cpu().numpy(), pref)
