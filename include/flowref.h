@@ -65,7 +65,9 @@ typedef struct fr_graph {
 typedef struct fr_options {
     int32_t mb;            /* 1: most balanced minimum cut (Section 4.1.1); 0: smallest source set */
     int32_t mb_reps;       /* R >= 1 topological sweeps; sweep r >= 1 keys components by splitmix64(seed ^ r ^ minid) */
-    int32_t adaptive;      /* 1: adaptive flow iterations (Section 4.1); fr_refine_pair only */
+    int32_t adaptive;      /* 1: adaptive flow iterations (Section 4.1) in fr_refine_pair, fr_refine_batch
+                              (each round's pairs iterate together, every pair on its own alpha;
+                              launched round by round, no graph replay) and fr_refine_active */
     int32_t max_iters;     /* iteration cap of the adaptive loop (default 10) */
     double alpha_max;      /* alpha' >= 1, the upper bound of alpha */
     uint64_t seed;         /* sweep keys for r >= 1 */

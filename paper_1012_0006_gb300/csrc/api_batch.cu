@@ -689,6 +689,12 @@ extern "C" fr_status fr_refine_batch(fr_ctx *ctx, const fr_graph *g, int32_t *pa
     if (st == FR_OK) st = check_params(ctx, eps, alpha, &opt);
     if (st == FR_OK && cap > 0 && !results) { ctx_error(ctx, "results is NULL"); st = FR_ERR_INVALID_ARG; }
     if (st != FR_OK) { if (summary) summary->status = st; return st; }
+    if (opt.adaptive) {
+        // adaptive flow iterations (Section 4.1) per pair: the rounds' pairs iterate
+        // together, each on its own alpha, launch sequence by launch sequence -- the
+        // first outer round of active block scheduling, where every block is active
+        return fr_refine_active(ctx, g, part, k, eps, alpha, &opt, 1, cap, results, summary, nullptr);
+    }
     CK(cudaSetDevice(ctx->device));
     release_corridor(ctx);
     st = batch_core(ctx, g, part, k, eps, alpha, &opt, cap, results, summary);

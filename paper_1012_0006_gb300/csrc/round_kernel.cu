@@ -339,6 +339,11 @@ __device__ bool grid_scan(const Work &w, long long N, ValF val, EmitF emit, long
 
 // ============================================================== step kernel ==
 
+// Visit-list offsets of the BFS levels of this launch (kLvlCap levels; deeper levels are
+// not recorded and the select then scans the whole list).
+constexpr int kLvlCap = 64;
+__shared__ long long g_lvl[kLvlCap + 2];
+
 template <int TPB>
 struct StepKernel {
     const Work &w;
@@ -423,6 +428,10 @@ struct StepKernel {
                 s_lc[s] = 0;
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qcnt[(level + 2) % 3] = 0;
+            if (threadIdx.x == 0 && level <= kLvlCap) {
+                g_lvl[level] = base;
+                g_lvl[level + 1] = base + cnt;
+            }
             any = __syncthreads_or(any);
             if (!any) {
                 vtotal = base + cnt;
@@ -500,8 +509,21 @@ struct StepKernel {
         anysel = __syncthreads_or(anysel);
         const long long total = vtotal;
         if (anysel) {
-            for (int s = threadIdx.x; s < ns; s += TPB) s_T[s] = 0;   // prefix being built
+            // the overflow levels' entries: the visit list is in level order
+            int lmin = INT_MAX, lmax = -1;
+            for (int s = threadIdx.x; s < ns; s += TPB) {
+                s_T[s] = 0;   // prefix being built
+                if (s_state[s] == SS_SELECT) { lmin = min(lmin, s_lstar[s]); lmax = max(lmax, s_lstar[s]); }
+            }
+            lmin = __reduce_min_sync(FULL, lmin);
+            lmax = __reduce_max_sync(FULL, lmax);
+            __shared__ int s_lmm[2];
+            if (threadIdx.x == 0) { s_lmm[0] = INT_MAX; s_lmm[1] = -1; }
             __syncthreads();
+            if ((threadIdx.x & 31) == 0) { atomicMin(&s_lmm[0], lmin); atomicMax(&s_lmm[1], lmax); }
+            __syncthreads();
+            const bool rec = s_lmm[1] < kLvlCap;
+            const long long e_lo = rec ? g_lvl[s_lmm[0]] : 0, e_hi = rec ? g_lvl[s_lmm[1] + 1] : total;
             // histograms are triple buffered: pass p fills buffer p % 3 (cleared by the
             // host or during pass p - 2) and clears buffer (p + 1) % 3, last read in pass p - 2
             const long long hsz = (long long)ns * kHistBins;
@@ -512,7 +534,7 @@ struct StepKernel {
                     long long *nxt = w.hist + ((pass + 1) % 3) * hsz;
                     for (long long i = G.tid; i < hsz; i += G.size) nxt[i] = 0;
                 }
-                for (long long e = G.tid; e < total; e += G.size) {
+                for (long long e = e_lo + G.tid; e < e_hi; e += G.size) {
                     const int v = w.vq_v[e], s = w.vq_s[e];
                     if (s_state[s] != SS_SELECT) continue;
                     const GraphDev &Gr = w.graphs[w.pairs[s >> 1].g];

@@ -81,3 +81,29 @@ def test_invalid_max_outer_leaves_part(F, ctx):
                                     check=False)
     assert st == 1   # FR_ERR_INVALID_ARG
     assert np.array_equal(part.cpu().numpy(), np.array(w["part"], np.int32))
+
+
+@pytest.mark.parametrize("name,make,okw", [
+    ("rgg2d-4096", lambda: I.config(2, scale=1 / 16), dict(mb=1, adaptive=1, max_iters=8, alpha_max=16.0)),
+    ("grid3d-32", lambda: I.config(3, scale=1 / 64), dict(mb=1, adaptive=1, max_iters=5, alpha_max=8.0)),
+    ("small", lambda: I.random_small(7100, n_max=2500, k_max=8), dict(mb=0, adaptive=1, max_iters=6, alpha_max=8.0)),
+    ("small-fm", lambda: I.random_small(7101, n_max=2500, k_max=8),
+     dict(mb=1, adaptive=1, max_iters=6, alpha_max=8.0, fm_permille=50)),
+], ids=lambda x: x if isinstance(x, str) else "")
+def test_batch_with_adaptive_iterations(F, ctx, name, make, okw):
+    """fr_refine_batch with adaptive flow iterations: every pair of a round on its own
+    alpha, against the oracle's batch (same pairs, results and partition)."""
+    import torch
+    w = make()
+    st, pref, rref, nr = O.refine_batch(w, alpha=1.0, opts=O.options(**okw))
+    assert st == 0
+    g = F.DeviceGraph.from_workload(w)
+    part = torch.as_tensor(np.array(w["part"], np.int32)).cuda()
+    st, res, summ = ctx.refine_batch(g, part, w["k"], w["eps"], 1.0, F.default_options(**okw))
+    assert summ["npairs"] == len(rref) and summ["nrounds"] == nr
+    for rg, rc in zip(res, rref):
+        for f in FIELDS + ("cut_fm", "fm_moves"):
+            assert rg[f] == rc[f], (f, rg["a"], rg["b"], rg["round"])
+    assert np.array_equal(part.cpu().numpy(), pref)
+    if name.startswith("rgg2d"):
+        assert any(r["iters"] > 1 for r in rref)   # the adaptive loop did iterate
