@@ -293,11 +293,13 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     barrier(pg)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev0.record()
     pairs = arcs = flow_ns = 0
     launches = 0
-    for _ in range(args.steps):
+    for i in range(args.steps):
         summ = step()
+        evs[i].record()
         pairs += summ["npairs"]
         arcs += summ["corridor_arcs"]
         flow_ns += summ["flow_ns"]
@@ -307,6 +309,7 @@ def run_ours(args, world, rank, local, pg):
     barrier(pg)
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
+    step_ms = [ev0.elapsed_time(evs[0])] + [evs[i - 1].elapsed_time(evs[i]) for i in range(1, args.steps)]
     t_max = reduce_max(pg, t_ms, dev)
     pairs_all = reduce_sum(pg, pairs, dev)
     value = pairs_all / (t_max / 1e3)
@@ -399,7 +402,10 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0:
         out = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3),
+            "per_step_ms": {"median": round(statistics.median(step_ms), 3), "min": round(min(step_ms), 3),
+                            "max": round(max(step_ms), 3)},
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": desc, "n": w["n"], "nnz": w["nnz"], "k": k,
                        "pairs_per_step": int(pairs / args.steps), "rounds_per_step": nr,

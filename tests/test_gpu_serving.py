@@ -104,3 +104,32 @@ def test_a_bad_request_fails_alone(gpu_lib):
     assert res[100][0]["status"] == F.FR_ERR_INVALID_ARG
     assert np.array_equal(res[100][1][:graphs[bad["gi"]]["n"]], bad["part"])
     assert all(res[r["tag"]][0]["status"] == 0 for r in reqs)
+
+
+def test_served_results_match_the_oracle(gpu_lib):
+    """A seeded sample of the request mix through the server against the CPU oracle's
+    sweep of the same request (partition, pairs, rounds, cuts)."""
+    import oracle as O
+    F = gpu_lib
+    graphs = _graphs()
+    reqs = _requests(graphs, 16, seed=11)
+    opts = F.default_options(mb=1)
+    with F.Server(0, max_inflight=6, opts=opts) as srv:
+        ids = [srv.add_graph(g["xadj"], g["adjncy"], g["adjwgt"], g["vwgt"]) for g in graphs]
+        for r in reqs:
+            srv.submit(ids[r["gi"]], r["part"], r["k"], r["eps"], r["alpha"], r["tag"])
+        got = {}
+        for _ in reqs:
+            resp, part = srv.next(max(g["n"] for g in graphs), timeout_ms=120000)
+            got[resp["tag"]] = (resp, part)
+    for r in reqs:
+        g = graphs[r["gi"]]
+        w = dict(n=g["n"], xadj=g["xadj"], adjncy=g["adjncy"], adjwgt=g["adjwgt"], vwgt=g["vwgt"],
+                 part=r["part"], k=r["k"], eps=r["eps"], alpha=r["alpha"])
+        st, pref, rref, nr = O.refine_batch(w, opts=O.options(mb=1))
+        assert st == 0
+        resp, part = got[r["tag"]]
+        assert resp["status"] == 0
+        assert np.array_equal(part[:g["n"]], pref)
+        assert (resp["npairs"], resp["nrounds"]) == (len(rref), nr)
+        assert resp["cut_after"] - resp["cut_before"] == sum(x["cut_after"] - x["cut_before"] for x in rref)
