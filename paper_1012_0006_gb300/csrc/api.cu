@@ -149,6 +149,7 @@ fr_status ensure_reps(fr_ctx *ctx, int reps) {
         ctx_error(ctx, "sweep workspace exceeds the arena bound");
         return FR_ERR_OOM;
     }
+    destroy_graph_cache(ctx);   // captured sweeps hold pointers into the old workspace
     if (ctx->reps_mem) cudaFree(ctx->reps_mem);
     ctx->reps_mem = nullptr;
     ctx->reps_bytes = 0;
@@ -243,7 +244,7 @@ fr_status ensure_base(fr_ctx *ctx, int n, int nnz, int k, int reps) {
     CK(cudaMemsetAsync(ctx->dist, 0xFF, sizeof(int) * (size_t)nn, ctx->stream));
     CK(cudaMemsetAsync(ctx->lid, 0xFF, sizeof(int) * (size_t)nn, ctx->stream));
     CK(cudaMemsetAsync(ctx->cbits, 0, sizeof(unsigned int) * (size_t)(nn / 32 + 2), ctx->stream));
-    ctx->graph_valid = false;
+    destroy_graph_cache(ctx);   // captured sweeps hold pointers into the old workspace
     return ensure_reps(ctx, rr);
 }
 
@@ -291,7 +292,7 @@ fr_status ensure_fm(fr_ctx *ctx, int n, int nnz, int k, int P) {
     CK(cudaMemsetAsync(f.flags, 0, (size_t)nn, ctx->stream));
     CK(cudaMemsetAsync(f.blockn, 0, sizeof(int) * (size_t)kk, ctx->stream));
     CK(cudaMemsetAsync(f.blockarcs, 0, sizeof(int) * (size_t)kk, ctx->stream));
-    ctx->graph_valid = false;
+    destroy_graph_cache(ctx);   // captured sweeps hold pointers into the old workspace
     return FR_OK;
 }
 
@@ -339,7 +340,7 @@ fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps) {
     ctx->ctl = carve<Ctl>(p, rr);
     ctx->hist = carve<long long>(p, 3LL * 2 * pp * kHistBins);
     ctx->pcur = carve<int>(p, pp);
-    ctx->graph_valid = false;
+    destroy_graph_cache(ctx);   // captured sweeps hold pointers into the old workspace
     return ensure_reps(ctx, rp);
 }
 

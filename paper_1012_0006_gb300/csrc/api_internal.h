@@ -82,7 +82,6 @@ struct fr_ctx {
     int *pcur = nullptr;
     long long *sw_absd = nullptr;
     int *sw_j = nullptr;
-    bool graph_valid = false;
     // corridor handle state
     unsigned long long gen = 0;
     fr_corridor *live = nullptr;

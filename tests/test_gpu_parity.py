@@ -433,3 +433,13 @@ def test_arena_bound_gives_oom(F):
     with F.Context(0, arena_bytes=1 << 16) as small:
         st, res, summ = small.refine_batch(g, part, w["k"], w["eps"], w["alpha"], check=False)
         assert st == F.FR_ERR_OOM
+
+
+def test_captured_sweeps_survive_workspace_growth(F):
+    """A captured sweep is replayed only while the workspace it points into lives:
+    small graph (captured, replayed), larger graph (workspaces reallocated), small
+    graph again -- the oracle's partition every time."""
+    small, big = I.config(3, scale=1 / 64), I.config(4, scale=1 / 16)
+    with F.Context(0) as c:
+        for w in (small, small, big, small, big, small):
+            _check_batch(F, c, w)
