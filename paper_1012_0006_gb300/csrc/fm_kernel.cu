@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(kFmTPB, 1) fm_pair_kernel(Work w, FmDev f) {
 
     mark(T_FM_SORT);
     // 3. the moves (warp 0).  vbits: the top entry of a stack is known to be current
-    // (set by a push or a check, cleared by a pop or when the top's vertex may have
-    // changed), with its vertex, the entry below and the adjacency range cached.  While
+    // (set by a push or a check, cleared when the top is popped or goes stale), with its
+    // vertex, the entry below and the adjacency range cached.  While
     // a move updates its neighbours, lane 0 checks the entry below the popped one, so
     // that the next pop from the same stack usually needs no memory round trip.
     if (warp == 0) {
@@ -402,8 +402,17 @@ __global__ void __launch_bounds__(kFmTPB, 1) fm_pair_kernel(Work w, FmDev f) {
                 const unsigned fm_ = __ballot_sync(0xffffffffu, fresh);
                 if (fresh) vl[tl + __popc(fm_ & lanemask_lt())] = u;
                 tl += __popc(fm_);
-                // the stack holding u's old entry may have it on top: its top is unknown now
-                if (okey >= 0) atomicAnd(&S.vbits[okey >> 5], ~(1u << (okey & 31)));
+                // u's old entry is stale now.  If it is the known-current top of its stack,
+                // take it off: the entry below becomes the top, not yet checked.  (A top known
+                // to be current that belongs to another vertex stays current.)  Done before any
+                // lane reads a top for a push.
+                if (okey >= 0 && ((S.vbits[okey >> 5] >> (okey & 31)) & 1u) && S.topv[okey] == u) {
+                    const int nb = S.topb[okey];
+                    S.top[okey] = nb;
+                    if (nb < 0) atomicAnd(&S.bits[okey >> 5], ~(1u << (okey & 31)));
+                    atomicAnd(&S.vbits[okey >> 5], ~(1u << (okey & 31)));
+                }
+                __syncwarp();
                 const bool push = act && nex > 0;
                 const unsigned pm = __ballot_sync(0xffffffffu, push);
                 if (nxt + __popc(pm) > eend) {   // cannot happen: pushes <= boundary + arcs
