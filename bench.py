@@ -594,7 +594,22 @@ def run_serving(F, device, full=False, requests=None, log_prefix=""):
     st = srv.stats()
     srv.close()
     lat = np.array(lat)
+    # the oracle on a seeded 1 % sample of the requests (at most 15, ~10 s): per-request time
+    import oracle as O
+    sample = [reqs[i] for i in sorted(set(rs.integers(0, len(reqs), max(1, min(15, len(reqs) // 100))).tolist()))]
+    t2 = time.perf_counter()
+    ndone = 0
+    for gi, k, eps in sample:
+        g = pool[gi]
+        w = dict(n=g["n"], xadj=g["xadj"], adjncy=g["adjncy"], adjwgt=g["adjwgt"], vwgt=g["vwgt"],
+                 part=parts[(gi, k)], k=k, eps=eps, alpha=2.0)
+        assert O.refine_batch(w, opts=O.options(mb=1))[0] == 0
+        ndone += 1
+        if time.perf_counter() - t2 > 10.0:
+            break
+    cpu_ms = (time.perf_counter() - t2) * 1e3 / ndone
     return {"requests": len(reqs), "failed": int(sum(1 for x in stat if x != 0)),
+            "cpu_oracle_ms_per_request": round(cpu_ms, 2), "cpu_oracle_sample": ndone,
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "requests_per_s": round(len(reqs) / el, 2), "saturated_requests_per_s": round(sat, 2),
             "arrival_rate": round(lam, 2), "steps": st["steps"], "max_concurrent": st["max_concurrent"],
