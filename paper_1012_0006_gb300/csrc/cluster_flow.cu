@@ -247,27 +247,38 @@ struct ClusterFlow {
         for (int q = 0; q < p; ++q) pbase += __ldcg(&w.pacc[q].nc);
         int *pmem = w.cid + pbase, *pacs = w.outoff + pbase, *plocal = w.color;
         {
-            // one pass: every thread counts a contiguous slice of the CTA's share of
-            // the union, one block scan and one cluster prefix place its members
+            // every warp takes a contiguous chunk of the CTA's share of the union and
+            // reads it 32 entries at a time (coalesced), counting and then placing the
+            // pair's members with ballots; one block scan over the warps' counts and one
+            // cluster prefix give the positions, so the list stays in local-id order
             const long long per = (nu + C - 1) / C;
             const long long c0 = per * rank, c1 = min((long long)nu, c0 + per);
-            const long long tper = (max(0LL, c1 - c0) + TPB - 1) / TPB;
-            const long long t0 = c0 + tper * threadIdx.x, t1 = min(c1, t0 + tper);
+            const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const long long wper = ((max(0LL, c1 - c0) + TPB / 32 - 1) / (TPB / 32) + 31) / 32 * 32;
+            const long long w0 = min(c1, c0 + wper * wid), w1 = min(c1, w0 + wper);
             int mine = 0;
-            for (long long i = t0; i < t1; ++i) mine += (__ldcg(&w.sid[i]) >> 1) == p;
+            for (long long b = w0; b < w1; b += 32) {
+                const long long i = b + lane;
+                mine += __popc(__ballot_sync(FULL, i < w1 && (__ldcg(&w.sid[i]) >> 1) == p));
+            }
             int tot;
-            const int ex0 = block_exclusive_scan<TPB>(mine, &tot);
+            const int ex0 = block_exclusive_scan<TPB>(lane == 0 ? mine : 0, &tot);
             if (threadIdx.x == 0) hdr0->counts[rank] = tot;
             sync();
-            int pos = ex0;
+            int pos = __shfl_sync(FULL, ex0, 0);
             for (int r = 0; r < rank; ++r) pos += *(volatile int *)&hdr0->counts[r];
             sync();   // counts read before they are reused
-            for (long long i = t0; i < t1; ++i)
-                if ((__ldcg(&w.sid[i]) >> 1) == p) {
-                    pmem[pos] = (int)i;
-                    plocal[i] = pos;
-                    ++pos;
+            for (long long b = w0; b < w1; b += 32) {
+                const long long i = b + lane;
+                const bool m = i < w1 && (__ldcg(&w.sid[i]) >> 1) == p;
+                const unsigned bal = __ballot_sync(FULL, m);
+                if (m) {
+                    const int at = pos + __popc(bal & ((1u << lane) - 1u));
+                    pmem[at] = (int)i;
+                    plocal[i] = at;
                 }
+                pos += __popc(bal);
+            }
         }
         __threadfence();
         sync();
