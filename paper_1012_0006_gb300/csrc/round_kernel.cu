@@ -527,8 +527,11 @@ struct StepKernel {
             // histograms are triple buffered: pass p fills buffer p % 3 (cleared by the
             // host or during pass p - 2) and clears buffer (p + 1) % 3, last read in pass p - 2
             const long long hsz = (long long)ns * kHistBins;
-            for (int pass = 0; pass < 4; ++pass) {
-                const int shift = 24 - 8 * pass;
+            // ids are below total_n: the digits above its highest byte are zero for every
+            // vertex, and those passes are skipped
+            const int first = w.total_n <= (1 << 8) ? 3 : w.total_n <= (1 << 16) ? 2 : w.total_n <= (1 << 24) ? 1 : 0;
+            for (int pass = 0; pass < 4 - first; ++pass) {
+                const int shift = 24 - 8 * (pass + first);
                 long long *hist = w.hist + (pass % 3) * hsz;
                 if (pass >= 1) {
                     long long *nxt = w.hist + ((pass + 1) % 3) * hsz;
