@@ -205,3 +205,28 @@ def test_fm_option_range_is_checked():
     for bad in (-1, 1001):
         st, _, _ = O.refine_pair(w, 0, 1, opts=O.options(fm_permille=bad))
         assert st == 1   # FRO_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fm_full_runs_replayed(seed):
+    """permille = 1000: the search only stops when both queues are empty (every boundary
+    vertex that can move has moved), on weighted graphs with zero vertex weights among
+    them, and the replay still matches move by move."""
+    w = I.random_small(5600 + seed, n_max=90, k_max=3)
+    res = replay(w, 0, 1, 1000, 1000 + seed, _lmax(w))
+    assert res["tried"] >= res["kept"]
+
+
+def test_fm_empty_boundary_is_a_no_op():
+    """Two blocks with no edge between them: no vertex is movable, nothing changes."""
+    xadj, adj, coords = I.grid2d(8, 8)
+    n = 64
+    part = np.zeros(n, np.int32)
+    part[coords[:, 0] >= 4] = 2                  # blocks 0 and 2 touch; block 1 holds one far corner
+    part[0] = 1
+    part[1] = 0
+    w = dict(n=n, nnz=len(adj), xadj=xadj, adjncy=adj, adjwgt=np.ones(len(adj), np.int32),
+             vwgt=np.ones(n, np.int32), part=part, k=3, eps=0.5, alpha=1.0)
+    # block 1 = {0} is adjacent to 1 and 8 (block 0): pair (1, 2) has no cut edge
+    st, out, res, moves = O.fm_pair(w, 1, 2, 1000, seed=0)
+    assert st == 0 and res["tried"] == 0 and res["kept"] == 0 and np.array_equal(out, part)
