@@ -10,8 +10,8 @@ step, so each step refines the same input.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank runs an independent replica (the method has no
-cross-GPU exchange in this build); rank 0 prints one JSON line.
+Under torchrun each rank runs an independent replica (the pairs of a round never
+exchange data, and no rank shares a graph with another); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -64,7 +65,7 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        self.path = os.path.join(os.environ.get("FR_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_rank{device}.csv")
 
     def start(self):
         try:

@@ -1050,8 +1050,9 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
 
 /* Section 4.3 (scheduling quotient graph refinement) and the appendix pseudocode
  * of active block scheduling, with the pairwise improvement restricted to the flow
- * refinement of Section 4.1 (the paper's pairwise step also runs FM searches,
- * which are not part of this build).  Every block starts active.  An outer round
+ * refinement of Section 4.1, preceded by the two-way FM search when fm_permille
+ * is set (the paper's pseudocode also runs multi-try FM searches, which this
+ * oracle does not implement).  Every block starts active.  An outer round
  * takes the quotient edges (a, b) of the current partition with a or b active,
  * marks every block inactive, and refines those pairs; a pair whose refinement
  * changed the partition marks a and b active again.  The outer rounds end when no

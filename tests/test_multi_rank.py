@@ -1,7 +1,7 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks on 127.0.0.1.
 
-bench.py runs one independent replica per GPU (the method has no exchange inside
-a round in this build); the ranks only meet in the barrier and in the max/sum
+bench.py runs one independent replica per GPU (the pairs of a round exchange no
+data, and each rank holds its own graph); the ranks only meet in the barrier and in the max/sum
 reductions of the timing, and rank 0 alone prints.  These tests run those pieces
 with world_size 2 on the gloo backend, without a GPU."""
 import json
