@@ -427,3 +427,55 @@ def test_adaptive_iterations_invariants():
     W = O.total_weight(w["vwgt"])
     assert max(ra.wA_after, ra.wB_after) <= O.lmax(W, 1, 2, w["eps"])
     assert ra.alpha_final in {1.0, 2.0, 4.0, 8.0, 16.0}
+
+
+def _adaptive_replay(w, a, b, alpha, alpha_max, max_iters, mb):
+    """The adaptive loop of Section 4.1 (reading D12) written out over the oracle's
+    single-iteration pieces (corridor, max flow, cut; each pinned above): returns the
+    final partition, the iterations run and the final alpha."""
+    part = np.array(w["part"], np.int32, copy=True)
+    vw = np.asarray(w["vwgt"], np.int64)
+    W = int(vw.sum())
+    Lmax = O.lmax(W, int(vw.max()), w["k"], w["eps"])
+    cut = O.pair_cut(w, part, a, b)
+    wA, wB = int(vw[part == a].sum()), int(vw[part == b].sum())
+    al, iters = alpha, 0
+    while iters < max_iters:
+        iters += 1
+        pb = O.Problem.build(w, a, b, O.budget_base(W, w["k"], w["eps"], al), part=part)
+        pb.maxflow()
+        _, side, _, _ = pb.cut(mb=mb)
+        trial = part.copy()
+        trial[pb.export()["gid"]] = np.where(side.astype(bool), b, a)
+        ncut = O.pair_cut(w, trial, a, b)
+        nA, nB = int(vw[trial == a].sum()), int(vw[trial == b].sum())
+        feasible = max(nA, nB) <= Lmax
+        if feasible and ncut < cut:
+            part, cut, wA, wB = trial, ncut, nA, nB
+            al = min(2.0 * al, alpha_max)
+            continue
+        if feasible:
+            if ncut == cut and max(nA, nB) < max(wA, wB):
+                part, cut, wA, wB = trial, ncut, nA, nB
+            break
+        if al == 1.0:
+            break
+        al = max(al / 2.0, 1.0)
+    return part, iters, al
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_adaptive_loop_replayed(seed):
+    """The oracle's adaptive flow iterations against the loop written out here from
+    D12 over the oracle's one-iteration pieces: same partition, iterations and alpha."""
+    w = I.random_small(5700 + seed, n_max=1500, k_max=3) if seed % 2 else I.config(2, scale=1 / 64)
+    pa, pb, _, _ = O.rounds(w)
+    a, b = int(pa[0]), int(pb[0])
+    mb = seed % 3 == 0
+    alpha, amax, iters = (1.0, 16.0, 10) if seed < 4 else (4.0, 8.0, 3)
+    exp, it, al = _adaptive_replay(w, a, b, alpha, amax, iters, int(mb))
+    st, part, res = O.refine_pair(w, a, b, alpha=alpha,
+                                  opts=O.options(mb=int(mb), adaptive=1, max_iters=iters, alpha_max=amax))
+    assert st == 0
+    assert np.array_equal(part, exp)
+    assert (res.iters, res.alpha_final) == (it, al)
