@@ -50,6 +50,11 @@
  *              block weight); stop after more than permille/1000 of the pair's
  *              vertices moved since the last best, or when both queues are empty
  *   pairwise   with FM on: FM first, then the flow iterations on its result
+ *
+ * Parity unpinned: the order of the sweeps r >= 1 (their splitmix64 keys) is
+ * checked only for what any valid order must satisfy (a topological order of the
+ * component DAG, every step a minimum cut); the quality of the most balanced cut
+ * against the true optimum is bounded by brute force, not fixed.
  *   batch      greedy edge colouring of the quotient graph in lexicographic
  *              (a, b) order (smallest free colour); each colour is a round of
  *              block-disjoint pairs; rounds in colour order, pairs of a round
