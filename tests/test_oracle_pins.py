@@ -479,3 +479,31 @@ def test_adaptive_loop_replayed(seed):
     assert st == 0
     assert np.array_equal(part, exp)
     assert (res.iters, res.alpha_final) == (it, al)
+
+
+def test_sweeps_with_keys_are_valid_orders():
+    """Sweeps r >= 1 (splitmix64 keys): each is a permutation of the components whose
+    every prefix moved to the sink side leaves a minimum cut (the prefix is closed under
+    the residual arcs), checked by brute force; d_j is the weight difference of that cut."""
+    checked = 0
+    for w, p in _small_cases(30):
+        ex = p.export()
+        F = p.maxflow(0)
+        masks, cut, bits = BF.cut_values(ex)
+        in_s, to_t, comp = p.residual_sets()
+        cA = int(w["vwgt"][w["part"] == 0].sum())
+        cB = int(w["vwgt"][w["part"] == 1].sum())
+        vw = w["vwgt"][ex["gid"]]
+        wA, wB = BF.side_weights(ex, vw, cA, cB, bits)
+        comps = sorted(set(int(c) for c in comp if c >= 0))
+        for r in (1, 2, 3):
+            order, d = p.sweep(r, seed=17 + r)
+            assert sorted(order.tolist()) == comps
+            for j in range(len(order) + 1):
+                moved = set(order[:j].tolist())
+                src = [(bool(in_s[i]) or (comp[i] >= 0 and comp[i] not in moved)) for i in range(p.nc)]
+                mk = BF.mask_of(src)
+                assert cut[mk] == F
+                assert wA[mk] - wB[mk] == d[j]
+        checked += 1
+    assert checked >= 20
