@@ -443,3 +443,21 @@ def test_captured_sweeps_survive_workspace_growth(F):
     with F.Context(0) as c:
         for w in (small, small, big, small, big, small):
             _check_batch(F, c, w)
+
+
+def test_batch_with_the_largest_block_count(F, ctx):
+    """k = 1024 (the largest the library takes): a 3D rgg of 32,768 vertices cut by RCB
+    into 1,024 blocks of 32, a quotient graph of thousands of pairs in many rounds; k =
+    1025 is refused."""
+    n = 32768
+    xadj, adj, coords = I.rgg(3, n, I.rgg_radius(3, n, 12.0), 4242)
+    vwgt = np.ones(n, np.int32)
+    part = I.rcb(coords, vwgt, 1024)
+    I.noise(xadj, adj, vwgt, 1024, part, 300, 77)
+    w = I._workload("rgg3d 32768 k=1024", xadj, adj, I.edge_weights(xadj, adj, 1, 10, 5), vwgt, part, 1024,
+                    eps=0.05, alpha=2.0, mb=1)
+    _, summ = _check_batch(F, ctx, w)
+    assert summ["npairs"] > 2000 and summ["nrounds"] > 10
+    g, p = _dev(F, w)
+    st, _, _ = ctx.refine_batch(g, p, 1025, w["eps"], w["alpha"], F.default_options(), check=False)
+    assert st == F.FR_ERR_INVALID_ARG
