@@ -22,7 +22,7 @@ i64p = ctypes.POINTER(ctypes.c_int64)
 class Options(ctypes.Structure):
     _fields_ = [("mb", ctypes.c_int32), ("mb_reps", ctypes.c_int32), ("adaptive", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("alpha_max", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("fm_permille", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("fm_permille", ctypes.c_int32), ("mt_alpha", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -32,6 +32,22 @@ class PairResult(ctypes.Structure):
                 ("accepted", ctypes.c_int32), ("iters", ctypes.c_int32), ("alpha_final", ctypes.c_double),
                 ("status", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("round", ctypes.c_int32),
                 ("cut_fm", ctypes.c_int64), ("fm_moves", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+
+
+class KwayResult(ctypes.Structure):
+    _fields_ = [("gain", ctypes.c_int64), ("tried", ctypes.c_int32), ("kept", ctypes.c_int32),
+                ("stop", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+
+
+class MTResult(ctypes.Structure):
+    _fields_ = [("gain", ctypes.c_int64), ("searches", ctypes.c_int32), ("tried", ctypes.c_int32),
+                ("kept", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
@@ -104,7 +120,25 @@ def lib():
         L.fro_refine_active.restype = ctypes.c_int32
         L.fro_refine_active.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
                                         ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32,
-                                        ctypes.c_int32, ctypes.POINTER(PairResult), i32p, i32p]
+                                        ctypes.c_int32, ctypes.POINTER(PairResult), i32p, i32p,
+                                        ctypes.POINTER(MTResult)]
+        L.fro_kaspar_stop.restype = ctypes.c_int32
+        L.fro_kaspar_stop.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double]
+        L.fro_kway_search.restype = ctypes.c_int32
+        L.fro_kway_search.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, i64p,
+                                      ctypes.c_int64, i32p, ctypes.c_int32, i32p, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(KwayResult), i32p, i32p, i64p,
+                                      ctypes.c_int32]
+        L.fro_multitry.restype = ctypes.c_int32
+        L.fro_multitry.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int64,
+                                   ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.POINTER(MTResult), i8p]
+        L.fro_mt_seed.restype = ctypes.c_uint64
+        L.fro_mt_seed.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32]
+        L.fro_kway_global.restype = ctypes.c_int32
+        L.fro_kway_global.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.POINTER(KwayResult), i32p]
         L.fro_fm_pair.restype = ctypes.c_int32
         L.fro_fm_pair.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(FMResult), i32p,
@@ -125,8 +159,8 @@ def _c32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
 
 
-def options(mb=0, mb_reps=1, adaptive=0, max_iters=1, alpha_max=1.0, seed=0, fm_permille=0):
-    return Options(mb, mb_reps, adaptive, max_iters, alpha_max, seed, fm_permille, 0)
+def options(mb=0, mb_reps=1, adaptive=0, max_iters=1, alpha_max=1.0, seed=0, fm_permille=0, mt_alpha=0):
+    return Options(mb, mb_reps, adaptive, max_iters, alpha_max, seed, fm_permille, mt_alpha)
 
 
 def validate(w):
@@ -267,9 +301,10 @@ def refine_batch(w, part=None, eps=None, alpha=None, opts=None):
     return st, part, [res[i].as_dict() for i in range(npairs.value)], nrounds.value
 
 
-def refine_active(w, part=None, eps=None, alpha=None, opts=None, max_outer=16, cap=None):
+def refine_active(w, part=None, eps=None, alpha=None, opts=None, max_outer=16, cap=None, mt_out=None):
     """Active block scheduling with flow refinement (fro_refine_active); returns
-    (status, part, per-refinement results in processing order, outer rounds run)."""
+    (status, part, per-refinement results in processing order, outer rounds run).
+    mt_out (a dict, optional) receives the totals of the multi-try passes."""
     part = np.array(w["part"] if part is None else part, np.int32, copy=True)
     eps = w["eps"] if eps is None else eps
     alpha = w["alpha"] if alpha is None else alpha
@@ -279,9 +314,12 @@ def refine_active(w, part=None, eps=None, alpha=None, opts=None, max_outer=16, c
     cap = cap if cap is not None else max(1, max_outer * k * (k - 1) // 2)
     res = (PairResult * cap)()
     npairs, nouter = ctypes.c_int32(), ctypes.c_int32()
+    mt = MTResult()
     st = lib().fro_refine_active(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
                                  k, eps, alpha, ctypes.byref(opts), max_outer, cap, res,
-                                 ctypes.byref(npairs), ctypes.byref(nouter))
+                                 ctypes.byref(npairs), ctypes.byref(nouter), ctypes.byref(mt))
+    if mt_out is not None:
+        mt_out.update(mt.as_dict())
     return st, part, [res[i].as_dict() for i in range(min(npairs.value, cap))], nouter.value
 
 
@@ -333,3 +371,69 @@ def fm_pair(w, a, b, permille, seed=0, part=None, Lmax=None):
                            a, b, Lmax, permille, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(res), _p(moves), w["n"])
     d = res.as_dict()
     return st, part, d, moves[:d["tried"]]
+
+
+def kaspar_stop(p, S1, S2, alpha, beta):
+    """KaSPar stopping rule of the k-way search (fro_kaspar_stop)."""
+    return lib().fro_kaspar_stop(p, S1, S2, alpha, beta)
+
+
+def mt_seed(seed, a, b):
+    return lib().fro_mt_seed(seed & 0xFFFFFFFFFFFFFFFF, a, b)
+
+
+def kway_search(w, init, alpha, beta=None, tseed=0, part=None, blockw=None, Lmax=None, touched=None, sid=1):
+    """One k-way local search (fro_kway_search) from the start set init; returns
+    (status, part, blockw, result dict, log) with log = (vertices, targets, gains)
+    of every move made, in order, before the rollback."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    k = w["k"]
+    if blockw is None:
+        blockw = np.bincount(part, weights=np.asarray(w["vwgt"], np.int64), minlength=k).astype(np.int64)
+    blockw = np.array(blockw, np.int64, copy=True)
+    if Lmax is None:
+        W = int(np.asarray(w["vwgt"], np.int64).sum())
+        Lmax = lmax(W, int(np.asarray(w["vwgt"]).max()), k, w["eps"])
+    if beta is None:
+        beta = float(np.log(w["n"]))
+    init = _c32(init)
+    n = w["n"]
+    lv, lt, lg = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int64)
+    res = KwayResult()
+    tp = _p(touched) if touched is not None else None
+    st = lib().fro_kway_search(n, _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part), k,
+                               _p(blockw, i64p), Lmax, _p(init), len(init), tp, sid, alpha, beta,
+                               tseed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(res), _p(lv), _p(lt), _p(lg, i64p), n)
+    d = res.as_dict()
+    t = d["tried"]
+    return st, part, blockw, d, (lv[:t], lt[:t], lg[:t])
+
+
+def multitry(w, pairs, alpha, seed=0, part=None, Lmax=None):
+    """One multi-try FM pass over the pairs of a matching (fro_multitry); returns
+    (status, part, totals dict, changed-block flags)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    k = w["k"]
+    if Lmax is None:
+        W = int(np.asarray(w["vwgt"], np.int64).sum())
+        Lmax = lmax(W, int(np.asarray(w["vwgt"]).max()), k, w["eps"])
+    pa = _c32([p[0] for p in pairs])
+    pb = _c32([p[1] for p in pairs])
+    res = MTResult()
+    changed = np.zeros(k, np.int8)
+    st = lib().fro_multitry(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part), k,
+                            Lmax, len(pairs), _p(pa), _p(pb), alpha, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(res),
+                            _p(changed, i8p))
+    return st, part, res.as_dict(), changed.astype(bool)
+
+
+def kway_global(w, alpha=10, init_mode=0, max_rounds=10, seed=0, part=None, eps=None):
+    """Global k-way refinement rounds (fro_kway_global); returns (status, part, totals, rounds)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    res = KwayResult()
+    nr = ctypes.c_int32()
+    st = lib().fro_kway_global(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
+                               w["k"], eps, init_mode, alpha, max_rounds, seed & 0xFFFFFFFFFFFFFFFF,
+                               ctypes.byref(res), ctypes.byref(nr))
+    return st, part, res.as_dict(), nr.value

@@ -15,6 +15,10 @@
  *   Section 4.1.1 Picard-Queyranne closed sets, smallest source set from
  *                 Ford-Fulkerson labelling, SCC contraction of the residual
  *                 graph, removal of S/T components, topological sweeps
+ *   Section 2.2   two-way FM with TopGain; k-way local search with one queue and
+ *                 the KaSPar stopping rule p mu^2 > alpha sigma^2 + beta
+ *   Section 4.2   multi-try FM (k-way searches from single boundary vertices)
+ *   Section 4.3   active block scheduling
  *
  * Readings where the paper is silent or ambiguous are fixed as follows and are
  * shared with the CUDA path only as a written specification:
@@ -50,6 +54,20 @@
  *              block weight); stop after more than permille/1000 of the pair's
  *              vertices moved since the last best, or when both queues are empty
  *   pairwise   with FM on: FM first, then the flow iterations on its result
+ *   k-way      one queue keyed by (max gain, stamp), larger first, stamps in the
+ *              order of insertions and key changes (start set in its order, then
+ *              per move the moved vertex's neighbours in CSR order); target = the
+ *              adjacent block of largest connection weight, ties to the smaller
+ *              splitmix64(tseed ^ u << 32 ^ P); a vertex whose target would exceed
+ *              L_max leaves the queue unmoved; after a move every unmoved neighbour
+ *              is keyed again (boundary) or leaves the queue (not boundary); stop by
+ *              the KaSPar rule after each move that is not a new minimum, or an
+ *              empty queue; roll back to the first lowest-cut prefix
+ *   multi-try  per pair of a matching, the vertices with a neighbour in the other
+ *              block, in splitmix64 order, visited round-robin over the pairs; a
+ *              vertex no search of the pass queued that is still a boundary vertex
+ *              starts a search from itself and its untouched boundary neighbours;
+ *              no vertex is queued by two searches of one pass; beta = ln n
  *
  * Parity unpinned: the order of the sweeps r >= 1 (their splitmix64 keys) is
  * checked only for what any valid order must satisfy (a topological order of the
@@ -81,7 +99,8 @@ typedef struct fro_options {
     int32_t fm_permille; /* > 0: two-way FM before the flows, stopped after more than
                             fm_permille / 1000 of the pair's vertices moved without an
                             improvement; 0: no FM */
-    int32_t pad0;
+    int32_t mt_alpha;    /* > 0: multi-try FM pass (KaSPar alpha) after each matching of
+                            fro_refine_active; 0: none (other entry points need 0) */
 } fro_options;
 
 typedef struct fro_pair_result {
@@ -100,6 +119,23 @@ typedef struct fro_fm_result {
     int32_t tried;       /* moves made before the stopping rule */
     int32_t kept;        /* moves kept after the rollback (a prefix) */
 } fro_fm_result;
+
+/* Result of one k-way search (or the sum over several). */
+typedef struct fro_kway_result {
+    int64_t gain;        /* cut decrease kept (>= 0) */
+    int32_t tried;       /* moves made before the stop */
+    int32_t kept;        /* moves kept after the rollback (a prefix) */
+    int32_t stop;        /* 1: the KaSPar rule stopped the (last) search; 0: empty queue */
+    int32_t pad0;
+} fro_kway_result;
+
+/* Totals of multi-try passes. */
+typedef struct fro_mt_result {
+    int64_t gain;        /* cut decrease kept */
+    int32_t searches;    /* k-way searches started */
+    int32_t tried, kept; /* moves made / kept */
+    int32_t pad0;
+} fro_mt_result;
 
 /* Input checks of Section 2.1 (omega > 0, c >= 0, symmetric simple CSR, 0 <= part < k). */
 int32_t fro_validate(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
@@ -151,7 +187,7 @@ int32_t fro_refine_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, c
                         const int32_t *vwgt, int32_t *part, int32_t k, int32_t a, int32_t b, double eps,
                         double alpha, const fro_options *opt, fro_pair_result *res);
 
-/* Two-way FM with TopGain on pair (a, b) (Section 2.2; stopping rule of Section 5):
+/* Two-way FM with TopGain on pair (a, b) (Section 2.2; stopping rule of Section 6):
  * moves vertices of a and b between the two blocks of part, then rolls back to the
  * best prefix.  moves (optional, moves_cap entries) receives every vertex moved, in
  * order, before the rollback.  FM keys: seed' = splitmix64(seed ^ a << 32 ^ b);
@@ -161,6 +197,36 @@ int32_t fro_fm_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const
                     const int32_t *vwgt, int32_t *part, int32_t a, int32_t b, int64_t Lmax, int32_t permille,
                     uint64_t seed, fro_fm_result *out, int32_t *moves, int32_t moves_cap);
 uint64_t fro_fm_seed(uint64_t seed, int32_t a, int32_t b);
+
+/* KaSPar stopping rule (Section 2.2): 1 iff p mu^2 > alpha sigma^2 + beta with
+ * mu = S1/p, sigma^2 = S2/p - mu^2 (S1, S2: sum of the p gains and of their
+ * squares), evaluated as the double expression (p*mu)*mu > alpha*sigma^2 + beta. */
+int32_t fro_kaspar_stop(int32_t p, int64_t S1, int64_t S2, int32_t alpha, double beta);
+
+/* One k-way local search (Section 2.2) from init[0..ninit) in that order, on part and
+ * the block weights blockw[k] (both updated to the kept prefix).  touched (may be
+ * NULL): multi-try marks, see fro_multitry; id >= 1 marks this search.  tseed keys
+ * the target ties.  The logs (optional, log_cap entries) receive every move in
+ * order before the rollback: vertex, target block, gain. */
+int32_t fro_kway_search(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, int32_t *part, int32_t k, int64_t *blockw, int64_t Lmax,
+                        const int32_t *init, int32_t ninit, int32_t *touched, int32_t id, int32_t alpha,
+                        double beta, uint64_t tseed, fro_kway_result *out, int32_t *log_v, int32_t *log_to,
+                        int64_t *log_gain, int32_t log_cap);
+
+/* One multi-try FM pass (Section 4.2) over the pairs (pa[i], pb[i]) of a matching;
+ * changed[k] (optional) marks every block a kept move left or entered. */
+int32_t fro_multitry(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, int32_t *part, int32_t k, int64_t Lmax, int32_t np, const int32_t *pa,
+                     const int32_t *pb, int32_t alpha, uint64_t seed, fro_mt_result *out, int8_t *changed);
+uint64_t fro_mt_seed(uint64_t seed, int32_t a, int32_t b);
+
+/* Global k-way refinement (Section 2.2, setup of Section 6): rounds of one k-way
+ * search from the whole boundary (init_mode 0) or the corner vertices (1) until a
+ * round finds no improvement or max_rounds ran. */
+int32_t fro_kway_global(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, int32_t *part, int32_t k, double eps, int32_t init_mode,
+                        int32_t alpha, int32_t max_rounds, uint64_t seed, fro_kway_result *out, int32_t *rounds);
 
 /* Quotient graph rounds: pair list (a < b, lexicographic) with the colour of each pair. */
 int32_t fro_rounds(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *part, int32_t k,
@@ -188,11 +254,13 @@ int32_t fro_refine_batch_mt(int32_t n, const int32_t *xadj, const int32_t *adjnc
 /* Active block scheduling with flow refinement of each scheduled pair (adaptive
  * flow iterations if opt->adaptive): outer rounds over the quotient edges with an
  * active end until no block is active or max_outer rounds ran.  Per-pair results in
- * processing order (round = matching index counted over all outer rounds). */
+ * processing order (round = matching index counted over all outer rounds).  With
+ * opt->mt_alpha > 0 a multi-try pass follows each matching; mt (optional) receives
+ * the totals of those passes. */
 int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                           const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                           const fro_options *opt, int32_t max_outer, int32_t cap, fro_pair_result *res,
-                          int32_t *npairs, int32_t *nouter);
+                          int32_t *npairs, int32_t *nouter, fro_mt_result *mt);
 
 /* Pair cut omega(E_ab) of the current partition. */
 int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,

@@ -713,7 +713,7 @@ int64_t fro_cut(fro_problem *p, int32_t mb, int32_t reps, uint64_t seed, int8_t 
  * start with the boundary vertices in random order; TopGain takes the block whose
  * best vertex has the larger gain (random tie), but the heavier block while a block
  * is overloaded; after the stopping rule the moves are rolled back to the best cut
- * found within the balance constraint.  Section 5 (setup) gives the stopping rule:
+ * found within the balance constraint.  Section 6 (setup) gives the stopping rule:
  * stop once more than a fraction of the pair's vertices moved without an
  * improvement.  Readings (also in the header): gains and the boundary are taken
  * within G[A u B]; a queue holds the unmoved vertices of its block with an edge to
@@ -875,12 +875,14 @@ int32_t fro_fm_pair(int32_t n, const int32_t *xadj, const int32_t *adjncy, const
 /* ------------------------------------- refinement of one pair (4.1) ------ */
 
 static int bad_fm(const fro_options *opt) { return opt && (opt->fm_permille < 0 || opt->fm_permille > 1000); }
+/* multi-try FM runs in active block scheduling only; elsewhere mt_alpha must be 0 */
+static int bad_mt(const fro_options *opt) { return opt && opt->mt_alpha != 0; }
 
 static int32_t check_pair_args(int32_t k, int32_t a, int32_t b, double eps, double alpha, const fro_options *opt) {
     if (k < 2 || a < 0 || b < 0 || a >= k || b >= k || a == b) return FRO_ERR_INVALID_ARG;
     if (!(eps > 0.0) || !(alpha >= 1.0)) return FRO_ERR_INVALID_ARG;
     if (opt && (opt->mb_reps < 0 || opt->max_iters < 0 || (opt->adaptive && !(opt->alpha_max >= 1.0)) ||
-                opt->fm_permille < 0 || opt->fm_permille > 1000))
+                opt->fm_permille < 0 || opt->fm_permille > 1000 || opt->mt_alpha != 0))
         return FRO_ERR_INVALID_ARG;
     return FRO_OK;
 }
@@ -901,7 +903,7 @@ static int32_t refine_pair_core(int32_t n, const int32_t *xadj, const int32_t *a
     for (int32_t v = 0; v < n; ++v) { if (part[v] == a) wA += vwgt[v]; else if (part[v] == b) wB += vwgt[v]; }
     res->cut_before = cut; res->wA_before = wA; res->wB_before = wB;
     if (opt && opt->fm_permille > 0) {
-        /* pairwise improvement: FM first, then the flows on its result (Section 5 setup) */
+        /* pairwise improvement: FM first, then the flows on its result (Section 6 setup) */
         fro_fm_result fr;
         fro_fm_pair(n, xadj, adjncy, adjwgt, vwgt, part, a, b, Lmax, opt->fm_permille, seed, &fr, NULL, 0);
         cut = fr.cut_after; wA = fr.wA_after; wB = fr.wB_after;
@@ -997,7 +999,7 @@ int32_t fro_refine_batch(int32_t n, const int32_t *xadj, const int32_t *adjncy, 
                          const fro_options *opt, int32_t cap, fro_pair_result *res, int32_t *npairs,
                          int32_t *nrounds) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || bad_fm(opt) || bad_mt(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
@@ -1025,7 +1027,7 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
                                 const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                                 const fro_options *opt, int32_t max_pairs, int32_t *done) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || bad_fm(opt) || bad_mt(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
@@ -1046,13 +1048,358 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
     return FRO_OK;
 }
 
+/* ---------------------- k-way local search (2.2) and multi-try FM (4.2) ---- */
+
+/* Section 2.2 (k-way local search): a single priority queue P over the vertices
+ * of a start set S, keyed by the max gain g(v) = max_P g_P(v) over the blocks P
+ * that v is adjacent to (g_P(v) = omega(v, P) - omega(v, own block)); the search
+ * takes the vertex of highest gain again and again and moves it to its best block
+ * unless that block would exceed L_max; each vertex moves at most once; it stops
+ * when P is empty or when the KaSPar rule finds a further improvement unlikely,
+ * and rolls back to the lowest cut it saw.  Section 4.2 (multi-try FM) starts such
+ * searches from single boundary vertices of a block pair.  Readings (also in
+ * fro.h) are given where each is used. */
+
+/* KaSPar stopping rule (Osipov & Sanders, as adopted in Section 2.2): over the p
+ * moves since the cut last reached a new minimum, with mean mu and population
+ * variance sigma^2 of their gains, stop once p mu^2 > alpha sigma^2 + beta.  Each
+ * operation is one rounded double operation, in this order (no contraction). */
+static int kaspar_stop(int32_t p, int64_t S1, int64_t S2, int32_t alpha, double beta) {
+    const double pd = (double)p;
+    const double mu = (double)S1 / pd;
+    const double var = (double)S2 / pd - mu * mu;
+    const double lhs = (pd * mu) * mu;
+    const double rhs = (double)alpha * var + beta;
+    return lhs > rhs;
+}
+
+int32_t fro_kaspar_stop(int32_t p, int64_t S1, int64_t S2, int32_t alpha, double beta) {
+    return p > 0 ? kaspar_stop(p, S1, S2, alpha, beta) : 0;
+}
+
+typedef struct {
+    fm_heap q;          /* keys (gain, stamp, v), larger first */
+    int32_t *tgt;       /* [n] target block of the vertex's current key */
+    int8_t *moved;      /* [n] moved by the current search */
+    int64_t *acc;       /* [k] connection weights of the vertex being keyed (zero between uses) */
+    int32_t *blk;       /* [k] blocks with acc != 0 */
+    int32_t *lv, *lfrom, *lto;   /* [n] moves of the current search: vertex, source, target */
+    int64_t *lg;        /* [n] gain of each move */
+} kway_ctx;
+
+static void kway_ctx_init(kway_ctx *C, int32_t n, int32_t k) {
+    C->q.h = XALLOC(fm_key, n);
+    C->q.n = 0;
+    C->q.pos = XALLOC(int32_t, n);
+    for (int32_t v = 0; v < n; ++v) C->q.pos[v] = -1;
+    C->tgt = XALLOC(int32_t, n);
+    C->moved = XALLOC(int8_t, n);
+    C->acc = XALLOC(int64_t, k);
+    C->blk = XALLOC(int32_t, k);
+    C->lv = XALLOC(int32_t, n);
+    C->lfrom = XALLOC(int32_t, n);
+    C->lto = XALLOC(int32_t, n);
+    C->lg = XALLOC(int64_t, n);
+}
+
+static void kway_ctx_free(kway_ctx *C) {
+    free(C->q.h); free(C->q.pos); free(C->tgt); free(C->moved); free(C->acc); free(C->blk);
+    free(C->lv); free(C->lfrom); free(C->lto); free(C->lg);
+}
+
+/* Max gain of u and its target block.  Target: the adjacent block other than u's
+ * own with the largest connection weight; equal weights go to the smaller
+ * splitmix64(tseed ^ u << 32 ^ P), then to the smaller P (the random tie).
+ * Returns 0 when u has no neighbour outside its block (not a boundary vertex). */
+static int kway_gain(const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *part,
+                     int32_t u, uint64_t tseed, kway_ctx *C, int64_t *gain, int32_t *to) {
+    int32_t nb = 0;
+    int64_t own = 0;
+    for (int32_t j = xadj[u]; j < xadj[u + 1]; ++j) {
+        const int32_t P = part[adjncy[j]];
+        if (P == part[u]) { own += adjwgt[j]; continue; }
+        if (C->acc[P] == 0) C->blk[nb++] = P;
+        C->acc[P] += adjwgt[j];
+    }
+    if (nb == 0) return 0;
+    int32_t best = -1;
+    int64_t bw = 0;
+    uint64_t bh = 0;
+    for (int32_t i = 0; i < nb; ++i) {
+        const int32_t P = C->blk[i];
+        const int64_t w = C->acc[P];
+        const uint64_t h = fro_splitmix64(tseed ^ ((uint64_t)(uint32_t)u << 32) ^ (uint64_t)(uint32_t)P);
+        if (best < 0 || w > bw || (w == bw && (h < bh || (h == bh && P < best)))) { best = P; bw = w; bh = h; }
+        C->acc[P] = 0;
+    }
+    *gain = bw - own;
+    *to = best;
+    return 1;
+}
+
+static int kway_boundary(const int32_t *xadj, const int32_t *adjncy, const int32_t *part, int32_t u) {
+    for (int32_t j = xadj[u]; j < xadj[u + 1]; ++j)
+        if (part[adjncy[j]] != part[u]) return 1;
+    return 0;
+}
+
+/* One k-way search from the start set init[0..ninit) (in that order).  Readings:
+ *   key      (gain, stamp), larger first; a stamp is taken per insertion or key
+ *            change, in the order they happen: the start set in its order, then
+ *            after each move the moved vertex's neighbours in CSR order
+ *   balance  v moves to its target P only if c(P) + c(v) <= L_max; otherwise it
+ *            leaves the queue unmoved (a later move of a neighbour keys it again)
+ *   update   after a move every unmoved neighbour the search may touch is keyed
+ *            again if it is a boundary vertex (queued if it was not) and leaves the
+ *            queue if it is not
+ *   stop     the KaSPar rule after every move that does not reach a new minimum
+ *            cut (p, S1, S2 restart at each new minimum), or an empty queue
+ *   rollback to the first prefix with the lowest cut (the empty prefix included)
+ *   touched  (multi-try) touched[v] = id of the search of the current pass that
+ *            queued v, 0 if none; a vertex queued by another search is neither
+ *            queued nor moved by this one.  touched = NULL: no such restriction. */
+static void kway_run(kway_ctx *C, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, int32_t *part, int64_t *blockw, int64_t Lmax, const int32_t *init,
+                     int32_t ninit, int32_t *touched, int32_t id, int32_t alpha, double beta, uint64_t tseed,
+                     fro_kway_result *out) {
+    uint64_t stamp = 0;
+    for (int32_t i = 0; i < ninit; ++i) {
+        const int32_t v = init[i];
+        if (C->q.pos[v] >= 0 || (touched && touched[v] != 0 && touched[v] != id)) continue;
+        int64_t g;
+        int32_t to;
+        if (!kway_gain(xadj, adjncy, adjwgt, part, v, tseed, C, &g, &to)) continue;
+        fm_key key = { g, stamp++, v };
+        C->tgt[v] = to;
+        fm_set(&C->q, key);
+        if (touched) touched[v] = id;
+    }
+    int64_t delta = 0, best = 0, S1 = 0, S2 = 0;
+    int32_t nm = 0, best_len = 0, p = 0, stop = 0;
+    while (C->q.n > 0) {
+        const fm_key top = C->q.h[0];
+        const int32_t v = top.v, to = C->tgt[v], from = part[v];
+        fm_remove(&C->q, v);
+        if (blockw[to] + vwgt[v] > Lmax) continue;   /* would overload the target: not moved */
+        part[v] = to;
+        blockw[from] -= vwgt[v];
+        blockw[to] += vwgt[v];
+        C->moved[v] = 1;
+        C->lv[nm] = v; C->lfrom[nm] = from; C->lto[nm] = to; C->lg[nm] = top.gain;
+        ++nm;
+        delta -= top.gain;
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            const int32_t u = adjncy[j];
+            if (C->moved[u] || (touched && touched[u] != 0 && touched[u] != id)) continue;
+            int64_t g;
+            int32_t t2;
+            if (kway_gain(xadj, adjncy, adjwgt, part, u, tseed, C, &g, &t2)) {
+                fm_key key = { g, stamp++, u };
+                C->tgt[u] = t2;
+                fm_set(&C->q, key);
+                if (touched) touched[u] = id;
+            } else {
+                fm_remove(&C->q, u);
+            }
+        }
+        if (delta < best) {
+            best = delta; best_len = nm; p = 0; S1 = 0; S2 = 0;
+        } else {
+            ++p;
+            S1 += top.gain;
+            S2 += top.gain * top.gain;
+            if (kaspar_stop(p, S1, S2, alpha, beta)) { stop = 1; break; }
+        }
+    }
+    for (int32_t i = nm - 1; i >= best_len; --i) {   /* roll back */
+        const int32_t v = C->lv[i], to = part[v];
+        part[v] = C->lfrom[i];
+        blockw[to] -= vwgt[v];
+        blockw[C->lfrom[i]] += vwgt[v];
+    }
+    for (int32_t i = 0; i < nm; ++i) C->moved[C->lv[i]] = 0;
+    for (int32_t i = 0; i < C->q.n; ++i) C->q.pos[C->q.h[i].v] = -1;
+    C->q.n = 0;
+    out->gain = -best;
+    out->tried = nm;
+    out->kept = best_len;
+    out->stop = stop;
+}
+
+int32_t fro_kway_search(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, int32_t *part, int32_t k, int64_t *blockw, int64_t Lmax,
+                        const int32_t *init, int32_t ninit, int32_t *touched, int32_t id, int32_t alpha,
+                        double beta, uint64_t tseed, fro_kway_result *out, int32_t *log_v, int32_t *log_to,
+                        int64_t *log_gain, int32_t log_cap) {
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || k < 2 || ninit < 0 || alpha < 0 || (touched && id < 1)) return FRO_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < ninit; ++i)
+        if (init[i] < 0 || init[i] >= n) return FRO_ERR_INVALID_ARG;
+    kway_ctx C;
+    kway_ctx_init(&C, n, k);
+    kway_run(&C, xadj, adjncy, adjwgt, vwgt, part, blockw, Lmax, init, ninit, touched, id, alpha, beta, tseed, out);
+    for (int32_t i = 0; i < out->tried && i < log_cap; ++i) {
+        if (log_v) log_v[i] = C.lv[i];
+        if (log_to) log_to[i] = C.lto[i];
+        if (log_gain) log_gain[i] = C.lg[i];
+    }
+    kway_ctx_free(&C);
+    return FRO_OK;
+}
+
+/* Seeds of the multi-try pass: the todo list of pair (a, b) is ordered by
+ * splitmix64(fro_mt_seed(seed, a, b) ^ v); target ties use splitmix64(~seed). */
+uint64_t fro_mt_seed(uint64_t seed, int32_t a, int32_t b) { return fro_splitmix64(fro_fm_seed(seed, a, b) + 1); }
+
+typedef struct { uint64_t key; int32_t v; } todo_item;
+
+static int cmp_todo(const void *pa, const void *pb) {
+    const todo_item *x = (const todo_item *)pa, *y = (const todo_item *)pb;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+/* Section 4.2 (multi-try FM) for the pairs (pa[i], pb[i]), i < np, of one matching,
+ * run after their pairwise improvements (Section 4.3).  Readings (also in fro.h):
+ *   todo     pair (a, b): its vertices with a neighbour in the other block, as the
+ *            pass starts, in a random order (ascending splitmix64 keys); the pairs'
+ *            lists are visited round-robin: entry 0 of every pair in pair order,
+ *            then entry 1, and so on (the pairs' improvements ran side by side)
+ *   search   a todo vertex starts a k-way search if no search of this pass has
+ *            queued it and it still has a neighbour in another block; the start
+ *            set is that vertex, then its neighbours (CSR order) that are boundary
+ *            vertices no search of the pass has queued
+ *   touched  a vertex queued by one search of the pass is never queued by another
+ *   beta     ln n, the natural logarithm of the graph's vertex count
+ * changed[x] (k entries, may be NULL) is set to 1 for the source and target block
+ * of every kept move. */
+int32_t fro_multitry(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, int32_t *part, int32_t k, int64_t Lmax, int32_t np, const int32_t *pa,
+                     const int32_t *pb, int32_t alpha, uint64_t seed, fro_mt_result *out, int8_t *changed) {
+    memset(out, 0, sizeof(*out));
+    if (np < 0 || alpha < 0) return FRO_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < np; ++i)
+        if (pa[i] < 0 || pb[i] < 0 || pa[i] >= k || pb[i] >= k || pa[i] == pb[i]) return FRO_ERR_INVALID_ARG;
+    const double beta = log((double)n);
+    const uint64_t tseed = fro_splitmix64(~seed);
+    int64_t *blockw = XALLOC(int64_t, k);
+    for (int32_t v = 0; v < n; ++v) blockw[part[v]] += vwgt[v];
+    /* the todo lists, fixed as the pass starts */
+    todo_item **todo = XALLOC(todo_item *, np);
+    int32_t *len = XALLOC(int32_t, np), maxlen = 0;
+    for (int32_t i = 0; i < np; ++i) {
+        const int32_t a = pa[i], b = pb[i];
+        const uint64_t ms = fro_mt_seed(seed, a, b);
+        todo[i] = XALLOC(todo_item, n);
+        for (int32_t v = 0; v < n; ++v) {
+            if (part[v] != a && part[v] != b) continue;
+            const int32_t other = part[v] == a ? b : a;
+            for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j)
+                if (part[adjncy[j]] == other) {
+                    todo[i][len[i]].key = fro_splitmix64(ms ^ (uint64_t)(uint32_t)v);
+                    todo[i][len[i]].v = v;
+                    ++len[i];
+                    break;
+                }
+        }
+        qsort(todo[i], (size_t)len[i], sizeof(todo_item), cmp_todo);
+        if (len[i] > maxlen) maxlen = len[i];
+    }
+    kway_ctx C;
+    kway_ctx_init(&C, n, k);
+    int32_t *touched = XALLOC(int32_t, n);
+    int32_t *init = XALLOC(int32_t, n);
+    int32_t id = 0;
+    for (int32_t j = 0; j < maxlen; ++j)
+        for (int32_t i = 0; i < np; ++i) {
+            if (j >= len[i]) continue;
+            const int32_t v = todo[i][j].v;
+            if (touched[v] || !kway_boundary(xadj, adjncy, part, v)) continue;
+            int32_t ni = 0;
+            init[ni++] = v;
+            for (int32_t q = xadj[v]; q < xadj[v + 1]; ++q) {
+                const int32_t u = adjncy[q];
+                if (!touched[u] && kway_boundary(xadj, adjncy, part, u)) init[ni++] = u;
+            }
+            fro_kway_result r;
+            kway_run(&C, xadj, adjncy, adjwgt, vwgt, part, blockw, Lmax, init, ni, touched, ++id, alpha, beta,
+                     tseed, &r);
+            out->searches += 1;
+            out->gain += r.gain;
+            out->tried += r.tried;
+            out->kept += r.kept;
+            if (changed)
+                for (int32_t q = 0; q < r.kept; ++q) changed[C.lfrom[q]] = changed[C.lto[q]] = 1;
+        }
+    for (int32_t i = 0; i < np; ++i) free(todo[i]);
+    free(todo); free(len); free(touched); free(init); free(blockw);
+    kway_ctx_free(&C);
+    return FRO_OK;
+}
+
+/* Section 2.2 with the setup of Section 6 ("Configuring the Algorithm"): rounds of
+ * one k-way search each, started from the complete partition boundary (init_mode 0)
+ * or from the corner vertices only (init_mode 1: vertices whose neighbourhood,
+ * with themselves, meets at least three blocks), in a random order (ascending
+ * splitmix64(splitmix64(seed ^ r) ^ v) in round r); the rounds stop after the first
+ * round without an improvement, or after max_rounds.  Sums of all rounds in out;
+ * *rounds = rounds run. */
+int32_t fro_kway_global(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, int32_t *part, int32_t k, double eps, int32_t init_mode,
+                        int32_t alpha, int32_t max_rounds, uint64_t seed, fro_kway_result *out, int32_t *rounds) {
+    memset(out, 0, sizeof(*out));
+    if (rounds) *rounds = 0;
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK && (!(eps > 0.0) || alpha < 0 || max_rounds < 1 || (init_mode != 0 && init_mode != 1)))
+        st = FRO_ERR_INVALID_ARG;
+    if (st != FRO_OK) return st;
+    const int64_t Lmax = fro_lmax(fro_total_weight(n, vwgt), fro_max_weight(n, vwgt), k, eps);
+    const double beta = log((double)n);
+    const uint64_t tseed = fro_splitmix64(~seed);
+    int64_t *blockw = XALLOC(int64_t, k);
+    for (int32_t v = 0; v < n; ++v) blockw[part[v]] += vwgt[v];
+    todo_item *S = XALLOC(todo_item, n);
+    int32_t *init = XALLOC(int32_t, n);
+    int8_t *seen = XALLOC(int8_t, k);
+    kway_ctx C;
+    kway_ctx_init(&C, n, k);
+    int32_t r = 0;
+    for (; r < max_rounds; ++r) {
+        const uint64_t rs = fro_splitmix64(seed ^ (uint64_t)(uint32_t)r);
+        int32_t ns = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            int32_t nb = 0;   /* blocks other than v's own around v */
+            for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+                const int32_t P = part[adjncy[j]];
+                if (P != part[v] && !seen[P]) { seen[P] = 1; ++nb; }
+            }
+            for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) seen[part[adjncy[j]]] = 0;
+            if (nb >= (init_mode == 1 ? 2 : 1)) { S[ns].key = fro_splitmix64(rs ^ (uint64_t)(uint32_t)v); S[ns].v = v; ++ns; }
+        }
+        qsort(S, (size_t)ns, sizeof(todo_item), cmp_todo);
+        for (int32_t i = 0; i < ns; ++i) init[i] = S[i].v;
+        fro_kway_result rr;
+        kway_run(&C, xadj, adjncy, adjwgt, vwgt, part, blockw, Lmax, init, ns, NULL, 0, alpha, beta, tseed, &rr);
+        out->gain += rr.gain;
+        out->tried += rr.tried;
+        out->kept += rr.kept;
+        out->stop = rr.stop;
+        if (rr.gain <= 0) { ++r; break; }
+    }
+    if (rounds) *rounds = r;
+    free(blockw); free(S); free(init); free(seen);
+    kway_ctx_free(&C);
+    return FRO_OK;
+}
+
 /* --------------------------------------- active block scheduling --------- */
 
 /* Section 4.3 (scheduling quotient graph refinement) and the appendix pseudocode
  * of active block scheduling, with the pairwise improvement restricted to the flow
  * refinement of Section 4.1, preceded by the two-way FM search when fm_permille
- * is set (the paper's pseudocode also runs multi-try FM searches, which this
- * oracle does not implement).  Every block starts active.  An outer round
+ * is set; with mt_alpha set, a multi-try FM pass (Section 4.2) started from the
+ * boundaries of a matching's pairs follows the pairwise improvements of that
+ * matching, and every block a kept multi-try move left or entered becomes active.  Every block starts active.  An outer round
  * takes the quotient edges (a, b) of the current partition with a or b active,
  * marks every block inactive, and refines those pairs; a pair whose refinement
  * changed the partition marks a and b active again.  The outer rounds end when no
@@ -1062,9 +1409,10 @@ int32_t fro_refine_batch_sample(int32_t n, const int32_t *xadj, const int32_t *a
 int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                           const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                           const fro_options *opt, int32_t max_outer, int32_t cap, fro_pair_result *res,
-                          int32_t *npairs, int32_t *nouter) {
+                          int32_t *npairs, int32_t *nouter, fro_mt_result *mt) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || max_outer < 1 || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || max_outer < 1 || bad_fm(opt) || (opt && opt->mt_alpha < 0)))
+        st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
@@ -1075,6 +1423,11 @@ int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy,
     int32_t maxp = k * (k - 1) / 2;
     int32_t *pa = XALLOC(int32_t, maxp), *pb = XALLOC(int32_t, maxp), *pr = XALLOC(int32_t, maxp);
     for (int32_t x = 0; x < k; ++x) active[x] = 1;
+    const int32_t mt_alpha = opt ? opt->mt_alpha : 0;
+    const uint64_t seed = opt ? opt->seed : 0;
+    int32_t *ma = XALLOC(int32_t, maxp), *mb_ = XALLOC(int32_t, maxp);
+    int8_t *changed = XALLOC(int8_t, k);
+    if (mt) memset(mt, 0, sizeof(*mt));
     int32_t out = 0, outer = 0, round_base = 0;
     for (; outer < max_outer; ++outer) {
         int32_t any = 0;
@@ -1101,7 +1454,7 @@ int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy,
                 if (c + 1 > nr) nr = c + 1;
             }
         for (int32_t x = 0; x < k; ++x) active[x] = 0;
-        for (int32_t r = 0; r < nr; ++r)
+        for (int32_t r = 0; r < nr; ++r) {
             for (int32_t i = 0; i < np; ++i) {
                 if (pr[i] != r) continue;
                 fro_pair_result tmp;
@@ -1112,9 +1465,25 @@ int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy,
                 if (out < cap) res[out] = tmp;
                 ++out;
             }
+            if (mt_alpha > 0) {
+                /* after the pairwise improvements of the matching: one multi-try pass
+                 * started from the boundaries of its pairs; every block a kept move
+                 * left or entered becomes active */
+                int32_t nm = 0;
+                for (int32_t i = 0; i < np; ++i)
+                    if (pr[i] == r) { ma[nm] = pa[i]; mb_[nm] = pb[i]; ++nm; }
+                memset(changed, 0, (size_t)k);
+                fro_mt_result m;
+                fro_multitry(n, xadj, adjncy, adjwgt, vwgt, part, k, Lmax, nm, ma, mb_, mt_alpha, seed, &m, changed);
+                for (int32_t x = 0; x < k; ++x) if (changed[x]) active[x] = 1;
+                if (mt) {
+                    mt->gain += m.gain; mt->searches += m.searches; mt->tried += m.tried; mt->kept += m.kept;
+                }
+            }
+        }
         round_base += nr;
     }
-    free(active); free(adj); free(used); free(pa); free(pb); free(pr);
+    free(active); free(adj); free(used); free(pa); free(pb); free(pr); free(ma); free(mb_); free(changed);
     if (npairs) *npairs = out;
     if (nouter) *nouter = outer;
     return FRO_OK;
@@ -1172,7 +1541,7 @@ int32_t fro_refine_batch_mt(int32_t n, const int32_t *xadj, const int32_t *adjnc
                             const fro_options *opt, int32_t nthreads, int32_t max_rounds, int32_t cap,
                             fro_pair_result *res, int32_t *npairs, int32_t *nrounds, int32_t *done) {
     int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
-    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || nthreads < 1 || bad_fm(opt))) st = FRO_ERR_INVALID_ARG;
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || nthreads < 1 || bad_fm(opt) || bad_mt(opt))) st = FRO_ERR_INVALID_ARG;
     if (st != FRO_OK) return st;
     int64_t W = fro_total_weight(n, vwgt);
     int64_t Lmax = fro_lmax(W, fro_max_weight(n, vwgt), k, eps);
