@@ -91,6 +91,12 @@ typedef struct fr_options {
                               paper's setup); 0 = no FM.  fr_refine_pair, fr_refine_batch and
                               fr_refine_active; needs a simple graph and every gain within
                               +-1023 (max weighted degree of the graph), else FR_ERR_TOO_LARGE */
+    int32_t mt_alpha;      /* > 0: fr_refine_active runs a multi-try FM pass (Section 4.2) after
+                              the pairwise improvements of every matching, its k-way searches
+                              stopped by the KaSPar rule p mu^2 > mt_alpha sigma^2 + ln n
+                              (Section 2.2; 10 in the paper's setup); blocks a kept move left or
+                              entered become active.  0: none.  Other entry points need 0;
+                              needs k <= 1024 and every gain within +-1023 */
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b);
@@ -125,7 +131,22 @@ typedef struct fr_batch_result {
     int64_t corridor_arcs;  /* sum of corridor arcs over all pairs */
     int64_t device_ns;      /* device time of the rounds (CUDA events) */
     int64_t flow_ns;        /* device time spent in the max-flow phase (in-kernel timers) */
+    int64_t mt_gain;        /* fr_refine_active with mt_alpha > 0: cut decrease of the multi-try
+                               passes (included in cut_after) */
+    int32_t mt_searches;    /* k-way searches they started */
+    int32_t mt_tried;       /* moves they made */
+    int32_t mt_kept;        /* moves kept after the rollbacks */
+    int32_t pad0;
 } fr_batch_result;
+
+/* Totals of one multi-try FM pass (fr_multitry). */
+typedef struct fr_mt_result {
+    int64_t gain;           /* cut decrease kept */
+    int32_t searches;       /* k-way searches started */
+    int32_t tried;          /* moves made */
+    int32_t kept;           /* moves kept after the rollbacks */
+    int32_t status;
+} fr_mt_result;
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -135,7 +156,8 @@ void fr_default_options(fr_options *opt);
 
 /* sizeof of the structs of this header, for bindings to check their layouts:
  * which = 0 fr_graph, 1 fr_options, 2 fr_pair_result, 3 fr_batch_result,
- * 4 fr_profile_info, 5 fr_server_config, 6 fr_request, 7 fr_response; -1 for
+ * 4 fr_profile_info, 5 fr_server_config, 6 fr_request, 7 fr_response,
+ * 8 fr_mt_result; -1 for
  * any other value.  Needs no device. */
 int32_t fr_struct_size(int32_t which);
 
@@ -216,9 +238,11 @@ fr_status fr_refine_batch(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t
                           const fr_options *opt, int32_t cap, fr_pair_result *results, fr_batch_result *summary);
 
 /* Active block scheduling (Section 4.3 and the appendix pseudocode of active block
- * scheduling) with the flow refinement of Section 4.1 as the pairwise step (the
- * paper's pairwise step also runs FM searches, which this library does not have).
- * Every block starts active; an outer round takes the quotient edges (a, b) of the
+ * scheduling) with the flow refinement of Section 4.1 as the pairwise step, preceded
+ * by the two-way FM search when opt->fm_permille > 0, and with a multi-try FM pass
+ * (fr_multitry) over each matching's pairs after their pairwise steps when
+ * opt->mt_alpha > 0 (every block a kept multi-try move left or entered becomes
+ * active; summary->mt_* receive its totals).  Every block starts active; an outer round takes the quotient edges (a, b) of the
  * current partition with a or b active, marks every block inactive, colours the
  * edges into matchings (lexicographic order, smallest colour free at both ends) and
  * refines the pairs matching by matching, each with adaptive flow iterations
@@ -232,6 +256,27 @@ fr_status fr_refine_batch(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t
 fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
                            const fr_options *opt, int32_t max_outer, int32_t cap, fr_pair_result *results,
                            fr_batch_result *summary, int32_t *nouter);
+
+/* One multi-try FM pass (Section 4.2) over the np block-disjoint pairs (pa[i], pb[i])
+ * (HOST arrays, pair order), as fr_refine_active runs it after a matching: each pair's
+ * vertices with a neighbour in the other block of the pair form its todo list, in the
+ * order of splitmix64(splitmix64(splitmix64(seed ^ a << 32 ^ b) + 1) ^ v); the lists
+ * are visited round-robin (entry j of every pair, then entry j + 1); a listed vertex
+ * that no earlier search of the pass queued and that still has a neighbour in another
+ * block starts a k-way local search (Section 2.2) from itself and its unqueued boundary
+ * neighbours (CSR order).  A search keeps one queue keyed by max gain (ties: the later
+ * keying first), moves the best vertex to its best adjacent block (ties: smaller
+ * splitmix64(splitmix64(~seed) ^ v << 32 ^ P), then smaller P) unless that block would
+ * exceed L_max = floor((1 + eps) c(V) / k) + max c(v), moves each vertex at most once,
+ * keys the unmoved neighbours of a moved vertex again, queues no vertex another search
+ * of the pass queued, stops when the queue is empty or p mu^2 > alpha sigma^2 + ln n
+ * over the gains of the p moves since the last new minimum cut (KaSPar), and rolls
+ * back to the first lowest cut.  part: DEVICE, updated in place (unchanged on error).
+ * changed (HOST, k entries, optional): 1 for every block a kept move left or entered.
+ * Needs alpha >= 0, k <= 1024 and every gain within +-1023 (FR_ERR_TOO_LARGE). */
+fr_status fr_multitry(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, int32_t np,
+                      const int32_t *pa, const int32_t *pb, int32_t alpha, uint64_t seed, fr_mt_result *out,
+                      int8_t *changed);
 
 /* Same as fr_refine_batch for a graph and partition in HOST memory: uploads the
  * arrays, refines, and copies part back (the end-to-end form; graph buffers are

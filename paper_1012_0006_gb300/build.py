@@ -29,7 +29,9 @@ CUDA_SOURCES = [
     "api.cu",
     "api_batch.cu",
     "api_active.cu",
+    "api_mt.cu",
     "fm_kernel.cu",
+    "mt_kernel.cu",
     "round_kernel.cu",
     "prep_kernel.cu",
     "serve.cu",

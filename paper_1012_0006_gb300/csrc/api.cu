@@ -419,6 +419,7 @@ extern "C" int32_t fr_struct_size(int32_t which) {
     case 5: return (int32_t)sizeof(fr_server_config);
     case 6: return (int32_t)sizeof(fr_request);
     case 7: return (int32_t)sizeof(fr_response);
+    case 8: return (int32_t)sizeof(fr_mt_result);
     default: return -1;
     }
 }
@@ -485,6 +486,7 @@ extern "C" fr_status fr_destroy(fr_ctx *ctx) {
     free_base(ctx);
     free_pairs(ctx);
     free_fm(ctx);
+    free_mt(ctx);
     if (ctx->reps_mem) cudaFree(ctx->reps_mem);
     if (ctx->hg_mem) cudaFree(ctx->hg_mem);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -550,6 +552,7 @@ fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *
             ctx_error(ctx, "fm_permille must be in [0, 1000]");
             return FR_ERR_INVALID_ARG;
         }
+        if (opt->mt_alpha < 0) { ctx_error(ctx, "mt_alpha must be >= 0"); return FR_ERR_INVALID_ARG; }
         if (opt->cluster_ctas != 0) {
             bool known = false;
             for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) known |= opt->cluster_ctas == fr_ctx::kClusterSizes[t];
@@ -769,6 +772,7 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
     if (res) memset(res, 0, sizeof(*res));
     fr_status st = check_graph(ctx, g, part, k);
     if (st == FR_OK) st = check_params(ctx, eps, alpha, &opt);
+    if (st == FR_OK && opt.mt_alpha != 0) { ctx_error(ctx, "mt_alpha: fr_refine_active only"); st = FR_ERR_INVALID_ARG; }
     if (st == FR_OK && (a < 0 || b < 0 || a >= k || b >= k || a == b)) {
         ctx_error(ctx, "pair (%d, %d) invalid for k=%d", a, b, k);
         st = FR_ERR_INVALID_ARG;

@@ -7,8 +7,10 @@
 // edges into matchings (lexicographic order, smallest colour free at both ends, as
 // for the sweep's rounds) and refines the pairs matching by matching; a pair whose
 // refinement changed the partition marks a and b active.  The run ends when no
-// block is active or after max_outer outer rounds.  Inside a matching every pair
-// runs its own adaptive loop; the pairs still iterating go through the round kernels
+// block is active or after max_outer outer rounds.  With mt_alpha > 0 a multi-try FM
+// pass (Section 4.2) over the matching's pairs follows their pairwise steps, and every
+// block one of its kept moves left or entered becomes active.  Inside a matching every
+// pair runs its own adaptive loop; the pairs still iterating go through the round kernels
 // together, each with its own corridor budget, so a step is one launch sequence for
 // all of them (the pairs are block-disjoint, so their iterations do not interact).
 #include <cuda_runtime.h>
@@ -167,6 +169,7 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
     release_corridor(ctx);
     st = ensure_base(ctx, g->n, g->nnz, k, opt.mb_reps);
     if (st == FR_OK && opt.fm_permille > 0) st = ensure_fm(ctx, g->n, g->nnz, k, k / 2 + 1);
+    if (st == FR_OK && opt.mt_alpha > 0) st = ensure_mt(ctx, g->n, g->nnz, k, k / 2 + 1);
     if (st != FR_OK) { if (summary) summary->status = st; return st; }
     CK(cudaMemcpyAsync(ctx->part_backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
     const int adaptive = opt.adaptive ? 1 : 0;
@@ -178,6 +181,9 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
     std::vector<unsigned int> qb(((size_t)k * k + 31) / 32);
     long long W = 0, Lmax = 0, cut0 = 0, dcut_total = 0, corridor_arcs = 0;
     int out_n = 0, rounds_total = 0, accepted_total = 0, outer = 0;
+    MtRes mt_tot;
+    memset(&mt_tot, 0, sizeof(mt_tot));
+    std::vector<int8_t> changed(k);
     for (; outer < max_outer && st == FR_OK; ++outer) {
         if (std::find(active.begin(), active.end(), 1) == active.end()) break;
         PrepOut po;
@@ -187,6 +193,11 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
             W = po.W;
             Lmax = host_lmax(W, po.maxc, k, eps);
             cut0 = po.totcut;
+            if (opt.mt_alpha > 0 && po.maxwdeg > kMtGmax) {
+                ctx_error(ctx, "multi-try: max weighted degree %d exceeds %d", po.maxwdeg, kMtGmax);
+                st = FR_ERR_TOO_LARGE;
+                break;
+            }
         }
         CK(cudaMemcpy(qb.data(), ctx->qbits, sizeof(unsigned int) * qb.size(), cudaMemcpyDeviceToHost));
         // the quotient edges with an active end, coloured into matchings
@@ -260,6 +271,21 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
                 }
             }
             if (st != FR_OK) break;
+            if (opt.mt_alpha > 0) {
+                // the multi-try pass from the boundaries of the matching's pairs
+                std::vector<int32_t> ma, mb;
+                for (const PairRun &q : run) { ma.push_back(q.a); mb.push_back(q.b); }
+                MtRes m;
+                st = run_mt_pass(ctx, g, part, k, ma.data(), mb.data(), (int)ma.size(), Lmax, opt.mt_alpha, opt.seed,
+                                 true, &m, changed.data());
+                if (st != FR_OK) break;
+                for (int x = 0; x < k; ++x)
+                    if (changed[x]) active[x] = 1;
+                mt_tot.gain += m.gain;
+                mt_tot.searches += m.searches;
+                mt_tot.tried += m.tried;
+                mt_tot.kept += m.kept;
+            }
             for (const PairRun &q : run) {
                 if (q.accepted || q.fm_moves > 0) active[q.a] = active[q.b] = 1;   // partition changed
                 accepted_total += q.accepted;
@@ -302,7 +328,11 @@ extern "C" fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *p
         summary->accepted = accepted_total;
         summary->status = FR_OK;
         summary->cut_before = cut0;
-        summary->cut_after = cut0 + dcut_total;
+        summary->cut_after = cut0 + dcut_total - mt_tot.gain;
+        summary->mt_gain = mt_tot.gain;
+        summary->mt_searches = mt_tot.searches;
+        summary->mt_tried = mt_tot.tried;
+        summary->mt_kept = mt_tot.kept;
         summary->corridor_arcs = corridor_arcs;
         summary->device_ns = (int64_t)((double)ms * 1e6);
     }

@@ -687,6 +687,7 @@ extern "C" fr_status fr_refine_batch(fr_ctx *ctx, const fr_graph *g, int32_t *pa
     if (summary) memset(summary, 0, sizeof(*summary));
     fr_status st = check_graph(ctx, g, part, k);
     if (st == FR_OK) st = check_params(ctx, eps, alpha, &opt);
+    if (st == FR_OK && opt.mt_alpha != 0) { ctx_error(ctx, "mt_alpha: fr_refine_active only"); st = FR_ERR_INVALID_ARG; }
     if (st == FR_OK && cap > 0 && !results) { ctx_error(ctx, "results is NULL"); st = FR_ERR_INVALID_ARG; }
     if (st != FR_OK) { if (summary) summary->status = st; return st; }
     if (opt.adaptive) {
@@ -757,6 +758,7 @@ extern "C" fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *
     if (base.mb_reps < 1) base.mb_reps = 1;
     fr_status st = check_graph(ctx, g, part, k);
     if (st == FR_OK) st = check_params(ctx, eps, alpha, &base);
+    if (st == FR_OK && base.mt_alpha != 0) { ctx_error(ctx, "mt_alpha: fr_refine_active only"); st = FR_ERR_INVALID_ARG; }
     if (st != FR_OK) return st;
     if (trials < 1) trials = 1;
     CK(cudaSetDevice(ctx->device));

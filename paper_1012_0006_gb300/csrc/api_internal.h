@@ -9,6 +9,7 @@
 #include "fr_internal.cuh"
 #include "round_kernel.cuh"
 #include "fm_kernel.cuh"
+#include "mt_kernel.cuh"
 
 constexpr int kMaxK = 1024;                 // blocks per partition (quotient graph in device bitmaps)
 constexpr size_t kHostStage = 8u << 20;     // pinned staging for small host<->device copies
@@ -95,6 +96,11 @@ struct fr_ctx {
     size_t fm_bytes = 0;
     int fm_n = 0, fm_nnz = 0, fm_k = 0, fm_p = 0;
     fr::FmDev fm = {};
+    // multi-try FM state (allocated on the first call with mt_alpha > 0)
+    void *mt_mem = nullptr;
+    size_t mt_bytes = 0;
+    int mt_n = 0, mt_nnz = 0, mt_k = 0, mt_p = 0;
+    fr::MtDev mt = {};
     // captured CUDA graphs of batch sweeps
     std::vector<GraphCacheEntry> gcache;
     bool use_graphs = true;
@@ -138,6 +144,16 @@ fr_status reset_idle(fr_ctx *ctx);
 // FM workspace for graphs up to n vertices / nnz arcs, k blocks and P pairs per call.
 fr_status ensure_fm(fr_ctx *ctx, int n, int nnz, int k, int P);
 void free_fm(fr_ctx *ctx);
+// Multi-try workspace for graphs up to n vertices / nnz arcs, k blocks, P pairs per pass.
+fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P);
+void free_mt(fr_ctx *ctx);
+// One multi-try pass over the pairs (pa[i], pb[i]) on part (a DEVICE array of g's
+// vertices) with block weight bound Lmax; ctx->blockw and the boundary candidate list
+// (if bl_on) are kept current.  changed (HOST, k entries, optional) receives the
+// blocks a kept move left or entered.
+fr_status run_mt_pass(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, const int32_t *pa, const int32_t *pb,
+                      int np, long long Lmax, int alpha, unsigned long long seed, bool bl_on, fr::MtRes *out,
+                      int8_t *changed);
 // The FM state of the pairs [p0, ...) of a call (results at res + p0).
 fr::FmDev fm_view(fr_ctx *ctx, int p0, const fr_options *opt);
 // Launches of one flow iteration over the pairs of w after the boundary scan:

@@ -1,0 +1,200 @@
+// C ABI, part 4: multi-try FM passes (Sanders & Schulz, Section 4.2; k-way local
+// search with the KaSPar stopping rule of Section 2.2): the workspace, one pass over
+// the pairs of a matching (used by fr_refine_active after each matching), and the
+// stand-alone entry point fr_multitry.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "api_internal.h"
+
+using namespace fr;
+
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+namespace {
+
+template <typename T>
+T *carve_mt(char *&p, long long count) {
+    T *r = reinterpret_cast<T *>(p);
+    p += ((sizeof(T) * (size_t)count + 255) / 256) * 256;
+    return r;
+}
+
+}  // namespace
+
+fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P) {
+    if (ctx->mt_mem && n <= ctx->mt_n && nnz <= ctx->mt_nnz && k <= ctx->mt_k && P <= ctx->mt_p) return FR_OK;
+    const long long nn = std::max(n, ctx->mt_n), mm = std::max(nnz, ctx->mt_nnz);
+    const int kk = std::max(k, ctx->mt_k), pp = std::max(P, ctx->mt_p);
+    // queue entries of one search: its start set (<= max degree + 1) plus one per arc of
+    // a moved vertex; todo lists: each padded to a power of two (< 2 x its length, 1 if empty)
+    const long long ecap = nn + mm + 64, scap = 2 * nn + pp;
+    if (ecap > INT_MAX) {
+        ctx_error(ctx, "multi-try: n + nnz exceeds the entry index range");
+        return FR_ERR_TOO_LARGE;
+    }
+    size_t b = 0;
+    auto add = [&](size_t elem, long long cnt) { b += ((elem * (size_t)cnt + 255) / 256) * 256; };
+    add(4, nn); add(4, nn); add(4, nn); add(1, nn);     // tch ver tgt mvd
+    add(4, nn); add(4, nn);                             // lv lfrom
+    add(4, ecap); add(4, ecap); add(4, ecap);           // ent_v ent_ver ent_below
+    add(4, kk);                                         // bpair
+    add(4, pp); add(4, pp); add(4, pp); add(4, pp);     // pa pb cnt fil
+    add(8, pp + 1);                                     // off
+    add(8, scap); add(4, scap);                         // tkey tv
+    add(8, kk); add(1, kk);                             // bw chg
+    add(sizeof(MtRes), 1);                              // res
+    if (ctx->arena_limit && b + ctx->base_bytes + ctx->pair_bytes + ctx->fm_bytes > ctx->arena_limit) {
+        ctx_error(ctx, "multi-try workspace of %zu bytes exceeds the arena bound", b);
+        return FR_ERR_OOM;
+    }
+    free_mt(ctx);
+    if (cudaMalloc(&ctx->mt_mem, b) != cudaSuccess) {
+        ctx->mt_mem = nullptr;
+        cudaGetLastError();
+        ctx_error(ctx, "cudaMalloc(%zu) for the multi-try workspace failed", b);
+        return FR_ERR_OOM;
+    }
+    ctx->mt_bytes = b;
+    ctx->mt_n = (int)nn; ctx->mt_nnz = (int)mm; ctx->mt_k = kk; ctx->mt_p = pp;
+    char *p = reinterpret_cast<char *>(ctx->mt_mem);
+    MtDev &m = ctx->mt;
+    m.tch = carve_mt<int>(p, nn); m.ver = carve_mt<int>(p, nn); m.tgt = carve_mt<int>(p, nn);
+    m.mvd = carve_mt<unsigned char>(p, nn);
+    m.lv = carve_mt<int>(p, nn); m.lfrom = carve_mt<int>(p, nn);
+    m.ent_v = carve_mt<int>(p, ecap); m.ent_ver = carve_mt<int>(p, ecap); m.ent_below = carve_mt<int>(p, ecap);
+    m.bpair = carve_mt<int>(p, kk);
+    m.pa = carve_mt<int>(p, pp); m.pb = carve_mt<int>(p, pp); m.cnt = carve_mt<int>(p, pp); m.fil = carve_mt<int>(p, pp);
+    m.off = carve_mt<long long>(p, pp + 1);
+    m.tkey = carve_mt<unsigned long long>(p, scap); m.tv = carve_mt<int>(p, scap);
+    m.bw = carve_mt<long long>(p, kk); m.chg = carve_mt<unsigned char>(p, kk);
+    m.res = carve_mt<MtRes>(p, 1);
+    m.ecap = ecap; m.scap = scap;
+    // versions start at zero; the moved marks are zero between searches
+    CK(cudaMemsetAsync(m.ver, 0, sizeof(int) * (size_t)nn, ctx->stream));
+    CK(cudaMemsetAsync(m.mvd, 0, (size_t)nn, ctx->stream));
+    return FR_OK;
+}
+
+void free_mt(fr_ctx *ctx) {
+    if (ctx->mt_mem) cudaFree(ctx->mt_mem);
+    ctx->mt_mem = nullptr;
+    ctx->mt_bytes = 0;
+    ctx->mt_n = ctx->mt_nnz = ctx->mt_k = ctx->mt_p = 0;
+    ctx->mt = MtDev{};
+}
+
+fr_status run_mt_pass(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, const int32_t *pa, const int32_t *pb,
+                      int np, long long Lmax, int alpha, unsigned long long seed, bool bl_on, MtRes *out,
+                      int8_t *changed) {
+    memset(out, 0, sizeof(*out));
+    if (np <= 0) return FR_OK;
+    if (k > kMtMaxK) {
+        ctx_error(ctx, "multi-try: k = %d exceeds %d", k, kMtMaxK);
+        return FR_ERR_TOO_LARGE;
+    }
+    fr_status st = ensure_mt(ctx, g->n, g->nnz, k, np);
+    if (st != FR_OK) return st;
+    MtDev md = ctx->mt;
+    // staging: pairs and the block -> pair map
+    int *h = reinterpret_cast<int *>(ctx->h_stage + 4096);
+    if (4096 + sizeof(int) * (size_t)(2 * np + k) > kHostStage / 2) {
+        ctx_error(ctx, "multi-try: %d pairs / k = %d exceed the staging buffer", np, k);
+        return FR_ERR_TOO_LARGE;
+    }
+    int *hb = h + 2 * np;
+    for (int x = 0; x < k; ++x) hb[x] = -1;
+    for (int i = 0; i < np; ++i) {
+        if (pa[i] < 0 || pb[i] < 0 || pa[i] >= k || pb[i] >= k || pa[i] == pb[i] || hb[pa[i]] >= 0 ||
+            hb[pb[i]] >= 0) {
+            ctx_error(ctx, "multi-try: pairs must be valid and block-disjoint");
+            return FR_ERR_INVALID_ARG;
+        }
+        h[i] = pa[i];
+        h[np + i] = pb[i];
+        hb[pa[i]] = hb[pb[i]] = i;
+    }
+    CK(cudaMemcpyAsync(md.pa, h, sizeof(int) * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(md.pb, h + np, sizeof(int) * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(md.bpair, hb, sizeof(int) * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), ctx->stream));
+    md.np = np;
+    md.alpha = alpha;
+    md.beta = std::log((double)g->n);
+    md.seed = seed;
+    GraphDev G;
+    memset(&G, 0, sizeof(G));
+    G.xadj = g->xadj; G.adjncy = g->adjncy; G.adjwgt = g->adjwgt; G.vwgt = g->vwgt;
+    G.part = part; G.blockw = ctx->blockw;
+    G.n = g->n; G.nnz = g->nnz; G.k = k; G.Lmax = Lmax;
+    if (bl_on) { G.bl = ctx->bl; G.blc = ctx->blc; G.inb = ctx->inb; }
+    int nl = 0;
+    CK(launch_mt(G, md, ctx->ctl, ctx->sms, ctx->stream, &nl));
+    ctx->last_launches += nl;
+    char *o = ctx->h_stage + kHostStage / 2;
+    Ctl *hc = reinterpret_cast<Ctl *>(o);
+    MtRes *hr = reinterpret_cast<MtRes *>(o + 1024);
+    unsigned char *hchg = reinterpret_cast<unsigned char *>(o + 2048);
+    CK(cudaMemcpyAsync(hc, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hr, md.res, sizeof(MtRes), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hchg, md.chg, (size_t)k, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    st = status_from_ctl(ctx, *hc, "multi-try pass");
+    if (st != FR_OK) {
+        reset_idle(ctx);
+        return st;
+    }
+    *out = *hr;
+    if (changed)
+        for (int x = 0; x < k; ++x) changed[x] = hchg[x] ? 1 : 0;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_multitry(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, int32_t np,
+                                 const int32_t *pa, const int32_t *pb, int32_t alpha, uint64_t seed,
+                                 fr_mt_result *out, int8_t *changed) {
+    if (!ctx) return FR_ERR_INVALID_ARG;
+    if (out) memset(out, 0, sizeof(*out));
+    fr_status st = check_graph(ctx, g, part, k);
+    if (st == FR_OK && (!(eps > 0.0) || !std::isfinite(eps) || alpha < 0 || np < 0 || (np > 0 && (!pa || !pb)))) {
+        ctx_error(ctx, "fr_multitry: eps > 0, alpha >= 0 and np pairs needed");
+        st = FR_ERR_INVALID_ARG;
+    }
+    if (st != FR_OK) { if (out) out->status = st; return st; }
+    CK(cudaSetDevice(ctx->device));
+    release_corridor(ctx);
+    ctx->last_launches = 0;
+    st = ensure_base(ctx, g->n, g->nnz, k, 1);
+    PrepOut po;
+    if (st == FR_OK) st = run_prep(ctx, g, part, k, false, false, &po);
+    if (st == FR_OK && po.maxwdeg > kMtGmax) {
+        ctx_error(ctx, "multi-try: max weighted degree %d exceeds %d", po.maxwdeg, kMtGmax);
+        st = FR_ERR_TOO_LARGE;
+    }
+    if (st != FR_OK) { if (out) out->status = st; return st; }
+    CK(cudaMemcpyAsync(ctx->part_backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
+    MtRes r;
+    st = run_mt_pass(ctx, g, part, k, pa, pb, np, host_lmax(po.W, po.maxc, k, eps), alpha, seed, true, &r, changed);
+    if (st != FR_OK) {
+        cudaMemcpyAsync(part, ctx->part_backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        if (out) out->status = st;
+        return st;
+    }
+    if (out) {
+        out->gain = r.gain;
+        out->searches = r.searches;
+        out->tried = r.tried;
+        out->kept = r.kept;
+        out->status = FR_OK;
+    }
+    return FR_OK;
+}

@@ -1,0 +1,471 @@
+// Multi-try FM after the pairwise improvements of a matching (Sanders & Schulz,
+// Section 4.2, run from active block scheduling as Section 4.3 describes): every
+// boundary vertex of a pair goes on the pair's todo list, the list is taken in a
+// random order, and each vertex that no earlier search of the pass touched and that
+// still lies on the boundary starts a k-way local search from itself and its boundary
+// neighbours; no search touches a vertex an earlier search of the pass touched.
+//
+// The k-way search is the one of Section 2.2: a single queue keyed by the max gain
+// g(v) = max_P omega(v, P) - omega(v, own block) over the blocks P next to v; the
+// best vertex moves to its best block unless that block would exceed L_max; each
+// vertex moves at most once; the search stops when the queue is empty or by the
+// KaSPar rule (over the p moves since the last new minimum, with mean mu and variance
+// sigma^2 of their gains: p mu^2 > alpha sigma^2 + beta, beta = ln n) and rolls back
+// to the first lowest cut.  Readings, as in the CPU oracle: keys order by gain, then
+// by the time of the vertex's last keying (later first): the start set in its order,
+// then after each move the moved vertex's neighbours in CSR order; target ties go to
+// the smaller splitmix64(tseed ^ u << 32 ^ P); a vertex that may not move leaves the
+// queue; after a move every unmoved neighbour the search may touch is keyed again if
+// it is a boundary vertex and leaves the queue if not; the pairs' todo lists are
+// visited round-robin (entry j of every pair in pair order, then entry j + 1).
+//
+// GPU form.  The searches of a pass are sequential by definition: each sees the
+// partition and the touched marks the earlier ones left.  So one warp runs the whole
+// pass (all lanes in lockstep; lane 0 pops and moves, the lanes key the moved
+// vertex's neighbours 32 at a time, each lane computing its neighbour's connection
+// weights from the adjacency in registers).  The queue is an array of gain buckets,
+// each a stack of (vertex, version) entries in global memory with its top and a
+// non-empty bitmap in shared memory: keying pushes an entry with the vertex's next
+// version (so each stack stays ordered by keying time) and makes the old one stale;
+// pops skip stale entries.  The block weights live in shared memory for the pass.
+// Grid-wide kernels before it count the pair boundaries and block weights, fill the
+// todo lists and sort each (one CTA per pair, bitonic by key).
+#include <climits>
+
+#include "mt_kernel.cuh"
+
+namespace fr {
+
+constexpr int kMtTPB = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Pair of the pass that v's block belongs to (and the partner block), if v has a
+// neighbour in the partner block; else -1.
+__device__ __forceinline__ int mt_pair_of(const GraphDev &G, const MtDev &m, int v, int *partner) {
+    const int x = G.part[v];
+    const int p = m.bpair[x];
+    if (p < 0) return -1;
+    const int other = m.pa[p] == x ? m.pb[p] : m.pa[p];
+    const int j1 = __ldg(G.xadj + v + 1);
+    for (int j = __ldg(G.xadj + v); j < j1; ++j)
+        if (G.part[__ldg(G.adjncy + j)] == other) {
+            *partner = other;
+            return p;
+        }
+    return -1;
+}
+
+__device__ __forceinline__ unsigned long long mt_list_seed(unsigned long long seed, int a, int b) {
+    return splitmix64(splitmix64(seed ^ ((unsigned long long)(unsigned)a << 32) ^ (unsigned)b) + 1);
+}
+
+// Block weights and the todo list length of every pair.
+__global__ void __launch_bounds__(kMtTPB) mt_count_kernel(GraphDev G, MtDev m) {
+    extern __shared__ long long s_bw[];   // [k]
+    for (int i = threadIdx.x; i < G.k; i += blockDim.x) s_bw[i] = 0;
+    __syncthreads();
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
+        const int c = __ldg(G.vwgt + v);
+        if (c) atomicAdd(reinterpret_cast<unsigned long long *>(s_bw + G.part[v]), (unsigned long long)c);
+        int partner;
+        const int p = mt_pair_of(G, m, v, &partner);
+        if (p >= 0) atomicAdd(m.cnt + p, 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < G.k; i += blockDim.x)
+        if (s_bw[i]) atomicAdd(reinterpret_cast<unsigned long long *>(m.bw + i), (unsigned long long)s_bw[i]);
+}
+
+// Todo list offsets, each list padded to a power of two for its sort.
+__global__ void mt_offsets_kernel(MtDev m, Ctl *ctl) {
+    if (threadIdx.x != 0) return;
+    long long o = 0;
+    for (int p = 0; p < m.np; ++p) {
+        m.off[p] = o;
+        long long q = 1;
+        while (q < m.cnt[p]) q <<= 1;
+        o += q;
+        m.fil[p] = 0;
+    }
+    m.off[m.np] = o;
+    if (o > m.scap) fail(ctl, E_INTERNAL, 801);
+}
+
+__global__ void __launch_bounds__(kMtTPB) mt_fill_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    if (__ldcg(&ctl->error)) return;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
+        int partner;
+        const int p = mt_pair_of(G, m, v, &partner);
+        if (p < 0) continue;
+        const int pos = atomicAdd(m.fil + p, 1);
+        if (pos >= m.cnt[p]) {   // cannot happen: the count pass saw the same partition
+            fail(ctl, E_INTERNAL, 802);
+            return;
+        }
+        const long long i = m.off[p] + pos;
+        m.tv[i] = v;
+        m.tkey[i] = splitmix64(mt_list_seed(m.seed, m.pa[p], m.pb[p]) ^ (unsigned long long)(unsigned)v);
+    }
+}
+
+// One CTA per pair: its todo list ascending by (key, vertex), bitonic in global memory.
+__global__ void __launch_bounds__(kMtTPB) mt_sort_kernel(MtDev m, Ctl *ctl) {
+    if (__ldcg(&ctl->error)) return;
+    const int p = blockIdx.x;
+    const long long o = m.off[p], len = m.off[p + 1] - o;
+    const int c = m.cnt[p];
+    unsigned long long *K = m.tkey + o;
+    int *V = m.tv + o;
+    for (long long i = c + threadIdx.x; i < len; i += blockDim.x) {
+        K[i] = ~0ull;
+        V[i] = INT_MAX;
+    }
+    __syncthreads();
+    for (long long kk = 2; kk <= len; kk <<= 1)
+        for (long long j = kk >> 1; j > 0; j >>= 1) {
+            for (long long i = threadIdx.x; i < len; i += blockDim.x) {
+                const long long l = i ^ j;
+                if (l <= i) continue;
+                const unsigned long long ki = K[i], kl = K[l];
+                const int vi = V[i], vl = V[l];
+                const bool l_less = kl < ki || (kl == ki && vl < vi);
+                const bool i_less = ki < kl || (ki == kl && vi < vl);
+                if ((i & kk) == 0 ? l_less : i_less) {
+                    K[i] = kl; K[l] = ki;
+                    V[i] = vl; V[l] = vi;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// ---------------------------------------------------------------- the pass ----
+
+// Max gain of u and its target: the adjacent block other than u's own with the largest
+// connection weight, ties to the smaller splitmix64(tseed ^ u << 32 ^ P), then the
+// smaller P.  False if u has no neighbour outside its block.  Up to 8 blocks around u
+// are summed in registers; more fall back to summing each block over the adjacency.
+__device__ bool mt_gain(const GraphDev &G, int u, unsigned long long tseed, int &gain, int &to) {
+    constexpr int T = 8;
+    const int pu = G.part[u];
+    const int j0 = __ldg(G.xadj + u), j1 = __ldg(G.xadj + u + 1);
+    int tb[T], tw[T];
+#pragma unroll
+    for (int s = 0; s < T; ++s) { tb[s] = -1; tw[s] = 0; }
+    int own = 0, nt = 0;
+    bool over = false;
+    for (int j = j0; j < j1; ++j) {
+        const int P = G.part[__ldg(G.adjncy + j)];
+        const int w = __ldg(G.adjwgt + j);
+        if (P == pu) { own += w; continue; }
+        bool hit = false;
+#pragma unroll
+        for (int s = 0; s < T; ++s)
+            if (tb[s] == P) { tw[s] += w; hit = true; }
+        if (!hit) {
+            if (nt < T) {
+#pragma unroll
+                for (int s = 0; s < T; ++s)
+                    if (s == nt) { tb[s] = P; tw[s] = w; }
+                ++nt;
+            } else {
+                over = true;
+            }
+        }
+    }
+    if (nt == 0) return false;
+    const unsigned long long hu = tseed ^ ((unsigned long long)(unsigned)u << 32);
+    int best = -1, bw = 0;
+    unsigned long long bh = 0;
+    auto consider = [&](int P, int w) {
+        const unsigned long long h = splitmix64(hu ^ (unsigned)P);
+        if (best < 0 || w > bw || (w == bw && (h < bh || (h == bh && P < best)))) { best = P; bw = w; bh = h; }
+    };
+    if (!over) {
+#pragma unroll
+        for (int s = 0; s < T; ++s)
+            if (s < nt) consider(tb[s], tw[s]);
+    } else {
+        for (int j = j0; j < j1; ++j) {
+            const int P = G.part[__ldg(G.adjncy + j)];
+            if (P == pu) continue;
+            bool first = true;
+            for (int q = j0; q < j && first; ++q) first = G.part[__ldg(G.adjncy + q)] != P;
+            if (!first) continue;
+            int wsum = 0;
+            for (int q = j; q < j1; ++q)
+                if (G.part[__ldg(G.adjncy + q)] == P) wsum += __ldg(G.adjwgt + q);
+            consider(P, wsum);
+        }
+    }
+    gain = bw - own;
+    to = best;
+    return true;
+}
+
+// KaSPar rule in the oracle's order of rounded double operations.
+__device__ __forceinline__ bool kaspar_stop(int p, long long S1, long long S2, int alpha, double beta) {
+    const double pd = (double)p;
+    const double mu = __ddiv_rn((double)S1, pd);
+    const double var = __dsub_rn(__ddiv_rn((double)S2, pd), __dmul_rn(mu, mu));
+    const double lhs = __dmul_rn(__dmul_rn(pd, mu), mu);
+    const double rhs = __dadd_rn(__dmul_rn((double)alpha, var), beta);
+    return lhs > rhs;
+}
+
+__device__ __forceinline__ unsigned mt_lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+struct MtShared {
+    int top[kMtBuckets];               // top entry of each gain bucket, -1 empty
+    unsigned bits[kMtBuckets / 32];    // non-empty buckets (possibly holding only stale entries)
+    long long bw[kMtMaxK];             // block weights during the pass
+};
+
+// Pushes the lanes' entries (in lane order) onto their buckets: entries go to
+// [nxt, nxt + popc(pm)); a lower lane's entry lies below a higher lane's in one bucket.
+__device__ __forceinline__ void mt_push(MtShared &S, const MtDev &m, unsigned pm, bool push, int bk, int u, int nv,
+                                        long long nxt, int lane) {
+    const long long pos = nxt + __popc(pm & mt_lanemask_lt());
+    const unsigned grp = __match_any_sync(kFull, push ? bk : -1 - lane);
+    const unsigned lower = grp & mt_lanemask_lt();
+    const long long pos_lower = __shfl_sync(kFull, pos, lower ? 31 - __clz(lower) : lane);
+    int below = -1;
+    if (push) below = lower ? (int)pos_lower : S.top[bk];
+    __syncwarp();
+    if (push) {
+        m.ent_v[pos] = u;
+        m.ent_ver[pos] = nv;
+        m.ent_below[pos] = below;
+        if ((grp & ~lower & ~(1u << lane)) == 0) {   // highest lane of its bucket
+            S.top[bk] = (int)pos;
+            atomicOr(&S.bits[bk >> 5], 1u << (bk & 31));
+        }
+    }
+    __syncwarp();
+}
+
+// The whole pass: one warp.
+__global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    __shared__ MtShared S;
+    const int lane = threadIdx.x;
+    if (__ldcg(&ctl->error)) return;
+    if (G.k > kMtMaxK) {
+        if (lane == 0) fail(ctl, E_TOO_LARGE, 803);
+        return;
+    }
+    for (int i = lane; i < G.k; i += 32) S.bw[i] = m.bw[i];
+    const unsigned long long tseed = splitmix64(~m.seed);
+    const long long Lmax = G.Lmax;
+    int maxlen = 0;
+    for (int p = 0; p < m.np; ++p) maxlen = max(maxlen, m.cnt[p]);
+    long long gain_tot = 0;
+    int searches = 0, tried_tot = 0, kept_tot = 0, sid = 0;
+    bool bad = false;
+    __syncwarp();
+    for (int j = 0; j < maxlen && !bad; ++j)
+        for (int p = 0; p < m.np && !bad; ++p) {
+            if (j >= m.cnt[p]) continue;
+            const int v = m.tv[m.off[p] + j];
+            if (m.tch[v] != 0) continue;
+            const int pv = G.part[v];
+            const int x0 = __ldg(G.xadj + v), x1 = __ldg(G.xadj + v + 1);
+            bool bnd = false;
+            for (int jb = x0; jb < x1 && !bnd; jb += 32) {
+                const int jj = jb + lane;
+                bnd = __any_sync(kFull, jj < x1 && G.part[__ldg(G.adjncy + jj)] != pv);
+            }
+            if (!bnd) continue;
+            ++sid;
+            // ---- one k-way search ----
+            for (int i = lane; i < kMtBuckets; i += 32) S.top[i] = -1;
+            for (int i = lane; i < kMtBuckets / 32; i += 32) S.bits[i] = 0;
+            __syncwarp();
+            long long nxt = 0;
+            // start set: v, then its neighbours in CSR order that no search of the pass
+            // queued and that are boundary vertices (all chosen before any is queued)
+            const int deg = x1 - x0;
+            for (int base = -1; base < deg && !bad; base += 32) {
+                const int i = base + lane;
+                int u = -1;
+                if (i < 0) u = v;
+                else if (i < deg) u = __ldg(G.adjncy + x0 + i);
+                int g = 0, t = -1;
+                bool push = false;
+                if (u >= 0 && (u == v || m.tch[u] == 0)) push = mt_gain(G, u, tseed, g, t);
+                const bool range = __all_sync(kFull, !push || (g >= -kMtGmax && g <= kMtGmax));
+                const unsigned pm = __ballot_sync(kFull, push);
+                if (!range || nxt + __popc(pm) > m.ecap) {
+                    if (lane == 0) fail(ctl, range ? E_INTERNAL : E_TOO_LARGE, 804);
+                    bad = true;
+                    break;
+                }
+                int nv = 0;
+                if (push) {
+                    nv = m.ver[u] + 1;
+                    m.ver[u] = nv;
+                    m.tgt[u] = t;
+                    m.tch[u] = sid;
+                }
+                mt_push(S, m, pm, push, g + kMtGmax, u, nv, nxt, lane);
+                nxt += __popc(pm);
+            }
+            long long delta = 0, best = 0, S1 = 0, S2 = 0;
+            int nm = 0, best_len = 0, pc = 0;
+            while (!bad) {
+                // pop the highest current entry
+                int x = -1, g = 0;
+                for (;;) {
+                    int hb = -1;
+                    for (int k2 = 1; k2 >= 0; --k2) {
+                        const unsigned word = S.bits[lane * 2 + k2];
+                        if (hb < 0 && word) hb = (lane * 2 + k2) * 32 + 31 - __clz(word);
+                    }
+                    const unsigned has = __ballot_sync(kFull, hb >= 0);
+                    if (!has) break;
+                    const int b = __shfl_sync(kFull, hb, 31 - __clz(has));
+                    int got = -1;
+                    if (lane == 0) {
+                        const int e = S.top[b];
+                        if (e < 0 || e >= nxt) {   // (never: a set bit has a pushed top entry)
+                            S.top[b] = -1;
+                            S.bits[b >> 5] &= ~(1u << (b & 31));
+                        } else {
+                            const int xv = m.ent_v[e], below = m.ent_below[e];
+                            S.top[b] = below;
+                            if (below < 0) S.bits[b >> 5] &= ~(1u << (b & 31));
+                            if (m.ent_ver[e] == m.ver[xv]) {   // current: it leaves the queue
+                                got = xv;
+                                m.ver[xv] = m.ver[xv] + 1;
+                            }
+                        }
+                    }
+                    got = __shfl_sync(kFull, got, 0);
+                    __syncwarp();
+                    if (got >= 0) { x = got; g = b - kMtGmax; break; }
+                }
+                if (x < 0) break;   // the queue is empty
+                const int to = m.tgt[x];
+                const int from = G.part[x];
+                const long long cx = __ldg(G.vwgt + x);
+                if (S.bw[to] + cx > Lmax) continue;   // would overload the target: not moved
+                if (lane == 0) {
+                    G.part[x] = to;
+                    S.bw[from] -= cx;
+                    S.bw[to] += cx;
+                    m.mvd[x] = 1;
+                    m.lv[nm] = x;
+                    m.lfrom[nm] = from;
+                }
+                ++nm;
+                delta -= g;
+                __syncwarp();
+                // key the neighbours again, 32 at a time in CSR order
+                const int y0 = __ldg(G.xadj + x), y1 = __ldg(G.xadj + x + 1);
+                for (int jb = y0; jb < y1; jb += 32) {
+                    const int jj = jb + lane;
+                    const int u = jj < y1 ? __ldg(G.adjncy + jj) : -1;
+                    bool elig = false, push = false;
+                    int gu = 0, tu = -1;
+                    if (u >= 0 && !m.mvd[u]) {
+                        const int tc = m.tch[u];
+                        elig = tc == 0 || tc == sid;
+                        if (elig) push = mt_gain(G, u, tseed, gu, tu);
+                    }
+                    const bool range = __all_sync(kFull, !push || (gu >= -kMtGmax && gu <= kMtGmax));
+                    const unsigned pm = __ballot_sync(kFull, push);
+                    if (!range || nxt + __popc(pm) > m.ecap) {
+                        if (lane == 0) fail(ctl, range ? E_INTERNAL : E_TOO_LARGE, 805);
+                        bad = true;
+                        break;
+                    }
+                    int nv = 0;
+                    if (elig) {   // its old entry (if any) is stale from here on
+                        nv = m.ver[u] + 1;
+                        m.ver[u] = nv;
+                    }
+                    if (push) {
+                        m.tgt[u] = tu;
+                        m.tch[u] = sid;
+                    }
+                    mt_push(S, m, pm, push, gu + kMtGmax, u, nv, nxt, lane);
+                    nxt += __popc(pm);
+                }
+                if (bad) break;
+                if (delta < best) {
+                    best = delta; best_len = nm; pc = 0; S1 = 0; S2 = 0;
+                } else {
+                    ++pc;
+                    S1 += g;
+                    S2 += (long long)g * g;
+                    if (kaspar_stop(pc, S1, S2, m.alpha, m.beta)) break;
+                }
+            }
+            __syncwarp();
+            // roll back to the first lowest cut; clear the moved marks
+            for (int i = best_len + lane; i < nm; i += 32) {
+                const int y = m.lv[i], f0 = m.lfrom[i], t = G.part[y];
+                const long long cy = __ldg(G.vwgt + y);
+                G.part[y] = f0;
+                atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[t]), (unsigned long long)(-cy));
+                atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[f0]), (unsigned long long)cy);
+            }
+            __syncwarp();
+            for (int i = lane; i < nm; i += 32) m.mvd[m.lv[i]] = 0;
+            // kept moves: changed blocks and boundary candidates (the moved vertex and its
+            // neighbours outside its new block, as a flow's commit does)
+            for (int i = lane; i < best_len; i += 32) {
+                const int y = m.lv[i], t = G.part[y];
+                m.chg[m.lfrom[i]] = 1;
+                m.chg[t] = 1;
+                if (G.bl) {
+                    if (!__ldcg(G.inb + y) && atomicExch(G.inb + y, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = y;
+                    const int z1 = __ldg(G.xadj + y + 1);
+                    for (int q = __ldg(G.xadj + y); q < z1; ++q) {
+                        const int z = __ldg(G.adjncy + q);
+                        if (__ldcg(G.inb + z) || G.part[z] == t) continue;
+                        if (atomicExch(G.inb + z, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = z;
+                    }
+                }
+            }
+            __syncwarp();
+            gain_tot -= best;
+            tried_tot += nm;
+            kept_tot += best_len;
+            ++searches;
+        }
+    __syncwarp();
+    for (int i = lane; i < G.k; i += 32) {
+        m.bw[i] = S.bw[i];
+        G.blockw[i] = S.bw[i];
+    }
+    if (lane == 0) {
+        m.res->gain = gain_tot;
+        m.res->searches = searches;
+        m.res->tried = tried_tot;
+        m.res->kept = kept_tot;
+    }
+}
+
+cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cudaStream_t st, int *nl) {
+    if (md.np <= 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(md.tch, 0, sizeof(int) * (size_t)G.n, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.cnt, 0, sizeof(int) * (size_t)md.np, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.bw, 0, sizeof(long long) * (size_t)G.k, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.chg, 0, (size_t)G.k, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.res, 0, sizeof(MtRes), st)) != cudaSuccess) return e;
+    const int grid = 4 * (sms > 0 ? sms : 1);
+    mt_count_kernel<<<grid, kMtTPB, sizeof(long long) * (size_t)G.k, st>>>(G, md);
+    mt_offsets_kernel<<<1, 32, 0, st>>>(md, ctl);
+    mt_fill_kernel<<<grid, kMtTPB, 0, st>>>(G, md, ctl);
+    mt_sort_kernel<<<md.np, kMtTPB, 0, st>>>(md, ctl);
+    mt_pass_kernel<<<1, 32, 0, st>>>(G, md, ctl);
+    *nl += 5;
+    return cudaGetLastError();
+}
+
+}  // namespace fr

@@ -1,0 +1,53 @@
+// Multi-try FM (k-way local searches with the KaSPar stopping rule) after the pairwise
+// improvements of a matching: device state and launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fr_internal.cuh"
+
+namespace fr {
+
+constexpr int kMtGmax = 1023;                 // |gain| bound (max weighted degree)
+constexpr int kMtBuckets = 2 * kMtGmax + 2;   // gain buckets of the single queue
+constexpr int kMtMaxK = 1024;                 // block weights cached in shared memory
+
+// Totals of one pass.
+struct MtRes {
+    long long gain;          // cut decrease kept
+    int searches, tried, kept;
+    int pad;
+};
+
+// Device state of a multi-try pass over the pairs of one matching of one graph.
+// Per-vertex arrays: tch is cleared before every pass (by the launcher); ver only
+// grows; mvd is zero between searches.
+struct MtDev {
+    int *tch;                    // [n] search of this pass that queued the vertex, 0 = none
+    int *ver;                    // [n] key version: a queue entry is current iff it matches
+    int *tgt;                    // [n] target block of the vertex's current key
+    unsigned char *mvd;          // [n] moved by the current search
+    int *lv, *lfrom;             // [n] moves of the current search: vertex, source block
+    int *ent_v, *ent_ver, *ent_below;   // [ecap] bucket stack entries of the current search
+    int *bpair;                  // [k] pair of the pass that the block belongs to, -1 none
+    int *pa, *pb;                // [P] the pairs, in pass order
+    int *cnt, *fil;              // [P] todo list lengths, fill cursors
+    long long *off;              // [P + 1] todo list offsets (each padded to a power of two)
+    unsigned long long *tkey;    // [scap] todo sort keys
+    int *tv;                     // [scap] todo vertices
+    long long *bw;               // [k] block weights, accumulated as the pass starts
+    unsigned char *chg;          // [k] blocks a kept move left or entered
+    MtRes *res;
+    long long ecap, scap;
+    int np, alpha;
+    double beta;                 // ln n
+    unsigned long long seed;     // option seed: todo orders and target ties derive from it
+};
+
+// Enqueues one multi-try pass over the md.np pairs already in md.pa / md.pb (md.bpair
+// set): boundary counts and block weights, todo lists, their sort, and the searches.
+// G is the graph as the pairwise step leaves it; the pass updates part, blockw and the
+// boundary candidate list.  *nl += kernels launched.
+cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cudaStream_t st, int *nl);
+
+}  // namespace fr

@@ -215,8 +215,8 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
     if (!g || !part || g->n < 1 || g->nnz < 0 || !g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->adjwgt)) ||
         k < 2 || a < 0 || b < 0 || a >= k || b >= k || a == b || !(eps > 0.0) || !std::isfinite(eps) ||
         !(alpha >= 1.0) || !std::isfinite(alpha) || opt.mb_reps < 0 || opt.max_iters < 0 ||
-        (opt.adaptive && !(opt.alpha_max >= 1.0)) || opt.fm_permille != 0)
-        st = FR_ERR_INVALID_ARG;   // (the FM step needs the context's workspace: fr_refine_pair)
+        (opt.adaptive && !(opt.alpha_max >= 1.0)) || opt.fm_permille != 0 || opt.mt_alpha != 0)
+        st = FR_ERR_INVALID_ARG;   // (FM steps need the context's workspace: fr_refine_pair)
     else if (g->n > kNaMaxN || g->nnz > kNaMaxNNZ || k > kNaMaxK || opt.mb_reps > kNaMaxReps)
         st = FR_ERR_TOO_LARGE;   // beyond the fixed scratch: use fr_refine_pair
     if (st != FR_OK) {

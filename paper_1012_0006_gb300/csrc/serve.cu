@@ -356,7 +356,7 @@ static void server_loop(fr_server *S) {
 }
 
 extern "C" fr_status fr_server_create(fr_server **out, const fr_server_config *cfg) {
-    if (!out || !cfg || cfg->max_inflight < 1 || cfg->opt.fm_permille != 0) return FR_ERR_INVALID_ARG;
+    if (!out || !cfg || cfg->max_inflight < 1 || cfg->opt.fm_permille != 0 || cfg->opt.mt_alpha != 0) return FR_ERR_INVALID_ARG;
     *out = nullptr;
     fr_server *S = new fr_server();
     S->cfg = *cfg;

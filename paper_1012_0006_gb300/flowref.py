@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
                 ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
-                ("pre_waves", ctypes.c_int32), ("fm_permille", ctypes.c_int32)]
+                ("pre_waves", ctypes.c_int32), ("fm_permille", ctypes.c_int32), ("mt_alpha", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -58,7 +58,17 @@ class PairResult(ctypes.Structure):
 class BatchResult(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int32), ("nrounds", ctypes.c_int32), ("accepted", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64),
-                ("corridor_arcs", ctypes.c_int64), ("device_ns", ctypes.c_int64), ("flow_ns", ctypes.c_int64)]
+                ("corridor_arcs", ctypes.c_int64), ("device_ns", ctypes.c_int64), ("flow_ns", ctypes.c_int64),
+                ("mt_gain", ctypes.c_int64), ("mt_searches", ctypes.c_int32), ("mt_tried", ctypes.c_int32),
+                ("mt_kept", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+
+
+class MtResult(ctypes.Structure):
+    _fields_ = [("gain", ctypes.c_int64), ("searches", ctypes.c_int32), ("tried", ctypes.c_int32),
+                ("kept", ctypes.c_int32), ("status", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -139,6 +149,8 @@ SYMBOLS = {
                                         ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(PairResult), ctypes.POINTER(BatchResult),
                                         ctypes.POINTER(ctypes.c_int32)]),
+    "fr_multitry": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                   i32p, i32p, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(MtResult), i8p]),
     "fr_refine_batch_host": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_int32,
                                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
                                             ctypes.c_int32, ctypes.POINTER(PairResult),
@@ -374,6 +386,21 @@ class Context:
             self._check(st)
         pairs = [res[i].as_dict() for i in range(min(summ.npairs, cap))]
         return st, pairs, summ.as_dict(), nouter.value
+
+    def multitry(self, g: DeviceGraph, part, k, eps, pairs, alpha, seed=0, check=True):
+        """One multi-try FM pass over block-disjoint pairs (fr_multitry); returns
+        (status, totals, changed-block flags)."""
+        pa = np.ascontiguousarray([p[0] for p in pairs], np.int32)
+        pb = np.ascontiguousarray([p[1] for p in pairs], np.int32)
+        out = MtResult()
+        changed = np.zeros(k, np.int8)
+        gc = g.c()
+        st = lib().fr_multitry(self.h, ctypes.byref(gc), _ptr(part), k, eps, len(pairs), pa.ctypes.data_as(i32p),
+                               pb.ctypes.data_as(i32p), alpha, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(out),
+                               changed.ctypes.data_as(i8p))
+        if check:
+            self._check(st)
+        return st, out.as_dict(), changed.astype(bool)
 
     def refine_batch_host(self, xadj, adjncy, adjwgt, vwgt, part, k, eps, alpha, opts=None, cap=0):
         """Host-buffer form: arrays are numpy or (pinned) CPU tensors; part is updated in place."""

@@ -60,6 +60,7 @@ def test_missing_library_is_an_error(built, monkeypatch):
 def test_default_options(built):
     o = built.default_options()
     assert (o.mb, o.mb_reps, o.adaptive, o.max_iters, o.alpha_max, o.pulse_cap) == (0, 1, 0, 10, 1.0, 1 << 20)
+    assert (o.fm_permille, o.mt_alpha) == (0, 0)
 
 
 def test_status_strings(built):
@@ -71,7 +72,7 @@ def test_struct_layouts_match_the_header(built):
     """The binding's ctypes structs have the sizes the compiled library uses."""
     F = built
     structs = [F.Graph, F.Options, F.PairResult, F.BatchResult, F.ProfileInfo, F.ServerConfig, F.Request,
-               F.Response]
+               F.Response, F.MtResult]
     for i, st in enumerate(structs):
         assert F.lib().fr_struct_size(i) == ctypes.sizeof(st), st.__name__
     assert F.lib().fr_struct_size(len(structs)) == -1
