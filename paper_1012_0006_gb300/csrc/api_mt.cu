@@ -102,6 +102,7 @@ fr_status run_mt_pass(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, 
         return FR_ERR_TOO_LARGE;
     }
     fr_status st = ensure_mt(ctx, g->n, g->nnz, k, np);
+    if (st == FR_OK && !ctx->ctl) st = ensure_pairs(ctx, 1, 1, 1);   // the control block lives there
     if (st != FR_OK) return st;
     MtDev md = ctx->mt;
     // staging: pairs and the block -> pair map
