@@ -454,6 +454,7 @@ def multitry_pass(F, ctx, g, part0, w, alpha=10, reps=2, cpu=True):
     device time (CUDA events around fr_multitry, min of reps after one warm run; the pass
     runs its searches in order on one warp), what it gained on the cut, and the oracle's
     pass on the host (one run, one thread)."""
+    import numpy as np
     import torch
     part_np = part0.cpu().numpy()
     pairs = [(int(a), int(b)) for a, b, r in zip(*ctx.rounds(g, part0, w["k"])[:3]) if r == 0]
