@@ -154,10 +154,8 @@ __device__ bool mt_gain(const GraphDev &G, int u, unsigned long long tseed, int 
     for (int s = 0; s < T; ++s) { tb[s] = -1; tw[s] = 0; }
     int own = 0, nt = 0;
     bool over = false;
-    for (int j = j0; j < j1; ++j) {
-        const int P = G.part[__ldg(G.adjncy + j)];
-        const int w = __ldg(G.adjwgt + j);
-        if (P == pu) { own += w; continue; }
+    auto fold = [&](int P, int w) {
+        if (P == pu) { own += w; return; }
         bool hit = false;
 #pragma unroll
         for (int s = 0; s < T; ++s)
@@ -172,7 +170,21 @@ __device__ bool mt_gain(const GraphDev &G, int u, unsigned long long tseed, int 
                 over = true;
             }
         }
+    };
+    // four arcs at a time, so that their blocks are loaded together
+    int j = j0;
+    for (; j + 4 <= j1; j += 4) {
+        const int a0 = __ldg(G.adjncy + j), a1 = __ldg(G.adjncy + j + 1);
+        const int a2 = __ldg(G.adjncy + j + 2), a3 = __ldg(G.adjncy + j + 3);
+        const int w0 = __ldg(G.adjwgt + j), w1 = __ldg(G.adjwgt + j + 1);
+        const int w2 = __ldg(G.adjwgt + j + 2), w3 = __ldg(G.adjwgt + j + 3);
+        const int P0 = G.part[a0], P1 = G.part[a1], P2 = G.part[a2], P3 = G.part[a3];
+        fold(P0, w0);
+        fold(P1, w1);
+        fold(P2, w2);
+        fold(P3, w3);
     }
+    for (; j < j1; ++j) fold(G.part[__ldg(G.adjncy + j)], __ldg(G.adjwgt + j));
     if (nt == 0) return false;
     const unsigned long long hu = tseed ^ ((unsigned long long)(unsigned)u << 32);
     int best = -1, bw = 0;
@@ -266,10 +278,26 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
     int searches = 0, tried_tot = 0, kept_tot = 0, sid = 0;
     bool bad = false;
     __syncwarp();
-    for (int j = 0; j < maxlen && !bad; ++j)
-        for (int p = 0; p < m.np && !bad; ++p) {
-            if (j >= m.cnt[p]) continue;
-            const int v = m.tv[m.off[p] + j];
+    // the todo entries in pass order (entry j of every pair, then j + 1), 32 at a time:
+    // the lanes fetch them and their touched marks together; marks only ever go from 0
+    // to set during a pass, so an entry seen touched is skipped at once and the others
+    // are checked again when their turn comes
+    const long long total = (long long)maxlen * m.np;
+    for (long long pos = 0; pos < total && !bad; pos += 32) {
+        const long long q = pos + lane;
+        int cv = -1;
+        bool fresh = false;
+        if (q < total) {
+            const int j = (int)(q / m.np), p = (int)(q - (long long)j * m.np);
+            if (j < m.cnt[p]) {
+                cv = m.tv[m.off[p] + j];
+                fresh = m.tch[cv] == 0;
+            }
+        }
+        unsigned live = __ballot_sync(kFull, fresh);
+        while (live && !bad) {
+            const int v = __shfl_sync(kFull, cv, __ffs(live) - 1);
+            live &= live - 1;
             if (m.tch[v] != 0) continue;
             const int pv = G.part[v];
             const int x0 = __ldg(G.xadj + v), x1 = __ldg(G.xadj + v + 1);
@@ -437,6 +465,7 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
             kept_tot += best_len;
             ++searches;
         }
+    }
     __syncwarp();
     for (int i = lane; i < G.k; i += 32) {
         m.bw[i] = S.bw[i];
