@@ -53,6 +53,18 @@ class MTResult(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
 
 
+class VcycleResult(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("pad0", ctypes.c_int32), ("cut_before", ctypes.c_int64),
+                ("cut_after", ctypes.c_int64), ("level_n", ctypes.c_int32 * 64), ("level_pairs", ctypes.c_int32 * 64),
+                ("level_cut", ctypes.c_int64 * 64)]
+
+    def as_dict(self):
+        L = self.levels
+        return dict(levels=L, cut_before=self.cut_before, cut_after=self.cut_after,
+                    level_n=list(self.level_n[:L]), level_pairs=list(self.level_pairs[:L]),
+                    level_cut=list(self.level_cut[:L]))
+
+
 class FMResult(ctypes.Structure):
     _fields_ = [("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64), ("wA_after", ctypes.c_int64),
                 ("wB_after", ctypes.c_int64), ("tried", ctypes.c_int32), ("kept", ctypes.c_int32)]
@@ -139,6 +151,15 @@ def lib():
         L.fro_kway_global.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_double,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.POINTER(KwayResult), i32p]
+        L.fro_match.restype = ctypes.c_int32
+        L.fro_match.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int64,
+                                ctypes.c_uint64, i32p]
+        L.fro_contract.restype = ctypes.c_int32
+        L.fro_contract.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, i32p, i32p, i32p, i32p, i32p, i32p]
+        L.fro_vcycle.restype = ctypes.c_int32
+        L.fro_vcycle.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_double,
+                                 ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.POINTER(VcycleResult)]
         L.fro_fm_pair.restype = ctypes.c_int32
         L.fro_fm_pair.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(FMResult), i32p,
@@ -437,3 +458,41 @@ def kway_global(w, alpha=10, init_mode=0, max_rounds=10, seed=0, part=None, eps=
                                w["k"], eps, init_mode, alpha, max_rounds, seed & 0xFFFFFFFFFFFFFFFF,
                                ctypes.byref(res), ctypes.byref(nr))
     return st, part, res.as_dict(), nr.value
+
+
+def match(w, seed_l=0, part=None, W=None):
+    """Greedy matching of one level (fro_match); returns (pairs, mate)."""
+    part = _c32(w["part"] if part is None else part)
+    if W is None:
+        W = int(np.asarray(w["vwgt"], np.int64).sum())
+    mate = np.empty(w["n"], np.int32)
+    pairs = lib().fro_match(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part),
+                            w["k"], W, seed_l & 0xFFFFFFFFFFFFFFFF, _p(mate))
+    return pairs, mate
+
+
+def contract(w, mate):
+    """Contraction of a matching (fro_contract); returns (cmap, coarse workload arrays)."""
+    n, nnz = w["n"], len(w["adjncy"])
+    cmap = np.empty(n, np.int32)
+    cx, ca, cw, cv = (np.empty(n + 1, np.int32), np.empty(max(nnz, 1), np.int32), np.empty(max(nnz, 1), np.int32),
+                      np.empty(n, np.int32))
+    cn = ctypes.c_int32()
+    cnnz = lib().fro_contract(n, _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(_c32(mate)),
+                              _p(cmap), ctypes.byref(cn), _p(cx), _p(ca), _p(cw), _p(cv))
+    c = cn.value
+    return cmap, dict(n=c, nnz=cnnz, xadj=cx[:c + 1].copy(), adjncy=ca[:cnnz].copy(), adjwgt=cw[:cnnz].copy(),
+                      vwgt=cv[:c].copy())
+
+
+def vcycle(w, opts=None, max_levels=64, active_outer=0, part=None, eps=None, alpha=None):
+    """One V-cycle with the given partition (fro_vcycle); returns (status, part, result dict)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    alpha = w["alpha"] if alpha is None else alpha
+    if opts is None:
+        opts = options(mb=w.get("mb", 0))
+    res = VcycleResult()
+    st = lib().fro_vcycle(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part), w["k"],
+                          eps, alpha, ctypes.byref(opts), max_levels, active_outer, ctypes.byref(res))
+    return st, part, res.as_dict()

@@ -63,6 +63,10 @@
  *              is keyed again (boundary) or leaves the queue (not boundary); stop by
  *              the KaSPar rule after each move that is not a new minimum, or an
  *              empty queue; roll back to the first lowest-cut prefix
+ *   multilevel greedy matching in expansion*2 order (exact, c as max(c, 1); ties
+ *              by a seeded splitmix64 key) inside blocks, ends at most 1.5 W/(20k);
+ *              coarse ids in the order of the pairs' smaller fine ids; contract
+ *              while n > max(60k, n0/(60k)); refine every level with its own L_max
  *   multi-try  per pair of a matching, the vertices with a neighbour in the other
  *              block, in splitmix64 order, visited round-robin over the pairs; a
  *              vertex no search of the pass queued that is still a boundary vertex
@@ -136,6 +140,17 @@ typedef struct fro_mt_result {
     int32_t tried, kept; /* moves made / kept */
     int32_t pad0;
 } fro_mt_result;
+
+/* Multilevel V-cycle with a given partition (fro_vcycle). */
+#define FRO_MAX_LEVELS 64
+typedef struct fro_vcycle_result {
+    int32_t levels;                      /* graphs in the hierarchy, the input included */
+    int32_t pad0;
+    int64_t cut_before, cut_after;       /* total cut of the input and the output partition */
+    int32_t level_n[FRO_MAX_LEVELS];     /* vertices of each level (0 = the input) */
+    int32_t level_pairs[FRO_MAX_LEVELS]; /* pair refinements run on each level */
+    int64_t level_cut[FRO_MAX_LEVELS];   /* total cut after the level's refinement */
+} fro_vcycle_result;
 
 /* Input checks of Section 2.1 (omega > 0, c >= 0, symmetric simple CSR, 0 <= part < k). */
 int32_t fro_validate(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
@@ -261,6 +276,27 @@ int32_t fro_refine_active(int32_t n, const int32_t *xadj, const int32_t *adjncy,
                           const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha,
                           const fro_options *opt, int32_t max_outer, int32_t cap, fro_pair_result *res,
                           int32_t *npairs, int32_t *nouter, fro_mt_result *mt);
+
+/* Greedy matching of one level (Sections 2.2 and 5): edges inside one block whose ends
+ * weigh at most 1.5 W / (20 k), ordered by expansion*2 (exact; c taken as max(c, 1)),
+ * then by splitmix64(seed_l ^ min << 32 ^ max) (larger first), then by (min, max);
+ * mate[v] = partner or -1.  Returns the matched pairs. */
+int32_t fro_match(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vwgt,
+                  const int32_t *part, int32_t k, int64_t W, uint64_t seed_l, int32_t *mate);
+/* Contraction of a matching (Section 2.1): coarse vertex of a pair or single vertex
+ * numbered by its smaller fine id; rows sorted by coarse id, parallel edges merged.
+ * cmap[n]; the coarse arrays need room for n + 1, nnz, nnz, n entries.  Returns nnz. */
+int32_t fro_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, const int32_t *mate, int32_t *cmap, int32_t *cn, int32_t *cxadj,
+                     int32_t *cadjncy, int32_t *cadjwgt, int32_t *cvwgt);
+/* One V-cycle with the given partition (Section 5): contract level by level with
+ * fro_match (seed_l = splitmix64(opt->seed ^ level)) while the graph has more than
+ * max(60 k, n / (60 k)) vertices, a matching is non-empty and fewer than max_levels
+ * levels exist; then from the coarsest level up, project and refine with one
+ * fro_refine_batch sweep (or fro_refine_active with active_outer outer rounds). */
+int32_t fro_vcycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                   const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha, const fro_options *opt,
+                   int32_t max_levels, int32_t active_outer, fro_vcycle_result *out);
 
 /* Pair cut omega(E_ab) of the current partition. */
 int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,

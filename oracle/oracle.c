@@ -1579,3 +1579,246 @@ int32_t fro_refine_batch_mt(int32_t n, const int32_t *xadj, const int32_t *adjnc
     if (done) *done = out;
     return FRO_OK;
 }
+
+/* ------------------------------------- multilevel V-cycle (2.1, 2.2, 5) ---- */
+
+/* Section 2.1 defines matching, contraction (c(x) = c(u) + c(v), parallel edges
+ * merged with summed weights) and the three phases; Section 2.2 rates edges with
+ * expansion*2(u, v) = omega(u, v)^2 / (c(u) c(v)), matches to maximise the rated
+ * weight and keeps nodes heavier than 1.5 n / (20 k) out of contractions; Section
+ * 5 (global search) reuses a given partition: edges between two blocks are never
+ * matched, so the partition is the coarsest graph's initial partition and every
+ * level refines it.  Readings (also in fro.h):
+ *   rating   expansion*2 with c replaced by max(c, 1) (zero vertex weights are
+ *            allowed here); compared exactly as omega1^2 c2(u) c2(v) against
+ *            omega2^2 c1(u) c1(v) in 128-bit integers
+ *   order    edges by rating, larger first; equal ratings by the larger
+ *            splitmix64(seed_l ^ min(u, v) << 32 ^ max(u, v)) (random tie
+ *            breaking), then by the smaller (min, max) pair; seed_l =
+ *            splitmix64(seed ^ level)
+ *   matching the greedy matching in that order (an edge joins if both ends are
+ *            still free) over the edges inside one block whose ends both weigh at
+ *            most 1.5 W / (20 k) (W = c(V) of the input, n in the paper's unit-weight
+ *            setting), i.e. 40 k c(v) <= 3 W.  GPA is replaced by greedy matching:
+ *            both are 1/2-approximations of the maximum rated matching, and greedy
+ *            has an exact parallel form (locally dominant edges)
+ *   ids      the coarse vertex of a matched pair or a single vertex is numbered in
+ *            the order of its smaller fine id; coarse rows list their neighbours
+ *            in increasing coarse id, parallel edges merged, the matched edge gone
+ *   levels   contract while the graph has more than max(60 k, n / (60 k)) vertices,
+ *            a level matches at least one edge, and fewer than max_levels levels
+ *            exist
+ *   refine   on the coarsest level, then after each projection (part(v) =
+ *            part(coarse vertex of v)), one sweep of fro_refine_batch, or
+ *            fro_refine_active when active_outer > 0, with L_max of that level's
+ *            graph */
+
+typedef struct {
+    int32_t n, nnz;
+    int32_t *xadj, *adjncy, *adjwgt, *vwgt;
+} ml_graph;
+
+static void ml_free(ml_graph *g) {
+    free(g->xadj); free(g->adjncy); free(g->adjwgt); free(g->vwgt);
+}
+
+typedef struct { int32_t u, v, w; uint64_t h; int64_t cu, cv; } ml_edge;
+
+/* 1 if edge x comes before edge y in the matching order */
+static int ml_before(const ml_edge *x, const ml_edge *y) {
+    const unsigned __int128 lx = (unsigned __int128)((uint64_t)x->w * (uint64_t)x->w) * (uint64_t)y->cu * (uint64_t)y->cv;
+    const unsigned __int128 ly = (unsigned __int128)((uint64_t)y->w * (uint64_t)y->w) * (uint64_t)x->cu * (uint64_t)x->cv;
+    if (lx != ly) return lx > ly;
+    if (x->h != y->h) return x->h > y->h;
+    if (x->u != y->u) return x->u < y->u;
+    return x->v < y->v;
+}
+
+static int ml_cmp(const void *a, const void *b) {
+    const ml_edge *x = (const ml_edge *)a, *y = (const ml_edge *)b;
+    if (ml_before(x, y)) return -1;
+    if (ml_before(y, x)) return 1;
+    return 0;
+}
+
+/* Greedy matching of one level (mate[v] = partner or -1). */
+static int32_t ml_match(const int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                        const int32_t *vwgt, const int32_t *part, int32_t k, int64_t W, uint64_t seed_l,
+                        int32_t *mate) {
+    int64_t m = 0;
+    for (int32_t v = 0; v < n; ++v) mate[v] = -1;
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) if (v < adjncy[j]) ++m;
+    ml_edge *E = XALLOC(ml_edge, m);
+    int64_t ne = 0;
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j) {
+            const int32_t u = adjncy[j];
+            if (v >= u || part[v] != part[u]) continue;
+            if (40LL * k * vwgt[v] > 3 * W || 40LL * k * vwgt[u] > 3 * W) continue;
+            ml_edge e;
+            e.u = v; e.v = u; e.w = adjwgt[j];
+            e.h = fro_splitmix64(seed_l ^ ((uint64_t)(uint32_t)v << 32) ^ (uint64_t)(uint32_t)u);
+            e.cu = vwgt[v] > 0 ? vwgt[v] : 1;
+            e.cv = vwgt[u] > 0 ? vwgt[u] : 1;
+            E[ne++] = e;
+        }
+    qsort(E, (size_t)ne, sizeof(ml_edge), ml_cmp);
+    int32_t pairs = 0;
+    for (int64_t i = 0; i < ne; ++i)
+        if (mate[E[i].u] < 0 && mate[E[i].v] < 0) {
+            mate[E[i].u] = E[i].v;
+            mate[E[i].v] = E[i].u;
+            ++pairs;
+        }
+    free(E);
+    return pairs;
+}
+
+static int cmp_pair_i32(const void *a, const void *b) {
+    const int32_t *x = (const int32_t *)a, *y = (const int32_t *)b;
+    return (x[0] > y[0]) - (x[0] < y[0]);
+}
+
+/* Contraction of a matching: coarse graph and cmap[v] = coarse vertex of v. */
+static void ml_contract(const ml_graph *g, const int32_t *mate, ml_graph *c, int32_t *cmap) {
+    int32_t nc = 0;
+    for (int32_t v = 0; v < g->n; ++v)
+        if (mate[v] < 0 || v < mate[v]) cmap[v] = nc++;
+    for (int32_t v = 0; v < g->n; ++v)
+        if (mate[v] >= 0 && v > mate[v]) cmap[v] = cmap[mate[v]];
+    int32_t *first = XALLOC(int32_t, nc);   /* smaller member of each coarse vertex */
+    for (int32_t v = g->n - 1; v >= 0; --v) first[cmap[v]] = v;
+    c->n = nc;
+    c->xadj = XALLOC(int32_t, nc + 1);
+    c->vwgt = XALLOC(int32_t, nc);
+    int64_t *acc = XALLOC(int64_t, nc);
+    int32_t *row = XALLOC(int32_t, 2 * (size_t)(g->nnz > 0 ? g->nnz : 1));
+    int32_t *adj = XALLOC(int32_t, g->nnz), *wgt = XALLOC(int32_t, g->nnz);
+    int32_t cnt = 0;
+    for (int32_t x = 0; x < nc; ++x) {
+        c->xadj[x] = cnt;
+        const int32_t mem[2] = { first[x], mate[first[x]] };
+        int32_t nr = 0;
+        for (int t = 0; t < 2; ++t) {
+            const int32_t v = mem[t];
+            if (v < 0) continue;
+            c->vwgt[x] += g->vwgt[v];
+            for (int32_t j = g->xadj[v]; j < g->xadj[v + 1]; ++j) {
+                const int32_t y = cmap[g->adjncy[j]];
+                if (y == x) continue;   /* the matched edge */
+                if (acc[y] == 0) { row[2 * nr] = y; row[2 * nr + 1] = 0; ++nr; }
+                acc[y] += g->adjwgt[j];
+            }
+        }
+        qsort(row, (size_t)nr, 2 * sizeof(int32_t), cmp_pair_i32);
+        for (int32_t i = 0; i < nr; ++i) {
+            const int32_t y = row[2 * i];
+            adj[cnt] = y;
+            wgt[cnt] = (int32_t)acc[y];
+            acc[y] = 0;
+            ++cnt;
+        }
+    }
+    c->xadj[nc] = cnt;
+    c->nnz = cnt;
+    c->adjncy = adj;
+    c->adjwgt = wgt;
+    free(first); free(acc); free(row);
+}
+
+int32_t fro_match(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vwgt,
+                  const int32_t *part, int32_t k, int64_t W, uint64_t seed_l, int32_t *mate) {
+    if (n < 1 || k < 1 || W < 0) return -1;
+    return ml_match(n, xadj, adjncy, adjwgt, vwgt, part, k, W, seed_l, mate);
+}
+
+int32_t fro_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                     const int32_t *vwgt, const int32_t *mate, int32_t *cmap, int32_t *cn, int32_t *cxadj,
+                     int32_t *cadjncy, int32_t *cadjwgt, int32_t *cvwgt) {
+    ml_graph g = { n, xadj[n], (int32_t *)xadj, (int32_t *)adjncy, (int32_t *)adjwgt, (int32_t *)vwgt };
+    ml_graph c;
+    ml_contract(&g, mate, &c, cmap);
+    *cn = c.n;
+    memcpy(cxadj, c.xadj, sizeof(int32_t) * (size_t)(c.n + 1));
+    memcpy(cadjncy, c.adjncy, sizeof(int32_t) * (size_t)c.nnz);
+    memcpy(cadjwgt, c.adjwgt, sizeof(int32_t) * (size_t)c.nnz);
+    memcpy(cvwgt, c.vwgt, sizeof(int32_t) * (size_t)c.n);
+    int32_t nnz = c.nnz;
+    ml_free(&c);
+    return nnz;
+}
+
+int32_t fro_vcycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                   const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha, const fro_options *opt,
+                   int32_t max_levels, int32_t active_outer, fro_vcycle_result *out) {
+    memset(out, 0, sizeof(*out));
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || max_levels < 1 || max_levels > FRO_MAX_LEVELS ||
+                         active_outer < 0 || bad_fm(opt) || (opt && opt->mt_alpha < 0) ||
+                         (bad_mt(opt) && active_outer == 0)))
+        st = FRO_ERR_INVALID_ARG;
+    if (st != FRO_OK) return st;
+    const uint64_t seed = opt ? opt->seed : 0;
+    const int64_t W = fro_total_weight(n, vwgt);
+    int64_t thr = 60LL * k;
+    if ((int64_t)n / (60LL * k) > thr) thr = (int64_t)n / (60LL * k);
+    ml_graph G[FRO_MAX_LEVELS];
+    int32_t *cmap[FRO_MAX_LEVELS];
+    int32_t *P[FRO_MAX_LEVELS];
+    G[0].n = n; G[0].nnz = xadj[n];
+    G[0].xadj = (int32_t *)xadj; G[0].adjncy = (int32_t *)adjncy; G[0].adjwgt = (int32_t *)adjwgt;
+    G[0].vwgt = (int32_t *)vwgt;
+    P[0] = XALLOC(int32_t, n);
+    memcpy(P[0], part, sizeof(int32_t) * (size_t)n);
+    int32_t L = 1;
+    out->cut_before = 0;
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j)
+            if (v < adjncy[j] && part[v] != part[adjncy[j]]) out->cut_before += adjwgt[j];
+    /* contraction */
+    while (L < max_levels && G[L - 1].n > thr) {
+        const ml_graph *g = &G[L - 1];
+        int32_t *mate = XALLOC(int32_t, g->n);
+        const int32_t pairs = ml_match(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, P[L - 1], k, W,
+                                       fro_splitmix64(seed ^ (uint64_t)(L - 1)), mate);
+        if (pairs == 0) { free(mate); break; }
+        cmap[L - 1] = XALLOC(int32_t, g->n);
+        ml_contract(g, mate, &G[L], cmap[L - 1]);
+        P[L] = XALLOC(int32_t, G[L].n);
+        for (int32_t v = 0; v < g->n; ++v) P[L][cmap[L - 1][v]] = P[L - 1][v];
+        free(mate);
+        ++L;
+    }
+    out->levels = L;
+    for (int32_t l = 0; l < L; ++l) out->level_n[l] = G[l].n;
+    /* refinement from the coarsest level up */
+    const int32_t cap = k * (k - 1) / 2 * (active_outer > 0 ? active_outer : 1);
+    fro_pair_result *res = XALLOC(fro_pair_result, cap > 0 ? cap : 1);
+    for (int32_t l = L - 1; l >= 0 && st == FRO_OK; --l) {
+        if (l < L - 1)
+            for (int32_t v = 0; v < G[l].n; ++v) P[l][v] = P[l + 1][cmap[l][v]];
+        int32_t np_ = 0, nr_ = 0;
+        if (active_outer > 0)
+            st = fro_refine_active(G[l].n, G[l].xadj, G[l].adjncy, G[l].adjwgt, G[l].vwgt, P[l], k, eps, alpha, opt,
+                                   active_outer, cap, res, &np_, &nr_, NULL);
+        else
+            st = fro_refine_batch(G[l].n, G[l].xadj, G[l].adjncy, G[l].adjwgt, G[l].vwgt, P[l], k, eps, alpha, opt,
+                                  cap, res, &np_, &nr_);
+        out->level_pairs[l] = np_;
+        int64_t cut = 0;
+        for (int32_t v = 0; v < G[l].n; ++v)
+            for (int32_t j = G[l].xadj[v]; j < G[l].xadj[v + 1]; ++j)
+                if (v < G[l].adjncy[j] && P[l][v] != P[l][G[l].adjncy[j]]) cut += G[l].adjwgt[j];
+        out->level_cut[l] = cut;
+    }
+    if (st == FRO_OK) {
+        memcpy(part, P[0], sizeof(int32_t) * (size_t)n);
+        out->cut_after = out->level_cut[0];
+    }
+    for (int32_t l = 0; l < L; ++l) free(P[l]);
+    for (int32_t l = 1; l < L; ++l) ml_free(&G[l]);
+    for (int32_t l = 0; l + 1 < L; ++l) free(cmap[l]);
+    free(res);
+    return st;
+}

@@ -1,0 +1,242 @@
+"""Pins of the oracle's multilevel V-cycle with a given partition: greedy matching in
+expansion*2 order, contraction, projection and refinement on every level (Section 2.1
+matching and contraction; Section 2.2 ratings and the weight bound on contracted nodes;
+Section 5 global search: no edge between two blocks is matched).
+
+The matching is pinned by its certificate: a set of allowed edges is the greedy
+matching in a strict priority order iff an allowed edge belongs to it exactly when no
+adjacent edge of the set has a higher priority (induction over the order).  The
+priorities are recomputed here exactly with Python integers (splitmix64 written out
+from its published definition).  Contraction is checked against S^T A S with the
+0/1 membership matrix S (scipy), projection against the cut identity, and the V-cycle
+is rebuilt from single matchings, contractions and batch sweeps.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_1012_0006_gb300 import inputs as I
+
+M64 = (1 << 64) - 1
+
+
+def splitmix64(x):
+    z = (x + 0x9E3779B97F4A7C15) & M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def _edges(w):
+    xadj, adj, wg = (np.asarray(w[k]) for k in ("xadj", "adjncy", "adjwgt"))
+    src = np.repeat(np.arange(w["n"]), np.diff(xadj))
+    m = src < adj
+    return src[m], adj[m], wg[m]
+
+
+def _cut(w, part):
+    u, v, wt = _edges(w)
+    part = np.asarray(part)
+    return int(wt[part[u] != part[v]].sum())
+
+
+class Prio:
+    """Exact priority of an edge: larger expansion*2, then larger hash, then smaller (u, v)."""
+
+    def __init__(self, w, seed_l):
+        self.vw = [max(int(c), 1) for c in np.asarray(w["vwgt"])]
+        self.seed_l = seed_l
+
+    def key(self, u, v, wt):
+        return (wt * wt, self.vw[u] * self.vw[v], splitmix64(self.seed_l ^ (u << 32) ^ v), u, v)
+
+    @staticmethod
+    def higher(a, b):
+        # rating a[0]/a[1] against b[0]/b[1], exactly
+        if a[0] * b[1] != b[0] * a[1]:
+            return a[0] * b[1] > b[0] * a[1]
+        if a[2] != b[2]:
+            return a[2] > b[2]
+        return (a[3], a[4]) < (b[3], b[4])
+
+
+def check_greedy(w, seed_l, mate, part=None):
+    part = np.asarray(w["part"] if part is None else part)
+    vw = np.asarray(w["vwgt"], np.int64)
+    W, k = int(vw.sum()), w["k"]
+    pr = Prio(w, seed_l)
+    u_, v_, w_ = _edges(w)
+    allowed = {}
+    for u, v, wt in zip(u_.tolist(), v_.tolist(), w_.tolist()):
+        if part[u] == part[v] and 40 * k * vw[u] <= 3 * W and 40 * k * vw[v] <= 3 * W:
+            allowed[(u, v)] = pr.key(u, v, wt)
+    mate = np.asarray(mate)
+    M = set()
+    for v in range(w["n"]):
+        if mate[v] >= 0:
+            assert mate[mate[v]] == v
+            e = (min(v, int(mate[v])), max(v, int(mate[v])))
+            assert e in allowed, "matched edge not allowed"
+            M.add(e)
+    inc = {}
+    for e in M:
+        inc[e[0]] = e
+        inc[e[1]] = e
+    for e, ke in allowed.items():
+        higher_matched = any(f in M and f != e and Prio.higher(allowed[f], ke)
+                             for f in (inc.get(e[0]), inc.get(e[1])) if f is not None)
+        assert (e in M) == (not higher_matched), e
+    return len(M)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_matching_is_the_greedy_one(seed):
+    w = I.random_small(12000 + seed, n_max=700, k_max=5)
+    for seed_l in (0, splitmix64(seed)):
+        pairs, mate = O.match(w, seed_l=seed_l)
+        assert pairs == check_greedy(w, seed_l, mate)
+
+
+def test_matching_closed_forms():
+    # a path with strictly falling edge weights: greedy takes (0,1), (2,3), ...
+    n = 12
+    xadj = np.zeros(n + 1, np.int32)
+    adj, wgt = [], []
+    for v in range(n):
+        row = [u for u in (v - 1, v + 1) if 0 <= u < n]
+        adj += row
+        wgt += [100 - min(v, u) for u in row]
+        xadj[v + 1] = len(adj)
+    w = dict(n=n, xadj=xadj, adjncy=np.array(adj, np.int32), adjwgt=np.array(wgt, np.int32),
+             vwgt=np.ones(n, np.int32), part=np.zeros(n, np.int32), k=1)
+    pairs, mate = O.match(w, W=10 ** 6)
+    assert pairs == 6 and [int(mate[v]) for v in range(n)] == [v ^ 1 for v in range(n)]
+    # a star: equal edge weights, the lightest leaf wins (expansion*2 = omega^2 / (c(u) c(v)))
+    leaves = [5, 3, 7, 2, 9]
+    n = 1 + len(leaves)
+    xadj = np.array([0, len(leaves)] + [len(leaves) + i + 1 for i in range(len(leaves))], np.int32)
+    adj = np.array(list(range(1, n)) + [0] * len(leaves), np.int32)
+    w = dict(n=n, xadj=xadj, adjncy=adj, adjwgt=np.full(len(adj), 4, np.int32),
+             vwgt=np.array([1] + leaves, np.int32), part=np.zeros(n, np.int32), k=1)
+    pairs, mate = O.match(w, W=10 ** 6)
+    assert pairs == 1 and mate[0] == 1 + leaves.index(2)
+    # the same star with the centre above 1.5 W / (20 k): nothing may be matched
+    pairs, mate = O.match(w, W=10)
+    assert pairs == 0 and (mate == -1).all()
+
+
+def test_no_edge_between_blocks_is_matched():
+    w = I.random_small(12100, n_max=800, k_max=6)
+    pairs, mate = O.match(w, seed_l=5)
+    part = np.asarray(w["part"])
+    m = mate >= 0
+    assert (part[m] == part[mate[m]]).all()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_contraction_is_the_quotient_graph(seed):
+    w = I.random_small(12200 + seed, n_max=900, k_max=5)
+    pairs, mate = O.match(w, seed_l=seed)
+    cmap, c = O.contract(w, mate)
+    n, nc = w["n"], c["n"]
+    assert nc == n - pairs
+    # S^T A S: coarse edge weights, the matched edges on the diagonal
+    xadj = np.asarray(w["xadj"])
+    A = sp.csr_matrix((np.asarray(w["adjwgt"], np.int64), np.asarray(w["adjncy"]), xadj), shape=(n, n))
+    S = sp.csr_matrix((np.ones(n, np.int64), (np.arange(n), cmap)), shape=(n, nc))
+    Q = (S.T @ A @ S).tolil()
+    Q.setdiag(0)
+    Q = Q.tocsr()
+    Q.eliminate_zeros()
+    C = sp.csr_matrix((c["adjwgt"].astype(np.int64), c["adjncy"], c["xadj"]), shape=(nc, nc))
+    assert (Q != C).nnz == 0
+    # rows sorted, no loops, weights summed
+    for x in range(nc):
+        row = c["adjncy"][c["xadj"][x]:c["xadj"][x + 1]]
+        assert (np.diff(row) > 0).all() and x not in row
+    assert np.array_equal(c["vwgt"], np.bincount(cmap, weights=np.asarray(w["vwgt"]), minlength=nc).astype(np.int32))
+    # coarse ids follow the smaller fine member
+    rep = np.full(nc, n, np.int64)
+    np.minimum.at(rep, cmap, np.arange(n))
+    assert (np.diff(rep) > 0).all()
+    # the partition carries over with the same cut (no matched edge crosses blocks)
+    part = np.asarray(w["part"])
+    cpart = np.empty(nc, np.int32)
+    cpart[cmap] = part
+    assert (cpart[cmap] == part).all()
+    cw = dict(c, k=w["k"])
+    assert _cut(cw, cpart) == _cut(w, part)
+
+
+def _rebuild(w, opts, max_levels, active_outer=0):
+    """The V-cycle written out from single matchings, contractions and refinements."""
+    k = w["k"]
+    W = int(np.asarray(w["vwgt"], np.int64).sum())
+    thr = max(60 * k, w["n"] // (60 * k))
+    levels, maps = [dict(w, part=np.array(w["part"], np.int32))], []
+    while len(levels) < max_levels and levels[-1]["n"] > thr:
+        g = levels[-1]
+        pairs, mate = O.match(g, seed_l=splitmix64((opts.seed ^ (len(levels) - 1)) & M64), W=W)
+        if pairs == 0:
+            break
+        cmap, c = O.contract(g, mate)
+        cp = np.empty(c["n"], np.int32)
+        cp[cmap] = g["part"]
+        levels.append(dict(c, part=cp, k=k, eps=w["eps"], alpha=w["alpha"]))
+        maps.append(cmap)
+    cuts = [0] * len(levels)
+    part = levels[-1]["part"]
+    for l in range(len(levels) - 1, -1, -1):
+        g = levels[l]
+        if l < len(levels) - 1:
+            part = part[maps[l]]
+        if active_outer:
+            st, part, _, _ = O.refine_active(g, part=part, opts=opts, max_outer=active_outer)
+        else:
+            st, part, _, _ = O.refine_batch(g, part=part, opts=opts)
+        assert st == 0
+        cuts[l] = _cut(g, part)
+    return [g["n"] for g in levels], cuts, part
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_vcycle_rebuilt_from_its_steps(seed):
+    w = I.random_small(12300 + seed, n_max=2500, k_max=6)
+    opts = O.options(mb=seed % 2, seed=seed)
+    for max_levels, active in ((64, 0), (3, 0), (64, 2)):
+        st, part, r = O.vcycle(w, opts=opts, max_levels=max_levels, active_outer=active)
+        assert st == 0
+        ns, cuts, want = _rebuild(w, opts, max_levels, active)
+        assert r["level_n"] == ns and r["level_cut"] == cuts
+        assert np.array_equal(part, want)
+        assert r["cut_after"] == _cut(w, part) == cuts[0]
+        assert r["cut_before"] == _cut(w, w["part"])
+        # refinement never raises the cut, and projection keeps it
+        assert all(cuts[l] <= cuts[l + 1] for l in range(len(cuts) - 1))
+        assert cuts[-1] <= r["cut_before"]
+
+
+def test_vcycle_stops_where_it_should():
+    w = I.config(4, scale=1 / 64)   # 65,536 vertices, k = 64: threshold max(3840, 17) vertices
+    st, part, r = O.vcycle(w, opts=O.options(mb=1))
+    assert st == 0
+    ns = r["level_n"]
+    assert all(n > 3840 for n in ns[:-1]) and (ns[-1] <= 3840 or r["levels"] == 64)
+    assert r["cut_after"] < r["cut_before"]
+
+
+def test_vcycle_option_checks():
+    w = I.random_small(12400, n_max=200)
+    assert O.vcycle(w, max_levels=0)[0] == 1
+    assert O.vcycle(w, max_levels=65)[0] == 1
+    assert O.vcycle(w, opts=O.options(mt_alpha=10))[0] == 1            # multi-try needs active scheduling
+    assert O.vcycle(w, opts=O.options(mt_alpha=10), active_outer=2)[0] == 0
+
+
+def test_vcycle_threshold_is_strict():
+    # k = 2: contraction runs while the graph has more than max(120, n / 120) vertices
+    for nx, ny, want in ((12, 10, 1), (11, 11, 2)):
+        w = I.grid2d_halves(nx=nx, ny=ny, swaps=4)
+        st, part, r = O.vcycle(w, max_levels=2)
+        assert st == 0 and r["levels"] == want and r["level_n"][0] == nx * ny
