@@ -392,6 +392,7 @@ def run_ours(args, world, rank, local, pg):
     active = active_blocks(F, ctx, g, part0, w) if args.active else None
     fm = fm_sweeps(F, ctx, g, part0, w) if args.fm else None
     mtp = multitry_pass(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
+    vc = multilevel(F, ctx, g, part0, w) if args.vcycle else None
 
     serving = None
     if args.serve or args.serve_full:
@@ -422,7 +423,7 @@ def run_ours(args, world, rank, local, pg):
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare,
-            "active_blocks": active, "fm": fm, "multitry": mtp,
+            "active_blocks": active, "fm": fm, "multitry": mtp, "vcycle": vc,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -481,6 +482,32 @@ def multitry_pass(F, ctx, g, part0, w, alpha=10, reps=2, cpu=True):
         out["parity"] = bool(tref == {f: tot[f] for f in ("gain", "searches", "tried", "kept")} and
                              np.array_equal(pref, part.cpu().numpy()))
     return out
+
+
+def multilevel(F, ctx, g, part0, w, reps=2):
+    """One V-cycle with the bench workload's partition (fr_vcycle, Section 5): greedy
+    expansion*2 matchings inside blocks, contraction down to max(60 k, n / (60 k))
+    vertices, then a flow sweep on every level from the coarsest up; device time (CUDA
+    events around the call, min of reps after one warm run) and the cut against one flat
+    sweep of the input level."""
+    import torch
+    opts = F.default_options(mb=int(w["mb"]))
+    part = part0.clone()
+    st, flat = ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], opts, results=False)[::2]
+    best, r = None, None
+    for _ in range(reps + 1):
+        part.copy_(part0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, r = ctx.vcycle(g, part, w["k"], w["eps"], w["alpha"], opts)
+        e1.record()
+        torch.cuda.synchronize()
+        if _ > 0:
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+    return {"workload": "bench workload and partition, one V-cycle, one sweep per level",
+            "ms": round(best, 2), "levels": r["levels"], "level_n": r["level_n"], "level_pairs": r["level_pairs"],
+            "coarsen_ms": round(r["coarsen_ms"], 2), "refine_ms": round(r["refine_ms"], 2),
+            "cut_before": r["cut_before"], "cut_after": r["cut_after"], "cut_after_flat_sweep": flat["cut_after"]}
 
 
 def fm_sweeps(F, ctx, g, part0, w, reps=3):
@@ -726,6 +753,8 @@ def main():
                     help="active block scheduling with adaptive flow iterations on the bench workload")
     ap.add_argument("--fm", action=argparse.BooleanOptionalAction, default=True,
                     help="sweeps with the two-way FM step before each flow (1 %% and 5 %% stopping rules)")
+    ap.add_argument("--vcycle", action=argparse.BooleanOptionalAction, default=True,
+                    help="one multilevel V-cycle with the workload's partition, a sweep per level")
     ap.add_argument("--mt", action=argparse.BooleanOptionalAction, default=True,
                     help="one multi-try FM pass over the first matching, against the oracle's")
     args = ap.parse_args()

@@ -139,6 +139,19 @@ typedef struct fr_batch_result {
     int32_t pad0;
 } fr_batch_result;
 
+/* One multilevel V-cycle (fr_vcycle). */
+#define FR_MAX_LEVELS 64
+typedef struct fr_vcycle_result {
+    int32_t levels;                       /* graphs in the hierarchy, the input included */
+    int32_t status;
+    int64_t cut_before, cut_after;        /* total cut of the input and the output partition */
+    int32_t level_n[FR_MAX_LEVELS];       /* vertices of each level (0 = the input) */
+    int32_t level_pairs[FR_MAX_LEVELS];   /* pair refinements run on each level */
+    int64_t level_cut[FR_MAX_LEVELS];     /* total cut after the level's refinement */
+    double coarsen_ms;                    /* matching and contraction, all levels (host clock, synchronised) */
+    double refine_ms;                     /* projection and refinement, all levels */
+} fr_vcycle_result;
+
 /* Totals of one multi-try FM pass (fr_multitry). */
 typedef struct fr_mt_result {
     int64_t gain;           /* cut decrease kept */
@@ -157,7 +170,7 @@ void fr_default_options(fr_options *opt);
 /* sizeof of the structs of this header, for bindings to check their layouts:
  * which = 0 fr_graph, 1 fr_options, 2 fr_pair_result, 3 fr_batch_result,
  * 4 fr_profile_info, 5 fr_server_config, 6 fr_request, 7 fr_response,
- * 8 fr_mt_result; -1 for
+ * 8 fr_mt_result, 9 fr_vcycle_result; -1 for
  * any other value.  Needs no device. */
 int32_t fr_struct_size(int32_t which);
 
@@ -277,6 +290,38 @@ fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_
 fr_status fr_multitry(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, int32_t np,
                       const int32_t *pa, const int32_t *pb, int32_t alpha, uint64_t seed, fr_mt_result *out,
                       int8_t *changed);
+
+/* ---- multilevel V-cycle with a given partition (Sections 2.1, 2.2, 5) ---- */
+
+/* Greedy matching of one level: the edges inside one block of part whose ends both weigh
+ * at most 1.5 W / (20 k) (40 k c(v) <= 3 W), ordered by expansion*2 = omega^2 / (c(u) c(v))
+ * (exact, c taken as max(c, 1)), then by the larger splitmix64(seed_l ^ min << 32 ^ max),
+ * then by the smaller (min, max); an edge joins when both ends are free.  Computed on the
+ * device with locally dominant edges (the same matching).  mate: DEVICE, n entries,
+ * receives the partner or -1.  *pairs (HOST): matched pairs. */
+fr_status fr_match(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, int64_t W, uint64_t seed_l,
+                   int32_t *mate, int32_t *pairs);
+
+/* Contraction of a matching (Section 2.1): the smaller end of a pair, or a single vertex,
+ * represents a coarse vertex, numbered in the order of those fine ids; c(x) is the sum of
+ * its members; rows list the coarse neighbours by increasing id, parallel edges merged
+ * with summed weights, the matched edge dropped.  All arrays DEVICE: cmap[n]; coarse
+ * xadj / adjncy / adjwgt / vwgt with room for n + 1, nnz, nnz and n entries.  *cn, *cnnz
+ * (HOST): coarse sizes. */
+fr_status fr_contract(fr_ctx *ctx, const fr_graph *g, const int32_t *mate, int32_t *cmap, int32_t *cn, int32_t *cnnz,
+                      int32_t *cxadj, int32_t *cadjncy, int32_t *cadjwgt, int32_t *cvwgt);
+
+/* One V-cycle with the given partition (Section 5: no edge between two blocks is matched,
+ * so part is the coarsest level's partition): contract with fr_match (seed_l =
+ * splitmix64(opt->seed ^ level)) and fr_contract while the graph has more than
+ * max(60 k, n / (60 k)) vertices, the matching is not empty and fewer than max_levels
+ * (<= FR_MAX_LEVELS) levels exist; then from the coarsest level up, project the partition
+ * and refine it with one fr_refine_batch sweep, or fr_refine_active with active_outer
+ * outer rounds (each level with its own L_max).  part: DEVICE, updated in place,
+ * unchanged on error.  out (HOST, optional): the hierarchy's sizes and the cut per
+ * level.  opt->mt_alpha needs active_outer > 0. */
+fr_status fr_vcycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
+                    const fr_options *opt, int32_t max_levels, int32_t active_outer, fr_vcycle_result *out);
 
 /* Same as fr_refine_batch for a graph and partition in HOST memory: uploads the
  * arrays, refines, and copies part back (the end-to-end form; graph buffers are

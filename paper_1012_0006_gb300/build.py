@@ -30,8 +30,10 @@ CUDA_SOURCES = [
     "api_batch.cu",
     "api_active.cu",
     "api_mt.cu",
+    "api_ml.cu",
     "fm_kernel.cu",
     "mt_kernel.cu",
+    "ml_kernel.cu",
     "round_kernel.cu",
     "prep_kernel.cu",
     "serve.cu",

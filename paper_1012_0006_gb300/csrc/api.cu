@@ -420,6 +420,7 @@ extern "C" int32_t fr_struct_size(int32_t which) {
     case 6: return (int32_t)sizeof(fr_request);
     case 7: return (int32_t)sizeof(fr_response);
     case 8: return (int32_t)sizeof(fr_mt_result);
+    case 9: return (int32_t)sizeof(fr_vcycle_result);
     default: return -1;
     }
 }

@@ -66,6 +66,18 @@ class BatchResult(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
 
 
+class VcycleResult(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("status", ctypes.c_int32), ("cut_before", ctypes.c_int64),
+                ("cut_after", ctypes.c_int64), ("level_n", ctypes.c_int32 * 64), ("level_pairs", ctypes.c_int32 * 64),
+                ("level_cut", ctypes.c_int64 * 64), ("coarsen_ms", ctypes.c_double), ("refine_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        L = self.levels
+        return dict(levels=L, status=self.status, cut_before=self.cut_before, cut_after=self.cut_after,
+                    level_n=list(self.level_n[:L]), level_pairs=list(self.level_pairs[:L]),
+                    level_cut=list(self.level_cut[:L]), coarsen_ms=self.coarsen_ms, refine_ms=self.refine_ms)
+
+
 class MtResult(ctypes.Structure):
     _fields_ = [("gain", ctypes.c_int64), ("searches", ctypes.c_int32), ("tried", ctypes.c_int32),
                 ("kept", ctypes.c_int32), ("status", ctypes.c_int32)]
@@ -151,6 +163,12 @@ SYMBOLS = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "fr_multitry": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                    i32p, i32p, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(MtResult), i8p]),
+    "fr_match": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, vp,
+                                ctypes.POINTER(ctypes.c_int32)]),
+    "fr_contract": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp]),
+    "fr_vcycle": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                 ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(VcycleResult)]),
     "fr_refine_batch_host": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_int32,
                                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
                                             ctypes.c_int32, ctypes.POINTER(PairResult),
@@ -401,6 +419,48 @@ class Context:
         if check:
             self._check(st)
         return st, out.as_dict(), changed.astype(bool)
+
+    def match(self, g: DeviceGraph, part, k, W, seed_l=0, check=True):
+        """Greedy matching of one level (fr_match); returns (status, pairs, mate as a device tensor)."""
+        import torch
+        mate = torch.empty(g.n, dtype=torch.int32, device=part.device)
+        pairs = ctypes.c_int32()
+        gc = g.c()
+        st = lib().fr_match(self.h, ctypes.byref(gc), _ptr(part), k, W, seed_l & 0xFFFFFFFFFFFFFFFF, _ptr(mate),
+                            ctypes.byref(pairs))
+        if check:
+            self._check(st)
+        return st, pairs.value, mate
+
+    def contract(self, g: DeviceGraph, mate, check=True):
+        """Contraction of a matching (fr_contract); returns (status, cmap, coarse arrays as numpy)."""
+        import torch
+        dev = mate.device
+        cmap = torch.empty(g.n, dtype=torch.int32, device=dev)
+        cx = torch.empty(g.n + 1, dtype=torch.int32, device=dev)
+        ca = torch.empty(max(g.nnz, 1), dtype=torch.int32, device=dev)
+        cw = torch.empty(max(g.nnz, 1), dtype=torch.int32, device=dev)
+        cv = torch.empty(g.n, dtype=torch.int32, device=dev)
+        cn, cnnz = ctypes.c_int32(), ctypes.c_int32()
+        gc = g.c()
+        st = lib().fr_contract(self.h, ctypes.byref(gc), _ptr(mate), _ptr(cmap), ctypes.byref(cn), ctypes.byref(cnnz),
+                               _ptr(cx), _ptr(ca), _ptr(cw), _ptr(cv))
+        if check:
+            self._check(st)
+        c, m = cn.value, cnnz.value
+        return st, cmap.cpu().numpy(), dict(n=c, nnz=m, xadj=cx[:c + 1].cpu().numpy(), adjncy=ca[:m].cpu().numpy(),
+                                            adjwgt=cw[:m].cpu().numpy(), vwgt=cv[:c].cpu().numpy())
+
+    def vcycle(self, g: DeviceGraph, part, k, eps, alpha, opts=None, max_levels=64, active_outer=0, check=True):
+        """One V-cycle with the given partition (fr_vcycle); returns (status, result dict)."""
+        res = VcycleResult()
+        gc = g.c()
+        o = opts if opts is not None else default_options()
+        st = lib().fr_vcycle(self.h, ctypes.byref(gc), _ptr(part), k, eps, alpha, ctypes.byref(o), max_levels,
+                             active_outer, ctypes.byref(res))
+        if check:
+            self._check(st)
+        return st, res.as_dict()
 
     def refine_batch_host(self, xadj, adjncy, adjwgt, vwgt, part, k, eps, alpha, opts=None, cap=0):
         """Host-buffer form: arrays are numpy or (pinned) CPU tensors; part is updated in place."""
