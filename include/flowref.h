@@ -314,7 +314,8 @@ fr_status fr_contract(fr_ctx *ctx, const fr_graph *g, const int32_t *mate, int32
 /* One V-cycle with the given partition (Section 5: no edge between two blocks is matched,
  * so part is the coarsest level's partition): contract with fr_match (seed_l =
  * splitmix64(opt->seed ^ level)) and fr_contract while the graph has more than
- * max(60 k, n / (60 k)) vertices, the matching is not empty and fewer than max_levels
+ * max(60 k, n / (60 k)) vertices, the matching holds at least n_level / 20 pairs (a
+ * level that would shrink by less than 5 % has stalled) and fewer than max_levels
  * (<= FR_MAX_LEVELS) levels exist; then from the coarsest level up, project the partition
  * and refine it with one fr_refine_batch sweep, or fr_refine_active with active_outer
  * outer rounds (each level with its own L_max).  part: DEVICE, updated in place,

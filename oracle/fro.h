@@ -66,7 +66,8 @@
  *   multilevel greedy matching in expansion*2 order (exact, c as max(c, 1); ties
  *              by a seeded splitmix64 key) inside blocks, ends at most 1.5 W/(20k);
  *              coarse ids in the order of the pairs' smaller fine ids; contract
- *              while n > max(60k, n0/(60k)); refine every level with its own L_max
+ *              while n > max(60k, n0/(60k)) and a matching holds >= n/20 pairs;
+ *              refine every level with its own L_max
  *   multi-try  per pair of a matching, the vertices with a neighbour in the other
  *              block, in splitmix64 order, visited round-robin over the pairs; a
  *              vertex no search of the pass queued that is still a boundary vertex
@@ -291,8 +292,8 @@ int32_t fro_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, cons
                      int32_t *cadjncy, int32_t *cadjwgt, int32_t *cvwgt);
 /* One V-cycle with the given partition (Section 5): contract level by level with
  * fro_match (seed_l = splitmix64(opt->seed ^ level)) while the graph has more than
- * max(60 k, n / (60 k)) vertices, a matching is non-empty and fewer than max_levels
- * levels exist; then from the coarsest level up, project and refine with one
+ * max(60 k, n / (60 k)) vertices, the matching holds at least n_level / 20 pairs and
+ * fewer than max_levels levels exist; then from the coarsest level up, project and refine with one
  * fro_refine_batch sweep (or fro_refine_active with active_outer outer rounds). */
 int32_t fro_vcycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                    const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha, const fro_options *opt,

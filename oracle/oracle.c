@@ -1606,7 +1606,9 @@ int32_t fro_refine_batch_mt(int32_t n, const int32_t *xadj, const int32_t *adjnc
  *            the order of its smaller fine id; coarse rows list their neighbours
  *            in increasing coarse id, parallel edges merged, the matched edge gone
  *   levels   contract while the graph has more than max(60 k, n / (60 k)) vertices,
- *            a level matches at least one edge, and fewer than max_levels levels
+ *            the level's matching holds at least n_level / 20 pairs (contraction
+ *            that shrinks a level by less than 5 % has stalled: the weight bound
+ *            keeps the heavy vertices single), and fewer than max_levels levels
  *            exist
  *   refine   on the coarsest level, then after each projection (part(v) =
  *            part(coarse vertex of v)), one sweep of fro_refine_batch, or
@@ -1782,7 +1784,7 @@ int32_t fro_vcycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const 
         int32_t *mate = XALLOC(int32_t, g->n);
         const int32_t pairs = ml_match(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, P[L - 1], k, W,
                                        fro_splitmix64(seed ^ (uint64_t)(L - 1)), mate);
-        if (pairs == 0) { free(mate); break; }
+        if (pairs == 0 || 20LL * pairs < g->n) { free(mate); break; }   /* stalled: under 5 % */
         cmap[L - 1] = XALLOC(int32_t, g->n);
         ml_contract(g, mate, &G[L], cmap[L - 1]);
         P[L] = XALLOC(int32_t, G[L].n);

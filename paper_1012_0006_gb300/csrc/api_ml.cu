@@ -221,7 +221,7 @@ extern "C" fr_status fr_vcycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, in
         const int l = (int)lv.size() - 1;
         int pairs = 0;
         st = match_level(ctx, &f.g, f.part, k, W, splitmix64(opt.seed ^ (unsigned long long)l), mate, s, &pairs);
-        if (st != FR_OK || pairs == 0) break;
+        if (st != FR_OK || pairs == 0 || 20LL * pairs < f.g.n) break;   // stalled: under 5 %
         const int n_f = f.g.n;
         const int nc_bound = n_f - pairs;
         int *cmap = pool.get<int>(n_f);

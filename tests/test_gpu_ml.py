@@ -142,3 +142,10 @@ def test_vcycle_checks(F, ctx):
     st, _ = ctx.vcycle(g, part, w["k"], w["eps"], w["alpha"], F.default_options(mt_alpha=10), check=False)
     assert st == F.FR_ERR_INVALID_ARG
     assert (part == before).all()
+
+
+def test_vcycle_stall_rule(F, ctx):
+    from tests.test_oracle_multilevel import _stars
+    for leaves in (25, 14):
+        r = _vcycle(F, ctx, _stars(40, leaves), dict(mb=0))
+        assert (r["levels"] == 1) == (leaves == 25)

@@ -178,7 +178,7 @@ def _rebuild(w, opts, max_levels, active_outer=0):
     while len(levels) < max_levels and levels[-1]["n"] > thr:
         g = levels[-1]
         pairs, mate = O.match(g, seed_l=splitmix64((opts.seed ^ (len(levels) - 1)) & M64), W=W)
-        if pairs == 0:
+        if pairs == 0 or 20 * pairs < g["n"]:
             break
         cmap, c = O.contract(g, mate)
         cp = np.empty(c["n"], np.int32)
@@ -217,12 +217,29 @@ def test_vcycle_rebuilt_from_its_steps(seed):
         assert cuts[-1] <= r["cut_before"]
 
 
+def _coarsest(w, levels, seed):
+    """The coarsest graph of a V-cycle's hierarchy, rebuilt from single steps."""
+    W = int(np.asarray(w["vwgt"], np.int64).sum())
+    g = dict(w, part=np.array(w["part"], np.int32))
+    for l in range(levels - 1):
+        _, mate = O.match(g, seed_l=splitmix64(seed ^ l), W=W)
+        cmap, c = O.contract(g, mate)
+        cp = np.empty(c["n"], np.int32)
+        cp[cmap] = g["part"]
+        g = dict(c, part=cp, k=w["k"], eps=w["eps"], alpha=w["alpha"])
+    return g
+
+
 def test_vcycle_stops_where_it_should():
     w = I.config(4, scale=1 / 64)   # 65,536 vertices, k = 64: threshold max(3840, 17) vertices
     st, part, r = O.vcycle(w, opts=O.options(mb=1))
     assert st == 0
     ns = r["level_n"]
-    assert all(n > 3840 for n in ns[:-1]) and (ns[-1] <= 3840 or r["levels"] == 64)
+    assert all(n > 3840 for n in ns[:-1])
+    if ns[-1] > 3840 and r["levels"] < 64:   # stalled: the next matching shrinks the level by under 5 %
+        g = _coarsest(w, r["levels"], 0)
+        pairs, _ = O.match(g, seed_l=splitmix64(r["levels"] - 1), W=int(np.asarray(w["vwgt"]).sum()))
+        assert 20 * pairs < ns[-1]
     assert r["cut_after"] < r["cut_before"]
 
 
@@ -240,3 +257,37 @@ def test_vcycle_threshold_is_strict():
         w = I.grid2d_halves(nx=nx, ny=ny, swaps=4)
         st, part, r = O.vcycle(w, max_levels=2)
         assert st == 0 and r["levels"] == want and r["level_n"][0] == nx * ny
+
+
+def _stars(s, leaves):
+    """s stars (hub + leaves, hub-leaf weight 2) whose hubs form a ring (weight 1); the
+    first half of the stars in block 0.  A matching pairs each hub with one leaf only."""
+    size = leaves + 1
+    n = s * size
+    rows = [[] for _ in range(n)]
+    for i in range(s):
+        hub = i * size
+        for j in range(1, size):
+            rows[hub].append((hub + j, 2))
+            rows[hub + j].append((hub, 2))
+        nxt = ((i + 1) % s) * size
+        rows[hub].append((nxt, 1))
+        rows[nxt].append((hub, 1))
+    xadj = np.zeros(n + 1, np.int32)
+    xadj[1:] = np.cumsum([len(r) for r in rows])
+    adj = np.array([u for r in rows for u, _ in sorted(r)], np.int32)
+    wgt = np.array([c for r in rows for _, c in sorted(r)], np.int32)
+    part = (np.arange(n) // size >= s // 2).astype(np.int32)
+    return dict(n=n, nnz=len(adj), xadj=xadj, adjncy=adj, adjwgt=wgt, vwgt=np.ones(n, np.int32), part=part, k=2,
+                eps=0.03, alpha=1.0, mb=0)
+
+
+def test_vcycle_stops_when_contraction_stalls():
+    # 26 vertices per star: a matching has s pairs, under n / 20: contraction has stalled
+    w = _stars(40, 25)
+    st, part, r = O.vcycle(w)
+    assert st == 0 and r["levels"] == 1 and O.match(w)[0] == 40
+    # 15 vertices per star: s pairs >= n / 20 on every level, so contraction goes on
+    w = _stars(40, 14)
+    st, part, r = O.vcycle(w)
+    assert st == 0 and r["levels"] > 5 and r["level_n"][1] == 600 - 40
