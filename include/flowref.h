@@ -152,6 +152,17 @@ typedef struct fr_vcycle_result {
     double refine_ms;                     /* projection and refinement, all levels */
 } fr_vcycle_result;
 
+/* One global search cycle (fr_cycle). */
+typedef struct fr_cycle_result {
+    int32_t coarsenings;                        /* matchings computed (stalled ones included) */
+    int32_t refinements;                        /* refinement sweeps run */
+    int32_t depth;                              /* levels of the deepest branch */
+    int32_t status;
+    int64_t cut_before, cut_after;
+    int32_t level_coarsenings[FR_MAX_LEVELS];   /* coarsenings of level-l graphs */
+    double ms;                                  /* host clock around the call (synchronised) */
+} fr_cycle_result;
+
 /* Totals of one multi-try FM pass (fr_multitry). */
 typedef struct fr_mt_result {
     int64_t gain;           /* cut decrease kept */
@@ -170,7 +181,7 @@ void fr_default_options(fr_options *opt);
 /* sizeof of the structs of this header, for bindings to check their layouts:
  * which = 0 fr_graph, 1 fr_options, 2 fr_pair_result, 3 fr_batch_result,
  * 4 fr_profile_info, 5 fr_server_config, 6 fr_request, 7 fr_response,
- * 8 fr_mt_result, 9 fr_vcycle_result; -1 for
+ * 8 fr_mt_result, 9 fr_vcycle_result, 10 fr_cycle_result; -1 for
  * any other value.  Needs no device. */
 int32_t fr_struct_size(int32_t which);
 
@@ -323,6 +334,20 @@ fr_status fr_contract(fr_ctx *ctx, const fr_graph *g, const int32_t *mate, int32
  * level.  opt->mt_alpha needs active_outer > 0. */
 fr_status fr_vcycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
                     const fr_options *opt, int32_t max_levels, int32_t active_outer, fr_vcycle_result *out);
+
+/* A global search cycle with the given partition (Section 5 and its pseudocode):
+ * type 0 V-cycle (the result of fr_vcycle), 1 W-cycle, 2 F-cycle, level split parameter
+ * d >= 1 (the paper's default is 2).  A cycle on a graph coarsens it (as fr_vcycle does),
+ * runs a cycle on the coarse graph, projects and refines; on levels l with l % d == 0 it
+ * then coarsens the refined graph again and repeats (a second trial) -- for F-cycles only
+ * while fewer than two coarsenings of level-l graphs were made in the run.  A graph that
+ * cannot be coarsened is refined and ends its branch.  The c-th coarsening of a level-l
+ * graph in the run uses seed_l = splitmix64(opt->seed ^ l ^ c << 32).  Every coarse
+ * graph lives only while its branch runs.  part: DEVICE, updated in place, unchanged on
+ * error. */
+fr_status fr_cycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
+                   const fr_options *opt, int32_t type, int32_t d, int32_t max_levels, int32_t active_outer,
+                   fr_cycle_result *out);
 
 /* Same as fr_refine_batch for a graph and partition in HOST memory: uploads the
  * arrays, refines, and copies part back (the end-to-end form; graph buffers are

@@ -65,6 +65,17 @@ class VcycleResult(ctypes.Structure):
                     level_cut=list(self.level_cut[:L]))
 
 
+class CycleResult(ctypes.Structure):
+    _fields_ = [("coarsenings", ctypes.c_int32), ("refinements", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("pad0", ctypes.c_int32), ("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64),
+                ("level_coarsenings", ctypes.c_int32 * 64)]
+
+    def as_dict(self):
+        return dict(coarsenings=self.coarsenings, refinements=self.refinements, depth=self.depth,
+                    cut_before=self.cut_before, cut_after=self.cut_after,
+                    level_coarsenings=list(self.level_coarsenings[:max(self.depth, 1)]))
+
+
 class FMResult(ctypes.Structure):
     _fields_ = [("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64), ("wA_after", ctypes.c_int64),
                 ("wB_after", ctypes.c_int64), ("tried", ctypes.c_int32), ("kept", ctypes.c_int32)]
@@ -160,6 +171,10 @@ def lib():
         L.fro_vcycle.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_double,
                                  ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32,
                                  ctypes.POINTER(VcycleResult)]
+        L.fro_cycle.restype = ctypes.c_int32
+        L.fro_cycle.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_double,
+                                ctypes.c_double, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(CycleResult)]
         L.fro_fm_pair.restype = ctypes.c_int32
         L.fro_fm_pair.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(FMResult), i32p,
@@ -495,4 +510,20 @@ def vcycle(w, opts=None, max_levels=64, active_outer=0, part=None, eps=None, alp
     res = VcycleResult()
     st = lib().fro_vcycle(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part), w["k"],
                           eps, alpha, ctypes.byref(opts), max_levels, active_outer, ctypes.byref(res))
+    return st, part, res.as_dict()
+
+
+CYCLES = {"V": 0, "W": 1, "F": 2}
+
+
+def cycle(w, kind="F", d=2, opts=None, max_levels=64, active_outer=0, part=None, eps=None, alpha=None):
+    """A global search cycle with the given partition (fro_cycle); returns (status, part, result dict)."""
+    part = np.array(w["part"] if part is None else part, np.int32, copy=True)
+    eps = w["eps"] if eps is None else eps
+    alpha = w["alpha"] if alpha is None else alpha
+    if opts is None:
+        opts = options(mb=w.get("mb", 0))
+    res = CycleResult()
+    st = lib().fro_cycle(w["n"], _p(w["xadj"]), _p(w["adjncy"]), _p(w["adjwgt"]), _p(w["vwgt"]), _p(part), w["k"],
+                         eps, alpha, ctypes.byref(opts), CYCLES[kind], d, max_levels, active_outer, ctypes.byref(res))
     return st, part, res.as_dict()

@@ -68,6 +68,10 @@
  *              coarse ids in the order of the pairs' smaller fine ids; contract
  *              while n > max(60k, n0/(60k)) and a matching holds >= n/20 pairs;
  *              refine every level with its own L_max
+ *   cycles     W: a second trial (a new coarsening of the refined graph) on every
+ *              level l % d == 0; F: also only while fewer than two coarsenings of
+ *              that level were made; the c-th coarsening of a level uses seed_l =
+ *              splitmix64(seed ^ l ^ c << 32); every graph is refined after each trial
  *   multi-try  per pair of a matching, the vertices with a neighbour in the other
  *              block, in splitmix64 order, visited round-robin over the pairs; a
  *              vertex no search of the pass queued that is still a boundary vertex
@@ -152,6 +156,16 @@ typedef struct fro_vcycle_result {
     int32_t level_pairs[FRO_MAX_LEVELS]; /* pair refinements run on each level */
     int64_t level_cut[FRO_MAX_LEVELS];   /* total cut after the level's refinement */
 } fro_vcycle_result;
+
+/* W-, F- (and V-) cycles with a given partition (fro_cycle). */
+typedef struct fro_cycle_result {
+    int32_t coarsenings;                       /* matchings computed (stalled ones included) */
+    int32_t refinements;                       /* refinement sweeps run */
+    int32_t depth;                             /* levels of the deepest branch */
+    int32_t pad0;
+    int64_t cut_before, cut_after;
+    int32_t level_coarsenings[FRO_MAX_LEVELS]; /* coarsenings of level-l graphs */
+} fro_cycle_result;
 
 /* Input checks of Section 2.1 (omega > 0, c >= 0, symmetric simple CSR, 0 <= part < k). */
 int32_t fro_validate(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
@@ -298,6 +312,13 @@ int32_t fro_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, cons
 int32_t fro_vcycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                    const int32_t *vwgt, int32_t *part, int32_t k, double eps, double alpha, const fro_options *opt,
                    int32_t max_levels, int32_t active_outer, fro_vcycle_result *out);
+
+/* A global search cycle with the given partition (Section 5): type 0 V-cycle (the same
+ * result as fro_vcycle), 1 W-cycle, 2 F-cycle, level split parameter d >= 1.  The c-th
+ * coarsening of a level-l graph uses seed_l = splitmix64(opt->seed ^ l ^ c << 32). */
+int32_t fro_cycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vwgt,
+                  int32_t *part, int32_t k, double eps, double alpha, const fro_options *opt, int32_t type, int32_t d,
+                  int32_t max_levels, int32_t active_outer, fro_cycle_result *out);
 
 /* Pair cut omega(E_ab) of the current partition. */
 int64_t fro_pair_cut(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,

@@ -1824,3 +1824,120 @@ int32_t fro_vcycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const 
     free(res);
     return st;
 }
+
+/* W- and F-cycles (Section 5, the global search pseudocode): a cycle on graph G
+ * coarsens G, runs a cycle on the coarse graph, projects and refines G; on levels that
+ * allow an independent trial it then coarsens G again (with a new seed, respecting the
+ * partition it has now), runs a second cycle on that graph, projects and refines G once
+ * more.  Readings (also in fro.h):
+ *   coarsest a graph that cannot be coarsened (at most max(60 k, n / (60 k)) vertices,
+ *            the level cap reached, or a stalled matching as in fro_vcycle) is refined
+ *            and ends the recursion; a V-cycle is the cycle without second trials
+ *   trials   W-cycle: a second trial on every level l with l % d == 0 (the level split
+ *            parameter); F-cycle: also only while fewer than two coarsenings of level-l
+ *            graphs have been made in the whole run; a second coarsening that stalls
+ *            skips the trial
+ *   seeds    the c-th coarsening of a level-l graph in the run (c = 0, 1, ...) uses
+ *            seed_l = splitmix64(seed ^ l ^ c << 32) (c = 0 gives fro_vcycle's seeds)
+ *   refine   one fro_refine_batch sweep, or fro_refine_active with active_outer rounds */
+
+typedef struct {
+    int32_t k, type, d, max_levels, active_outer;
+    double eps, alpha;
+    const fro_options *opt;
+    int64_t W, thr;
+    int32_t count[FRO_MAX_LEVELS];   /* coarsenings made per level */
+    fro_cycle_result *out;
+    int32_t st;
+} ml_run;
+
+static void ml_refine(ml_run *R, const ml_graph *g, int32_t *P) {
+    if (R->st != FRO_OK) return;
+    const int32_t cap = R->k * (R->k - 1) / 2 * (R->active_outer > 0 ? R->active_outer : 1);
+    fro_pair_result *res = XALLOC(fro_pair_result, cap > 0 ? cap : 1);
+    int32_t a = 0, b = 0;
+    if (R->active_outer > 0)
+        R->st = fro_refine_active(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, P, R->k, R->eps, R->alpha, R->opt,
+                                  R->active_outer, cap, res, &a, &b, NULL);
+    else
+        R->st = fro_refine_batch(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, P, R->k, R->eps, R->alpha, R->opt,
+                                 cap, res, &a, &b);
+    R->out->refinements += 1;
+    free(res);
+}
+
+/* One coarsening of (g, P) at level l; returns 0 if it stalled. */
+static int ml_coarsen(ml_run *R, int32_t l, const ml_graph *g, const int32_t *P, ml_graph *c, int32_t **cmap,
+                      int32_t **cP) {
+    if (l + 1 >= R->max_levels || g->n <= R->thr) return 0;
+    const uint64_t seed = R->opt ? R->opt->seed : 0;
+    const uint64_t sl = fro_splitmix64(seed ^ (uint64_t)l ^ ((uint64_t)(uint32_t)R->count[l] << 32));
+    R->count[l] += 1;
+    R->out->coarsenings += 1;
+    int32_t *mate = XALLOC(int32_t, g->n);
+    const int32_t pairs = ml_match(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, P, R->k, R->W, sl, mate);
+    if (pairs == 0 || 20LL * pairs < g->n) { free(mate); return 0; }
+    *cmap = XALLOC(int32_t, g->n);
+    ml_contract(g, mate, c, *cmap);
+    *cP = XALLOC(int32_t, c->n);
+    for (int32_t v = 0; v < g->n; ++v) (*cP)[(*cmap)[v]] = P[v];
+    free(mate);
+    return 1;
+}
+
+static void ml_cycle(ml_run *R, int32_t l, const ml_graph *g, int32_t *P) {
+    if (R->st != FRO_OK) return;
+    if (l + 1 > R->out->depth) R->out->depth = l + 1;
+    for (int32_t trial = 0; trial < 2; ++trial) {
+        if (trial == 1) {
+            if (l % R->d != 0 || R->type == 0) break;
+            if (R->type == 2 && R->count[l] >= 2) break;
+        }
+        ml_graph c;
+        int32_t *cmap = NULL, *cP = NULL;
+        if (!ml_coarsen(R, l, g, P, &c, &cmap, &cP)) {
+            if (trial == 0) ml_refine(R, g, P);   /* the coarsest graph of this branch */
+            break;
+        }
+        ml_cycle(R, l + 1, &c, cP);
+        for (int32_t v = 0; v < g->n; ++v) P[v] = cP[cmap[v]];
+        ml_refine(R, g, P);
+        ml_free(&c);
+        free(cmap); free(cP);
+    }
+}
+
+int32_t fro_cycle(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vwgt,
+                  int32_t *part, int32_t k, double eps, double alpha, const fro_options *opt, int32_t type, int32_t d,
+                  int32_t max_levels, int32_t active_outer, fro_cycle_result *out) {
+    memset(out, 0, sizeof(*out));
+    int32_t st = fro_validate(n, xadj, adjncy, adjwgt, vwgt, part, k);
+    if (st == FRO_OK && (!(eps > 0.0) || !(alpha >= 1.0) || type < 0 || type > 2 || d < 1 || max_levels < 1 ||
+                         max_levels > FRO_MAX_LEVELS || active_outer < 0 || bad_fm(opt) ||
+                         (opt && opt->mt_alpha < 0) || (bad_mt(opt) && active_outer == 0)))
+        st = FRO_ERR_INVALID_ARG;
+    if (st != FRO_OK) return st;
+    ml_run R;
+    memset(&R, 0, sizeof(R));
+    R.k = k; R.type = type; R.d = d; R.max_levels = max_levels; R.active_outer = active_outer;
+    R.eps = eps; R.alpha = alpha; R.opt = opt; R.out = out; R.st = FRO_OK;
+    R.W = fro_total_weight(n, vwgt);
+    R.thr = 60LL * k;
+    if ((int64_t)n / (60LL * k) > R.thr) R.thr = (int64_t)n / (60LL * k);
+    ml_graph g = { n, xadj[n], (int32_t *)xadj, (int32_t *)adjncy, (int32_t *)adjwgt, (int32_t *)vwgt };
+    int32_t *P = XALLOC(int32_t, n);
+    memcpy(P, part, sizeof(int32_t) * (size_t)n);
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j)
+            if (v < adjncy[j] && part[v] != part[adjncy[j]]) out->cut_before += adjwgt[j];
+    ml_cycle(&R, 0, &g, P);
+    if (R.st == FRO_OK) {
+        memcpy(part, P, sizeof(int32_t) * (size_t)n);
+        for (int32_t v = 0; v < n; ++v)
+            for (int32_t j = xadj[v]; j < xadj[v + 1]; ++j)
+                if (v < adjncy[j] && part[v] != part[adjncy[j]]) out->cut_after += adjwgt[j];
+        for (int32_t l = 0; l < FRO_MAX_LEVELS; ++l) out->level_coarsenings[l] = R.count[l];
+    }
+    free(P);
+    return R.st;
+}

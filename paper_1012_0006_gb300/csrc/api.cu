@@ -421,6 +421,7 @@ extern "C" int32_t fr_struct_size(int32_t which) {
     case 7: return (int32_t)sizeof(fr_response);
     case 8: return (int32_t)sizeof(fr_mt_result);
     case 9: return (int32_t)sizeof(fr_vcycle_result);
+    case 10: return (int32_t)sizeof(fr_cycle_result);
     default: return -1;
     }
 }

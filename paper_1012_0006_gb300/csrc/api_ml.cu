@@ -296,3 +296,160 @@ extern "C" fr_status fr_vcycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, in
     }
     return FR_OK;
 }
+
+// ------------------------------------------------------- W- and F-cycles ----
+
+namespace {
+
+struct CycleRun {
+    fr_ctx *ctx;
+    int k, type, d, max_levels, active_outer;
+    double eps, alpha;
+    fr_options opt;
+    long long W, thr;
+    int count[FR_MAX_LEVELS];
+    fr_cycle_result *out;
+    fr_status st;
+    MlScratch *s;
+    int *mate;
+};
+
+void cycle_refine(CycleRun &R, const fr_graph &g, int *part) {
+    if (R.st != FR_OK) return;
+    fr_batch_result summ;
+    fr_graph gg = g;
+    if (R.active_outer > 0)
+        R.st = fr_refine_active(R.ctx, &gg, part, R.k, R.eps, R.alpha, &R.opt, R.active_outer, 0, nullptr, &summ,
+                                nullptr);
+    else
+        R.st = fr_refine_batch(R.ctx, &gg, part, R.k, R.eps, R.alpha, &R.opt, 0, nullptr, &summ);
+    R.out->refinements += 1;
+}
+
+// One coarsening of (g, part) at level l into pool memory; false if it stalled (or failed).
+bool cycle_coarsen(CycleRun &R, int l, const fr_graph &g, const int *part, DevPool &pool, fr_graph &cg, int *&cmap,
+                   int *&cpart) {
+    fr_ctx *ctx = R.ctx;
+    if (l + 1 >= R.max_levels || g.n <= R.thr) return false;
+    const unsigned long long sl =
+        splitmix64(R.opt.seed ^ (unsigned long long)l ^ ((unsigned long long)(unsigned)R.count[l] << 32));
+    R.count[l] += 1;
+    R.out->coarsenings += 1;
+    int pairs = 0;
+    R.st = match_level(ctx, &g, part, R.k, R.W, sl, R.mate, *R.s, &pairs);
+    if (R.st != FR_OK || pairs == 0 || 20LL * pairs < g.n) return false;
+    const int nc_bound = g.n - pairs;
+    cmap = pool.get<int>(g.n);
+    int *cxadj = pool.get<int>((long long)nc_bound + 1);
+    int *cvwgt = pool.get<int>(nc_bound);
+    cpart = pool.get<int>(nc_bound);
+    if (!cmap || !cxadj || !cvwgt || !cpart) {
+        ctx_error(ctx, "cudaMalloc for a coarse graph failed");
+        R.st = FR_ERR_OOM;
+        return false;
+    }
+    int *cadj = nullptr, *cwgt = nullptr, cn = 0, cnnz = 0;
+    R.st = contract_level(ctx, &g, R.mate, cmap, *R.s, cxadj, &cadj, &cwgt, cvwgt, &cn, &cnnz,
+                          [&](int cnt) { return pool.get<int>(cnt); });
+    if (R.st != FR_OK) return false;
+    if (cn != nc_bound) {
+        ctx_error(ctx, "contraction gave %d vertices, expected %d", cn, nc_bound);
+        R.st = FR_ERR_INTERNAL;
+        return false;
+    }
+    cudaError_t e = launch_ml_down(g.n, cmap, part, cpart, ctx->stream);
+    if (e != cudaSuccess) {
+        R.st = cuda_fail(ctx, e, "launch_ml_down");
+        return false;
+    }
+    cg.n = cn; cg.nnz = cnnz; cg.xadj = cxadj; cg.adjncy = cadj; cg.adjwgt = cwgt; cg.vwgt = cvwgt;
+    return true;
+}
+
+void cycle_run(CycleRun &R, int l, const fr_graph &g, int *part) {
+    if (R.st != FR_OK) return;
+    R.out->depth = std::max(R.out->depth, l + 1);
+    for (int trial = 0; trial < 2; ++trial) {
+        if (trial == 1 && (R.type == 0 || l % R.d != 0 || (R.type == 2 && R.count[l] >= 2))) break;
+        DevPool pool;   // this trial's coarse graph, freed when the trial ends
+        fr_graph cg;
+        int *cmap = nullptr, *cpart = nullptr;
+        if (!cycle_coarsen(R, l, g, part, pool, cg, cmap, cpart)) {
+            if (R.st == FR_OK && trial == 0) cycle_refine(R, g, part);   // the coarsest graph of this branch
+            break;
+        }
+        cycle_run(R, l + 1, cg, cpart);
+        if (R.st != FR_OK) return;
+        cudaError_t e = launch_ml_up(g.n, cmap, cpart, part, R.ctx->stream);
+        if (e != cudaSuccess) {
+            R.st = cuda_fail(R.ctx, e, "launch_ml_up");
+            return;
+        }
+        cycle_refine(R, g, part);
+        cudaStreamSynchronize(R.ctx->stream);   // the pool is freed next
+    }
+}
+
+}  // namespace
+
+extern "C" fr_status fr_cycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, double alpha,
+                              const fr_options *opt_in, int32_t type, int32_t d, int32_t max_levels,
+                              int32_t active_outer, fr_cycle_result *out) {
+    if (!ctx) return FR_ERR_INVALID_ARG;
+    fr_options opt;
+    if (opt_in) opt = *opt_in; else fr_default_options(&opt);
+    fr_cycle_result local;
+    fr_cycle_result *o = out ? out : &local;
+    memset(o, 0, sizeof(*o));
+    fr_status st = check_graph(ctx, g, part, k);
+    if (st == FR_OK) st = check_params(ctx, eps, alpha, &opt);
+    if (st == FR_OK && (type < 0 || type > 2 || d < 1 || max_levels < 1 || max_levels > FR_MAX_LEVELS ||
+                        active_outer < 0 || (opt.mt_alpha != 0 && active_outer == 0))) {
+        ctx_error(ctx, "fr_cycle: type 0-2, d >= 1, max_levels in [1, %d], active_outer >= 0, mt_alpha only with "
+                  "active_outer", FR_MAX_LEVELS);
+        st = FR_ERR_INVALID_ARG;
+    }
+    if (st != FR_OK) { o->status = st; return st; }
+    CK(cudaSetDevice(ctx->device));
+    release_corridor(ctx);
+    st = ensure_base(ctx, g->n, g->nnz, k, opt.mb_reps);
+    PrepOut po;
+    if (st == FR_OK) st = run_prep(ctx, g, part, k, false, opt.checked != 0, &po);
+    if (st != FR_OK) { o->status = st; return st; }
+    const auto t0 = std::chrono::steady_clock::now();
+    DevPool pool;
+    MlScratch s;
+    int *backup = pool.get<int>(g->n);
+    int *mate = pool.get<int>(g->n);
+    if (!backup || !mate || !s.make(pool, g->n)) {
+        ctx_error(ctx, "cudaMalloc for the cycle scratch failed");
+        o->status = FR_ERR_OOM;
+        return FR_ERR_OOM;
+    }
+    CK(cudaMemcpyAsync(backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CycleRun R;
+    memset(&R, 0, sizeof(R));
+    R.ctx = ctx; R.k = k; R.type = type; R.d = d; R.max_levels = max_levels; R.active_outer = active_outer;
+    R.eps = eps; R.alpha = alpha; R.opt = opt; R.W = po.W;
+    R.thr = std::max(60LL * k, (long long)g->n / (60LL * k));
+    R.out = o; R.st = FR_OK; R.s = &s; R.mate = mate;
+    cycle_run(R, 0, *g, part);
+    cudaStreamSynchronize(ctx->stream);
+    destroy_graph_cache(ctx);   // captured sweeps of coarse graphs point into freed memory
+    st = R.st;
+    if (st != FR_OK) {
+        cudaMemcpyAsync(part, backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        o->status = st;
+        return st;
+    }
+    PrepOut pa;
+    st = run_prep(ctx, g, part, k, false, false, &pa);
+    if (st != FR_OK) { o->status = st; return st; }
+    o->status = FR_OK;
+    o->cut_before = po.totcut;
+    o->cut_after = pa.totcut;
+    for (int l = 0; l < FR_MAX_LEVELS; ++l) o->level_coarsenings[l] = R.count[l];
+    o->ms = ms_since(t0);
+    return FR_OK;
+}

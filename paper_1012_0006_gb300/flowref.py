@@ -78,6 +78,17 @@ class VcycleResult(ctypes.Structure):
                     level_cut=list(self.level_cut[:L]), coarsen_ms=self.coarsen_ms, refine_ms=self.refine_ms)
 
 
+class CycleResult(ctypes.Structure):
+    _fields_ = [("coarsenings", ctypes.c_int32), ("refinements", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("cut_before", ctypes.c_int64), ("cut_after", ctypes.c_int64),
+                ("level_coarsenings", ctypes.c_int32 * 64), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(coarsenings=self.coarsenings, refinements=self.refinements, depth=self.depth,
+                    status=self.status, cut_before=self.cut_before, cut_after=self.cut_after,
+                    level_coarsenings=list(self.level_coarsenings[:max(self.depth, 1)]), ms=self.ms)
+
+
 class MtResult(ctypes.Structure):
     _fields_ = [("gain", ctypes.c_int64), ("searches", ctypes.c_int32), ("tried", ctypes.c_int32),
                 ("kept", ctypes.c_int32), ("status", ctypes.c_int32)]
@@ -169,6 +180,9 @@ SYMBOLS = {
                                    ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp]),
     "fr_vcycle": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(VcycleResult)]),
+    "fr_cycle": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.POINTER(CycleResult)]),
     "fr_refine_batch_host": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_int32,
                                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(Options),
                                             ctypes.c_int32, ctypes.POINTER(PairResult),
@@ -458,6 +472,19 @@ class Context:
         o = opts if opts is not None else default_options()
         st = lib().fr_vcycle(self.h, ctypes.byref(gc), _ptr(part), k, eps, alpha, ctypes.byref(o), max_levels,
                              active_outer, ctypes.byref(res))
+        if check:
+            self._check(st)
+        return st, res.as_dict()
+
+    def cycle(self, g: DeviceGraph, part, k, eps, alpha, kind="F", d=2, opts=None, max_levels=64, active_outer=0,
+              check=True):
+        """A global search cycle with the given partition (fr_cycle; kind V, W or F);
+        returns (status, result dict)."""
+        res = CycleResult()
+        gc = g.c()
+        o = opts if opts is not None else default_options()
+        st = lib().fr_cycle(self.h, ctypes.byref(gc), _ptr(part), k, eps, alpha, ctypes.byref(o),
+                            {"V": 0, "W": 1, "F": 2}[kind], d, max_levels, active_outer, ctypes.byref(res))
         if check:
             self._check(st)
         return st, res.as_dict()

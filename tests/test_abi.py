@@ -72,7 +72,7 @@ def test_struct_layouts_match_the_header(built):
     """The binding's ctypes structs have the sizes the compiled library uses."""
     F = built
     structs = [F.Graph, F.Options, F.PairResult, F.BatchResult, F.ProfileInfo, F.ServerConfig, F.Request,
-               F.Response, F.MtResult, F.VcycleResult]
+               F.Response, F.MtResult, F.VcycleResult, F.CycleResult]
     for i, st in enumerate(structs):
         assert F.lib().fr_struct_size(i) == ctypes.sizeof(st), st.__name__
     assert F.lib().fr_struct_size(len(structs)) == -1

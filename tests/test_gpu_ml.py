@@ -149,3 +149,31 @@ def test_vcycle_stall_rule(F, ctx):
     for leaves in (25, 14):
         r = _vcycle(F, ctx, _stars(40, leaves), dict(mb=0))
         assert (r["levels"] == 1) == (leaves == 25)
+
+
+def _cycle(F, ctx, w, kind, d, okw, active_outer=0):
+    st, pref, rref = O.cycle(w, kind, d=d, opts=O.options(**okw), active_outer=active_outer)
+    assert st == 0
+    g, part = _dev(F, w)
+    st, r = ctx.cycle(g, part, w["k"], w["eps"], w["alpha"], kind=kind, d=d, opts=F.default_options(**okw),
+                      active_outer=active_outer)
+    for f in ("coarsenings", "refinements", "depth", "cut_before", "cut_after", "level_coarsenings"):
+        assert r[f] == rref[f], (kind, f)
+    assert np.array_equal(part.cpu().numpy(), pref)
+    return r
+
+
+@pytest.mark.parametrize("seed", [15200, 15204, 15213, 15214])   # seeded graphs of 1,600-2,700 vertices
+def test_cycles_random_small(F, ctx, seed):
+    w = I.random_small(seed, n_max=3000, k_max=5)
+    for kind, d in (("V", 2), ("W", 2), ("F", 2), ("F", 1)):
+        _cycle(F, ctx, w, kind, d, dict(mb=seed % 2, seed=seed))
+
+
+def test_cycles_workload(F, ctx):
+    w = I.config(4, scale=1 / 64)
+    rv = _cycle(F, ctx, w, "V", 2, dict(mb=1, seed=2))
+    rf = _cycle(F, ctx, w, "F", 2, dict(mb=1, seed=2))
+    assert rf["coarsenings"] > rv["coarsenings"]
+    _cycle(F, ctx, I.random_small(15300, n_max=2000, k_max=4), "W", 1, dict(mb=1, fm_permille=50, mt_alpha=10),
+           active_outer=2)

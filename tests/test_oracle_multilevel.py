@@ -291,3 +291,92 @@ def test_vcycle_stops_when_contraction_stalls():
     w = _stars(40, 14)
     st, part, r = O.vcycle(w)
     assert st == 0 and r["levels"] > 5 and r["level_n"][1] == 600 - 40
+
+
+def _cycle_rebuild(w, kind, d, opts, max_levels=64):
+    """The global search cycles of Section 5 written out from single matchings,
+    contractions and sweeps, following the pseudocode's recursion."""
+    k = w["k"]
+    W = int(np.asarray(w["vwgt"], np.int64).sum())
+    thr = max(60 * k, w["n"] // (60 * k))
+    count = [0] * 64
+    stats = dict(coarsenings=0, refinements=0)
+
+    def refine(g, part):
+        st, part, _, _ = O.refine_batch(g, part=part, opts=opts)
+        assert st == 0
+        stats["refinements"] += 1
+        return part
+
+    def coarsen(l, g, part):
+        if l + 1 >= max_levels or g["n"] <= thr:
+            return None
+        sl = splitmix64((opts.seed ^ l ^ (count[l] << 32)) & M64)
+        count[l] += 1
+        stats["coarsenings"] += 1
+        pairs, mate = O.match(g, seed_l=sl, part=part, W=W)
+        if pairs == 0 or 20 * pairs < g["n"]:
+            return None
+        cmap, c = O.contract(g, mate)
+        cp = np.empty(c["n"], np.int32)
+        cp[cmap] = part
+        return dict(c, k=k, eps=w["eps"], alpha=w["alpha"]), cmap, cp
+
+    def cyc(l, g, part):
+        for trial in (0, 1):
+            if trial == 1 and (kind == "V" or l % d or (kind == "F" and count[l] >= 2)):
+                break
+            r = coarsen(l, g, part)
+            if r is None:
+                if trial == 0:
+                    part = refine(g, part)
+                break
+            c, cmap, cp = r
+            part = refine(g, cyc(l + 1, c, cp)[cmap])
+        return part
+
+    part = cyc(0, dict(w), np.array(w["part"], np.int32))
+    return part, stats, count
+
+
+@pytest.mark.parametrize("seed", [15200, 15204, 15213, 15214, 15240])   # 1,600-2,700 vertices
+def test_cycles_rebuilt_from_their_steps(seed):
+    w = I.random_small(seed, n_max=3000, k_max=5)
+    opts = O.options(mb=seed % 2, seed=seed)
+    for kind, d in (("V", 2), ("W", 2), ("W", 1), ("F", 2), ("F", 1)):
+        st, part, r = O.cycle(w, kind, d=d, opts=opts)
+        assert st == 0
+        want, stats, count = _cycle_rebuild(w, kind, d, opts)
+        assert np.array_equal(part, want), (kind, d)
+        assert (r["coarsenings"], r["refinements"]) == (stats["coarsenings"], stats["refinements"])
+        assert r["level_coarsenings"] == count[:len(r["level_coarsenings"])]
+        assert r["cut_after"] == _cut(w, part) <= r["cut_before"]
+    # the V-cycle of the recursion is fro_vcycle
+    st, pv, rv = O.vcycle(w, opts=opts)
+    st, pc, rc = O.cycle(w, "V", opts=opts)
+    assert np.array_equal(pv, pc) and rv["cut_after"] == rc["cut_after"]
+
+
+def test_cycle_trial_counts():
+    # 64x64 grid, k = 2: threshold 120, six contractions of about half each, no stalls
+    w = I.grid2d_halves(nx=64, ny=64, swaps=200)
+    st, _, rv = O.cycle(w, "V")
+    L = rv["depth"]
+    assert rv["level_coarsenings"][:L - 1] == [1] * (L - 1)
+    st, _, rw = O.cycle(w, "W", d=1)
+    # W with d = 1: every call above the coarsest levels coarsens twice, so level l is
+    # coarsened 2^(l+1) times (near the bottom some branches end a level earlier)
+    top = L - 3
+    assert rw["level_coarsenings"][:top] == [2 ** (l + 1) for l in range(top)]
+    assert all(c <= 2 ** (l + 1) for l, c in enumerate(rw["level_coarsenings"]))
+    st, _, rf = O.cycle(w, "F", d=1)
+    # F with d = 1: the second trial happens once per level and level l is reached by
+    # l + 1 calls, so it is coarsened l + 2 times
+    assert rf["level_coarsenings"][:top] == [l + 2 for l in range(top)]
+    assert rw["cut_after"] <= rv["cut_before"] and rf["cut_after"] <= rv["cut_before"]
+
+
+def test_cycle_option_checks():
+    w = I.random_small(15100, n_max=200)
+    st, *_ = O.cycle(w, "W", d=0)
+    assert st == 1
