@@ -504,10 +504,21 @@ def multilevel(F, ctx, g, part0, w, reps=2):
         torch.cuda.synchronize()
         if _ > 0:
             best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
-    return {"workload": "bench workload and partition, one V-cycle, one sweep per level",
-            "ms": round(best, 2), "levels": r["levels"], "level_n": r["level_n"], "level_pairs": r["level_pairs"],
-            "coarsen_ms": round(r["coarsen_ms"], 2), "refine_ms": round(r["refine_ms"], 2),
-            "cut_before": r["cut_before"], "cut_after": r["cut_after"], "cut_after_flat_sweep": flat["cut_after"]}
+    out = {"workload": "bench workload and partition, one V-cycle, one sweep per level",
+           "ms": round(best, 2), "levels": r["levels"], "level_n": r["level_n"], "level_pairs": r["level_pairs"],
+           "coarsen_ms": round(r["coarsen_ms"], 2), "refine_ms": round(r["refine_ms"], 2),
+           "cut_before": r["cut_before"], "cut_after": r["cut_after"], "cut_after_flat_sweep": flat["cut_after"]}
+    # the F- and W-cycles of Section 5 (level split parameter 2), one run each
+    for kind in ("F", "W"):
+        part.copy_(part0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, c = ctx.cycle(g, part, w["k"], w["eps"], w["alpha"], kind=kind, d=2, opts=opts)
+        e1.record()
+        torch.cuda.synchronize()
+        out[kind + "_cycle"] = {"ms": round(e0.elapsed_time(e1), 2), "coarsenings": c["coarsenings"],
+                                "refinements": c["refinements"], "cut_after": c["cut_after"]}
+    return out
 
 
 def fm_sweeps(F, ctx, g, part0, w, reps=3):
