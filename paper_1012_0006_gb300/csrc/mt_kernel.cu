@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(kMtTPB) mt_sort_kernel(MtDev m, Ctl *ctl) {
 // connection weight, ties to the smaller splitmix64(tseed ^ u << 32 ^ P), then the
 // smaller P.  False if u has no neighbour outside its block.  Up to 8 blocks around u
 // are summed in registers; more fall back to summing each block over the adjacency.
-__device__ bool mt_gain(const GraphDev &G, int u, unsigned long long tseed, int &gain, int &to) {
+// (pu, j0, j1: u's block and adjacency range, loaded by the caller)
+__device__ bool mt_gain(const GraphDev &G, int u, int pu, int j0, int j1, unsigned long long tseed, int &gain,
+                        int &to) {
     constexpr int T = 8;
-    const int pu = G.part[u];
-    const int j0 = __ldg(G.xadj + u), j1 = __ldg(G.xadj + u + 1);
     int tb[T], tw[T];
 #pragma unroll
     for (int s = 0; s < T; ++s) { tb[s] = -1; tw[s] = 0; }
@@ -213,6 +213,10 @@ __device__ bool mt_gain(const GraphDev &G, int u, unsigned long long tseed, int 
     gain = bw - own;
     to = best;
     return true;
+}
+
+__device__ __forceinline__ bool mt_gain(const GraphDev &G, int u, unsigned long long tseed, int &gain, int &to) {
+    return mt_gain(G, u, G.part[u], __ldg(G.xadj + u), __ldg(G.xadj + u + 1), tseed, gain, to);
 }
 
 // KaSPar rule in the oracle's order of rounded double operations.
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
             int nm = 0, best_len = 0, pc = 0;
             while (!bad) {
                 // pop the highest current entry
-                int x = -1, g = 0;
+                int x = -1, g = 0, xto = 0, xfrom = 0, xc = 0, xy0 = 0, xy1 = 0;
                 for (;;) {
                     int hb = -1;
                     for (int k2 = 1; k2 >= 0; --k2) {
@@ -355,30 +359,43 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
                     const unsigned has = __ballot_sync(kFull, hb >= 0);
                     if (!has) break;
                     const int b = __shfl_sync(kFull, hb, 31 - __clz(has));
-                    int got = -1;
+                    int got = -1, gto = 0, gfrom = 0, gc = 0, gy0 = 0, gy1 = 0;
                     if (lane == 0) {
                         const int e = S.top[b];
                         if (e < 0 || e >= nxt) {   // (never: a set bit has a pushed top entry)
                             S.top[b] = -1;
                             S.bits[b >> 5] &= ~(1u << (b & 31));
                         } else {
-                            const int xv = m.ent_v[e], below = m.ent_below[e];
+                            const int xv = m.ent_v[e], below = m.ent_below[e], ev = m.ent_ver[e];
+                            // the vertex's state, loaded together with its version
+                            const int vv = m.ver[xv], tg = m.tgt[xv], pf = G.part[xv];
+                            const int cw = __ldg(G.vwgt + xv), a0 = __ldg(G.xadj + xv), a1 = __ldg(G.xadj + xv + 1);
                             S.top[b] = below;
                             if (below < 0) S.bits[b >> 5] &= ~(1u << (b & 31));
-                            if (m.ent_ver[e] == m.ver[xv]) {   // current: it leaves the queue
+                            if (ev == vv) {   // current: it leaves the queue
                                 got = xv;
-                                m.ver[xv] = m.ver[xv] + 1;
+                                m.ver[xv] = vv + 1;
+                                gto = tg; gfrom = pf; gc = cw; gy0 = a0; gy1 = a1;
                             }
                         }
                     }
                     got = __shfl_sync(kFull, got, 0);
                     __syncwarp();
-                    if (got >= 0) { x = got; g = b - kMtGmax; break; }
+                    if (got >= 0) {
+                        x = got;
+                        g = b - kMtGmax;
+                        xto = __shfl_sync(kFull, gto, 0);
+                        xfrom = __shfl_sync(kFull, gfrom, 0);
+                        xc = __shfl_sync(kFull, gc, 0);
+                        xy0 = __shfl_sync(kFull, gy0, 0);
+                        xy1 = __shfl_sync(kFull, gy1, 0);
+                        break;
+                    }
                 }
                 if (x < 0) break;   // the queue is empty
-                const int to = m.tgt[x];
-                const int from = G.part[x];
-                const long long cx = __ldg(G.vwgt + x);
+                const int to = xto;
+                const int from = xfrom;
+                const long long cx = xc;
                 if (S.bw[to] + cx > Lmax) continue;   // would overload the target: not moved
                 if (lane == 0) {
                     G.part[x] = to;
@@ -392,16 +409,19 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
                 delta -= g;
                 __syncwarp();
                 // key the neighbours again, 32 at a time in CSR order
-                const int y0 = __ldg(G.xadj + x), y1 = __ldg(G.xadj + x + 1);
+                const int y0 = xy0, y1 = xy1;
                 for (int jb = y0; jb < y1; jb += 32) {
                     const int jj = jb + lane;
                     const int u = jj < y1 ? __ldg(G.adjncy + jj) : -1;
                     bool elig = false, push = false;
                     int gu = 0, tu = -1;
-                    if (u >= 0 && !m.mvd[u]) {
-                        const int tc = m.tch[u];
-                        elig = tc == 0 || tc == sid;
-                        if (elig) push = mt_gain(G, u, tseed, gu, tu);
+                    if (u >= 0) {
+                        // u's marks, block and adjacency range, loaded together
+                        const unsigned char mv = m.mvd[u];
+                        const int tc = m.tch[u], pu = G.part[u];
+                        const int u0 = __ldg(G.xadj + u), u1 = __ldg(G.xadj + u + 1);
+                        elig = !mv && (tc == 0 || tc == sid);
+                        if (elig) push = mt_gain(G, u, pu, u0, u1, tseed, gu, tu);
                     }
                     const bool range = __all_sync(kFull, !push || (gu >= -kMtGmax && gu <= kMtGmax));
                     const unsigned pm = __ballot_sync(kFull, push);
