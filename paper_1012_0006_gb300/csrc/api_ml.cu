@@ -262,19 +262,22 @@ extern "C" fr_status fr_vcycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, in
             if (e != cudaSuccess) { st = cuda_fail(ctx, e, "launch_ml_up"); break; }
         }
         fr_batch_result summ;
+        // coarse graphs live only during this call: their sweeps launch directly instead
+        // of being captured into the context's graph cache
+        const bool graphs = ctx->use_graphs;
+        if (l > 0) ctx->use_graphs = false;
         if (active_outer > 0)
             st = fr_refine_active(ctx, &lv[l].g, lv[l].part, k, eps, alpha, &opt, active_outer, 0, nullptr, &summ,
                                   nullptr);
         else
             st = fr_refine_batch(ctx, &lv[l].g, lv[l].part, k, eps, alpha, &opt, 0, nullptr, &summ);
+        ctx->use_graphs = graphs;
         if (st != FR_OK) break;
         lpairs[l] = summ.npairs;
         lcut[l] = summ.cut_after;
     }
     cudaStreamSynchronize(ctx->stream);
     const double refine_ms = ms_since(t1);
-    // captured sweeps of the coarse levels point into memory freed below
-    destroy_graph_cache(ctx);
     if (st != FR_OK) {
         cudaMemcpyAsync(part, backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
@@ -314,15 +317,19 @@ struct CycleRun {
     int *mate;
 };
 
-void cycle_refine(CycleRun &R, const fr_graph &g, int *part) {
+void cycle_refine(CycleRun &R, int l, const fr_graph &g, int *part) {
     if (R.st != FR_OK) return;
     fr_batch_result summ;
     fr_graph gg = g;
+    // coarse graphs live only while their branch runs: their sweeps launch directly
+    const bool graphs = R.ctx->use_graphs;
+    if (l > 0) R.ctx->use_graphs = false;
     if (R.active_outer > 0)
         R.st = fr_refine_active(R.ctx, &gg, part, R.k, R.eps, R.alpha, &R.opt, R.active_outer, 0, nullptr, &summ,
                                 nullptr);
     else
         R.st = fr_refine_batch(R.ctx, &gg, part, R.k, R.eps, R.alpha, &R.opt, 0, nullptr, &summ);
+    R.ctx->use_graphs = graphs;
     R.out->refinements += 1;
 }
 
@@ -375,7 +382,7 @@ void cycle_run(CycleRun &R, int l, const fr_graph &g, int *part) {
         fr_graph cg;
         int *cmap = nullptr, *cpart = nullptr;
         if (!cycle_coarsen(R, l, g, part, pool, cg, cmap, cpart)) {
-            if (R.st == FR_OK && trial == 0) cycle_refine(R, g, part);   // the coarsest graph of this branch
+            if (R.st == FR_OK && trial == 0) cycle_refine(R, l, g, part);   // the coarsest graph of this branch
             break;
         }
         cycle_run(R, l + 1, cg, cpart);
@@ -385,7 +392,7 @@ void cycle_run(CycleRun &R, int l, const fr_graph &g, int *part) {
             R.st = cuda_fail(R.ctx, e, "launch_ml_up");
             return;
         }
-        cycle_refine(R, g, part);
+        cycle_refine(R, l, g, part);
         cudaStreamSynchronize(R.ctx->stream);   // the pool is freed next
     }
 }
@@ -435,7 +442,6 @@ extern "C" fr_status fr_cycle(fr_ctx *ctx, const fr_graph *g, int32_t *part, int
     R.out = o; R.st = FR_OK; R.s = &s; R.mate = mate;
     cycle_run(R, 0, *g, part);
     cudaStreamSynchronize(ctx->stream);
-    destroy_graph_cache(ctx);   // captured sweeps of coarse graphs point into freed memory
     st = R.st;
     if (st != FR_OK) {
         cudaMemcpyAsync(part, backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream);
