@@ -318,7 +318,8 @@ fr_status fr_match(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t 
  * its members; rows list the coarse neighbours by increasing id, parallel edges merged
  * with summed weights, the matched edge dropped.  All arrays DEVICE: cmap[n]; coarse
  * xadj / adjncy / adjwgt / vwgt with room for n + 1, nnz, nnz and n entries.  *cn, *cnnz
- * (HOST): coarse sizes. */
+ * (HOST): coarse sizes.  FR_ERR_INVALID_ARG unless every mate entry is -1 or a partner
+ * u != v in range with mate[u] = v (checked on the device first). */
 fr_status fr_contract(fr_ctx *ctx, const fr_graph *g, const int32_t *mate, int32_t *cmap, int32_t *cn, int32_t *cnnz,
                       int32_t *cxadj, int32_t *cadjncy, int32_t *cadjwgt, int32_t *cvwgt);
 

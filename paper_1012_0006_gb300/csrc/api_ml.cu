@@ -168,6 +168,16 @@ extern "C" fr_status fr_contract(fr_ctx *ctx, const fr_graph *g, const int32_t *
         ctx_error(ctx, "cudaMalloc for the contraction scratch failed");
         return FR_ERR_OOM;
     }
+    // a caller's matching is checked first: the contraction indexes by it
+    int *h = reinterpret_cast<int *>(ctx->h_stage + 8192);
+    CK(cudaMemsetAsync(s.flags, 0, sizeof(int), ctx->stream));
+    CK(launch_ml_check(g->n, mate, s.flags, ctx->stream));
+    CK(cudaMemcpyAsync(h, s.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h[0]) {
+        ctx_error(ctx, "fr_contract: mate is not a matching (entries must be -1 or partners pointing back)");
+        return FR_ERR_INVALID_ARG;
+    }
     int *adj = cadjncy, *wgt = cadjwgt;
     return contract_level(ctx, g, mate, cmap, s, cxadj, &adj, &wgt, cvwgt, cn, cnnz,
                           [](int) -> int * { return nullptr; });

@@ -313,6 +313,15 @@ __global__ void __launch_bounds__(32 * kMlRowWarps) ml_rows_kernel(MlGraph g, in
     }
 }
 
+// *bad = 1 unless mate is a matching: every entry -1 or a partner in range that points back.
+__global__ void __launch_bounds__(kMlTPB) ml_check_kernel(int n, const int *mate, int *bad) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int m = mate[v];
+        if (m == -1) continue;
+        if (m < 0 || m >= n || m == v || mate[m] != v) *bad = 1;
+    }
+}
+
 __global__ void __launch_bounds__(kMlTPB) ml_down_kernel(int n, const int *cmap, const int *part, int *cpart) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) cpart[cmap[v]] = part[v];
 }
@@ -372,6 +381,11 @@ cudaError_t launch_ml_rows(const MlGraph &g, int nc, const int *mate, const int 
     const int grid = (int)(b > 8192 ? 8192 : b);
     ml_rows_kernel<<<grid, 32 * kMlRowWarps, 0, st>>>(g, nc, mate, cmap, crep, rowcap, count ? 1 : 0, cdeg, cxadj,
                                                        cadj, cwgt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ml_check(int n, const int *mate, int *bad, cudaStream_t st) {
+    ml_check_kernel<<<ml_grid(n), kMlTPB, 0, st>>>(n, mate, bad);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ cudaError_t launch_ml_cmap(const MlGraph &g, const int *mate, const int *cid, in
 cudaError_t launch_ml_rows(const MlGraph &g, int nc, const int *mate, const int *cmap, const int *crep,
                            const int *rowcap, bool count, int *cdeg, const int *cxadj, int *cadj, int *cwgt,
                            cudaStream_t st);
+// *bad = 1 unless mate is a matching (entries -1 or in-range partners pointing back).
+cudaError_t launch_ml_check(int n, const int *mate, int *bad, cudaStream_t st);
 // cpart[cmap[v]] = part[v]  /  part[v] = cpart[cmap[v]].
 cudaError_t launch_ml_down(int n, const int *cmap, const int *part, int *cpart, cudaStream_t st);
 cudaError_t launch_ml_up(int n, const int *cmap, const int *cpart, int *part, cudaStream_t st);

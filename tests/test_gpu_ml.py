@@ -177,3 +177,15 @@ def test_cycles_workload(F, ctx):
     assert rf["coarsenings"] > rv["coarsenings"]
     _cycle(F, ctx, I.random_small(15300, n_max=2000, k_max=4), "W", 1, dict(mb=1, fm_permille=50, mt_alpha=10),
            active_outer=2)
+
+
+def test_contract_rejects_a_non_matching(F, ctx):
+    import torch
+    w = I.random_small(14500, n_max=500, k_max=3)
+    g, _ = _dev(F, w)
+    n = w["n"]
+    for bad in ([1, 2, 0], [0], [n]):   # not pointing back, a self loop, out of range
+        mate = np.full(n, -1, np.int32)
+        mate[:len(bad)] = bad
+        st, _, _ = ctx.contract(g, torch.as_tensor(mate).cuda(), check=False)
+        assert st == F.FR_ERR_INVALID_ARG
