@@ -303,6 +303,9 @@ fr_status fr_multitry(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, 
                       int8_t *changed);
 
 /* ---- multilevel V-cycle with a given partition (Sections 2.1, 2.2, 5) ---- */
+/* These calls allocate their scratch and the coarse graphs with cudaMalloc for the length
+ * of the call (about twice the input graph for a V-cycle, the current branch for W- and
+ * F-cycles), outside the context's arena bound; FR_ERR_OOM if an allocation fails. */
 
 /* Greedy matching of one level: the edges inside one block of part whose ends both weigh
  * at most 1.5 W / (20 k) (40 k c(v) <= 3 W), ordered by expansion*2 = omega^2 / (c(u) c(v))
