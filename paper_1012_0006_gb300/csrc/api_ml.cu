@@ -51,7 +51,7 @@ struct MlScratch {
         crep = pool.get<int>(n);
         rowcap = pool.get<int>(n);
         cdeg = pool.get<int>(n);
-        tmp = pool.get<int>((long long)(n + 1023) / 1024 + 2);
+        tmp = pool.get<int>(((long long)n + 1023) / 1024 + 2);
         flags = pool.get<int>(2);
         return cand && isrep && cid && crep && rowcap && cdeg && tmp && flags;
     }

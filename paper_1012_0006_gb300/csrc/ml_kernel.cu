@@ -355,7 +355,7 @@ cudaError_t launch_ml_finish(int n, int *mate, int *pairs, cudaStream_t st) {
 
 cudaError_t launch_ml_scan(const int *in, int *out, int n, int *tmp, cudaStream_t st) {
     if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), st);
-    const int nb = (n + 1023) / 1024;
+    const int nb = (int)(((long long)n + 1023) / 1024);
     ml_scan_a<<<nb, kMlTPB, 0, st>>>(in, out, n, tmp);
     ml_scan_b<<<1, kMlTPB, 0, st>>>(tmp, nb);
     ml_scan_c<<<nb, kMlTPB, 0, st>>>(out, n, tmp);
