@@ -122,3 +122,56 @@ def test_pair_parallel_sweep_stops_after_max_rounds():
     assert all(r["round"] == 0 for r in res)
     _, pseq, rseq, _ = O.refine_batch(w, opts=opts)
     assert res == rseq[:done]
+
+
+def _colours(edges):
+    used, col = {}, {}
+    for a, b in edges:
+        c = 0
+        while c in used.get(a, ()) or c in used.get(b, ()):
+            c += 1
+        used.setdefault(a, set()).add(c)
+        used.setdefault(b, set()).add(c)
+        col[(a, b)] = c
+    return col
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_schedule_with_multitry_replay(seed):
+    """Active scheduling with a multi-try pass after every matching (Section 4.3), rebuilt
+    from pinned pieces: fro_refine_pair for each pair of a matching, then fro_multitry on
+    the matching's pairs; blocks a kept multi-try move touched become active."""
+    w = I.random_small(4400 + seed, n_max=2500, k_max=7)
+    okw = dict(mb=seed % 2, seed=seed, fm_permille=(0, 50)[seed % 2])
+    mt = {}
+    max_outer = 6
+    st, final, res, nouter = O.refine_active(w, opts=O.options(mt_alpha=10, **okw), max_outer=max_outer, mt_out=mt)
+    assert st == 0
+    vw = np.asarray(w["vwgt"])
+    Lmax = O.lmax(int(vw.sum()), int(vw.max()), w["k"], w["eps"])
+    part = np.array(w["part"], np.int32)
+    active = set(range(w["k"]))
+    i, gain, searches = 0, 0, 0
+    for outer in range(nouter):
+        edges = [(a, b) for a, b in _quotient_edges(w, part) if a in active or b in active]
+        col = _colours(edges)
+        nxt = set()
+        for c in sorted(set(col.values())):
+            group = sorted(e for e in edges if col[e] == c)
+            for a, b in group:
+                r = res[i]
+                assert (r["a"], r["b"]) == (a, b)
+                st2, part, rr = O.refine_pair(w, a, b, part=part, opts=O.options(**okw))
+                assert st2 == 0 and rr.cut_after == r["cut_after"]
+                if rr.accepted or rr.fm_moves > 0:
+                    nxt |= {a, b}
+                i += 1
+            st3, part, tot, changed = O.multitry(dict(w, part=part), group, 10, seed=seed, Lmax=Lmax)
+            assert st3 == 0
+            nxt |= set(np.flatnonzero(changed).tolist())
+            gain += tot["gain"]
+            searches += tot["searches"]
+        active = nxt
+    assert i == len(res) and np.array_equal(part, final)
+    assert (gain, searches) == (mt["gain"], mt["searches"])
+    assert not active or nouter == max_outer
