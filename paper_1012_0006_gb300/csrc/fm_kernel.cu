@@ -4,7 +4,7 @@
 // every vertex moves at most once, the queues start with the boundary in random order,
 // TopGain takes the block whose best vertex has the larger gain and the heavier block
 // while one is overloaded, and the moves are rolled back to the best cut found within
-// the balance constraint; the setup of Section 5 stops a search once more than a given
+// the balance constraint; the setup of Section 6 stops a search once more than a given
 // fraction of the pair's vertices moved without an improvement, and runs the FM search
 // first and the flow after it).
 //

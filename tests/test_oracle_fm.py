@@ -1,5 +1,5 @@
 """Pins of the oracle's two-way FM with TopGain (Section 2.2; stopping rule of the
-Section 5 setup).
+Section 6, "Configuring the Algorithm").
 
 The oracle keeps its queues in binary heaps.  The pin replays every run from its
 move log with nothing but brute force: at each step it recomputes every gain from
