@@ -765,7 +765,7 @@ def main():
     ap.add_argument("--fm", action=argparse.BooleanOptionalAction, default=True,
                     help="sweeps with the two-way FM step before each flow (1 %% and 5 %% stopping rules)")
     ap.add_argument("--vcycle", action=argparse.BooleanOptionalAction, default=True,
-                    help="one multilevel V-cycle with the workload's partition, a sweep per level")
+                    help="one multilevel V-, F- and W-cycle with the workload's partition, a sweep per level")
     ap.add_argument("--mt", action=argparse.BooleanOptionalAction, default=True,
                     help="one multi-try FM pass over the first matching, against the oracle's")
     args = ap.parse_args()
