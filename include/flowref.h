@@ -456,16 +456,21 @@ fr_status fr_autotune(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32
  *
  * It needs no fr_ctx and never calls cudaMalloc, cudaFree or any other
  * allocating routine.  Its workspace is one static device array of about 23 MB
- * that every GPU which loads libflowref.so holds until the process exits.  The
- * first call on a device looks up that array's device address (with that device
- * current) and caches it; make that first call before any stream capture.
+ * that every GPU which loads libflowref.so holds until the process exits.  Every
+ * call looks up that array's device address on the current device (a host-side
+ * lookup, so a context created again after cudaDeviceReset is followed); the
+ * first call on a device also loads the library's kernels there, so make it
+ * before any stream capture on that device.
  * Work is queued on `stream` (a cudaStream_t, NULL = the legacy default stream)
- * and the call returns when it is done.
+ * and the call returns when it is done.  part is left unchanged on any error: the
+ * array keeps a copy of it, written back if an iteration fails after an earlier
+ * one was applied.
  *
  * Limits: n <= FR_NOALLOC_MAX_N, nnz <= FR_NOALLOC_MAX_NNZ, k <=
  * FR_NOALLOC_MAX_K, mb_reps <= FR_NOALLOC_MAX_REPS; larger problems return
  * FR_ERR_TOO_LARGE without touching part (use fr_refine_pair for them).
- * opt->fm_permille must be 0 (FR_ERR_INVALID_ARG otherwise).
+ * Options are checked as fr_refine_pair checks them; opt->fm_permille and
+ * opt->mt_alpha must be 0 (FR_ERR_INVALID_ARG otherwise).
  * Every call uses the same array, which keeps the previous call's contents;
  * each call clears what it needs before use.  Two calls whose work overlaps on
  * the GPU (concurrent streams or host threads, on the same device) race on the

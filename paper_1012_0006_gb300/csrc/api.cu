@@ -532,39 +532,33 @@ fr_status check_graph(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32
     return FR_OK;
 }
 
-fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *opt) {
-    if (!(eps > 0.0) || !std::isfinite(eps)) { ctx_error(ctx, "epsilon must be > 0"); return FR_ERR_INVALID_ARG; }
-    if (!(alpha >= 1.0) || !std::isfinite(alpha)) { ctx_error(ctx, "alpha must be >= 1"); return FR_ERR_INVALID_ARG; }
-    if (opt) {
-        if (opt->mb_reps < 0 || opt->max_iters < 0 || opt->pulse_cap < 0) {
-            ctx_error(ctx, "negative option");
-            return FR_ERR_INVALID_ARG;
-        }
-        if (opt->adaptive && !(opt->alpha_max >= 1.0)) { ctx_error(ctx, "alpha_max must be >= 1"); return FR_ERR_INVALID_ARG; }
-        if (opt->block_threads && opt->block_threads != 256 && opt->block_threads != 512) {
-            ctx_error(ctx, "block_threads must be 256 or 512");
-            return FR_ERR_INVALID_ARG;
-        }
-        if (opt->mb_reps > 64) { ctx_error(ctx, "mb_reps > 64"); return FR_ERR_INVALID_ARG; }
-        if (opt->pre_waves < -1 || opt->pre_waves > 4) {
-            ctx_error(ctx, "pre_waves must be in [-1, 4]");
-            return FR_ERR_INVALID_ARG;
-        }
-        if (opt->fm_permille < 0 || opt->fm_permille > 1000) {
-            ctx_error(ctx, "fm_permille must be in [0, 1000]");
-            return FR_ERR_INVALID_ARG;
-        }
-        if (opt->mt_alpha < 0) { ctx_error(ctx, "mt_alpha must be >= 0"); return FR_ERR_INVALID_ARG; }
-        if (opt->cluster_ctas != 0) {
+fr_status validate_params(double eps, double alpha, const fr_options *opt, const char **why) {
+    *why = nullptr;
+    if (!(eps > 0.0) || !std::isfinite(eps)) *why = "epsilon must be > 0";
+    else if (!(alpha >= 1.0) || !std::isfinite(alpha)) *why = "alpha must be >= 1";
+    else if (opt) {
+        if (opt->mb_reps < 0 || opt->max_iters < 0 || opt->pulse_cap < 0) *why = "negative option";
+        else if (opt->adaptive && !(opt->alpha_max >= 1.0)) *why = "alpha_max must be >= 1";
+        else if (opt->block_threads && opt->block_threads != 256 && opt->block_threads != 512)
+            *why = "block_threads must be 256 or 512";
+        else if (opt->mb_reps > 64) *why = "mb_reps > 64";
+        else if (opt->pre_waves < -1 || opt->pre_waves > 4) *why = "pre_waves must be in [-1, 4]";
+        else if (opt->fm_permille < 0 || opt->fm_permille > 1000) *why = "fm_permille must be in [0, 1000]";
+        else if (opt->mt_alpha < 0) *why = "mt_alpha must be >= 0";
+        else if (opt->cluster_ctas != 0) {
             bool known = false;
             for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) known |= opt->cluster_ctas == fr_ctx::kClusterSizes[t];
-            if (!known) {
-                ctx_error(ctx, "cluster_ctas must be 0, 4, 6, 8, 12 or 16");
-                return FR_ERR_INVALID_ARG;
-            }
+            if (!known) *why = "cluster_ctas must be 0, 4, 6, 8, 12 or 16";
         }
     }
-    return FR_OK;
+    return *why ? FR_ERR_INVALID_ARG : FR_OK;
+}
+
+fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *opt) {
+    const char *why = nullptr;
+    const fr_status st = validate_params(eps, alpha, opt, &why);
+    if (st != FR_OK) ctx_error(ctx, "%s", why);
+    return st;
 }
 
 // Validation pass + W, max c, block weights (and the quotient graph when qbits).
@@ -787,6 +781,9 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
     PrepOut po;
     if (st == FR_OK) st = run_prep(ctx, g, part, k, false, opt.checked != 0, &po);
     if (st != FR_OK) { if (res) res->status = st; return st; }
+    // part as it came: the FM step or an accepted iteration may write it before a later
+    // step fails, and an error must leave it unchanged
+    CK(cudaMemcpyAsync(ctx->part_backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
     const long long W = po.W;
     const long long Lmax = host_lmax(W, po.maxc, k, eps);
     const int adaptive = opt.adaptive ? 1 : 0;
@@ -818,7 +815,12 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
             memcpy(&c, ctx->h_stage + 4096, sizeof(Ctl));
             st = status_from_ctl(ctx, c, "fr_refine_pair (FM)");
         }
-        if (st != FR_OK) { if (res) res->status = st; return st; }
+        if (st != FR_OK) {
+            cudaMemcpyAsync(part, ctx->part_backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream);
+            cudaStreamSynchronize(ctx->stream);
+            if (res) res->status = st;
+            return st;
+        }
     }
     while (iters < max_iters) {
         ++iters;
@@ -836,6 +838,15 @@ extern "C" fr_status fr_refine_pair(fr_ctx *ctx, const fr_graph *g, int32_t *par
         if (o.feasible) break;
         if (!adaptive || al == 1.0) break;
         al = al / 2.0 > 1.0 ? al / 2.0 : 1.0;
+    }
+    if (st != FR_OK) {
+        // a later iteration failed after an earlier one was applied: undo everything
+        cudaError_t e = cudaMemcpyAsync(part, ctx->part_backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice,
+                                        ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "restoring part");
+        accepted = 0;
+        cur_cut = cut_before < 0 ? 0 : cut_before; cur_A = wA0; cur_B = wB0;
     }
     if (res) {
         res->status = st;

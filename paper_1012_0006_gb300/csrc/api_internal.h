@@ -135,6 +135,8 @@ fr::Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *o
 int choose_tpb(fr_ctx *ctx, const fr_options *opt);
 int choose_grid(fr_ctx *ctx, const fr_options *opt, int tpb, int nsides, long long est_vertices);
 fr_status check_graph(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k);
+// Checks of eps, alpha and the options that need no context; *why names the first failure.
+fr_status validate_params(double eps, double alpha, const fr_options *opt, const char **why);
 fr_status check_params(fr_ctx *ctx, double eps, double alpha, const fr_options *opt);
 fr_status run_prep(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k, bool quotient, bool checked,
                    fr::PrepOut *host_out);

@@ -7,7 +7,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "api_internal.h"
 
@@ -25,7 +24,7 @@ constexpr size_t al(size_t b) { return (b + 255) / 256 * 256; }
 
 // Bytes of every carved array, in carving order (must match carve_all below).
 constexpr size_t kNaBytes =
-    4 * al(4ull * kNaMaxN) +                                  // dist lid vq_v vq_s
+    5 * al(4ull * kNaMaxN) +                                  // dist lid vq_v vq_s part0
     al(4ull * (kNaMaxN / 32 + 2)) +                           // cbits
     21 * al(4ull * (kNaMaxN + 1)) +                           // union vertex arrays
     2 * al(8ull * kNaMaxN) + 2 * al(1ull * kNaMaxN) +         // ex cw / border side_out
@@ -42,6 +41,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 struct Scratch {
     int *dist, *lid, *vq_v, *vq_s;
+    int *part0;   // part as the call found it (restored on error)
     unsigned int *cbits;
     int *gid, *sid, *off, *infc, *fx, *lab, *rflag, *color, *scc, *vc, *fq0, *fq1, *spare;
     int *cpair, *cmin, *cid, *indeg, *outoff, *ocur, *plist, *sinkc;
@@ -75,6 +75,7 @@ T *take(char *&p, size_t count) {
 void carve_all(char *p, Scratch &s) {
     const size_t N = kNaMaxN, N1 = kNaMaxN + 1, M = kNaMaxNNZ, R = kNaMaxReps;
     s.dist = take<int>(p, N); s.lid = take<int>(p, N); s.vq_v = take<int>(p, N); s.vq_s = take<int>(p, N);
+    s.part0 = take<int>(p, N);
     s.cbits = take<unsigned int>(p, N / 32 + 2);
     int **v21[21] = {&s.gid, &s.sid, &s.off, &s.infc, &s.fx, &s.lab, &s.rflag, &s.color, &s.scc, &s.vc, &s.fq0,
                      &s.fq1, &s.spare, &s.cpair, &s.cmin, &s.cid, &s.indeg, &s.outoff, &s.ocur, &s.plist, &s.sinkc};
@@ -100,20 +101,15 @@ void carve_all(char *p, Scratch &s) {
     s.sw_j = take<int>(p, R);
 }
 
-// Device address of the scratch, looked up once per device (with that device current).
-std::mutex g_mu;
-void *g_addr[64] = {nullptr};
-
-cudaError_t scratch_address(int dev, void **out) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!g_addr[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = ptr;
-    }
-    *out = g_addr[dev];
+// Device address of the scratch on the current device.  It is looked up on every call
+// (a host-side table lookup): an address kept from an earlier call could belong to a
+// context that no longer exists (after cudaDeviceReset the module is loaded again and
+// the array may sit elsewhere).
+cudaError_t scratch_address(void **out) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = ptr;
     return cudaSuccess;
 }
 
@@ -211,12 +207,15 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
     fr_options opt;
     if (opt_in) opt = *opt_in; else fr_default_options(&opt);
     if (res) memset(res, 0, sizeof(*res));
-    fr_status st = FR_OK;
-    if (!g || !part || g->n < 1 || g->nnz < 0 || !g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->adjwgt)) ||
-        k < 2 || a < 0 || b < 0 || a >= k || b >= k || a == b || !(eps > 0.0) || !std::isfinite(eps) ||
-        !(alpha >= 1.0) || !std::isfinite(alpha) || opt.mb_reps < 0 || opt.max_iters < 0 ||
-        (opt.adaptive && !(opt.alpha_max >= 1.0)) || opt.fm_permille != 0 || opt.mt_alpha != 0)
-        st = FR_ERR_INVALID_ARG;   // (FM steps need the context's workspace: fr_refine_pair)
+    // the same checks as fr_refine_pair's (no context, so no message), plus no FM or
+    // multi-try step: those need the context's workspace
+    const char *why = nullptr;
+    fr_status st = validate_params(eps, alpha, &opt, &why);
+    if (st == FR_OK &&
+        (!g || !part || g->n < 1 || g->nnz < 0 || !g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->adjwgt)) ||
+         k < 2 || k > kMaxK || a < 0 || b < 0 || a >= k || b >= k || a == b || opt.fm_permille != 0 ||
+         opt.mt_alpha != 0))
+        st = FR_ERR_INVALID_ARG;
     else if (g->n > kNaMaxN || g->nnz > kNaMaxNNZ || k > kNaMaxK || opt.mb_reps > kNaMaxReps)
         st = FR_ERR_TOO_LARGE;   // beyond the fixed scratch: use fr_refine_pair
     if (st != FR_OK) {
@@ -224,9 +223,8 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
         return st;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int dev = 0;
     void *base = nullptr;
-    if (cudaGetDevice(&dev) != cudaSuccess || scratch_address(dev, &base) != cudaSuccess) {
+    if (scratch_address(&base) != cudaSuccess) {
         cudaGetLastError();
         if (res) res->status = FR_ERR_CUDA;
         return FR_ERR_CUDA;
@@ -241,6 +239,7 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
         cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (g->n / 32 + 2), s) != cudaSuccess ||
         cudaMemsetAsync(S.prep, 0, sizeof(PrepOut), s) != cudaSuccess ||
         cudaMemsetAsync(S.blockw, 0, sizeof(long long) * k, s) != cudaSuccess ||
+        cudaMemcpyAsync(S.part0, part, sizeof(int) * g->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         launch_prep(g->xadj, g->adjncy, g->adjwgt, g->vwgt, part, g->n, g->nnz, k, S.blockw, nullptr, S.prep, s) !=
             cudaSuccess ||
         (opt.checked && launch_check_symmetric(g->xadj, g->adjncy, g->adjwgt, g->n, S.prep, s) != cudaSuccess) ||
@@ -264,6 +263,9 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
     NaIter o;
     memset(&o, 0, sizeof(o));
     long long cut0 = -1, wA0 = 0, wB0 = 0, cut = 0, wA = 0, wB = 0;
+    Ctl last;   // counters of the last iteration that succeeded
+    memset(&last, 0, sizeof(last));
+    int ncomp = 0;
     while (iters < max_iters) {
         ++iters;
         st = na_iteration(S, g, part, k, a, b, host_budget_base(W, k, eps, al), Lmax, opt, s, &o);
@@ -271,6 +273,8 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
             // a failed step may stop before releasing its BFS marks; the next call clears them
             break;
         }
+        last = o.ctl;
+        ncomp = o.ncomp;
         if (cut0 < 0) { cut0 = o.oldcut; wA0 = o.cA; wB0 = o.cB; }
         cut = o.oldcut; wA = o.cA; wB = o.cB;
         if (o.accept) { cut = o.newcut; wA = o.nA; wB = o.nB; accepted = 1; }
@@ -283,6 +287,16 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
         if (!adaptive || al == 1.0) break;
         al = al / 2.0 > 1.0 ? al / 2.0 : 1.0;
     }
+    if (st != FR_OK) {
+        // an earlier iteration may have been applied before a later one failed: put part back
+        if (cudaMemcpyAsync(part, S.part0, sizeof(int) * g->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            st = FR_ERR_CUDA;
+        }
+        accepted = 0;
+        cut = cut0 < 0 ? 0 : cut0; wA = wA0; wB = wB0;
+    }
     if (res) {
         res->status = st;
         res->a = a; res->b = b;
@@ -294,8 +308,8 @@ extern "C" fr_status fr_refine_pair_noalloc(const fr_graph *g, int32_t *part, in
         res->cut_after = cut; res->wA_after = wA; res->wB_after = wB;
         res->corridor_n = o.nc; res->corridor_arcs = o.m;
         res->accepted = accepted;
-        res->pulses = o.ctl.pulses; res->relabels = o.ctl.relabels;
-        res->bfs_levels = o.ctl.levels; res->scc_rounds = o.ctl.scc_rounds; res->ncomp = o.ncomp;
+        res->pulses = last.pulses; res->relabels = last.relabels;
+        res->bfs_levels = last.levels; res->scc_rounds = last.scc_rounds; res->ncomp = ncomp;
     }
     return st;
 }

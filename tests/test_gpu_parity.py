@@ -13,6 +13,7 @@ import pytest
 
 import oracle as O
 from paper_1012_0006_gb300 import inputs as I
+from tests.pulse_caps import later_iteration_cap
 
 pytestmark = pytest.mark.gpu
 
@@ -425,6 +426,36 @@ def test_iteration_cap_leaves_part_unchanged(F, ctx):
     assert _torch().equal(part, before)
     # the context stays usable
     _check_batch(F, ctx, w)
+
+
+@pytest.mark.parametrize("mb", [0, 1])
+def test_error_in_a_later_adaptive_iteration_leaves_part_unchanged(F, ctx, mb):
+    """Iteration 1 is accepted and written to part; iteration 2 hits the pulse cap
+    (a host-side bound, no fault): the call fails and part is as it came in."""
+    torch = _torch()
+    tried = 0
+    for w in (I.config(2), I.config(2, scale=0.5), I.config(2, scale=0.25)):
+        if tried:
+            break
+        g = F.DeviceGraph.from_workload(w)
+        kw = dict(mb=mb)
+        cap = later_iteration_cap(
+            lambda p, al, k_: ctx.refine_pair(g, p, w["k"], 0, 1, w["eps"], al, F.default_options(**k_))[1], w, kw)
+        if cap is None:
+            continue
+        tried += 1
+        part = torch.as_tensor(np.array(w["part"], np.int32)).cuda()
+        before = part.clone()
+        st, res = ctx.refine_pair(g, part, w["k"], 0, 1, w["eps"], 1.0,
+                                  F.default_options(mb=mb, adaptive=1, max_iters=10, alpha_max=16.0,
+                                                    pulse_cap=cap), check=False)
+        assert st == F.FR_ERR_ITER_LIMIT and res.status == F.FR_ERR_ITER_LIMIT
+        assert res.iters >= 2
+        assert torch.equal(part, before)
+        # the context stays usable: a normal call gives the oracle's partition
+        _check_pair(F, ctx, w, 0, 1, dict(mb=mb, adaptive=1, max_iters=10, alpha_max=16.0),
+                    O.options(mb=mb, adaptive=1, max_iters=10, alpha_max=16.0))
+    assert tried, "no workload separates the pulse counts of the first two iterations"
 
 
 def test_arena_bound_gives_oom(F):
