@@ -81,10 +81,10 @@
  * Parity unpinned: the order of the sweeps r >= 1 (their splitmix64 keys) is
  * checked only for what any valid order must satisfy (a topological order of the
  * component DAG, every step a minimum cut); the quality of the most balanced cut
- * against the true optimum is bounded by brute force, not fixed; KaSPar decisions
- * within a relative 1e-9 of the threshold are taken in double arithmetic without an
- * exact pin; the F-cycle rule where a second coarsening stalls is fixed by reading
- * only.
+ * against the true optimum is bounded by brute force, not fixed.  (KaSPar decisions
+ * within a few ulps of the threshold are pinned to the documented double operations
+ * and the hand-derived ties of constant gains; the F-cycle's stalled second
+ * coarsening to a hand-derived recursion.)
  *   batch      greedy edge colouring of the quotient graph in lexicographic
  *              (a, b) order (smallest free colour); each colour is a round of
  *              block-disjoint pairs; rounds in colour order, pairs of a round

@@ -151,12 +151,12 @@ def test_vcycle_stall_rule(F, ctx):
         assert (r["levels"] == 1) == (leaves == 25)
 
 
-def _cycle(F, ctx, w, kind, d, okw, active_outer=0):
-    st, pref, rref = O.cycle(w, kind, d=d, opts=O.options(**okw), active_outer=active_outer)
+def _cycle(F, ctx, w, kind, d, okw, active_outer=0, max_levels=64):
+    st, pref, rref = O.cycle(w, kind, d=d, opts=O.options(**okw), active_outer=active_outer, max_levels=max_levels)
     assert st == 0
     g, part = _dev(F, w)
     st, r = ctx.cycle(g, part, w["k"], w["eps"], w["alpha"], kind=kind, d=d, opts=F.default_options(**okw),
-                      active_outer=active_outer)
+                      active_outer=active_outer, max_levels=max_levels)
     for f in ("coarsenings", "refinements", "depth", "cut_before", "cut_after", "level_coarsenings"):
         assert r[f] == rref[f], (kind, f)
     assert np.array_equal(part.cpu().numpy(), pref)
@@ -177,6 +177,18 @@ def test_cycles_workload(F, ctx):
     assert rf["coarsenings"] > rv["coarsenings"]
     _cycle(F, ctx, I.random_small(15300, n_max=2000, k_max=4), "W", 1, dict(mb=1, fm_permille=50, mt_alpha=10),
            active_outer=2)
+
+
+def test_cycles_where_a_second_coarsening_stalls(F, ctx):
+    """The hand-derived stall case of the oracle's pins (paths and isolated vertices, no
+    cut edge, max_levels = 2): the GPU's recursion counts the stalled coarsening and
+    skips the trial exactly as the oracle does."""
+    from tests.test_oracle_multilevel import stall_case
+    for stall, refinements in ((True, 2), (False, 4)):
+        w = stall_case(stall)
+        for kind, d in (("F", 1), ("W", 2)):
+            r = _cycle(F, ctx, w, kind, d, dict(mb=0), max_levels=2)
+            assert (r["coarsenings"], r["refinements"]) == (2, refinements)
 
 
 def test_contract_rejects_a_non_matching(F, ctx):

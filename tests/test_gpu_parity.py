@@ -434,7 +434,7 @@ def test_error_in_a_later_adaptive_iteration_leaves_part_unchanged(F, ctx, mb):
     (a host-side bound, no fault): the call fails and part is as it came in."""
     torch = _torch()
     tried = 0
-    for w in (I.config(2), I.config(2, scale=0.5), I.config(2, scale=0.25)):
+    for w in (I.config(2, scale=0.5), I.config(2, scale=0.25), I.config(2)):
         if tried:
             break
         g = F.DeviceGraph.from_workload(w)

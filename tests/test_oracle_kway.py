@@ -63,6 +63,71 @@ def test_kaspar_rule_against_exact_arithmetic():
     assert checked > 3900
 
 
+def kaspar_doubles(p, S1, S2, alpha, beta, order="paper"):
+    """The rule as both sides take it (a floating-point decision on an integer outcome):
+    every step one IEEE double operation rounded to nearest, in this order --
+    mu = S1 / p, sigma^2 = S2 / p - mu * mu, lhs = (p * mu) * mu, rhs = alpha * sigma^2 +
+    beta.  Python floats are IEEE doubles and round every operation (no fused
+    multiply-add).  order="pmm" and "ss" are two other plausible orders of the left
+    side, p * (mu * mu) and S1 * S1 / p, used to show the test tells orders apart."""
+    pd = float(p)
+    mu = float(S1) / pd
+    var = float(S2) / pd - mu * mu
+    if order == "paper":
+        lhs = (pd * mu) * mu
+    elif order == "pmm":
+        lhs = pd * (mu * mu)
+    else:
+        lhs = float(S1) * float(S1) / pd
+    rhs = float(alpha) * var + beta
+    return lhs > rhs
+
+
+def test_kaspar_rule_ties_by_hand():
+    """Constant gains g over p moves: mu = g and sigma^2 = 0 exactly in doubles, so the
+    rule is p g^2 > beta with no rounding at all; at beta = p g^2 the strict inequality
+    does not stop, one ulp below it does."""
+    for p, g in ((4, -3), (7, 2), (25, -1), (3, -5)):
+        lhs = float(p * g * g)
+        for alpha in (0, 10):
+            assert O.kaspar_stop(p, p * g, p * g * g, alpha, lhs) == 0
+            assert O.kaspar_stop(p, p * g, p * g * g, alpha, math.nextafter(lhs, -math.inf)) == 1
+            assert O.kaspar_stop(p, p * g, p * g * g, alpha, math.nextafter(lhs, math.inf)) == 0
+
+
+def test_kaspar_rule_within_the_rounding_band():
+    """Inputs built to land within a few ulps of the threshold, where exact arithmetic
+    and doubles can disagree: the oracle follows the documented double operations on
+    every one.  The band is really reached (exact and double decisions differ on some),
+    and the other two orders of the left side disagree with the documented one on some,
+    so a change of order would fail here."""
+    rs = np.random.default_rng(11)
+    n_cases = band = other = 0
+    for _ in range(3000):
+        p = int(rs.integers(2, 200))
+        g = rs.integers(-15, 6, size=p)
+        S1, S2 = int(g.sum()), int((g * g).sum())
+        alpha = int(rs.choice([0, 1, 3, 10, 50]))
+        pd = float(p)
+        mu = float(S1) / pd
+        var = float(S2) / pd - mu * mu
+        beta0 = (pd * mu) * mu - float(alpha) * var
+        if not beta0 > 0:
+            continue
+        b = beta0
+        for _ in range(3):
+            b = math.nextafter(b, -math.inf)
+        for _ in range(7):
+            want = kaspar_doubles(p, S1, S2, alpha, b)
+            assert O.kaspar_stop(p, S1, S2, alpha, b) == int(want), (p, S1, S2, alpha, b)
+            band += kaspar_exact(p, S1, S2, alpha, b)[0] != want
+            other += any(kaspar_doubles(p, S1, S2, alpha, b, o) != want for o in ("pmm", "ss"))
+            n_cases += 1
+            b = math.nextafter(b, math.inf)
+    assert n_cases > 10000
+    assert band > 100 and other > 100
+
+
 @pytest.mark.parametrize("g", [-1, -2, -3, -5, 4])
 @pytest.mark.parametrize("n", [10, 1000, 4194304])
 def test_kaspar_constant_gains_closed_form(g, n):

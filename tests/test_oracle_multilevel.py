@@ -380,3 +380,78 @@ def test_cycle_option_checks():
     w = I.random_small(15100, n_max=200)
     st, *_ = O.cycle(w, "W", d=0)
     assert st == 1
+
+
+def _paths_and_isolated(n, p3, p4):
+    """p3 paths of three vertices (ids 3i .. 3i+2), one path of four on the ids in p4,
+    every other vertex isolated; unit weights.  Block 0 holds the paths, block 1 the
+    isolated vertices, so no edge is cut: the quotient graph is empty and every
+    refinement leaves the partition as it is, while matchings run inside block 0."""
+    rows = [[] for _ in range(n)]
+
+    def edge(u, v):
+        rows[u].append(v)
+        rows[v].append(u)
+
+    for i in range(p3):
+        edge(3 * i, 3 * i + 1)
+        edge(3 * i + 1, 3 * i + 2)
+    for u, v in zip(p4, p4[1:]):
+        edge(u, v)
+    xadj = np.zeros(n + 1, np.int32)
+    xadj[1:] = np.cumsum([len(r) for r in rows])
+    adj = np.array([u for r in rows for u in sorted(r)], np.int32)
+    part = np.ones(n, np.int32)
+    part[:3 * p3] = 0
+    part[list(p4)] = 0
+    return dict(n=n, nnz=len(adj), xadj=xadj, adjncy=adj, adjwgt=np.ones(len(adj), np.int32),
+                vwgt=np.ones(n, np.int32), part=part, k=2, eps=0.03, alpha=1.0, mb=0)
+
+
+def _middle_first(p4, sl):
+    """Whether the greedy matching takes the middle edge of the path p4 first: its three
+    edges have equal expansion*2 ratings, so the larger splitmix64(sl ^ u << 32 ^ v)
+    (u < v) decides (ties of the hash are impossible for distinct edges here)."""
+    keys = [splitmix64(sl ^ (min(u, v) << 32) ^ max(u, v)) for u, v in zip(p4, p4[1:])]
+    return keys[1] > keys[0] and keys[1] > keys[2]
+
+
+def stall_case(stall_second):
+    """n = 200, k = 2 (threshold max(60k, n/(60k)) = 120 < n), 8 three-vertex paths and one
+    four-vertex path whose id block is chosen so that the first coarsening of level 0
+    (c = 0, seed_l = splitmix64(0 ^ 0 ^ 0 << 32)) matches both end edges of the four-path
+    (10 pairs: 20 * 10 = n, not under n, so it goes on), and the second (c = 1) matches its
+    middle edge (9 pairs: stalled) if stall_case(True), or both end edges again if False."""
+    s0, s1 = splitmix64(0), splitmix64(1 << 32)
+    for a in range(24, 196):
+        p4 = (a, a + 1, a + 2, a + 3)
+        if not _middle_first(p4, s0) and _middle_first(p4, s1) == stall_second:
+            return _paths_and_isolated(200, 8, p4)
+    raise AssertionError("no placement")
+
+
+@pytest.mark.parametrize("kind", ["F", "W"])
+@pytest.mark.parametrize("d", [1, 2])
+def test_cycle_second_coarsening_that_stalls(kind, d):
+    """Section 5 cycles where level 0's second coarsening stalls: derived by hand from the
+    pseudocode's recursion with max_levels = 2 (level 1 is never coarsened).
+      level 0, trial 0: coarsening 1 of level 0 (10 pairs) -> G1 (190 vertices);
+        level 1 cannot coarsen: refine G1 (refinement 1); project, refine G0 (2)
+      level 0, trial 1 (0 % d == 0; for F fewer than two level-0 coarsenings so far):
+        coarsening 2 of level 0 (seed c = 1) stalls at 9 pairs: the trial is skipped,
+        nothing more is refined.
+    So 2 coarsenings (both of level 0), 2 refinements, depth 2; with a second coarsening
+    that does not stall the trial runs: 2 coarsenings, 4 refinements."""
+    for stall, refinements in ((True, 2), (False, 4)):
+        w = stall_case(stall)
+        pairs0, _ = O.match(w, seed_l=splitmix64(0))
+        pairs1, _ = O.match(w, seed_l=splitmix64(1 << 32))
+        assert (pairs0, pairs1) == (10, 9 if stall else 10)
+        st, part, r = O.cycle(w, kind, d=d, max_levels=2)
+        assert st == 0
+        assert (r["coarsenings"], r["refinements"], r["depth"]) == (2, refinements, 2)
+        assert r["level_coarsenings"][:2] == [2, 0] and sum(r["level_coarsenings"]) == 2
+        assert np.array_equal(part, w["part"]) and r["cut_after"] == r["cut_before"] == 0
+    # the V-cycle never takes a second trial
+    st, part, r = O.cycle(stall_case(True), "V", max_levels=2)
+    assert (r["coarsenings"], r["refinements"], r["level_coarsenings"][:2]) == (1, 2, [1, 0])

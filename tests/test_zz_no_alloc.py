@@ -132,7 +132,7 @@ def test_noalloc_error_in_a_later_adaptive_iteration_leaves_part_unchanged(gpu_l
     import torch
     F = gpu_lib
     tried = 0
-    for w in (I.config(2), I.config(2, scale=0.5), I.config(2, scale=0.25)):
+    for w in (I.config(2, scale=0.5), I.config(2, scale=0.25), I.config(2)):
         g = F.DeviceGraph.from_workload(w)
         cap = later_iteration_cap(
             lambda p, al, kw: _noalloc(F, g, p, w["k"], 0, 1, w["eps"], al, F.default_options(**kw))[1], w,
