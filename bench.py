@@ -395,7 +395,7 @@ def run_ours(args, world, rank, local, pg):
     vc = multilevel(F, ctx, g, part0, w) if args.vcycle else None
 
     serving = None
-    if args.serve or args.serve_full:
+    if args.serve:
         serving = run_serving(F, local, full=args.serve_full, requests=args.serve_requests,
                               log_prefix=f"[rank {rank}] ")
 
@@ -608,17 +608,23 @@ def batched_vs_per_pair(F, ctx0, dev, reps=3):
 
 # ------------------------------------------------------------------ serving ----
 
-def run_serving(F, device, full=False, requests=None, log_prefix=""):
+def run_serving(F, device, full=True, requests=None, log_prefix="", parity_budget_s=120.0):
     """Continuous-batching serving of seeded refinement requests (Poisson arrivals).
 
     Pool: 2D grids and 2D/3D rggs (mean degree 8-12, unit or [1,10] weights), k in {2,4,8},
     eps in {0.01,0.03,0.05}, alpha 2, most balanced cuts, one sweep of rounds per request.
+    full: 48 graphs up to 2^21 vertices and 10,000 requests (the serving configuration);
+    otherwise a bounded sample (24 graphs up to 2^18 vertices, 1,500 requests).
     First the closed-loop saturated rate is measured (max_inflight requests always queued),
     then requests arrive as a Poisson process at 0.7 x that rate; latency is submit ->
-    completion on the host clock."""
+    completion on the host clock.  A seeded 1 % sample of the open-loop requests keeps its
+    served partition, and the oracle refines the same inputs on all host cores (one
+    request per thread): parity = every checked partition and cut equal."""
+    import concurrent.futures as cf
     import threading
     import numpy as np
     from paper_1012_0006_gb300 import inputs as I
+    import oracle as O
     t0 = time.time()
     if full:
         pool = I.serving_pool(count=48, max_n=1 << 21)
@@ -641,12 +647,19 @@ def run_serving(F, device, full=False, requests=None, log_prefix=""):
     opts = F.default_options(mb=1)
     srv = F.Server(device, max_inflight=32, opts=opts)
     ids = [srv.add_graph(g["xadj"], g["adjncy"], g["adjwgt"], g["vwgt"]) for g in pool]
+    # the parity sample: a seeded 1 % of the open-loop requests (tags 10,000,000 + index)
+    sample = sorted(set(rs.integers(0, len(reqs), max(1, len(reqs) // 100)).tolist()))
+    want = {10_000_000 + i for i in sample}
+    served = {}
 
     def drain(count, lat, stat):
         for _ in range(count):
-            resp, _ = srv.next(nmax, timeout_ms=600000)
+            resp, out = srv.next(nmax, timeout_ms=600000)
             lat.append(resp["latency_ms"])
             stat.append(resp["status"])
+            if resp["tag"] in want:
+                gi = reqs[resp["tag"] - 10_000_000][0]
+                served[resp["tag"] - 10_000_000] = (out[:pool[gi]["n"]].copy(), resp)
 
     # closed loop: everything queued at once (saturated)
     nsat = min(len(reqs), 400)
@@ -675,26 +688,53 @@ def run_serving(F, device, full=False, requests=None, log_prefix=""):
     st = srv.stats()
     srv.close()
     lat = np.array(lat)
-    # the oracle on a seeded 1 % sample of the requests (at most 15, ~10 s): per-request time
-    import oracle as O
-    sample = [reqs[i] for i in sorted(set(rs.integers(0, len(reqs), max(1, min(15, len(reqs) // 100))).tolist()))]
-    t2 = time.perf_counter()
-    ndone = 0
-    for gi, k, eps in sample:
+    log(f"{log_prefix}serving: {len(reqs)} requests in {el:.1f}s, p50 {np.percentile(lat, 50):.2f} ms, "
+        f"p99 {np.percentile(lat, 99):.2f} ms")
+
+    # parity and per-request CPU time: the oracle on the sample, one request per host thread
+    # (the oracle is plain C behind ctypes, which releases the GIL during the call)
+    def oracle_one(i):
+        gi, k, eps = reqs[i]
         g = pool[gi]
         w = dict(n=g["n"], xadj=g["xadj"], adjncy=g["adjncy"], adjwgt=g["adjwgt"], vwgt=g["vwgt"],
                  part=parts[(gi, k)], k=k, eps=eps, alpha=2.0)
-        assert O.refine_batch(w, opts=O.options(mb=1))[0] == 0
-        ndone += 1
-        if time.perf_counter() - t2 > 10.0:
-            break
-    cpu_ms = (time.perf_counter() - t2) * 1e3 / ndone
+        c0 = time.thread_time()
+        stq, part_o, res_o, _ = O.refine_batch(w, opts=O.options(mb=1))
+        cpu_s = time.thread_time() - c0
+        got, resp = served[i]
+        ok = (stq == 0 and resp["status"] == 0 and np.array_equal(got, part_o) and resp["npairs"] == len(res_o)
+              and resp["accepted"] == sum(r["accepted"] for r in res_o))
+        return ok, cpu_s, g["n"]
+
+    threads = len(os.sched_getaffinity(0))
+    t2 = time.perf_counter()
+    checked = equal = 0
+    cpu_tot = 0.0
+    nmax_checked = 0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = [ex.submit(oracle_one, i) for i in sample if i in served]
+        for f in futs:
+            left = parity_budget_s - (time.perf_counter() - t2)
+            try:
+                ok, cpu_s, n = f.result(timeout=max(left, 0.0))
+            except cf.TimeoutError:
+                break
+            checked += 1
+            equal += bool(ok)
+            cpu_tot += cpu_s
+            nmax_checked = max(nmax_checked, n)
+        for f in futs:
+            f.cancel()
+    parity_s = time.perf_counter() - t2
     return {"requests": len(reqs), "failed": int(sum(1 for x in stat if x != 0)),
-            "cpu_oracle_ms_per_request": round(cpu_ms, 2), "cpu_oracle_sample": ndone,
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "requests_per_s": round(len(reqs) / el, 2), "saturated_requests_per_s": round(sat, 2),
             "arrival_rate": round(lam, 2), "steps": st["steps"], "max_concurrent": st["max_concurrent"],
-            "pool": f"{len(pool)} graphs up to {nmax} vertices" + ("" if full else " (bounded sample of the mix)")}
+            "pool": f"{len(pool)} graphs up to {nmax} vertices" + ("" if full else " (bounded sample of the mix)"),
+            "parity": bool(checked > 0 and equal == checked), "parity_checked": checked,
+            "parity_sample": len(sample), "parity_largest_n": nmax_checked,
+            "cpu_oracle_ms_per_request": round(cpu_tot * 1e3 / max(checked, 1), 2),
+            "cpu_oracle_threads": threads, "cpu_oracle_wall_s": round(parity_s, 1)}
 
 
 # --------------------------------------------------------- reference arm ----
@@ -755,8 +795,10 @@ def main():
     ap.add_argument("--ref-threads", type=int, default=0, help="reference arm: host threads (0: all cores)")
     ap.add_argument("--ref-rounds", type=int, default=0, help="reference arm, threaded: rounds per step (0: the whole sweep)")
     ap.add_argument("--serve", action=argparse.BooleanOptionalAction, default=True,
-                    help="bounded serving measurement (p50/p99) in the JSON line")
-    ap.add_argument("--serve-full", action="store_true", help="the full serving mix: 48 graphs, 10,000 requests")
+                    help="serving measurement (p50/p99, parity on a 1 %% sample) in the JSON line")
+    ap.add_argument("--serve-full", action=argparse.BooleanOptionalAction, default=True,
+                    help="the full serving mix (48 graphs up to 2^21 vertices, 10,000 requests); "
+                         "--no-serve-full: a bounded sample (24 graphs up to 2^18, 1,500 requests)")
     ap.add_argument("--compare", action=argparse.BooleanOptionalAction, default=True,
                     help="128^3 grid: batched sweep vs one pair per launch")
     ap.add_argument("--serve-requests", type=int, default=None)
