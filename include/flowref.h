@@ -97,6 +97,12 @@ typedef struct fr_options {
                               (Section 2.2; 10 in the paper's setup); blocks a kept move left or
                               entered become active.  0: none.  Other entry points need 0;
                               needs k <= 1024 and every gain within +-1023 */
+    int32_t sweep_sched;   /* fr_refine_batch: 0 = a queue sweep where it applies -- every pair of
+                              the sweep in one launch of thread-block clusters, a pair started as
+                              soon as the earlier pairs that share one of its blocks committed
+                              (the same results as round by round; not with the FM step, and a
+                              sweep whose corridor outgrows a cluster runs round by round);
+                              1 = round by round (one launch sequence per matching) */
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b);
@@ -404,6 +410,11 @@ typedef struct fr_profile_info {
                                  initial stacks, the moves, rollback and bookkeeping */
     int32_t cluster_sizes[5]; /* CTAs per cluster the library can launch (4, 6, 8, 12, 16) */
     int32_t cluster_max_active[5]; /* clusters of each size resident at once on this GPU */
+    int32_t queue;            /* 1: the last fr_refine_batch ran as a queue sweep (fr_options.sweep_sched);
+                                 cluster_ms is then the whole sweep's device time */
+    int32_t queue_ctas;       /* CTAs per cluster of that queue sweep */
+    int32_t queue_clusters;   /* clusters it launched */
+    int32_t queue_fallbacks;  /* queue sweeps of this context that a pair outgrew (run round by round) */
 } fr_profile_info;
 
 /* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with

@@ -39,6 +39,8 @@ CUDA_SOURCES = [
     "serve.cu",
     "noalloc.cu",
     "cluster_flow.cu",
+    "queue_sweep.cu",
+    "api_queue.cu",
 ]
 
 

@@ -469,6 +469,12 @@ extern "C" fr_status fr_create(fr_ctx **out, int32_t device, size_t arena_bytes,
         }
         ctx->cl_cap[t] = mc;
         ctx->max_clusters = std::max(ctx->max_clusters, mc);
+        int qc = 0;
+        if (queue_capacity(fr_ctx::kClusterSizes[t], &qc) != cudaSuccess) {
+            cudaGetLastError();
+            qc = 0;
+        }
+        ctx->q_cap[t] = qc;
     }
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
@@ -489,6 +495,7 @@ extern "C" fr_status fr_destroy(fr_ctx *ctx) {
     free_pairs(ctx);
     free_fm(ctx);
     free_mt(ctx);
+    free_queue(ctx);
     if (ctx->reps_mem) cudaFree(ctx->reps_mem);
     if (ctx->hg_mem) cudaFree(ctx->hg_mem);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -545,6 +552,7 @@ fr_status validate_params(double eps, double alpha, const fr_options *opt, const
         else if (opt->pre_waves < -1 || opt->pre_waves > 4) *why = "pre_waves must be in [-1, 4]";
         else if (opt->fm_permille < 0 || opt->fm_permille > 1000) *why = "fm_permille must be in [0, 1000]";
         else if (opt->mt_alpha < 0) *why = "mt_alpha must be >= 0";
+        else if (opt->sweep_sched < 0 || opt->sweep_sched > 1) *why = "sweep_sched must be 0 or 1";
         else if (opt->cluster_ctas != 0) {
             bool known = false;
             for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) known |= opt->cluster_ctas == fr_ctx::kClusterSizes[t];

@@ -320,16 +320,6 @@ extern "C" fr_status fr_rounds(fr_ctx *ctx, const fr_graph *g, const int32_t *pa
 
 // ---------------------------------------------------------------- batch --
 
-struct BatchPlan {
-    int np, nr;
-    std::vector<int> off;      // round offsets
-    std::vector<int> grid;     // persistent-kernel CTAs per round
-    int tpb, k;
-    long long Ubase, Lmax, totcut;
-    std::vector<long long> est_max;   // estimated corridor vertices of each round's largest pair
-    double avg_degree = 12.0;
-};
-
 // Enqueues a whole sweep: pair descriptors, cleared per-round state, then per
 // round the boundary scan and the persistent step kernel.
 static fr_status enqueue_sweep(fr_ctx *ctx, const fr_graph *g, const BatchPlan &pl, const fr_options *opt) {
@@ -530,7 +520,9 @@ static fr_status plan_sweep(fr_ctx *ctx, const fr_graph *g, const int32_t *part,
     if (pl->np == 0) return FR_OK;
     if ((st = ensure_pairs(ctx, pl->np, pl->nr, opt->mb_reps)) != FR_OK) return st;
     // round offsets, pair lists and block weights for the grid estimate
-    std::vector<int> pa(pl->np), pb(pl->np);
+    std::vector<int> &pa = pl->pa, &pb = pl->pb;
+    pa.assign(pl->np, 0);
+    pb.assign(pl->np, 0);
     std::vector<long long> bw(k);
     pl->off.assign(pl->nr + 1, 0);
     CK(cudaMemcpyAsync(pl->off.data(), ctx->round_off, sizeof(int) * (pl->nr + 1), cudaMemcpyDeviceToHost, ctx->stream));
@@ -571,22 +563,40 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
     }
     if (opt->fm_permille > 0 && (st = ensure_fm(ctx, g->n, g->nnz, k, pl.np)) != FR_OK) return st;
     float ms = 0.f;
-    if ((st = run_sweep(ctx, g, part, pl, opt, &ms)) != FR_OK) return st;
+    std::vector<Ctl> C;
+    bool queued = false;
+    const int qt = queue_size_for(ctx, pl, opt);
+    if (qt >= 0) {
+        // every pair in one launch, each as soon as its predecessors on its blocks committed
+        if ((st = run_queue_sweep(ctx, g, part, pl, opt, qt, &ms, &queued, &C)) != FR_OK) {
+            sum.status = st;
+            if (summary) *summary = sum;
+            return st;
+        }
+        // a pair outgrew its cluster: part is restored; plan again and go round by round
+        if (!queued && (st = plan_sweep(ctx, g, part, k, eps, alpha, opt, &pl)) != FR_OK) return st;
+    }
+    ctx->last_queue = queued;
+    if (!queued) {
+        if ((st = run_sweep(ctx, g, part, pl, opt, &ms)) != FR_OK) return st;
+        C.assign(pl.nr, Ctl());
+        CK(cudaMemcpyAsync(C.data(), ctx->ctl, sizeof(Ctl) * pl.nr, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     std::vector<PairAcc> A(pl.np);
     std::vector<SideDev> S(2 * pl.np);
-    std::vector<Ctl> C(pl.nr);
-    std::vector<int> pa(pl.np), pb(pl.np);
+    const std::vector<int> &pa = pl.pa, &pb = pl.pb;
     std::vector<FmRes> FR(opt->fm_permille > 0 ? pl.np : 0);
     if (!FR.empty())
         CK(cudaMemcpyAsync(FR.data(), ctx->fm.res, sizeof(FmRes) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(S.data(), ctx->sides, sizeof(SideDev) * 2 * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(C.data(), ctx->ctl, sizeof(Ctl) * pl.nr, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(pa.data(), ctx->pair_a, sizeof(int) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(pb.data(), ctx->pair_b, sizeof(int) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<long long> qst(queued ? 4 * ctx->last_queue_clusters : 0);
+    for (int i = 0; i < (int)qst.size() / 4; ++i)
+        CK(cudaMemcpyAsync(&qst[4 * i], ctx->q_host[i].stat, 4 * sizeof(long long), cudaMemcpyDeviceToHost,
+                           ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     fr_status bad = FR_OK;
-    for (int r = 0; r < pl.nr && bad == FR_OK; ++r) bad = status_from_ctl(ctx, C[r], "fr_refine_batch");
+    for (size_t r = 0; r < C.size() && bad == FR_OK; ++r) bad = status_from_ctl(ctx, C[r], "fr_refine_batch");
     if (bad != FR_OK) {
         // leave part exactly as it was
         CK(cudaMemcpyAsync(part, ctx->part_backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -596,7 +606,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
         return bad;
     }
     long long flow_ns = 0;
-    for (int r = 0; r < pl.nr; ++r)
+    for (size_t r = 0; r < C.size(); ++r)
         flow_ns += C[r].timers[T_FLOW1] + C[r].timers[T_GR] + C[r].timers[T_FLOW2] + C[r].timers[T_CL_FLOW] +
                    C[r].timers[T_CL_RETURN];
     {
@@ -614,12 +624,14 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
         }
         P.n = g->n;
         P.nnz = g->nnz;
-        for (int r = 0; r < pl.nr; ++r) {
+        for (size_t r = 0; r < C.size(); ++r) {
             for (int t = 0; t < T_COUNT && t < 12; ++t) P.phase_ms[t] += C[r].timers[t] * 1e-6;
-            P.bfs_visited += C[r].vq_total;
+            if (!queued) {   // (per step; the queue sweep sums them per cluster below)
+                P.bfs_visited += C[r].vq_total;
+                P.corridor_n += C[r].nu;
+                P.corridor_arcs += C[r].mu;
+            }
             P.bfs_arcs += C[r].arcs_scanned;
-            P.corridor_n += C[r].nu;
-            P.corridor_arcs += C[r].mu;
             P.pulses += C[r].pulses;
             P.relabels += C[r].relabels;
             P.gr_arcs += C[r].gr_arcs;
@@ -636,6 +648,15 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.fallback_pairs += C[r].fallback;
             for (int t = 0; t < 3; ++t) P.fm_ms[t] += C[r].timers[T_FM_SORT + t] * 1e-6;
         }
+        for (size_t i = 0; i + 3 < qst.size(); i += 4) {
+            P.bfs_visited += qst[i];
+            P.corridor_n += qst[i + 1];
+            P.corridor_arcs += qst[i + 2];
+        }
+        P.queue = queued ? 1 : 0;
+        P.queue_ctas = queued ? ctx->last_queue_ctas : 0;
+        P.queue_clusters = queued ? ctx->last_queue_clusters : 0;
+        P.queue_fallbacks = ctx->queue_fallbacks;
     }
     for (int r = 0; r < pl.nr; ++r)
         for (int i = pl.off[r]; i < pl.off[r + 1]; ++i) {
@@ -660,8 +681,11 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
                 R.iters = 1;
                 R.alpha_final = alpha;
                 R.status = FR_OK;
-                R.pulses = C[r].pulses; R.relabels = C[r].relabels;
-                R.bfs_levels = C[r].levels; R.scc_rounds = C[r].scc_rounds; R.ncomp = a.ncomp;
+                if (!queued) {   // step-wide counters of the pair's round (the queue keeps none per pair)
+                    R.pulses = C[r].pulses; R.relabels = C[r].relabels;
+                    R.bfs_levels = C[r].levels; R.scc_rounds = C[r].scc_rounds;
+                }
+                R.ncomp = a.ncomp;
                 R.cut_fm = a.oldcut;
                 if (!FR.empty()) {   // before = before the FM step
                     R.cut_before = FR[i].cut0;

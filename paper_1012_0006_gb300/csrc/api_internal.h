@@ -10,6 +10,7 @@
 #include "round_kernel.cuh"
 #include "fm_kernel.cuh"
 #include "mt_kernel.cuh"
+#include "queue_sweep.cuh"
 
 constexpr int kMaxK = 1024;                 // blocks per partition (quotient graph in device bitmaps)
 constexpr size_t kHostStage = 8u << 20;     // pinned staging for small host<->device copies
@@ -112,6 +113,19 @@ struct fr_ctx {
     fr_profile_info prof = {};
     std::vector<float> round_ms;   // per round: scan, step 1, cluster kernels, step 2 (profiling)
     std::vector<float> pair_ms;    // per pair: round, cluster start and end after the round's first start
+    // queue sweep (every pair of a sweep in one launch of clusters, see queue_sweep.cu):
+    // resident clusters of the queue kernel per cluster size, and the per-cluster
+    // workspaces of the last size used (allocated on first use)
+    int q_cap[kNumClusterSizes] = {0, 0, 0, 0, 0};
+    void *q_mem = nullptr;
+    size_t q_bytes = 0;
+    int q_ctas = 0, q_clusters = 0, q_n = 0, q_nnz = 0, q_k = 0, q_reps = 0, q_np = 0;
+    long long q_nu = 0, q_mu = 0, q_vq = 0;
+    fr::QSlot *q_slots = nullptr;              // device array [q_clusters]
+    std::vector<fr::QSlot> q_host;             // the same descriptors on the host
+    int *q_ticket = nullptr, *q_gabort = nullptr, *q_prev = nullptr, *q_crank = nullptr;
+    bool last_queue = false;                   // the last fr_refine_batch ran as a queue sweep
+    int last_queue_ctas = 0, last_queue_clusters = 0, queue_fallbacks = 0;
 };
 
 struct fr_corridor {
@@ -121,6 +135,18 @@ struct fr_corridor {
     int32_t *part;
     fr_graph g;
     long long Ubase, Lmax;
+};
+
+// A planned sweep: pairs in round order (pa, pb), rounds, budgets, launch shapes.
+struct BatchPlan {
+    int np, nr;
+    std::vector<int> off;      // round offsets
+    std::vector<int> grid;     // persistent-kernel CTAs per round
+    int tpb, k;
+    long long Ubase, Lmax, totcut;
+    std::vector<long long> est_max;   // estimated corridor vertices of each round's largest pair
+    double avg_degree = 12.0;
+    std::vector<int> pa, pb;   // the pairs in round order
 };
 
 void ctx_error(fr_ctx *ctx, const char *fmt, ...);
@@ -167,4 +193,15 @@ cudaError_t launch_round(fr_ctx *ctx, fr::Work &w, int grid, int tpb, cudaStream
 cudaError_t launch_clusters(fr_ctx *ctx, fr::Work &w, long long est_pair_vertices, double avg_degree, int force,
                             cudaStream_t st, int *nl);
 void release_corridor(fr_ctx *ctx);
+void free_queue(fr_ctx *ctx);
+// Index into fr_ctx::kClusterSizes of the queue sweep's cluster size for plan pl, or -1
+// when the queue does not apply (FM step, no cluster capacity, estimate beyond 16 CTAs).
+int queue_size_for(fr_ctx *ctx, const BatchPlan &pl, const fr_options *opt);
+// Runs the sweep of plan pl as one queue launch with clusters of kClusterSizes[t] CTAs.
+// On success *ran = true and ctls holds one control block per cluster (statistics); if
+// a pair outgrew the per-cluster workspace, part and the idle state are restored and
+// *ran = false (the caller plans the sweep again and runs it round by round).  Other
+// device errors restore part and return the error.
+fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const BatchPlan &pl, const fr_options *opt,
+                          int t, float *ms, bool *ran, std::vector<fr::Ctl> *ctls);
 void destroy_graph_cache(fr_ctx *ctx);

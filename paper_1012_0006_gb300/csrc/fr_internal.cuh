@@ -48,7 +48,9 @@ enum TimerIdx { T_BFS = 0, T_SELECT, T_LID, T_BUILD, T_FLOW1, T_GR, T_FLOW2, T_R
 
 enum SideCode { SS_EXPAND = 1, SS_SELECT = 2, SS_DONE = 3 };
 
-enum ErrCode { E_OK = 0, E_INVALID = 1, E_ITER = 4, E_TOO_LARGE = 5, E_ABORT = 6, E_INTERNAL = 7 };
+// E_MISFIT: a pair's corridor outgrew the per-pair workspace of a queue sweep (visit
+// list, network or a cluster's shared memory); the sweep is run again round by round.
+enum ErrCode { E_OK = 0, E_INVALID = 1, E_ITER = 4, E_TOO_LARGE = 5, E_ABORT = 6, E_INTERNAL = 7, E_MISFIT = 8 };
 
 struct GraphDev {
     const int *xadj, *adjncy, *adjwgt, *vwgt;
@@ -71,7 +73,7 @@ struct GraphDev {
 
 // Side of block `blk` of graph Gr in this step, or -1.
 __device__ __forceinline__ int side_of(const GraphDev &Gr, int blk) {
-    const int s = __ldg(Gr.sob + blk);
+    const int s = __ldcg(Gr.sob + blk);   // (a queue sweep rewrites sob per pair: no read-only cache)
     return s < 0 ? -1 : s + Gr.sbase;
 }
 
@@ -107,6 +109,8 @@ struct PairAcc {
                          // launch, 2 solved by the second, 3 left to the grid-wide flow
     int ord;             // the pair whose network is the ord-th largest of the round (slot ord)
     unsigned long long t0, t1;   // global timer when a cluster took the pair and finished it
+    int done;            // queue sweep: 1 once the pair's commit is visible (release / acquire)
+    int pad;
 };
 
 struct Ctl {
@@ -179,6 +183,8 @@ struct Work {
     int pad_w2;
     unsigned long long seed;
     long long pulse_cap;
+    int *crank;                  // per graph arc: rank among its row's corridor arcs (NULL: outs holds it)
+    const int *gabort;           // queue sweep: abort flag of the whole sweep (NULL otherwise)
 };
 
 // ------------------------------------------------------------ device helpers --

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("pulse_cap", ctypes.c_int64), ("checked", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
                 ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
-                ("pre_waves", ctypes.c_int32), ("fm_permille", ctypes.c_int32), ("mt_alpha", ctypes.c_int32)]
+                ("pre_waves", ctypes.c_int32), ("fm_permille", ctypes.c_int32), ("mt_alpha", ctypes.c_int32),
+                ("sweep_sched", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -108,7 +109,9 @@ class ProfileInfo(ctypes.Structure):
                 ("cluster_remote_arcs", ctypes.c_int64),
                 ("fallback_pairs", ctypes.c_int64),
                 ("scan_listed", ctypes.c_int64), ("scan_rows", ctypes.c_int64), ("scan_arcs", ctypes.c_int64),
-                ("fm_ms", ctypes.c_double * 3), ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5)]
+                ("fm_ms", ctypes.c_double * 3), ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5),
+                ("queue", ctypes.c_int32), ("queue_ctas", ctypes.c_int32), ("queue_clusters", ctypes.c_int32),
+                ("queue_fallbacks", ctypes.c_int32)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")

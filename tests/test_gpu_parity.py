@@ -225,6 +225,74 @@ def test_batch_rgg3d_4M_full(F, ctx):
     _check_batch(F, ctx, I.config(4))
 
 
+# --------------------------------------------------------- queue sweep --
+
+def _queue_ran(ctx):
+    p = ctx.profile()
+    return p["queue"], p["queue_fallbacks"]
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_batch_random_small_both_schedules(F, ctx, sched):
+    """The queue sweep (0) and the round-by-round sweep (1) both give the oracle's
+    partition and per-pair results on random graphs of up to 2,000 vertices and k <= 8."""
+    for seed in range(12):
+        w = I.random_small(2100 + seed, n_max=2000, k_max=8)
+        _check_batch(F, ctx, w, dict(mb_reps=1 + seed % 2, seed=seed, sweep_sched=sched))
+
+
+@pytest.mark.parametrize("case", ["grid3d64", "rgg3d262K", "grid2d", "weighted_rgg3d_k128"])
+def test_queue_sweep_equals_round_sweep(F, ctx, case):
+    """Same partition, per-pair results and totals from both schedules, and the oracle's."""
+    if case == "grid3d64":
+        w = I.config(3, scale=1 / 8)
+    elif case == "rgg3d262K":
+        w = I.config(4, scale=1 / 16)
+    elif case == "grid2d":
+        w = I.config(1)
+    else:
+        n = 65536
+        xadj, adj, coords = I.rgg(3, n, I.rgg_radius(3, n, 12.0), 777)
+        wgt = I.edge_weights(xadj, adj, 1, 10, 778)
+        vw = I.uniform_i32(n, 1, 4, 779)
+        part = I.rcb(coords, vw, 128)
+        I.noise(xadj, adj, vw, 128, part, -10000, 780)
+        w = dict(name="rgg3d k128", n=n, nnz=len(adj), xadj=xadj, adjncy=adj, adjwgt=wgt, vwgt=vw, part=part,
+                 k=128, eps=0.03, alpha=2.0, mb=1)
+    pq, sq = _check_batch(F, ctx, w, dict(sweep_sched=0))
+    ran, _ = _queue_ran(ctx)
+    assert ran == 1
+    pr, sr = _check_batch(F, ctx, w, dict(sweep_sched=1))
+    assert _queue_ran(ctx)[0] == 0
+    assert _torch().equal(pq, pr)
+    assert (sq["cut_after"], sq["accepted"], sq["corridor_arcs"]) == (sr["cut_after"], sr["accepted"],
+                                                                         sr["corridor_arcs"])
+
+
+def test_queue_sweep_that_outgrows_its_clusters_runs_round_by_round(F):
+    """Forced 4-CTA clusters on the 2D rgg at alpha = 16 (corridors of ~31,000 vertices,
+    far beyond 4 CTAs' shared memory): the queue sweep stops, part is restored, and the
+    sweep runs round by round -- the oracle's partition all the same."""
+    w = dict(I.config(2), alpha=16.0, mb=1)
+    with F.Context(0) as c:
+        _check_batch(F, c, w, dict(cluster_ctas=4))
+        ran, fallbacks = _queue_ran(c)
+        assert ran == 0 and fallbacks == 1
+
+
+def test_queue_sweep_repeated_runs_are_identical(F, ctx):
+    """Pairs start in an order that depends on timing; the results may not."""
+    w = I.config(4, scale=1 / 16)
+    g, part0 = _dev(F, w)
+    parts = []
+    for _ in range(4):
+        part = part0.clone()
+        ctx.refine_batch(g, part, w["k"], w["eps"], w["alpha"], F.default_options(mb=1))
+        assert _queue_ran(ctx)[0] == 1
+        parts.append(part)
+    assert all(_torch().equal(parts[0], p) for p in parts[1:])
+
+
 def test_batch_equals_pairs_in_round_order(F, ctx):
     w = I.config(3, scale=1 / 64)
     g, part = _dev(F, w)
