@@ -415,6 +415,7 @@ typedef struct fr_profile_info {
     int32_t queue_ctas;       /* CTAs per cluster of that queue sweep */
     int32_t queue_clusters;   /* clusters it launched */
     int32_t queue_fallbacks;  /* queue sweeps of this context that a pair outgrew (run round by round) */
+    double queue_scan_ms;     /* queue sweep: the pairs' boundary scans, summed over pairs (in-kernel timers) */
 } fr_profile_info;
 
 /* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with

@@ -647,6 +647,7 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.scan_arcs += C[r].scan_arcs;
             P.fallback_pairs += C[r].fallback;
             for (int t = 0; t < 3; ++t) P.fm_ms[t] += C[r].timers[T_FM_SORT + t] * 1e-6;
+            P.queue_scan_ms += C[r].timers[T_QSCAN] * 1e-6;
         }
         for (size_t i = 0; i + 3 < qst.size(); i += 4) {
             P.bfs_visited += qst[i];

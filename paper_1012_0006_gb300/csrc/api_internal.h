@@ -124,6 +124,9 @@ struct fr_ctx {
     fr::QSlot *q_slots = nullptr;              // device array [q_clusters]
     std::vector<fr::QSlot> q_host;             // the same descriptors on the host
     int *q_ticket = nullptr, *q_gabort = nullptr, *q_prev = nullptr, *q_crank = nullptr;
+    int *qb_sorted = nullptr, *qb_start = nullptr, *qb_cnt = nullptr, *qb_app = nullptr, *qb_pool = nullptr,
+        *qb_lst = nullptr;
+    int qb_cap = 0;
     bool last_queue = false;                   // the last fr_refine_batch ran as a queue sweep
     int last_queue_ctas = 0, last_queue_clusters = 0, queue_fallbacks = 0;
 };

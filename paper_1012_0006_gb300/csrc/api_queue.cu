@@ -30,7 +30,7 @@ constexpr unsigned long long kWaitNs = 10ull * 1000 * 1000 * 1000;   // one depe
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct QCaps {
-    long long nu, mu, vq, words;
+    long long nu, mu, vq;
 };
 
 // Per-pair capacities of a cluster of `ctas` CTAs: a network that fits its shared
@@ -41,7 +41,6 @@ QCaps caps_for(int ctas, int n) {
     c.nu = (long long)ctas * dyn / 28 + 64;
     c.mu = (long long)ctas * dyn / 16 + 64;
     c.vq = std::min<long long>(n, std::max<long long>(4 * c.nu, 1 << 16));
-    c.words = n / 32 + 2;
     return c;
 }
 
@@ -53,7 +52,6 @@ size_t slot_bytes(const QCaps &c, int ctas, int k, int reps) {
     add(sizeof(Ctl), 1);
     add(8, 3LL * 2 * kHistBins);                    // hist
     add(4, ctas + 1);                               // cta_cnt
-    add(4, c.words);                                // cbits
     add(4, c.vq); add(4, c.vq);                     // vq_v vq_s
     for (int i = 0; i < 21; ++i) add(4, c.nu + 1);  // gid .. sinkc, pcur
     add(8, c.nu); add(8, c.nu);                     // ex cw
@@ -85,7 +83,12 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
     const int cc = std::max(clusters, ctx->q_ctas == ctas ? ctx->q_clusters : 0);
     const QCaps c = caps_for(ctas, nn);
     const size_t per = slot_bytes(c, ctas, kk, rr);
-    size_t bytes = al256(4) + al256(4) + al256(8ull * pp) + al256(4ull * mm) + al256(sizeof(QSlot) * cc) + per * cc;
+    // per-block candidate lists: the sweep's candidates bucketed, and a region per block
+    // for the commits' appends (a sweep that fills one runs again round by round)
+    const long long qcap = std::max<long long>(4096, 8LL * ((nn + kk - 1) / kk));
+    size_t bytes = al256(4) + al256(4) + al256(8ull * pp) + al256(4ull * mm) + al256(sizeof(QSlot) * cc) + per * cc +
+                   al256(4ull * nn) + al256(4ull * (kk + 1)) + 2 * al256(4ull * kk) + al256(4ull * kk * qcap) +
+                   al256(4ull * nn);
     if (ctx->arena_limit && bytes + ctx->base_bytes + ctx->pair_bytes + ctx->reps_bytes > ctx->arena_limit) {
         ctx_error(ctx, "queue sweep workspace exceeds the arena bound");
         return FR_ERR_OOM;
@@ -107,6 +110,13 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
     ctx->q_prev = take<int>(p, 2LL * pp);
     ctx->q_crank = take<int>(p, mm);
     ctx->q_slots = take<QSlot>(p, cc);
+    ctx->qb_sorted = take<int>(p, nn);
+    ctx->qb_start = take<int>(p, kk + 1);
+    ctx->qb_cnt = take<int>(p, kk);
+    ctx->qb_app = take<int>(p, kk);
+    ctx->qb_pool = take<int>(p, (long long)kk * qcap);
+    ctx->qb_lst = take<int>(p, nn);
+    ctx->qb_cap = (int)qcap;
     ctx->q_host.assign(cc, QSlot());
     for (int i = 0; i < cc; ++i) {
         QSlot &S = ctx->q_host[i];
@@ -115,7 +125,6 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
         S.ctl = take<Ctl>(p, 1);
         S.hist = take<long long>(p, 3LL * 2 * kHistBins);
         S.cta_cnt = take<int>(p, ctas + 1);
-        S.cbits = take<unsigned int>(p, c.words);
         S.vq_v = take<int>(p, c.vq); S.vq_s = take<int>(p, c.vq);
         int **v21[21] = {&S.gid, &S.sid, &S.off, &S.infc, &S.fx, &S.lab, &S.rflag, &S.color, &S.scc, &S.vc,
                          &S.fq0, &S.fq1, &S.cid, &S.cpair, &S.cmin, &S.indeg, &S.outoff, &S.ocur, &S.plist,
@@ -130,9 +139,8 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
         S.hkey = take<unsigned long long>(p, (long long)rr * c.nu);
         S.sw_absd = take<long long>(p, rr); S.sw_j = take<int>(p, rr);
         S.stat = take<long long>(p, 4);
-        // idle state: no block paired, no corridor bit set
+        // idle state: no block paired
         CK(cudaMemsetAsync(S.sob, 0xFF, sizeof(int) * (size_t)kk, ctx->stream));
-        CK(cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
     }
     CK(cudaMemcpyAsync(ctx->q_slots, ctx->q_host.data(), sizeof(QSlot) * cc, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -140,15 +148,12 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
     return FR_OK;
 }
 
-// After a failed or abandoned queue sweep: BFS marks, corridor bits and block sides idle.
+// After a failed or abandoned queue sweep: BFS marks and block sides idle.
 fr_status reset_queue_idle(fr_ctx *ctx) {
     fr_status st = reset_idle(ctx);
     if (st != FR_OK) return st;
-    const QCaps c = caps_for(ctx->q_ctas, ctx->q_n);
-    for (const QSlot &S : ctx->q_host) {
+    for (const QSlot &S : ctx->q_host)
         CK(cudaMemsetAsync(S.sob, 0xFF, sizeof(int) * (size_t)ctx->q_k, ctx->stream));
-        CK(cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
-    }
     CK(cudaStreamSynchronize(ctx->stream));
     return FR_OK;
 }
@@ -233,6 +238,12 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
     q.wt.mu_cap = (int)ctx->q_mu;
     q.wt.crank = ctx->q_crank;
     q.wt.total_n = g->n;
+    q.wt.qb_sorted = ctx->qb_sorted;
+    q.wt.qb_start = ctx->qb_start;
+    q.wt.qb_app = ctx->qb_app;
+    q.wt.qb_pool = ctx->qb_pool;
+    q.wt.qb_lst = ctx->qb_lst;
+    q.wt.qb_cap = ctx->qb_cap;
     q.slots = ctx->q_slots;
     q.np = pl.np;
     q.ticket = ctx->q_ticket;
@@ -250,12 +261,16 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
             CK(cudaMemsetAsync(ctx->q_host[i].ctl, 0, sizeof(Ctl), ctx->stream));
             CK(cudaMemsetAsync(ctx->q_host[i].stat, 0, 4 * sizeof(long long), ctx->stream));
         }
-        CK(launch_tail_fill(ctx->bl, ctx->blc, g->n, ctx->stream));
+        CK(cudaMemsetAsync(ctx->qb_lst, 0xFF, sizeof(int) * (size_t)g->n, ctx->stream));
+        CK(cudaMemsetAsync(ctx->qb_cnt, 0, sizeof(int) * (size_t)pl.k, ctx->stream));
+        CK(launch_qb_build(ctx->bl, ctx->blc, part, pl.k, ctx->qb_cnt, ctx->qb_start, ctx->qb_app, ctx->qb_lst,
+                           ctx->qb_sorted, ctx->stream));
         CK(launch_queue_sweep(q, ctas, clusters, ctx->stream));
         return FR_OK;
     };
-    // launches of the sweep: prep, colouring, pair fill, tail fill, the queue kernel
-    const long long launches = 5;
+    // launches of the sweep: prep, compaction, colouring, pair fill, the three list
+    // kernels, the queue kernel
+    const long long launches = 8;
     std::vector<long long> key = {-7, (long long)(uintptr_t)g->xadj, (long long)(uintptr_t)part, g->n, g->nnz,
                                   pl.np, pl.Ubase, opt->mb, reps, (long long)opt->seed, opt->gr_interval,
                                   opt->inner_ops, opt->pulse_cap, (long long)(uintptr_t)ctx->base_mem,

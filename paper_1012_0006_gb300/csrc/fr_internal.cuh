@@ -44,7 +44,9 @@ enum TimerIdx { T_BFS = 0, T_SELECT, T_LID, T_BUILD, T_FLOW1, T_GR, T_FLOW2, T_R
                 // cluster kernel, summed over pairs: member scan and load, flow to t, return to s, reach
                 T_CL_LOAD, T_CL_FLOW, T_CL_RETURN, T_CL_REACH, T_CL_SCC, T_CL_MEMBERS, T_CL_RELABEL,
                 // FM step, summed over pairs: boundary sort and initial stacks, moves, rollback
-                T_FM_SORT, T_FM_MOVES, T_FM_FINISH, T_COUNT };
+                T_FM_SORT, T_FM_MOVES, T_FM_FINISH,
+                // queue sweep, summed over pairs: the single pair's boundary scan
+                T_QSCAN, T_COUNT };
 
 enum SideCode { SS_EXPAND = 1, SS_SELECT = 2, SS_DONE = 3 };
 
@@ -184,6 +186,15 @@ struct Work {
     unsigned long long seed;
     long long pulse_cap;
     int *crank;                  // per graph arc: rank among its row's corridor arcs (NULL: outs holds it)
+    int list_ids;                // 1: local ids in visit-list order (queue sweep), 0: in global id order
+    // queue sweep: the boundary candidates bucketed by block.  Block x's candidates are
+    // qb_sorted[qb_start[x] .. qb_start[x + 1]) (the sweep's start) and the first
+    // qb_app[x] entries of its region qb_pool[x * qb_cap ..) (appended by commits);
+    // qb_lst[v] = the block whose list got v's latest entry (-1: none).  NULL: the
+    // graph's global list (GraphDev.bl) serves.
+    const int *qb_sorted, *qb_start;
+    int *qb_app, *qb_pool, *qb_lst;
+    int qb_cap;
     const int *gabort;           // queue sweep: abort flag of the whole sweep (NULL otherwise)
 };
 

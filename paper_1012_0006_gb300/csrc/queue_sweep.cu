@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TPB, 1) queue_kernel(QueueArgs q, size_t smem_
             w.ctl = S.ctl;
             w.prev_err = nullptr;
             w.ngraphs = 1; w.npairs = 1; w.nsides = 2;
-            w.vq_v = S.vq_v; w.vq_s = S.vq_s; w.cbits = S.cbits;
+            w.vq_v = S.vq_v; w.vq_s = S.vq_s; w.cbits = nullptr;   // (ids in visit-list order: no bitmap)
             w.gid = S.gid; w.sid = S.sid; w.off = S.off; w.head = S.head; w.rev = S.rev; w.res = S.res;
             w.cap = S.cap; w.infc = S.infc; w.fx = S.fx; w.lab = S.lab; w.rflag = S.rflag; w.color = S.color;
             w.scc = S.scc; w.vc = S.vc; w.ex = S.ex; w.border = S.border; w.side_out = S.side_out;
@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(TPB, 1) queue_kernel(QueueArgs q, size_t smem_
             w.sw_absd = S.sw_absd; w.sw_j = S.sw_j;
             w.cluster_mode = 1;
             w.cl_tier = 0;
+            w.list_ids = 1;
             w.gabort = q.gabort;
             s_w = w;
             g_nsync = 0;
@@ -226,20 +227,58 @@ cudaError_t queue_capacity(int cluster, int *max_clusters) {
 
 size_t queue_smem() { return g_queue_dyn_smem > 0 ? (size_t)g_queue_dyn_smem : 0; }
 
-// bl[*blc .. n) = -1: entries a queue sweep's commits have not written yet read as
-// "no vertex" instead of a stale id from an earlier sweep.
-__global__ void tail_fill_kernel(int *bl, const int *blc, int n) {
-    const long long start = *blc;
-    for (long long i = start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        bl[i] = -1;
+// The sweep's boundary candidates bucketed by block (counting sort; order inside a
+// block does not matter): counts, offsets, placement; every listed vertex records its
+// block in lst (the others hold -1, set by the host).
+__global__ void qb_count_kernel(const int *bl, const int *blc, const int *part, int *cnt, int *lst) {
+    const int m = *blc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int v = bl[i], x = part[v];
+        atomicAdd(cnt + x, 1);
+        lst[v] = x;
+    }
 }
 
-cudaError_t launch_tail_fill(int *bl, const int *blc, int n, cudaStream_t st) {
+__global__ void qb_offsets_kernel(int *cnt, int *start, int *app, int k) {
+    // one CTA of 1024 threads, k <= 1024: exclusive scan of cnt into start; cnt and app
+    // are cleared for the placement pass and the sweep's appends
+    __shared__ int s[1024];
+    const int t = threadIdx.x;
+    int c = t < k ? cnt[t] : 0;
+    s[t] = c;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int y = t >= d ? s[t - d] : 0;
+        __syncthreads();
+        s[t] += y;
+        __syncthreads();
+    }
+    if (t < k) {
+        start[t] = s[t] - c;
+        cnt[t] = 0;
+        app[t] = 0;
+    }
+    if (t == 0) start[k] = s[1023];
+}
+
+__global__ void qb_place_kernel(const int *bl, const int *blc, const int *part, int *fill, const int *start,
+                                int *sorted) {
+    const int m = *blc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int v = bl[i], x = part[v];
+        sorted[start[x] + atomicAdd(fill + x, 1)] = v;
+    }
+}
+
+cudaError_t launch_qb_build(const int *bl, const int *blc, const int *part, int k, int *cnt, int *start, int *app,
+                            int *lst, int *sorted, cudaStream_t st) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    tail_fill_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, n);
+    if (k > 1024) return cudaErrorInvalidValue;
+    qb_count_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, part, cnt, lst);
+    qb_offsets_kernel<<<1, 1024, 0, st>>>(cnt, start, app, k);
+    qb_place_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, part, cnt, start, sorted);
     return cudaGetLastError();
 }
 

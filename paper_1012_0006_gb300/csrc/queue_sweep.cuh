@@ -9,16 +9,15 @@
 
 namespace fr {
 
-// Per-cluster workspace: the network, visit list, corridor bitmap and control block of
+// Per-cluster workspace: the network, visit list and control block of
 // the pair the cluster is working on.  Capacities are the QueueArgs' nu_cap / mu_cap /
-// vq_cap; the bitmap has n / 32 + 2 words.
+// vq_cap.
 struct QSlot {
     GraphDev *graph;      // this cluster's copy of the graph descriptor (its own sob)
     int *sob;             // [k] side of each block for the current pair, -1 otherwise
     Ctl *ctl;
     long long *hist;      // [3 * 2 * kHistBins]
     int *cta_cnt;         // [cluster size + 1]
-    unsigned int *cbits;
     int *vq_v, *vq_s;
     int *gid, *sid, *off, *infc, *fx, *lab, *rflag, *color, *scc, *vc, *fq0, *fq1;
     int *cid, *cpair, *cmin, *indeg, *outoff, *ocur, *plist, *sinkc, *pcur;
@@ -46,7 +45,10 @@ cudaError_t launch_queue_sweep(const QueueArgs &q, int cluster, int clusters, cu
 // Clusters of `cluster` CTAs the queue kernel can keep resident at once (0: none).
 cudaError_t queue_capacity(int cluster, int *max_clusters);
 size_t queue_smem();   // dynamic shared memory of one CTA of the queue kernel
-// bl[*blc .. n) = -1 (before a queue sweep; *blc is read on the device)
-cudaError_t launch_tail_fill(int *bl, const int *blc, int n, cudaStream_t st);
+// The candidate list bl[0, *blc) bucketed by block into sorted / start (k + 1 entries);
+// lst[v] = part[v] for listed v (the caller sets every entry to -1 first); cnt (k) is
+// scratch, app (k) is cleared.  k <= 1024.
+cudaError_t launch_qb_build(const int *bl, const int *blc, const int *part, int k, int *cnt, int *start, int *app,
+                            int *lst, int *sorted, cudaStream_t st);
 
 }  // namespace fr

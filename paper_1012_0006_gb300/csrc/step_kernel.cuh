@@ -64,7 +64,6 @@ struct ClusterGrp {
         }
         cooperative_groups::this_cluster().sync();
         if (threadIdx.x == 0) {
-            (void)ld_acquire(&w.ctl->bar_gen);   // as the grid barrier's wait: later loads see other CTAs' writes
             int v;
             asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(slot) : "memory");
             s_ok = v == 0;
@@ -230,14 +229,15 @@ struct StepKernel {
 
     // ------------------------------------------- boundary of a single pair --
     // S1 for the one pair of this step (a queue sweep runs each pair on its own, as
-    // soon as the pairs before it that share a block have committed): the listed
-    // candidates of blocks a and b are scanned like the round's boundary scan does,
-    // a vertex with a neighbour in the other block is a seed (BFS level 0), and
-    // omega(E_ab) sums the arcs seen from the lower-numbered block.  Other pairs'
-    // commits may append to the list while it is read: their entries are vertices
-    // of other blocks (or, before they are written, -1 or a stale id) and the seed
-    // mark is taken with a compare-and-swap, so a vertex listed twice counts once.
+    // soon as the pairs before it that share a block have committed): the candidates
+    // of blocks a and b (the per-block lists, or else the graph's list) are scanned
+    // like the round's boundary scan does, a vertex with a neighbour in the other
+    // block is a seed (BFS level 0), and omega(E_ab) sums the arcs seen from the
+    // lower-numbered block.  A list entry whose vertex has left the block since is
+    // skipped by its block test, and the seed mark is taken with a compare-and-swap,
+    // so a vertex listed twice counts once.
     __device__ bool scan_pair() {
+        unsigned long long t_scan = globaltimer();
         __shared__ int s_seed[TPB];
         __shared__ long long s_rcut[TPB];
         const GraphDev &Gr = w.graphs[0];
@@ -248,13 +248,37 @@ struct StepKernel {
         }
         const int lane = threadIdx.x & 31;
         const int wslot = threadIdx.x & ~31;
-        const int cnt = __ldcg(Gr.blc);
+        // the entries: the graph's list, or four segments (initial and appended
+        // candidates of block a, then of block b) laid end to end
+        int seg[4] = {0, 0, 0, 0};
+        const int *segp[4] = {nullptr, nullptr, nullptr, nullptr};
+        int cnt;
+        if (w.qb_sorted) {
+            const int blks[2] = {P.a, P.b};
+            for (int h = 0; h < 2; ++h) {
+                const int x = blks[h];
+                const int s0 = __ldcg(w.qb_start + x);
+                seg[2 * h] = __ldcg(w.qb_start + x + 1) - s0;
+                segp[2 * h] = w.qb_sorted + s0;
+                seg[2 * h + 1] = min(__ldcg(w.qb_app + x), w.qb_cap);
+                segp[2 * h + 1] = w.qb_pool + (long long)x * w.qb_cap;
+            }
+            cnt = seg[0] + seg[1] + seg[2] + seg[3];
+        } else {
+            cnt = __ldcg(Gr.blc);
+        }
         long long n_rows = 0, n_arcs = 0, cut = 0;
         for (long long base = G.warp * 32; base < cnt; base += G.nwarps * 32) {
             const long long li = base + lane;
             int v = 0, blk = -1, sd = -1, pb = -2, rs = 0, deg = 0;
             if (li < cnt) {
-                v = __ldcg(Gr.bl + li);
+                if (w.qb_sorted) {
+                    int q = (int)li, h = 0;
+                    while (q >= seg[h]) q -= seg[h++];
+                    v = __ldcg(segp[h] + q);
+                } else {
+                    v = __ldcg(Gr.bl + li);
+                }
                 if (v >= 0 && v < Gr.n) {
                     blk = __ldcg(Gr.part + v);
                     sd = blk == P.a ? 0 : (blk == P.b ? 1 : -1);
@@ -279,23 +303,33 @@ struct StepKernel {
             s_seed[threadIdx.x] = 0;
             s_rcut[threadIdx.x] = 0;
             __syncwarp();
-            for (int t0 = 0; t0 < total; t0 += 32) {
-                const int t = t0 + lane;
-                int src = 0;
+            // four chunks of 32 arcs per step, their loads issued together
+            for (int t0 = 0; t0 < total; t0 += 128) {
+                int e4[4], src4[4], pb4[4], blk4[4], u4[4], pu4[4];
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (__shfl_sync(FULL, incl, src + step - 1) <= t) src += step;
-                const int rs_s = __shfl_sync(FULL, rs, src);
-                const int ex_s = __shfl_sync(FULL, excl, src);
-                const int pb_s = __shfl_sync(FULL, pb, src);
-                const int blk_s = __shfl_sync(FULL, blk, src);
-                if (t < total) {
-                    const int e = rs_s + (t - ex_s);
-                    const int u = __ldg(Gr.adjncy + e);
-                    if (__ldcg(Gr.part + u) == pb_s) {
-                        s_seed[wslot + src] = 1;
-                        if (blk_s < pb_s) atomicAdd((unsigned long long *)&s_rcut[wslot + src],
-                                                    (unsigned long long)__ldg(Gr.adjwgt + e));
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + 32 * q + lane;
+                    int src = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (__shfl_sync(FULL, incl, src + step - 1) <= t) src += step;
+                    const int rs_s = __shfl_sync(FULL, rs, src);
+                    const int ex_s = __shfl_sync(FULL, excl, src);
+                    pb4[q] = __shfl_sync(FULL, pb, src);
+                    blk4[q] = __shfl_sync(FULL, blk, src);
+                    src4[q] = src;
+                    e4[q] = t < total ? rs_s + (t - ex_s) : -1;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u4[q] = e4[q] >= 0 ? __ldg(Gr.adjncy + e4[q]) : 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pu4[q] = e4[q] >= 0 ? __ldcg(Gr.part + u4[q]) : -3;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (e4[q] >= 0 && pu4[q] == pb4[q]) {
+                        s_seed[wslot + src4[q]] = 1;
+                        if (blk4[q] < pb4[q]) atomicAdd((unsigned long long *)&s_rcut[wslot + src4[q]],
+                                                        (unsigned long long)__ldg(Gr.adjwgt + e4[q]));
                     }
                 }
             }
@@ -323,7 +357,9 @@ struct StepKernel {
             if (cut) atomicAddLL(&w.pacc[0].oldcut, cut);
             if (Grp::rank() == 0) atomicAddLL(&w.ctl->scan_listed, (long long)cnt);
         }
-        return Grp::sync(w);
+        if (!Grp::sync(w)) return false;
+        timer_mark<Grp>(w, t_scan, T_QSCAN);
+        return true;
     }
 
     // ---------------------------------------------------------------- BFS --
@@ -563,11 +599,46 @@ struct StepKernel {
     }
 
     // -------------------------------------------------------------- local ids --
+    // With w.list_ids (the queue sweep: one pair, a cluster): the corridor vertices are
+    // numbered in the order of the visit list, by one scan over its entries -- work in
+    // the size of the BFS, not of the graph.  Nothing else depends on the numbering:
+    // cuts, residual sets and SCCs are sets, an SCC's key is the smallest global id
+    // of its members (computed in sweeps), and every edge is counted once by comparing
+    // its ends' ids.
+    __device__ bool lids_list() {
+        unsigned long long t0 = globaltimer();
+        const GraphDev &Gr = w.graphs[0];
+        long long nu = 0;
+        bool ok = grid_scan<TPB, Grp>(
+            w, vtotal, [&](long long e) -> int { return in_corridor(Gr, w.vq_v[e]) ? 1 : 0; },
+            [&](long long e, long long off) {
+                const int v = w.vq_v[e];
+                if (!in_corridor(Gr, v)) return;
+                if (off < w.nu_cap) {
+                    Gr.lid[v] = (int)off;
+                    w.gid[off] = v;
+                    w.sid[off] = w.vq_s[e];
+                } else {
+                    fail(w.ctl, E_MISFIT, 31);
+                }
+            },
+            &nu);
+        if (!ok) return false;
+        if (Grp::rank() == 0 && threadIdx.x == 0) {
+            w.ctl->nu = (int)nu;
+            w.ctl->hmax = (int)nu + 2;
+        }
+        if (!Grp::sync(w)) return false;
+        timer_mark<Grp>(w, t0, T_LID);
+        return true;
+    }
+
     // Union ids in increasing (base + v) order: the corridor vertices, found on the
     // visit list, set their bit in cbits; a scan over the words (popcounts, then
     // the set bits of each word in order) numbers them and clears the words again.
-    // The SCC labels rely on this order (smallest local id = smallest global id).
+    // The corridor export relies on this order (local ids ascending with global ids).
     __device__ bool lids() {
+        if (w.list_ids) return lids_list();
         unsigned long long t0 = globaltimer();
         for (long long e = G.tid; e < vtotal; e += G.size) {
             const int v = w.vq_v[e], s = w.vq_s[e];
@@ -630,16 +701,31 @@ struct StepKernel {
                 const GraphDev &Gr = w.graphs[P.g];
                 int bor = 0;
                 long long wdeg = 0;
-                const int j1 = __ldg(Gr.xadj + v + 1);
-                for (int j = __ldg(Gr.xadj + v); j < j1; ++j) {
-                    const int u = __ldg(Gr.adjncy + j);
-                    wdeg += __ldg(Gr.adjwgt + j);
-                    const int pu = __ldcg(Gr.part + u);
-                    int rk = -1;
-                    if (pu == P.a || pu == P.b) {
-                        if (__ldcg(Gr.lid + u) >= 0) rk = cnt++; else bor = 1;
+                const int j0 = __ldg(Gr.xadj + v), j1 = __ldg(Gr.xadj + v + 1);
+                // eight arcs at a time, the loads of each step issued together (the
+                // chain arc -> head's block -> head's local id is latency bound)
+                for (int jb = j0; jb < j1; jb += 8) {
+                    int u[8], c[8], pu[8], lu[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int j = min(jb + t, j1 - 1);
+                        u[t] = __ldg(Gr.adjncy + j);
+                        c[t] = __ldg(Gr.adjwgt + j);
                     }
-                    crank[Gr.ebase + j] = rk;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) pu[t] = __ldcg(Gr.part + u[t]);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) lu[t] = (pu[t] == P.a || pu[t] == P.b) ? __ldcg(Gr.lid + u[t]) : -1;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        if (jb + t >= j1) break;
+                        wdeg += c[t];
+                        int rk = -1;
+                        if (pu[t] == P.a || pu[t] == P.b) {
+                            if (lu[t] >= 0) rk = cnt++; else bor = 1;
+                        }
+                        crank[Gr.ebase + jb + t] = rk;
+                    }
                 }
                 w.off[i] = cnt;   // degree for now
                 w.border[i] = bor ? ((s & 1) ? 2 : 1) : 0;
@@ -667,8 +753,9 @@ struct StepKernel {
         if (!Grp::sync(w)) return false;
         // arcs, reverse arcs, residual = capacity: the corridor arcs of every row,
         // flattened over the lanes of a warp (warp_rows) so that long rows do not hold
-        // up one thread; arc e of row i goes to off[i] + crank[e].  ex[i] collects, for
-        // s-border rows, the capacity toward vertices off the s-border.
+        // up one thread and a row's arcs are read together; arc e of row i goes to
+        // off[i] + crank[e].  ex[i] collects, for s-border rows, the capacity toward
+        // vertices off the s-border.
         for (long long i = G.tid; i < nu; i += G.size) w.ex[i] = 0;
         if (!Grp::sync(w)) return false;
         warp_rows(
@@ -1184,7 +1271,7 @@ struct StepKernel {
                 if (__ldcg(&w.scc[i]) == (int)i) {
                     w.cid[i] = (int)off;
                     w.cpair[off] = w.sid[i] >> 1;
-                    w.cmin[off] = w.gid[i];
+                    w.cmin[off] = INT_MAX;   // the smallest global id of the members (below)
                     w.cw[off] = 0;
                     w.indeg[off] = 0;
                     w.ocur[off] = 0;
@@ -1220,6 +1307,7 @@ struct StepKernel {
                         const int cc = __ldcg(&w.cid[sc]);
                         w.vc[i] = cc;
                         atomicAddLL(&w.cw[cc], c);
+                        atomicMin(&w.cmin[cc], w.gid[i]);
                     }
                 }
             }
@@ -1479,6 +1567,15 @@ struct StepKernel {
         return true;
     }
 
+    // v onto the candidate list of block x unless its latest entry is there already
+    // (queue sweep; only the cluster holding a pair of x appends to x's list)
+    __device__ void qb_append(int v, int x) {
+        if (__ldcg(w.qb_lst + v) == x || atomicExch(w.qb_lst + v, x) == x) return;
+        const int pos = atomicAdd(w.qb_app + x, 1);
+        if (pos < w.qb_cap) w.qb_pool[(long long)x * w.qb_cap + pos] = v;
+        else fail(w.ctl, E_MISFIT, 320);
+    }
+
     // ---------------------------------------------------------------- commit --
     __device__ bool commit() {
         Ctl *ctl = w.ctl;
@@ -1502,7 +1599,16 @@ struct StepKernel {
                 const int v = w.gid[i];
                 Gr.part[v] = nb;
                 const int ob = (s & 1) ? Pd.b : Pd.a;
-                if (Gr.bl && nb != ob) {
+                if (w.qb_pool && nb != ob) {
+                    // the same upkeep on the per-block lists: v joins the list of its new
+                    // block, its neighbours left in the old block join that block's list
+                    qb_append(v, nb);
+                    const int j1 = __ldg(Gr.xadj + v + 1);
+                    for (int j = __ldg(Gr.xadj + v); j < j1; ++j) {
+                        const int x = __ldg(Gr.adjncy + j);
+                        if (__ldcg(Gr.part + x) == ob) qb_append(x, ob);
+                    }
+                } else if (Gr.bl && nb != ob) {
                     // A moved vertex may now be on a boundary, and so may its neighbours
                     // in its old block (the others had it as a foreign neighbour already).
                     if (!__ldcg(Gr.inb + v) && atomicExch(Gr.inb + v, 1) == 0) Gr.bl[atomicAdd(Gr.blc, 1)] = v;

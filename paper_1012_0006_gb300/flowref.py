@@ -111,7 +111,7 @@ class ProfileInfo(ctypes.Structure):
                 ("scan_listed", ctypes.c_int64), ("scan_rows", ctypes.c_int64), ("scan_arcs", ctypes.c_int64),
                 ("fm_ms", ctypes.c_double * 3), ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5),
                 ("queue", ctypes.c_int32), ("queue_ctas", ctypes.c_int32), ("queue_clusters", ctypes.c_int32),
-                ("queue_fallbacks", ctypes.c_int32)]
+                ("queue_fallbacks", ctypes.c_int32), ("queue_scan_ms", ctypes.c_double)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")
