@@ -237,8 +237,11 @@ def recorded_traffic(kernel):
 
 
 def bytes_model(P):
-    """Algorithmic HBM bytes per kernel type for one sweep (element bytes the method must touch)."""
+    """Algorithmic HBM bytes per kernel type for one sweep (element bytes the method must touch).
+    In a queue sweep every phase runs in the one queue kernel: its pairs' boundary scans
+    read the per-block candidate lists, and local ids come from the visit list alone."""
     n, nnz = P["n"], P["nnz"]
+    queue = bool(P.get("queue"))
     # boundary scan over the candidate list: entry and part[v] per listed vertex,
     # xadj per row of the round's blocks, adjncy and part[u] per arc of those rows
     scan = 8 * P["scan_listed"] + 8 * P["scan_rows"] + 8 * P["scan_arcs"]
@@ -246,7 +249,8 @@ def bytes_model(P):
     nc, m = P["corridor_n"], P["corridor_arcs"]
     bfs = 16 * vis + 12 * arcs                              # queue entries, dist, adjncy + part + dist per arc
     select = 4 * 8 * vis                                    # four radix passes over the overflow levels
-    lid = 12 * vis + (n // 8) * P["nrounds"] + 12 * nc      # marks, bitmap words, gid/sid/lid
+    # marks, bitmap words (round by round), gid/sid/lid
+    lid = 12 * vis + (0 if queue else (n // 8) * P["nrounds"]) + 12 * nc
     build = 12 * nc + 28 * m                                # rows, head, rev, res, cap, ranks
     cut = 24 * nc                                           # DAG of components, sweeps, eval, commit
     step = bfs + select + lid + build + cut
@@ -254,7 +258,7 @@ def bytes_model(P):
     # arc 24 B: head, reverse, residual, both capacities), results out (vertex 20 B,
     # arc residual 4 B)
     cluster = 52 * nc + 28 * m
-    return dict(scan=scan, step=step, bfs=bfs, build=build, cluster=cluster)
+    return dict(scan=scan, step=step, bfs=bfs, build=build, cluster=cluster, queue=scan + step + cluster)
 
 
 # ------------------------------------------------------------------ ours ----
@@ -335,10 +339,16 @@ def run_ours(args, world, rank, local, pg):
     clu_ms = statistics.median(p["cluster_ms"] for p in profs)
     bm = bytes_model(P)
     peak, peak_kind = measured_peak_gbs()
-    launches_per_round = 2 if clu_ms > 0 else 1          # step kernels per round
-    per = {"scan_kernel": (bm["scan"], scan_ms, nr), "step_kernel": (bm["step"], step_ms, nr * launches_per_round)}
-    if clu_ms > 0:
-        per["cluster_flow_kernel"] = (bm["cluster"], clu_ms, nr)
+    if P["queue"]:
+        # one queue kernel per sweep runs every phase of every pair; its setup launches
+        # (pair fill, clears, the per-block lists) are the rest
+        per = {"queue_kernel": (bm["queue"], clu_ms, 1), "queue_setup": (0, scan_ms, 5)}
+    else:
+        launches_per_round = 2 if clu_ms > 0 else 1          # step kernels per round
+        per = {"scan_kernel": (bm["scan"], scan_ms, nr),
+               "step_kernel": (bm["step"], step_ms, nr * launches_per_round)}
+        if clu_ms > 0:
+            per["cluster_flow_kernel"] = (bm["cluster"], clu_ms, nr)
     dominant = max(per, key=lambda kk: per[kk][1])
     kernels = {}
     for name, (byts, ms, nl) in per.items():
@@ -353,11 +363,20 @@ def run_ours(args, world, rank, local, pg):
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dominant,
                 "peak_kind": peak_kind, "bytes_per_launch": int(byts / nl), "launch_ms": round(ms / nl, 4)}
     ph = P["phase_ms"]
-    # wall time of the max flows: the cluster kernels (flow, reach and SCCs of every
-    # pair) plus the grid-wide flow phases of pairs left to them
-    flow_ms = clu_ms + ph["flow"] + ph["relabel"] + ph["return"]
+    if P["queue"]:
+        # the pairs' max flows overlap in the queue kernel's clusters: their summed
+        # in-kernel time (network load, flow to t, return) over the clusters running them
+        cp = P["cluster_phase_ms"]
+        flow_ms = (cp["load"] + cp["flow"] + cp["return"]) / max(P["queue_clusters"], 1)
+    else:
+        # wall time of the max flows: the cluster kernels (flow, reach and SCCs of every
+        # pair) plus the grid-wide flow phases of pairs left to them
+        flow_ms = clu_ms + ph["flow"] + ph["relabel"] + ph["return"]
     arcs_rate = reduce_sum(pg, P["corridor_arcs"] / max(flow_ms * 1e-3, 1e-12), dev)
     kernels.update({
+        "schedule": ({"queue": True, "cluster_ctas": P["queue_ctas"], "clusters": P["queue_clusters"],
+                      "boundary_scan_ms_summed_over_pairs": round(P["queue_scan_ms"], 3)}
+                     if P["queue"] else {"queue": False, "rounds": nr}),
         "phases_ms": {kk: round(v, 3) for kk, v in ph.items()},
         "bfs_gbs": round(bm["bfs"] / max(ph["bfs"] * 1e-3, 1e-12) / 1e9, 1),
         "cluster_phases_ms_summed_over_pairs": {kk: round(v, 3) for kk, v in P["cluster_phase_ms"].items()},

@@ -74,7 +74,8 @@ typedef struct fr_options {
     int64_t pulse_cap;     /* push-relabel pulse cap per flow (0: default 1<<20) */
     int32_t checked;       /* 1: verify CSR symmetry and weights on the device first */
     int32_t block_threads; /* launch shape; 0 = tuned default (see fr_autotune) */
-    int32_t grid_blocks;   /* CTAs of the persistent kernel; 0 = tuned default */
+    int32_t grid_blocks;   /* CTAs of the persistent kernel; 0 = tuned default (a queue sweep: at most
+                              this many CTAs in clusters; 0 = every cluster that fits at once) */
     int32_t gr_interval;   /* pulses between global relabels; 0 = tuned default */
     int32_t inner_ops;     /* push/relabel operations per vertex per pulse; 0 = default */
     int32_t pulse_passes;  /* lock-free pulse passes between grid barriers; 0 = default */

@@ -200,7 +200,9 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
                           int t, float *ms, bool *ran, std::vector<Ctl> *ctls) {
     *ran = false;
     const int ctas = fr_ctx::kClusterSizes[t];
-    const int clusters = std::max(1, std::min(ctx->q_cap[t], pl.np));
+    // resident clusters, or fewer when opt->grid_blocks bounds the CTAs
+    int clusters = std::max(1, std::min(ctx->q_cap[t], pl.np));
+    if (opt->grid_blocks > 0) clusters = std::max(1, std::min(clusters, opt->grid_blocks / ctas));
     const int reps = opt->mb_reps > 0 ? opt->mb_reps : 1;
     fr_status st = ensure_queue(ctx, ctas, clusters, g->n, g->nnz, pl.k, reps, pl.np);
     if (st != FR_OK) return st;
@@ -265,9 +267,16 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
         CK(cudaMemsetAsync(ctx->qb_cnt, 0, sizeof(int) * (size_t)pl.k, ctx->stream));
         CK(launch_qb_build(ctx->bl, ctx->blc, part, pl.k, ctx->qb_cnt, ctx->qb_start, ctx->qb_app, ctx->qb_lst,
                            ctx->qb_sorted, ctx->stream));
+        if (ctx->profiling) CK(cudaEventRecord(ctx->pev[0], ctx->stream));
         CK(launch_queue_sweep(q, ctas, clusters, ctx->stream));
+        if (ctx->profiling) CK(cudaEventRecord(ctx->pev[1], ctx->stream));
         return FR_OK;
     };
+    while (ctx->profiling && ctx->pev.size() < 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->pev.push_back(e);
+    }
     // launches of the sweep: prep, compaction, colouring, pair fill, the three list
     // kernels, the queue kernel
     const long long launches = 8;
@@ -338,6 +347,11 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
         if ((st = reset_queue_idle(ctx)) != FR_OK) return st;
         if (gab == E_MISFIT) {
             ++ctx->queue_fallbacks;
+            int where = 0;
+            for (const Ctl &x : *ctls)
+                if (x.error == E_MISFIT) { where = x.error_where; break; }
+            ctx_error(ctx, "queue sweep: a pair outgrew its cluster's workspace (check %d); ran round by round",
+                      where);
             return FR_OK;   // *ran = false: the caller runs the sweep round by round
         }
         Ctl c;
@@ -348,7 +362,12 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
         return status_from_ctl(ctx, c, "fr_refine_batch (queue sweep)");
     }
     if (ctx->profiling) {
-        ctx->prof.cluster_ms = *ms;   // the queue kernel is the sweep (its small setup launches included)
+        // the queue kernel alone; the setup launches before it (pair fill, clears, lists)
+        float qk = 0.f, pre = 0.f;
+        CK(cudaEventElapsedTime(&pre, ctx->ev0, ctx->pev[0]));
+        CK(cudaEventElapsedTime(&qk, ctx->pev[0], ctx->pev[1]));
+        ctx->prof.cluster_ms = qk;
+        ctx->prof.scan_ms = pre;
         std::vector<PairAcc> A(pl.np);
         CK(cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));

@@ -29,6 +29,9 @@ struct ClusterHdr {
     int nvcap, nacap;           // common capacities (identical in every CTA)
     int nv, na;                 // this CTA's vertices and arcs
     int counts[kClusterMax];    // scratch for the member scan (CTA 0's copy)
+    int counts2[kClusterMax];   // second scratch (byte prefix of the split)
+    int kloc[3][kClusterMax + 1];   // candidate splits (by arcs, by bytes, by vertices; CTA 0's copy)
+    int cabc[3][kClusterMax + 1];
     int grab[2];                // slot of the size order taken (CTA 0's copy, by parity)
     long long flow;
 };
@@ -271,9 +274,17 @@ struct ClusterFlow {
         }
         __threadfence();
         sync();
-        // arc prefix over members (each CTA a slice of the member list, each thread a
-        // contiguous part of it)
+        // arc and shared-memory byte prefixes over members (each CTA a slice of the
+        // member list, each thread a contiguous part of it), and three candidate splits
+        // into C contiguous ranges: equal arcs (the work of the flow), equal bytes (29
+        // per vertex, 16 or 20 per arc) and equal vertices.  Every CTA carves its arrays
+        // for the largest range's vertices and arcs, so the first candidate that fits
+        // shared memory is taken: the arc split where it fits, the others where the
+        // order of the vertices puts many light vertices together.
+        const int ab = w.narrow ? 16 : 20;
         {
+            const long long Btot = 29LL * V + (long long)ab * A;
+            const long long tot3[3] = {(long long)A, Btot, (long long)V};
             const int per = (V + C - 1) / C;
             const int k0 = min(V, per * rank), k1 = min(V, k0 + per);
             const int tper = (k1 - k0 + TPB - 1) / TPB;
@@ -283,41 +294,74 @@ struct ClusterFlow {
                 const int i = __ldcg(&pmem[k]);
                 mine += w.off[i + 1] - w.off[i];
             }
-            int tot;
+            int tot, btot;
             const int e0 = block_exclusive_scan<TPB>(mine, &tot);
-            if (threadIdx.x == 0) hdr0->counts[rank] = tot;
+            const int b0 = block_exclusive_scan<TPB>(29 * (s1 - s0) + ab * mine, &btot);
+            if (threadIdx.x == 0) {
+                hdr0->counts[rank] = tot;
+                hdr0->counts2[rank] = btot;
+            }
             sync();
             int run = e0;
-            for (int r = 0; r < rank; ++r) run += *(volatile int *)&hdr0->counts[r];
+            long long brun = b0;
+            for (int r = 0; r < rank; ++r) {
+                run += *(volatile int *)&hdr0->counts[r];
+                brun += *(volatile int *)&hdr0->counts2[r];
+            }
             sync();
-            // split points: klo[r] = the first member whose prefix reaches A * r / C, so
-            // the member whose arcs (prefix, prefix + degree] hold that target is the one
-            // before it; its thread writes klo and the range's first arc into CTA 0
+            // split points of candidate c: kloc[c][r] = the first member whose prefix
+            // reaches tot3[c] * r / C, so the member whose share (prefix, prefix + size]
+            // holds that target is the one before it; its thread writes the split and
+            // the range's first arc into CTA 0
             if (rank == 0 && threadIdx.x == 0) {
-                hdr->klo[0] = 0;
-                hdr->cab[0] = 0;
-                hdr->klo[C] = V;
-                hdr->cab[C] = A;
-                for (int r = 1; r < C; ++r)
-                    if ((long long)A * r / C <= 0) { hdr->klo[r] = 0; hdr->cab[r] = 0; }
+                for (int c = 0; c < 3; ++c) {
+                    hdr->kloc[c][0] = 0;
+                    hdr->cabc[c][0] = 0;
+                    hdr->kloc[c][C] = V;
+                    hdr->cabc[c][C] = A;
+                    for (int r = 1; r < C; ++r)
+                        if (tot3[c] * r / C <= 0) { hdr->kloc[c][r] = 0; hdr->cabc[c][r] = 0; }
+                }
             }
             for (int k = s0; k < s1; ++k) {
                 const int i = __ldcg(&pmem[k]);
                 const int d = w.off[i + 1] - w.off[i];
+                const int b = 29 + ab * d;
                 pacs[k] = run;
-                for (int r = 1; r < C; ++r) {
-                    const long long target = (long long)A * r / C;
-                    if (target > run && target <= run + d) {
-                        hdr0->klo[r] = k + 1;
-                        hdr0->cab[r] = run + d;
+                const long long lo3[3] = {(long long)run, brun, (long long)k};
+                const long long sz3[3] = {(long long)d, (long long)b, 1};
+                for (int c = 0; c < 3; ++c)
+                    for (int r = 1; r < C; ++r) {
+                        const long long target = tot3[c] * r / C;
+                        if (target > lo3[c] && target <= lo3[c] + sz3[c]) {
+                            hdr0->kloc[c][r] = k + 1;
+                            hdr0->cabc[c][r] = run + d;
+                        }
                     }
-                }
                 run += d;
+                brun += b;
             }
         }
         __threadfence();
         sync();
-        // the C ranges of about A / C arcs each, copied from CTA 0 (same in every CTA)
+        if (rank == 0 && threadIdx.x == 0) {
+            int pick = 0;
+            for (int c = 0; c < 3; ++c) {
+                int nvc = 0, nac = 0;
+                for (int r = 0; r < C; ++r) {
+                    nvc = max(nvc, hdr->kloc[c][r + 1] - hdr->kloc[c][r]);
+                    nac = max(nac, hdr->cabc[c][r + 1] - hdr->cabc[c][r]);
+                }
+                pick = c;
+                if (bytes_for(nvc, nac, w.narrow != 0) <= smem_bytes) break;
+            }
+            for (int r = 0; r <= C; ++r) {
+                hdr->klo[r] = hdr->kloc[pick][r];
+                hdr->cab[r] = hdr->cabc[pick][r];
+            }
+        }
+        sync();
+        // the C ranges, copied from CTA 0 (same in every CTA)
         if (threadIdx.x <= C && rank != 0) {
             hdr->klo[threadIdx.x] = *(volatile int *)&hdr0->klo[threadIdx.x];
             hdr->cab[threadIdx.x] = *(volatile int *)&hdr0->cab[threadIdx.x];
