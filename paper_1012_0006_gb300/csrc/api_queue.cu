@@ -30,7 +30,7 @@ constexpr unsigned long long kWaitNs = 10ull * 1000 * 1000 * 1000;   // one depe
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct QCaps {
-    long long nu, mu, vq;
+    long long nu, mu, vq, words, swords;
 };
 
 // Per-pair capacities of a cluster of `ctas` CTAs: a network that fits its shared
@@ -41,6 +41,8 @@ QCaps caps_for(int ctas, int n) {
     c.nu = (long long)ctas * dyn / 28 + 64;
     c.mu = (long long)ctas * dyn / 16 + 64;
     c.vq = std::min<long long>(n, std::max<long long>(4 * c.nu, 1 << 16));
+    c.words = n / 32 + 2;
+    c.swords = n / 32768 + 2;
     return c;
 }
 
@@ -52,6 +54,9 @@ size_t slot_bytes(const QCaps &c, int ctas, int k, int reps) {
     add(sizeof(Ctl), 1);
     add(8, 3LL * 2 * kHistBins);                    // hist
     add(4, ctas + 1);                               // cta_cnt
+    add(4, c.words);                                // cbits
+    add(4, c.words);                                // sdbits
+    add(4, c.swords);                               // sbits
     add(4, c.vq); add(4, c.vq);                     // vq_v vq_s
     for (int i = 0; i < 21; ++i) add(4, c.nu + 1);  // gid .. sinkc, pcur
     add(8, c.nu); add(8, c.nu);                     // ex cw
@@ -125,6 +130,9 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
         S.ctl = take<Ctl>(p, 1);
         S.hist = take<long long>(p, 3LL * 2 * kHistBins);
         S.cta_cnt = take<int>(p, ctas + 1);
+        S.cbits = take<unsigned int>(p, c.words);
+        S.sdbits = take<unsigned int>(p, c.words);
+        S.sbits = take<unsigned int>(p, c.swords);
         S.vq_v = take<int>(p, c.vq); S.vq_s = take<int>(p, c.vq);
         int **v21[21] = {&S.gid, &S.sid, &S.off, &S.infc, &S.fx, &S.lab, &S.rflag, &S.color, &S.scc, &S.vc,
                          &S.fq0, &S.fq1, &S.cid, &S.cpair, &S.cmin, &S.indeg, &S.outoff, &S.ocur, &S.plist,
@@ -139,8 +147,11 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
         S.hkey = take<unsigned long long>(p, (long long)rr * c.nu);
         S.sw_absd = take<long long>(p, rr); S.sw_j = take<int>(p, rr);
         S.stat = take<long long>(p, 4);
-        // idle state: no block paired
+        // idle state: no block paired, no corridor bit set
         CK(cudaMemsetAsync(S.sob, 0xFF, sizeof(int) * (size_t)kk, ctx->stream));
+        CK(cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
+        CK(cudaMemsetAsync(S.sdbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
+        CK(cudaMemsetAsync(S.sbits, 0, sizeof(unsigned int) * (size_t)c.swords, ctx->stream));
     }
     CK(cudaMemcpyAsync(ctx->q_slots, ctx->q_host.data(), sizeof(QSlot) * cc, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -148,12 +159,17 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
     return FR_OK;
 }
 
-// After a failed or abandoned queue sweep: BFS marks and block sides idle.
+// After a failed or abandoned queue sweep: BFS marks, corridor bits and block sides idle.
 fr_status reset_queue_idle(fr_ctx *ctx) {
     fr_status st = reset_idle(ctx);
     if (st != FR_OK) return st;
-    for (const QSlot &S : ctx->q_host)
+    const QCaps c = caps_for(ctx->q_ctas, ctx->q_n);
+    for (const QSlot &S : ctx->q_host) {
         CK(cudaMemsetAsync(S.sob, 0xFF, sizeof(int) * (size_t)ctx->q_k, ctx->stream));
+        CK(cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
+        CK(cudaMemsetAsync(S.sdbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
+        CK(cudaMemsetAsync(S.sbits, 0, sizeof(unsigned int) * (size_t)c.swords, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return FR_OK;
 }

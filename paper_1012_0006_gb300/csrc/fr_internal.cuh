@@ -141,6 +141,7 @@ struct Ctl {
     int fallback;             // pairs the cluster kernels left to the grid-wide flow
     int cl_next[2];           // next slot of the size order each cluster launch takes
     int cl_left;              // pairs the first cluster launch left (written by it only)
+    int vmin, vmax;           // queue sweep: smallest and largest vertex id on the pair's visit list
 };
 
 // Everything a kernel needs, passed by value.
@@ -186,7 +187,10 @@ struct Work {
     unsigned long long seed;
     long long pulse_cap;
     int *crank;                  // per graph arc: rank among its row's corridor arcs (NULL: outs holds it)
-    int list_ids;                // 1: local ids in visit-list order (queue sweep), 0: in global id order
+    int list_ids;                // 1: queue sweep (local ids by visit order, or by id over the window
+                                 //    of the visit list's ids), 0: in global id order
+    unsigned int *sbits;         // queue sweep: one bit per 1,024 vertex ids (groups holding corridor bits)
+    unsigned int *sdbits;        // queue sweep: one bit per vertex, set for corridor vertices of side b
     // queue sweep: the boundary candidates bucketed by block.  Block x's candidates are
     // qb_sorted[qb_start[x] .. qb_start[x + 1]) (the sweep's start) and the first
     // qb_app[x] entries of its region qb_pool[x * qb_cap ..) (appended by commits);

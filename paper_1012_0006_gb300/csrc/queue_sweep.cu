@@ -50,6 +50,8 @@ __device__ void reset_step(Ctl *c) {
     c->fallback = 0;
     c->cl_next[0] = c->cl_next[1] = 0;
     c->cl_left = 0;
+    c->vmin = INT_MAX;
+    c->vmax = -1;
 }
 
 }  // namespace
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(TPB, 1) queue_kernel(QueueArgs q, size_t smem_
             w.ctl = S.ctl;
             w.prev_err = nullptr;
             w.ngraphs = 1; w.npairs = 1; w.nsides = 2;
-            w.vq_v = S.vq_v; w.vq_s = S.vq_s; w.cbits = nullptr;   // (ids in visit-list order: no bitmap)
+            w.vq_v = S.vq_v; w.vq_s = S.vq_s; w.cbits = S.cbits; w.sbits = S.sbits; w.sdbits = S.sdbits;
             w.gid = S.gid; w.sid = S.sid; w.off = S.off; w.head = S.head; w.rev = S.rev; w.res = S.res;
             w.cap = S.cap; w.infc = S.infc; w.fx = S.fx; w.lab = S.lab; w.rflag = S.rflag; w.color = S.color;
             w.scc = S.scc; w.vc = S.vc; w.ex = S.ex; w.border = S.border; w.side_out = S.side_out;

@@ -18,6 +18,9 @@ struct QSlot {
     Ctl *ctl;
     long long *hist;      // [3 * 2 * kHistBins]
     int *cta_cnt;         // [cluster size + 1]
+    unsigned int *cbits;  // corridor bitmap over the graph's vertices (zero between pairs)
+    unsigned int *sbits;  // one bit per 1,024 vertices: groups with corridor bits (zero between pairs)
+    unsigned int *sdbits; // corridor vertices of side b, one bit per vertex (zero between pairs)
     int *vq_v, *vq_s;
     int *gid, *sid, *off, *infc, *fx, *lab, *rflag, *color, *scc, *vc, *fq0, *fq1;
     int *cid, *cpair, *cmin, *indeg, *outoff, *ocur, *plist, *sinkc, *pcur;

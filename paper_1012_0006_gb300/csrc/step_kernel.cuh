@@ -227,6 +227,16 @@ struct StepKernel {
         }
     }
 
+    // the id range of the visit list (queue sweep; the whole warp calls it)
+    __device__ __forceinline__ void track_ids(bool got, int v) {
+        const int mn = __reduce_min_sync(FULL, got ? v : INT_MAX);
+        const int mx = __reduce_max_sync(FULL, got ? v : -1);
+        if ((threadIdx.x & 31) == 0 && mx >= 0) {
+            atomicMin(&w.ctl->vmin, mn);
+            atomicMax(&w.ctl->vmax, mx);
+        }
+    }
+
     // ------------------------------------------- boundary of a single pair --
     // S1 for the one pair of this step (a queue sweep runs each pair on its own, as
     // soon as the pairs before it that share a block have committed): the candidates
@@ -336,6 +346,7 @@ struct StepKernel {
             __syncwarp();
             const bool seed = sd >= 0 && s_seed[threadIdx.x] != 0 && atomicCAS(Gr.dist + v, -1, 0) == -1;
             if (seed) cut += s_rcut[threadIdx.x];
+            if (w.list_ids) track_ids(seed, v);
             const int pos = warp_agg_inc(&w.ctl->qcnt[0], seed);
             if (seed) {
                 if (pos < w.vq_cap) {
@@ -445,6 +456,7 @@ struct StepKernel {
                         ++arcs;
                     }
                     const int slot = warp_append(qc, got);
+                    if (w.list_ids) track_ids(got, u);
                     if (got) {
                         const long long idx = next_base + slot;
                         if (idx < w.vq_cap) {
@@ -633,12 +645,97 @@ struct StepKernel {
         return true;
     }
 
+    // Local ids in id order for one pair (queue sweep) from a two-level bitmap: a
+    // corridor vertex sets its bit in cbits (and in sdbits if it is on side b) and its
+    // group's bit (1,024 ids) in sbits; the scan then reads only the words of marked
+    // groups in the window [g0, g1).
+    __device__ bool lids_window(long long g0, long long g1) {
+        unsigned long long t0 = globaltimer();
+        const GraphDev &Gr = w.graphs[0];
+        for (long long e = G.tid; e < vtotal; e += G.size) {
+            const int v = w.vq_v[e];
+            if (in_corridor(Gr, v)) {
+                atomicOr(&w.cbits[v >> 5], 1u << (v & 31));
+                if (w.vq_s[e]) atomicOr(&w.sdbits[v >> 5], 1u << (v & 31));   // side b
+                const unsigned gb = 1u << ((v >> 10) & 31);   // (most groups are marked already:
+                if (!(__ldcg(&w.sbits[v >> 15]) & gb)) atomicOr(&w.sbits[v >> 15], gb);   // no atomic)
+            }
+        }
+        if (!Grp::sync(w)) return false;
+        // a warp per group: lane z reads word z (coalesced); the group's count goes to
+        // gcnt, a scan over the groups gives their offsets, and the warp numbers the
+        // group's vertices in id order
+        auto marked = [&](long long g) { return (__ldcg(&w.sbits[g >> 5]) >> (g & 31)) & 1u; };
+        const int lane = threadIdx.x & 31;
+        int *gcnt = w.fq0;   // (free until the network exists; the caller checks the size)
+        for (long long g = g0 + G.warp; g < g1; g += G.nwarps) {
+            int c = 0;
+            if (marked(g)) c = __popc(__ldcg(&w.cbits[g * 32 + lane]));
+            c = __reduce_add_sync(FULL, c);
+            if (lane == 0) gcnt[g - g0] = c;
+        }
+        if (!Grp::sync(w)) return false;
+        long long nu = 0;
+        bool ok = grid_scan<TPB, Grp>(
+            w, g1 - g0, [&](long long gr) -> int { return __ldcg(&gcnt[gr]); },
+            [&](long long gr, long long off) { w.fq1[gr] = (int)off; }, &nu);
+        if (!ok) return false;
+        if (nu > w.nu_cap && G.tid == 0) fail(w.ctl, E_MISFIT, 32);
+        if (!Grp::sync(w)) return false;
+        if (nu <= w.nu_cap) {
+            for (long long g = g0 + G.warp; g < g1; g += G.nwarps) {
+                if (!__ldcg(&gcnt[g - g0])) continue;   // (the same in every lane)
+                const long long x = g * 32 + lane;
+                unsigned m = __ldcg(&w.cbits[x]);
+                const unsigned sd = __ldcg(&w.sdbits[x]);
+                int incl = __popc(m);
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(FULL, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                int off = __ldcg(&w.fq1[g - g0]) + incl - __popc(m);
+                if (m) {
+                    w.cbits[x] = 0;
+                    w.sdbits[x] = 0;
+                }
+                for (; m; m &= m - 1) {
+                    const int bit = __ffs(m) - 1;
+                    const int v = (int)((x << 5) + bit);
+                    Gr.lid[v] = off;
+                    w.gid[off] = v;
+                    w.sid[off] = (sd >> bit) & 1;
+                    ++off;
+                }
+            }
+        }
+        if (Grp::rank() == 0 && threadIdx.x == 0) {
+            w.ctl->nu = (int)nu;
+            w.ctl->hmax = (int)nu + 2;
+        }
+        if (!Grp::sync(w)) return false;
+        // the group marks of the window, cleared for the next pair (nothing reads them now)
+        for (long long s = (g0 >> 5) + G.tid; s <= ((g1 - 1) >> 5); s += G.size) w.sbits[s] = 0;
+        timer_mark<Grp>(w, t0, T_LID);
+        return true;
+    }
+
     // Union ids in increasing (base + v) order: the corridor vertices, found on the
     // visit list, set their bit in cbits; a scan over the words (popcounts, then
     // the set bits of each word in order) numbers them and clears the words again.
     // The corridor export relies on this order (local ids ascending with global ids).
     __device__ bool lids() {
-        if (w.list_ids) return lids_list();
+        // the queue sweep numbers by id when the visit list's id range is narrow (the
+        // ids of spatially ordered meshes: neighbours get nearby local ids and mostly
+        // the same CTA of the cluster), by visit order otherwise
+        if (w.list_ids) {
+            const int vmin = __ldcg(&w.ctl->vmin), vmax = __ldcg(&w.ctl->vmax);
+            if (vmax < 0 || !w.sbits) return lids_list();
+            const long long g0 = vmin >> 10, g1 = (vmax >> 10) + 1;
+            if (g1 - g0 > max(4096LL, vtotal) || g1 - g0 > (long long)w.nu_cap) return lids_list();
+            return lids_window(g0, g1);
+        }
+        const long long w0 = 0, w1 = (w.total_n + 31) >> 5;
         unsigned long long t0 = globaltimer();
         for (long long e = G.tid; e < vtotal; e += G.size) {
             const int v = w.vq_v[e], s = w.vq_s[e];
@@ -650,10 +747,10 @@ struct StepKernel {
         }
         if (!Grp::sync(w)) return false;
         long long nu = 0;
-        const long long nwords = (w.total_n + 31) >> 5;
         bool ok = grid_scan<TPB, Grp>(
-            w, nwords, [&](long long x) -> int { return __popc(__ldcg(&w.cbits[x])); },
-            [&](long long x, long long off) {
+            w, w1 - w0, [&](long long x) -> int { return __popc(__ldcg(&w.cbits[w0 + x])); },
+            [&](long long xr, long long off) {
+                const long long x = w0 + xr;
                 unsigned m = __ldcg(&w.cbits[x]);
                 if (!m) return;
                 w.cbits[x] = 0;

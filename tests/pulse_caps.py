@@ -9,13 +9,15 @@ fault is involved: the kernels stop at the cap and report it.
 import numpy as np
 
 
-def later_iteration_cap(run, w, kw, runs=3):
+def later_iteration_cap(run, w, kw, runs=3, exact=False):
     """run(part_tensor, alpha, opts_kw) -> fr_pair_result of one non-adaptive call on
     pair (0, 1).  Returns a cap at least a quarter above the first iteration's pulses
     and an eighth below the second's (lock-free pulse counts vary a little between
     runs), or None if the counts do not separate that far or the first iteration would
     not continue the loop.  On the 2D rgg workloads of 16,384 and 32,768 vertices the
-    two take 17 and 33 pulses."""
+    two take 17 and 33 pulses.  exact=True (the level-ordered waves of flow_sched = 1,
+    whose counts do not vary): the first iteration's count itself, if the second's is
+    larger in every run."""
     import torch
     p0 = torch.as_tensor(np.array(w["part"], np.int32)).cuda()
     first, p1 = [], None
@@ -33,5 +35,7 @@ def later_iteration_cap(run, w, kw, runs=3):
         if r.status != 0:
             return None
         second.append(r.pulses)
+    if exact:
+        return max(first) if min(second) > max(first) else None
     lo, hi = max(first) * 5 // 4 + 1, min(second) * 7 // 8
     return (lo + hi) // 2 if lo <= hi else None

@@ -506,16 +506,17 @@ def test_error_in_a_later_adaptive_iteration_leaves_part_unchanged(F, ctx, mb):
         if tried:
             break
         g = F.DeviceGraph.from_workload(w)
-        kw = dict(mb=mb)
+        kw = dict(mb=mb, flow_sched=1)   # level-ordered waves: counts that do not vary between runs
         cap = later_iteration_cap(
-            lambda p, al, k_: ctx.refine_pair(g, p, w["k"], 0, 1, w["eps"], al, F.default_options(**k_))[1], w, kw)
+            lambda p, al, k_: ctx.refine_pair(g, p, w["k"], 0, 1, w["eps"], al, F.default_options(**k_))[1], w, kw,
+            exact=True)
         if cap is None:
             continue
         tried += 1
         part = torch.as_tensor(np.array(w["part"], np.int32)).cuda()
         before = part.clone()
         st, res = ctx.refine_pair(g, part, w["k"], 0, 1, w["eps"], 1.0,
-                                  F.default_options(mb=mb, adaptive=1, max_iters=10, alpha_max=16.0,
+                                  F.default_options(mb=mb, flow_sched=1, adaptive=1, max_iters=10, alpha_max=16.0,
                                                     pulse_cap=cap), check=False)
         assert st == F.FR_ERR_ITER_LIMIT and res.status == F.FR_ERR_ITER_LIMIT
         assert res.iters >= 2
