@@ -203,11 +203,12 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-# Device code of the flow sweep: the cluster max-flow kernel and the kernels that write
-# the networks it reads.  A recorded DRAM traffic of the sweep's dominant kernel holds only
-# while these are unchanged.
-SWEEP_KERNEL_SOURCES = ("cluster_flow.cu", "fr_internal.cuh", "prep_kernel.cu", "round_kernel.cu",
-                        "round_kernel.cuh")
+# Device code of the flow sweep: the queue kernel (every phase of every pair), the
+# round-by-round step and cluster kernels, and the kernels that write what they read.  A
+# recorded DRAM traffic of the sweep's dominant kernel holds only while these are unchanged.
+SWEEP_KERNEL_SOURCES = ("cluster_flow.cu", "cluster_flow.cuh", "fr_internal.cuh", "prep_kernel.cu",
+                        "round_kernel.cu", "round_kernel.cuh", "step_kernel.cuh", "queue_sweep.cu",
+                        "queue_sweep.cuh")
 
 
 def kernel_source_hash():
@@ -277,7 +278,7 @@ def run_ours(args, world, rank, local, pg):
     part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
     part = part0.clone()
     ctx = F.Context(local)
-    opts = F.default_options(mb=int(w["mb"]))
+    opts = F.default_options(mb=int(w["mb"]), sweep_sched=args.sweep_sched)
     k, eps, alpha = w["k"], w["eps"], w["alpha"]
     tuned = None
     if not args.no_autotune:
@@ -809,6 +810,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--sweep-sched", type=int, default=0, choices=[0, 1],
+                    help="0: queue sweep (every pair in one launch of clusters), 1: round by round")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-pairs", type=int, default=6, help="reference arm, single thread: pairs per step")
     ap.add_argument("--ref-threads", type=int, default=0, help="reference arm: host threads (0: all cores)")

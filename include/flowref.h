@@ -104,6 +104,10 @@ typedef struct fr_options {
                               (the same results as round by round; not with the FM step, and a
                               sweep whose corridor outgrows a cluster runs round by round);
                               1 = round by round (one launch sequence per matching) */
+    int32_t gap_interval;  /* push-relabel: every gap_interval pulses between exact relabels, the gap
+                              heuristic (a label no vertex holds cuts every vertex above it off the
+                              target: they go to the top label at once); 0 = every 8 pulses,
+                              -1 = off.  Results do not depend on it */
 } fr_options;
 
 /* Outcome of one pair refinement.  cut_* are omega(E_ab); wA/wB are c(V_a), c(V_b);
@@ -417,6 +421,8 @@ typedef struct fr_profile_info {
     int32_t queue_clusters;   /* clusters it launched */
     int32_t queue_fallbacks;  /* queue sweeps of this context that a pair outgrew (run round by round) */
     double queue_scan_ms;     /* queue sweep: the pairs' boundary scans, summed over pairs (in-kernel timers) */
+    int64_t gaps;             /* gap checks of push-relabel that found a gap */
+    int64_t gap_lifted;       /* vertices they lifted to the top label */
 } fr_profile_info;
 
 /* on = 1: fr_refine_batch launches its kernels directly (no graph replay) with

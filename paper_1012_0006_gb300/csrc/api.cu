@@ -382,7 +382,13 @@ Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt) 
     w.pulse_cap = opt && opt->pulse_cap > 0 ? opt->pulse_cap : (1LL << 20);
     w.narrow = ctx->narrow_ok;
     w.pre_waves = opt && opt->pre_waves ? (opt->pre_waves < 0 ? 0 : opt->pre_waves) : ctx->tune_prewaves;
+    w.gap_interval = gap_interval_of(opt);
     return w;
+}
+
+int gap_interval_of(const fr_options *opt) {
+    if (!opt || opt->gap_interval == 0) return 8;
+    return opt->gap_interval < 0 ? 0 : opt->gap_interval;
 }
 
 int choose_tpb(fr_ctx *ctx, const fr_options *opt) {
@@ -553,6 +559,7 @@ fr_status validate_params(double eps, double alpha, const fr_options *opt, const
         else if (opt->fm_permille < 0 || opt->fm_permille > 1000) *why = "fm_permille must be in [0, 1000]";
         else if (opt->mt_alpha < 0) *why = "mt_alpha must be >= 0";
         else if (opt->sweep_sched < 0 || opt->sweep_sched > 1) *why = "sweep_sched must be 0 or 1";
+        else if (opt->gap_interval < -1) *why = "gap_interval must be >= -1";
         else if (opt->cluster_ctas != 0) {
             bool known = false;
             for (int t = 0; t < fr_ctx::kNumClusterSizes; ++t) known |= opt->cluster_ctas == fr_ctx::kClusterSizes[t];

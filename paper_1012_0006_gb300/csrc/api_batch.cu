@@ -406,6 +406,7 @@ static fr_status run_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const 
                                   opt->pulse_passes, ctx->tune_passes, (long long)(uintptr_t)ctx->reps_mem,
                                   opt->flow_sched, opt->cluster_ctas, ctx->tune_ctas, ctx->tune_sched,
                                   ctx->narrow_ok, opt->pre_waves, ctx->tune_prewaves, opt->fm_permille,
+                                  opt->gap_interval,
                                   (long long)(uintptr_t)ctx->fm_mem};
     for (int r = 0; r <= pl.nr; ++r) key.push_back(pl.off[r]);
     for (int r = 0; r < pl.nr; ++r) key.push_back(pl.grid[r]);
@@ -648,6 +649,8 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
             P.fallback_pairs += C[r].fallback;
             for (int t = 0; t < 3; ++t) P.fm_ms[t] += C[r].timers[T_FM_SORT + t] * 1e-6;
             P.queue_scan_ms += C[r].timers[T_QSCAN] * 1e-6;
+            P.gaps += C[r].gaps;
+            P.gap_lifted += C[r].gap_lifted;
         }
         for (size_t i = 0; i + 3 < qst.size(); i += 4) {
             P.bfs_visited += qst[i];

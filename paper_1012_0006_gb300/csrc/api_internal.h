@@ -162,6 +162,8 @@ fr_status ensure_pairs(fr_ctx *ctx, int P, int R, int reps);
 fr_status ensure_reps(fr_ctx *ctx, int reps);
 fr::Work make_work(fr_ctx *ctx, int r, int p0, int P, int n, const fr_options *opt);
 int choose_tpb(fr_ctx *ctx, const fr_options *opt);
+// Pulses between gap checks of push-relabel (fr_options.gap_interval: 0 -> 8, -1 -> none).
+int gap_interval_of(const fr_options *opt);
 int choose_grid(fr_ctx *ctx, const fr_options *opt, int tpb, int nsides, long long est_vertices);
 fr_status check_graph(fr_ctx *ctx, const fr_graph *g, const int32_t *part, int32_t k);
 // Checks of eps, alpha and the options that need no context; *why names the first failure.

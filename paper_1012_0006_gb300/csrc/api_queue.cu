@@ -302,7 +302,7 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
                                   (long long)(uintptr_t)ctx->pair_mem, (long long)(uintptr_t)ctx->q_mem,
                                   ctx->tune_gr, ctx->tune_inner, opt->pulse_passes, ctx->tune_passes,
                                   opt->flow_sched, ctx->tune_sched, ctx->narrow_ok, opt->pre_waves,
-                                  ctx->tune_prewaves, ctas, clusters, pl.Lmax};
+                                  ctx->tune_prewaves, ctas, clusters, pl.Lmax, opt->gap_interval};
     ctx->prof.scan_ms = ctx->prof.step_ms = ctx->prof.cluster_ms = 0;
     ctx->round_ms.clear();
     ctx->pair_ms.clear();

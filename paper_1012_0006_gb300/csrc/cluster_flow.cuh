@@ -886,6 +886,8 @@ struct ClusterFlow {
                 relabel(ph, nv, hmax);
                 since = 0;
                 ++relabels;
+            } else if (w.gap_interval > 0 && since % w.gap_interval == 0) {
+                gap(nv, hmax);
             }
         }
         if (rank == 0 && threadIdx.x == 0) {
@@ -893,6 +895,59 @@ struct ClusterFlow {
             atomicAddLL(&w.ctl->relabels, relabels);
         }
         return true;
+    }
+
+    // Gap heuristic (the paper's max-flow solver, HIPR, uses it): between barriers no
+    // label moves, and a valid labelling never lets a residual arc drop more than one
+    // label, so if no vertex holds some label h below the largest label held (below
+    // hmax), no vertex above h can reach the target: all of them go to hmax at once
+    // instead of climbing one push at a time until the next exact relabel.  The held
+    // labels are marked in a bitmap in CTA 0's claim array (free during the flow).
+    // Returns the vertices lifted (cluster-wide).
+    __device__ int gap(int nv, int hmax) {
+        const int nwords = (hmax + 31) >> 5;
+        if (nwords > hdr->nvcap) return 0;   // (tiny ranges: the bitmap does not fit; the same in every CTA)
+        unsigned *bm = reinterpret_cast<unsigned *>(cla);
+        if (rank == 0)
+            for (int i = threadIdx.x; i < nwords; i += TPB) bm[i] = 0u;
+        sync();
+        const unsigned bm0 = map_rank(cta_addr(bm), 0);
+        int top = 0;
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+            const int h = lab[lv];
+            if (h >= 1 && h < hmax) {
+                dsm_or(bm0 + 4u * (unsigned)(h >> 5), (int)(1u << (h & 31)));
+                top = max(top, h);
+            }
+        }
+        top = cluster_max(top);   // (its barrier also completes the marks)
+        // the smallest label in [1, top) that no vertex holds (CTA 0 reads its bitmap)
+        int pos = INT_MAX;
+        if (rank == 0)
+            for (int i = threadIdx.x; i <= (top >> 5); i += TPB) {
+                unsigned empty = ~bm[i];
+                if (i == 0) empty &= ~1u;                                     // label 0: the target
+                if (i == (top >> 5)) empty &= (top & 31) ? ((1u << (top & 31)) - 1u) : 0u;   // below top
+                if (empty) pos = min(pos, (i << 5) + __ffs(empty) - 1);
+            }
+        pos = __reduce_min_sync(FULL, pos);
+        const int found = cluster_max(pos == INT_MAX ? 0 : (1 << 30) - pos);
+        if (found == 0) return 0;
+        const int h0 = (1 << 30) - found;
+        int lifted = 0;
+        for (int lv = threadIdx.x; lv < nv; lv += TPB) {
+            const int h = lab[lv];
+            if (h > h0 && h < hmax) {
+                set_label(lv, hmax);
+                ++lifted;
+            }
+        }
+        lifted = cluster_sum(lifted);
+        if (rank == 0 && threadIdx.x == 0) {
+            atomicAddLL(&w.ctl->gaps, 1);
+            atomicAddLL(&w.ctl->gap_lifted, lifted);
+        }
+        return lifted;
     }
 
     // bit 1: reachable from s, seeded with the s-border and with every vertex

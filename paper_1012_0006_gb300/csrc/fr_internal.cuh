@@ -142,6 +142,9 @@ struct Ctl {
     int cl_next[2];           // next slot of the size order each cluster launch takes
     int cl_left;              // pairs the first cluster launch left (written by it only)
     int vmin, vmax;           // queue sweep: smallest and largest vertex id on the pair's visit list
+    long long gaps;           // gap checks that found a gap (push-relabel), summed
+    long long gap_lifted;     // vertices they lifted to hmax
+    int gap_top, gap_pos;     // grid-wide gap check: largest label below hmax, smallest empty label
 };
 
 // Everything a kernel needs, passed by value.
@@ -183,7 +186,7 @@ struct Work {
     int full_flow;               // 1: return every excess to s (a flow); 0: a maximum preflow
     int narrow;                  // 1: every arc capacity < 2^15 (cluster kernel packs residual and capacity sum)
     int pre_waves;               // cluster pulses: waves by levels before the first pulse
-    int pad_w2;
+    int gap_interval;            // pulses between gap checks of push-relabel (0: none)
     unsigned long long seed;
     long long pulse_cap;
     int *crank;                  // per graph arc: rank among its row's corridor arcs (NULL: outs holds it)

@@ -169,6 +169,7 @@ static fr_status na_iteration(const Scratch &S, const fr_graph *g, int32_t *part
     w.any_mb = opt.mb ? 1 : 0;
     w.seed = opt.seed;
     w.pulse_cap = opt.pulse_cap > 0 ? opt.pulse_cap : (1LL << 20);
+    w.gap_interval = gap_interval_of(&opt);
     const int tpb = opt.block_threads == 256 ? 256 : 512;
     int maxb = 1, sms = 1;
     if (step_max_grid(tpb, 2, &maxb, &sms) != cudaSuccess) return FR_ERR_CUDA;

@@ -1133,10 +1133,68 @@ struct StepKernel {
                 if (!global_relabel(phase2, hmax, nu)) return false;
                 since_gr = 0;
                 timer_mark<Grp>(w, t0, T_GR);
+            } else if (w.gap_interval > 0 && since_gr % w.gap_interval == 0) {
+                if (!gap_check(hmax, nu)) return false;
             }
         }
         if (G.tid == 0) ctl->pulses += pulses;
         return true;
+    }
+
+    // Gap heuristic over the union network (the paper's max-flow solver, HIPR, uses it):
+    // with no push in flight, a label h below the largest held label (below hmax) that
+    // no vertex holds is held by no vertex of any pair, so no vertex above h reaches its
+    // pair's target (a valid labelling never lets a residual arc drop more than one
+    // label): they all go to hmax.  The held labels are marked in a bitmap in vc (free
+    // during the flow).
+    __device__ bool gap_check(int hmax, int nu) {
+        Ctl *ctl = w.ctl;
+        unsigned *bm = reinterpret_cast<unsigned *>(w.vc);
+        const int nwords = (hmax + 31) >> 5;
+        if (nwords > w.nu_cap) return true;
+        for (long long i = G.tid; i < nwords; i += G.size) bm[i] = 0u;
+        if (G.tid == 0) {
+            ctl->gap_top = 0;
+            ctl->gap_pos = INT_MAX;
+        }
+        if (!Grp::sync(w)) return false;
+        int top = 0;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int h = __ldcg(&w.lab[i]);
+            if (h >= 1 && h < hmax) {
+                const unsigned b = 1u << (h & 31);
+                if (!(__ldcg(&bm[h >> 5]) & b)) atomicOr(&bm[h >> 5], b);
+                top = max(top, h);
+            }
+        }
+        top = __reduce_max_sync(FULL, top);
+        if ((threadIdx.x & 31) == 0 && top) atomicMax(&ctl->gap_top, top);
+        if (!Grp::sync(w)) return false;
+        top = __ldcg(&ctl->gap_top);
+        int pos = INT_MAX;
+        for (long long i = G.tid; i <= (top >> 5); i += G.size) {
+            unsigned empty = ~__ldcg(&bm[i]);
+            if (i == 0) empty &= ~1u;                                                     // label 0: the target
+            if (i == (top >> 5)) empty &= (top & 31) ? ((1u << (top & 31)) - 1u) : 0u;   // below top
+            if (empty) pos = min(pos, (int)(i << 5) + __ffs(empty) - 1);
+        }
+        pos = __reduce_min_sync(FULL, pos);
+        if ((threadIdx.x & 31) == 0 && pos != INT_MAX) atomicMin(&ctl->gap_pos, pos);
+        if (!Grp::sync(w)) return false;
+        const int h0 = __ldcg(&ctl->gap_pos);
+        if (h0 == INT_MAX) return true;
+        long long lifted = 0;
+        for (long long i = G.tid; i < nu; i += G.size) {
+            const int h = __ldcg(&w.lab[i]);
+            if (h > h0 && h < hmax) {
+                w.lab[i] = hmax;
+                ++lifted;
+            }
+        }
+        lifted = block_sum_ll<TPB>(lifted);
+        if (threadIdx.x == 0 && lifted) atomicAddLL(&ctl->gap_lifted, lifted);
+        if (G.tid == 0) atomicAddLL(&ctl->gaps, 1);
+        return Grp::sync(w);
     }
 
     // Maximum preflow (phase 0).  The cut needs no more: with an arc v -> s of

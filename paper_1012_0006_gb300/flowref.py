@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("gr_interval", ctypes.c_int32), ("inner_ops", ctypes.c_int32),
                 ("pulse_passes", ctypes.c_int32), ("flow_sched", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
                 ("pre_waves", ctypes.c_int32), ("fm_permille", ctypes.c_int32), ("mt_alpha", ctypes.c_int32),
-                ("sweep_sched", ctypes.c_int32)]
+                ("sweep_sched", ctypes.c_int32), ("gap_interval", ctypes.c_int32)]
 
 
 class PairResult(ctypes.Structure):
@@ -111,7 +111,8 @@ class ProfileInfo(ctypes.Structure):
                 ("scan_listed", ctypes.c_int64), ("scan_rows", ctypes.c_int64), ("scan_arcs", ctypes.c_int64),
                 ("fm_ms", ctypes.c_double * 3), ("cluster_sizes", ctypes.c_int32 * 5), ("cluster_max_active", ctypes.c_int32 * 5),
                 ("queue", ctypes.c_int32), ("queue_ctas", ctypes.c_int32), ("queue_clusters", ctypes.c_int32),
-                ("queue_fallbacks", ctypes.c_int32), ("queue_scan_ms", ctypes.c_double)]
+                ("queue_fallbacks", ctypes.c_int32), ("queue_scan_ms", ctypes.c_double),
+                ("gaps", ctypes.c_int64), ("gap_lifted", ctypes.c_int64)]
 
     PHASES = ("bfs", "select", "lid", "build", "flow", "relabel", "return", "reach", "scc", "sweep", "eval",
               "commit")
