@@ -174,7 +174,8 @@ typedef struct fr_cycle_result {
     double ms;                                  /* host clock around the call (synchronised) */
 } fr_cycle_result;
 
-/* Totals of one multi-try FM pass (fr_multitry). */
+/* Totals of one multi-try FM pass (fr_multitry) or of global k-way rounds
+ * (fr_kway_global, where searches counts the rounds). */
 typedef struct fr_mt_result {
     int64_t gain;           /* cut decrease kept */
     int32_t searches;       /* k-way searches started */
@@ -312,6 +313,20 @@ fr_status fr_refine_active(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_
 fr_status fr_multitry(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, int32_t np,
                       const int32_t *pa, const int32_t *pb, int32_t alpha, uint64_t seed, fr_mt_result *out,
                       int8_t *changed);
+
+/* Global k-way refinement (Section 2.2, configured as Section 6 describes): rounds of
+ * one k-way local search each (the search of fr_multitry without its touched rule),
+ * started from every vertex with a neighbour in another block (init_mode 0) or only
+ * from the corner vertices, whose neighbours lie in at least two blocks other than
+ * their own (init_mode 1), queued in ascending splitmix64(splitmix64(seed ^ r) ^ v)
+ * order in round r = 0, 1, ...; target ties go to the smaller
+ * splitmix64(splitmix64(~seed) ^ v << 32 ^ P), then the smaller P.  The rounds end
+ * after the first one that gains nothing or after max_rounds (>= 1).  part: DEVICE,
+ * updated in place (unchanged on error).  out (HOST, optional): gain, tried and kept
+ * summed over the rounds; searches = rounds run.  Needs eps > 0, alpha >= 0,
+ * k <= 1024 and every gain within +-1023 (FR_ERR_TOO_LARGE). */
+fr_status fr_kway_global(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps, int32_t init_mode,
+                         int32_t alpha, int32_t max_rounds, uint64_t seed, fr_mt_result *out);
 
 /* ---- multilevel V-cycle with a given partition (Sections 2.1, 2.2, 5) ---- */
 /* These calls allocate their scratch and the coarse graphs with cudaMalloc for the length

@@ -1,7 +1,7 @@
 // C ABI, part 4: multi-try FM passes (Sanders & Schulz, Section 4.2; k-way local
 // search with the KaSPar stopping rule of Section 2.2): the workspace, one pass over
-// the pairs of a matching (used by fr_refine_active after each matching), and the
-// stand-alone entry point fr_multitry.
+// the pairs of a matching (used by fr_refine_active after each matching), the
+// stand-alone entry point fr_multitry, and the global k-way rounds (fr_kway_global).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -195,6 +195,82 @@ extern "C" fr_status fr_multitry(fr_ctx *ctx, const fr_graph *g, int32_t *part, 
         out->searches = r.searches;
         out->tried = r.tried;
         out->kept = r.kept;
+        out->status = FR_OK;
+    }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_kway_global(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k, double eps,
+                                    int32_t init_mode, int32_t alpha, int32_t max_rounds, uint64_t seed,
+                                    fr_mt_result *out) {
+    if (!ctx) return FR_ERR_INVALID_ARG;
+    if (out) memset(out, 0, sizeof(*out));
+    fr_status st = check_graph(ctx, g, part, k);
+    if (st == FR_OK && (!(eps > 0.0) || !std::isfinite(eps) || alpha < 0 || max_rounds < 1 ||
+                        (init_mode != 0 && init_mode != 1))) {
+        ctx_error(ctx, "fr_kway_global: eps > 0, alpha >= 0, max_rounds >= 1 and init_mode 0 or 1 needed");
+        st = FR_ERR_INVALID_ARG;
+    }
+    if (st == FR_OK && k > kMtMaxK) {
+        ctx_error(ctx, "k-way rounds: k = %d exceeds %d", k, kMtMaxK);
+        st = FR_ERR_TOO_LARGE;
+    }
+    if (st != FR_OK) { if (out) out->status = st; return st; }
+    CK(cudaSetDevice(ctx->device));
+    release_corridor(ctx);
+    ctx->last_launches = 0;
+    st = ensure_base(ctx, g->n, g->nnz, k, 1);
+    PrepOut po;
+    if (st == FR_OK) st = run_prep(ctx, g, part, k, false, false, &po);
+    if (st == FR_OK && po.maxwdeg > kMtGmax) {
+        ctx_error(ctx, "k-way rounds: max weighted degree %d exceeds %d", po.maxwdeg, kMtGmax);
+        st = FR_ERR_TOO_LARGE;
+    }
+    if (st == FR_OK) st = ensure_mt(ctx, g->n, g->nnz, k, 1);
+    if (st == FR_OK && !ctx->ctl) st = ensure_pairs(ctx, 1, 1, 1);   // the control block lives there
+    if (st != FR_OK) { if (out) out->status = st; return st; }
+    CK(cudaMemcpyAsync(ctx->part_backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), ctx->stream));
+    MtDev md = ctx->mt;
+    md.np = 0;
+    md.alpha = alpha;
+    md.beta = std::log((double)g->n);
+    md.seed = seed;
+    GraphDev G;
+    memset(&G, 0, sizeof(G));
+    G.xadj = g->xadj; G.adjncy = g->adjncy; G.adjwgt = g->adjwgt; G.vwgt = g->vwgt;
+    G.part = part; G.blockw = ctx->blockw;
+    G.n = g->n; G.nnz = g->nnz; G.k = k; G.Lmax = host_lmax(po.W, po.maxc, k, eps);
+    char *o = ctx->h_stage + kHostStage / 2;
+    Ctl *hc = reinterpret_cast<Ctl *>(o);
+    MtRes *hr = reinterpret_cast<MtRes *>(o + 1024);
+    fr_mt_result tot;
+    memset(&tot, 0, sizeof(tot));
+    for (int r = 0; r < max_rounds; ++r) {
+        int nl = 0;
+        const unsigned long long rs = splitmix64(seed ^ (unsigned long long)(unsigned)r);
+        cudaError_t e = launch_kway_round(G, md, ctx->ctl, init_mode == 1 ? 2 : 1, rs, ctx->sms, ctx->stream, &nl);
+        ctx->last_launches += nl;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hr, md.res, sizeof(MtRes), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        st = e == cudaSuccess ? status_from_ctl(ctx, *hc, "k-way round") : cuda_fail(ctx, e, "k-way round");
+        if (st != FR_OK) {
+            reset_idle(ctx);
+            cudaMemcpyAsync(part, ctx->part_backup, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice,
+                            ctx->stream);
+            cudaStreamSynchronize(ctx->stream);
+            if (out) out->status = st;
+            return st;
+        }
+        tot.gain += hr->gain;
+        tot.tried += hr->tried;
+        tot.kept += hr->kept;
+        tot.searches = r + 1;
+        if (hr->gain <= 0) break;
+    }
+    if (out) {
+        *out = tot;
         out->status = FR_OK;
     }
     return FR_OK;

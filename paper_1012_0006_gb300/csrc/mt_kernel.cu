@@ -30,6 +30,9 @@
 // pops skip stale entries.  The block weights live in shared memory for the pass.
 // Grid-wide kernels before it count the pair boundaries and block weights, fill the
 // todo lists and sort each (one CTA per pair, bitonic by key).
+//
+// The same search, without the touched rule and started from the whole boundary (or
+// its corner vertices), makes one round of the global k-way refinement (end of file).
 #include <climits>
 
 #include "mt_kernel.cuh"
@@ -264,6 +267,165 @@ __device__ __forceinline__ void mt_push(MtShared &S, const MtDev &m, unsigned pm
     __syncwarp();
 }
 
+// One k-way search (one warp) from the entries already pushed, nxt of them: pop the
+// highest current entry, move it unless its target would exceed L_max, key its unmoved
+// neighbours again (CSR order), stop by the KaSPar rule or an empty queue.  touch: the
+// multi-try pass's rule (a vertex another search of the pass queued is neither queued nor
+// moved; what this search queues is marked with sid); false: no such rule (the global
+// k-way rounds).  Returns the best prefix (best < 0 is the largest cut decrease),
+// the moves made and kept, and whether the KaSPar rule stopped it; bad on an error.
+__device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtShared &S, Ctl *ctl, int sid,
+                                          bool touch, long long &nxt, long long Lmax, unsigned long long tseed,
+                                          int lane, bool &bad, long long &best, int &nm, int &best_len,
+                                          bool &stopped) {
+    long long delta = 0, S1 = 0, S2 = 0;
+    int pc = 0;
+    best = 0;
+    nm = 0;
+    best_len = 0;
+    stopped = false;
+    while (!bad) {
+        // pop the highest current entry
+        int x = -1, g = 0, xto = 0, xfrom = 0, xc = 0, xy0 = 0, xy1 = 0;
+        for (;;) {
+            int hb = -1;
+            for (int k2 = 1; k2 >= 0; --k2) {
+                const unsigned word = S.bits[lane * 2 + k2];
+                if (hb < 0 && word) hb = (lane * 2 + k2) * 32 + 31 - __clz(word);
+            }
+            const unsigned has = __ballot_sync(kFull, hb >= 0);
+            if (!has) break;
+            const int b = __shfl_sync(kFull, hb, 31 - __clz(has));
+            int got = -1, gto = 0, gfrom = 0, gc = 0, gy0 = 0, gy1 = 0;
+            if (lane == 0) {
+                const int e = S.top[b];
+                if (e < 0 || e >= nxt) {   // (never: a set bit has a pushed top entry)
+                    S.top[b] = -1;
+                    S.bits[b >> 5] &= ~(1u << (b & 31));
+                } else {
+                    const int xv = m.ent_v[e], below = m.ent_below[e], ev = m.ent_ver[e];
+                    // the vertex's state, loaded together with its version
+                    const int vv = m.ver[xv], tg = m.tgt[xv], pf = G.part[xv];
+                    const int cw = __ldg(G.vwgt + xv), a0 = __ldg(G.xadj + xv), a1 = __ldg(G.xadj + xv + 1);
+                    S.top[b] = below;
+                    if (below < 0) S.bits[b >> 5] &= ~(1u << (b & 31));
+                    if (ev == vv) {   // current: it leaves the queue
+                        got = xv;
+                        m.ver[xv] = vv + 1;
+                        gto = tg; gfrom = pf; gc = cw; gy0 = a0; gy1 = a1;
+                    }
+                }
+            }
+            got = __shfl_sync(kFull, got, 0);
+            __syncwarp();
+            if (got >= 0) {
+                x = got;
+                g = b - kMtGmax;
+                xto = __shfl_sync(kFull, gto, 0);
+                xfrom = __shfl_sync(kFull, gfrom, 0);
+                xc = __shfl_sync(kFull, gc, 0);
+                xy0 = __shfl_sync(kFull, gy0, 0);
+                xy1 = __shfl_sync(kFull, gy1, 0);
+                break;
+            }
+        }
+        if (x < 0) break;   // the queue is empty
+        const int to = xto;
+        const int from = xfrom;
+        const long long cx = xc;
+        if (S.bw[to] + cx > Lmax) continue;   // would overload the target: not moved
+        if (lane == 0) {
+            G.part[x] = to;
+            S.bw[from] -= cx;
+            S.bw[to] += cx;
+            m.mvd[x] = 1;
+            m.lv[nm] = x;
+            m.lfrom[nm] = from;
+        }
+        ++nm;
+        delta -= g;
+        __syncwarp();
+        // key the neighbours again, 32 at a time in CSR order
+        const int y0 = xy0, y1 = xy1;
+        for (int jb = y0; jb < y1; jb += 32) {
+            const int jj = jb + lane;
+            const int u = jj < y1 ? __ldg(G.adjncy + jj) : -1;
+            bool elig = false, push = false;
+            int gu = 0, tu = -1;
+            if (u >= 0) {
+                // u's marks, block and adjacency range, loaded together
+                const unsigned char mv = m.mvd[u];
+                const int tc = touch ? m.tch[u] : 0, pu = G.part[u];
+                const int u0 = __ldg(G.xadj + u), u1 = __ldg(G.xadj + u + 1);
+                elig = !mv && (tc == 0 || tc == sid);
+                if (elig) push = mt_gain(G, u, pu, u0, u1, tseed, gu, tu);
+            }
+            const bool range = __all_sync(kFull, !push || (gu >= -kMtGmax && gu <= kMtGmax));
+            const unsigned pm = __ballot_sync(kFull, push);
+            if (!range || nxt + __popc(pm) > m.ecap) {
+                if (lane == 0) fail(ctl, range ? E_INTERNAL : E_TOO_LARGE, 805);
+                bad = true;
+                break;
+            }
+            int nv = 0;
+            if (elig) {   // its old entry (if any) is stale from here on
+                nv = m.ver[u] + 1;
+                m.ver[u] = nv;
+            }
+            if (push) {
+                m.tgt[u] = tu;
+                if (touch) m.tch[u] = sid;
+            }
+            mt_push(S, m, pm, push, gu + kMtGmax, u, nv, nxt, lane);
+            nxt += __popc(pm);
+        }
+        if (bad) break;
+        if (delta < best) {
+            best = delta; best_len = nm; pc = 0; S1 = 0; S2 = 0;
+        } else {
+            ++pc;
+            S1 += g;
+            S2 += (long long)g * g;
+            if (kaspar_stop(pc, S1, S2, m.alpha, m.beta)) {
+                stopped = true;
+                break;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// After a search: roll back to the first lowest cut, clear the moved marks, and for the
+// kept moves mark the blocks they left and entered and list the boundary candidates
+// (the moved vertex and its neighbours outside its new block, as a flow's commit does).
+__device__ __forceinline__ void mt_finish(const GraphDev &G, const MtDev &m, MtShared &S, int nm, int best_len,
+                                          int lane) {
+    for (int i = best_len + lane; i < nm; i += 32) {
+        const int y = m.lv[i], f0 = m.lfrom[i], t = G.part[y];
+        const long long cy = __ldg(G.vwgt + y);
+        G.part[y] = f0;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[t]), (unsigned long long)(-cy));
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[f0]), (unsigned long long)cy);
+    }
+    __syncwarp();
+    for (int i = lane; i < nm; i += 32) m.mvd[m.lv[i]] = 0;
+    for (int i = lane; i < best_len; i += 32) {
+        const int y = m.lv[i], t = G.part[y];
+        m.chg[m.lfrom[i]] = 1;
+        m.chg[t] = 1;
+        if (G.bl) {
+            if (!__ldcg(G.inb + y) && atomicExch(G.inb + y, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = y;
+            const int z1 = __ldg(G.xadj + y + 1);
+            for (int q = __ldg(G.xadj + y); q < z1; ++q) {
+                const int z = __ldg(G.adjncy + q);
+                if (__ldcg(G.inb + z) || G.part[z] == t) continue;
+                if (atomicExch(G.inb + z, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = z;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // The whole pass: one warp.
 __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl *ctl) {
     __shared__ MtShared S;
@@ -345,141 +507,11 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
                 mt_push(S, m, pm, push, g + kMtGmax, u, nv, nxt, lane);
                 nxt += __popc(pm);
             }
-            long long delta = 0, best = 0, S1 = 0, S2 = 0;
-            int nm = 0, best_len = 0, pc = 0;
-            while (!bad) {
-                // pop the highest current entry
-                int x = -1, g = 0, xto = 0, xfrom = 0, xc = 0, xy0 = 0, xy1 = 0;
-                for (;;) {
-                    int hb = -1;
-                    for (int k2 = 1; k2 >= 0; --k2) {
-                        const unsigned word = S.bits[lane * 2 + k2];
-                        if (hb < 0 && word) hb = (lane * 2 + k2) * 32 + 31 - __clz(word);
-                    }
-                    const unsigned has = __ballot_sync(kFull, hb >= 0);
-                    if (!has) break;
-                    const int b = __shfl_sync(kFull, hb, 31 - __clz(has));
-                    int got = -1, gto = 0, gfrom = 0, gc = 0, gy0 = 0, gy1 = 0;
-                    if (lane == 0) {
-                        const int e = S.top[b];
-                        if (e < 0 || e >= nxt) {   // (never: a set bit has a pushed top entry)
-                            S.top[b] = -1;
-                            S.bits[b >> 5] &= ~(1u << (b & 31));
-                        } else {
-                            const int xv = m.ent_v[e], below = m.ent_below[e], ev = m.ent_ver[e];
-                            // the vertex's state, loaded together with its version
-                            const int vv = m.ver[xv], tg = m.tgt[xv], pf = G.part[xv];
-                            const int cw = __ldg(G.vwgt + xv), a0 = __ldg(G.xadj + xv), a1 = __ldg(G.xadj + xv + 1);
-                            S.top[b] = below;
-                            if (below < 0) S.bits[b >> 5] &= ~(1u << (b & 31));
-                            if (ev == vv) {   // current: it leaves the queue
-                                got = xv;
-                                m.ver[xv] = vv + 1;
-                                gto = tg; gfrom = pf; gc = cw; gy0 = a0; gy1 = a1;
-                            }
-                        }
-                    }
-                    got = __shfl_sync(kFull, got, 0);
-                    __syncwarp();
-                    if (got >= 0) {
-                        x = got;
-                        g = b - kMtGmax;
-                        xto = __shfl_sync(kFull, gto, 0);
-                        xfrom = __shfl_sync(kFull, gfrom, 0);
-                        xc = __shfl_sync(kFull, gc, 0);
-                        xy0 = __shfl_sync(kFull, gy0, 0);
-                        xy1 = __shfl_sync(kFull, gy1, 0);
-                        break;
-                    }
-                }
-                if (x < 0) break;   // the queue is empty
-                const int to = xto;
-                const int from = xfrom;
-                const long long cx = xc;
-                if (S.bw[to] + cx > Lmax) continue;   // would overload the target: not moved
-                if (lane == 0) {
-                    G.part[x] = to;
-                    S.bw[from] -= cx;
-                    S.bw[to] += cx;
-                    m.mvd[x] = 1;
-                    m.lv[nm] = x;
-                    m.lfrom[nm] = from;
-                }
-                ++nm;
-                delta -= g;
-                __syncwarp();
-                // key the neighbours again, 32 at a time in CSR order
-                const int y0 = xy0, y1 = xy1;
-                for (int jb = y0; jb < y1; jb += 32) {
-                    const int jj = jb + lane;
-                    const int u = jj < y1 ? __ldg(G.adjncy + jj) : -1;
-                    bool elig = false, push = false;
-                    int gu = 0, tu = -1;
-                    if (u >= 0) {
-                        // u's marks, block and adjacency range, loaded together
-                        const unsigned char mv = m.mvd[u];
-                        const int tc = m.tch[u], pu = G.part[u];
-                        const int u0 = __ldg(G.xadj + u), u1 = __ldg(G.xadj + u + 1);
-                        elig = !mv && (tc == 0 || tc == sid);
-                        if (elig) push = mt_gain(G, u, pu, u0, u1, tseed, gu, tu);
-                    }
-                    const bool range = __all_sync(kFull, !push || (gu >= -kMtGmax && gu <= kMtGmax));
-                    const unsigned pm = __ballot_sync(kFull, push);
-                    if (!range || nxt + __popc(pm) > m.ecap) {
-                        if (lane == 0) fail(ctl, range ? E_INTERNAL : E_TOO_LARGE, 805);
-                        bad = true;
-                        break;
-                    }
-                    int nv = 0;
-                    if (elig) {   // its old entry (if any) is stale from here on
-                        nv = m.ver[u] + 1;
-                        m.ver[u] = nv;
-                    }
-                    if (push) {
-                        m.tgt[u] = tu;
-                        m.tch[u] = sid;
-                    }
-                    mt_push(S, m, pm, push, gu + kMtGmax, u, nv, nxt, lane);
-                    nxt += __popc(pm);
-                }
-                if (bad) break;
-                if (delta < best) {
-                    best = delta; best_len = nm; pc = 0; S1 = 0; S2 = 0;
-                } else {
-                    ++pc;
-                    S1 += g;
-                    S2 += (long long)g * g;
-                    if (kaspar_stop(pc, S1, S2, m.alpha, m.beta)) break;
-                }
-            }
-            __syncwarp();
-            // roll back to the first lowest cut; clear the moved marks
-            for (int i = best_len + lane; i < nm; i += 32) {
-                const int y = m.lv[i], f0 = m.lfrom[i], t = G.part[y];
-                const long long cy = __ldg(G.vwgt + y);
-                G.part[y] = f0;
-                atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[t]), (unsigned long long)(-cy));
-                atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[f0]), (unsigned long long)cy);
-            }
-            __syncwarp();
-            for (int i = lane; i < nm; i += 32) m.mvd[m.lv[i]] = 0;
-            // kept moves: changed blocks and boundary candidates (the moved vertex and its
-            // neighbours outside its new block, as a flow's commit does)
-            for (int i = lane; i < best_len; i += 32) {
-                const int y = m.lv[i], t = G.part[y];
-                m.chg[m.lfrom[i]] = 1;
-                m.chg[t] = 1;
-                if (G.bl) {
-                    if (!__ldcg(G.inb + y) && atomicExch(G.inb + y, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = y;
-                    const int z1 = __ldg(G.xadj + y + 1);
-                    for (int q = __ldg(G.xadj + y); q < z1; ++q) {
-                        const int z = __ldg(G.adjncy + q);
-                        if (__ldcg(G.inb + z) || G.part[z] == t) continue;
-                        if (atomicExch(G.inb + z, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = z;
-                    }
-                }
-            }
-            __syncwarp();
+            long long best;
+            int nm, best_len;
+            bool stopped;
+            mt_search(G, m, S, ctl, sid, true, nxt, Lmax, tseed, lane, bad, best, nm, best_len, stopped);
+            mt_finish(G, m, S, nm, best_len, lane);
             gain_tot -= best;
             tried_tot += nm;
             kept_tot += best_len;
@@ -514,6 +546,193 @@ cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cud
     mt_sort_kernel<<<md.np, kMtTPB, 0, st>>>(md, ctl);
     mt_pass_kernel<<<1, 32, 0, st>>>(G, md, ctl);
     *nl += 5;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- global k-way rounds ----
+// One round of Section 2.2 with the setup of Section 6: a single k-way search started
+// from every vertex with at least `need` blocks other than its own around it (1: the
+// whole boundary; 2: the corner vertices), in ascending splitmix64(rs ^ v) order.
+// Grid-wide: the start set is bucketed by the top bits of its keys (the keys are
+// hashes, so the buckets hold a few entries each), each bucket is sorted by one
+// thread, and the start vertices' gains and targets are computed side by side; then
+// one warp queues them in order and runs the search.  Bucket scratch: ent_below
+// (counts), ent_ver (fill cursors), ent_v (offsets, buckets + 1); the sorted start
+// set: tv, with its packed gains and targets in tkey.
+
+// True if v has at least `need` distinct blocks other than its own among its
+// neighbours (need is 1 or 2).
+__device__ __forceinline__ bool kw_start(const GraphDev &G, int v, int need) {
+    const int pv = G.part[v];
+    const int j1 = __ldg(G.xadj + v + 1);
+    int first = -1;
+    for (int j = __ldg(G.xadj + v); j < j1; ++j) {
+        const int P = G.part[__ldg(G.adjncy + j)];
+        if (P == pv || P == first) continue;
+        if (need == 1 || first >= 0) return true;
+        first = P;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kMtTPB) kw_count_kernel(GraphDev G, MtDev m, int need, unsigned long long rs,
+                                                          int bbits) {
+    extern __shared__ long long s_bw[];   // [k]
+    for (int i = threadIdx.x; i < G.k; i += blockDim.x) s_bw[i] = 0;
+    __syncthreads();
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
+        const int c = __ldg(G.vwgt + v);
+        if (c) atomicAdd(reinterpret_cast<unsigned long long *>(s_bw + G.part[v]), (unsigned long long)c);
+        if (!kw_start(G, v, need)) continue;
+        const unsigned long long key = splitmix64(rs ^ (unsigned long long)(unsigned)v);
+        atomicAdd(m.ent_below + (int)(key >> (64 - bbits)), 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < G.k; i += blockDim.x)
+        if (s_bw[i]) atomicAdd(reinterpret_cast<unsigned long long *>(m.bw + i), (unsigned long long)s_bw[i]);
+}
+
+// Exclusive scan of the bucket counts (one CTA of 1,024 threads); the start set's size
+// goes to cnt[0].
+__global__ void __launch_bounds__(1024) kw_offsets_kernel(MtDev m, int nb) {
+    __shared__ int part_sum[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + 1023) / 1024, b0 = min(nb, t * per), b1 = min(nb, b0 + per);
+    int s = 0;
+    for (int b = b0; b < b1; ++b) s += m.ent_below[b];
+    part_sum[t] = s;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int x = t >= d ? part_sum[t - d] : 0;
+        __syncthreads();
+        part_sum[t] += x;
+        __syncthreads();
+    }
+    int o = part_sum[t] - s;
+    for (int b = b0; b < b1; ++b) {
+        m.ent_v[b] = o;
+        m.ent_ver[b] = 0;
+        o += m.ent_below[b];
+    }
+    if (t == 1023) {
+        m.ent_v[nb] = part_sum[1023];
+        m.cnt[0] = part_sum[1023];
+    }
+}
+
+__global__ void __launch_bounds__(kMtTPB) kw_place_kernel(GraphDev G, MtDev m, int need, unsigned long long rs,
+                                                          int bbits) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
+        if (!kw_start(G, v, need)) continue;
+        const unsigned long long key = splitmix64(rs ^ (unsigned long long)(unsigned)v);
+        const int b = (int)(key >> (64 - bbits));
+        const int pos = m.ent_v[b] + atomicAdd(m.ent_ver + b, 1);
+        m.tkey[pos] = key;
+        m.tv[pos] = v;
+    }
+}
+
+// Each bucket ascending by (key, vertex), one thread per bucket (insertion sort).
+__global__ void __launch_bounds__(kMtTPB) kw_bsort_kernel(MtDev m, int nb) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int o0 = m.ent_v[b], o1 = m.ent_v[b + 1];
+        for (int i = o0 + 1; i < o1; ++i) {
+            const unsigned long long ki = m.tkey[i];
+            const int vi = m.tv[i];
+            int j = i - 1;
+            while (j >= o0 && (m.tkey[j] > ki || (m.tkey[j] == ki && m.tv[j] > vi))) {
+                m.tkey[j + 1] = m.tkey[j];
+                m.tv[j + 1] = m.tv[j];
+                --j;
+            }
+            m.tkey[j + 1] = ki;
+            m.tv[j + 1] = vi;
+        }
+    }
+}
+
+// Gain and target of every start vertex on the round's starting partition, packed as
+// (gain + kMtGmax) << 32 | target into tkey; a gain out of range fails the round.
+__global__ void __launch_bounds__(kMtTPB) kw_gain_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    const int ns = m.cnt[0];
+    const unsigned long long tseed = splitmix64(~m.seed);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+        int g = 0, t = -1;
+        if (!mt_gain(G, m.tv[i], tseed, g, t) || g < -kMtGmax || g > kMtGmax) {
+            fail(ctl, E_INTERNAL, 806);
+            return;
+        }
+        m.tkey[i] = ((unsigned long long)(unsigned)(g + kMtGmax) << 32) | (unsigned)t;
+    }
+}
+
+// The round's search: one warp queues the start set in its order and searches.
+// res: gain kept, tried, kept; pad = 1 if the KaSPar rule stopped the search.
+__global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    __shared__ MtShared S;
+    const int lane = threadIdx.x;
+    if (__ldcg(&ctl->error)) return;
+    for (int i = lane; i < G.k; i += 32) S.bw[i] = m.bw[i];
+    for (int i = lane; i < kMtBuckets; i += 32) S.top[i] = -1;
+    for (int i = lane; i < kMtBuckets / 32; i += 32) S.bits[i] = 0;
+    __syncwarp();
+    const unsigned long long tseed = splitmix64(~m.seed);
+    const int ns = m.cnt[0];
+    bool bad = false;
+    long long nxt = 0;
+    for (int base = 0; base < ns; base += 32) {
+        const int i = base + lane;
+        const bool push = i < ns;
+        int u = -1, g = 0, nv = 0;
+        if (push) {
+            const unsigned long long pk = m.tkey[i];
+            u = m.tv[i];
+            g = (int)(pk >> 32) - kMtGmax;
+            nv = m.ver[u] + 1;
+            m.ver[u] = nv;
+            m.tgt[u] = (int)(unsigned)pk;
+        }
+        const unsigned pm = __ballot_sync(kFull, push);
+        if (nxt + __popc(pm) > m.ecap) {   // (never: ecap >= n + nnz + 64)
+            if (lane == 0) fail(ctl, E_TOO_LARGE, 807);
+            bad = true;
+            break;
+        }
+        mt_push(S, m, pm, push, g + kMtGmax, u, nv, nxt, lane);
+        nxt += __popc(pm);
+    }
+    long long best = 0;
+    int nm = 0, best_len = 0;
+    bool stopped = false;
+    if (!bad) mt_search(G, m, S, ctl, 0, false, nxt, G.Lmax, tseed, lane, bad, best, nm, best_len, stopped);
+    mt_finish(G, m, S, nm, best_len, lane);
+    for (int i = lane; i < G.k; i += 32) m.bw[i] = S.bw[i];
+    if (lane == 0) {
+        m.res->gain = -best;
+        m.res->searches = 1;
+        m.res->tried = nm;
+        m.res->kept = best_len;
+        m.res->pad = stopped ? 1 : 0;
+    }
+}
+
+cudaError_t launch_kway_round(const GraphDev &G, const MtDev &md, Ctl *ctl, int need, unsigned long long rs,
+                              int sms, cudaStream_t st, int *nl) {
+    int bbits = 1;
+    while (bbits < 16 && (2ll << (bbits + 3)) <= G.n) ++bbits;   // about 8 vertices per bucket
+    const int nb = 1 << bbits;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(md.ent_below, 0, sizeof(int) * (size_t)nb, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.bw, 0, sizeof(long long) * (size_t)G.k, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.res, 0, sizeof(MtRes), st)) != cudaSuccess) return e;
+    const int grid = 4 * (sms > 0 ? sms : 1);
+    kw_count_kernel<<<grid, kMtTPB, sizeof(long long) * (size_t)G.k, st>>>(G, md, need, rs, bbits);
+    kw_offsets_kernel<<<1, 1024, 0, st>>>(md, nb);
+    kw_place_kernel<<<grid, kMtTPB, 0, st>>>(G, md, need, rs, bbits);
+    kw_bsort_kernel<<<(nb + kMtTPB - 1) / kMtTPB, kMtTPB, 0, st>>>(md, nb);
+    kw_gain_kernel<<<grid, kMtTPB, 0, st>>>(G, md, ctl);
+    kw_search_kernel<<<1, 32, 0, st>>>(G, md, ctl);
+    *nl += 6;
     return cudaGetLastError();
 }
 

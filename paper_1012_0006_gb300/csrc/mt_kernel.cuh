@@ -50,4 +50,13 @@ struct MtDev {
 // boundary candidate list.  *nl += kernels launched.
 cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cudaStream_t st, int *nl);
 
+// Enqueues one round of the global k-way refinement (Section 2.2, set up as in
+// Section 6): one k-way search from every vertex with at least `need` (1 or 2) blocks
+// other than its own around it, in ascending splitmix64(rs ^ v) order; target ties
+// use splitmix64(~md.seed).  Updates part and md.bw (recomputed as the round starts);
+// md.res receives the round's gain, moves tried and kept, and (pad) whether the KaSPar
+// rule stopped it.  G.bl must be null.  *nl += kernels launched.
+cudaError_t launch_kway_round(const GraphDev &G, const MtDev &md, Ctl *ctl, int need, unsigned long long rs,
+                              int sms, cudaStream_t st, int *nl);
+
 }  // namespace fr

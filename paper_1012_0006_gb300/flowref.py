@@ -178,6 +178,8 @@ SYMBOLS = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "fr_multitry": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                    i32p, i32p, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(MtResult), i8p]),
+    "fr_kway_global": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(MtResult)]),
     "fr_match": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, vp,
                                 ctypes.POINTER(ctypes.c_int32)]),
     "fr_contract": (ctypes.c_int, [vp, ctypes.POINTER(Graph), vp, vp, ctypes.POINTER(ctypes.c_int32),
@@ -437,6 +439,17 @@ class Context:
         if check:
             self._check(st)
         return st, out.as_dict(), changed.astype(bool)
+
+    def kway_global(self, g: DeviceGraph, part, k, eps, init_mode=0, alpha=10, max_rounds=10, seed=0, check=True):
+        """Global k-way refinement rounds (fr_kway_global); returns (status, totals
+        with searches = rounds run)."""
+        out = MtResult()
+        gc = g.c()
+        st = lib().fr_kway_global(self.h, ctypes.byref(gc), _ptr(part), k, eps, init_mode, alpha, max_rounds,
+                                  seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(out))
+        if check:
+            self._check(st)
+        return st, out.as_dict()
 
     def match(self, g: DeviceGraph, part, k, W, seed_l=0, check=True):
         """Greedy matching of one level (fr_match); returns (status, pairs, mate as a device tensor)."""
