@@ -409,6 +409,7 @@ def run_ours(args, world, rank, local, pg):
                "ms_per_step": round(tot / ke * 1e3, 3)}
 
     compare = batched_vs_per_pair(F, ctx, dev) if args.compare else None
+    rates = phase_rates(F, dev, P, pairs // max(args.steps, 1)) if args.compare else None
     active = active_blocks(F, ctx, g, part0, w) if args.active else None
     fm = fm_sweeps(F, ctx, g, part0, w) if args.fm else None
     mtp = multitry_pass(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
@@ -442,7 +443,7 @@ def run_ours(args, world, rank, local, pg):
                        "parallelism": "replicas" if world > 1 else "single", "launch_shape": tuned},
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
-            "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare,
+            "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare, "phase_rates": rates,
             "active_blocks": active, "fm": fm, "multitry": mtp, "vcycle": vc,
         }
         print(json.dumps(out), flush=True)
@@ -624,6 +625,68 @@ def batched_vs_per_pair(F, ctx0, dev, reps=3):
             "launch_shape": dict(flow_sched=best.flow_sched, cluster_ctas=best.cluster_ctas,
                                  inner_ops=best.inner_ops, gr_interval=best.gr_interval,
                                  pulse_passes=best.pulse_passes)}
+
+
+def phase_rates_of(P, peak, npairs):
+    """Corridor BFS and exact-relabel rates of one profiled sweep.  BFS: algorithmic bytes
+    (16 B per visited entry, 12 B per scanned arc) over the BFS phase time.  Relabel: arcs
+    whose tail passed its label on (the gr_arcs counter) over the relabel time; in a
+    cluster the network sits in distributed shared memory, so those arcs move no HBM
+    bytes; the grid-wide relabel reads head, residual and label per arc (12 B) from HBM.
+    In a queue sweep the phase times are summed over pairs (each pair's own cluster),
+    so a rate is one cluster's; `clusters` of them run side by side."""
+    ph, cp = P["phase_ms"], P["cluster_phase_ms"]
+    bm = bytes_model(P)
+    bfs_ms = ph["bfs"]
+    out = {"schedule": "queue" if P["queue"] else "rounds", "pairs": npairs, "rounds": P["nrounds"],
+           "clusters": P["queue_clusters"] if P["queue"] else None, "corridor_n": P["corridor_n"],
+           "corridor_arcs": P["corridor_arcs"]}
+    gbs = bm["bfs"] / max(bfs_ms * 1e-3, 1e-12) / 1e9
+    out["bfs"] = {"visited": P["bfs_visited"], "arcs": P["bfs_arcs"], "bytes": int(bm["bfs"]),
+                  "ms": round(bfs_ms, 3), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    rel_ms = cp["relabel"] + ph["relabel"]
+    grid = ph["relabel"] > cp["relabel"]
+    rate = P["gr_arcs"] / max(rel_ms * 1e-3, 1e-12)
+    out["relabel"] = {"relabels": P["relabels"], "arcs": P["gr_arcs"], "ms": round(rel_ms, 3),
+                      "arcs_per_s": round(rate, 1),
+                      "memory": "hbm" if grid else "distributed shared memory (no HBM bytes)"}
+    if grid:
+        out["relabel"].update(gbs=round(12 * rate / 1e9, 1), frac=round(12 * rate / 1e9 / peak, 4))
+    return out
+
+
+def phase_rates(F, dev, P4, pairs4, reps=3):
+    """BFS and relabel rates on the single-pair bisection at alpha 16 (its largest
+    adaptive corridor), on the 128^3 grid (k = 16), and on the bench workload (P4:
+    the profile the main run took), each with the sweep schedule the library picks."""
+    import numpy as np
+    import torch
+    from paper_1012_0006_gb300 import inputs as I
+    peak, peak_kind = measured_peak_gbs()
+    out = {"peak_gbs": peak, "peak_kind": peak_kind}
+    for name, cfg, alpha in (("rgg2d n=65536 k=2 alpha=16 (one pair)", 2, 16.0),
+                             ("grid3d 128^3 k=16 alpha=2", 3, None)):
+        w = I.config(cfg)
+        g = F.DeviceGraph.from_workload(w, device=dev)
+        part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
+        ctx = F.Context(dev.index if dev.index is not None else 0)
+        opts = F.default_options(mb=1)
+        a = alpha if alpha is not None else w["alpha"]
+        part = part0.clone()
+        ctx.refine_batch(g, part, w["k"], w["eps"], a, opts, results=False)   # warm (allocations)
+        ctx.set_profiling(True)
+        profs = []
+        for _ in range(reps):
+            part.copy_(part0)
+            _, _, summ = ctx.refine_batch(g, part, w["k"], w["eps"], a, opts, results=False)
+            profs.append(ctx.profile())
+        ctx.set_profiling(False)
+        P = min(profs, key=lambda q: q["phase_ms"]["bfs"])
+        out[name] = phase_rates_of(P, peak, summ["npairs"])
+        ctx.close()
+    if P4 is not None:
+        out["rgg3d n=4194304 k=64 alpha=4 (bench workload)"] = phase_rates_of(P4, peak, pairs4)
+    return out
 
 
 # ------------------------------------------------------------------ serving ----

@@ -43,9 +43,9 @@ fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P) {
     }
     size_t b = 0;
     auto add = [&](size_t elem, long long cnt) { b += ((elem * (size_t)cnt + 255) / 256) * 256; };
-    add(4, nn); add(4, nn); add(4, nn); add(1, nn);     // tch ver tgt mvd
+    add(4, nn); add(8, nn); add(4, 1); add(1, nn);      // tch cur epoch mvd
     add(4, nn); add(4, nn);                             // lv lfrom
-    add(4, ecap); add(4, ecap); add(4, ecap);           // ent_v ent_ver ent_below
+    add(32, ecap);                                      // ent (two int4 per entry)
     add(4, kk);                                         // bpair
     add(4, pp); add(4, pp); add(4, pp); add(4, pp);     // pa pb cnt fil
     add(8, pp + 1);                                     // off
@@ -67,10 +67,10 @@ fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P) {
     ctx->mt_n = (int)nn; ctx->mt_nnz = (int)mm; ctx->mt_k = kk; ctx->mt_p = pp;
     char *p = reinterpret_cast<char *>(ctx->mt_mem);
     MtDev &m = ctx->mt;
-    m.tch = carve_mt<int>(p, nn); m.ver = carve_mt<int>(p, nn); m.tgt = carve_mt<int>(p, nn);
+    m.tch = carve_mt<int>(p, nn); m.cur = carve_mt<unsigned long long>(p, nn); m.epoch = carve_mt<unsigned>(p, 1);
     m.mvd = carve_mt<unsigned char>(p, nn);
     m.lv = carve_mt<int>(p, nn); m.lfrom = carve_mt<int>(p, nn);
-    m.ent_v = carve_mt<int>(p, ecap); m.ent_ver = carve_mt<int>(p, ecap); m.ent_below = carve_mt<int>(p, ecap);
+    m.ent = carve_mt<int4>(p, 2 * ecap);
     m.bpair = carve_mt<int>(p, kk);
     m.pa = carve_mt<int>(p, pp); m.pb = carve_mt<int>(p, pp); m.cnt = carve_mt<int>(p, pp); m.fil = carve_mt<int>(p, pp);
     m.off = carve_mt<long long>(p, pp + 1);
@@ -79,7 +79,8 @@ fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P) {
     m.res = carve_mt<MtRes>(p, 1);
     m.ecap = ecap; m.scap = scap;
     // versions start at zero; the moved marks are zero between searches
-    CK(cudaMemsetAsync(m.ver, 0, sizeof(int) * (size_t)nn, ctx->stream));
+    CK(cudaMemsetAsync(m.cur, 0, sizeof(unsigned long long) * (size_t)nn, ctx->stream));
+    CK(cudaMemsetAsync(m.epoch, 0, sizeof(unsigned), ctx->stream));
     CK(cudaMemsetAsync(m.mvd, 0, (size_t)nn, ctx->stream));
     return FR_OK;
 }

@@ -627,7 +627,7 @@ struct ClusterFlow {
         const int na = hdr->na;
         for (int a = threadIdx.x; a < na; a += TPB) hlab[a] = hmax;
         sync();
-        long long rounds = 0;
+        long long arcs = 0;   // arcs this thread's vertices passed their labels along
         const int lane = threadIdx.x & 31;
         for (;;) {
             int nproc = 0;
@@ -639,7 +639,10 @@ struct ClusterFlow {
                     if (lv < nv) {
                         L = *(volatile int *)&lab[lv];
                         fr = L < rfl[lv];
-                        if (fr) rfl[lv] = L;
+                        if (fr) {
+                            rfl[lv] = L;
+                            arcs += cofs[lv + 1] - cofs[lv];
+                        }
                     }
                     nproc += fr;
                     for_flagged(fr, [&](int src, int gl, int G) {
@@ -653,10 +656,10 @@ struct ClusterFlow {
                     });
                 }
             }
-            ++rounds;
             if (cluster_sum(nproc) == 0) break;
         }
-        if (rank == 0 && threadIdx.x == 0) atomicAddLL(&w.ctl->gr_arcs, rounds);   // barrier windows, summed
+        for (int o = 16; o > 0; o >>= 1) arcs += __shfl_xor_sync(FULL, arcs, o);
+        if (lane == 0 && arcs) atomicAddLL(&w.ctl->gr_arcs, arcs);
         int top = 0;
         if (want_top) {
             top = 1;

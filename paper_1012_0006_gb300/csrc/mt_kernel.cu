@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(kMtTPB) mt_sort_kernel(MtDev m, Ctl *ctl) {
 // connection weight, ties to the smaller splitmix64(tseed ^ u << 32 ^ P), then the
 // smaller P.  False if u has no neighbour outside its block.  Up to 8 blocks around u
 // are summed in registers; more fall back to summing each block over the adjacency.
+// The arcs are read 16 at a time, their heads' blocks loaded together after them, so
+// that a vertex of degree <= 16 costs two dependent memory round trips.
 // (pu, j0, j1: u's block and adjacency range, loaded by the caller)
 __device__ bool mt_gain(const GraphDev &G, int u, int pu, int j0, int j1, unsigned long long tseed, int &gain,
                         int &to) {
@@ -174,20 +176,20 @@ __device__ bool mt_gain(const GraphDev &G, int u, int pu, int j0, int j1, unsign
             }
         }
     };
-    // four arcs at a time, so that their blocks are loaded together
-    int j = j0;
-    for (; j + 4 <= j1; j += 4) {
-        const int a0 = __ldg(G.adjncy + j), a1 = __ldg(G.adjncy + j + 1);
-        const int a2 = __ldg(G.adjncy + j + 2), a3 = __ldg(G.adjncy + j + 3);
-        const int w0 = __ldg(G.adjwgt + j), w1 = __ldg(G.adjwgt + j + 1);
-        const int w2 = __ldg(G.adjwgt + j + 2), w3 = __ldg(G.adjwgt + j + 3);
-        const int P0 = G.part[a0], P1 = G.part[a1], P2 = G.part[a2], P3 = G.part[a3];
-        fold(P0, w0);
-        fold(P1, w1);
-        fold(P2, w2);
-        fold(P3, w3);
+    constexpr int C = 16;
+    for (int j = j0; j < j1; j += C) {
+        int a[C], wv[C], P[C];
+#pragma unroll
+        for (int s = 0; s < C; ++s) {
+            a[s] = j + s < j1 ? __ldg(G.adjncy + j + s) : -1;
+            wv[s] = j + s < j1 ? __ldg(G.adjwgt + j + s) : 0;
+        }
+#pragma unroll
+        for (int s = 0; s < C; ++s) P[s] = a[s] >= 0 ? G.part[a[s]] : -1;
+#pragma unroll
+        for (int s = 0; s < C; ++s)
+            if (a[s] >= 0) fold(P[s], wv[s]);
     }
-    for (; j < j1; ++j) fold(G.part[__ldg(G.adjncy + j)], __ldg(G.adjwgt + j));
     if (nt == 0) return false;
     const unsigned long long hu = tseed ^ ((unsigned long long)(unsigned)u << 32);
     int best = -1, bw = 0;
@@ -240,14 +242,23 @@ __device__ __forceinline__ unsigned mt_lanemask_lt() {
 
 struct MtShared {
     int top[kMtBuckets];               // top entry of each gain bucket, -1 empty
-    unsigned bits[kMtBuckets / 32];    // non-empty buckets (possibly holding only stale entries)
+    unsigned bits[kMtBuckets / 32];    // non-empty buckets (possibly holding only dead entries)
     long long bw[kMtMaxK];             // block weights during the pass
 };
 
+// A queue entry: two int4, {vertex, entry below it in its bucket, live, target block}
+// and {block, weight, adjacency begin, adjacency end} of the vertex, so that a pop is
+// one memory round trip.  Keying a vertex again clears `live` in its previous entry of
+// the same search (cur[v] = search epoch << 32 | entry).
+__device__ __forceinline__ void mt_kill(const MtDev &m, unsigned long long cu, unsigned epoch) {
+    if ((unsigned)(cu >> 32) == epoch) reinterpret_cast<int *>(m.ent + 2 * (cu & 0xffffffffull))[2] = 0;
+}
+
 // Pushes the lanes' entries (in lane order) onto their buckets: entries go to
 // [nxt, nxt + popc(pm)); a lower lane's entry lies below a higher lane's in one bucket.
-__device__ __forceinline__ void mt_push(MtShared &S, const MtDev &m, unsigned pm, bool push, int bk, int u, int nv,
-                                        long long nxt, int lane) {
+// Each pushing lane's vertex u gets cur[u] = this entry.
+__device__ __forceinline__ void mt_push(MtShared &S, const MtDev &m, unsigned pm, bool push, int bk, int u, int tu,
+                                        int pu, int cw, int u0, int u1, unsigned epoch, long long nxt, int lane) {
     const long long pos = nxt + __popc(pm & mt_lanemask_lt());
     const unsigned grp = __match_any_sync(kFull, push ? bk : -1 - lane);
     const unsigned lower = grp & mt_lanemask_lt();
@@ -256,9 +267,9 @@ __device__ __forceinline__ void mt_push(MtShared &S, const MtDev &m, unsigned pm
     if (push) below = lower ? (int)pos_lower : S.top[bk];
     __syncwarp();
     if (push) {
-        m.ent_v[pos] = u;
-        m.ent_ver[pos] = nv;
-        m.ent_below[pos] = below;
+        m.ent[2 * pos] = make_int4(u, below, 1, tu);
+        m.ent[2 * pos + 1] = make_int4(pu, cw, u0, u1);
+        m.cur[u] = ((unsigned long long)epoch << 32) | (unsigned long long)pos;
         if ((grp & ~lower & ~(1u << lane)) == 0) {   // highest lane of its bucket
             S.top[bk] = (int)pos;
             atomicOr(&S.bits[bk >> 5], 1u << (bk & 31));
@@ -268,16 +279,17 @@ __device__ __forceinline__ void mt_push(MtShared &S, const MtDev &m, unsigned pm
 }
 
 // One k-way search (one warp) from the entries already pushed, nxt of them: pop the
-// highest current entry, move it unless its target would exceed L_max, key its unmoved
-// neighbours again (CSR order), stop by the KaSPar rule or an empty queue.  touch: the
-// multi-try pass's rule (a vertex another search of the pass queued is neither queued nor
-// moved; what this search queues is marked with sid); false: no such rule (the global
-// k-way rounds).  Returns the best prefix (best < 0 is the largest cut decrease),
-// the moves made and kept, and whether the KaSPar rule stopped it; bad on an error.
+// highest live entry, move its vertex unless the target would exceed L_max, key its
+// unmoved neighbours again (CSR order), stop by the KaSPar rule or an empty queue.
+// touch: the multi-try pass's rule (a vertex another search of the pass queued is
+// neither queued nor moved; what this search queues is marked with sid); false: no
+// such rule (the global k-way rounds).  Returns the best prefix (best < 0 is the
+// largest cut decrease), the moves made and kept, and whether the KaSPar rule stopped
+// it; bad on an error.
 __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtShared &S, Ctl *ctl, int sid,
-                                          bool touch, long long &nxt, long long Lmax, unsigned long long tseed,
-                                          int lane, bool &bad, long long &best, int &nm, int &best_len,
-                                          bool &stopped) {
+                                          bool touch, unsigned epoch, long long &nxt, long long Lmax,
+                                          unsigned long long tseed, int lane, bool &bad, long long &best, int &nm,
+                                          int &best_len, bool &stopped) {
     long long delta = 0, S1 = 0, S2 = 0;
     int pc = 0;
     best = 0;
@@ -285,7 +297,7 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
     best_len = 0;
     stopped = false;
     while (!bad) {
-        // pop the highest current entry
+        // pop the highest live entry
         int x = -1, g = 0, xto = 0, xfrom = 0, xc = 0, xy0 = 0, xy1 = 0;
         for (;;) {
             int hb = -1;
@@ -303,16 +315,12 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
                     S.top[b] = -1;
                     S.bits[b >> 5] &= ~(1u << (b & 31));
                 } else {
-                    const int xv = m.ent_v[e], below = m.ent_below[e], ev = m.ent_ver[e];
-                    // the vertex's state, loaded together with its version
-                    const int vv = m.ver[xv], tg = m.tgt[xv], pf = G.part[xv];
-                    const int cw = __ldg(G.vwgt + xv), a0 = __ldg(G.xadj + xv), a1 = __ldg(G.xadj + xv + 1);
-                    S.top[b] = below;
-                    if (below < 0) S.bits[b >> 5] &= ~(1u << (b & 31));
-                    if (ev == vv) {   // current: it leaves the queue
-                        got = xv;
-                        m.ver[xv] = vv + 1;
-                        gto = tg; gfrom = pf; gc = cw; gy0 = a0; gy1 = a1;
+                    const int4 h = m.ent[2 * e], d = m.ent[2 * e + 1];
+                    S.top[b] = h.y;
+                    if (h.y < 0) S.bits[b >> 5] &= ~(1u << (b & 31));
+                    if (h.z) {   // live: the vertex leaves the queue
+                        got = h.x;
+                        gto = h.w; gfrom = d.x; gc = d.y; gy0 = d.z; gy1 = d.w;
                     }
                 }
             }
@@ -351,12 +359,17 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
             const int jj = jb + lane;
             const int u = jj < y1 ? __ldg(G.adjncy + jj) : -1;
             bool elig = false, push = false;
-            int gu = 0, tu = -1;
+            int gu = 0, tu = -1, pu = 0, cw = 0, u0 = 0, u1 = 0;
+            unsigned long long cu = 0;
             if (u >= 0) {
-                // u's marks, block and adjacency range, loaded together
+                // u's marks, block, weight, adjacency range and entry, loaded together
                 const unsigned char mv = m.mvd[u];
-                const int tc = touch ? m.tch[u] : 0, pu = G.part[u];
-                const int u0 = __ldg(G.xadj + u), u1 = __ldg(G.xadj + u + 1);
+                const int tc = touch ? m.tch[u] : 0;
+                pu = G.part[u];
+                cw = __ldg(G.vwgt + u);
+                u0 = __ldg(G.xadj + u);
+                u1 = __ldg(G.xadj + u + 1);
+                cu = m.cur[u];
                 elig = !mv && (tc == 0 || tc == sid);
                 if (elig) push = mt_gain(G, u, pu, u0, u1, tseed, gu, tu);
             }
@@ -367,16 +380,9 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
                 bad = true;
                 break;
             }
-            int nv = 0;
-            if (elig) {   // its old entry (if any) is stale from here on
-                nv = m.ver[u] + 1;
-                m.ver[u] = nv;
-            }
-            if (push) {
-                m.tgt[u] = tu;
-                if (touch) m.tch[u] = sid;
-            }
-            mt_push(S, m, pm, push, gu + kMtGmax, u, nv, nxt, lane);
+            if (elig) mt_kill(m, cu, epoch);   // its old entry (if any) is dead from here on
+            if (push && touch) m.tch[u] = sid;
+            mt_push(S, m, pm, push, gu + kMtGmax, u, tu, pu, cw, u0, u1, epoch, nxt, lane);
             nxt += __popc(pm);
         }
         if (bad) break;
@@ -395,11 +401,14 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
     __syncwarp();
 }
 
-// After a search: roll back to the first lowest cut, clear the moved marks, and for the
-// kept moves mark the blocks they left and entered and list the boundary candidates
-// (the moved vertex and its neighbours outside its new block, as a flow's commit does).
+// After a search: roll back to the first lowest cut and clear the moved marks.  With
+// bookkeeping (the multi-try pass), for the kept moves mark the blocks they left and
+// entered and list the boundary candidates (the moved vertex and its neighbours outside
+// its new block, as a flow's commit does): the kept moves 32 at a time, then one move
+// at a time with the lanes on its arcs; bln counts the list (this warp alone appends
+// to it while the pass runs).
 __device__ __forceinline__ void mt_finish(const GraphDev &G, const MtDev &m, MtShared &S, int nm, int best_len,
-                                          int lane) {
+                                          int lane, bool keep, int &bln) {
     for (int i = best_len + lane; i < nm; i += 32) {
         const int y = m.lv[i], f0 = m.lfrom[i], t = G.part[y];
         const long long cy = __ldg(G.vwgt + y);
@@ -409,21 +418,60 @@ __device__ __forceinline__ void mt_finish(const GraphDev &G, const MtDev &m, MtS
     }
     __syncwarp();
     for (int i = lane; i < nm; i += 32) m.mvd[m.lv[i]] = 0;
-    for (int i = lane; i < best_len; i += 32) {
-        const int y = m.lv[i], t = G.part[y];
-        m.chg[m.lfrom[i]] = 1;
-        m.chg[t] = 1;
-        if (G.bl) {
-            if (!__ldcg(G.inb + y) && atomicExch(G.inb + y, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = y;
-            const int z1 = __ldg(G.xadj + y + 1);
-            for (int q = __ldg(G.xadj + y); q < z1; ++q) {
-                const int z = __ldg(G.adjncy + q);
-                if (__ldcg(G.inb + z) || G.part[z] == t) continue;
-                if (atomicExch(G.inb + z, 1) == 0) G.bl[atomicAdd(G.blc, 1)] = z;
+    if (!keep) {
+        __syncwarp();
+        return;
+    }
+    for (int ib = 0; ib < best_len; ib += 32) {
+        const int i = ib + lane;
+        int y = -1, t = 0, a0 = 0, a1 = 0;
+        if (i < best_len) {
+            y = m.lv[i];
+            const int f = m.lfrom[i];
+            t = G.part[y];
+            a0 = __ldg(G.xadj + y);
+            a1 = __ldg(G.xadj + y + 1);
+            m.chg[f] = 1;
+            m.chg[t] = 1;
+        }
+        if (!G.bl) continue;
+        const int cnt = min(32, best_len - ib);
+        for (int c = 0; c < cnt; ++c) {
+            const int yc = __shfl_sync(kFull, y, c), tc = __shfl_sync(kFull, t, c);
+            const int c0 = __shfl_sync(kFull, a0, c), c1 = __shfl_sync(kFull, a1, c);
+            // slot c0 - 1 stands for the moved vertex itself
+            for (int qb = c0 - 1; qb < c1; qb += 32) {
+                const int q = qb + lane;
+                int z = -1;
+                bool app = false;
+                if (q < c1) {
+                    z = q < c0 ? yc : __ldg(G.adjncy + q);
+                    app = !__ldcg(G.inb + z) && (q < c0 || G.part[z] != tc);
+                }
+                const unsigned am = __ballot_sync(kFull, app);
+                if (app) {
+                    G.inb[z] = 1;
+                    G.bl[bln + __popc(am & mt_lanemask_lt())] = z;
+                }
+                bln += __popc(am);
+                __syncwarp();
             }
         }
     }
     __syncwarp();
+}
+
+// Keys lane's vertex u for a start set (state loaded here): its gain and target, and,
+// if it is a boundary vertex, its entry in the lanes' push.  Returns whether it pushes.
+__device__ __forceinline__ bool mt_start_key(const GraphDev &G, const MtDev &m, int u, unsigned long long tseed,
+                                             int &g, int &t, int &pu, int &cw, int &u0, int &u1,
+                                             unsigned long long &cu) {
+    pu = G.part[u];
+    cw = __ldg(G.vwgt + u);
+    u0 = __ldg(G.xadj + u);
+    u1 = __ldg(G.xadj + u + 1);
+    cu = m.cur[u];
+    return mt_gain(G, u, pu, u0, u1, tseed, g, t);
 }
 
 // The whole pass: one warp.
@@ -442,6 +490,8 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
     for (int p = 0; p < m.np; ++p) maxlen = max(maxlen, m.cnt[p]);
     long long gain_tot = 0;
     int searches = 0, tried_tot = 0, kept_tot = 0, sid = 0;
+    unsigned epoch = *m.epoch;
+    int bln = G.bl ? *G.blc : 0;
     bool bad = false;
     __syncwarp();
     // the todo entries in pass order (entry j of every pair, then j + 1), 32 at a time:
@@ -474,6 +524,7 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
             }
             if (!bnd) continue;
             ++sid;
+            if (++epoch == 0) epoch = 1;
             // ---- one k-way search ----
             for (int i = lane; i < kMtBuckets; i += 32) S.top[i] = -1;
             for (int i = lane; i < kMtBuckets / 32; i += 32) S.bits[i] = 0;
@@ -487,9 +538,10 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
                 int u = -1;
                 if (i < 0) u = v;
                 else if (i < deg) u = __ldg(G.adjncy + x0 + i);
-                int g = 0, t = -1;
+                int g = 0, t = -1, pu = 0, cw = 0, u0 = 0, u1 = 0;
+                unsigned long long cu = 0;
                 bool push = false;
-                if (u >= 0 && (u == v || m.tch[u] == 0)) push = mt_gain(G, u, tseed, g, t);
+                if (u >= 0 && (u == v || m.tch[u] == 0)) push = mt_start_key(G, m, u, tseed, g, t, pu, cw, u0, u1, cu);
                 const bool range = __all_sync(kFull, !push || (g >= -kMtGmax && g <= kMtGmax));
                 const unsigned pm = __ballot_sync(kFull, push);
                 if (!range || nxt + __popc(pm) > m.ecap) {
@@ -497,21 +549,18 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
                     bad = true;
                     break;
                 }
-                int nv = 0;
                 if (push) {
-                    nv = m.ver[u] + 1;
-                    m.ver[u] = nv;
-                    m.tgt[u] = t;
+                    mt_kill(m, cu, epoch);
                     m.tch[u] = sid;
                 }
-                mt_push(S, m, pm, push, g + kMtGmax, u, nv, nxt, lane);
+                mt_push(S, m, pm, push, g + kMtGmax, u, t, pu, cw, u0, u1, epoch, nxt, lane);
                 nxt += __popc(pm);
             }
             long long best;
             int nm, best_len;
             bool stopped;
-            mt_search(G, m, S, ctl, sid, true, nxt, Lmax, tseed, lane, bad, best, nm, best_len, stopped);
-            mt_finish(G, m, S, nm, best_len, lane);
+            mt_search(G, m, S, ctl, sid, true, epoch, nxt, Lmax, tseed, lane, bad, best, nm, best_len, stopped);
+            mt_finish(G, m, S, nm, best_len, lane, true, bln);
             gain_tot -= best;
             tried_tot += nm;
             kept_tot += best_len;
@@ -524,6 +573,8 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
         G.blockw[i] = S.bw[i];
     }
     if (lane == 0) {
+        *m.epoch = epoch;
+        if (G.bl) *G.blc = bln;
         m.res->gain = gain_tot;
         m.res->searches = searches;
         m.res->tried = tried_tot;
@@ -556,9 +607,9 @@ cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cud
 // Grid-wide: the start set is bucketed by the top bits of its keys (the keys are
 // hashes, so the buckets hold a few entries each), each bucket is sorted by one
 // thread, and the start vertices' gains and targets are computed side by side; then
-// one warp queues them in order and runs the search.  Bucket scratch: ent_below
-// (counts), ent_ver (fill cursors), ent_v (offsets, buckets + 1); the sorted start
-// set: tv, with its packed gains and targets in tkey.
+// one warp queues them in order and runs the search.  Bucket scratch, in the entry
+// array (free until the search): counts, fill cursors and offsets of the nb buckets
+// (kw_scratch); the sorted start set: tv, with its packed gains and targets in tkey.
 
 // True if v has at least `need` distinct blocks other than its own among its
 // neighbours (need is 1 or 2).
@@ -575,8 +626,18 @@ __device__ __forceinline__ bool kw_start(const GraphDev &G, int v, int need) {
     return false;
 }
 
+// counts, fill cursors, offsets (nb + 1 each) of the start set's buckets
+struct KwScratch {
+    int *cnt, *fil, *off;
+};
+__device__ __forceinline__ KwScratch kw_scratch(const MtDev &m, int nb) {
+    int *b = reinterpret_cast<int *>(m.ent);
+    return {b, b + (nb + 1), b + 2 * (nb + 1)};
+}
+
 __global__ void __launch_bounds__(kMtTPB) kw_count_kernel(GraphDev G, MtDev m, int need, unsigned long long rs,
                                                           int bbits) {
+    const KwScratch K = kw_scratch(m, 1 << bbits);
     extern __shared__ long long s_bw[];   // [k]
     for (int i = threadIdx.x; i < G.k; i += blockDim.x) s_bw[i] = 0;
     __syncthreads();
@@ -585,7 +646,7 @@ __global__ void __launch_bounds__(kMtTPB) kw_count_kernel(GraphDev G, MtDev m, i
         if (c) atomicAdd(reinterpret_cast<unsigned long long *>(s_bw + G.part[v]), (unsigned long long)c);
         if (!kw_start(G, v, need)) continue;
         const unsigned long long key = splitmix64(rs ^ (unsigned long long)(unsigned)v);
-        atomicAdd(m.ent_below + (int)(key >> (64 - bbits)), 1);
+        atomicAdd(K.cnt + (int)(key >> (64 - bbits)), 1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < G.k; i += blockDim.x)
@@ -596,10 +657,11 @@ __global__ void __launch_bounds__(kMtTPB) kw_count_kernel(GraphDev G, MtDev m, i
 // goes to cnt[0].
 __global__ void __launch_bounds__(1024) kw_offsets_kernel(MtDev m, int nb) {
     __shared__ int part_sum[1024];
+    const KwScratch K = kw_scratch(m, nb);
     const int t = threadIdx.x;
     const int per = (nb + 1023) / 1024, b0 = min(nb, t * per), b1 = min(nb, b0 + per);
     int s = 0;
-    for (int b = b0; b < b1; ++b) s += m.ent_below[b];
+    for (int b = b0; b < b1; ++b) s += K.cnt[b];
     part_sum[t] = s;
     __syncthreads();
     for (int d = 1; d < 1024; d <<= 1) {
@@ -610,23 +672,24 @@ __global__ void __launch_bounds__(1024) kw_offsets_kernel(MtDev m, int nb) {
     }
     int o = part_sum[t] - s;
     for (int b = b0; b < b1; ++b) {
-        m.ent_v[b] = o;
-        m.ent_ver[b] = 0;
-        o += m.ent_below[b];
+        K.off[b] = o;
+        K.fil[b] = 0;
+        o += K.cnt[b];
     }
     if (t == 1023) {
-        m.ent_v[nb] = part_sum[1023];
+        K.off[nb] = part_sum[1023];
         m.cnt[0] = part_sum[1023];
     }
 }
 
 __global__ void __launch_bounds__(kMtTPB) kw_place_kernel(GraphDev G, MtDev m, int need, unsigned long long rs,
                                                           int bbits) {
+    const KwScratch K = kw_scratch(m, 1 << bbits);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
         if (!kw_start(G, v, need)) continue;
         const unsigned long long key = splitmix64(rs ^ (unsigned long long)(unsigned)v);
         const int b = (int)(key >> (64 - bbits));
-        const int pos = m.ent_v[b] + atomicAdd(m.ent_ver + b, 1);
+        const int pos = K.off[b] + atomicAdd(K.fil + b, 1);
         m.tkey[pos] = key;
         m.tv[pos] = v;
     }
@@ -634,8 +697,9 @@ __global__ void __launch_bounds__(kMtTPB) kw_place_kernel(GraphDev G, MtDev m, i
 
 // Each bucket ascending by (key, vertex), one thread per bucket (insertion sort).
 __global__ void __launch_bounds__(kMtTPB) kw_bsort_kernel(MtDev m, int nb) {
+    const KwScratch K = kw_scratch(m, nb);
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        const int o0 = m.ent_v[b], o1 = m.ent_v[b + 1];
+        const int o0 = K.off[b], o1 = K.off[b + 1];
         for (int i = o0 + 1; i < o1; ++i) {
             const unsigned long long ki = m.tkey[i];
             const int vi = m.tv[i];
@@ -678,19 +742,23 @@ __global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, C
     __syncwarp();
     const unsigned long long tseed = splitmix64(~m.seed);
     const int ns = m.cnt[0];
+    unsigned epoch = *m.epoch + 1;
+    if (epoch == 0) epoch = 1;
     bool bad = false;
     long long nxt = 0;
     for (int base = 0; base < ns; base += 32) {
         const int i = base + lane;
         const bool push = i < ns;
-        int u = -1, g = 0, nv = 0;
+        int u = -1, g = 0, t = 0, pu = 0, cw = 0, u0 = 0, u1 = 0;
         if (push) {
             const unsigned long long pk = m.tkey[i];
             u = m.tv[i];
             g = (int)(pk >> 32) - kMtGmax;
-            nv = m.ver[u] + 1;
-            m.ver[u] = nv;
-            m.tgt[u] = (int)(unsigned)pk;
+            t = (int)(unsigned)pk;
+            pu = G.part[u];
+            cw = __ldg(G.vwgt + u);
+            u0 = __ldg(G.xadj + u);
+            u1 = __ldg(G.xadj + u + 1);
         }
         const unsigned pm = __ballot_sync(kFull, push);
         if (nxt + __popc(pm) > m.ecap) {   // (never: ecap >= n + nnz + 64)
@@ -698,16 +766,17 @@ __global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, C
             bad = true;
             break;
         }
-        mt_push(S, m, pm, push, g + kMtGmax, u, nv, nxt, lane);
+        mt_push(S, m, pm, push, g + kMtGmax, u, t, pu, cw, u0, u1, epoch, nxt, lane);
         nxt += __popc(pm);
     }
     long long best = 0;
-    int nm = 0, best_len = 0;
+    int nm = 0, best_len = 0, bln = 0;
     bool stopped = false;
-    if (!bad) mt_search(G, m, S, ctl, 0, false, nxt, G.Lmax, tseed, lane, bad, best, nm, best_len, stopped);
-    mt_finish(G, m, S, nm, best_len, lane);
+    if (!bad) mt_search(G, m, S, ctl, 0, false, epoch, nxt, G.Lmax, tseed, lane, bad, best, nm, best_len, stopped);
+    mt_finish(G, m, S, nm, best_len, lane, false, bln);
     for (int i = lane; i < G.k; i += 32) m.bw[i] = S.bw[i];
     if (lane == 0) {
+        *m.epoch = epoch;
         m.res->gain = -best;
         m.res->searches = 1;
         m.res->tried = nm;
@@ -722,7 +791,7 @@ cudaError_t launch_kway_round(const GraphDev &G, const MtDev &md, Ctl *ctl, int 
     while (bbits < 16 && (2ll << (bbits + 3)) <= G.n) ++bbits;   // about 8 vertices per bucket
     const int nb = 1 << bbits;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(md.ent_below, 0, sizeof(int) * (size_t)nb, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(md.ent, 0, sizeof(int) * (size_t)nb, st)) != cudaSuccess) return e;   // bucket counts
     if ((e = cudaMemsetAsync(md.bw, 0, sizeof(long long) * (size_t)G.k, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(md.res, 0, sizeof(MtRes), st)) != cudaSuccess) return e;
     const int grid = 4 * (sms > 0 ? sms : 1);

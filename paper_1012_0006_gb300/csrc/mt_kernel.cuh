@@ -20,15 +20,16 @@ struct MtRes {
 };
 
 // Device state of a multi-try pass over the pairs of one matching of one graph.
-// Per-vertex arrays: tch is cleared before every pass (by the launcher); ver only
-// grows; mvd is zero between searches.
+// Per-vertex arrays: tch is cleared before every pass (by the launcher); mvd is zero
+// between searches; cur is meaningful only for the current search's epoch.
 struct MtDev {
     int *tch;                    // [n] search of this pass that queued the vertex, 0 = none
-    int *ver;                    // [n] key version: a queue entry is current iff it matches
-    int *tgt;                    // [n] target block of the vertex's current key
+    unsigned long long *cur;     // [n] epoch << 32 | the vertex's latest entry in that search
+    unsigned *epoch;             // [1] epoch of the last search run (searches number 1, 2, ...)
     unsigned char *mvd;          // [n] moved by the current search
     int *lv, *lfrom;             // [n] moves of the current search: vertex, source block
-    int *ent_v, *ent_ver, *ent_below;   // [ecap] bucket stack entries of the current search
+    int4 *ent;                   // [2 ecap] bucket stack entries of the current search:
+                                 //   {vertex, entry below, live, target}, {block, weight, adjacency range}
     int *bpair;                  // [k] pair of the pass that the block belongs to, -1 none
     int *pa, *pb;                // [P] the pairs, in pass order
     int *cnt, *fil;              // [P] todo list lengths, fill cursors
