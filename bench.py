@@ -50,6 +50,9 @@ def make_workload(name):
     elif name == "grid2d":
         w = I.config(1)
         desc = "grid2d 64x64 k=2 eps=0.03 alpha=1 (quick checks)"
+    elif name == "rgg2d":
+        w = dict(I.config(2), alpha=16.0)
+        desc = "rgg2d n=65536 deg~8 k=2 eps=0.03 alpha=16 (one pair, the largest adaptive corridor)"
     else:
         raise SystemExit(f"unknown workload {name}")
     return w, desc
@@ -670,7 +673,7 @@ def phase_rates(F, dev, P4, pairs4, reps=3):
         g = F.DeviceGraph.from_workload(w, device=dev)
         part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
         ctx = F.Context(dev.index if dev.index is not None else 0)
-        opts = F.default_options(mb=1)
+        opts = F.default_options(mb=int(w["mb"]))
         a = alpha if alpha is not None else w["alpha"]
         part = part0.clone()
         ctx.refine_batch(g, part, w["k"], w["eps"], a, opts, results=False)   # warm (allocations)
@@ -869,7 +872,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rgg3d", choices=["rgg3d", "grid3d", "grid2d"])
+    ap.add_argument("--workload", default="rgg3d", choices=["rgg3d", "grid3d", "grid2d", "rgg2d"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kMtTPB) mt_sort_kernel(MtDev m, Ctl *ctl) {
 // smaller P.  False if u has no neighbour outside its block.  Up to 8 blocks around u
 // are summed in registers; more fall back to summing each block over the adjacency.
 // The arcs are read 16 at a time, their heads' blocks loaded together after them, so
-// that a vertex of degree <= 16 costs two dependent memory round trips.
+// that a vertex costs two dependent memory round trips per 16 arcs; a vertex of degree
+// <= 32 takes the register-only path below.
 // (pu, j0, j1: u's block and adjacency range, loaded by the caller)
 __device__ bool mt_gain(const GraphDev &G, int u, int pu, int j0, int j1, unsigned long long tseed, int &gain,
                         int &to) {
@@ -177,6 +178,65 @@ __device__ bool mt_gain(const GraphDev &G, int u, int pu, int j0, int j1, unsign
         }
     };
     constexpr int C = 16;
+    constexpr int CF = 32;
+    if (j1 - j0 <= CF) {
+        // degree <= 32: the arcs and their heads' blocks in registers, then one pass over
+        // them per distinct foreign block (in the order of first appearance), each a set
+        // of independent compares; a target's hash only when its weight ties the best
+        const int deg = j1 - j0;
+        int a[CF], wv[CF], P[CF];
+#pragma unroll
+        for (int s = 0; s < CF; ++s) {
+            a[s] = s < deg ? __ldg(G.adjncy + j0 + s) : 0;
+            wv[s] = s < deg ? __ldg(G.adjwgt + j0 + s) : 0;
+        }
+#pragma unroll
+        for (int s = 0; s < CF; ++s) P[s] = s < deg ? G.part[a[s]] : pu;
+        unsigned rem = 0;
+#pragma unroll
+        for (int s = 0; s < CF; ++s) {
+            if (P[s] == pu) own += wv[s];
+            else rem |= 1u << s;
+        }
+        if (!rem) return false;
+        const unsigned long long hu = tseed ^ ((unsigned long long)(unsigned)u << 32);
+        int best = -1, bw = 0;
+        unsigned long long bh = 0;
+        bool hv = false;
+        while (rem) {
+            int B = 0;
+#pragma unroll
+            for (int s = CF - 1; s >= 0; --s)
+                if ((rem >> s) & 1u) B = P[s];
+            int wB = 0;
+            unsigned hit = 0;
+#pragma unroll
+            for (int s = 0; s < CF; ++s)
+                if (((rem >> s) & 1u) && P[s] == B) {
+                    wB += wv[s];
+                    hit |= 1u << s;
+                }
+            rem &= ~hit;
+            if (best < 0 || wB > bw) {
+                best = B;
+                bw = wB;
+                hv = false;
+            } else if (wB == bw) {
+                const unsigned long long hB = splitmix64(hu ^ (unsigned)B);
+                if (!hv) {
+                    bh = splitmix64(hu ^ (unsigned)best);
+                    hv = true;
+                }
+                if (hB < bh || (hB == bh && B < best)) {
+                    best = B;
+                    bh = hB;
+                }
+            }
+        }
+        gain = bw - own;
+        to = best;
+        return true;
+    }
     for (int j = j0; j < j1; j += C) {
         int a[C], wv[C], P[C];
 #pragma unroll
@@ -224,8 +284,23 @@ __device__ __forceinline__ bool mt_gain(const GraphDev &G, int u, unsigned long 
     return mt_gain(G, u, G.part[u], __ldg(G.xadj + u), __ldg(G.xadj + u + 1), tseed, gain, to);
 }
 
-// KaSPar rule in the oracle's order of rounded double operations.
+// KaSPar rule p mu^2 > alpha sigma^2 + beta (mu, sigma^2: mean and variance of the p
+// gains since the last new minimum; S1, S2: their sum and sum of squares), decided as the
+// oracle's rounded double operations in its order decide it.  Times p^2 the rule reads
+// D = p S1^2 - alpha (p S2 - S1^2) - beta p^2 > 0.  D is first estimated in single
+// precision; with M the sum of the four terms' magnitudes, that estimate is within about
+// 1.1e-6 M of the exact D (18 roundings of 2^-24), and the double expression within
+// about 1e-15 M, so whenever the estimate exceeds 1e-5 M in magnitude all three have the
+// same sign.  Only the rest take the double path (FP64 is slow on this part).
 __device__ __forceinline__ bool kaspar_stop(int p, long long S1, long long S2, int alpha, double beta) {
+    {
+        const float pf = (float)p, s1 = (float)S1, s2 = (float)S2, af = (float)alpha, bf = (float)beta;
+        const float s11 = s1 * s1;
+        const float t1 = pf * s11, t2 = af * (pf * s2), t3 = af * s11, t4 = bf * (pf * pf);
+        const float D = ((t1 - t2) + t3) - t4;
+        const float M = ((t1 + t2) + t3) + t4;
+        if (fabsf(D) > 1e-5f * M) return D > 0.f;
+    }
     const double pd = (double)p;
     const double mu = __ddiv_rn((double)S1, pd);
     const double var = __dsub_rn(__ddiv_rn((double)S2, pd), __dmul_rn(mu, mu));
