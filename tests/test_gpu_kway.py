@@ -90,3 +90,12 @@ def test_rounds_without_boundary_and_option_checks(F, ctx):
     st, _ = ctx.kway_global(g2, part2, w["k"], w["eps"], check=False)
     assert st == F.FR_ERR_TOO_LARGE
     assert (part == before).all() and (part2 == before).all()
+
+
+@pytest.mark.parametrize("seed,init_mode", [(1, 0), (2, 0), (3, 1), (4, 1)])
+def test_rounds_hub_graph(F, ctx, seed, init_mode):
+    # hubs of degree 33-110 with neighbours in up to 16 blocks (serial gain path and its
+    # re-summing fallback), in the start set and keyed again as their neighbours move
+    from tests.hub_graph import hub_workload
+    w = hub_workload(seed, weighted=seed % 2 == 1)
+    _rounds(F, ctx, w, init_mode, 10, 6, seed)

@@ -141,3 +141,13 @@ def test_multitry_option_checks(F, ctx):
     st, *_ = ctx.refine_active(g2, part2, w["k"], w["eps"], 1.0, F.default_options(mt_alpha=10), check=False)
     assert st == F.FR_ERR_TOO_LARGE
     assert (part2 == before).all()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_pass_hub_graph(F, ctx, seed):
+    # hubs of degree 33-110 with neighbours in up to 16 blocks: the searches' serial gain
+    # path (degree > 32) and its re-summing fallback (more than eight adjacent blocks)
+    from tests.hub_graph import hub_workload
+    w = hub_workload(seed, weighted=seed != 2)
+    for r in range(2):
+        _pass(F, ctx, w, _matching(w, r), (10, 1)[r], seed + r)
