@@ -416,6 +416,7 @@ def run_ours(args, world, rank, local, pg):
     active = active_blocks(F, ctx, g, part0, w) if args.active else None
     fm = fm_sweeps(F, ctx, g, part0, w) if args.fm else None
     mtp = multitry_pass(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
+    kwr = kway_rounds(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
     vc = multilevel(F, ctx, g, part0, w) if args.vcycle else None
 
     serving = None
@@ -447,7 +448,7 @@ def run_ours(args, world, rank, local, pg):
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare, "phase_rates": rates,
-            "active_blocks": active, "fm": fm, "multitry": mtp, "vcycle": vc,
+            "active_blocks": active, "fm": fm, "multitry": mtp, "kway_rounds": kwr, "vcycle": vc,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -504,6 +505,38 @@ def multitry_pass(F, ctx, g, part0, w, alpha=10, reps=2, cpu=True):
         st, pref, tref, _ = O.multitry(wo, pairs, alpha)
         out["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
         out["parity"] = bool(tref == {f: tot[f] for f in ("gain", "searches", "tried", "kept")} and
+                             np.array_equal(pref, part.cpu().numpy()))
+    return out
+
+
+def kway_rounds(F, ctx, g, part0, w, cpu=True):
+    """Global k-way refinement rounds as the paper's setup runs them (Section 6: from the
+    complete partition boundary, alpha = 10, at most ten rounds, stopping after a round
+    without improvement) on the bench workload: device time (CUDA events around
+    fr_kway_global, one run after a warm one), the rounds' totals, and the oracle's rounds
+    on the host (one run, one thread) with a parity flag."""
+    import numpy as np
+    import torch
+    part = part0.clone()
+    ctx.kway_global(g, part, w["k"], w["eps"], init_mode=0, alpha=10, max_rounds=10, seed=0)   # warm
+    part.copy_(part0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, tot = ctx.kway_global(g, part, w["k"], w["eps"], init_mode=0, alpha=10, max_rounds=10, seed=0)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": "bench workload and partition, whole-boundary start sets, alpha 10, <= 10 rounds",
+           "ms": round(ms, 2), "rounds": tot["searches"], "gain": tot["gain"], "moves_tried": tot["tried"],
+           "moves_kept": tot["kept"], "moves_per_s": round(tot["tried"] / (ms / 1e3), 1)}
+    if cpu:
+        import oracle as O
+        wo = dict(w, part=part0.cpu().numpy())
+        t0 = time.perf_counter()
+        st, pref, tref, rref = O.kway_global(wo, alpha=10, init_mode=0, max_rounds=10, seed=0)
+        out["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+        out["parity"] = bool((tref["gain"], tref["tried"], tref["kept"], rref) ==
+                             (tot["gain"], tot["tried"], tot["kept"], tot["searches"]) and
                              np.array_equal(pref, part.cpu().numpy()))
     return out
 
@@ -897,7 +930,7 @@ def main():
     ap.add_argument("--vcycle", action=argparse.BooleanOptionalAction, default=True,
                     help="one multilevel V-, F- and W-cycle with the workload's partition, a sweep per level")
     ap.add_argument("--mt", action=argparse.BooleanOptionalAction, default=True,
-                    help="one multi-try FM pass over the first matching, against the oracle's")
+                    help="one multi-try FM pass over the first matching and the global k-way rounds, against the oracle's")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 (timing rule)")
