@@ -592,8 +592,8 @@ static fr_status batch_core(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32
     CK(cudaMemcpyAsync(A.data(), ctx->pacc, sizeof(PairAcc) * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(S.data(), ctx->sides, sizeof(SideDev) * 2 * pl.np, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<long long> qst(queued ? 4 * ctx->last_queue_clusters : 0);
-    for (int i = 0; i < (int)qst.size() / 4; ++i)
-        CK(cudaMemcpyAsync(&qst[4 * i], ctx->q_host[i].stat, 4 * sizeof(long long), cudaMemcpyDeviceToHost,
+    if (!qst.empty())
+        CK(cudaMemcpyAsync(qst.data(), ctx->q_stats, sizeof(long long) * qst.size(), cudaMemcpyDeviceToHost,
                            ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     fr_status bad = FR_OK;

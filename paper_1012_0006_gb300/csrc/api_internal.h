@@ -123,6 +123,12 @@ struct fr_ctx {
     long long q_nu = 0, q_mu = 0, q_vq = 0;
     fr::QSlot *q_slots = nullptr;              // device array [q_clusters]
     std::vector<fr::QSlot> q_host;             // the same descriptors on the host
+    // the slots' graph descriptors, control blocks and counters, each array contiguous so
+    // that a sweep sets and reads them with one copy apiece
+    fr::GraphDev *q_graphs = nullptr;
+    struct alignas(256) QCtl { fr::Ctl c; };   // one control block per 256 bytes: no line shared by two clusters
+    QCtl *q_ctls = nullptr;
+    long long *q_stats = nullptr;              // [4 q_clusters]
     int *q_ticket = nullptr, *q_gabort = nullptr, *q_prev = nullptr, *q_crank = nullptr;
     int *qb_sorted = nullptr, *qb_start = nullptr, *qb_cnt = nullptr, *qb_app = nullptr, *qb_pool = nullptr,
         *qb_lst = nullptr;

@@ -49,9 +49,7 @@ QCaps caps_for(int ctas, int n) {
 size_t slot_bytes(const QCaps &c, int ctas, int k, int reps) {
     size_t b = 0;
     auto add = [&](size_t elem, long long cnt) { b += al256(elem * (size_t)cnt); };
-    add(sizeof(GraphDev), 1);
     add(4, k);                                      // sob
-    add(sizeof(Ctl), 1);
     add(8, 3LL * 2 * kHistBins);                    // hist
     add(4, ctas + 1);                               // cta_cnt
     add(4, c.words);                                // cbits
@@ -65,7 +63,6 @@ size_t slot_bytes(const QCaps &c, int ctas, int k, int reps) {
     for (int i = 0; i < 3; ++i) add(4, (long long)reps * c.nu);   // indeg_r order hcomp
     add(8, (long long)reps * c.nu);                 // hkey
     add(8, reps); add(4, reps);                     // sw_absd sw_j
-    add(8, 4);                                      // stat
     return b;
 }
 
@@ -91,7 +88,8 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
     // per-block candidate lists: the sweep's candidates bucketed, and a region per block
     // for the commits' appends (a sweep that fills one runs again round by round)
     const long long qcap = std::max<long long>(4096, 8LL * ((nn + kk - 1) / kk));
-    size_t bytes = al256(4) + al256(4) + al256(8ull * pp) + al256(4ull * mm) + al256(sizeof(QSlot) * cc) + per * cc +
+    size_t bytes = al256(4) + al256(4) + al256(8ull * pp) + al256(4ull * mm) + al256(sizeof(QSlot) * cc) +
+                   al256(sizeof(GraphDev) * cc) + al256(sizeof(fr_ctx::QCtl) * cc) + al256(32ull * cc) + per * cc +
                    al256(4ull * nn) + al256(4ull * (kk + 1)) + 2 * al256(4ull * kk) + al256(4ull * kk * qcap) +
                    al256(4ull * nn);
     if (ctx->arena_limit && bytes + ctx->base_bytes + ctx->pair_bytes + ctx->reps_bytes > ctx->arena_limit) {
@@ -122,12 +120,15 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
     ctx->qb_pool = take<int>(p, (long long)kk * qcap);
     ctx->qb_lst = take<int>(p, nn);
     ctx->qb_cap = (int)qcap;
+    ctx->q_graphs = take<GraphDev>(p, cc);
+    ctx->q_ctls = take<fr_ctx::QCtl>(p, cc);
+    ctx->q_stats = take<long long>(p, 4LL * cc);
     ctx->q_host.assign(cc, QSlot());
     for (int i = 0; i < cc; ++i) {
         QSlot &S = ctx->q_host[i];
-        S.graph = take<GraphDev>(p, 1);
+        S.graph = ctx->q_graphs + i;
         S.sob = take<int>(p, kk);
-        S.ctl = take<Ctl>(p, 1);
+        S.ctl = &ctx->q_ctls[i].c;
         S.hist = take<long long>(p, 3LL * 2 * kHistBins);
         S.cta_cnt = take<int>(p, ctas + 1);
         S.cbits = take<unsigned int>(p, c.words);
@@ -146,7 +147,7 @@ fr_status ensure_queue(fr_ctx *ctx, int ctas, int clusters, int n, int nnz, int 
         S.hcomp = take<int>(p, (long long)rr * c.nu);
         S.hkey = take<unsigned long long>(p, (long long)rr * c.nu);
         S.sw_absd = take<long long>(p, rr); S.sw_j = take<int>(p, rr);
-        S.stat = take<long long>(p, 4);
+        S.stat = ctx->q_stats + 4LL * i;
         // idle state: no block paired, no corridor bit set
         CK(cudaMemsetAsync(S.sob, 0xFF, sizeof(int) * (size_t)kk, ctx->stream));
         CK(cudaMemsetAsync(S.cbits, 0, sizeof(unsigned int) * (size_t)c.words, ctx->stream));
@@ -183,6 +184,9 @@ void free_queue(fr_ctx *ctx) {
     ctx->q_ctas = ctx->q_clusters = ctx->q_n = ctx->q_nnz = ctx->q_k = ctx->q_reps = ctx->q_np = 0;
     ctx->q_host.clear();
     ctx->q_slots = nullptr;
+    ctx->q_graphs = nullptr;
+    ctx->q_ctls = nullptr;
+    ctx->q_stats = nullptr;
 }
 
 int queue_size_for(fr_ctx *ctx, const BatchPlan &pl, const fr_options *opt) {
@@ -243,8 +247,7 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
             last[pl.pa[j]] = last[pl.pb[j]] = j;
         }
     }
-    for (int i = 0; i < clusters; ++i)
-        CK(cudaMemcpyAsync(ctx->q_host[i].graph, &hg[i], sizeof(GraphDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->q_graphs, hg, sizeof(GraphDev) * (size_t)clusters, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->q_prev, hp, sizeof(int) * 2 * (size_t)pl.np, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->part_backup, part, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream));
 
@@ -275,10 +278,8 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
         CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc) * (size_t)pl.np, ctx->stream));
         CK(cudaMemsetAsync(ctx->q_ticket, 0, sizeof(int), ctx->stream));
         CK(cudaMemsetAsync(ctx->q_gabort, 0, sizeof(int), ctx->stream));
-        for (int i = 0; i < clusters; ++i) {
-            CK(cudaMemsetAsync(ctx->q_host[i].ctl, 0, sizeof(Ctl), ctx->stream));
-            CK(cudaMemsetAsync(ctx->q_host[i].stat, 0, 4 * sizeof(long long), ctx->stream));
-        }
+        CK(cudaMemsetAsync(ctx->q_ctls, 0, sizeof(fr_ctx::QCtl) * (size_t)clusters, ctx->stream));
+        CK(cudaMemsetAsync(ctx->q_stats, 0, 4 * sizeof(long long) * (size_t)clusters, ctx->stream));
         CK(cudaMemsetAsync(ctx->qb_lst, 0xFF, sizeof(int) * (size_t)g->n, ctx->stream));
         CK(cudaMemsetAsync(ctx->qb_cnt, 0, sizeof(int) * (size_t)pl.k, ctx->stream));
         CK(launch_qb_build(ctx->bl, ctx->blc, part, pl.k, ctx->qb_cnt, ctx->qb_start, ctx->qb_app, ctx->qb_lst,
@@ -350,11 +351,13 @@ fr_status run_queue_sweep(fr_ctx *ctx, const fr_graph *g, int32_t *part, const B
     ctx->sweep_launches = launches;
     ctx->last_launches = launches;
     int gab = 0;
-    CK(cudaMemcpy(&gab, ctx->q_gabort, sizeof(int), cudaMemcpyDeviceToHost));
-    ctls->assign(clusters, Ctl());
-    for (int i = 0; i < clusters; ++i)
-        CK(cudaMemcpyAsync(&(*ctls)[i], ctx->q_host[i].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&gab, ctx->q_gabort, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<fr_ctx::QCtl> qc(clusters);
+    CK(cudaMemcpyAsync(qc.data(), ctx->q_ctls, sizeof(fr_ctx::QCtl) * (size_t)clusters, cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctls->resize(clusters);
+    for (int i = 0; i < clusters; ++i) (*ctls)[i] = qc[i].c;
     ctx->last_queue_ctas = ctas;
     ctx->last_queue_clusters = clusters;
     if (gab != 0) {

@@ -250,9 +250,109 @@ cudaError_t launch_check_symmetric(const int *xadj, const int *adjncy, const int
     return cudaGetLastError();
 }
 
+// The same colouring for k <= kColorSmallK in one CTA's shared memory: each row of the
+// quotient bitmap lists its edges (a, b > a) in parallel and a scan over the rows gives
+// the lexicographic edge list; one thread colours the edges in that order (the greedy
+// rule is sequential) and sorts them by round, stably; the threads write the outputs.
+// Identical results to color_kernel.
+constexpr int kColorSmallK = 90;
+constexpr int kColorMaxEdges = kColorSmallK * (kColorSmallK - 1) / 2;
+constexpr int kColorWords = (2 * kColorSmallK + 31) / 32;
+
+__global__ void __launch_bounds__(256) color_small_kernel(const unsigned int *qbits, int k, int *pair_a, int *pair_b,
+                                                         int *pair_round, int *round_off, int *sob_round,
+                                                         PrepOut *out) {
+    __shared__ int s_edge[kColorMaxEdges];   // a << 16 | b, lexicographic; then in round order
+    __shared__ short s_col[kColorMaxEdges];
+    __shared__ unsigned s_used[kColorSmallK * kColorWords];
+    __shared__ int s_rowc[kColorSmallK + 1];
+    __shared__ int s_off[2 * kColorSmallK + 2];
+    __shared__ int s_np, s_nr;
+    const int t = threadIdx.x;
+    const int cw = (2 * k + 31) / 32;
+    for (int i = t; i < k * cw; i += blockDim.x) s_used[i] = 0;
+    // row a: its edges (a, b), b > a
+    for (int a2 = t; a2 < k; a2 += blockDim.x) {
+        int c = 0;
+        for (int b2 = a2 + 1; b2 < k; ++b2) {
+            const int bit = a2 * k + b2;
+            c += (qbits[bit >> 5] >> (bit & 31)) & 1u;
+        }
+        s_rowc[a2] = c;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int o = 0;
+        for (int a2 = 0; a2 < k; ++a2) {
+            const int c = s_rowc[a2];
+            s_rowc[a2] = o;
+            o += c;
+        }
+        s_rowc[k] = o;
+        s_np = o;
+    }
+    __syncthreads();
+    for (int a2 = t; a2 < k; a2 += blockDim.x) {
+        int o = s_rowc[a2];
+        for (int b2 = a2 + 1; b2 < k; ++b2) {
+            const int bit = a2 * k + b2;
+            if ((qbits[bit >> 5] >> (bit & 31)) & 1u) s_edge[o++] = (a2 << 16) | b2;
+        }
+    }
+    __syncthreads();
+    const int np = s_np;
+    if (t == 0) {
+        // greedy: the smallest colour free at both ends
+        int nr = 0;
+        for (int e = 0; e < np; ++e) {
+            const int a2 = s_edge[e] >> 16, b2 = s_edge[e] & 0xFFFF;
+            int c = 0;
+            for (int wi = 0; wi < cw; ++wi) {
+                const unsigned freebits = ~(s_used[a2 * cw + wi] | s_used[b2 * cw + wi]);
+                if (freebits) { c = wi * 32 + __ffs(freebits) - 1; break; }
+            }
+            s_used[a2 * cw + (c >> 5)] |= 1u << (c & 31);
+            s_used[b2 * cw + (c >> 5)] |= 1u << (c & 31);
+            s_col[e] = (short)c;
+            if (c + 1 > nr) nr = c + 1;
+        }
+        s_nr = nr;
+        // round offsets (stable counting sort by round keeps the lexicographic order)
+        for (int r = 0; r <= nr; ++r) s_off[r] = 0;
+        for (int e = 0; e < np; ++e) s_off[s_col[e] + 1]++;
+        for (int r = 0; r < nr; ++r) s_off[r + 1] += s_off[r];
+    }
+    __syncthreads();
+    const int nr = s_nr;
+    for (int r = t; r <= nr; r += blockDim.x) round_off[r] = s_off[r];
+    for (long long i = t; i < (long long)nr * k; i += blockDim.x) sob_round[i] = -1;
+    __syncthreads();
+    // positions: round offset + rank among the earlier edges of the same round, one
+    // thread per edge (np <= 4005: a quadratic count is cheap here)
+    for (int e = t; e < np; e += blockDim.x) {
+        const int c = s_col[e];
+        int rk = 0;
+        for (int q = 0; q < e; ++q) rk += s_col[q] == c;
+        const int pos = s_off[c] + rk;
+        const int a2 = s_edge[e] >> 16, b2 = s_edge[e] & 0xFFFF;
+        pair_a[pos] = a2;
+        pair_b[pos] = b2;
+        pair_round[pos] = c;
+        sob_round[(long long)c * k + a2] = 2 * rk;
+        sob_round[(long long)c * k + b2] = 2 * rk + 1;
+    }
+    if (t == 0) {
+        out->npairs = np;
+        out->nrounds = nr;
+    }
+}
+
 cudaError_t launch_color(const unsigned int *qbits, int k, int *pair_a, int *pair_b, int *pair_round,
                          int *round_off, int *sob_round, unsigned int *used, PrepOut *out, cudaStream_t st) {
-    color_kernel<<<1, 32, 0, st>>>(qbits, k, pair_a, pair_b, pair_round, round_off, sob_round, used, out);
+    if (k <= kColorSmallK)
+        color_small_kernel<<<1, 256, 0, st>>>(qbits, k, pair_a, pair_b, pair_round, round_off, sob_round, out);
+    else
+        color_kernel<<<1, 32, 0, st>>>(qbits, k, pair_a, pair_b, pair_round, round_off, sob_round, used, out);
     return cudaGetLastError();
 }
 

@@ -232,13 +232,23 @@ size_t queue_smem() { return g_queue_dyn_smem > 0 ? (size_t)g_queue_dyn_smem : 0
 // The sweep's boundary candidates bucketed by block (counting sort; order inside a
 // block does not matter): counts, offsets, placement; every listed vertex records its
 // block in lst (the others hold -1, set by the host).
-__global__ void qb_count_kernel(const int *bl, const int *blc, const int *part, int *cnt, int *lst) {
+// Per-CTA block histograms in shared memory (k <= 1024), then one global addition per
+// (CTA, block): the candidates of a k-way partition hit k counters, and global atomics
+// on so few addresses serialise.
+__global__ void __launch_bounds__(256) qb_count_kernel(const int *bl, const int *blc, const int *part, int k,
+                                                       int *cnt, int *lst) {
+    __shared__ int h[1024];
+    for (int x = threadIdx.x; x < k; x += blockDim.x) h[x] = 0;
+    __syncthreads();
     const int m = *blc;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int v = bl[i], x = part[v];
-        atomicAdd(cnt + x, 1);
+        atomicAdd(h + x, 1);
         lst[v] = x;
     }
+    __syncthreads();
+    for (int x = threadIdx.x; x < k; x += blockDim.x)
+        if (h[x]) atomicAdd(cnt + x, h[x]);
 }
 
 __global__ void qb_offsets_kernel(int *cnt, int *start, int *app, int k) {
@@ -263,12 +273,25 @@ __global__ void qb_offsets_kernel(int *cnt, int *start, int *app, int k) {
     if (t == 0) start[k] = s[1023];
 }
 
-__global__ void qb_place_kernel(const int *bl, const int *blc, const int *part, int *fill, const int *start,
-                                int *sorted) {
+// Each CTA places one contiguous chunk of the list: it counts its chunk per block in
+// shared memory, reserves a range of each block's bucket with one global addition, and
+// places the entries with shared-memory offsets.  (The order inside a bucket is free:
+// the pairs' boundary scans do not depend on it.)
+__global__ void __launch_bounds__(256) qb_place_kernel(const int *bl, const int *blc, const int *part, int k,
+                                                       int *fill, const int *start, int *sorted) {
+    __shared__ int h[1024];
     const int m = *blc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const int v = bl[i], x = part[v];
-        sorted[start[x] + atomicAdd(fill + x, 1)] = v;
+    const long long per = ((long long)m + gridDim.x - 1) / gridDim.x;
+    const long long c0 = per * blockIdx.x, c1 = min((long long)m, c0 + per);
+    for (int x = threadIdx.x; x < k; x += blockDim.x) h[x] = 0;
+    __syncthreads();
+    for (long long i = c0 + threadIdx.x; i < c1; i += blockDim.x) atomicAdd(h + part[bl[i]], 1);
+    __syncthreads();
+    for (int x = threadIdx.x; x < k; x += blockDim.x) h[x] = h[x] ? start[x] + atomicAdd(fill + x, h[x]) : 0;
+    __syncthreads();
+    for (long long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const int v = bl[i];
+        sorted[atomicAdd(h + part[v], 1)] = v;
     }
 }
 
@@ -278,9 +301,9 @@ cudaError_t launch_qb_build(const int *bl, const int *blc, const int *part, int 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (k > 1024) return cudaErrorInvalidValue;
-    qb_count_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, part, cnt, lst);
+    qb_count_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, part, k, cnt, lst);
     qb_offsets_kernel<<<1, 1024, 0, st>>>(cnt, start, app, k);
-    qb_place_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, part, cnt, start, sorted);
+    qb_place_kernel<<<nsm * 4, 256, 0, st>>>(bl, blc, part, k, cnt, start, sorted);
     return cudaGetLastError();
 }
 
