@@ -317,6 +317,33 @@ def test_rounds_parity(F, ctx):
         assert list(pr) == sorted(pr)
 
 
+@pytest.mark.parametrize("k,dense", [(2, False), (31, False), (64, True), (89, True), (90, True), (91, True),
+                                     (130, False), (130, True)])
+def test_rounds_parity_many_blocks(F, ctx, k, dense):
+    # the colouring runs in one CTA's shared memory up to k = 90 and on one thread
+    # beyond; dense: a random partition, so that every pair of blocks is adjacent
+    # (k (k - 1) / 2 pairs, up to 2k - 1 colours)
+    xadj, adj, coords = I.rgg(2, 20000, I.rgg_radius(2, 20000, 10.0), 77 + k)
+    n = len(xadj) - 1
+    vwgt = np.ones(n, np.int32)
+    if dense:
+        part = np.random.Generator(np.random.Philox(k)).integers(0, k, n).astype(np.int32)
+    else:
+        part = I.rcb(coords, vwgt, k)
+    w = dict(name=f"rgg2d k={k}", n=n, nnz=len(adj), xadj=xadj, adjncy=adj, adjwgt=np.ones(len(adj), np.int32),
+             vwgt=vwgt, part=part, k=k, eps=0.03)
+    g, dpart = _dev(F, w)
+    pa, pb, pr, nr = ctx.rounds(g, dpart, k)
+    oa, ob, orr, onr = O.rounds(w)
+    got = sorted(zip(pa.tolist(), pb.tolist(), pr.tolist()))
+    exp = sorted(zip(oa.tolist(), ob.tolist(), orr.tolist()))
+    assert got == exp and nr == onr
+    assert list(pr) == sorted(pr)
+    # inside a round the pairs keep their lexicographic order
+    rows = list(zip(pr.tolist(), pa.tolist(), pb.tolist()))
+    assert rows == sorted(rows)
+
+
 def test_launch_shapes_give_identical_partitions(F, ctx):
     """Races would show as shape-dependent results: grid, block size, relabel interval, ops per pulse."""
     w = I.config(4, scale=1 / 128)
