@@ -418,6 +418,7 @@ def run_ours(args, world, rank, local, pg):
     mtp = multitry_pass(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
     kwr = kway_rounds(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
     vc = multilevel(F, ctx, g, part0, w) if args.vcycle else None
+    nxt = next_rows(F, dev, cpu=not args.no_cpu) if args.next_rows else None
 
     serving = None
     if args.serve:
@@ -448,7 +449,7 @@ def run_ours(args, world, rank, local, pg):
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare, "phase_rates": rates,
-            "active_blocks": active, "fm": fm, "multitry": mtp, "kway_rounds": kwr, "vcycle": vc,
+            "active_blocks": active, "fm": fm, "multitry": mtp, "kway_rounds": kwr, "next_rows_vs_oracle": nxt, "vcycle": vc,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -506,6 +507,74 @@ def multitry_pass(F, ctx, g, part0, w, alpha=10, reps=2, cpu=True):
         out["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
         out["parity"] = bool(tref == {f: tot[f] for f in ("gain", "searches", "tried", "kept")} and
                              np.array_equal(pref, part.cpu().numpy()))
+    return out
+
+
+def next_rows(F, dev, cpu=True):
+    """The rows next to the path on the bench workload at 1/16 scale (rgg3d n = 262,144,
+    k = 64), each against the oracle on the same input: one sweep with the FM step
+    before every pair's flow (fm_permille 10), active block scheduling with adaptive
+    flow iterations (alpha 1 -> 16) and with a multi-try pass after every matching
+    (mt_alpha 10, four outer rounds), and one V-cycle.  Device time: CUDA events around
+    the call, one run after a warm one; oracle: one run, one thread; parity: identical
+    partitions and totals."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1012_0006_gb300 import inputs as I
+    w = I.config(4, scale=1 / 16)
+    k, eps = w["k"], w["eps"]
+    g = F.DeviceGraph.from_workload(w, device=dev)
+    part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
+    ctx = F.Context(dev.index if dev.index is not None else 0)
+    out = {"workload": f"rgg3d n={w['n']} k={k} eps={eps} (the bench workload at 1/16 scale)"}
+
+    def timed(fn):
+        part = part0.clone()
+        fn(part)
+        part.copy_(part0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn(part)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r, part.cpu().numpy()
+
+    def host(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return (time.perf_counter() - t0) * 1e3, r
+
+    # FM step then flow, one sweep
+    fo = dict(mb=1, fm_permille=10)
+    ms, (st, _, summ), got = timed(lambda p: ctx.refine_batch(g, p, k, eps, w["alpha"], F.default_options(**fo),
+                                                              results=False))
+    e = {"ms": round(ms, 2), "pairs": summ["npairs"], "cut_before": summ["cut_before"], "cut_after": summ["cut_after"]}
+    if cpu:
+        oms, (ost, pref, rref, nr) = host(lambda: O.refine_batch(w, opts=O.options(**fo)))
+        e.update(oracle_ms=round(oms, 1), parity=bool(ost == 0 and np.array_equal(pref, got) and nr == summ["nrounds"]))
+    out["fm_sweep"] = e
+    # active block scheduling, adaptive iterations; and with multi-try passes
+    for name, ao, mo in (("active_adaptive", dict(mb=1, adaptive=1, max_iters=10, alpha_max=16.0), 16),
+                         ("active_multitry", dict(mb=1, mt_alpha=10), 4)):
+        ms, (st, res, summ, nouter), got = timed(
+            lambda p: ctx.refine_active(g, p, k, eps, 1.0, F.default_options(**ao), max_outer=mo))
+        e = {"ms": round(ms, 2), "outer_rounds": nouter, "refinements": len(res), "cut_before": summ["cut_before"],
+             "cut_after": summ["cut_after"]}
+        if cpu:
+            oms, (ost, pref, rref, onr) = host(lambda: O.refine_active(w, alpha=1.0, opts=O.options(**ao), max_outer=mo))
+            e.update(oracle_ms=round(oms, 1),
+                     parity=bool(ost == 0 and np.array_equal(pref, got) and onr == nouter and len(rref) == len(res)))
+        out[name] = e
+    # one V-cycle
+    ms, (st, r), got = timed(lambda p: ctx.vcycle(g, p, k, eps, w["alpha"], F.default_options(mb=1)))
+    e = {"ms": round(ms, 2), "levels": r["levels"], "cut_before": r["cut_before"], "cut_after": r["cut_after"]}
+    if cpu:
+        oms, (ost, pref, rr) = host(lambda: O.vcycle(w, opts=O.options(mb=1)))
+        e.update(oracle_ms=round(oms, 1),
+                 parity=bool(ost == 0 and np.array_equal(pref, got) and rr["level_n"] == r["level_n"]))
+    out["vcycle"] = e
+    ctx.close()
     return out
 
 
@@ -929,6 +998,8 @@ def main():
                     help="sweeps with the two-way FM step before each flow (1 %% and 5 %% stopping rules)")
     ap.add_argument("--vcycle", action=argparse.BooleanOptionalAction, default=True,
                     help="one multilevel V-, F- and W-cycle with the workload's partition, a sweep per level")
+    ap.add_argument("--next-rows", action=argparse.BooleanOptionalAction, default=True,
+                    help="FM sweep, active scheduling and a V-cycle at 1/16 scale, each against the oracle")
     ap.add_argument("--mt", action=argparse.BooleanOptionalAction, default=True,
                     help="one multi-try FM pass over the first matching and the global k-way rounds, against the oracle's")
     args = ap.parse_args()
