@@ -419,6 +419,7 @@ def run_ours(args, world, rank, local, pg):
     kwr = kway_rounds(F, ctx, g, part0, w, cpu=not args.no_cpu) if args.mt else None
     vc = multilevel(F, ctx, g, part0, w) if args.vcycle else None
     nxt = next_rows(F, dev, cpu=not args.no_cpu) if args.next_rows else None
+    spc = single_pair_configs(F, dev, cpu=not args.no_cpu) if args.next_rows else None
 
     serving = None
     if args.serve:
@@ -449,7 +450,7 @@ def run_ours(args, world, rank, local, pg):
             "corridor_arcs_per_sec_through_maxflow": round(arcs_rate, 1),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "cpu_baseline_pair_parallel": cpu_mt, "clocks": clk, "serving": serving, "batched_vs_per_pair": compare, "phase_rates": rates,
-            "active_blocks": active, "fm": fm, "multitry": mtp, "kway_rounds": kwr, "next_rows_vs_oracle": nxt, "vcycle": vc,
+            "active_blocks": active, "fm": fm, "multitry": mtp, "kway_rounds": kwr, "next_rows_vs_oracle": nxt, "single_pair_configs": spc, "vcycle": vc,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -507,6 +508,53 @@ def multitry_pass(F, ctx, g, part0, w, alpha=10, reps=2, cpu=True):
         out["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
         out["parity"] = bool(tref == {f: tot[f] for f in ("gain", "searches", "tried", "kept")} and
                              np.array_equal(pref, part.cpu().numpy()))
+    return out
+
+
+def single_pair_configs(F, dev, cpu=True, reps=3):
+    """The two single-pair configurations as they are defined: the 64 x 64 grid bisection
+    (one plain flow refinement, alpha 1) and the rgg2d n = 65,536 bisection with adaptive
+    flow iterations (alpha 1, 2, 4, ... up to 16, at most ten iterations), one pair per
+    launch through fr_refine_pair.  Device: CUDA events around the call, min of reps
+    after a warm run; oracle: one run, one thread; parity: identical partitions, flow,
+    cuts and iterations."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1012_0006_gb300 import inputs as I
+    ctx = F.Context(dev.index if dev.index is not None else 0)
+    out = {}
+    for name, cfg in (("grid2d 64x64 k=2 alpha=1, one refinement", 1),
+                      ("rgg2d n=65536 k=2, adaptive alpha 1 -> 16", 2)):
+        w = I.config(cfg)
+        ok = dict(mb=int(w["mb"]), adaptive=int(w["adaptive"]), max_iters=int(w["max_iters"]),
+                  alpha_max=float(w["alpha_max"]))
+        g = F.DeviceGraph.from_workload(w, device=dev)
+        part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
+        part = part0.clone()
+        ctx.refine_pair(g, part, w["k"], 0, 1, w["eps"], w["alpha"], F.default_options(**ok))   # warm
+        best, res = None, None
+        for _ in range(reps):
+            part.copy_(part0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st, res = ctx.refine_pair(g, part, w["k"], 0, 1, w["eps"], w["alpha"], F.default_options(**ok))
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        e = {"ms": round(best, 3), "refinements_per_s": round(1e3 / best, 1), "flow": res.flow,
+             "cut_before": res.cut_before, "cut_after": res.cut_after, "iters": res.iters,
+             "alpha_final": res.alpha_final, "corridor_n": res.corridor_n}
+        if cpu:
+            t0 = time.perf_counter()
+            ost, pref, rref = O.refine_pair(w, opts=O.options(**ok))
+            e["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+            e["parity"] = bool(ost == 0 and np.array_equal(pref, part.cpu().numpy()) and
+                               (rref.flow, rref.cut_before, rref.cut_after, rref.iters) ==
+                               (res.flow, res.cut_before, res.cut_after, res.iters))
+        out[name] = e
+    ctx.close()
     return out
 
 
@@ -999,7 +1047,8 @@ def main():
     ap.add_argument("--vcycle", action=argparse.BooleanOptionalAction, default=True,
                     help="one multilevel V-, F- and W-cycle with the workload's partition, a sweep per level")
     ap.add_argument("--next-rows", action=argparse.BooleanOptionalAction, default=True,
-                    help="FM sweep, active scheduling and a V-cycle at 1/16 scale, each against the oracle")
+                    help="FM sweep, active scheduling and a V-cycle at 1/16 scale, and the two single-pair "
+                         "configurations, each against the oracle")
     ap.add_argument("--mt", action=argparse.BooleanOptionalAction, default=True,
                     help="one multi-try FM pass over the first matching and the global k-way rounds, against the oracle's")
     args = ap.parse_args()
