@@ -515,9 +515,10 @@ def single_pair_configs(F, dev, cpu=True, reps=3):
     """The two single-pair configurations as they are defined: the 64 x 64 grid bisection
     (one plain flow refinement, alpha 1) and the rgg2d n = 65,536 bisection with adaptive
     flow iterations (alpha 1, 2, 4, ... up to 16, at most ten iterations), one pair per
-    launch through fr_refine_pair.  Device: CUDA events around the call, min of reps
-    after a warm run; oracle: one run, one thread; parity: identical partitions, flow,
-    cuts and iterations."""
+    launch through fr_refine_pair; then the rgg2d bisection at fixed alpha 1, 2, 4, 8, 16,
+    plain and most balanced, with the corridor and the max flow's share of the time.
+    Device: CUDA events around the call, min of reps after a warm run; oracle: one run,
+    one thread; parity: identical partitions, flow, cuts and iterations."""
     import numpy as np
     import torch
     import oracle as O
@@ -554,6 +555,50 @@ def single_pair_configs(F, dev, cpu=True, reps=3):
                                (rref.flow, rref.cut_before, rref.cut_after, rref.iters) ==
                                (res.flow, res.cut_before, res.cut_after, res.iters))
         out[name] = e
+    # the rgg2d bisection at fixed alpha (one refinement each, plain and most balanced):
+    # corridor size and the max flow's share, through fr_refine_batch's phase timers
+    # (k = 2: one pair, one round)
+    w = I.config(2)
+    g = F.DeviceGraph.from_workload(w, device=dev)
+    part0 = torch.as_tensor(np.array(w["part"], np.int32)).to(dev)
+    sweep = []
+    for mb in (0, 1):
+        for alpha in (1.0, 2.0, 4.0, 8.0, 16.0):
+            opts = F.default_options(mb=mb)
+            part = part0.clone()
+            ctx2 = F.Context(dev.index if dev.index is not None else 0)
+            ctx2.refine_batch(g, part, 2, w["eps"], alpha, opts, results=False)   # warm
+            best = None
+            for _ in range(reps):
+                part.copy_(part0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _, res, summ = ctx2.refine_batch(g, part, 2, w["eps"], alpha, opts)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            got = part.cpu().numpy()
+            ctx2.set_profiling(True)
+            part.copy_(part0)
+            ctx2.refine_batch(g, part, 2, w["eps"], alpha, opts, results=False)
+            P = ctx2.profile()
+            ctx2.close()
+            ph, cp = P["phase_ms"], P["cluster_phase_ms"]
+            flow_ms = ph["flow"] + ph["relabel"] + ph["return"] + cp["load"] + cp["flow"] + cp["return"]
+            r = res[0]
+            e = {"mb": mb, "alpha": alpha, "ms": round(best, 3), "corridor_n": r["corridor_n"],
+                 "corridor_arcs": r["corridor_arcs"], "flow": r["flow"], "cut_after": r["cut_after"],
+                 "max_flow_ms": round(flow_ms, 3),
+                 "corridor_arcs_per_s_through_max_flow": round(r["corridor_arcs"] / max(flow_ms * 1e-3, 1e-12), 1)}
+            if cpu:
+                t0 = time.perf_counter()
+                ost, pref, rref = O.refine_pair(w, alpha=alpha, opts=O.options(mb=mb))
+                e["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+                e["parity"] = bool(ost == 0 and np.array_equal(pref, got) and rref.flow == r["flow"] and
+                                   rref.cut_after == r["cut_after"])
+            sweep.append(e)
+    out["rgg2d n=65536 k=2, fixed alpha, one refinement"] = sweep
     ctx.close()
     return out
 
