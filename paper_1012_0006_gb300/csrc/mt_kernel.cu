@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kMtTPB) kw_gain_kernel(GraphDev G, MtDev m, Ct
 }
 
 // The round's search: one warp queues the start set in its order and searches.
-// res: gain kept, tried, kept; pad = 1 if the KaSPar rule stopped the search.
+// res: gain kept, tried, kept; stopped = 1 if the KaSPar rule stopped the search.
 __global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, Ctl *ctl) {
     __shared__ MtShared S;
     const int lane = threadIdx.x;
@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, C
         m.res->searches = 1;
         m.res->tried = nm;
         m.res->kept = best_len;
-        m.res->pad = stopped ? 1 : 0;
+        m.res->stopped = stopped ? 1 : 0;
     }
 }
 

@@ -16,7 +16,7 @@ constexpr int kMtMaxK = 1024;                 // block weights cached in shared 
 struct MtRes {
     long long gain;          // cut decrease kept
     int searches, tried, kept;
-    int pad;
+    int stopped;             // global k-way round: 1 if the KaSPar rule stopped its search
 };
 
 // Device state of a multi-try pass over the pairs of one matching of one graph.
@@ -55,7 +55,7 @@ cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cud
 // Section 6): one k-way search from every vertex with at least `need` (1 or 2) blocks
 // other than its own around it, in ascending splitmix64(rs ^ v) order; target ties
 // use splitmix64(~md.seed).  Updates part and md.bw (recomputed as the round starts);
-// md.res receives the round's gain, moves tried and kept, and (pad) whether the KaSPar
+// md.res receives the round's gain, moves tried and kept, and (stopped) whether the KaSPar
 // rule stopped it.  G.bl must be null.  *nl += kernels launched.
 cudaError_t launch_kway_round(const GraphDev &G, const MtDev &md, Ctl *ctl, int need, unsigned long long rs,
                               int sms, cudaStream_t st, int *nl);
