@@ -608,7 +608,8 @@ def next_rows(F, dev, cpu=True):
     k = 64), each against the oracle on the same input: one sweep with the FM step
     before every pair's flow (fm_permille 10), active block scheduling with adaptive
     flow iterations (alpha 1 -> 16) and with a multi-try pass after every matching
-    (mt_alpha 10, four outer rounds), and one V-cycle.  Device time: CUDA events around
+    (mt_alpha 10, four outer rounds), one V-cycle, and (at 1/64 scale) a W- and an
+    F-cycle with level split parameter 2.  Device time: CUDA events around
     the call, one run after a warm one; oracle: one run, one thread; parity: identical
     partitions and totals."""
     import numpy as np
@@ -667,6 +668,28 @@ def next_rows(F, dev, cpu=True):
         e.update(oracle_ms=round(oms, 1),
                  parity=bool(ost == 0 and np.array_equal(pref, got) and rr["level_n"] == r["level_n"]))
     out["vcycle"] = e
+    # W- and F-cycles (level split parameter 2) on the bench workload at 1/64 scale
+    w2 = I.config(4, scale=1 / 64)
+    g2 = F.DeviceGraph.from_workload(w2, device=dev)
+    p2 = torch.as_tensor(np.array(w2["part"], np.int32)).to(dev)
+    for kind in ("F", "W"):
+        part = p2.clone()
+        ctx.cycle(g2, part, w2["k"], w2["eps"], w2["alpha"], kind=kind, d=2, opts=F.default_options(mb=1))   # warm
+        part.copy_(p2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, c = ctx.cycle(g2, part, w2["k"], w2["eps"], w2["alpha"], kind=kind, d=2, opts=F.default_options(mb=1))
+        e1.record()
+        torch.cuda.synchronize()
+        e = {"workload": f"rgg3d n={w2['n']} k={w2['k']} (1/64 scale)", "ms": round(e0.elapsed_time(e1), 2),
+             "coarsenings": c["coarsenings"], "refinements": c["refinements"], "cut_before": c["cut_before"],
+             "cut_after": c["cut_after"]}
+        if cpu:
+            oms, (ost, pref, rc) = host(lambda: O.cycle(w2, kind=kind, d=2, opts=O.options(mb=1)))
+            e.update(oracle_ms=round(oms, 1),
+                     parity=bool(ost == 0 and np.array_equal(pref, part.cpu().numpy()) and
+                                 rc["coarsenings"] == c["coarsenings"] and rc["refinements"] == c["refinements"]))
+        out[kind + "_cycle"] = e
     ctx.close()
     return out
 
