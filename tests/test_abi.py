@@ -76,3 +76,24 @@ def test_struct_layouts_match_the_header(built):
     for i, st in enumerate(structs):
         assert F.lib().fr_struct_size(i) == ctypes.sizeof(st), st.__name__
     assert F.lib().fr_struct_size(len(structs)) == -1
+
+
+def declared_arities():
+    """Parameter count of every function declaration in the header."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(fr_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        name, params = m.group(1), m.group(2).strip()
+        if name.endswith("_t"):
+            continue
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(built):
+    arities = declared_arities()
+    assert len(arities) >= 20
+    wrong = {name: (n, len(built.SYMBOLS[name][1])) for name, n in arities.items()
+             if name in built.SYMBOLS and len(built.SYMBOLS[name][1]) != n}
+    assert not wrong, wrong
