@@ -24,10 +24,11 @@
 // pass (all lanes in lockstep; lane 0 pops and moves, the lanes key the moved
 // vertex's neighbours 32 at a time, each lane computing its neighbour's connection
 // weights from the adjacency in registers).  The queue is an array of gain buckets,
-// each a stack of (vertex, version) entries in global memory with its top and a
-// non-empty bitmap in shared memory: keying pushes an entry with the vertex's next
-// version (so each stack stays ordered by keying time) and makes the old one stale;
-// pops skip stale entries.  The block weights live in shared memory for the pass.
+// each a stack of entries in global memory with its top and a non-empty bitmap in
+// shared memory; an entry carries what the move needs (vertex, target, block, weight,
+// adjacency range) and a live flag: keying pushes a new entry (so each stack stays
+// ordered by keying time) and clears the flag of the vertex's previous entry of the same
+// search; pops skip dead entries.  The block weights live in shared memory for the pass.
 // Grid-wide kernels before it count the pair boundaries and block weights, fill the
 // todo lists and sort each (one CTA per pair, bitonic by key).
 //
