@@ -627,9 +627,9 @@ fr_status setup_single(fr_ctx *ctx, const fr_graph *g, int32_t *part, int32_t k,
     CK(cudaMemsetAsync(ctx->sides, 0, 2 * sizeof(SideDev), ctx->stream));
     CK(cudaMemsetAsync(ctx->pacc, 0, sizeof(PairAcc), ctx->stream));
     CK(cudaMemsetAsync(ctx->hist, 0, sizeof(long long) * 3 * 2 * kHistBins, ctx->stream));
-    // cudaMemcpyAsync from pageable staging would be synchronous; h_stage is pinned, so keep it
-    // alive until the copies ran
-    CK(cudaStreamSynchronize(ctx->stream));
+    // h_stage is pinned, so the copies run asynchronously: its bytes [1024, 1544) must stay
+    // as written until they ran.  Every caller synchronises the stream (reading its results
+    // back) before anything writes there again, so no synchronisation is needed here.
     return FR_OK;
 }
 
