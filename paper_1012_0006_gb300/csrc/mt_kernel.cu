@@ -423,8 +423,7 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
             S.bw[from] -= cx;
             S.bw[to] += cx;
             m.mvd[x] = 1;
-            m.lv[nm] = x;
-            m.lfrom[nm] = from;
+            m.lmv[nm] = make_int4(x, from, to, (int)cx);
         }
         ++nm;
         delta -= g;
@@ -478,61 +477,27 @@ __device__ __forceinline__ void mt_search(const GraphDev &G, const MtDev &m, MtS
 }
 
 // After a search: roll back to the first lowest cut and clear the moved marks.  With
-// bookkeeping (the multi-try pass), for the kept moves mark the blocks they left and
-// entered and list the boundary candidates (the moved vertex and its neighbours outside
-// its new block, as a flow's commit does): the kept moves 32 at a time, then one move
-// at a time with the lanes on its arcs; bln counts the list (this warp alone appends
-// to it while the pass runs).
+// bookkeeping (the multi-try pass), mark the blocks the kept moves left and entered and
+// list the kept movers (kbase: the pass's count so far) for the boundary list, which
+// mt_bl_kernel fills after the pass.
 __device__ __forceinline__ void mt_finish(const GraphDev &G, const MtDev &m, MtShared &S, int nm, int best_len,
-                                          int lane, bool keep, int &bln) {
+                                          int lane, bool keep, int &kbase) {
     for (int i = best_len + lane; i < nm; i += 32) {
-        const int y = m.lv[i], f0 = m.lfrom[i], t = G.part[y];
-        const long long cy = __ldg(G.vwgt + y);
-        G.part[y] = f0;
-        atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[t]), (unsigned long long)(-cy));
-        atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[f0]), (unsigned long long)cy);
+        const int4 mv = m.lmv[i];
+        G.part[mv.x] = mv.y;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[mv.z]), (unsigned long long)(-(long long)mv.w));
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S.bw[mv.y]), (unsigned long long)(long long)mv.w);
     }
     __syncwarp();
-    for (int i = lane; i < nm; i += 32) m.mvd[m.lv[i]] = 0;
-    if (!keep) {
-        __syncwarp();
-        return;
-    }
-    for (int ib = 0; ib < best_len; ib += 32) {
-        const int i = ib + lane;
-        int y = -1, t = 0, a0 = 0, a1 = 0;
-        if (i < best_len) {
-            y = m.lv[i];
-            const int f = m.lfrom[i];
-            t = G.part[y];
-            a0 = __ldg(G.xadj + y);
-            a1 = __ldg(G.xadj + y + 1);
-            m.chg[f] = 1;
-            m.chg[t] = 1;
+    for (int i = lane; i < nm; i += 32) m.mvd[m.lmv[i].x] = 0;
+    if (keep) {
+        for (int i = lane; i < best_len; i += 32) {
+            const int4 mv = m.lmv[i];
+            m.chg[mv.y] = 1;
+            m.chg[mv.z] = 1;
+            m.kept[kbase + i] = mv.x;
         }
-        if (!G.bl) continue;
-        const int cnt = min(32, best_len - ib);
-        for (int c = 0; c < cnt; ++c) {
-            const int yc = __shfl_sync(kFull, y, c), tc = __shfl_sync(kFull, t, c);
-            const int c0 = __shfl_sync(kFull, a0, c), c1 = __shfl_sync(kFull, a1, c);
-            // slot c0 - 1 stands for the moved vertex itself
-            for (int qb = c0 - 1; qb < c1; qb += 32) {
-                const int q = qb + lane;
-                int z = -1;
-                bool app = false;
-                if (q < c1) {
-                    z = q < c0 ? yc : __ldg(G.adjncy + q);
-                    app = !__ldcg(G.inb + z) && (q < c0 || G.part[z] != tc);
-                }
-                const unsigned am = __ballot_sync(kFull, app);
-                if (app) {
-                    G.inb[z] = 1;
-                    G.bl[bln + __popc(am & mt_lanemask_lt())] = z;
-                }
-                bln += __popc(am);
-                __syncwarp();
-            }
-        }
+        kbase += best_len;
     }
     __syncwarp();
 }
@@ -567,7 +532,7 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
     long long gain_tot = 0;
     int searches = 0, tried_tot = 0, kept_tot = 0, sid = 0;
     unsigned epoch = *m.epoch;
-    int bln = G.bl ? *G.blc : 0;
+    int kbase = 0;   // kept movers listed so far (the list is kept_tot long at the end)
     bool bad = false;
     __syncwarp();
     // the todo entries in pass order (entry j of every pair, then j + 1), 32 at a time:
@@ -636,7 +601,7 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
             int nm, best_len;
             bool stopped;
             mt_search(G, m, S, ctl, sid, true, epoch, nxt, Lmax, tseed, lane, bad, best, nm, best_len, stopped);
-            mt_finish(G, m, S, nm, best_len, lane, true, bln);
+            mt_finish(G, m, S, nm, best_len, lane, true, kbase);
             gain_tot -= best;
             tried_tot += nm;
             kept_tot += best_len;
@@ -650,11 +615,31 @@ __global__ void __launch_bounds__(32, 1) mt_pass_kernel(GraphDev G, MtDev m, Ctl
     }
     if (lane == 0) {
         *m.epoch = epoch;
-        if (G.bl) *G.blc = bln;
         m.res->gain = gain_tot;
         m.res->searches = searches;
         m.res->tried = tried_tot;
         m.res->kept = kept_tot;
+    }
+}
+
+// The boundary candidates of the pass's kept moves, as a flow's commit lists them: each
+// mover and its neighbours outside its block (one warp per mover).  Taken on the
+// partition the pass leaves: a vertex that is a boundary vertex after the pass is a
+// mover, a neighbour of one in another block, or was one before the pass (and listed).
+__global__ void __launch_bounds__(kMtTPB) mt_bl_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    if (__ldcg(&ctl->error)) return;
+    const int nk = m.res->kept;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nk; i += nw) {
+        const int y = m.kept[i], t = G.part[y];
+        const int a0 = __ldg(G.xadj + y), a1 = __ldg(G.xadj + y + 1);
+        // slot a0 - 1 stands for the mover itself
+        for (int q = a0 - 1 + lane; q < a1; q += 32) {
+            const int z = q < a0 ? y : __ldg(G.adjncy + q);
+            if ((q < a0 || G.part[z] != t) && !__ldcg(G.inb + z) && atomicExch(G.inb + z, 1) == 0)
+                G.bl[atomicAdd(G.blc, 1)] = z;
+        }
     }
 }
 
@@ -673,6 +658,10 @@ cudaError_t launch_mt(const GraphDev &G, const MtDev &md, Ctl *ctl, int sms, cud
     mt_sort_kernel<<<md.np, kMtTPB, 0, st>>>(md, ctl);
     mt_pass_kernel<<<1, 32, 0, st>>>(G, md, ctl);
     *nl += 5;
+    if (G.bl) {
+        mt_bl_kernel<<<grid, kMtTPB, 0, st>>>(G, md, ctl);
+        *nl += 1;
+    }
     return cudaGetLastError();
 }
 
@@ -846,10 +835,10 @@ __global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, C
         nxt += __popc(pm);
     }
     long long best = 0;
-    int nm = 0, best_len = 0, bln = 0;
+    int nm = 0, best_len = 0, kbase = 0;
     bool stopped = false;
     if (!bad) mt_search(G, m, S, ctl, 0, false, epoch, nxt, G.Lmax, tseed, lane, bad, best, nm, best_len, stopped);
-    mt_finish(G, m, S, nm, best_len, lane, false, bln);
+    mt_finish(G, m, S, nm, best_len, lane, false, kbase);
     for (int i = lane; i < G.k; i += 32) m.bw[i] = S.bw[i];
     if (lane == 0) {
         *m.epoch = epoch;

@@ -27,7 +27,8 @@ struct MtDev {
     unsigned long long *cur;     // [n] epoch << 32 | the vertex's latest entry in that search
     unsigned *epoch;             // [1] epoch of the last search run (searches number 1, 2, ...)
     unsigned char *mvd;          // [n] moved by the current search
-    int *lv, *lfrom;             // [n] moves of the current search: vertex, source block
+    int4 *lmv;                   // [n] moves of the current search: {vertex, source, target, weight}
+    int *kept;                   // [n] the pass's kept movers (a vertex moves at most once in a pass)
     int4 *ent;                   // [2 ecap] bucket stack entries of the current search:
                                  //   {vertex, entry below, live, target}, {block, weight, adjacency range}
     int *bpair;                  // [k] pair of the pass that the block belongs to, -1 none
