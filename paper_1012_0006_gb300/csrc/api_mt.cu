@@ -45,6 +45,8 @@ fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P) {
     auto add = [&](size_t elem, long long cnt) { b += ((elem * (size_t)cnt + 255) / 256) * 256; };
     add(4, nn); add(8, nn); add(4, 1); add(1, nn);      // tch cur epoch mvd
     add(16, nn); add(4, nn);                            // lmv kept
+    const long long kwch = (nn + kKwChunk - 1) / kKwChunk + 1;
+    add(4, (2 * kwch + 1) * kMtBuckets);                // kwtab
     add(32, ecap);                                      // ent (two int4 per entry)
     add(4, kk);                                         // bpair
     add(4, pp); add(4, pp); add(4, pp); add(4, pp);     // pa pb cnt fil
@@ -70,6 +72,8 @@ fr_status ensure_mt(fr_ctx *ctx, int n, int nnz, int k, int P) {
     m.tch = carve_mt<int>(p, nn); m.cur = carve_mt<unsigned long long>(p, nn); m.epoch = carve_mt<unsigned>(p, 1);
     m.mvd = carve_mt<unsigned char>(p, nn);
     m.lmv = carve_mt<int4>(p, nn); m.kept = carve_mt<int>(p, nn);
+    m.kwtab = carve_mt<int>(p, (2 * kwch + 1) * kMtBuckets);
+    m.kwchunks = (int)kwch;
     m.ent = carve_mt<int4>(p, 2 * ecap);
     m.bpair = carve_mt<int>(p, kk);
     m.pa = carve_mt<int>(p, pp); m.pb = carve_mt<int>(p, pp); m.cnt = carve_mt<int>(p, pp); m.fil = carve_mt<int>(p, pp);

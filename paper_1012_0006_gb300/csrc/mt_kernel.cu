@@ -795,49 +795,114 @@ __global__ void __launch_bounds__(kMtTPB) kw_gain_kernel(GraphDev G, MtDev m, Ct
     }
 }
 
-// The round's search: one warp queues the start set in its order and searches.
-// res: gain kept, tried, kept; stopped = 1 if the KaSPar rule stopped the search.
-__global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, Ctl *ctl) {
-    __shared__ MtShared S;
-    const int lane = threadIdx.x;
-    if (__ldcg(&ctl->error)) return;
-    for (int i = lane; i < G.k; i += 32) S.bw[i] = m.bw[i];
-    for (int i = lane; i < kMtBuckets; i += 32) S.top[i] = -1;
-    for (int i = lane; i < kMtBuckets / 32; i += 32) S.bits[i] = 0;
-    __syncwarp();
-    const unsigned long long tseed = splitmix64(~m.seed);
+// The round's queue, built on the grid: the start set pushed in its order makes bucket
+// stacks in which an entry lies on the entry of the same bucket before it.  Each warp
+// takes a chunk of kKwChunk entries and links them within the chunk (32 at a time, a
+// shared-memory table of each bucket's last entry so far); kw_stitch_kernel then finds,
+// per chunk and bucket, the last entry of the chunks before it, and kw_fix_kernel links
+// each chunk's first entry of a bucket to it.  Entries as mt_push writes them.
+constexpr int kKwWarps = 4;   // warps per CTA of kw_stack_kernel (a 2,048-entry table each)
+
+__global__ void __launch_bounds__(32 * kKwWarps) kw_stack_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    __shared__ int s_last[kKwWarps][kMtBuckets];
+    if (__ldcg(&ctl->error)) return;   // (a gain out of range left the packed keys unwritten)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int ns = m.cnt[0];
+    const int nch = (ns + kKwChunk - 1) / kKwChunk;
+    const int chunk = blockIdx.x * kKwWarps + wid;
+    if (chunk >= nch || chunk >= m.kwchunks) return;   // (the whole warp leaves together)
     unsigned epoch = *m.epoch + 1;
     if (epoch == 0) epoch = 1;
-    bool bad = false;
-    long long nxt = 0;
-    for (int base = 0; base < ns; base += 32) {
+    int *last = s_last[wid];
+    for (int b = lane; b < kMtBuckets; b += 32) last[b] = -1;
+    __syncwarp();
+    const int c0 = chunk * kKwChunk, c1 = min(ns, c0 + kKwChunk);
+    for (int base = c0; base < c1; base += 32) {
         const int i = base + lane;
-        const bool push = i < ns;
-        int u = -1, g = 0, t = 0, pu = 0, cw = 0, u0 = 0, u1 = 0;
-        if (push) {
+        const bool valid = i < c1;
+        int u = 0, b = 0, t = 0, pu = 0, cw = 0, u0 = 0, u1 = 0;
+        if (valid) {
             const unsigned long long pk = m.tkey[i];
             u = m.tv[i];
-            g = (int)(pk >> 32) - kMtGmax;
+            b = min((int)(pk >> 32), kMtBuckets - 1);   // (always in range: the gains were checked)
             t = (int)(unsigned)pk;
             pu = G.part[u];
             cw = __ldg(G.vwgt + u);
             u0 = __ldg(G.xadj + u);
             u1 = __ldg(G.xadj + u + 1);
         }
-        const unsigned pm = __ballot_sync(kFull, push);
-        if (nxt + __popc(pm) > m.ecap) {   // (never: ecap >= n + nnz + 64)
-            if (lane == 0) fail(ctl, E_TOO_LARGE, 807);
-            bad = true;
-            break;
+        const unsigned grp = __match_any_sync(kFull, valid ? b : -1 - lane);
+        const unsigned lower = grp & mt_lanemask_lt();
+        int below = -1;
+        if (valid) below = lower ? base + 31 - __clz(lower) : last[b];
+        __syncwarp();
+        if (valid) {
+            m.ent[2LL * i] = make_int4(u, below, 1, t);
+            m.ent[2LL * i + 1] = make_int4(pu, cw, u0, u1);
+            m.cur[u] = ((unsigned long long)epoch << 32) | (unsigned long long)(unsigned)i;
+            if ((grp & ~lower & ~(1u << lane)) == 0) last[b] = i;   // highest lane of its bucket
         }
-        mt_push(S, m, pm, push, g + kMtGmax, u, t, pu, cw, u0, u1, epoch, nxt, lane);
-        nxt += __popc(pm);
+        __syncwarp();
     }
+    int *cl = m.kwtab + (long long)chunk * kMtBuckets;
+    for (int b = lane; b < kMtBuckets; b += 32) cl[b] = last[b];
+}
+
+// One thread per bucket: over the chunks in order, the last entry before each chunk,
+// and the bucket's top after all of them.
+__global__ void __launch_bounds__(256) kw_stitch_kernel(MtDev m) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= kMtBuckets) return;
+    const int ns = m.cnt[0];
+    const int nch = min((ns + kKwChunk - 1) / kKwChunk, m.kwchunks);
+    const int *cl = m.kwtab;
+    int *prev = m.kwtab + (long long)m.kwchunks * kMtBuckets;
+    int carry = -1;
+    for (int k = 0; k < nch; ++k) {
+        prev[(long long)k * kMtBuckets + b] = carry;
+        const int p = cl[(long long)k * kMtBuckets + b];
+        if (p >= 0) carry = p;
+    }
+    m.kwtab[2LL * m.kwchunks * kMtBuckets + b] = carry;
+}
+
+__global__ void __launch_bounds__(kMtTPB) kw_fix_kernel(MtDev m, Ctl *ctl) {
+    if (__ldcg(&ctl->error)) return;
+    const int ns = m.cnt[0];
+    const int *prev = m.kwtab + (long long)m.kwchunks * kMtBuckets;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+        int *below = reinterpret_cast<int *>(m.ent + 2LL * i) + 1;
+        if (*below >= 0) continue;
+        const int b = min((int)(m.tkey[i] >> 32), kMtBuckets - 1);
+        *below = prev[(long long)(i / kKwChunk) * kMtBuckets + b];
+    }
+}
+
+// The round's search: one warp takes the queue the grid built and searches.
+// res: gain kept, tried, kept; stopped = 1 if the KaSPar rule stopped the search.
+__global__ void __launch_bounds__(32, 1) kw_search_kernel(GraphDev G, MtDev m, Ctl *ctl) {
+    __shared__ MtShared S;
+    const int lane = threadIdx.x;
+    if (__ldcg(&ctl->error)) return;
+    for (int i = lane; i < G.k; i += 32) S.bw[i] = m.bw[i];
+    const int *top = m.kwtab + 2LL * m.kwchunks * kMtBuckets;
+    for (int i = lane; i < kMtBuckets; i += 32) S.top[i] = top[i];
+    for (int w = lane; w < kMtBuckets / 32; w += 32) {
+        unsigned word = 0;
+        for (int j = 0; j < 32; ++j) word |= (top[w * 32 + j] >= 0 ? 1u : 0u) << j;
+        S.bits[w] = word;
+    }
+    __syncwarp();
+    const unsigned long long tseed = splitmix64(~m.seed);
+    const int ns = m.cnt[0];
+    unsigned epoch = *m.epoch + 1;
+    if (epoch == 0) epoch = 1;
+    bool bad = false;
+    long long nxt = ns;
     long long best = 0;
     int nm = 0, best_len = 0, kbase = 0;
     bool stopped = false;
-    if (!bad) mt_search(G, m, S, ctl, 0, false, epoch, nxt, G.Lmax, tseed, lane, bad, best, nm, best_len, stopped);
+    mt_search(G, m, S, ctl, 0, false, epoch, nxt, G.Lmax, tseed, lane, bad, best, nm, best_len, stopped);
     mt_finish(G, m, S, nm, best_len, lane, false, kbase);
     for (int i = lane; i < G.k; i += 32) m.bw[i] = S.bw[i];
     if (lane == 0) {
@@ -865,8 +930,13 @@ cudaError_t launch_kway_round(const GraphDev &G, const MtDev &md, Ctl *ctl, int 
     kw_place_kernel<<<grid, kMtTPB, 0, st>>>(G, md, need, rs, bbits);
     kw_bsort_kernel<<<(nb + kMtTPB - 1) / kMtTPB, kMtTPB, 0, st>>>(md, nb);
     kw_gain_kernel<<<grid, kMtTPB, 0, st>>>(G, md, ctl);
+    // the queue: chunks of the start set linked by warps, stitched per bucket, fixed up
+    const int chunks = (G.n + kKwChunk - 1) / kKwChunk;   // >= the start set's chunks
+    kw_stack_kernel<<<(chunks + kKwWarps - 1) / kKwWarps, 32 * kKwWarps, 0, st>>>(G, md, ctl);
+    kw_stitch_kernel<<<(kMtBuckets + 255) / 256, 256, 0, st>>>(md);
+    kw_fix_kernel<<<grid, kMtTPB, 0, st>>>(md, ctl);
     kw_search_kernel<<<1, 32, 0, st>>>(G, md, ctl);
-    *nl += 6;
+    *nl += 9;
     return cudaGetLastError();
 }
 

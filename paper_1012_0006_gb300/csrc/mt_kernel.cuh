@@ -11,6 +11,7 @@ namespace fr {
 constexpr int kMtGmax = 1023;                 // |gain| bound (max weighted degree)
 constexpr int kMtBuckets = 2 * kMtGmax + 2;   // gain buckets of the single queue
 constexpr int kMtMaxK = 1024;                 // block weights cached in shared memory
+constexpr int kKwChunk = 1024;                // start entries per warp when a round's queue is built
 
 // Totals of one pass.
 struct MtRes {
@@ -29,6 +30,10 @@ struct MtDev {
     unsigned char *mvd;          // [n] moved by the current search
     int4 *lmv;                   // [n] moves of the current search: {vertex, source, target, weight}
     int *kept;                   // [n] the pass's kept movers (a vertex moves at most once in a pass)
+    int *kwtab;                  // global rounds: per chunk of the start set and gain bucket, the
+                                 // chunk's last entry, then the last entry before the chunk
+                                 // (2 x kwchunks x kMtBuckets), then each bucket's top (kMtBuckets)
+    int kwchunks;                // chunks the table holds (ceil(n / kKwChunk) + 1)
     int4 *ent;                   // [2 ecap] bucket stack entries of the current search:
                                  //   {vertex, entry below, live, target}, {block, weight, adjacency range}
     int *bpair;                  // [k] pair of the pass that the block belongs to, -1 none
